@@ -1,0 +1,246 @@
+"""FP64 CPU oracle for the Urchin reverse ray tracer — TEST INFRASTRUCTURE.
+
+Plain, slow restatement of what the paper (Altay & Theuns, arXiv:1304.4235)
+defines, written in C (``urchin_oracle.c``) and wrapped here with ctypes.
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline/reference
+leg of ``bench.py`` may import this package.  It shares no code with the CUDA
+library and the CUDA library never imports it.
+
+Functions (FP64 throughout; each follows the passage named in the C source):
+  sigma_th, sigma(E, which), spectrum(...)        App. C1, Eq. gamma
+  m4_shape(q), gt_shape(q), chord(kernel, b,u1,u2) Eq. spline, Eq. Gt, I(h,b,z1,z2)
+  columns(...), columns_points(...)               Eq. nhi, Eq. colden (brute force)
+  healpix(nside)                                  Sec. 3.2 (Gorski et al. 2005)
+  gamma(...)                                      Eq. gamma_shld
+  rates(T), xeq(...)                              App. C3, Eqs. xroots / xphys
+  solve(...)                                      Sec. 4 iteration driver (Jacobi)
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "urchin_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liburchin_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+KERNEL_M4 = 0
+KERNEL_GT = 1
+XSEC_VERNER = 0
+XSEC_HYDROGENIC = 1
+XSEC_POWERLAW = 2
+CASE_A, CASE_B, CASE_AUTO = 0, 1, 2
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (-O2, OpenMP, strict IEEE: no fast-math)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared",
+                           "-o", tmp, _SRC, "-lm"])
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = C.CDLL(build())
+            d, i, i64, vp = C.c_double, C.c_int, C.c_int64, C.c_void_p
+            sig = {
+                "oracle_sigma_th": (d, []),
+                "oracle_E_th": (d, []),
+                "oracle_sigma_hydrogenic": (d, [d, d]),
+                "oracle_sigma_powerlaw": (d, [d]),
+                "oracle_sigma_verner": (d, [d]),
+                "oracle_sigma": (d, [i, d]),
+                "oracle_spectrum": (None, [i, vp, vp, i, d, vp, vp]),
+                "oracle_m4_shape": (d, [d]),
+                "oracle_gt_shape": (d, [d]),
+                "oracle_chord_m4": (d, [d, d, d]),
+                "oracle_chord_gt": (d, [d, d, d]),
+                "oracle_chord": (d, [i, d, d, d]),
+                "oracle_columns_points": (None, [i64, vp, vp, vp, vp, vp, vp, i, d, d,
+                                                 vp, i64, vp, i, d, i, vp]),
+                "oracle_columns": (None, [i64, vp, vp, vp, vp, vp, vp, i, d, d,
+                                          vp, i64, vp, i, d, i, vp]),
+                "oracle_healpix": (None, [i, vp]),
+                "oracle_gamma": (None, [vp, i64, i, i, vp, vp, vp, vp]),
+                "oracle_rates": (None, [d, vp, vp, vp]),
+                "oracle_xeq": (d, [d, d, d, d, i]),
+                "oracle_solve": (i, [i64, vp, vp, vp, vp, vp, vp, vp, d, i, d, d,
+                                     vp, i, d, i, i, vp, vp, d, d, i, i, vp, vp, vp, vp]),
+                "oracle_num_threads": (i, []),
+            }
+            for name, (res, args) in sig.items():
+                f = getattr(lib, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _p(a):
+    return a.ctypes.data_as(C.c_void_p) if a is not None else None
+
+
+# -- cross sections and spectrum (App. C1) ----------------------------------
+def sigma_th() -> float:
+    return _load().oracle_sigma_th()
+
+
+def E_th() -> float:
+    return _load().oracle_E_th()
+
+
+def sigma(E_eV, which: int = XSEC_VERNER):
+    lib = _load()
+    return np.array([lib.oracle_sigma(which, float(e)) for e in np.atleast_1d(E_eV)])
+
+
+def sigma_hydrogenic(E_eV, Z=1.0):
+    lib = _load()
+    return np.array([lib.oracle_sigma_hydrogenic(float(e), float(Z)) for e in np.atleast_1d(E_eV)])
+
+
+def spectrum(edges, J, gamma_thin: float, xsec: int = XSEC_VERNER):
+    """s_j = sigma_j / sigma_th and w_j (sum w = gamma_thin)."""
+    edges, J = _f64(edges), _f64(J)
+    F = J.shape[0]
+    s = np.zeros(F)
+    w = np.zeros(F)
+    _load().oracle_spectrum(F, _p(edges), _p(J), xsec, gamma_thin, _p(s), _p(w))
+    return s, w
+
+
+# -- kernels (Eq. spline, Eq. Gt) --------------------------------------------
+def m4_shape(q: float) -> float:
+    return _load().oracle_m4_shape(float(q))
+
+
+def gt_shape(q: float) -> float:
+    return _load().oracle_gt_shape(float(q))
+
+
+def chord(kernel: int, b: float, u1: float, u2: float) -> float:
+    """int_{u1}^{u2} shape(sqrt(b^2+u^2)) du, lengths in units of h."""
+    return _load().oracle_chord(kernel, float(b), float(u1), float(u2))
+
+
+# -- columns (Eq. colden) ----------------------------------------------------
+def _particles(w):
+    pos = np.asarray(w.pos, dtype=np.float64)
+    return (np.ascontiguousarray(pos[:, 0]), np.ascontiguousarray(pos[:, 1]),
+            np.ascontiguousarray(pos[:, 2]), _f64(w.h), _f64(w.mass_H))
+
+
+def columns(w, x, dirs, origins=None, l_ray=None, kernel=KERNEL_M4):
+    """Threshold optical depth tau[o, k] = sigma_th N_HI of ray k from particle
+    origins[o] (all particles when None).  ``w`` is a workloads.Workload."""
+    px, py, pz, h, m = _particles(w)
+    x = _f64(x)
+    dirs = _f64(dirs).reshape(-1, 3)
+    R = dirs.shape[0]
+    org = None if origins is None else np.ascontiguousarray(origins, dtype=np.int64)
+    n_orig = w.n if org is None else org.shape[0]
+    out = np.zeros((n_orig, R))
+    _load().oracle_columns(w.n, _p(px), _p(py), _p(pz), _p(h), _p(m), _p(x),
+                           int(w.periodic), float(w.box), float(w.unit_cm),
+                           _p(org), n_orig, _p(dirs), R,
+                           float(w.l_ray if l_ray is None else l_ray), kernel, _p(out))
+    return out
+
+
+def columns_points(w, x, points, dirs, l_ray, kernel=KERNEL_M4):
+    px, py, pz, h, m = _particles(w)
+    x = _f64(x)
+    pts = _f64(points).reshape(-1, 3)
+    dirs = _f64(dirs).reshape(-1, 3)
+    out = np.zeros((pts.shape[0], dirs.shape[0]))
+    _load().oracle_columns_points(w.n, _p(px), _p(py), _p(pz), _p(h), _p(m), _p(x),
+                                  int(w.periodic), float(w.box), float(w.unit_cm),
+                                  _p(pts), pts.shape[0], _p(dirs), dirs.shape[0],
+                                  float(l_ray), kernel, _p(out))
+    return out
+
+
+# -- rays (Sec. 3.2) ---------------------------------------------------------
+def healpix(nside: int) -> np.ndarray:
+    out = np.zeros((12 * nside * nside, 3))
+    _load().oracle_healpix(nside, _p(out))
+    return out
+
+
+# -- Gamma (Eq. gamma_shld) --------------------------------------------------
+def gamma(tau, s, w):
+    tau = _f64(tau)
+    n_orig, R = tau.shape
+    s, w = _f64(s), _f64(w)
+    g = np.zeros(n_orig)
+    te = np.zeros(n_orig)
+    _load().oracle_gamma(_p(tau), n_orig, R, s.shape[0], _p(s), _p(w), _p(g), _p(te))
+    return g, te
+
+
+# -- rates and equilibrium (App. C3) -----------------------------------------
+def rates(T: float):
+    a = (C.c_double * 3)()
+    lib = _load()
+    aA, aB, gc = C.c_double(), C.c_double(), C.c_double()
+    lib.oracle_rates(float(T), C.byref(aA), C.byref(aB), C.byref(gc))
+    del a
+    return aA.value, aB.value, gc.value
+
+
+def xeq(Gamma, nH, T, y=0.0, caseB=False):
+    lib = _load()
+    G, nH, T, cb = np.broadcast_arrays(np.atleast_1d(np.asarray(Gamma, dtype=np.float64)),
+                                       np.asarray(nH, dtype=np.float64),
+                                       np.asarray(T, dtype=np.float64),
+                                       np.asarray(caseB, dtype=bool))
+    return np.array([lib.oracle_xeq(float(g), float(n), float(t), float(y), int(c))
+                     for g, n, t, c in zip(G, nH, T, cb)])
+
+
+# -- driver (Sec. 4) ---------------------------------------------------------
+def solve(w, s, wts, dirs, tol=1e-3, tau_skip=1e-4, max_iter=100, case_rule=CASE_AUTO,
+          kernel=KERNEL_M4, y=0.0, x_start=None, sweeps=None, l_ray=None):
+    """Jacobi iteration of Sec. 4.  ``sweeps`` = exact sweep count (step-matched
+    mode) instead of the tolerance test.  Returns (x, frozen, stats) with
+    stats = dict(sweeps, max_rel_dx, rays, converged)."""
+    px, py, pz, h, m = _particles(w)
+    nH, T = _f64(w.nH), _f64(w.T)
+    dirs = _f64(dirs).reshape(-1, 3)
+    s, wts = _f64(s), _f64(wts)
+    x = np.zeros(w.n)
+    frozen = np.zeros(w.n, dtype=np.int32)
+    st = np.zeros(3)
+    xs = None if x_start is None else _f64(x_start)
+    mi = -int(sweeps) if sweeps is not None else int(max_iter)
+    rc = _load().oracle_solve(w.n, _p(px), _p(py), _p(pz), _p(h), _p(m), _p(nH), _p(T),
+                              float(y), int(w.periodic), float(w.box), float(w.unit_cm),
+                              _p(dirs), dirs.shape[0],
+                              float(w.l_ray if l_ray is None else l_ray), kernel,
+                              s.shape[0], _p(s), _p(wts), float(tol), float(tau_skip),
+                              mi, case_rule, _p(xs), _p(x), _p(frozen), _p(st))
+    return x, frozen.astype(bool), dict(sweeps=int(st[0]), max_rel_dx=float(st[1]),
+                                        rays=float(st[2]), converged=(rc == 0))
+
+
+def num_threads() -> int:
+    return _load().oracle_num_threads()

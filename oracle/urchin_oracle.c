@@ -1,0 +1,508 @@
+/*
+ * FP64 CPU oracle for Urchin reverse ray tracing (Altay & Theuns, arXiv:1304.4235).
+ *
+ * TEST INFRASTRUCTURE.  This file is the plain, slow, obviously-correct
+ * restatement of what the paper defines, used only to check the CUDA library:
+ * only the test-suite, the smoke check and the benchmark's CPU-baseline /
+ * reference leg load it.  It shares no code, header, table or constant
+ * generator with the CUDA path and never calls it.
+ *
+ * Every function below states the passage it follows.  Readings where the
+ * paper is silent or garbled:
+ *   - Verner et al. (1996) H I fit: the printed form lacks the exponent -P on
+ *     (1 + sqrt(x/x_a)); the published fit has it, and only with it does
+ *     sigma(13.6 eV) come out at sigma_th (App. C1, Eq. sigma_ver).
+ *   - Rate coefficients (App. C3 points to fits in Theuns et al. 1998, not
+ *     printed): alpha_A, alpha_B and collisional ionisation gamma from the
+ *     Hui & Gnedin (1997) fits.
+ *   - Root of the Riccati quadratic (Eq. xroots, x_-): evaluated as
+ *     2P / (-Q + sqrt(Q^2 - 4PR)), the same root by Vieta's formula, which
+ *     does not cancel when Gamma >> alpha n_H.
+ *   - Update order: Jacobi (every Gamma of a sweep from the previous sweep's
+ *     x), the order-independent variant Sec. 4 allows for parallel codes.
+ *   - Rays start at the particle centre and sum every particle whose
+ *     smoothing sphere they cross, the particle itself included (Eq. colden);
+ *     periodic boxes add every periodic image within reach.
+ *   - Frequency quadrature: w_j ~ J(nu_j) sigma(nu_j) / (h nu_j) (nu_{j+1/2}
+ *     - nu_{j-1/2}) at geometric bin centres, rescaled so sum_j w_j =
+ *     Gamma_thin (Eq. gamma and Sec. 3.3.3, ~100 bins).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_PI 3.14159265358979323846
+#define OR_KERNEL_M4 0
+#define OR_KERNEL_GT 1
+
+/* ------------------------------------------------------------------------ */
+/* Photoionisation cross sections, App. C1.                                 */
+/* ------------------------------------------------------------------------ */
+
+/* Eq. sigma_ana: sigma_th = 2^9 pi / (3 e^4) alpha_fs pi a_0^2 (CODATA 2018). */
+double oracle_sigma_th(void)
+{
+    const double alpha_fs = 7.2973525693e-3;
+    const double a0_cm = 5.29177210903e-9;
+    return pow(2.0, 9.0) * OR_PI / (3.0 * exp(4.0)) * alpha_fs * OR_PI * a0_cm * a0_cm;
+}
+
+/* Ionisation threshold of H I in eV (13.6057 eV, Rydberg energy). */
+double oracle_E_th(void) { return 13.605693122994; }
+
+/* Eq. sigma_ana: exact hydrogenic cross section of an ion of charge Z,
+ * threshold Z^2 E_th; zero below threshold. */
+double oracle_sigma_hydrogenic(double E_eV, double Z)
+{
+    double Eth = Z * Z * oracle_E_th();
+    if (E_eV < Eth) return 0.0;
+    double r = E_eV / Eth;            /* nu / nu_th */
+    double eps = sqrt(r - 1.0);
+    double shape;
+    if (eps < 1e-6) {
+        shape = 1.0;                  /* limit eps -> 0 of the bracket */
+    } else {
+        shape = exp(4.0 - 4.0 * atan(eps) / eps) / (1.0 - exp(-2.0 * OR_PI / eps));
+    }
+    return oracle_sigma_th() / (Z * Z) * pow(1.0 / r, 4.0) * shape;
+}
+
+/* Eq. sigma_pwr: sigma_th (nu/nu_th)^-3. */
+double oracle_sigma_powerlaw(double E_eV)
+{
+    if (E_eV < oracle_E_th()) return 0.0;
+    return oracle_sigma_th() * pow(E_eV / oracle_E_th(), -3.0);
+}
+
+/* Eq. sigma_ver with the exponent -P restored (see header):
+ * sigma = sigma_0 (x-1)^2 x^(0.5P-5.5) (1 + sqrt(x/x_a))^-P, x = E/E_0. */
+double oracle_sigma_verner(double E_eV)
+{
+    if (E_eV < oracle_E_th()) return 0.0;
+    const double E0 = 0.4298, sigma0 = 5.475e4 * 1e-18, xa = 32.88, P = 2.963;
+    double x = E_eV / E0;
+    return sigma0 * (x - 1.0) * (x - 1.0) * pow(x, 0.5 * P - 5.5) * pow(1.0 + sqrt(x / xa), -P);
+}
+
+double oracle_sigma(int which, double E_eV)
+{
+    if (which == 1) return oracle_sigma_hydrogenic(E_eV, 1.0);
+    if (which == 2) return oracle_sigma_powerlaw(E_eV);
+    return oracle_sigma_verner(E_eV);
+}
+
+/* Binned spectrum for Eq. gamma_shld: s_j = sigma_j / sigma_th and weights
+ * w_j with sum_j w_j = Gamma_thin (Eq. gamma: Gamma = 4 pi int J sigma/(h nu)
+ * dnu; 4 pi and h drop out of the normalisation). */
+void oracle_spectrum(int F, const double* E_edges, const double* J, int xsec,
+                     double gamma_thin, double* s_out, double* w_out)
+{
+    double sth = oracle_sigma_th(), tot = 0.0;
+    for (int j = 0; j < F; ++j) {
+        double Ej = sqrt(E_edges[j] * E_edges[j + 1]);
+        double sj = oracle_sigma(xsec, Ej);
+        s_out[j] = sj / sth;
+        w_out[j] = J[j] * sj / Ej * (E_edges[j + 1] - E_edges[j]);
+        tot += w_out[j];
+    }
+    for (int j = 0; j < F; ++j) w_out[j] *= gamma_thin / tot;
+}
+
+/* ------------------------------------------------------------------------ */
+/* SPH kernels, Sec. 4.1.1.                                                  */
+/* ------------------------------------------------------------------------ */
+
+/* Eq. spline: M4 shape with the 8/(pi h^3) prefactor removed. */
+double oracle_m4_shape(double q)
+{
+    if (q < 0.0) q = -q;
+    if (q <= 0.5) return 1.0 - 6.0 * q * q + 6.0 * q * q * q;
+    if (q <= 1.0) return 2.0 * (1.0 - q) * (1.0 - q) * (1.0 - q);
+    return 0.0;
+}
+
+/* Eq. Gt constants: t = 2 pi^(1/6), A h = t, and the bracket
+ * D = erf(t) - 2 t exp(-t^2)/sqrt(pi) so that N = 8/(pi h^3) / D. */
+static double gt_t(void) { return 2.0 * pow(OR_PI, 1.0 / 6.0); }
+static double gt_D(void)
+{
+    double t = gt_t();
+    return erf(t) - 2.0 * t * exp(-t * t) / sqrt(OR_PI);
+}
+
+/* Eq. Gt shape with the 8/(pi h^3) prefactor removed: exp(-A^2 r^2) / D, r<=h. */
+double oracle_gt_shape(double q)
+{
+    if (q < 0.0) q = -q;
+    if (q > 1.0) return 0.0;
+    double t = gt_t();
+    return exp(-t * t * q * q) / gt_D();
+}
+
+/* Antiderivatives in u of q^n with q = sqrt(b^2 + u^2) (b, u in units of h):
+ *   int q   du = (u q + b^2 asinh(u/b)) / 2
+ *   int q^2 du = b^2 u + u^3 / 3
+ *   int q^3 du = u q^3 / 4 + 3 b^2 u q / 8 + 3 b^4 asinh(u/b) / 8
+ * (b^k asinh(u/b) -> 0 as b -> 0 for k >= 2). */
+static double b2_asinh(double b, double u, int power)
+{
+    if (b <= 0.0) return 0.0;
+    return pow(b, (double)power) * asinh(u / b);
+}
+static double Q1(double b, double u) { double q = sqrt(b * b + u * u); return 0.5 * (u * q + b2_asinh(b, u, 2)); }
+static double Q2(double b, double u) { return b * b * u + u * u * u / 3.0; }
+static double Q3(double b, double u)
+{
+    double q = sqrt(b * b + u * u);
+    return u * q * q * q / 4.0 + 3.0 * b * b * u * q / 8.0 + 3.0 * b2_asinh(b, u, 4) / 8.0;
+}
+/* inner piece 1 - 6q^2 + 6q^3 (q <= 1/2) and outer piece 2(1-q)^3 (1/2 < q <= 1) */
+static double m4_inner_prim(double b, double u) { return u - 6.0 * Q2(b, u) + 6.0 * Q3(b, u); }
+static double m4_outer_prim(double b, double u) { return 2.0 * u - 6.0 * Q1(b, u) + 6.0 * Q2(b, u) - 2.0 * Q3(b, u); }
+
+/* int_{u1}^{u2} M4shape(sqrt(b^2+u^2)) du for b in [0,1], u1 <= u2, both
+ * inside the chord |u| <= sqrt(1-b^2).  Closed form of the line integral
+ * through the M4 kernel used by Eq. colden. */
+double oracle_chord_m4(double b, double u1, double u2)
+{
+    if (b >= 1.0 || u2 <= u1) return 0.0;
+    double c = sqrt(1.0 - b * b);
+    if (u1 < -c) u1 = -c;
+    if (u2 > c) u2 = c;
+    if (u2 <= u1) return 0.0;
+    if (b >= 0.5) return m4_outer_prim(b, u2) - m4_outer_prim(b, u1);
+    double s = sqrt(0.25 - b * b);   /* |u| at which q = 1/2 */
+    double total = 0.0, lo, hi;
+    lo = u1; hi = fmin(u2, -s);                 /* outer piece, u < -s */
+    if (hi > lo) total += m4_outer_prim(b, hi) - m4_outer_prim(b, lo);
+    lo = fmax(u1, -s); hi = fmin(u2, s);        /* inner piece, |u| <= s */
+    if (hi > lo) total += m4_inner_prim(b, hi) - m4_inner_prim(b, lo);
+    lo = fmax(u1, s); hi = u2;                  /* outer piece, u > s */
+    if (hi > lo) total += m4_outer_prim(b, hi) - m4_outer_prim(b, lo);
+    return total;
+}
+
+/* Eq. I(h,b,z1,z2) for the truncated Gaussian in units of h, prefactor
+ * 8/(pi h^2) removed: exp(-t^2 b^2) sqrt(pi)/(2 t D) [erf(t z2) - erf(t z1)],
+ * limits clipped to the chord inside r <= h. */
+double oracle_chord_gt(double b, double u1, double u2)
+{
+    if (b >= 1.0 || u2 <= u1) return 0.0;
+    double c = sqrt(1.0 - b * b);
+    if (u1 < -c) u1 = -c;
+    if (u2 > c) u2 = c;
+    if (u2 <= u1) return 0.0;
+    double t = gt_t();
+    return exp(-t * t * b * b) * sqrt(OR_PI) / (2.0 * t * gt_D()) * (erf(t * u2) - erf(t * u1));
+}
+
+double oracle_chord(int kernel, double b, double u1, double u2)
+{
+    return kernel == OR_KERNEL_GT ? oracle_chord_gt(b, u1, u2) : oracle_chord_m4(b, u1, u2);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Columns, Eq. nhi / Eq. colden, brute force over all particles.           */
+/* ------------------------------------------------------------------------ */
+
+/* Threshold optical depth tau = sigma_th N_HI along the segment
+ * o + t dir, t in [0, l_ray], by direct summation over every particle j
+ * (and, for a periodic box of side L, over every periodic image of j that
+ * can reach the segment):
+ *     N_HI = sum_j (m_j x_j / m_p) int_0^L W(|r(t) - r_j| / h_j) dt.
+ * Lengths are in the caller's unit; unit_cm converts them to cm. */
+static double column_from_point(int64_t n, const double* px, const double* py, const double* pz,
+                                const double* h, const double* mass_H, const double* x,
+                                int periodic, double L, double unit_cm, int nimg,
+                                const double* o, const double* dir, double l_ray, int kernel)
+{
+    double sum = 0.0;
+    for (int64_t j = 0; j < n; ++j) {
+        double hj = h[j];
+        for (int a = -nimg; a <= nimg; ++a)
+        for (int bb = -nimg; bb <= nimg; ++bb)
+        for (int c = -nimg; c <= nimg; ++c) {
+            double dx = px[j] + (periodic ? a * L : 0.0) - o[0];
+            double dy = py[j] + (periodic ? bb * L : 0.0) - o[1];
+            double dz = pz[j] + (periodic ? c * L : 0.0) - o[2];
+            double tc = dx * dir[0] + dy * dir[1] + dz * dir[2];
+            /* impact parameter from |d x dir| */
+            double cx = dy * dir[2] - dz * dir[1];
+            double cy = dz * dir[0] - dx * dir[2];
+            double cz = dx * dir[1] - dy * dir[0];
+            double b2 = cx * cx + cy * cy + cz * cz;
+            if (b2 >= hj * hj) continue;
+            double half = sqrt(hj * hj - b2);
+            double t1 = fmax(0.0, tc - half), t2 = fmin(l_ray, tc + half);
+            if (t2 <= t1) continue;
+            double F = oracle_chord(kernel, sqrt(b2) / hj, (t1 - tc) / hj, (t2 - tc) / hj);
+            double hcm = hj * unit_cm;
+            sum += mass_H[j] * x[j] * (8.0 / OR_PI) / (hcm * hcm) * F;
+        }
+    }
+    return oracle_sigma_th() * sum;
+}
+
+static int image_range(int periodic, double L, int64_t n, const double* h, double l_ray)
+{
+    if (!periodic) return 0;
+    double hmax = 0.0;
+    for (int64_t j = 0; j < n; ++j) hmax = fmax(hmax, h[j]);
+    /* a segment of length l_ray starting inside [0,L)^3 reaches spheres whose
+     * centres lie within l_ray + hmax of the box */
+    return (int)ceil((l_ray + hmax) / L);
+}
+
+/* Rays from arbitrary points: tau_out[p*R + k] for point p, direction k. */
+void oracle_columns_points(int64_t n, const double* px, const double* py, const double* pz,
+                           const double* h, const double* mass_H, const double* x,
+                           int periodic, double L, double unit_cm,
+                           const double* points, int64_t n_points,
+                           const double* dirs, int R, double l_ray, int kernel, double* tau_out)
+{
+    int nimg = image_range(periodic, L, n, h, l_ray);
+    int64_t total = n_points * (int64_t)R;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t r = 0; r < total; ++r) {
+        int64_t p = r / R;
+        int k = (int)(r % R);
+        tau_out[r] = column_from_point(n, px, py, pz, h, mass_H, x, periodic, L, unit_cm, nimg,
+                                       points + 3 * p, dirs + 3 * k, l_ray, kernel);
+    }
+}
+
+/* Rays from particle centres (Sec. 3.2): origins[o] are particle indices
+ * (NULL = all particles); tau_out[o*R + k]. */
+void oracle_columns(int64_t n, const double* px, const double* py, const double* pz,
+                    const double* h, const double* mass_H, const double* x,
+                    int periodic, double L, double unit_cm,
+                    const int64_t* origins, int64_t n_orig,
+                    const double* dirs, int R, double l_ray, int kernel, double* tau_out)
+{
+    double* pts = (double*)malloc(sizeof(double) * 3 * (size_t)(n_orig > 0 ? n_orig : 1));
+    for (int64_t o = 0; o < n_orig; ++o) {
+        int64_t i = origins ? origins[o] : o;
+        pts[3 * o] = px[i]; pts[3 * o + 1] = py[i]; pts[3 * o + 2] = pz[i];
+    }
+    oracle_columns_points(n, px, py, pz, h, mass_H, x, periodic, L, unit_cm,
+                          pts, n_orig, dirs, R, l_ray, kernel, tau_out);
+    free(pts);
+}
+
+/* ------------------------------------------------------------------------ */
+/* HEALPix ray directions (Sec. 3.2; Gorski et al. 2005 ring scheme).       */
+/* ------------------------------------------------------------------------ */
+
+/* Pixel centres of the ring scheme, pixel p -> (z, phi):
+ * north cap rings i < N_side hold 4i pixels at z = 1 - i^2/(3 N_side^2),
+ * phi = pi/(2i) (j - 1/2); equatorial rings N_side <= i <= 3 N_side hold
+ * 4 N_side pixels at z = 4/3 - 2i/(3 N_side), phi = pi/(2 N_side) (j - s/2)
+ * with s = (i - N_side + 1) mod 2; the south cap mirrors the north. */
+void oracle_healpix(int nside, double* dirs)
+{
+    int64_t npix = 12LL * nside * nside;
+    int64_t ncap = 2LL * nside * (nside - 1);
+    for (int64_t p = 0; p < npix; ++p) {
+        double z, phi;
+        if (p < ncap) {
+            double ph = 0.5 * (double)(p + 1);
+            int64_t i = (int64_t)floor(sqrt(ph - sqrt(floor(ph)))) + 1;
+            int64_t j = p + 1 - 2 * i * (i - 1);
+            z = 1.0 - (double)(i * i) / (3.0 * nside * nside);
+            phi = OR_PI / (2.0 * i) * ((double)j - 0.5);
+        } else if (p < npix - ncap) {
+            int64_t pp = p - ncap;
+            int64_t i = pp / (4 * nside) + nside;
+            int64_t j = pp % (4 * nside) + 1;
+            int64_t s = (i - nside + 1) % 2;
+            z = 4.0 / 3.0 - 2.0 * (double)i / (3.0 * nside);
+            phi = OR_PI / (2.0 * nside) * ((double)j - 0.5 * (double)s);
+        } else {
+            int64_t pp = npix - p;
+            double ph = 0.5 * (double)pp;
+            int64_t i = (int64_t)floor(sqrt(ph - sqrt(floor(ph)))) + 1;
+            int64_t j = 4 * i + 1 - (pp - 2 * i * (i - 1));
+            z = -1.0 + (double)(i * i) / (3.0 * nside * nside);
+            phi = OR_PI / (2.0 * i) * ((double)j - 0.5);
+        }
+        double st = sqrt(fmax(0.0, 1.0 - z * z));
+        dirs[3 * p] = st * cos(phi);
+        dirs[3 * p + 1] = st * sin(phi);
+        dirs[3 * p + 2] = z;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Shielded photoionisation rate, Eq. gamma_shld.                           */
+/* ------------------------------------------------------------------------ */
+
+/* Gamma_i = (1/N_ray) sum_k sum_j w_j exp(-s_j tau_ik), the 4 pi of
+ * Eq. gamma_shld being absorbed in w (sum_j w_j = Gamma_thin), and
+ * tau_eff = -ln(Gamma_i / Gamma_thin). */
+void oracle_gamma(const double* tau, int64_t n_orig, int R, int F,
+                  const double* s, const double* w, double* gamma_out, double* tau_eff_out)
+{
+    double gthin = 0.0;
+    for (int j = 0; j < F; ++j) gthin += w[j];
+#pragma omp parallel for schedule(static)
+    for (int64_t o = 0; o < n_orig; ++o) {
+        double g = 0.0;
+        for (int k = 0; k < R; ++k)
+            for (int j = 0; j < F; ++j)
+                g += w[j] * exp(-s[j] * tau[o * R + k]);
+        g /= (double)R;
+        gamma_out[o] = g;
+        if (tau_eff_out) tau_eff_out[o] = -log(g / gthin);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Rate coefficients (App. C3 refers to published fits; Hui & Gnedin 1997). */
+/* ------------------------------------------------------------------------ */
+
+/* lambda = 2 T_HI / T with T_HI = 157807 K.
+ *   alpha_A = 1.269e-13 lambda^1.503 / [1 + (lambda/0.522)^0.470]^1.923
+ *   alpha_B = 2.753e-14 lambda^1.500 / [1 + (lambda/2.740)^0.407]^2.242
+ *   gamma   = 21.11 T^-1.5 exp(-lambda/2) lambda^-1.089
+ *             / [1 + (lambda/0.354)^0.874]^1.101          (cm^3 s^-1) */
+void oracle_rates(double T, double* alphaA, double* alphaB, double* gamma_c)
+{
+    double lam = 2.0 * 157807.0 / T;
+    if (alphaA) *alphaA = 1.269e-13 * pow(lam, 1.503) / pow(1.0 + pow(lam / 0.522, 0.470), 1.923);
+    if (alphaB) *alphaB = 2.753e-14 * pow(lam, 1.500) / pow(1.0 + pow(lam / 2.740, 0.407), 2.242);
+    if (gamma_c) *gamma_c = 21.11 * pow(T, -1.5) * exp(-0.5 * lam) * pow(lam, -1.089)
+                            / pow(1.0 + pow(lam / 0.354, 0.874), 1.101);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Ionisation equilibrium, App. C3 (Eqs. dxdt, xroots, xphys).              */
+/* ------------------------------------------------------------------------ */
+
+/* Physical root x_- of R x^2 + Q x + P = 0 with
+ *   R = (gamma + alpha) n_H,  Q = -[Gamma + alpha n_H + R (1 + y)],
+ *   P = alpha n_H (1 + y),
+ * written 2P / (-Q + sqrt(Q^2 - 4PR)) (equal to x_- by Vieta).  The
+ * discriminant is evaluated through the identity
+ *   Q^2 - 4PR = (Gamma + R(1+y) - alpha n_H)^2 + 4 Gamma alpha n_H,
+ *   R(1+y) - alpha n_H = alpha n_H y + gamma n_H (1+y),
+ * whose terms are all non-negative, so it does not cancel when
+ * gamma << alpha (near-neutral gas). */
+double oracle_xeq(double Gamma, double nH, double T, double y, int caseB)
+{
+    double aA, aB, gc;
+    oracle_rates(T, &aA, &aB, &gc);
+    double alpha = caseB ? aB : aA;
+    double R = (gc + alpha) * nH;
+    double Q = -(Gamma + alpha * nH + R * (1.0 + y));
+    double P = alpha * nH * (1.0 + y);
+    double excess = alpha * nH * y + gc * nH * (1.0 + y);
+    double disc = (Gamma + excess) * (Gamma + excess) + 4.0 * Gamma * alpha * nH;
+    return 2.0 * P / (-Q + sqrt(disc));
+}
+
+/* Case choice (Sec. 3.3.3 / Sec. 4): 0 = always A, 1 = always B,
+ * 2 = B when tau_eff >= 1. */
+static int use_caseB(int case_rule, double tau_eff)
+{
+    if (case_rule == 0) return 0;
+    if (case_rule == 1) return 1;
+    return tau_eff >= 1.0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Iteration driver, Sec. 4 (initial x_thin, tau_skip freeze, dx_tol).      */
+/* ------------------------------------------------------------------------ */
+
+/* Runs the Jacobi iteration:
+ *   x <- x_thin (Gamma = Gamma_thin, tau_eff = 0);
+ *   sweep 0 traces every particle, freezes those with tau_eff < tau_skip at
+ *   x_thin for good and updates the others;
+ *   later sweeps trace the non-frozen particles only, computing every Gamma
+ *   from the previous sweep's x before any x changes;
+ *   stop when max over non-frozen particles of |x_new - x| / x < tol, or
+ *   after max_iter sweeps.
+ * If max_iter < 0 the run does exactly -max_iter sweeps (step-matched mode).
+ * x_out[n] receives the final x, frozen_out[n] (optional) 1 for frozen
+ * particles, stats[0] = sweeps done, stats[1] = last max |dx|/x,
+ * stats[2] = rays traced.  x_start (optional) replaces x_thin as the start
+ * (sweep 0 still applies the freeze rule).  Returns 0 when converged, 1 when
+ * the sweep limit ended the run. */
+int oracle_solve(int64_t n, const double* px, const double* py, const double* pz,
+                 const double* h, const double* mass_H, const double* nH, const double* T,
+                 double y, int periodic, double L, double unit_cm,
+                 const double* dirs, int R, double l_ray, int kernel,
+                 int F, const double* s, const double* w,
+                 double tol, double tau_skip, int max_iter, int case_rule,
+                 const double* x_start, double* x_out, int* frozen_out, double* stats)
+{
+    double gthin = 0.0;
+    for (int j = 0; j < F; ++j) gthin += w[j];
+    double* x = x_out;
+    int* frozen = (int*)calloc((size_t)n, sizeof(int));
+    double* tau = (double*)malloc(sizeof(double) * (size_t)n * R);
+    double* G = (double*)malloc(sizeof(double) * (size_t)n);
+    double* te = (double*)malloc(sizeof(double) * (size_t)n);
+    double* xn = (double*)malloc(sizeof(double) * (size_t)n);
+    int64_t* act = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+    for (int64_t i = 0; i < n; ++i)
+        x[i] = x_start ? x_start[i] : oracle_xeq(gthin, nH[i], T[i], y, use_caseB(case_rule, 0.0));
+    int fixed = max_iter < 0;
+    int limit = fixed ? -max_iter : max_iter;
+    int sweeps = 0, converged = 0;
+    double maxrel = 0.0, rays = 0.0;
+    int64_t nact = n;
+    for (int64_t i = 0; i < n; ++i) act[i] = i;
+    while (sweeps < limit) {
+        oracle_columns(n, px, py, pz, h, mass_H, x, periodic, L, unit_cm,
+                       act, nact, dirs, R, l_ray, kernel, tau);
+        oracle_gamma(tau, nact, R, F, s, w, G, te);
+        rays += (double)nact * R;
+        if (sweeps == 0) {
+            int64_t m = 0;
+            for (int64_t o = 0; o < nact; ++o) {
+                int64_t i = act[o];
+                if (te[o] < tau_skip) { frozen[i] = 1; continue; }
+                act[m] = i; G[m] = G[o]; te[m] = te[o]; ++m;
+            }
+            nact = m;
+        }
+        maxrel = 0.0;
+        for (int64_t o = 0; o < nact; ++o) {
+            int64_t i = act[o];
+            xn[o] = oracle_xeq(G[o], nH[i], T[i], y, use_caseB(case_rule, te[o]));
+            double rel = fabs(xn[o] - x[i]) / x[i];
+            if (rel > maxrel) maxrel = rel;
+        }
+        for (int64_t o = 0; o < nact; ++o) x[act[o]] = xn[o];
+        ++sweeps;
+        if (!fixed && maxrel < tol) { converged = 1; break; }
+    }
+    if (frozen_out) for (int64_t i = 0; i < n; ++i) frozen_out[i] = frozen[i];
+    if (stats) { stats[0] = sweeps; stats[1] = maxrel; stats[2] = rays; }
+    free(frozen); free(tau); free(G); free(te); free(xn); free(act);
+    return (fixed || converged) ? 0 : 1;
+}
+
+/* Directional derivative of the sweep map along v (for checking tangents):
+ * dtau = sigma_th sum_j (m_j v_j / m_p) int W dl is the column of Eq. colden
+ * with x replaced by v (columns are linear in x). */
+void oracle_columns_linear(int64_t n, const double* px, const double* py, const double* pz,
+                           const double* h, const double* mass_H, const double* v,
+                           int periodic, double L, double unit_cm,
+                           const int64_t* origins, int64_t n_orig,
+                           const double* dirs, int R, double l_ray, int kernel, double* out)
+{
+    oracle_columns(n, px, py, pz, h, mass_H, v, periodic, L, unit_cm,
+                   origins, n_orig, dirs, R, l_ray, kernel, out);
+}
+
+int oracle_num_threads(void)
+{
+#ifdef _OPENMP
+    extern int omp_get_max_threads(void);
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
