@@ -1,0 +1,343 @@
+#!/usr/bin/env python
+"""Benchmark of the reverse ray tracing solve (Altay & Theuns, arXiv:1304.4235)
+on the 262144-particle self-shielding halo: n_H = 10 (r/kpc)^-2 cm^-3 over
+r = 1-100 kpc, T = 1e4 K, h from 48 neighbours, 12 HEALPix rays per particle
+of length 200 kpc, 100 frequency bins (nu^-1.5, 13.6-54.4 eV), FP32 columns
+and spectral sum, FP64 equilibrium; iterate to max |dx|/x < 1e-3.
+
+One step = one full pass of the hot path on a fresh copy of the inputs:
+BVH build, then the solve from x_thin to convergence.  Metric: rays/s (all
+rays traced, value and tangent) and particle-updates/s, whole job.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--method plain|newton]
+                  [--segments recompute|store|auto] [--impl ours|reference]
+
+Under torchrun every rank solves its own copy of the halo (replicas; the
+method needs no exchange between independent halos) and rank 0 prints one
+JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "rays/s and particle-updates/s to converged x (rel 1e-3), Newton+adjoint vs plain"
+WORKLOAD = "halo_262144_nside1_l200kpc_F100"
+
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the traversal
+# kernel, from one ncu capture, keyed by the hash of the traversal sources at
+# capture time (reported as null once the kernel has changed).
+TRACE_TRAFFIC = {}
+
+
+def source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("trace.cu", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_1304_4235_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--method", choices=["plain", "newton"], default="plain")
+    ap.add_argument("--segments", choices=["recompute", "store", "auto"], default="recompute")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [v.strip() for v in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_sample(w, s, wts, dirs, seconds: float):
+    """The FP64 oracle on a bounded sample of the workload: one sweep (columns
+    of every ray, Gamma and the equilibrium x) for a seeded sample of origins
+    sized to take about `seconds` of CPU time."""
+    import oracle as O
+    import workloads as W
+
+    x0 = O.xeq(wts.sum(), w.nH, w.T, 0.0, False)
+
+    def run(count, seed):
+        org = W.random_origins(w.n, count, seed)
+        t0 = time.perf_counter()
+        tau = O.columns(w, x0, dirs, origins=org)
+        g, te = O.gamma(tau, s, wts)
+        O.xeq(g, w.nH[org], w.T[org], 0.0, te >= 1)
+        return time.perf_counter() - t0
+
+    t = run(32, 1)
+    count = int(min(w.n, max(32, 32 * seconds / max(t, 1e-3))))
+    dt = run(count, 2)
+    rays = count * dirs.shape[0]
+    return {"rays": rays, "origins": count, "seconds": dt, "cores": O.num_threads()}
+
+
+def reference_arm(args, w):
+    import oracle as O
+
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    e, J = w.spectrum()
+    s, wts = O.spectrum(e, J, w.gamma_thin)
+    dirs = O.healpix(w.nside)
+    per = max(2.0, args.cpu_seconds / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        oracle_sample(w, s, wts, dirs, per)
+    runs = [oracle_sample(w, s, wts, dirs, per) for _ in range(args.steps)]
+    rays = sum(r["rays"] for r in runs)
+    secs = sum(r["seconds"] for r in runs)
+    value = rays / secs
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
+        "particle_updates_per_s": sum(r["origins"] for r in runs) / secs,
+        "cpu_baseline": {"value": value, "unit": "rays/s", "cores": runs[0]["cores"], "kind": "oracle",
+                         "sample": f"{runs[0]['origins']} seeded origins x {dirs.shape[0]} rays, one sweep "
+                                   f"(brute-force columns over all {w.n} particles, Gamma, x) per step"},
+        "e2e": {"value": value, "unit": "rays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    import workloads as W
+
+    w = W.halo()
+    if args.impl == "reference":
+        reference_arm(args, w)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_1304_4235_gb300 import urchin as U
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    U.load()
+
+    method = U.METHOD_NEWTON if args.method == "newton" else U.METHOD_PLAIN
+    segs = {"recompute": U.SEG_RECOMPUTE, "store": U.SEG_STORE, "auto": U.SEG_AUTO}[args.segments]
+    pos = w.pos.astype(np.float32)
+    host = {
+        "px": np.ascontiguousarray(pos[:, 0]), "py": np.ascontiguousarray(pos[:, 1]),
+        "pz": np.ascontiguousarray(pos[:, 2]), "h": np.ascontiguousarray(w.h, dtype=np.float32),
+        "m": np.ascontiguousarray(w.mass_H), "nH": np.ascontiguousarray(w.nH),
+        "T": np.ascontiguousarray(w.T),
+    }
+    pinned = {k: torch.from_numpy(v).pin_memory() for k, v in host.items()}
+    d = {k: v.to(dev) for k, v in pinned.items()}
+    e, J = w.spectrum()
+    s_h, w_h = U.urchin_spectrum_weights(e, J, w.gamma_thin)
+    s_d, w_d = torch.from_numpy(s_h).to(dev), torch.from_numpy(w_h).to(dev)
+    dirs = U.urchin_healpix_dirs(w.nside)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(dd, x_out=None):
+        bvh = U.urchin_build_bvh(dd["px"], dd["py"], dd["pz"], dd["h"], dd["m"], w.periodic, w.box, w.unit_cm)
+        x = torch.empty(w.n, dtype=torch.float64, device=dev) if x_out is None else x_out
+        x, st = U.urchin_solve(bvh, dirs, w.l_ray, s_d, w_d, dd["nH"], dd["T"], x, tol=1e-3, tau_skip=1e-4,
+                               max_iter=200, method=method, segments=segs, precision=U.F32,
+                               case_rule=U.CASE_AUTO, profile=True, raise_not_converged=False)
+        bvh.close()
+        return x, st
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
+    for _ in range(args.warmup):
+        step(d)
+
+    clocks = Clocks(dev.index if dev.index is not None else 0)
+    stats = []
+    step_ms = []
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    launches0 = U.urchin_kernel_launches()
+    clocks.start()
+    for _ in range(args.steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        _, st = step(d)
+        b.record(stream)
+        b.synchronize()
+        step_ms.append(a.elapsed_time(b))
+        stats.append(st)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    launches = U.urchin_kernel_launches() - launches0
+
+    total_ms = sum(step_ms)
+    rays = sum(st["rays"] for st in stats)
+    updates = sum(st["particle_updates"] for st in stats)
+    hits = sum(st["hits"] for st in stats)
+    trace_s = sum(st["trace_s"] for st in stats)
+    trace_launches = sum(st["trace_launches"] for st in stats)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        c = torch.tensor([float(rays), float(updates)], dtype=torch.float64, device=dev)
+        dist.all_reduce(c, op=dist.ReduceOp.SUM)
+        rays, updates = float(c[0].item()), float(c[1].item())
+
+    # end to end through the public API with host buffers: pinned H2D of the
+    # inputs, build, solve, D2H of x, all inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        x_host = torch.empty(w.n, dtype=torch.float64).pin_memory()
+        e2e_ms, e2e_rays = [], 0
+        h2d = sum(v.numel() * v.element_size() for v in pinned.values())
+        d2h = x_host.numel() * x_host.element_size()
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize(dev)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            dd = {k: v.to(dev, non_blocking=True) for k, v in pinned.items()}
+            x, st = step(dd)
+            x_host.copy_(x, non_blocking=True)
+            b.record(stream)
+            b.synchronize()
+            e2e_ms.append(a.elapsed_time(b))
+            e2e_rays += st["rays"]
+        e2e = {"value": e2e_rays / (sum(e2e_ms) * 1e-3) * world, "unit": "rays/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    hbm, peak_kind = peaks()
+    alg_bytes = hits * 20 + rays / world * 4          # particle records + tau written
+    per_launch_bytes = alg_bytes / max(trace_launches, 1)
+    per_launch_s = trace_s / max(trace_launches, 1)
+    achieved = per_launch_bytes / per_launch_s / 1e9 if per_launch_s > 0 else None
+    traffic = TRACE_TRAFFIC.get(source_hash())
+    st0 = stats[-1]
+    line = {
+        "metric": METRIC, "value": rays / (total_ms * 1e-3), "unit": "rays/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "particles": w.n, "rays_per_particle": w.R, "l_ray_kpc": w.l_ray,
+                   "bins": w.F, "method": args.method, "segments": args.segments, "tol": 1e-3,
+                   "l2": "flushed before each step (256 MB write)"},
+        "particle_updates_per_s": updates / (total_ms * 1e-3),
+        "iterations": st0["iterations"], "n_active": st0["n_active"], "converged": bool(st0["converged"]),
+        "wall_s_to_converged": total_ms * 1e-3 / args.steps,
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": (achieved / hbm) if achieved else None, "traffic": traffic,
+                     "kernel": "k_trace<float,M4>", "peak_kind": peak_kind,
+                     "alg_bytes_per_launch": per_launch_bytes, "launch_ms": per_launch_s * 1e3,
+                     "hits_per_launch": hits / max(trace_launches, 1)},
+        "clocks": clk,
+        "e2e": e2e,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        import oracle as O
+        e_, J_ = w.spectrum()
+        so, wo = O.spectrum(e_, J_, w.gamma_thin)
+        r = oracle_sample(w, so, wo, O.healpix(w.nside), args.cpu_seconds)
+        line["cpu_baseline"] = {
+            "value": r["rays"] / r["seconds"], "unit": "rays/s", "cores": r["cores"], "kind": "oracle",
+            "sample": f"{r['origins']} seeded origins x {w.R} rays, one sweep (brute-force columns over all "
+                      f"{w.n} particles, Gamma, x), {r['seconds']:.1f} s"}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,254 @@
+/*
+ * urchin.h -- C ABI of the GB300 reverse ray tracer for self-shielding from
+ * the UV background (Altay & Theuns, "Urchin: A Reverse Ray Tracer for
+ * Astrophysical Applications", arXiv:1304.4235).
+ *
+ * The library computes, for every SPH gas particle, the hydrogen columns
+ * along N_ray HEALPix rays cast outward from the particle (Sec. 3.2,
+ * Eq. colden), folds them through a binned UV-background spectrum into the
+ * shielded photoionisation rate (Eq. gamma_shld), solves the ionisation
+ * equilibrium for the neutral fraction x (App. C3, Eq. xroots) and iterates
+ * to convergence (Sec. 4).  All arithmetic runs in CUDA kernels for sm_103a.
+ *
+ * Conventions shared by every entry point
+ *   - Pointers documented as "device" are CUDA device pointers owned by the
+ *     caller; "host" pointers are ordinary host memory read during the call.
+ *   - Calls are asynchronous on `stream` (NULL = legacy default stream)
+ *     unless stated otherwise; outputs are valid once the stream reaches
+ *     the call.  urchin_solve synchronises the stream (it reads a
+ *     convergence scalar once per sweep).
+ *   - Every call returns URCHIN_OK (0) or a negative URCHIN_ERR_* status; no
+ *     exception, abort or device trap crosses the ABI.  urchin_last_error()
+ *     returns a message for the calling thread's most recent failure.
+ *   - Lengths (positions, h, box side, l_ray) share one caller-chosen unit;
+ *     `unit_cm` converts it to cm.  Columns are returned as threshold
+ *     optical depth tau = sigma_th N_HI with sigma_th = 2^9 pi/(3 e^4)
+ *     alpha_fs pi a_0^2 = 6.3043e-18 cm^2 (App. C1, Eq. sigma_ana).
+ *   - Work arrays the library needs are taken from the stream-ordered
+ *     allocator of the calling device (cudaMallocAsync) and released on the
+ *     same stream before the call returns; urchin_build_bvh's result holds
+ *     device memory until urchin_free_bvh.
+ */
+#ifndef URCHIN_H
+#define URCHIN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define URCHIN_API __attribute__((visibility("default")))
+#else
+#define URCHIN_API
+#endif
+
+/* A cudaStream_t (the runtime's stream handle type). */
+typedef struct CUstream_st* urchin_stream_t;
+
+/* ---- status codes ------------------------------------------------------ */
+#define URCHIN_OK                 0
+#define URCHIN_ERR_ARG           -1   /* invalid argument (NULL, size, range)   */
+#define URCHIN_ERR_CUDA          -2   /* a CUDA runtime call failed             */
+#define URCHIN_ERR_NOMEM         -3   /* device allocation failed               */
+#define URCHIN_ERR_NOT_CONVERGED -4   /* solve hit max_iter before dx_tol       */
+#define URCHIN_ERR_NONFINITE     -5   /* NaN/Inf in an input or a result        */
+
+/* ---- options ----------------------------------------------------------- */
+#define URCHIN_KERNEL_M4        0     /* cubic spline, Eq. spline               */
+#define URCHIN_KERNEL_GT        1     /* truncated Gaussian, Eq. Gt             */
+#define URCHIN_F32              0     /* columns and spectral sum in float      */
+#define URCHIN_F64              1     /* everything in double                   */
+#define URCHIN_CASE_A           0     /* case A recombination everywhere        */
+#define URCHIN_CASE_B           1     /* case B recombination everywhere        */
+#define URCHIN_CASE_AUTO        2     /* case B iff tau_eff >= 1 (Sec. 4)       */
+#define URCHIN_XSEC_VERNER      0     /* Verner et al. 1996 fit, App. C1        */
+#define URCHIN_XSEC_HYDROGENIC  1     /* exact hydrogenic, Eq. sigma_ana        */
+#define URCHIN_XSEC_POWERLAW    2     /* sigma_th (nu/nu_th)^-3, Eq. sigma_pwr  */
+#define URCHIN_METHOD_PLAIN     0     /* Jacobi fixed point (Sec. 4)            */
+#define URCHIN_METHOD_NEWTON    1     /* Newton-Krylov on the same fixed point  */
+#define URCHIN_SEG_RECOMPUTE    0     /* trace the BVH every sweep              */
+#define URCHIN_SEG_STORE        1     /* store per-ray segment lists once       */
+#define URCHIN_SEG_AUTO         2     /* store when the lists fit in memory     */
+
+#define URCHIN_MAX_RAYS       192     /* HEALPix N_side <= 4                    */
+#define URCHIN_MAX_BINS      4096     /* frequency bins                         */
+
+/* ---- data -------------------------------------------------------------- */
+
+/* SPH particles, structure of arrays (Eq. nhi: r_i, h_i, m_i). */
+typedef struct {
+    int64_t       n;        /* particle count, >= 1                            */
+    const float*  pos_x;    /* device [n] position                             */
+    const float*  pos_y;    /* device [n]                                      */
+    const float*  pos_z;    /* device [n]                                      */
+    const float*  h;        /* device [n] smoothing length = kernel support
+                               radius (W vanishes at |r - r_i| = h_i), > 0     */
+    const double* mass_H;   /* device [n] hydrogen mass in proton masses
+                               (m_i / m_p of Eq. nhi), >= 0                    */
+} urchin_particles;
+
+/* Simulation volume.  Periodic boxes are the cube [0, L)^3; rays then sum
+ * every periodic image of every particle they reach. */
+typedef struct {
+    int    periodic;        /* 0 = isolated, 1 = periodic cube                 */
+    double L;               /* box side (length unit), > 0 when periodic       */
+    double unit_cm;         /* cm per length unit, > 0                         */
+} urchin_box;
+
+/* Binned UV-background spectrum (Eq. gamma_shld, Sec. 3.3.3):
+ * Gamma/Gamma_thin = (1/N_ray) sum_k sum_j w_j exp(-s_j tau_k) / sum_j w_j. */
+typedef struct {
+    int           F;        /* bins, 1..URCHIN_MAX_BINS                        */
+    const double* s;        /* device [F] sigma(nu_j) / sigma_th, >= 0         */
+    const double* w;        /* device [F] rate weights (s^-1), >= 0, with
+                               sum_j w_j = Gamma_thin > 0                      */
+} urchin_spectrum;
+
+/* Opaque bounding-volume hierarchy over the particles' smoothing spheres
+ * (Morton-ordered copy of the particle data plus a binary radix tree). */
+typedef struct urchin_bvh urchin_bvh;
+
+/* ---- entry points ------------------------------------------------------ */
+
+/* Message for this thread's most recent failing call ("" if none). */
+URCHIN_API const char* urchin_last_error(void);
+
+/* Library version string. */
+URCHIN_API const char* urchin_version(void);
+
+/* Number of CUDA kernels this library has launched in this process
+ * (instrumentation for benchmarks; no counterpart in the paper). */
+URCHIN_API int64_t urchin_kernel_launches(void);
+
+/* HEALPix ray directions (Sec. 3.2; App. A: N_pix = 12 N_side^2): the unit
+ * vectors to the pixel centres of the ring scheme of Gorski et al. (2005),
+ * written to host `dirs_out[12 nside^2 * 3]` (x, y, z per ray).  Host only,
+ * no GPU work.  Errors: ERR_ARG if nside < 1 or 12 nside^2 > URCHIN_MAX_RAYS
+ * or dirs_out is NULL. */
+URCHIN_API int urchin_healpix_dirs(int nside, double* dirs_out);
+
+/* Binned spectrum weights for Eq. gamma_shld from a sampled UVB (host only):
+ * E_edges[F+1] bin edges in eV (increasing, first >= 13.6057 eV), J[F] the
+ * specific intensity at the geometric bin centres (any amplitude).  Writes
+ * host s_out[F] = sigma(E_j)/sigma_th and w_out[F] proportional to
+ * J_j sigma(E_j) / E_j (E_{j+1/2} - E_{j-1/2}), normalised to
+ * sum w = gamma_thin (Eq. gamma with the 4 pi/h factors absorbed).
+ * `xsec` selects the cross section (URCHIN_XSEC_*).  Errors: ERR_ARG. */
+URCHIN_API int urchin_spectrum_weights(int F, const double* E_edges, const double* J, int xsec,
+                            double gamma_thin, double* s_out, double* w_out);
+
+/* Build the BVH (no counterpart in the paper, which does not describe its
+ * search structure): Morton codes of the sphere centres, radix sort, binary
+ * radix tree, bottom-up bounds, and a Morton-ordered copy of the particles.
+ * The particle arrays are only read during the call.  `*out` receives a
+ * library-owned object; release it with urchin_free_bvh.  The call
+ * synchronises `stream`.  Errors: ERR_ARG (NULL, n < 1, h <= 0 or
+ * non-positive sizes), ERR_NONFINITE (NaN/Inf in positions, h or mass),
+ * ERR_NOMEM, ERR_CUDA. */
+URCHIN_API int urchin_build_bvh(const urchin_particles* p, const urchin_box* box,
+                     urchin_bvh** out, urchin_stream_t stream);
+
+/* Release a BVH (NULL is ignored).  Synchronous. */
+URCHIN_API void urchin_free_bvh(urchin_bvh* bvh);
+
+/* Particle count of a BVH, or -1 for NULL. */
+URCHIN_API int64_t urchin_bvh_size(const urchin_bvh* bvh);
+
+/* Columns, Eq. colden: for origin o and direction k,
+ *   tau[o*R + k] = sigma_th sum_j (m_j x_j / m_p) int_0^{l_ray} W(|r_i + t n_k - r_j| / h_j) dt,
+ * summed over every particle (and periodic image) whose smoothing sphere
+ * the segment crosses, the origin particle included (its half chord).
+ *   x        device [n] neutral fractions (double, original particle order)
+ *   dirs     host [R*3] unit directions (e.g. from urchin_healpix_dirs)
+ *   R        1..URCHIN_MAX_RAYS
+ *   l_ray    segment length >= 0 (length unit)
+ *   origins  device [n_orig] particle indices (original order), or NULL for
+ *            all n particles (then n_orig must equal n)
+ *   kernel   URCHIN_KERNEL_M4 or URCHIN_KERNEL_GT
+ *   precision URCHIN_F32: tau_out is float[n_orig*R]; URCHIN_F64: double
+ * Errors: ERR_ARG, ERR_NOMEM, ERR_CUDA.  n_orig = 0 is a no-op. */
+URCHIN_API int urchin_trace_columns(const urchin_bvh* bvh, const double* x, const double* dirs, int R,
+                         double l_ray, const int32_t* origins, int64_t n_orig,
+                         int kernel, int precision, void* tau_out, urchin_stream_t stream);
+
+/* Shielded rate, Eq. gamma_shld: for each of n_orig particles with R columns
+ * tau[o*R + k] (float for URCHIN_F32, double for URCHIN_F64),
+ *   gamma_out[o]   = (1/R) sum_k sum_j w_j exp(-s_j tau_ok)     (device, double)
+ *   tau_eff_out[o] = -ln(gamma_out[o] / sum_j w_j)              (device, float;
+ *                    may be NULL)
+ * tau_eff stays finite where gamma underflows double.  Errors: ERR_ARG,
+ * ERR_CUDA. */
+URCHIN_API int urchin_gamma(const void* tau, int precision, int64_t n_orig, int R,
+                 const urchin_spectrum* sp, double* gamma_out, float* tau_eff_out,
+                 urchin_stream_t stream);
+
+/* Ionisation equilibrium, App. C3 (Eqs. dxdt, xroots): the physical root
+ * x_- of R x^2 + Q x + P = 0 with R = (gamma_c + alpha) n_H,
+ * Q = -[Gamma + alpha n_H + R (1+y)], P = alpha n_H (1+y), in FP64, where
+ * alpha = alpha_A or alpha_B(T) and gamma_c(T) are the Hui & Gnedin (1997)
+ * fits.  case_rule URCHIN_CASE_AUTO takes case B where tau_eff >= 1 (then
+ * tau_eff must not be NULL).  All arrays device [n], double except tau_eff.
+ * Errors: ERR_ARG, ERR_CUDA. */
+URCHIN_API int urchin_equilibrium(const double* gamma, const float* tau_eff, const double* nH,
+                       const double* T, int64_t n, int case_rule, double y,
+                       double* x_out, urchin_stream_t stream);
+
+typedef struct {
+    int             R;            /* rays per particle                         */
+    const double*   dirs;         /* host [R*3]                                */
+    double          l_ray;        /* ray length (length unit)                  */
+    urchin_spectrum spectrum;     /* device arrays                             */
+    const double*   nH;           /* device [n] hydrogen density (cm^-3)       */
+    const double*   T;            /* device [n] temperature (K)                */
+    double          y;            /* electrons from heavier elements per H     */
+    double          tol;          /* dx_tol: stop when max |dx|/x < tol        */
+    double          tau_skip;     /* freeze particles with tau_eff < tau_skip
+                                     after the first sweep                     */
+    int             max_iter;     /* sweep limit (plain) / Newton step limit   */
+    int             method;       /* URCHIN_METHOD_*                           */
+    int             segments;     /* URCHIN_SEG_*                              */
+    int             gmres_m;      /* Krylov dimension per Newton step          */
+    int             kernel;       /* URCHIN_KERNEL_*                           */
+    int             precision;    /* URCHIN_F32 / URCHIN_F64 (columns, Gamma)  */
+    int             case_rule;    /* URCHIN_CASE_*                             */
+    int             warm_start;   /* 0: start from x_thin; 1: from x_inout     */
+    int             profile;      /* 1: time every traversal with CUDA events
+                                     and count kernel-chord evaluations        */
+} urchin_solve_params;
+
+typedef struct {
+    int     iterations;           /* sweeps (plain) or Newton steps            */
+    int     traversals;           /* BVH traversals + stored-segment sweeps    */
+    int64_t rays;                 /* rays evaluated (value and tangent)        */
+    int64_t particle_updates;     /* x updates of non-frozen particles         */
+    int64_t n_active;             /* particles not frozen after sweep 0        */
+    int64_t nnz;                  /* stored segments (0 in recompute mode)     */
+    double  max_rel_dx;           /* last max |dx|/x over non-frozen particles */
+    double  wall_s;               /* host wall time of the call                */
+    int     converged;            /* 1 if max_rel_dx < tol                     */
+    int     segments_stored;      /* 1 if the stored-segment mode ran          */
+    int64_t hits;                 /* ray-sphere chord evaluations (profile=1)  */
+    double  trace_s;              /* GPU time of the traversals (profile=1)    */
+    int     trace_launches;       /* traversal kernel launches                 */
+} urchin_solve_stats;
+
+/* Iterate to the equilibrium neutral fraction (Sec. 4): x starts at x_thin
+ * (Gamma = Gamma_thin) unless warm_start; sweep 0 traces every particle and
+ * freezes those with tau_eff < tau_skip at their current x; each later sweep
+ * recomputes Gamma for all non-frozen particles from the previous sweep's x
+ * (Jacobi) and updates them; the run stops when max |dx|/x < tol.
+ * URCHIN_METHOD_NEWTON solves the same fixed point x = E(Gamma(x)) with a
+ * Newton-Krylov iteration in ln x (GMRES, tangent columns).  x_inout is
+ * device [n] double in the original particle order.  `stats` may be NULL.
+ * Synchronises `stream`.  Returns URCHIN_ERR_NOT_CONVERGED (x_inout then
+ * holds the last iterate) when max_iter is reached first. */
+URCHIN_API int urchin_solve(const urchin_bvh* bvh, const urchin_solve_params* params,
+                 double* x_inout, urchin_solve_stats* stats, urchin_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* URCHIN_H */

@@ -1,0 +1,188 @@
+// Internal declarations shared by the translation units of liburchin.
+// Nothing here is part of the public ABI (include/urchin.h).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+
+#include "urchin.h"
+
+namespace urchin {
+
+// ---- error reporting ------------------------------------------------------
+int set_error(int status, const char* fmt, ...);
+void clear_error();
+
+#define URCHIN_TRY_CUDA(call)                                                          \
+    do {                                                                               \
+        cudaError_t e_ = (call);                                                       \
+        if (e_ != cudaSuccess) {                                                       \
+            if (e_ == cudaErrorMemoryAllocation) {                                     \
+                cudaGetLastError();                                                    \
+                return ::urchin::set_error(URCHIN_ERR_NOMEM, "%s: out of device memory", \
+                                           #call);                                     \
+            }                                                                          \
+            return ::urchin::set_error(URCHIN_ERR_CUDA, "%s failed: %s (%s:%d)", #call,    \
+                                       cudaGetErrorString(e_), __FILE__, __LINE__);    \
+        }                                                                              \
+    } while (0)
+
+#define URCHIN_TRY(expr)                 \
+    do {                                 \
+        int s_ = (expr);                 \
+        if (s_ != URCHIN_OK) return s_;  \
+    } while (0)
+
+// ---- physical constants (SI-free, cgs) ------------------------------------
+constexpr double kPi = 3.14159265358979323846;
+// App. C1, Eq. sigma_ana: sigma_th = 2^9 pi/(3 e^4) alpha_fs pi a_0^2
+double sigma_th_cm2();
+constexpr double kRydbergEV = 13.605693122994;
+
+// Truncated Gaussian constants of Eq. Gt in units of h: t = A h = 2 pi^(1/6),
+// D = erf(t) - 2 t exp(-t^2)/sqrt(pi); chord prefactor sqrt(pi)/(2 t D).
+struct GtConst {
+    double t2;      // t^2
+    double t;       // t
+    double pref;    // sqrt(pi) / (2 t D)
+};
+GtConst gt_constants();
+
+// ---- stream-ordered scratch ----------------------------------------------
+// One cudaMallocAsync block released with cudaFreeAsync on the same stream.
+struct Scratch {
+    void* ptr = nullptr;
+    cudaStream_t stream = nullptr;
+    Scratch() = default;
+    Scratch(const Scratch&) = delete;
+    Scratch& operator=(const Scratch&) = delete;
+    ~Scratch() { release(); }
+    int alloc(size_t bytes, cudaStream_t s);
+    void release();
+    template <typename T>
+    T* at(size_t offset_bytes) const { return reinterpret_cast<T*>(static_cast<char*>(ptr) + offset_bytes); }
+};
+
+// Bump allocator used to carve one Scratch block into aligned arrays.
+struct Layout {
+    size_t bytes = 0;
+    size_t take(size_t n) {
+        size_t off = (bytes + 255) & ~size_t(255);
+        bytes = off + n;
+        return off;
+    }
+};
+
+int grid_for(const void* kernel, int block, size_t smem, int* grid_out);
+
+// Check the launch just made and count it (urchin_kernel_launches).
+int launched();
+
+// ---- scans ----------------------------------------------------------------
+// Exclusive prefix sum of n uint32 values (in may alias out).  `tmp` needs
+// scan_tmp_bytes(n) bytes of device memory.
+size_t scan_tmp_bytes(int64_t n);
+int scan_exclusive_u32(const uint32_t* in, uint32_t* out, int64_t n, void* tmp,
+                       uint32_t* total_dev, cudaStream_t s);
+
+// Stable LSD radix sort of (key, value) pairs on the low `bits` bits of key.
+size_t radix_tmp_bytes(int64_t n);
+int radix_sort_pairs(uint32_t* keys, int32_t* vals, int64_t n, int bits, void* tmp,
+                     cudaStream_t s);
+
+// Stream compaction: out[m] = i for every i with flags[i] != 0, in order;
+// *count_dev = m.  `tmp` needs compact_tmp_bytes(n).
+size_t compact_tmp_bytes(int64_t n);
+int compact_indices(const uint8_t* flags, int64_t n, int32_t* out, uint32_t* count_dev, void* tmp,
+                    cudaStream_t s);
+
+}  // namespace urchin
+
+// ---- the BVH object --------------------------------------------------------
+// Internal node layout (64 bytes, 4 float4), both children in one node:
+//   n[0] = (left.lo.xyz, left.ref)    n[1] = (left.hi.xyz, left.count)
+//   n[2] = (right.lo.xyz, right.ref)  n[3] = (right.hi.xyz, right.count)
+// ref/count are int bit patterns: count == 0 -> ref is an internal node
+// index; count > 0 -> leaf holding particles [ref, ref + count) in Morton
+// order.  An empty child has lo > hi.  Node 0 is the root.
+struct urchin_bvh {
+    int64_t n = 0;
+    int periodic = 0;
+    double L = 0.0;
+    double unit_cm = 1.0;
+    float hmax = 0.f;
+    float root_lo[3] = {0, 0, 0};
+    float root_hi[3] = {0, 0, 0};
+    int device = 0;
+    int n_nodes = 0;
+    float4* nodes = nullptr;      // [4 * n_nodes]
+    float4* xyzh = nullptr;       // [n] Morton order
+    float* A32 = nullptr;         // [n] sigma_th (m/m_p) (8/pi) / (h unit_cm)^2
+    double* A64 = nullptr;        // [n]
+    int32_t* perm = nullptr;      // [n] Morton slot -> original index
+    int32_t* inv = nullptr;       // [n] original index -> Morton slot
+};
+
+namespace urchin {
+
+// Bits of the device status word shared by the kernels of one call.
+constexpr unsigned kStStack = 1u;       // traversal stack overflow
+constexpr unsigned kStOrigin = 2u;      // origin index out of range
+constexpr unsigned kStNonfinite = 4u;   // non-finite or non-positive x
+constexpr unsigned kStInput = 8u;       // n_H or T not finite and > 0
+constexpr unsigned kStWarm = 16u;       // warm-start x outside (0, 1]
+constexpr unsigned kStVisit = 32u;      // traversal visit limit (malformed tree)
+
+constexpr int kLeafMax = 4;       // subtrees with <= kLeafMax particles become leaves
+constexpr int kStackMax = 64;     // traversal stack (tree depth <= 62 for 30-bit codes)
+
+// Column tracing shared by urchin_trace_columns and urchin_solve.
+struct TraceJob {
+    const urchin_bvh* bvh;
+    const float* w32;             // [n] A_j x_j, Morton order (F32)
+    const double* w64;            // [n] (F64)
+    const double* dirs_dev;       // [R*3]
+    int R;
+    double l_ray;
+    const int32_t* items;         // [n_items] Morton origin per item, NULL = identity
+    int64_t n_items;
+    int64_t row_stride;           // out index = row * row_stride + k * k_stride
+    int64_t k_stride;
+    const int32_t* out_row;       // [n_items] output row per item, NULL = item index
+    void* out;                    // float or double
+    int kernel;
+    int precision;
+    unsigned int* counter;        // one device uint (work queue), zeroed here
+    unsigned int* status;         // one device uint: error flags (may be NULL)
+    unsigned long long* hits;     // chord evaluations (may be NULL)
+};
+int launch_trace(const TraceJob& job, cudaStream_t s);
+
+// w = A * x gathered into Morton order: w[s] = A[s] * x[perm[s]]
+int launch_weights(const urchin_bvh* bvh, const double* x_orig, float* w32, double* w64,
+                   cudaStream_t s);
+
+// Spectral rate per origin (Eq. gamma_shld).
+struct GammaJob {
+    const void* tau;              // tau index = row * row_stride + k * k_stride
+    int precision;
+    int64_t n_rows;
+    int R;
+    int64_t row_stride, k_stride;
+    const double* s;              // [F] device
+    const double* w;              // [F] device
+    int F;
+    double* gamma_out;            // [n_rows]
+    float* tau_eff_out;           // [n_rows] or NULL
+};
+int launch_gamma(const GammaJob& job, cudaStream_t s);
+
+// Rates of App. C3 (Hui & Gnedin 1997) on the device, per particle.
+int launch_equilibrium(const double* gamma, const float* tau_eff, const double* nH,
+                       const double* T, int64_t n, int case_rule, double y, double* x_out,
+                       cudaStream_t s);
+
+}  // namespace urchin

@@ -1,0 +1,494 @@
+// Iteration driver of Sec. 4: x starts at x_thin, sweep 0 traces every
+// particle and freezes those with tau_eff < tau_skip, later sweeps trace the
+// non-frozen particles and update them all from the previous sweep's x
+// (Jacobi), until max |dx|/x < dx_tol.
+//
+// State lives in Morton order on the device.  A sweep is two kernels: the
+// persistent traversal (columns of all active rays) and a fused kernel that
+// folds each particle's R columns through the spectrum, solves the
+// equilibrium in FP64, writes x and the tracer weight A_j x_j, and reduces
+// max |dx|/x.  The host reads that scalar once per sweep.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <vector>
+
+#include "solver.cuh"
+#include "spectral_device.cuh"
+
+namespace urchin {
+
+namespace {
+
+constexpr int kSweepThreads = 256;
+
+__global__ void k_setup(const urchin_bvh b, const double* __restrict__ nH, const double* __restrict__ T,
+                        const double* __restrict__ x_in, int warm, double gthin, int case_rule, double y,
+                        double* nHm, double* aA, double* aB, double* gc, double* x, float* w32, double* w64,
+                        unsigned* status)
+{
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < b.n;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        int32_t i = b.perm[s];
+        double n_ = nH[i], t_ = T[i];
+        if (!(n_ > 0.0) || !(t_ > 0.0) || !isfinite(n_) || !isfinite(t_)) atomicOr(status, kStInput);
+        Rates r = hg97_rates(t_);
+        nHm[s] = n_;
+        aA[s] = r.alphaA;
+        aB[s] = r.alphaB;
+        gc[s] = r.gamma_c;
+        double xv;
+        if (warm) {
+            xv = x_in[i];
+            if (!(xv > 0.0) || !(xv <= 1.0)) atomicOr(status, kStWarm);
+        } else {
+            // x_thin: Gamma = Gamma_thin, tau_eff = 0 (case A unless forced to B)
+            xv = x_equilibrium(gthin, n_, case_rule == URCHIN_CASE_B ? r.alphaB : r.alphaA, r.gamma_c, y);
+        }
+        x[s] = xv;
+        double wv = b.A64[s] * xv;
+        if (w32) w32[s] = (float)wv;
+        if (w64) w64[s] = wv;
+    }
+}
+
+__global__ void k_finish(const int32_t* __restrict__ perm, const double* __restrict__ x, int64_t n, double* x_out)
+{
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n;
+         s += (int64_t)gridDim.x * blockDim.x)
+        x_out[perm[s]] = x[s];
+}
+
+__device__ __forceinline__ void atomic_max_pos(unsigned long long* addr, double v)
+{
+    // non-negative doubles order like their bit patterns
+    atomicMax(addr, (unsigned long long)__double_as_longlong(v));
+}
+
+template <typename Real>
+__device__ void sweep_spectrum(const double* s, const double* w, int F, Real* e2, Real* e2s, Real* wn,
+                               double* sh)
+{
+    __shared__ double red[kSweepThreads / 32][2];
+    double tot = 0.0, smin = 1e300;
+    for (int j = threadIdx.x; j < F; j += blockDim.x) {
+        tot += w[j];
+        smin = fmin(smin, s[j]);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        tot += __shfl_xor_sync(0xffffffffu, tot, o);
+        smin = fmin(smin, __shfl_xor_sync(0xffffffffu, smin, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[threadIdx.x >> 5][0] = tot;
+        red[threadIdx.x >> 5][1] = smin;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0, m = 1e300;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+            t += red[i][0];
+            m = fmin(m, red[i][1]);
+        }
+        sh[0] = t;
+        sh[1] = m;
+    }
+    __syncthreads();
+    const double g = sh[0], m = sh[1];
+    for (int j = threadIdx.x; j < F; j += blockDim.x) {
+        e2[j] = (Real)((s[j] - m) * 1.4426950408889634);
+        wn[j] = (Real)(w[j] / g);
+        if (e2s) e2s[j] = (Real)s[j];
+    }
+    __syncthreads();
+}
+
+// One sweep's spectral fold + equilibrium update (see file comment).  With
+// want_tangent, also stores per ray c_tk = (1/E) dE/dGamma dGamma/dtau_k for
+// the Newton tangent (in log-safe form).
+template <typename Real>
+__global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs A)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Real* e2 = reinterpret_cast<Real*>(smem_raw);
+    Real* wn = e2 + A.F;
+    Real* sj = wn + A.F;
+    double* lk = reinterpret_cast<double*>(smem_raw + ((3 * (size_t)A.F * sizeof(Real) + 15) & ~size_t(15)));
+    double* lk2 = lk + kSweepThreads;
+    __shared__ double sh[2];
+    sweep_spectrum<Real>(A.s, A.w, A.F, e2, A.want_tangent ? sj : nullptr, wn, sh);
+    const int rows_per_block = kSweepThreads / A.R;
+    const int local = threadIdx.x / A.R;
+    const int k = threadIdx.x % A.R;
+    const double gthin = sh[0], smin = sh[1];
+    double my_max = 0.0;
+    unsigned err = 0;
+    for (int64_t row0 = (int64_t)blockIdx.x * rows_per_block; row0 < A.n_items;
+         row0 += (int64_t)gridDim.x * rows_per_block) {
+        const int64_t row = row0 + local;
+        const bool active = local < rows_per_block && row < A.n_items;
+        if (active) {
+            Real tau = static_cast<const Real*>(A.tau)[row + (int64_t)k * A.k_stride];
+            Real S = Real(0), c = Real(0), S2 = Real(0), c2 = Real(0);
+            for (int j = 0; j < A.F; ++j) {
+                Real v = wn[j] * exp2(-e2[j] * tau);
+                Real yy = v - c;
+                Real t = S + yy;
+                c = (t - S) - yy;
+                S = t;
+                if (A.want_tangent) {
+                    Real v2 = v * sj[j];
+                    Real y2 = v2 - c2;
+                    Real t2 = S2 + y2;
+                    c2 = (t2 - S2) - y2;
+                    S2 = t2;
+                }
+            }
+            lk[local * A.R + k] = -smin * (double)tau + log((double)S);
+            if (A.want_tangent) lk2[local * A.R + k] = -smin * (double)tau + log((double)fmax(S2, Real(1e-37)));
+        }
+        __syncthreads();
+        if (active && k == 0) {
+            double m = -1e300;
+            for (int r = 0; r < A.R; ++r) m = fmax(m, lk[local * A.R + r]);
+            double acc = 0.0;
+            for (int r = 0; r < A.R; ++r) acc += exp(lk[local * A.R + r] - m);
+            const double lmean = m + log(acc / (double)A.R);     // ln(Gamma/Gamma_thin)
+            const double G = gthin * exp(lmean);
+            const double te = -lmean;
+            const int32_t i = A.items ? A.items[row] : (int32_t)row;
+            bool update = true;
+            if (A.sweep0) {
+                update = !(te < A.tau_skip);
+                A.active[i] = update ? 1 : 0;
+            }
+            if (A.gamma_out) A.gamma_out[row] = G;
+            if (A.tau_eff_out) A.tau_eff_out[row] = (float)te;
+            if (update) {
+                const bool caseB = A.case_rule == URCHIN_CASE_B || (A.case_rule == URCHIN_CASE_AUTO && te >= 1.0);
+                const double alpha = caseB ? A.aB[i] : A.aA[i];
+                const double xo = A.x[i];
+                const double xn = x_equilibrium(G, A.nH[i], alpha, A.gc[i], A.y);
+                if (!isfinite(xn) || !(xn > 0.0)) err |= kStNonfinite;
+                const double rel = fabs(xn - xo) / xo;
+                my_max = fmax(my_max, rel);
+                if (A.want_tangent) {
+                    // elasticity Gamma dE/dGamma / E and per-ray dGamma/dtau_k / Gamma
+                    const double dEdG = dx_dgamma(xn, A.nH[i], alpha, A.gc[i], G, A.y);
+                    const double elas = (G > 0.0) ? G * dEdG / xn : 0.0;
+                    for (int r = 0; r < A.R; ++r) {
+                        const double dlog = exp(lk2[local * A.R + r] - lmean) / (double)A.R;
+                        A.ctan[row + (int64_t)r * A.k_stride] = -elas * dlog;
+                    }
+                    A.xeq_out[row] = xn;
+                } else {
+                    A.x[i] = xn;
+                    const double wv = A.A64[i] * xn;
+                    if (A.w32) A.w32[i] = (float)wv;
+                    if (A.w64) A.w64[i] = wv;
+                }
+            }
+        }
+        __syncthreads();
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        my_max = fmax(my_max, __shfl_xor_sync(0xffffffffu, my_max, o));
+        err |= __shfl_xor_sync(0xffffffffu, err, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (my_max > 0.0) atomic_max_pos(A.maxrel, my_max);
+        if (err) atomicOr(A.status, err);
+    }
+}
+
+}  // namespace
+
+int launch_sweep(const SweepArgs& A, cudaStream_t s)
+{
+    if (A.n_items <= 0) return URCHIN_OK;
+    const size_t rsz = A.precision == URCHIN_F64 ? sizeof(double) : sizeof(float);
+    size_t smem = ((3 * (size_t)A.F * rsz + 15) & ~size_t(15)) + 2 * sizeof(double) * kSweepThreads;
+    const void* fn = A.precision == URCHIN_F64 ? (const void*)k_sweep<double> : (const void*)k_sweep<float>;
+    if (smem > 48 * 1024)
+        URCHIN_TRY_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int rows_per_block = kSweepThreads / A.R;
+    int64_t need = (A.n_items + rows_per_block - 1) / rows_per_block;
+    int grid = 0;
+    URCHIN_TRY(grid_for(fn, kSweepThreads, smem, &grid));
+    if (need < grid) grid = (int)std::max<int64_t>(need, 1);
+    if (A.precision == URCHIN_F64) k_sweep<double><<<grid, kSweepThreads, smem, s>>>(A);
+    else k_sweep<float><<<grid, kSweepThreads, smem, s>>>(A);
+    URCHIN_TRY(launched());
+    return URCHIN_OK;
+}
+
+int Solver::init(const urchin_bvh* bvh_, const urchin_solve_params* P_, double* x_inout, cudaStream_t s_)
+{
+    bvh = bvh_;
+    P = *P_;
+    s = s_;
+    n = bvh->n;
+    f64 = P.precision == URCHIN_F64;
+    const size_t rsz = f64 ? sizeof(double) : sizeof(float);
+    Layout lay;
+    size_t o_misc = lay.take(64);
+    size_t o_dirs = lay.take(sizeof(double) * 3 * (size_t)P.R);
+    size_t o_x = lay.take(sizeof(double) * (size_t)n);
+    size_t o_nH = lay.take(sizeof(double) * (size_t)n);
+    size_t o_aA = lay.take(sizeof(double) * (size_t)n);
+    size_t o_aB = lay.take(sizeof(double) * (size_t)n);
+    size_t o_gc = lay.take(sizeof(double) * (size_t)n);
+    size_t o_w = lay.take(rsz * (size_t)n);
+    size_t o_act = lay.take((size_t)n);
+    size_t o_list = lay.take(sizeof(int32_t) * (size_t)n);
+    size_t o_tau = lay.take(rsz * (size_t)n * P.R);
+    size_t o_comp = lay.take(compact_tmp_bytes(n));
+    URCHIN_TRY(scr.alloc(lay.bytes, s));
+    misc = scr.at<unsigned long long>(o_misc);   // [0] maxrel, [1] counter+status
+    dirs = scr.at<double>(o_dirs);
+    x = scr.at<double>(o_x);
+    nH = scr.at<double>(o_nH);
+    aA = scr.at<double>(o_aA);
+    aB = scr.at<double>(o_aB);
+    gc = scr.at<double>(o_gc);
+    w32 = f64 ? nullptr : scr.at<float>(o_w);
+    w64 = f64 ? scr.at<double>(o_w) : nullptr;
+    active = scr.at<uint8_t>(o_act);
+    list = scr.at<int32_t>(o_list);
+    tau = scr.at<void>(o_tau);
+    comp_tmp = scr.at<void>(o_comp);
+    counter = reinterpret_cast<unsigned*>(misc + 1);
+    status = counter + 1;
+    hits = P.profile ? misc + 3 : nullptr;
+    URCHIN_TRY_CUDA(cudaMemsetAsync(misc, 0, 64, s));
+    URCHIN_TRY_CUDA(cudaMemcpyAsync(dirs, P.dirs, sizeof(double) * 3 * (size_t)P.R, cudaMemcpyHostToDevice, s));
+    std::vector<double> wh((size_t)P.spectrum.F);
+    URCHIN_TRY_CUDA(cudaMemcpyAsync(wh.data(), P.spectrum.w, sizeof(double) * wh.size(), cudaMemcpyDeviceToHost, s));
+    URCHIN_TRY_CUDA(cudaStreamSynchronize(s));
+    gthin = 0.0;
+    for (double v : wh) gthin += v;
+    if (!(gthin > 0.0) || !std::isfinite(gthin))
+        return set_error(URCHIN_ERR_ARG, "urchin_solve: spectrum weights must sum to a finite Gamma_thin > 0");
+    unsigned grid = (unsigned)std::min<int64_t>((n + 255) / 256, 4096);
+    k_setup<<<grid, 256, 0, s>>>(*bvh, P.nH, P.T, x_inout, P.warm_start, gthin, P.case_rule, P.y, nH, aA, aB, gc,
+                                 x, w32, w64, status);
+    URCHIN_TRY(launched());
+    unsigned st = 0;
+    URCHIN_TRY_CUDA(cudaMemcpyAsync(&st, status, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    URCHIN_TRY_CUDA(cudaStreamSynchronize(s));
+    if (st & kStInput) return set_error(URCHIN_ERR_ARG, "urchin_solve: n_H and T must be finite and > 0");
+    if (st & kStWarm) return set_error(URCHIN_ERR_ARG, "urchin_solve: warm-start x must lie in (0, 1]");
+    return URCHIN_OK;
+}
+
+int Solver::trace(const int32_t* items, int64_t n_items, const float* tw32, const double* tw64)
+{
+    TraceJob job{};
+    job.bvh = bvh;
+    job.w32 = tw32;
+    job.w64 = tw64;
+    job.dirs_dev = dirs;
+    job.R = P.R;
+    job.l_ray = P.l_ray;
+    job.items = items;
+    job.n_items = n_items;
+    job.row_stride = 1;
+    job.k_stride = n_items;
+    job.out_row = nullptr;
+    job.out = tau;
+    job.kernel = P.kernel;
+    job.precision = P.precision;
+    job.counter = counter;
+    job.status = status;
+    job.hits = hits;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    if (P.profile) {
+        for (auto& e : ev) {
+            URCHIN_TRY_CUDA(cudaEventCreate(&e));
+            events.push_back(e);
+        }
+        URCHIN_TRY_CUDA(cudaEventRecord(ev[0], s));
+    }
+    URCHIN_TRY(launch_trace(job, s));
+    if (P.profile) URCHIN_TRY_CUDA(cudaEventRecord(ev[1], s));
+    stats.traversals += 1;
+    stats.trace_launches += 1;
+    stats.rays += n_items * P.R;
+    return URCHIN_OK;
+}
+
+SweepArgs Solver::sweep_args(const int32_t* items, int64_t n_items, int sweep0)
+{
+    SweepArgs A{};
+    A.tau = tau;
+    A.precision = P.precision;
+    A.k_stride = n_items;
+    A.items = items;
+    A.n_items = n_items;
+    A.R = P.R;
+    A.s = P.spectrum.s;
+    A.w = P.spectrum.w;
+    A.F = P.spectrum.F;
+    A.x = x;
+    A.A64 = bvh->A64;
+    A.w32 = w32;
+    A.w64 = w64;
+    A.nH = nH;
+    A.aA = aA;
+    A.aB = aB;
+    A.gc = gc;
+    A.y = P.y;
+    A.case_rule = P.case_rule;
+    A.tau_skip = P.tau_skip;
+    A.sweep0 = sweep0;
+    A.active = active;
+    A.maxrel = misc;
+    A.status = status;
+    return A;
+}
+
+int Solver::read_scalars(double* maxrel, unsigned* st)
+{
+    unsigned long long h[2];
+    URCHIN_TRY_CUDA(cudaMemcpyAsync(h, misc, sizeof(h), cudaMemcpyDeviceToHost, s));
+    URCHIN_TRY_CUDA(cudaStreamSynchronize(s));
+    double m;
+    memcpy(&m, &h[0], sizeof(double));
+    *maxrel = m;
+    *st = (unsigned)(h[1] >> 32);
+    return URCHIN_OK;
+}
+
+int Solver::first_sweep()
+{
+    // sweep 0: every particle traced; tau_eff < tau_skip freezes it
+    URCHIN_TRY_CUDA(cudaMemsetAsync(misc, 0, sizeof(unsigned long long), s));
+    URCHIN_TRY(trace(nullptr, n, w32, w64));
+    URCHIN_TRY(launch_sweep(sweep_args(nullptr, n, 1), s));
+    uint32_t* cnt = reinterpret_cast<uint32_t*>(misc + 2);
+    URCHIN_TRY(compact_indices(active, n, list, cnt, comp_tmp, s));
+    uint32_t hc = 0;
+    URCHIN_TRY_CUDA(cudaMemcpyAsync(&hc, cnt, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    double m;
+    unsigned st;
+    URCHIN_TRY(read_scalars(&m, &st));
+    if (st & kStNonfinite) return set_error(URCHIN_ERR_NONFINITE, "urchin_solve: non-finite neutral fraction");
+    if (st & (kStStack | kStVisit)) return set_error(URCHIN_ERR_CUDA, "urchin_solve: traversal stack/visit limit hit");
+    n_act = hc;
+    stats.n_active = n_act;
+    stats.particle_updates += n_act;
+    stats.iterations = 1;
+    stats.max_rel_dx = m;
+    return URCHIN_OK;
+}
+
+int Solver::plain()
+{
+    URCHIN_TRY(first_sweep());
+    if (stats.max_rel_dx < P.tol) {
+        stats.converged = 1;
+        return URCHIN_OK;
+    }
+    while (stats.iterations < P.max_iter) {
+        URCHIN_TRY_CUDA(cudaMemsetAsync(misc, 0, sizeof(unsigned long long), s));
+        URCHIN_TRY(trace(list, n_act, w32, w64));
+        URCHIN_TRY(launch_sweep(sweep_args(list, n_act, 0), s));
+        double m;
+        unsigned st;
+        URCHIN_TRY(read_scalars(&m, &st));
+        if (st & kStNonfinite) return set_error(URCHIN_ERR_NONFINITE, "urchin_solve: non-finite neutral fraction");
+        if (st & (kStStack | kStVisit)) return set_error(URCHIN_ERR_CUDA, "urchin_solve: traversal stack/visit limit hit");
+        stats.iterations += 1;
+        stats.particle_updates += n_act;
+        stats.max_rel_dx = m;
+        if (m < P.tol) {
+            stats.converged = 1;
+            break;
+        }
+    }
+    return URCHIN_OK;
+}
+
+int Solver::newton()
+{
+    return set_error(URCHIN_ERR_ARG, "urchin_solve: Newton-Krylov is not available yet");
+}
+
+int Solver::finish(double* x_inout)
+{
+    unsigned grid = (unsigned)std::min<int64_t>((n + 255) / 256, 4096);
+    k_finish<<<grid, 256, 0, s>>>(bvh->perm, x, n, x_inout);
+    URCHIN_TRY(launched());
+    if (P.profile) {
+        unsigned long long h = 0;
+        URCHIN_TRY_CUDA(cudaMemcpyAsync(&h, hits, sizeof(h), cudaMemcpyDeviceToHost, s));
+        URCHIN_TRY_CUDA(cudaStreamSynchronize(s));
+        stats.hits = (int64_t)h;
+        double total = 0.0;
+        for (size_t i = 0; i + 1 < events.size(); i += 2) {
+            float ms = 0.f;
+            URCHIN_TRY_CUDA(cudaEventElapsedTime(&ms, events[i], events[i + 1]));
+            total += ms;
+        }
+        stats.trace_s = total * 1e-3;
+    }
+    scr.release();
+    URCHIN_TRY_CUDA(cudaStreamSynchronize(s));
+    return URCHIN_OK;
+}
+
+Solver::~Solver()
+{
+    for (cudaEvent_t e : events) cudaEventDestroy(e);
+}
+
+}  // namespace urchin
+
+extern "C" int urchin_solve(const urchin_bvh* bvh, const urchin_solve_params* P, double* x_inout,
+                            urchin_solve_stats* stats, urchin_stream_t stream)
+{
+    using namespace urchin;
+    clear_error();
+    auto t0 = std::chrono::steady_clock::now();
+    if (stats) memset(stats, 0, sizeof(*stats));
+    if (!bvh || !P || !x_inout) return set_error(URCHIN_ERR_ARG, "urchin_solve: NULL bvh, params or x_inout");
+    if (P->R < 1 || P->R > URCHIN_MAX_RAYS || !P->dirs)
+        return set_error(URCHIN_ERR_ARG, "urchin_solve: bad ray set (R = %d)", P->R);
+    for (int k = 0; k < P->R; ++k) {
+        const double* d = P->dirs + 3 * k;
+        double nn = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        if (!std::isfinite(nn) || std::fabs(nn - 1.0) > 1e-6)
+            return set_error(URCHIN_ERR_ARG, "urchin_solve: direction %d is not a unit vector", k);
+    }
+    if (!(P->l_ray >= 0.0) || !std::isfinite(P->l_ray)) return set_error(URCHIN_ERR_ARG, "urchin_solve: bad l_ray");
+    if (P->spectrum.F < 1 || P->spectrum.F > URCHIN_MAX_BINS || !P->spectrum.s || !P->spectrum.w)
+        return set_error(URCHIN_ERR_ARG, "urchin_solve: bad spectrum");
+    if (!P->nH || !P->T) return set_error(URCHIN_ERR_ARG, "urchin_solve: NULL nH or T");
+    if (!(P->tol > 0.0) || !(P->tau_skip >= 0.0) || P->max_iter < 1 || !(P->y >= 0.0))
+        return set_error(URCHIN_ERR_ARG, "urchin_solve: need tol > 0, tau_skip >= 0, max_iter >= 1, y >= 0");
+    if (P->kernel != URCHIN_KERNEL_M4 && P->kernel != URCHIN_KERNEL_GT)
+        return set_error(URCHIN_ERR_ARG, "urchin_solve: unknown kernel");
+    if (P->precision != URCHIN_F32 && P->precision != URCHIN_F64)
+        return set_error(URCHIN_ERR_ARG, "urchin_solve: unknown precision");
+    if (P->case_rule != URCHIN_CASE_A && P->case_rule != URCHIN_CASE_B && P->case_rule != URCHIN_CASE_AUTO)
+        return set_error(URCHIN_ERR_ARG, "urchin_solve: unknown case_rule");
+    if (P->method != URCHIN_METHOD_PLAIN && P->method != URCHIN_METHOD_NEWTON)
+        return set_error(URCHIN_ERR_ARG, "urchin_solve: unknown method");
+    if (P->segments != URCHIN_SEG_RECOMPUTE && P->segments != URCHIN_SEG_STORE && P->segments != URCHIN_SEG_AUTO)
+        return set_error(URCHIN_ERR_ARG, "urchin_solve: unknown segments mode");
+    if (P->method == URCHIN_METHOD_NEWTON && (P->gmres_m < 1 || P->gmres_m > 64))
+        return set_error(URCHIN_ERR_ARG, "urchin_solve: gmres_m must be in [1, 64]");
+    cudaStream_t s = (cudaStream_t)stream;
+    Solver S;
+    int st = S.init(bvh, P, x_inout, s);
+    if (st == URCHIN_OK) st = S.run();
+    if (st == URCHIN_OK) st = S.finish(x_inout);
+    else cudaStreamSynchronize(s);
+    S.stats.wall_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (stats) *stats = S.stats;
+    if (st != URCHIN_OK) return st;
+    if (!S.stats.converged)
+        return set_error(URCHIN_ERR_NOT_CONVERGED, "urchin_solve: max |dx|/x = %.3e after %d iterations",
+                         S.stats.max_rel_dx, S.stats.iterations);
+    return URCHIN_OK;
+}

@@ -1,0 +1,86 @@
+// Solver state shared by the plain (Jacobi) and Newton-Krylov drivers.
+#pragma once
+
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+
+namespace urchin {
+
+struct SweepArgs {
+    const void* tau;           // float or double per precision
+    int precision;
+    int64_t k_stride;          // tau[row + k * k_stride]
+    const int32_t* items;      // Morton particle per row (NULL = identity)
+    int64_t n_items;
+    int R;
+    const double* s;
+    const double* w;
+    int F;
+    double* x;                 // Morton order
+    const double* A64;
+    float* w32;
+    double* w64;
+    const double* nH;
+    const double* aA;
+    const double* aB;
+    const double* gc;
+    double y;
+    int case_rule;
+    double tau_skip;
+    int sweep0;
+    uint8_t* active;           // written in sweep 0
+    unsigned long long* maxrel;
+    unsigned* status;
+    double* gamma_out;         // [n_items] optional
+    float* tau_eff_out;        // [n_items] optional
+    int want_tangent;          // Newton: keep x, emit E and tangent factors
+    double* ctan;              // [n_items * R] (k-major, stride k_stride)
+    double* xeq_out;           // [n_items]
+};
+
+int launch_sweep(const SweepArgs& A, cudaStream_t s);
+
+struct Solver {
+    const urchin_bvh* bvh = nullptr;
+    urchin_solve_params P{};
+    cudaStream_t s = nullptr;
+    int64_t n = 0;
+    int64_t n_act = 0;
+    bool f64 = false;
+    double gthin = 0.0;
+    urchin_solve_stats stats{};
+    Scratch scr;
+    unsigned long long* misc = nullptr;
+    unsigned* counter = nullptr;
+    unsigned* status = nullptr;
+    double* dirs = nullptr;
+    double* x = nullptr;
+    double* nH = nullptr;
+    double* aA = nullptr;
+    double* aB = nullptr;
+    double* gc = nullptr;
+    float* w32 = nullptr;
+    double* w64 = nullptr;
+    uint8_t* active = nullptr;
+    int32_t* list = nullptr;
+    void* tau = nullptr;
+    void* comp_tmp = nullptr;
+    unsigned long long* hits = nullptr;          // misc[3], counted when P.profile
+    std::vector<cudaEvent_t> events;             // start/stop pairs of each traversal
+
+    ~Solver();
+
+    int init(const urchin_bvh* bvh, const urchin_solve_params* P, double* x_inout, cudaStream_t s);
+    int trace(const int32_t* items, int64_t n_items, const float* tw32, const double* tw64);
+    SweepArgs sweep_args(const int32_t* items, int64_t n_items, int sweep0);
+    int read_scalars(double* maxrel, unsigned* status);
+    int first_sweep();
+    int plain();
+    int newton();
+    int run() { return P.method == URCHIN_METHOD_NEWTON ? newton() : plain(); }
+    int finish(double* x_inout);
+};
+
+}  // namespace urchin

@@ -1,0 +1,491 @@
+// Column tracing (Sec. 3.2 and Eq. colden): for each (origin particle,
+// HEALPix direction) the segment r_i + t n_k, t in [0, l_ray], is walked
+// through the LBVH and every smoothing sphere it crosses adds
+//   A_j x_j * int W(q) du      (A_j = sigma_th m_j/m_p (8/pi) / h_j^2)
+// with the line integral in closed form: the M4 spline of Eq. spline via
+// antiderivatives of q, q^2, q^3 along the chord, or the truncated Gaussian
+// of Eq. Gt via the erf form I(h,b,z1,z2).
+//
+// Work distribution: a persistent grid; each warp takes tasks of 32
+// Morton-consecutive origins in one direction from an atomic queue, so the
+// 32 rays of a warp are parallel and start close together (coherent node
+// fetches).  Each lane walks its own ray with a private stack.
+#include <algorithm>
+#include <cmath>
+
+#include "common.cuh"
+
+namespace urchin {
+
+namespace {
+
+struct TraceParams {
+    const float4* nodes;
+    int n_nodes;
+    int n;
+    const float4* xyzh;
+    const float* w32;
+    const double* w64;
+    const double* dirs;
+    int R;
+    double l_ray;
+    const int32_t* items;
+    int64_t n_items;
+    int64_t row_stride, k_stride;
+    const int32_t* out_row;
+    void* out;
+    unsigned* counter;
+    unsigned* status;
+    unsigned long long* hits;
+    int periodic;
+    double Lbox;
+    int nimg;
+    float root_lo[3], root_hi[3];
+    double gt_t2, gt_t, gt_pref;
+    int64_t n_chunks;
+};
+
+template <typename Real> struct RealOps;
+template <> struct RealOps<float> {
+    static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
+    static __device__ __forceinline__ float log_(float x) { return logf(x); }
+    static __device__ __forceinline__ float exp_(float x) { return expf(x); }
+    static __device__ __forceinline__ float erf_(float x) { return erff(x); }
+    static __device__ __forceinline__ float weight(const TraceParams& P, int j) { return __ldg(P.w32 + j); }
+};
+template <> struct RealOps<double> {
+    static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+    static __device__ __forceinline__ double log_(double x) { return log(x); }
+    static __device__ __forceinline__ double exp_(double x) { return exp(x); }
+    static __device__ __forceinline__ double erf_(double x) { return erf(x); }
+    static __device__ __forceinline__ double weight(const TraceParams& P, int j) { return __ldg(P.w64 + j); }
+};
+
+// ---- M4 chord integrals in units of h -------------------------------------
+// With q = sqrt(beta^2 + a^2) and L(a) = asinh(a/beta) = ln(a + q) - ln(beta):
+//   inner piece (q <= 1/2), integrand 1 - 6q^2 + 6q^3:
+//     Fi(a) = a(1 - 6b2 - 2a^2) + 3/2 a q^3 + 9/4 b2 a q + 9/4 b2^2 L
+//   outer piece (1/2 < q <= 1), integrand 2(1-q)^3:
+//     Fo(a) = a(2 + 6b2 + 2a^2) - 3 a q - 1/2 a q^3 - 3/4 b2 a q - (3 b2 + 3/4 b2^2) L
+// and the odd antiderivative from 0 is H(a) = Fi(a) for a <= s, else
+// Fo(a) + Fi(s) - Fo(s) with s = sqrt(1/4 - b2) (b2 < 1/4), where
+//   Fi(s) - Fo(s) = -s(1/4 + 13/2 b2) + (3 b2 + 3 b2^2) L(s).
+// At the chord end a = c = sqrt(1 - b2) (q = 1):
+//   Fo(c) = c(1/2 + 13/4 b2) - (3 b2 + 3/4 b2^2) L(c).
+template <typename Real>
+__device__ __forceinline__ Real m4_join(Real b2, Real lb, Real& s_out)
+{
+    using O = RealOps<Real>;
+    Real s = O::sqrt_(Real(0.25) - b2);
+    s_out = s;
+    Real Ls = b2 > Real(0) ? O::log_(s + Real(0.5)) - lb : Real(0);
+    return -s * (Real(0.25) + Real(6.5) * b2) + (Real(3) * b2 + Real(3) * b2 * b2) * Ls;
+}
+
+template <typename Real>
+__device__ __forceinline__ Real m4_full(Real b2, Real c)
+{
+    using O = RealOps<Real>;
+    Real lb = b2 > Real(0) ? Real(0.5) * O::log_(b2) : Real(0);
+    Real Lc = b2 > Real(0) ? O::log_(c + Real(1)) - lb : Real(0);
+    Real H = c * (Real(0.5) + Real(3.25) * b2) - (Real(3) * b2 + Real(0.75) * b2 * b2) * Lc;
+    if (b2 < Real(0.25)) {
+        Real s;
+        H += m4_join(b2, lb, s);
+    }
+    return Real(2) * H;
+}
+
+template <typename Real>
+__device__ __forceinline__ Real m4_H(Real b2, Real lb, Real a)
+{
+    using O = RealOps<Real>;
+    Real q = O::sqrt_(b2 + a * a);
+    Real La = b2 > Real(0) ? O::log_(a + q) - lb : Real(0);
+    Real q3 = q * q * q;
+    if (b2 < Real(0.25)) {
+        Real s;
+        Real join = m4_join(b2, lb, s);
+        if (a <= s)
+            return a * (Real(1) - Real(6) * b2 - Real(2) * a * a) + Real(1.5) * a * q3 +
+                   Real(2.25) * b2 * a * q + Real(2.25) * b2 * b2 * La;
+        return a * (Real(2) + Real(6) * b2 + Real(2) * a * a) - Real(3) * a * q - Real(0.5) * a * q3 -
+               Real(0.75) * b2 * a * q - (Real(3) * b2 + Real(0.75) * b2 * b2) * La + join;
+    }
+    return a * (Real(2) + Real(6) * b2 + Real(2) * a * a) - Real(3) * a * q - Real(0.5) * a * q3 -
+           Real(0.75) * b2 * a * q - (Real(3) * b2 + Real(0.75) * b2 * b2) * La;
+}
+
+template <typename Real>
+__device__ __forceinline__ Real m4_part(Real b2, Real u1, Real u2)
+{
+    using O = RealOps<Real>;
+    Real lb = b2 > Real(0) ? Real(0.5) * O::log_(b2) : Real(0);
+    Real g2 = u2 >= Real(0) ? m4_H(b2, lb, u2) : -m4_H(b2, lb, -u2);
+    Real g1 = u1 >= Real(0) ? m4_H(b2, lb, u1) : -m4_H(b2, lb, -u1);
+    return g2 - g1;
+}
+
+// ---- truncated Gaussian (Eq. Gt, I(h,b,z1,z2)) ----------------------------
+template <typename Real>
+__device__ __forceinline__ Real gt_chord(const TraceParams& P, Real b2, Real u1, Real u2)
+{
+    using O = RealOps<Real>;
+    Real t = Real(P.gt_t);
+    return Real(P.gt_pref) * O::exp_(-Real(P.gt_t2) * b2) * (O::erf_(t * u2) - O::erf_(t * u1));
+}
+
+struct Kahan {
+    __device__ __forceinline__ static void add(float& s, float& c, float v)
+    {
+        float y = v - c;
+        float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ static void add(double& s, double& c, double v)
+    {
+        double y = v - c;
+        double t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+};
+
+// Segment [0, L] of o + t d against an axis-aligned box (float slab test).
+__device__ __forceinline__ bool seg_box(float ox, float oy, float oz, float ix, float iy, float iz,
+                                        float L, float4 lo, float4 hi)
+{
+    float tx0 = (lo.x - ox) * ix, tx1 = (hi.x - ox) * ix;
+    float ty0 = (lo.y - oy) * iy, ty1 = (hi.y - oy) * iy;
+    float tz0 = (lo.z - oz) * iz, tz1 = (hi.z - oz) * iz;
+    float tn = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), 0.f));
+    float tf = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), L));
+    return tn <= tf;
+}
+
+__device__ __forceinline__ float safe_inv(double d)
+{
+    return fabs(d) > 1e-20 ? (float)(1.0 / d) : copysignf(1e30f, (float)d);
+}
+
+template <typename Real, int KERNEL>
+__device__ __forceinline__ void leaf_hits(const TraceParams& P, int ref, int cnt, Real sx, Real sy, Real sz,
+                                          Real dx, Real dy, Real dz, Real L, Real& sum, Real& comp,
+                                          unsigned& nhit)
+{
+    using O = RealOps<Real>;
+    if (ref < 0 || cnt > kLeafMax || ref + cnt > P.n) return;   // never true for a well-formed tree
+    for (int j = ref; j < ref + cnt; ++j) {
+        float4 q = __ldg(P.xyzh + j);
+        Real ex = Real(q.x) - sx, ey = Real(q.y) - sy, ez = Real(q.z) - sz;
+        Real tc = ex * dx + ey * dy + ez * dz;
+        Real cx = ey * dz - ez * dy, cy = ez * dx - ex * dz, cz = ex * dy - ey * dx;
+        Real b2 = cx * cx + cy * cy + cz * cz;
+        Real h = Real(q.w);
+        Real h2 = h * h;
+        if (b2 >= h2) continue;
+        Real ch = O::sqrt_(h2 - b2);
+        if (tc + ch <= Real(0) || tc - ch >= L) continue;
+        Real ih = Real(1) / h;
+        Real beta2 = b2 * ih * ih;
+        Real F;
+        if (tc - ch >= Real(0) && tc + ch <= L) {
+            Real c = ch * ih;
+            if (KERNEL == URCHIN_KERNEL_M4) F = m4_full(beta2, c);
+            else F = gt_chord(P, beta2, -c, c);
+        } else {
+            Real u1 = (fmax(Real(0), tc - ch) - tc) * ih;
+            Real u2 = (fmin(L, tc + ch) - tc) * ih;
+            if (KERNEL == URCHIN_KERNEL_M4) F = m4_part(beta2, u1, u2);
+            else F = gt_chord(P, beta2, u1, u2);
+        }
+        Kahan::add(sum, comp, O::weight(P, j) * F);
+        ++nhit;
+    }
+}
+
+template <typename Real, int KERNEL>
+__device__ Real ray_column(const TraceParams& P, float4 o, Real dx, Real dy, Real dz, unsigned& err,
+                           unsigned& nhit)
+{
+    const Real L = Real(P.l_ray);
+    const float Lf = (float)P.l_ray * 1.000001f + 1e-30f;
+    const float ix = safe_inv((double)dx), iy = safe_inv((double)dy), iz = safe_inv((double)dz);
+    Real sum = Real(0), comp = Real(0);
+    const int nimg = P.periodic ? P.nimg : 0;
+    const float4 rlo = make_float4(P.root_lo[0], P.root_lo[1], P.root_lo[2], 0.f);
+    const float4 rhi = make_float4(P.root_hi[0], P.root_hi[1], P.root_hi[2], 0.f);
+    int stack[kStackMax];
+    for (int ax = -nimg; ax <= nimg; ++ax)
+    for (int ay = -nimg; ay <= nimg; ++ay)
+    for (int az = -nimg; az <= nimg; ++az) {
+        // images of the particles at r_j + a L are reached by shifting the
+        // origin to r_i - a L
+        Real sx = Real(o.x) - Real(ax) * Real(P.Lbox);
+        Real sy = Real(o.y) - Real(ay) * Real(P.Lbox);
+        Real sz = Real(o.z) - Real(az) * Real(P.Lbox);
+        float fx = (float)sx, fy = (float)sy, fz = (float)sz;
+        if (!seg_box(fx, fy, fz, ix, iy, iz, Lf, rlo, rhi)) continue;
+        int sp = 0;
+        int node = 0;
+        // a traversal visits every internal node at most once; the cap only
+        // guards against a malformed tree
+        int budget = P.n_nodes + 1;
+        for (;;) {
+            if (--budget < 0) {
+                err |= kStVisit;
+                break;
+            }
+            if ((unsigned)node >= (unsigned)P.n_nodes) {   // never true for a well-formed tree
+                err |= kStVisit;
+                break;
+            }
+            const float4* nd = P.nodes + 4 * (int64_t)node;
+            float4 a = __ldg(nd), b = __ldg(nd + 1), c = __ldg(nd + 2), d = __ldg(nd + 3);
+            int lref = __float_as_int(a.w), lcnt = __float_as_int(b.w);
+            int rref = __float_as_int(c.w), rcnt = __float_as_int(d.w);
+            bool hl = seg_box(fx, fy, fz, ix, iy, iz, Lf, a, b);
+            bool hr = rcnt >= 0 && seg_box(fx, fy, fz, ix, iy, iz, Lf, c, d);
+            if (hl && lcnt > 0) {
+                leaf_hits<Real, KERNEL>(P, lref, lcnt, sx, sy, sz, dx, dy, dz, L, sum, comp, nhit);
+                hl = false;
+            }
+            if (hr && rcnt > 0) {
+                leaf_hits<Real, KERNEL>(P, rref, rcnt, sx, sy, sz, dx, dy, dz, L, sum, comp, nhit);
+                hr = false;
+            }
+            if (hl && hr) {
+                if (sp < kStackMax) stack[sp++] = rref;
+                else err |= kStStack;
+                node = lref;
+            } else if (hl) {
+                node = lref;
+            } else if (hr) {
+                node = rref;
+            } else {
+                if (sp == 0) break;
+                node = stack[--sp];
+            }
+        }
+    }
+    return sum;
+}
+
+template <typename Real, int KERNEL>
+__global__ void __launch_bounds__(256) k_trace(TraceParams P)
+{
+    extern __shared__ double s_dirs[];
+    for (int t = threadIdx.x; t < 3 * P.R; t += blockDim.x) s_dirs[t] = P.dirs[t];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const unsigned long long total = (unsigned long long)P.n_chunks * (unsigned long long)P.R;
+    unsigned err = 0;
+    unsigned long long hits = 0;
+    for (;;) {
+        unsigned task = 0;
+        if (lane == 0) task = atomicAdd(P.counter, 1u);
+        task = __shfl_sync(0xffffffffu, task, 0);
+        if ((unsigned long long)task >= total) break;
+        const int k = (int)(task / P.n_chunks);
+        const int64_t chunk = (int64_t)(task % P.n_chunks);
+        const int64_t item = chunk * 32 + lane;
+        if (item < P.n_items) {
+            int32_t org = P.items ? P.items[item] : (int32_t)item;
+            float4 o = __ldg(P.xyzh + org);
+            Real dx = Real(s_dirs[3 * k]), dy = Real(s_dirs[3 * k + 1]), dz = Real(s_dirs[3 * k + 2]);
+            unsigned nhit = 0;
+            Real tau = ray_column<Real, KERNEL>(P, o, dx, dy, dz, err, nhit);
+            hits += nhit;
+            int64_t row = P.out_row ? (int64_t)P.out_row[item] : item;
+            static_cast<Real*>(P.out)[row * P.row_stride + (int64_t)k * P.k_stride] = tau;
+        }
+    }
+    if (err && P.status) atomicOr(P.status, err);
+    if (P.hits) {
+        for (int o = 16; o > 0; o >>= 1) hits += __shfl_xor_sync(0xffffffffu, hits, o);
+        if (lane == 0 && hits) atomicAdd(P.hits, hits);
+    }
+}
+
+template <typename Real, int KERNEL>
+int launch_one(const TraceParams& P, cudaStream_t s)
+{
+    const void* fn = (const void*)k_trace<Real, KERNEL>;
+    size_t smem = sizeof(double) * 3 * (size_t)P.R;
+    int grid = 0;
+    URCHIN_TRY(grid_for(fn, 256, smem, &grid));
+    int64_t tasks = P.n_chunks * P.R;
+    int64_t need = (tasks + 7) / 8;       // 8 warps per block
+    if (need < grid) grid = (int)std::max<int64_t>(need, 1);
+    k_trace<Real, KERNEL><<<grid, 256, smem, s>>>(P);
+    URCHIN_TRY(launched());
+    return URCHIN_OK;
+}
+
+}  // namespace
+
+int launch_trace(const TraceJob& job, cudaStream_t s)
+{
+    if (job.n_items <= 0) return URCHIN_OK;
+    const urchin_bvh* b = job.bvh;
+    TraceParams P;
+    P.nodes = b->nodes;
+    P.n_nodes = b->n_nodes;
+    P.n = (int)b->n;
+    P.xyzh = b->xyzh;
+    P.w32 = job.w32;
+    P.w64 = job.w64;
+    P.dirs = job.dirs_dev;
+    P.R = job.R;
+    P.l_ray = job.l_ray;
+    P.items = job.items;
+    P.n_items = job.n_items;
+    P.row_stride = job.row_stride;
+    P.k_stride = job.k_stride;
+    P.out_row = job.out_row;
+    P.out = job.out;
+    P.counter = job.counter;
+    P.status = job.status;
+    P.hits = job.hits;
+    P.periodic = b->periodic;
+    P.Lbox = b->L;
+    // every image within l_ray + h_max of the box can reach the segment
+    P.nimg = b->periodic ? (int)std::ceil((job.l_ray + (double)b->hmax) / b->L) : 0;
+    for (int a = 0; a < 3; ++a) {
+        P.root_lo[a] = b->root_lo[a];
+        P.root_hi[a] = b->root_hi[a];
+    }
+    GtConst g = gt_constants();
+    P.gt_t2 = g.t2;
+    P.gt_t = g.t;
+    P.gt_pref = g.pref;
+    P.n_chunks = (job.n_items + 31) / 32;
+    if ((unsigned long long)P.n_chunks * (unsigned long long)job.R >= 0xffffffffull)
+        return set_error(URCHIN_ERR_ARG, "trace: too many rays for one launch");
+    URCHIN_TRY_CUDA(cudaMemsetAsync(job.counter, 0, sizeof(unsigned), s));
+    if (job.precision == URCHIN_F64) {
+        if (job.kernel == URCHIN_KERNEL_GT) return launch_one<double, URCHIN_KERNEL_GT>(P, s);
+        return launch_one<double, URCHIN_KERNEL_M4>(P, s);
+    }
+    if (job.kernel == URCHIN_KERNEL_GT) return launch_one<float, URCHIN_KERNEL_GT>(P, s);
+    return launch_one<float, URCHIN_KERNEL_M4>(P, s);
+}
+
+// w[s] = A[s] x[perm[s]]
+__global__ void k_weights(const float* __restrict__ A32, const double* __restrict__ A64,
+                          const int32_t* __restrict__ perm, const double* __restrict__ x, int64_t n,
+                          float* w32, double* w64)
+{
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        double xv = x[perm[s]];
+        if (w64) w64[s] = A64[s] * xv;
+        if (w32) w32[s] = (float)(A64[s] * xv);
+    }
+}
+
+int launch_weights(const urchin_bvh* b, const double* x_orig, float* w32, double* w64, cudaStream_t s)
+{
+    unsigned grid = (unsigned)std::min<int64_t>((b->n + 255) / 256, 4096);
+    k_weights<<<grid, 256, 0, s>>>(b->A32, b->A64, b->perm, x_orig, b->n, w32, w64);
+    URCHIN_TRY(launched());
+    return URCHIN_OK;
+}
+
+__global__ void k_map_origins(const int32_t* __restrict__ origins, const int32_t* __restrict__ inv,
+                              int64_t n_orig, int64_t n, int32_t* items, unsigned* status)
+{
+    for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < n_orig;
+         o += (int64_t)gridDim.x * blockDim.x) {
+        int32_t i = origins[o];
+        if (i < 0 || i >= n) {
+            atomicOr(status, kStOrigin);
+            items[o] = 0;
+        } else {
+            items[o] = inv[i];
+        }
+    }
+}
+
+}  // namespace urchin
+
+extern "C" int urchin_trace_columns(const urchin_bvh* bvh, const double* x, const double* dirs, int R,
+                                    double l_ray, const int32_t* origins, int64_t n_orig, int kernel,
+                                    int precision, void* tau_out, urchin_stream_t stream)
+{
+    using namespace urchin;
+    clear_error();
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!bvh || !x || !dirs) return set_error(URCHIN_ERR_ARG, "urchin_trace_columns: NULL bvh, x or dirs");
+    if (R < 1 || R > URCHIN_MAX_RAYS)
+        return set_error(URCHIN_ERR_ARG, "urchin_trace_columns: R = %d out of range [1, %d]", R, URCHIN_MAX_RAYS);
+    if (!(l_ray >= 0.0) || !std::isfinite(l_ray))
+        return set_error(URCHIN_ERR_ARG, "urchin_trace_columns: l_ray must be finite and >= 0");
+    if (kernel != URCHIN_KERNEL_M4 && kernel != URCHIN_KERNEL_GT)
+        return set_error(URCHIN_ERR_ARG, "urchin_trace_columns: unknown kernel %d", kernel);
+    if (precision != URCHIN_F32 && precision != URCHIN_F64)
+        return set_error(URCHIN_ERR_ARG, "urchin_trace_columns: unknown precision %d", precision);
+    if (n_orig < 0) return set_error(URCHIN_ERR_ARG, "urchin_trace_columns: n_orig < 0");
+    if (!origins && n_orig != bvh->n)
+        return set_error(URCHIN_ERR_ARG, "urchin_trace_columns: origins NULL requires n_orig == n");
+    if (n_orig == 0) return URCHIN_OK;
+    if (!tau_out) return set_error(URCHIN_ERR_ARG, "urchin_trace_columns: tau_out is NULL");
+    for (int i = 0; i < 3 * R; ++i)
+        if (!std::isfinite(dirs[i])) return set_error(URCHIN_ERR_ARG, "urchin_trace_columns: non-finite direction");
+    for (int k = 0; k < R; ++k) {
+        double nn = dirs[3 * k] * dirs[3 * k] + dirs[3 * k + 1] * dirs[3 * k + 1] + dirs[3 * k + 2] * dirs[3 * k + 2];
+        if (std::fabs(nn - 1.0) > 1e-6)
+            return set_error(URCHIN_ERR_ARG, "urchin_trace_columns: direction %d is not a unit vector", k);
+    }
+    const int64_t n = bvh->n;
+    const bool f64 = precision == URCHIN_F64;
+    Layout lay;
+    size_t o_ctr = lay.take(2 * sizeof(unsigned));
+    size_t o_dirs = lay.take(sizeof(double) * 3 * (size_t)R);
+    size_t o_w = lay.take((f64 ? sizeof(double) : sizeof(float)) * (size_t)n);
+    size_t o_items = lay.take(origins ? sizeof(int32_t) * (size_t)n_orig : 0);
+    Scratch scr;
+    URCHIN_TRY(scr.alloc(lay.bytes, s));
+    unsigned* ctr = scr.at<unsigned>(o_ctr);
+    URCHIN_TRY_CUDA(cudaMemsetAsync(ctr, 0, 2 * sizeof(unsigned), s));
+    URCHIN_TRY_CUDA(cudaMemcpyAsync(scr.at<double>(o_dirs), dirs, sizeof(double) * 3 * (size_t)R,
+                                    cudaMemcpyHostToDevice, s));
+    URCHIN_TRY(launch_weights(bvh, x, f64 ? nullptr : scr.at<float>(o_w), f64 ? scr.at<double>(o_w) : nullptr, s));
+    TraceJob job{};
+    job.bvh = bvh;
+    job.w32 = f64 ? nullptr : scr.at<float>(o_w);
+    job.w64 = f64 ? scr.at<double>(o_w) : nullptr;
+    job.dirs_dev = scr.at<double>(o_dirs);
+    job.R = R;
+    job.l_ray = l_ray;
+    job.n_items = n_orig;
+    job.row_stride = R;
+    job.k_stride = 1;
+    job.out = tau_out;
+    job.kernel = kernel;
+    job.precision = precision;
+    job.counter = ctr;
+    job.status = ctr + 1;
+    if (origins) {
+        int32_t* items = scr.at<int32_t>(o_items);
+        unsigned grid = (unsigned)std::min<int64_t>((n_orig + 255) / 256, 4096);
+        k_map_origins<<<grid, 256, 0, s>>>(origins, bvh->inv, n_orig, n, items, ctr + 1);
+        URCHIN_TRY(launched());
+        job.items = items;
+        job.out_row = nullptr;
+    } else {
+        // all particles, in Morton order for coherence; row = original index
+        job.items = nullptr;
+        job.out_row = bvh->perm;
+    }
+    URCHIN_TRY(launch_trace(job, s));
+    unsigned st = 0;
+    URCHIN_TRY_CUDA(cudaMemcpyAsync(&st, ctr + 1, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    scr.release();
+    URCHIN_TRY_CUDA(cudaStreamSynchronize(s));
+    if (st & kStOrigin) return set_error(URCHIN_ERR_ARG, "urchin_trace_columns: origin index out of range");
+    if (st & kStStack) return set_error(URCHIN_ERR_CUDA, "urchin_trace_columns: traversal stack overflow");
+    if (st & kStVisit) return set_error(URCHIN_ERR_CUDA, "urchin_trace_columns: malformed tree (visit limit)");
+    return URCHIN_OK;
+}

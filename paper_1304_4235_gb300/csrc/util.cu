@@ -1,0 +1,348 @@
+// Error reporting, constants, scratch memory, and the device scan / radix
+// sort / compaction primitives used by the BVH build and the solver.
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <string>
+
+#include "common.cuh"
+
+namespace urchin {
+
+static thread_local char g_last_error[512] = "";
+
+int set_error(int status, const char* fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
+    va_end(ap);
+    return status;
+}
+
+void clear_error() { g_last_error[0] = '\0'; }
+
+double sigma_th_cm2()
+{
+    const double alpha_fs = 7.2973525693e-3;       // CODATA 2018
+    const double bohr_cm = 5.29177210903e-9;       // CODATA 2018
+    const double e4 = std::exp(4.0);
+    return 512.0 * kPi / (3.0 * e4) * alpha_fs * kPi * bohr_cm * bohr_cm;
+}
+
+GtConst gt_constants()
+{
+    GtConst c;
+    c.t = 2.0 * std::pow(kPi, 1.0 / 6.0);
+    c.t2 = c.t * c.t;
+    double D = std::erf(c.t) - 2.0 * c.t * std::exp(-c.t2) / std::sqrt(kPi);
+    c.pref = std::sqrt(kPi) / (2.0 * c.t * D);
+    return c;
+}
+
+int Scratch::alloc(size_t bytes, cudaStream_t s)
+{
+    release();
+    stream = s;
+    if (bytes == 0) bytes = 256;
+    cudaError_t e = cudaMallocAsync(&ptr, bytes, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        ptr = nullptr;
+        return set_error(e == cudaErrorMemoryAllocation ? URCHIN_ERR_NOMEM : URCHIN_ERR_CUDA,
+                         "cudaMallocAsync(%zu bytes): %s", bytes, cudaGetErrorString(e));
+    }
+    return URCHIN_OK;
+}
+
+void Scratch::release()
+{
+    if (ptr) cudaFreeAsync(ptr, stream);
+    ptr = nullptr;
+}
+
+static std::atomic<long long> g_launches{0};
+
+int launched()
+{
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return set_error(URCHIN_ERR_CUDA, "kernel launch failed: %s", cudaGetErrorString(e));
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return URCHIN_OK;
+}
+
+int grid_for(const void* kernel, int block, size_t smem, int* grid_out)
+{
+    int dev = 0, sms = 0, per_sm = 0;
+    URCHIN_TRY_CUDA(cudaGetDevice(&dev));
+    URCHIN_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    URCHIN_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem));
+    if (per_sm < 1) per_sm = 1;
+    *grid_out = sms * per_sm;
+    return URCHIN_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Exclusive scan: tiles of kScanTile values per block, recursive on tile sums.
+// ---------------------------------------------------------------------------
+constexpr int kScanThreads = 512;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+// Block-wide exclusive scan of one value per thread; returns the prefix and
+// writes the block total to *total.
+__device__ uint32_t block_excl_scan(uint32_t v, uint32_t* total)
+{
+    __shared__ uint32_t warp_sums[kScanThreads / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t incl = warp_incl_scan(v);
+    if (lane == 31) warp_sums[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t ws = (lane < kScanThreads / 32) ? warp_sums[lane] : 0u;
+        uint32_t wi = warp_incl_scan(ws);
+        if (lane < kScanThreads / 32) warp_sums[lane] = wi - ws;
+        if (lane == kScanThreads / 32 - 1) *total = wi;
+    }
+    __syncthreads();
+    uint32_t r = incl - v + warp_sums[wid];
+    __syncthreads();
+    return r;
+}
+
+__global__ void k_scan_tiles(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tile_sums,
+                             uint32_t* total_dev)
+{
+    __shared__ uint32_t tot;
+    int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    uint32_t v[kScanItems];
+    uint32_t sum = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        v[i] = (base + i < n) ? in[base + i] : 0u;
+        sum += v[i];
+    }
+    uint32_t pre = block_excl_scan(sum, &tot);
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        if (base + i < n) out[base + i] = pre;
+        pre += v[i];
+    }
+    if (threadIdx.x == 0) {
+        if (tile_sums) tile_sums[blockIdx.x] = tot;
+        if (total_dev && gridDim.x == 1) *total_dev = tot;
+    }
+}
+
+__global__ void k_scan_add(uint32_t* out, int64_t n, const uint32_t* tile_pre)
+{
+    int64_t base = (int64_t)blockIdx.x * kScanTile;
+    uint32_t add = tile_pre[blockIdx.x];
+    for (int i = threadIdx.x; i < kScanTile; i += blockDim.x)
+        if (base + i < n) out[base + i] += add;
+}
+
+static int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+size_t scan_tmp_bytes(int64_t n)
+{
+    size_t bytes = 0;
+    int64_t m = n;
+    while (m > kScanTile) {
+        m = ceil_div(m, kScanTile);
+        bytes += ((size_t)m * 4 + 255) & ~size_t(255);
+    }
+    return bytes + 256;
+}
+
+int scan_exclusive_u32(const uint32_t* in, uint32_t* out, int64_t n, void* tmp, uint32_t* total_dev,
+                       cudaStream_t s)
+{
+    if (n <= 0) {
+        if (total_dev) URCHIN_TRY_CUDA(cudaMemsetAsync(total_dev, 0, 4, s));
+        return URCHIN_OK;
+    }
+    int64_t tiles = ceil_div(n, kScanTile);
+    if (tiles == 1) {
+        k_scan_tiles<<<1, kScanThreads, 0, s>>>(in, out, n, nullptr, total_dev);
+        URCHIN_TRY(launched());
+        return URCHIN_OK;
+    }
+    uint32_t* sums = static_cast<uint32_t*>(tmp);
+    void* rest = static_cast<char*>(tmp) + (((size_t)tiles * 4 + 255) & ~size_t(255));
+    k_scan_tiles<<<(unsigned)tiles, kScanThreads, 0, s>>>(in, out, n, sums, nullptr);
+    URCHIN_TRY(launched());
+    URCHIN_TRY(scan_exclusive_u32(sums, sums, tiles, rest, total_dev, s));
+    k_scan_add<<<(unsigned)tiles, kScanThreads, 0, s>>>(out, n, sums);
+    URCHIN_TRY(launched());
+    return URCHIN_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Stable LSD radix sort, 4-bit digits, 256 threads x 16 items per tile.
+// ---------------------------------------------------------------------------
+constexpr int kRadixThreads = 256;
+constexpr int kRadixRounds = 16;
+constexpr int kRadixTile = kRadixThreads * kRadixRounds;
+constexpr int kRadixDigits = 16;
+
+__global__ void k_radix_hist(const uint32_t* keys, int64_t n, int shift, uint32_t* hist, int nblocks)
+{
+    __shared__ uint32_t cnt[kRadixDigits];
+    if (threadIdx.x < kRadixDigits) cnt[threadIdx.x] = 0;
+    __syncthreads();
+    int64_t base = (int64_t)blockIdx.x * kRadixTile;
+    for (int r = 0; r < kRadixRounds; ++r) {
+        int64_t i = base + (int64_t)r * kRadixThreads + threadIdx.x;
+        if (i < n) atomicAdd(&cnt[(keys[i] >> shift) & 15u], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x < kRadixDigits) hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = cnt[threadIdx.x];
+}
+
+__global__ void k_radix_scatter(const uint32_t* kin, const int32_t* vin, uint32_t* kout, int32_t* vout,
+                                int64_t n, int shift, const uint32_t* offsets, int nblocks)
+{
+    constexpr int W = kRadixThreads / 32;
+    __shared__ uint32_t running[kRadixDigits];
+    __shared__ uint32_t wcnt[W][kRadixDigits + 1];
+    __shared__ uint32_t wpre[W][kRadixDigits + 1];
+    __shared__ uint32_t rtot[kRadixDigits];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (threadIdx.x < kRadixDigits)
+        running[threadIdx.x] = offsets[(int64_t)threadIdx.x * nblocks + blockIdx.x];
+    const uint32_t lt = (1u << lane) - 1u;
+    int64_t base = (int64_t)blockIdx.x * kRadixTile;
+    for (int r = 0; r < kRadixRounds; ++r) {
+        for (int t = threadIdx.x; t < W * (kRadixDigits + 1); t += blockDim.x)
+            (&wcnt[0][0])[t] = 0;
+        __syncthreads();
+        int64_t i = base + (int64_t)r * kRadixThreads + threadIdx.x;
+        bool valid = i < n;
+        uint32_t key = valid ? kin[i] : 0u;
+        int32_t val = valid ? vin[i] : 0;
+        uint32_t d = valid ? ((key >> shift) & 15u) : (uint32_t)kRadixDigits;
+        uint32_t peers = __match_any_sync(0xffffffffu, d);
+        uint32_t rank = __popc(peers & lt);
+        if (rank == 0) wcnt[wid][d] = __popc(peers);
+        __syncthreads();
+        if (threadIdx.x < kRadixDigits) {
+            uint32_t acc = 0;
+            for (int w = 0; w < W; ++w) {
+                wpre[w][threadIdx.x] = acc;
+                acc += wcnt[w][threadIdx.x];
+            }
+            rtot[threadIdx.x] = acc;
+        }
+        __syncthreads();
+        if (valid) {
+            uint32_t pos = running[d] + wpre[wid][d] + rank;
+            if (pos < n) {          // always true for a consistent histogram
+                kout[pos] = key;
+                vout[pos] = val;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x < kRadixDigits) running[threadIdx.x] += rtot[threadIdx.x];
+        __syncthreads();
+    }
+}
+
+size_t radix_tmp_bytes(int64_t n)
+{
+    int64_t nblocks = ceil_div(n, kRadixTile);
+    size_t b = 0;
+    b += ((size_t)n * 4 + 255) & ~size_t(255);                      // alt keys
+    b += ((size_t)n * 4 + 255) & ~size_t(255);                      // alt vals
+    b += ((size_t)nblocks * kRadixDigits * 4 + 255) & ~size_t(255); // histogram
+    b += scan_tmp_bytes(nblocks * kRadixDigits);
+    return b;
+}
+
+int radix_sort_pairs(uint32_t* keys, int32_t* vals, int64_t n, int bits, void* tmp, cudaStream_t s)
+{
+    if (n <= 1) return URCHIN_OK;
+    int64_t nblocks = ceil_div(n, kRadixTile);
+    char* p = static_cast<char*>(tmp);
+    uint32_t* k2 = reinterpret_cast<uint32_t*>(p);
+    p += ((size_t)n * 4 + 255) & ~size_t(255);
+    int32_t* v2 = reinterpret_cast<int32_t*>(p);
+    p += ((size_t)n * 4 + 255) & ~size_t(255);
+    uint32_t* hist = reinterpret_cast<uint32_t*>(p);
+    p += ((size_t)nblocks * kRadixDigits * 4 + 255) & ~size_t(255);
+    void* stmp = p;
+    int passes = (bits + 3) / 4;
+    uint32_t *ka = keys, *kb = k2;
+    int32_t *va = vals, *vb = v2;
+    for (int pass = 0; pass < passes; ++pass) {
+        int shift = 4 * pass;
+        k_radix_hist<<<(unsigned)nblocks, kRadixThreads, 0, s>>>(ka, n, shift, hist, (int)nblocks);
+        URCHIN_TRY(launched());
+        URCHIN_TRY(scan_exclusive_u32(hist, hist, nblocks * kRadixDigits, stmp, nullptr, s));
+        k_radix_scatter<<<(unsigned)nblocks, kRadixThreads, 0, s>>>(ka, va, kb, vb, n, shift, hist,
+                                                                    (int)nblocks);
+        URCHIN_TRY(launched());
+        uint32_t* tk = ka; ka = kb; kb = tk;
+        int32_t* tv = va; va = vb; vb = tv;
+    }
+    if (ka != keys) {
+        URCHIN_TRY_CUDA(cudaMemcpyAsync(keys, ka, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
+        URCHIN_TRY_CUDA(cudaMemcpyAsync(vals, va, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
+    }
+    return URCHIN_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Compaction
+// ---------------------------------------------------------------------------
+__global__ void k_flags_u32(const uint8_t* flags, uint32_t* out, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = flags[i] ? 1u : 0u;
+}
+
+__global__ void k_compact_scatter(const uint8_t* flags, const uint32_t* pos, int64_t n, int32_t* out)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        if (flags[i] && pos[i] < n) out[pos[i]] = (int32_t)i;
+}
+
+size_t compact_tmp_bytes(int64_t n)
+{
+    return (((size_t)n * 4 + 255) & ~size_t(255)) + scan_tmp_bytes(n);
+}
+
+int compact_indices(const uint8_t* flags, int64_t n, int32_t* out, uint32_t* count_dev, void* tmp,
+                    cudaStream_t s)
+{
+    uint32_t* pos = static_cast<uint32_t*>(tmp);
+    void* stmp = static_cast<char*>(tmp) + (((size_t)n * 4 + 255) & ~size_t(255));
+    unsigned grid = (unsigned)std::min<int64_t>(ceil_div(n, 256), 4096);
+    if (grid == 0) grid = 1;
+    k_flags_u32<<<grid, 256, 0, s>>>(flags, pos, n);
+    URCHIN_TRY(launched());
+    URCHIN_TRY(scan_exclusive_u32(pos, pos, n, stmp, count_dev, s));
+    k_compact_scatter<<<grid, 256, 0, s>>>(flags, pos, n, out);
+    URCHIN_TRY(launched());
+    return URCHIN_OK;
+}
+
+}  // namespace urchin
+
+extern "C" const char* urchin_last_error(void) { return urchin::g_last_error; }
+
+extern "C" const char* urchin_version(void) { return "urchin-gb300 0.1 (sm_103a)"; }
+
+extern "C" int64_t urchin_kernel_launches(void) { return (int64_t)urchin::g_launches.load(); }
