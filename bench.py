@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--max-iter", type=int, default=200, help="sweep / Newton-step limit of one solve")
+    ap.add_argument("--halo-n", type=int, default=262144, help="particles (profiling of smaller cases)")
     return ap.parse_args()
 
 
@@ -181,7 +183,7 @@ def main():
     args = parse()
     import workloads as W
 
-    w = W.halo()
+    w = W.halo(n=args.halo_n)
     if args.impl == "reference":
         reference_arm(args, w)
         return
@@ -222,7 +224,7 @@ def main():
         bvh = U.urchin_build_bvh(dd["px"], dd["py"], dd["pz"], dd["h"], dd["m"], w.periodic, w.box, w.unit_cm)
         x = torch.empty(w.n, dtype=torch.float64, device=dev) if x_out is None else x_out
         x, st = U.urchin_solve(bvh, dirs, w.l_ray, s_d, w_d, dd["nH"], dd["T"], x, tol=1e-3, tau_skip=1e-4,
-                               max_iter=200, method=method, segments=segs, precision=U.F32,
+                               max_iter=args.max_iter, method=method, segments=segs, precision=U.F32,
                                case_rule=U.CASE_AUTO, profile=True, raise_not_converged=False)
         bvh.close()
         return x, st
@@ -321,7 +323,9 @@ def main():
                      "frac": (achieved / hbm) if achieved else None, "traffic": traffic,
                      "kernel": "k_trace<float,M4>", "peak_kind": peak_kind,
                      "alg_bytes_per_launch": per_launch_bytes, "launch_ms": per_launch_s * 1e3,
-                     "hits_per_launch": hits / max(trace_launches, 1)},
+                     "hits_per_launch": hits / max(trace_launches, 1),
+                     "sphere_tests_per_hit": sum(st["sphere_tests"] for st in stats) / max(hits, 1),
+                     "node_visits_per_hit": sum(st["node_visits"] for st in stats) / max(hits, 1)},
         "clocks": clk,
         "e2e": e2e,
     }

@@ -232,6 +232,8 @@ typedef struct {
     int64_t hits;                 /* ray-sphere chord evaluations (profile=1)  */
     double  trace_s;              /* GPU time of the traversals (profile=1)    */
     int     trace_launches;       /* traversal kernel launches                 */
+    int64_t sphere_tests;         /* ray-sphere tests at leaves (profile=1)    */
+    int64_t node_visits;          /* internal nodes visited (profile=1)        */
 } urchin_solve_stats;
 
 /* Iterate to the equilibrium neutral fraction (Sec. 4): x starts at x_thin

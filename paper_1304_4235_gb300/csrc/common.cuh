@@ -88,6 +88,11 @@ size_t scan_tmp_bytes(int64_t n);
 int scan_exclusive_u32(const uint32_t* in, uint32_t* out, int64_t n, void* tmp,
                        uint32_t* total_dev, cudaStream_t s);
 
+// Exclusive prefix sum of n uint32 counts into uint64 offsets.
+size_t scan64_tmp_bytes(int64_t n);
+int scan_counts_u64(const uint32_t* in, uint64_t* out, int64_t n, void* tmp, uint64_t* total_dev,
+                    cudaStream_t s);
+
 // Stable LSD radix sort of (key, value) pairs on the low `bits` bits of key.
 size_t radix_tmp_bytes(int64_t n);
 int radix_sort_pairs(uint32_t* keys, int32_t* vals, int64_t n, int bits, void* tmp,
@@ -124,6 +129,7 @@ struct urchin_bvh {
     double* A64 = nullptr;        // [n]
     int32_t* perm = nullptr;      // [n] Morton slot -> original index
     int32_t* inv = nullptr;       // [n] original index -> Morton slot
+    float2* ktab = nullptr;       // [kKTab + 1] full-chord M4 table
 };
 
 namespace urchin {
@@ -135,8 +141,14 @@ constexpr unsigned kStNonfinite = 4u;   // non-finite or non-positive x
 constexpr unsigned kStInput = 8u;       // n_H or T not finite and > 0
 constexpr unsigned kStWarm = 16u;       // warm-start x outside (0, 1]
 constexpr unsigned kStVisit = 32u;      // traversal visit limit (malformed tree)
+constexpr unsigned kStSegment = 64u;    // stored-segment fill disagrees with its count
 
-constexpr int kLeafMax = 4;       // subtrees with <= kLeafMax particles become leaves
+constexpr int kLeafMax = 4;
+constexpr int kKTab = 2048;       // intervals of the full-chord M4 table in t = b^2/h^2
+
+// Full-chord M4 integral K(t) = int_{-c}^{c} shape(sqrt(t + u^2)) du, c = sqrt(1-t),
+// tabulated at t_i = i / kKTab as (K(t_i), dK/dt(t_i) / kKTab), host side.
+void m4_full_table(float2* out /* [kKTab + 1] */);       // subtrees with <= kLeafMax particles become leaves
 constexpr int kStackMax = 64;     // traversal stack (tree depth <= 62 for 30-bit codes)
 
 // Column tracing shared by urchin_trace_columns and urchin_solve.
@@ -158,6 +170,11 @@ struct TraceJob {
     unsigned int* counter;        // one device uint (work queue), zeroed here
     unsigned int* status;         // one device uint: error flags (may be NULL)
     unsigned long long* hits;     // chord evaluations (may be NULL)
+    int mode;                     // 0: columns, 1: count hits per ray, 2: fill segments (+ columns)
+    uint32_t* counts;             // mode 1: [R * n_items], index k * n_items + item
+    const uint64_t* row_ptr;      // mode 2: [R * n_items + 1] offsets of each ray's segments
+    int32_t* seg_col;             // mode 2: Morton index of the particle per segment
+    void* seg_val;                // mode 2: A_j * chord integral per segment (precision's type)
 };
 int launch_trace(const TraceJob& job, cudaStream_t s);
 

@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "common.cuh"
@@ -297,6 +298,8 @@ void free_bvh_arrays(urchin_bvh* b)
     cudaFree(b->A64);
     cudaFree(b->perm);
     cudaFree(b->inv);
+    cudaFree(b->ktab);
+    b->ktab = nullptr;
     b->nodes = nullptr;
     b->xyzh = nullptr;
     b->A32 = nullptr;
@@ -320,6 +323,19 @@ int build(const urchin_particles* p, const urchin_box* box, urchin_bvh* b, cudaS
     URCHIN_TRY_CUDA(cudaMalloc(&b->A64, sizeof(double) * (size_t)n));
     URCHIN_TRY_CUDA(cudaMalloc(&b->perm, sizeof(int32_t) * (size_t)n));
     URCHIN_TRY_CUDA(cudaMalloc(&b->inv, sizeof(int32_t) * (size_t)n));
+    URCHIN_TRY_CUDA(cudaMalloc(&b->ktab, sizeof(float2) * (kKTab + 1)));
+    {
+        static float2 table[kKTab + 1];
+        static bool ready = false;
+        static std::mutex mu;
+        std::lock_guard<std::mutex> lock(mu);
+        if (!ready) {
+            m4_full_table(table);
+            ready = true;
+        }
+        URCHIN_TRY_CUDA(cudaMemcpyAsync(b->ktab, table, sizeof(table), cudaMemcpyHostToDevice, s));
+        URCHIN_TRY_CUDA(cudaStreamSynchronize(s));
+    }
 
     const int64_t ni = std::max<int64_t>(1, n - 1);
     Layout lay;

@@ -1,0 +1,154 @@
+// Stored-segment columns (sparse matrix-vector product) and the small dense
+// vector kernels of the Newton-Krylov solver.
+//
+// With the per-ray segment lists stored once (column j, value A_j * chord
+// integral), a sweep's columns are tau_r = sum_e val_e x_{col_e}: a stream
+// over the segment arrays (8 bytes per segment in FP32) with a gather of x
+// from L2.  Rows are indexed k * n + particle (direction-major), as written by
+// the fill traversal.
+#include <algorithm>
+
+#include "linalg.cuh"
+
+namespace urchin {
+
+namespace {
+
+constexpr int kSpmvThreads = 256;
+
+// One warp per ray; lanes stride the ray's segments four at a time.
+template <typename Real>
+__global__ void __launch_bounds__(kSpmvThreads) k_spmv(SpmvArgs A)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (kSpmvThreads / 32);
+    const int64_t total = (int64_t)A.R * A.n_items;
+    const Real* val = static_cast<const Real*>(A.val);
+    const Real* xv = static_cast<const Real*>(A.xvec);
+    Real* out = static_cast<Real*>(A.out);
+    for (int64_t w = (int64_t)blockIdx.x * (kSpmvThreads / 32) + (threadIdx.x >> 5); w < total; w += warps) {
+        const int64_t k = w / A.n_items;
+        const int64_t a = w - k * A.n_items;
+        const int64_t i = A.items ? (int64_t)A.items[a] : a;
+        const int64_t row = k * A.n_rows_per_k + i;
+        const int64_t beg = (int64_t)A.row_ptr[row], end = (int64_t)A.row_ptr[row + 1];
+        Real s = Real(0), c = Real(0);
+        int64_t e = beg + lane;
+        for (; e + 96 < end; e += 128) {
+            const int32_t j0 = __ldcs(A.col + e), j1 = __ldcs(A.col + e + 32);
+            const int32_t j2 = __ldcs(A.col + e + 64), j3 = __ldcs(A.col + e + 96);
+            const Real v0 = __ldcs(val + e), v1 = __ldcs(val + e + 32);
+            const Real v2 = __ldcs(val + e + 64), v3 = __ldcs(val + e + 96);
+            const Real t = (v0 * __ldg(xv + j0) + v1 * __ldg(xv + j1)) + (v2 * __ldg(xv + j2) + v3 * __ldg(xv + j3));
+            const Real y = t - c;
+            const Real u = s + y;
+            c = (u - s) - y;
+            s = u;
+        }
+        for (; e < end; e += 32) {
+            const Real t = __ldcs(val + e) * __ldg(xv + __ldcs(A.col + e));
+            const Real y = t - c;
+            const Real u = s + y;
+            c = (u - s) - y;
+            s = u;
+        }
+        s -= c;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) out[a + k * A.n_items] = s;
+    }
+}
+
+// partial[i * nb + b] = sum over block b's share of V_i . w
+__global__ void k_dots(const double* __restrict__ V, int64_t ld, int count, const double* __restrict__ w,
+                       int64_t n, double* partial)
+{
+    __shared__ double red[8];
+    const int i = blockIdx.y;
+    const double* v = V + (int64_t)i * ld;
+    double acc = 0.0;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+        acc += v[t] * w[t];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q];
+        partial[(int64_t)i * gridDim.x + blockIdx.x] = t;
+    }
+    (void)count;
+}
+
+__global__ void k_dots_reduce(const double* partial, int nb, int count, double* out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    double t = 0.0;
+    for (int b = 0; b < nb; ++b) t += partial[(int64_t)i * nb + b];
+    out[i] = t;
+}
+
+// w -= sum_i coef[i] V_i
+__global__ void k_subtract(double* __restrict__ w, const double* __restrict__ V, int64_t ld, int count,
+                           const double* __restrict__ coef, int64_t n)
+{
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        double acc = w[t];
+        for (int i = 0; i < count; ++i) acc -= coef[i] * V[(int64_t)i * ld + t];
+        w[t] = acc;
+    }
+}
+
+// y = alpha x + beta y
+__global__ void k_axpby(double alpha, const double* __restrict__ x, double beta, double* __restrict__ y, int64_t n)
+{
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+        y[t] = alpha * x[t] + beta * y[t];
+}
+
+unsigned grid1(int64_t n) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 2048)); }
+
+}  // namespace
+
+int launch_spmv(const SpmvArgs& A, cudaStream_t s)
+{
+    if (A.n_items <= 0) return URCHIN_OK;
+    int64_t warps = (int64_t)A.R * A.n_items;
+    int grid = 0;
+    const void* fn = A.precision == URCHIN_F64 ? (const void*)k_spmv<double> : (const void*)k_spmv<float>;
+    URCHIN_TRY(grid_for(fn, kSpmvThreads, 0, &grid));
+    int64_t need = (warps + 7) / 8;
+    if (need < grid) grid = (int)std::max<int64_t>(need, 1);
+    if (A.precision == URCHIN_F64) k_spmv<double><<<grid, kSpmvThreads, 0, s>>>(A);
+    else k_spmv<float><<<grid, kSpmvThreads, 0, s>>>(A);
+    return launched();
+}
+
+size_t dots_tmp_bytes(int count) { return sizeof(double) * (size_t)count * 256 + 256; }
+
+int launch_dots(const double* V, int64_t ld, int count, const double* w, int64_t n, double* tmp, double* out,
+                cudaStream_t s)
+{
+    const int nb = (int)std::min<int64_t>(256, std::max<int64_t>(1, (n + 255) / 256));
+    dim3 g((unsigned)nb, (unsigned)count);
+    k_dots<<<g, 256, 0, s>>>(V, ld, count, w, n, tmp);
+    URCHIN_TRY(launched());
+    k_dots_reduce<<<(count + 63) / 64, 64, 0, s>>>(tmp, nb, count, out);
+    return launched();
+}
+
+int launch_subtract(double* w, const double* V, int64_t ld, int count, const double* coef, int64_t n,
+                    cudaStream_t s)
+{
+    k_subtract<<<grid1(n), 256, 0, s>>>(w, V, ld, count, coef, n);
+    return launched();
+}
+
+int launch_axpby(double alpha, const double* x, double beta, double* y, int64_t n, cudaStream_t s)
+{
+    k_axpby<<<grid1(n), 256, 0, s>>>(alpha, x, beta, y, n);
+    return launched();
+}
+
+}  // namespace urchin

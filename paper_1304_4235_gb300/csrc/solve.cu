@@ -13,6 +13,7 @@
 #include <cmath>
 #include <vector>
 
+#include "linalg.cuh"
 #include "solver.cuh"
 #include "spectral_device.cuh"
 
@@ -25,7 +26,7 @@ constexpr int kSweepThreads = 256;
 __global__ void k_setup(const urchin_bvh b, const double* __restrict__ nH, const double* __restrict__ T,
                         const double* __restrict__ x_in, int warm, double gthin, int case_rule, double y,
                         double* nHm, double* aA, double* aB, double* gc, double* x, float* w32, double* w64,
-                        unsigned* status)
+                        float* xs32, double* xs64, unsigned* status)
 {
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < b.n;
          s += (int64_t)gridDim.x * blockDim.x) {
@@ -49,6 +50,8 @@ __global__ void k_setup(const urchin_bvh b, const double* __restrict__ nH, const
         double wv = b.A64[s] * xv;
         if (w32) w32[s] = (float)wv;
         if (w64) w64[s] = wv;
+        if (xs32) xs32[s] = (float)xv;
+        if (xs64) xs64[s] = xv;
     }
 }
 
@@ -186,6 +189,8 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs A)
                     const double wv = A.A64[i] * xn;
                     if (A.w32) A.w32[i] = (float)wv;
                     if (A.w64) A.w64[i] = wv;
+                    if (A.xs32) A.xs32[i] = (float)xn;
+                    if (A.xs64) A.xs64[i] = xn;
                 }
             }
         }
@@ -198,6 +203,66 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs A)
     if ((threadIdx.x & 31) == 0) {
         if (my_max > 0.0) atomic_max_pos(A.maxrel, my_max);
         if (err) atomicOr(A.status, err);
+    }
+}
+
+// z_i = x_i v_a on the active particles (zero elsewhere, pre-cleared), and the
+// tracer weights A_i z_i when the tangent columns are traced
+__global__ void k_tangent_vector(const int32_t* __restrict__ items, int64_t n_act, const double* __restrict__ v,
+                                 const double* __restrict__ x, const double* __restrict__ A64, float* z32,
+                                 double* z64, float* wz32, double* wz64)
+{
+    for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < n_act; a += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t i = items[a];
+        const double z = x[i] * v[a];
+        if (z32) z32[i] = (float)z;
+        if (z64) z64[i] = z;
+        if (wz32) wz32[i] = (float)(A64[i] * z);
+        if (wz64) wz64[i] = A64[i] * z;
+    }
+}
+
+// (J v)_a = v_a - sum_k c_ak dtau_ak
+template <typename Real>
+__global__ void k_jv(const double* __restrict__ v, const double* __restrict__ ctan, const Real* __restrict__ dtau,
+                     int64_t n_act, int R, double* out)
+{
+    for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < n_act; a += (int64_t)gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int k = 0; k < R; ++k) acc += ctan[a + (int64_t)k * n_act] * (double)dtau[a + (int64_t)k * n_act];
+        out[a] = v[a] - acc;
+    }
+}
+
+// Newton residual -G_a = ln E_a - ln x_a
+__global__ void k_residual(const int32_t* __restrict__ items, int64_t n_act, const double* __restrict__ x,
+                           const double* __restrict__ E, double* r)
+{
+    for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < n_act; a += (int64_t)gridDim.x * blockDim.x)
+        r[a] = log(E[a]) - log(x[items[a]]);
+}
+
+// x_a <- x_a exp(d_a) (step limited to a factor e^3, x <= 1), or x_a <- E_a
+// when E is given; refresh the tracer weights and the column-precision copy
+__global__ void k_set_x(const int32_t* __restrict__ items, int64_t n_act, const double* __restrict__ d,
+                        const double* __restrict__ E, double* x, const double* __restrict__ A64, float* w32,
+                        double* w64, float* xs32, double* xs64)
+{
+    for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < n_act; a += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t i = items[a];
+        double xn;
+        if (E) {
+            xn = E[a];
+        } else {
+            const double step = fmin(fmax(d[a], -3.0), 3.0);
+            xn = fmin(1.0, x[i] * exp(step));
+        }
+        x[i] = xn;
+        const double wv = A64[i] * xn;
+        if (w32) w32[i] = (float)wv;
+        if (w64) w64[i] = wv;
+        if (xs32) xs32[i] = (float)xn;
+        if (xs64) xs64[i] = xn;
     }
 }
 
@@ -230,6 +295,8 @@ int Solver::init(const urchin_bvh* bvh_, const urchin_solve_params* P_, double* 
     n = bvh->n;
     f64 = P.precision == URCHIN_F64;
     const size_t rsz = f64 ? sizeof(double) : sizeof(float);
+    const bool may_store = P.segments != URCHIN_SEG_RECOMPUTE;
+    const int64_t rays = (int64_t)P.R * n;
     Layout lay;
     size_t o_misc = lay.take(64);
     size_t o_dirs = lay.take(sizeof(double) * 3 * (size_t)P.R);
@@ -239,12 +306,16 @@ int Solver::init(const urchin_bvh* bvh_, const urchin_solve_params* P_, double* 
     size_t o_aB = lay.take(sizeof(double) * (size_t)n);
     size_t o_gc = lay.take(sizeof(double) * (size_t)n);
     size_t o_w = lay.take(rsz * (size_t)n);
+    size_t o_xs = lay.take(may_store ? rsz * (size_t)n : 0);
     size_t o_act = lay.take((size_t)n);
     size_t o_list = lay.take(sizeof(int32_t) * (size_t)n);
-    size_t o_tau = lay.take(rsz * (size_t)n * P.R);
+    size_t o_tau = lay.take(rsz * (size_t)rays);
     size_t o_comp = lay.take(compact_tmp_bytes(n));
+    size_t o_cnt = lay.take(may_store ? sizeof(uint32_t) * (size_t)rays : 0);
+    size_t o_rp = lay.take(may_store ? sizeof(uint64_t) * (size_t)(rays + 1) : 0);
+    size_t o_st = lay.take(may_store ? scan64_tmp_bytes(rays) : 0);
     URCHIN_TRY(scr.alloc(lay.bytes, s));
-    misc = scr.at<unsigned long long>(o_misc);   // [0] maxrel, [1] counter+status
+    misc = scr.at<unsigned long long>(o_misc);   // [0] maxrel, [1] counter+status, [2] count, [3..5] profile
     dirs = scr.at<double>(o_dirs);
     x = scr.at<double>(o_x);
     nH = scr.at<double>(o_nH);
@@ -253,6 +324,13 @@ int Solver::init(const urchin_bvh* bvh_, const urchin_solve_params* P_, double* 
     gc = scr.at<double>(o_gc);
     w32 = f64 ? nullptr : scr.at<float>(o_w);
     w64 = f64 ? scr.at<double>(o_w) : nullptr;
+    if (may_store) {
+        xs32 = f64 ? nullptr : scr.at<float>(o_xs);
+        xs64 = f64 ? scr.at<double>(o_xs) : nullptr;
+        counts = scr.at<uint32_t>(o_cnt);
+        row_ptr = scr.at<uint64_t>(o_rp);
+        scan_tmp = scr.at<void>(o_st);
+    }
     active = scr.at<uint8_t>(o_act);
     list = scr.at<int32_t>(o_list);
     tau = scr.at<void>(o_tau);
@@ -271,13 +349,32 @@ int Solver::init(const urchin_bvh* bvh_, const urchin_solve_params* P_, double* 
         return set_error(URCHIN_ERR_ARG, "urchin_solve: spectrum weights must sum to a finite Gamma_thin > 0");
     unsigned grid = (unsigned)std::min<int64_t>((n + 255) / 256, 4096);
     k_setup<<<grid, 256, 0, s>>>(*bvh, P.nH, P.T, x_inout, P.warm_start, gthin, P.case_rule, P.y, nH, aA, aB, gc,
-                                 x, w32, w64, status);
+                                 x, w32, w64, xs32, xs64, status);
     URCHIN_TRY(launched());
     unsigned st = 0;
     URCHIN_TRY_CUDA(cudaMemcpyAsync(&st, status, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
     URCHIN_TRY_CUDA(cudaStreamSynchronize(s));
     if (st & kStInput) return set_error(URCHIN_ERR_ARG, "urchin_solve: n_H and T must be finite and > 0");
     if (st & kStWarm) return set_error(URCHIN_ERR_ARG, "urchin_solve: warm-start x must lie in (0, 1]");
+    return URCHIN_OK;
+}
+
+int Solver::timed_trace(TraceJob& job)
+{
+    job.counter = counter;
+    job.status = status;
+    job.hits = hits;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    if (P.profile) {
+        for (auto& e : ev) {
+            URCHIN_TRY_CUDA(cudaEventCreate(&e));
+            events.push_back(e);
+        }
+        URCHIN_TRY_CUDA(cudaEventRecord(ev[0], s));
+    }
+    URCHIN_TRY(launch_trace(job, s));
+    if (P.profile) URCHIN_TRY_CUDA(cudaEventRecord(ev[1], s));
+    stats.trace_launches += 1;
     return URCHIN_OK;
 }
 
@@ -298,23 +395,132 @@ int Solver::trace(const int32_t* items, int64_t n_items, const float* tw32, cons
     job.out = tau;
     job.kernel = P.kernel;
     job.precision = P.precision;
-    job.counter = counter;
-    job.status = status;
-    job.hits = hits;
-    cudaEvent_t ev[2] = {nullptr, nullptr};
-    if (P.profile) {
-        for (auto& e : ev) {
-            URCHIN_TRY_CUDA(cudaEventCreate(&e));
-            events.push_back(e);
-        }
-        URCHIN_TRY_CUDA(cudaEventRecord(ev[0], s));
-    }
-    URCHIN_TRY(launch_trace(job, s));
-    if (P.profile) URCHIN_TRY_CUDA(cudaEventRecord(ev[1], s));
+    job.mode = 0;
+    URCHIN_TRY(timed_trace(job));
     stats.traversals += 1;
-    stats.trace_launches += 1;
     stats.rays += n_items * P.R;
     return URCHIN_OK;
+}
+
+// Columns of the current x for the rays of `items` into tau (k-major).
+// Sweep 0 (all particles) also decides and builds the stored segments.
+int Solver::columns(const int32_t* items, int64_t n_items, int sweep0)
+{
+    if (!sweep0 && stored) {
+        SpmvArgs A{};
+        A.row_ptr = row_ptr;
+        A.col = seg_col;
+        A.val = seg_val;
+        A.xvec = f64 ? (const void*)xs64 : (const void*)xs32;
+        A.items = items;
+        A.n_items = n_items;
+        A.n_rows_per_k = n;
+        A.R = P.R;
+        A.precision = P.precision;
+        A.out = tau;
+        URCHIN_TRY(launch_spmv(A, s));
+        stats.traversals += 1;
+        stats.rays += n_items * P.R;
+        return URCHIN_OK;
+    }
+    if (!sweep0 || P.segments == URCHIN_SEG_RECOMPUTE) return trace(items, n_items, w32, w64);
+    // count every ray's hits, then decide whether the lists fit
+    TraceJob job{};
+    job.bvh = bvh;
+    job.w32 = w32;
+    job.w64 = w64;
+    job.dirs_dev = dirs;
+    job.R = P.R;
+    job.l_ray = P.l_ray;
+    job.items = items;
+    job.n_items = n_items;
+    job.row_stride = 1;
+    job.k_stride = n_items;
+    job.out = tau;
+    job.kernel = P.kernel;
+    job.precision = P.precision;
+    job.mode = 1;
+    job.counts = counts;
+    URCHIN_TRY(timed_trace(job));
+    const int64_t rays = (int64_t)P.R * n_items;
+    uint64_t* total = reinterpret_cast<uint64_t*>(misc + 6);
+    URCHIN_TRY(scan_counts_u64(counts, row_ptr, rays, scan_tmp, total, s));
+    URCHIN_TRY_CUDA(cudaMemcpyAsync(row_ptr + rays, total, sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+    uint64_t nnz = 0;
+    URCHIN_TRY_CUDA(cudaMemcpyAsync(&nnz, total, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+    URCHIN_TRY_CUDA(cudaStreamSynchronize(s));
+    const size_t vsz = f64 ? sizeof(double) : sizeof(float);
+    const size_t need = (size_t)nnz * (sizeof(int32_t) + vsz) + 1024;
+    bool fits = true;
+    if (P.segments == URCHIN_SEG_AUTO) {
+        size_t free_b = 0, total_b = 0;
+        URCHIN_TRY_CUDA(cudaMemGetInfo(&free_b, &total_b));
+        fits = need < (size_t)(0.85 * (double)free_b);
+    }
+    if (fits) {
+        Layout lay;
+        size_t o_col = lay.take(sizeof(int32_t) * (size_t)nnz);
+        size_t o_val = lay.take(vsz * (size_t)nnz);
+        int st = seg.alloc(lay.bytes, s);
+        if (st != URCHIN_OK) {
+            if (P.segments == URCHIN_SEG_STORE) return st;
+            fits = false;
+            clear_error();
+        } else {
+            seg_col = seg.at<int32_t>(o_col);
+            seg_val = seg.at<void>(o_val);
+        }
+    }
+    if (!fits) return trace(items, n_items, w32, w64);
+    stored = true;
+    stats.segments_stored = 1;
+    stats.nnz = (int64_t)nnz;
+    job.mode = 2;
+    job.row_ptr = row_ptr;
+    job.seg_col = seg_col;
+    job.seg_val = seg_val;
+    URCHIN_TRY(timed_trace(job));
+    stats.traversals += 2;
+    stats.rays += n_items * P.R;
+    return URCHIN_OK;
+}
+
+// Columns of the tangent vector (z = x v on the active particles) into tau.
+int Solver::linear_columns(const int32_t* items, int64_t n_items, const float* z32, const double* z64,
+                           float* wz32, double* wz64)
+{
+    stats.rays += n_items * P.R;
+    stats.traversals += 1;
+    if (stored) {
+        SpmvArgs A{};
+        A.row_ptr = row_ptr;
+        A.col = seg_col;
+        A.val = seg_val;
+        A.xvec = f64 ? (const void*)z64 : (const void*)z32;
+        A.items = items;
+        A.n_items = n_items;
+        A.n_rows_per_k = n;
+        A.R = P.R;
+        A.precision = P.precision;
+        A.out = tau;
+        return launch_spmv(A, s);
+    }
+    TraceJob job{};
+    job.bvh = bvh;
+    job.w32 = wz32;
+    job.w64 = wz64;
+    job.dirs_dev = dirs;
+    job.R = P.R;
+    job.l_ray = P.l_ray;
+    job.items = items;
+    job.n_items = n_items;
+    job.row_stride = 1;
+    job.k_stride = n_items;
+    job.out = tau;
+    job.kernel = P.kernel;
+    job.precision = P.precision;
+    job.mode = 0;
+    return timed_trace(job);
 }
 
 SweepArgs Solver::sweep_args(const int32_t* items, int64_t n_items, int sweep0)
@@ -333,6 +539,8 @@ SweepArgs Solver::sweep_args(const int32_t* items, int64_t n_items, int sweep0)
     A.A64 = bvh->A64;
     A.w32 = w32;
     A.w64 = w64;
+    A.xs32 = xs32;
+    A.xs64 = xs64;
     A.nH = nH;
     A.aA = aA;
     A.aB = aB;
@@ -356,6 +564,9 @@ int Solver::read_scalars(double* maxrel, unsigned* st)
     memcpy(&m, &h[0], sizeof(double));
     *maxrel = m;
     *st = (unsigned)(h[1] >> 32);
+    if (*st & kStNonfinite) return set_error(URCHIN_ERR_NONFINITE, "urchin_solve: non-finite neutral fraction");
+    if (*st & (kStStack | kStVisit)) return set_error(URCHIN_ERR_CUDA, "urchin_solve: traversal stack/visit limit hit");
+    if (*st & kStSegment) return set_error(URCHIN_ERR_CUDA, "urchin_solve: segment fill disagrees with its count");
     return URCHIN_OK;
 }
 
@@ -363,7 +574,7 @@ int Solver::first_sweep()
 {
     // sweep 0: every particle traced; tau_eff < tau_skip freezes it
     URCHIN_TRY_CUDA(cudaMemsetAsync(misc, 0, sizeof(unsigned long long), s));
-    URCHIN_TRY(trace(nullptr, n, w32, w64));
+    URCHIN_TRY(columns(nullptr, n, 1));
     URCHIN_TRY(launch_sweep(sweep_args(nullptr, n, 1), s));
     uint32_t* cnt = reinterpret_cast<uint32_t*>(misc + 2);
     URCHIN_TRY(compact_indices(active, n, list, cnt, comp_tmp, s));
@@ -372,8 +583,6 @@ int Solver::first_sweep()
     double m;
     unsigned st;
     URCHIN_TRY(read_scalars(&m, &st));
-    if (st & kStNonfinite) return set_error(URCHIN_ERR_NONFINITE, "urchin_solve: non-finite neutral fraction");
-    if (st & (kStStack | kStVisit)) return set_error(URCHIN_ERR_CUDA, "urchin_solve: traversal stack/visit limit hit");
     n_act = hc;
     stats.n_active = n_act;
     stats.particle_updates += n_act;
@@ -391,13 +600,11 @@ int Solver::plain()
     }
     while (stats.iterations < P.max_iter) {
         URCHIN_TRY_CUDA(cudaMemsetAsync(misc, 0, sizeof(unsigned long long), s));
-        URCHIN_TRY(trace(list, n_act, w32, w64));
+        URCHIN_TRY(columns(list, n_act, 0));
         URCHIN_TRY(launch_sweep(sweep_args(list, n_act, 0), s));
         double m;
         unsigned st;
         URCHIN_TRY(read_scalars(&m, &st));
-        if (st & kStNonfinite) return set_error(URCHIN_ERR_NONFINITE, "urchin_solve: non-finite neutral fraction");
-        if (st & (kStStack | kStVisit)) return set_error(URCHIN_ERR_CUDA, "urchin_solve: traversal stack/visit limit hit");
         stats.iterations += 1;
         stats.particle_updates += n_act;
         stats.max_rel_dx = m;
@@ -409,9 +616,151 @@ int Solver::plain()
     return URCHIN_OK;
 }
 
+// Newton-Krylov on the fixed point of the sweep map, in u = ln x over the
+// non-frozen particles: G(u) = u - ln E(Gamma(x)), with the recombination
+// case of each particle held at its current value.  J v = v - C dtau(x v)
+// where dtau is the column of the tangent vector (columns are linear in x)
+// and C holds c_ak = (1/E) dE/dGamma dGamma/dtau_k from the sweep kernel.
+// Each step solves J d = -G by GMRES(m) to relative residual eta and sets
+// x <- x exp(d); it stops when max |E - x| / x < dx_tol and returns x <- E,
+// the same test and the same final update as the plain sweep.
 int Solver::newton()
 {
-    return set_error(URCHIN_ERR_ARG, "urchin_solve: Newton-Krylov is not available yet");
+    URCHIN_TRY(first_sweep());
+    if (stats.max_rel_dx < P.tol || n_act == 0) {
+        stats.converged = 1;
+        return URCHIN_OK;
+    }
+    const int m = P.gmres_m;
+    const int64_t na = n_act;
+    const size_t rsz = f64 ? sizeof(double) : sizeof(float);
+    Layout lay;
+    size_t o_V = lay.take(sizeof(double) * (size_t)(m + 1) * na);
+    size_t o_E = lay.take(sizeof(double) * (size_t)na);
+    size_t o_c = lay.take(sizeof(double) * (size_t)na * P.R);
+    size_t o_d = lay.take(sizeof(double) * (size_t)na);
+    size_t o_z = lay.take(rsz * (size_t)n);
+    size_t o_wz = lay.take(stored ? 0 : rsz * (size_t)n);
+    size_t o_dt = lay.take(dots_tmp_bytes(m + 1));
+    size_t o_h = lay.take(sizeof(double) * (size_t)(m + 2));
+    URCHIN_TRY(nk.alloc(lay.bytes, s));
+    double* V = nk.at<double>(o_V);
+    double* E = nk.at<double>(o_E);
+    double* ctan = nk.at<double>(o_c);
+    double* d = nk.at<double>(o_d);
+    float* z32 = f64 ? nullptr : nk.at<float>(o_z);
+    double* z64 = f64 ? nk.at<double>(o_z) : nullptr;
+    float* wz32 = (stored || f64) ? nullptr : nk.at<float>(o_wz);
+    double* wz64 = (stored || !f64) ? nullptr : nk.at<double>(o_wz);
+    double* dtmp = nk.at<double>(o_dt);
+    double* hdev = nk.at<double>(o_h);
+    const unsigned g1 = (unsigned)std::max<int64_t>(1, std::min<int64_t>((na + 255) / 256, 2048));
+    std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1), hcol(m + 2), y(m);
+    double eta = 0.1, prev_norm = -1.0;
+
+    while (stats.iterations < P.max_iter) {
+        // residual at the current x (no update), with the tangent factors
+        URCHIN_TRY_CUDA(cudaMemsetAsync(misc, 0, sizeof(unsigned long long), s));
+        URCHIN_TRY(columns(list, na, 0));
+        SweepArgs A = sweep_args(list, na, 0);
+        A.want_tangent = 1;
+        A.ctan = ctan;
+        A.xeq_out = E;
+        URCHIN_TRY(launch_sweep(A, s));
+        double mrel;
+        unsigned st;
+        URCHIN_TRY(read_scalars(&mrel, &st));
+        stats.iterations += 1;
+        stats.particle_updates += na;
+        stats.max_rel_dx = mrel;
+        if (mrel < P.tol) {
+            k_set_x<<<g1, 256, 0, s>>>(list, na, nullptr, E, x, bvh->A64, w32, w64, xs32, xs64);
+            URCHIN_TRY(launched());
+            stats.converged = 1;
+            break;
+        }
+        if (stats.iterations >= P.max_iter) {
+            // out of steps: leave x at the last plain update, like the plain driver
+            k_set_x<<<g1, 256, 0, s>>>(list, na, nullptr, E, x, bvh->A64, w32, w64, xs32, xs64);
+            URCHIN_TRY(launched());
+            break;
+        }
+        // GMRES(m) for J d = -G, d0 = 0
+        k_residual<<<g1, 256, 0, s>>>(list, na, x, E, V);
+        URCHIN_TRY(launched());
+        URCHIN_TRY(launch_dots(V, na, 1, V, na, dtmp, hdev, s));
+        double beta2 = 0.0;
+        URCHIN_TRY_CUDA(cudaMemcpyAsync(&beta2, hdev, sizeof(double), cudaMemcpyDeviceToHost, s));
+        URCHIN_TRY_CUDA(cudaStreamSynchronize(s));
+        const double beta = std::sqrt(beta2);
+        if (prev_norm > 0.0) eta = std::min(0.1, std::max(1e-3, 0.9 * (beta / prev_norm) * (beta / prev_norm)));
+        prev_norm = beta;
+        URCHIN_TRY(launch_axpby(0.0, V, 1.0 / beta, V, na, s));
+        std::fill(gv.begin(), gv.end(), 0.0);
+        gv[0] = beta;
+        int kdim = 0;
+        for (int j = 0; j < m; ++j) {
+            double* vj = V + (size_t)j * na;
+            double* w = V + (size_t)(j + 1) * na;
+            // w = J v_j
+            if (z32) URCHIN_TRY_CUDA(cudaMemsetAsync(z32, 0, sizeof(float) * (size_t)n, s));
+            if (z64) URCHIN_TRY_CUDA(cudaMemsetAsync(z64, 0, sizeof(double) * (size_t)n, s));
+            if (wz32) URCHIN_TRY_CUDA(cudaMemsetAsync(wz32, 0, sizeof(float) * (size_t)n, s));
+            if (wz64) URCHIN_TRY_CUDA(cudaMemsetAsync(wz64, 0, sizeof(double) * (size_t)n, s));
+            k_tangent_vector<<<g1, 256, 0, s>>>(list, na, vj, x, bvh->A64, z32, z64, wz32, wz64);
+            URCHIN_TRY(launched());
+            URCHIN_TRY(linear_columns(list, na, z32, z64, wz32, wz64));
+            if (f64) k_jv<double><<<g1, 256, 0, s>>>(vj, ctan, static_cast<const double*>(tau), na, P.R, w);
+            else k_jv<float><<<g1, 256, 0, s>>>(vj, ctan, static_cast<const float*>(tau), na, P.R, w);
+            URCHIN_TRY(launched());
+            // classical Gram-Schmidt, twice
+            std::fill(hcol.begin(), hcol.end(), 0.0);
+            for (int pass = 0; pass < 2; ++pass) {
+                URCHIN_TRY(launch_dots(V, na, j + 1, w, na, dtmp, hdev, s));
+                URCHIN_TRY(launch_subtract(w, V, na, j + 1, hdev, na, s));
+                std::vector<double> hh(j + 1);
+                URCHIN_TRY_CUDA(cudaMemcpyAsync(hh.data(), hdev, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, s));
+                URCHIN_TRY_CUDA(cudaStreamSynchronize(s));
+                for (int i = 0; i <= j; ++i) hcol[i] += hh[i];
+            }
+            URCHIN_TRY(launch_dots(w, na, 1, w, na, dtmp, hdev, s));
+            double hn2 = 0.0;
+            URCHIN_TRY_CUDA(cudaMemcpyAsync(&hn2, hdev, sizeof(double), cudaMemcpyDeviceToHost, s));
+            URCHIN_TRY_CUDA(cudaStreamSynchronize(s));
+            const double hn = std::sqrt(std::max(hn2, 0.0));
+            hcol[j + 1] = hn;
+            if (hn > 0.0) URCHIN_TRY(launch_axpby(0.0, w, 1.0 / hn, w, na, s));
+            // Givens rotations on the new Hessenberg column
+            for (int i = 0; i < j; ++i) {
+                const double a = cs[i] * hcol[i] + sn[i] * hcol[i + 1];
+                hcol[i + 1] = -sn[i] * hcol[i] + cs[i] * hcol[i + 1];
+                hcol[i] = a;
+            }
+            const double r = std::hypot(hcol[j], hcol[j + 1]);
+            cs[j] = r > 0.0 ? hcol[j] / r : 1.0;
+            sn[j] = r > 0.0 ? hcol[j + 1] / r : 0.0;
+            hcol[j] = r;
+            hcol[j + 1] = 0.0;
+            gv[j + 1] = -sn[j] * gv[j];
+            gv[j] = cs[j] * gv[j];
+            for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hcol[i];
+            kdim = j + 1;
+            if (std::fabs(gv[j + 1]) <= eta * beta || hn == 0.0) break;
+        }
+        // y = H^-1 g (upper triangular), d = V y
+        for (int i = kdim - 1; i >= 0; --i) {
+            double acc = gv[i];
+            for (int k = i + 1; k < kdim; ++k) acc -= H[(size_t)i * m + k] * y[k];
+            y[i] = H[(size_t)i * m + i] != 0.0 ? acc / H[(size_t)i * m + i] : 0.0;
+        }
+        for (int i = 0; i < kdim; ++i) y[i] = -y[i];
+        URCHIN_TRY_CUDA(cudaMemcpyAsync(hdev, y.data(), sizeof(double) * kdim, cudaMemcpyHostToDevice, s));
+        URCHIN_TRY_CUDA(cudaMemsetAsync(d, 0, sizeof(double) * (size_t)na, s));
+        URCHIN_TRY(launch_subtract(d, V, na, kdim, hdev, na, s));
+        k_set_x<<<g1, 256, 0, s>>>(list, na, d, nullptr, x, bvh->A64, w32, w64, xs32, xs64);
+        URCHIN_TRY(launched());
+    }
+    return URCHIN_OK;
 }
 
 int Solver::finish(double* x_inout)
@@ -420,10 +769,12 @@ int Solver::finish(double* x_inout)
     k_finish<<<grid, 256, 0, s>>>(bvh->perm, x, n, x_inout);
     URCHIN_TRY(launched());
     if (P.profile) {
-        unsigned long long h = 0;
-        URCHIN_TRY_CUDA(cudaMemcpyAsync(&h, hits, sizeof(h), cudaMemcpyDeviceToHost, s));
+        unsigned long long h[3] = {0, 0, 0};
+        URCHIN_TRY_CUDA(cudaMemcpyAsync(h, hits, sizeof(h), cudaMemcpyDeviceToHost, s));
         URCHIN_TRY_CUDA(cudaStreamSynchronize(s));
-        stats.hits = (int64_t)h;
+        stats.hits = (int64_t)h[0];
+        stats.sphere_tests = (int64_t)h[1];
+        stats.node_visits = (int64_t)h[2];
         double total = 0.0;
         for (size_t i = 0; i + 1 < events.size(); i += 2) {
             float ms = 0.f;
@@ -432,6 +783,8 @@ int Solver::finish(double* x_inout)
         }
         stats.trace_s = total * 1e-3;
     }
+    nk.release();
+    seg.release();
     scr.release();
     URCHIN_TRY_CUDA(cudaStreamSynchronize(s));
     return URCHIN_OK;

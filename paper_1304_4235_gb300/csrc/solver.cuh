@@ -22,6 +22,8 @@ struct SweepArgs {
     const double* A64;
     float* w32;
     double* w64;
+    float* xs32;               // optional: x as float (stored-segment sweeps)
+    double* xs64;
     const double* nH;
     const double* aA;
     const double* aB;
@@ -67,10 +69,26 @@ struct Solver {
     int32_t* list = nullptr;
     void* tau = nullptr;
     void* comp_tmp = nullptr;
-    unsigned long long* hits = nullptr;          // misc[3], counted when P.profile
+    unsigned long long* hits = nullptr;          // misc[3..5], counted when P.profile
     std::vector<cudaEvent_t> events;             // start/stop pairs of each traversal
+    // stored segments
+    bool stored = false;
+    float* xs32 = nullptr;                       // x in the precision of the columns (Morton)
+    double* xs64 = nullptr;
+    uint32_t* counts = nullptr;
+    uint64_t* row_ptr = nullptr;
+    void* scan_tmp = nullptr;
+    int32_t* seg_col = nullptr;
+    void* seg_val = nullptr;
+    Scratch seg;
+    // Newton-Krylov
+    Scratch nk;
 
     ~Solver();
+    int columns(const int32_t* items, int64_t n_items, int sweep0);
+    int linear_columns(const int32_t* items, int64_t n_items, const float* z32, const double* z64,
+                       float* wz32, double* wz64);
+    int timed_trace(TraceJob& job);
 
     int init(const urchin_bvh* bvh, const urchin_solve_params* P, double* x_inout, cudaStream_t s);
     int trace(const int32_t* items, int64_t n_items, const float* tw32, const double* tw64);

@@ -20,6 +20,7 @@ namespace urchin {
 namespace {
 
 struct TraceParams {
+    const float2* ktab;           // [kKTab + 1] full-chord M4 table (value, slope x dt)
     const float4* nodes;
     int n_nodes;
     int n;
@@ -43,6 +44,24 @@ struct TraceParams {
     float root_lo[3], root_hi[3];
     double gt_t2, gt_t, gt_pref;
     int64_t n_chunks;
+    // stored-segment modes
+    uint32_t* counts;             // MODE_COUNT: hits per ray, index k * n_items + item
+    const uint64_t* row_ptr;      // MODE_FILL: first segment of each ray (same index), size + 1
+    int32_t* seg_col;             // MODE_FILL: Morton index of the particle
+    void* seg_val;                // MODE_FILL: A_j * chord integral (float or double)
+    const float* A32;
+    const double* A64;
+};
+
+constexpr int MODE_TAU = 0, MODE_COUNT = 1, MODE_FILL = 2;
+
+// Where a ray's hits go: the running column sum, and in MODE_FILL the
+// cursor into the ray's stored segment list.
+template <typename Real>
+struct Sink {
+    Real sum, comp;
+    unsigned nhit, ntest;
+    int64_t pos, end;
 };
 
 template <typename Real> struct RealOps;
@@ -135,6 +154,85 @@ __device__ __forceinline__ Real gt_chord(const TraceParams& P, Real b2, Real u1,
     return Real(P.gt_pref) * O::exp_(-Real(P.gt_t2) * b2) * (O::erf_(t * u2) - O::erf_(t * u1));
 }
 
+// ---- FP32 chord evaluation ------------------------------------------------
+// The antiderivatives above lose about two digits in FP32 over the outer
+// spline piece (terms of order 4 cancel to the small value of 2(1-q)^3), so
+// the FP32 path evaluates
+//   * full chords from a table of K(t) = int W du over the whole chord,
+//     t = b^2/h^2, with cubic Hermite interpolation (values and slopes at
+//     kKTab + 1 nodes, built on the host in double and staged in shared
+//     memory), and
+//   * partial chords piece by piece: the inner piece (q <= 1/2) by the
+//     antiderivative Fi (well conditioned), the outer piece by 8-point
+//     Gauss-Legendre quadrature of 2(1-q)^3, a smooth non-negative
+//     integrand on [s, c].
+__device__ __forceinline__ float m4_full_tab(const float2* tab, float t)
+{
+    float x = fminf(t, 1.0f) * (float)kKTab;
+    int i = min((int)x, kKTab - 1);
+    float f = x - (float)i;
+    float2 a = tab[i], b = tab[i + 1];
+    float f2 = f * f, f3 = f2 * f;
+    return (2.f * f3 - 3.f * f2 + 1.f) * a.x + (f3 - 2.f * f2 + f) * a.y + (3.f * f2 - 2.f * f3) * b.x +
+           (f3 - f2) * b.y;
+}
+
+__device__ __forceinline__ float m4_inner_prim_f(float b2, float a)
+{
+    float q = sqrtf(b2 + a * a);
+    float L = b2 > 0.f ? logf(a + q) - 0.5f * logf(b2) : 0.f;
+    return a * (1.f - 6.f * b2 - 2.f * a * a) + 1.5f * a * q * q * q + 2.25f * b2 * a * q + 2.25f * b2 * b2 * L;
+}
+
+// Gauss-Legendre nodes and weights on [-1, 1], n = 8
+__constant__ float kGLx[8] = {-0.9602898564975363f, -0.7966664774136267f, -0.5255324099163290f,
+                              -0.1834346424956498f, 0.1834346424956498f,  0.5255324099163290f,
+                              0.7966664774136267f,  0.9602898564975363f};
+__constant__ float kGLw[8] = {0.1012285362903763f, 0.2223810344533745f, 0.3137066458778873f,
+                              0.3626837833783620f, 0.3626837833783620f, 0.3137066458778873f,
+                              0.2223810344533745f, 0.1012285362903763f};
+
+__device__ __forceinline__ float m4_outer_gl(float b2, float a1, float a2)
+{
+    const float m = 0.5f * (a1 + a2), r = 0.5f * (a2 - a1);
+    float acc = 0.f;
+#pragma unroll
+    for (int g = 0; g < 8; ++g) {
+        float u = fmaf(r, kGLx[g], m);
+        float v = 1.f - sqrtf(fmaf(u, u, b2));
+        acc = fmaf(kGLw[g], v * v * v, acc);
+    }
+    return 2.f * r * acc;
+}
+
+// int_{a1}^{a2} M4shape du for 0 <= a1 < a2 <= c
+__device__ __forceinline__ float m4_piece_f(float b2, float a1, float a2)
+{
+    const float s = b2 < 0.25f ? sqrtf(0.25f - b2) : 0.f;
+    float r = 0.f;
+    if (a1 < s) r += m4_inner_prim_f(b2, fminf(a2, s)) - m4_inner_prim_f(b2, a1);
+    const float lo = fmaxf(a1, s);
+    if (a2 > lo) r += m4_outer_gl(b2, lo, a2);
+    return r;
+}
+
+__device__ __forceinline__ float m4_part_f(float b2, float u1, float u2)
+{
+    float t = 0.f;
+    if (u1 < 0.f) t += m4_piece_f(b2, fmaxf(0.f, -u2), -u1);
+    if (u2 > 0.f) t += m4_piece_f(b2, fmaxf(0.f, u1), u2);
+    return t;
+}
+
+// a*b - c*d with one rounding (Kahan's difference of products via FMA)
+__device__ __forceinline__ float dop(float a, float b, float c, float d)
+{
+    float w = c * d;
+    float e = fmaf(-c, d, w);
+    float f = fmaf(a, b, -w);
+    return f + e;
+}
+
 struct Kahan {
     __device__ __forceinline__ static void add(float& s, float& c, float v)
     {
@@ -169,13 +267,63 @@ __device__ __forceinline__ float safe_inv(double d)
     return fabs(d) > 1e-20 ? (float)(1.0 / d) : copysignf(1e30f, (float)d);
 }
 
-template <typename Real, int KERNEL>
+// FP32 hit evaluation: cheap rejection, then the impact parameter from an
+// error-free cross product, then the tabulated / piecewise chord integral.
+template <int KERNEL, int MODE>
+__device__ __forceinline__ void leaf_hits_f32(const TraceParams& P, const float2* tab, int ref, int cnt,
+                                              float sx, float sy, float sz, float dx, float dy, float dz,
+                                              float L, Sink<float>& k, unsigned& err)
+{
+    if (ref < 0 || cnt > kLeafMax || ref + cnt > P.n) return;   // never true for a well-formed tree
+    k.ntest += (unsigned)cnt;
+    for (int j = ref; j < ref + cnt; ++j) {
+        float4 q = __ldg(P.xyzh + j);
+        float ex = q.x - sx, ey = q.y - sy, ez = q.z - sz;
+        float cx = ey * dz - ez * dy, cy = ez * dx - ex * dz, cz = ex * dy - ey * dx;
+        float h2 = q.w * q.w;
+        if (cx * cx + cy * cy + cz * cz >= 1.0001f * h2) continue;
+        cx = dop(ey, dz, ez, dy);
+        cy = dop(ez, dx, ex, dz);
+        cz = dop(ex, dy, ey, dx);
+        float b2 = cx * cx + cy * cy + cz * cz;
+        if (b2 >= h2) continue;
+        float tc = ex * dx + ey * dy + ez * dz;
+        float ch = sqrtf(h2 - b2);
+        if (tc + ch <= 0.f || tc - ch >= L) continue;
+        ++k.nhit;
+        if (MODE == MODE_COUNT) continue;
+        float ih = 1.f / q.w;
+        float beta2 = b2 * ih * ih;
+        float F;
+        if (tc - ch >= 0.f && tc + ch <= L) {
+            if (KERNEL == URCHIN_KERNEL_M4) F = m4_full_tab(tab, beta2);
+            else F = gt_chord<float>(P, beta2, -ch * ih, ch * ih);
+        } else {
+            float u1 = (fmaxf(0.f, tc - ch) - tc) * ih;
+            float u2 = (fminf(L, tc + ch) - tc) * ih;
+            if (KERNEL == URCHIN_KERNEL_M4) F = m4_part_f(beta2, u1, u2);
+            else F = gt_chord<float>(P, beta2, u1, u2);
+        }
+        Kahan::add(k.sum, k.comp, __ldg(P.w32 + j) * F);
+        if (MODE == MODE_FILL) {
+            if (k.pos < k.end) {
+                P.seg_col[k.pos] = j;
+                static_cast<float*>(P.seg_val)[k.pos] = __ldg(P.A32 + j) * F;
+                ++k.pos;
+            } else {
+                err |= kStSegment;
+            }
+        }
+    }
+}
+
+template <typename Real, int KERNEL, int MODE>
 __device__ __forceinline__ void leaf_hits(const TraceParams& P, int ref, int cnt, Real sx, Real sy, Real sz,
-                                          Real dx, Real dy, Real dz, Real L, Real& sum, Real& comp,
-                                          unsigned& nhit)
+                                          Real dx, Real dy, Real dz, Real L, Sink<Real>& k, unsigned& err)
 {
     using O = RealOps<Real>;
     if (ref < 0 || cnt > kLeafMax || ref + cnt > P.n) return;   // never true for a well-formed tree
+    k.ntest += (unsigned)cnt;
     for (int j = ref; j < ref + cnt; ++j) {
         float4 q = __ldg(P.xyzh + j);
         Real ex = Real(q.x) - sx, ey = Real(q.y) - sy, ez = Real(q.z) - sz;
@@ -187,6 +335,8 @@ __device__ __forceinline__ void leaf_hits(const TraceParams& P, int ref, int cnt
         if (b2 >= h2) continue;
         Real ch = O::sqrt_(h2 - b2);
         if (tc + ch <= Real(0) || tc - ch >= L) continue;
+        ++k.nhit;
+        if (MODE == MODE_COUNT) continue;
         Real ih = Real(1) / h;
         Real beta2 = b2 * ih * ih;
         Real F;
@@ -200,19 +350,27 @@ __device__ __forceinline__ void leaf_hits(const TraceParams& P, int ref, int cnt
             if (KERNEL == URCHIN_KERNEL_M4) F = m4_part(beta2, u1, u2);
             else F = gt_chord(P, beta2, u1, u2);
         }
-        Kahan::add(sum, comp, O::weight(P, j) * F);
-        ++nhit;
+        Kahan::add(k.sum, k.comp, O::weight(P, j) * F);
+        if (MODE == MODE_FILL) {
+            if (k.pos < k.end) {
+                P.seg_col[k.pos] = j;
+                const Real A = sizeof(Real) == 4 ? Real(__ldg(P.A32 + j)) : Real(__ldg(P.A64 + j));
+                static_cast<Real*>(P.seg_val)[k.pos] = A * F;
+                ++k.pos;
+            } else {
+                err |= kStSegment;
+            }
+        }
     }
 }
 
-template <typename Real, int KERNEL>
-__device__ Real ray_column(const TraceParams& P, float4 o, Real dx, Real dy, Real dz, unsigned& err,
-                           unsigned& nhit)
+template <typename Real, int KERNEL, int MODE>
+__device__ void ray_column(const TraceParams& P, const float2* tab, float4 o, Real dx, Real dy, Real dz,
+                           Sink<Real>& sk, unsigned& err, unsigned& nvisit)
 {
     const Real L = Real(P.l_ray);
     const float Lf = (float)P.l_ray * 1.000001f + 1e-30f;
     const float ix = safe_inv((double)dx), iy = safe_inv((double)dy), iz = safe_inv((double)dz);
-    Real sum = Real(0), comp = Real(0);
     const int nimg = P.periodic ? P.nimg : 0;
     const float4 rlo = make_float4(P.root_lo[0], P.root_lo[1], P.root_lo[2], 0.f);
     const float4 rhi = make_float4(P.root_hi[0], P.root_hi[1], P.root_hi[2], 0.f);
@@ -241,6 +399,7 @@ __device__ Real ray_column(const TraceParams& P, float4 o, Real dx, Real dy, Rea
                 err |= kStVisit;
                 break;
             }
+            ++nvisit;
             const float4* nd = P.nodes + 4 * (int64_t)node;
             float4 a = __ldg(nd), b = __ldg(nd + 1), c = __ldg(nd + 2), d = __ldg(nd + 3);
             int lref = __float_as_int(a.w), lcnt = __float_as_int(b.w);
@@ -248,11 +407,17 @@ __device__ Real ray_column(const TraceParams& P, float4 o, Real dx, Real dy, Rea
             bool hl = seg_box(fx, fy, fz, ix, iy, iz, Lf, a, b);
             bool hr = rcnt >= 0 && seg_box(fx, fy, fz, ix, iy, iz, Lf, c, d);
             if (hl && lcnt > 0) {
-                leaf_hits<Real, KERNEL>(P, lref, lcnt, sx, sy, sz, dx, dy, dz, L, sum, comp, nhit);
+                if constexpr (sizeof(Real) == 4)
+                    leaf_hits_f32<KERNEL, MODE>(P, tab, lref, lcnt, sx, sy, sz, dx, dy, dz, L, sk, err);
+                else
+                    leaf_hits<Real, KERNEL, MODE>(P, lref, lcnt, sx, sy, sz, dx, dy, dz, L, sk, err);
                 hl = false;
             }
             if (hr && rcnt > 0) {
-                leaf_hits<Real, KERNEL>(P, rref, rcnt, sx, sy, sz, dx, dy, dz, L, sum, comp, nhit);
+                if constexpr (sizeof(Real) == 4)
+                    leaf_hits_f32<KERNEL, MODE>(P, tab, rref, rcnt, sx, sy, sz, dx, dy, dz, L, sk, err);
+                else
+                    leaf_hits<Real, KERNEL, MODE>(P, rref, rcnt, sx, sy, sz, dx, dy, dz, L, sk, err);
                 hr = false;
             }
             if (hl && hr) {
@@ -269,19 +434,21 @@ __device__ Real ray_column(const TraceParams& P, float4 o, Real dx, Real dy, Rea
             }
         }
     }
-    return sum;
 }
 
-template <typename Real, int KERNEL>
+template <typename Real, int KERNEL, int MODE>
 __global__ void __launch_bounds__(256) k_trace(TraceParams P)
 {
     extern __shared__ double s_dirs[];
+    float2* s_tab = reinterpret_cast<float2*>(s_dirs + 3 * P.R);
     for (int t = threadIdx.x; t < 3 * P.R; t += blockDim.x) s_dirs[t] = P.dirs[t];
+    if (sizeof(Real) == 4 && KERNEL == URCHIN_KERNEL_M4)
+        for (int t = threadIdx.x; t <= kKTab; t += blockDim.x) s_tab[t] = P.ktab[t];
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const unsigned long long total = (unsigned long long)P.n_chunks * (unsigned long long)P.R;
     unsigned err = 0;
-    unsigned long long hits = 0;
+    unsigned long long hits = 0, tests = 0, visits = 0;
     for (;;) {
         unsigned task = 0;
         if (lane == 0) task = atomicAdd(P.counter, 1u);
@@ -294,42 +461,113 @@ __global__ void __launch_bounds__(256) k_trace(TraceParams P)
             int32_t org = P.items ? P.items[item] : (int32_t)item;
             float4 o = __ldg(P.xyzh + org);
             Real dx = Real(s_dirs[3 * k]), dy = Real(s_dirs[3 * k + 1]), dz = Real(s_dirs[3 * k + 2]);
-            unsigned nhit = 0;
-            Real tau = ray_column<Real, KERNEL>(P, o, dx, dy, dz, err, nhit);
-            hits += nhit;
-            int64_t row = P.out_row ? (int64_t)P.out_row[item] : item;
-            static_cast<Real*>(P.out)[row * P.row_stride + (int64_t)k * P.k_stride] = tau;
+            unsigned nvisit = 0;
+            Sink<Real> sk{Real(0), Real(0), 0u, 0u, 0, 0};
+            const int64_t ray = (int64_t)k * P.n_items + item;
+            if (MODE == MODE_FILL) {
+                sk.pos = (int64_t)P.row_ptr[ray];
+                sk.end = (int64_t)P.row_ptr[ray + 1];
+            }
+            ray_column<Real, KERNEL, MODE>(P, s_tab, o, dx, dy, dz, sk, err, nvisit);
+            hits += sk.nhit;
+            tests += sk.ntest;
+            visits += nvisit;
+            if (MODE == MODE_COUNT) {
+                P.counts[ray] = sk.nhit;
+            } else {
+                if (MODE == MODE_FILL && sk.pos != sk.end) err |= kStSegment;
+                int64_t row = P.out_row ? (int64_t)P.out_row[item] : item;
+                static_cast<Real*>(P.out)[row * P.row_stride + (int64_t)k * P.k_stride] = sk.sum;
+            }
         }
     }
     if (err && P.status) atomicOr(P.status, err);
     if (P.hits) {
-        for (int o = 16; o > 0; o >>= 1) hits += __shfl_xor_sync(0xffffffffu, hits, o);
-        if (lane == 0 && hits) atomicAdd(P.hits, hits);
+        for (int o = 16; o > 0; o >>= 1) {
+            hits += __shfl_xor_sync(0xffffffffu, hits, o);
+            tests += __shfl_xor_sync(0xffffffffu, tests, o);
+            visits += __shfl_xor_sync(0xffffffffu, visits, o);
+        }
+        if (lane == 0) {
+            atomicAdd(P.hits, hits);
+            atomicAdd(P.hits + 1, tests);
+            atomicAdd(P.hits + 2, visits);
+        }
     }
 }
 
-template <typename Real, int KERNEL>
+template <typename Real, int KERNEL, int MODE>
 int launch_one(const TraceParams& P, cudaStream_t s)
 {
-    const void* fn = (const void*)k_trace<Real, KERNEL>;
-    size_t smem = sizeof(double) * 3 * (size_t)P.R;
+    const void* fn = (const void*)k_trace<Real, KERNEL, MODE>;
+    size_t smem = sizeof(double) * 3 * (size_t)P.R +
+                  ((sizeof(Real) == 4 && KERNEL == URCHIN_KERNEL_M4) ? sizeof(float2) * (kKTab + 1) : 0);
     int grid = 0;
     URCHIN_TRY(grid_for(fn, 256, smem, &grid));
     int64_t tasks = P.n_chunks * P.R;
     int64_t need = (tasks + 7) / 8;       // 8 warps per block
     if (need < grid) grid = (int)std::max<int64_t>(need, 1);
-    k_trace<Real, KERNEL><<<grid, 256, smem, s>>>(P);
+    k_trace<Real, KERNEL, MODE><<<grid, 256, smem, s>>>(P);
     URCHIN_TRY(launched());
     return URCHIN_OK;
 }
 
+template <typename Real, int KERNEL>
+int dispatch_k(const TraceParams& P, int mode, cudaStream_t s)
+{
+    if (mode == MODE_COUNT) return launch_one<Real, KERNEL, MODE_COUNT>(P, s);
+    if (mode == MODE_FILL) return launch_one<Real, KERNEL, MODE_FILL>(P, s);
+    return launch_one<Real, KERNEL, MODE_TAU>(P, s);
+}
+
+int dispatch_mode(const TraceParams& P, int precision, int kernel, int mode, cudaStream_t s)
+{
+    if (precision == URCHIN_F64) {
+        if (kernel == URCHIN_KERNEL_GT) return dispatch_k<double, URCHIN_KERNEL_GT>(P, mode, s);
+        return dispatch_k<double, URCHIN_KERNEL_M4>(P, mode, s);
+    }
+    if (kernel == URCHIN_KERNEL_GT) return dispatch_k<float, URCHIN_KERNEL_GT>(P, mode, s);
+    return dispatch_k<float, URCHIN_KERNEL_M4>(P, mode, s);
+}
+
 }  // namespace
+
+// Full-chord M4 integral in double from the antiderivatives above:
+// K(t) = 2 H(c), H(c) = Fo(c) [+ Fi(s) - Fo(s) when t < 1/4].
+static double m4_full_host(double t)
+{
+    if (t >= 1.0) return 0.0;
+    const double c = std::sqrt(1.0 - t);
+    const double lb = t > 0.0 ? 0.5 * std::log(t) : 0.0;
+    const double Lc = t > 0.0 ? std::log(c + 1.0) - lb : 0.0;
+    double H = c * (0.5 + 3.25 * t) - (3.0 * t + 0.75 * t * t) * Lc;
+    if (t < 0.25) {
+        const double sv = std::sqrt(0.25 - t);
+        const double Ls = t > 0.0 ? std::log(sv + 0.5) - lb : 0.0;
+        H += -sv * (0.25 + 6.5 * t) + (3.0 * t + 3.0 * t * t) * Ls;
+    }
+    return 2.0 * H;
+}
+
+void m4_full_table(float2* out)
+{
+    const double h = 1e-5;
+    for (int i = 0; i <= kKTab; ++i) {
+        const double t = (double)i / kKTab;
+        double d;
+        if (t < 2 * h) d = (-3.0 * m4_full_host(t) + 4.0 * m4_full_host(t + h) - m4_full_host(t + 2 * h)) / (2 * h);
+        else if (t > 1.0 - 2 * h) d = (3.0 * m4_full_host(t) - 4.0 * m4_full_host(t - h) + m4_full_host(t - 2 * h)) / (2 * h);
+        else d = (m4_full_host(t + h) - m4_full_host(t - h)) / (2 * h);
+        out[i] = make_float2((float)m4_full_host(t), (float)(d / kKTab));
+    }
+}
 
 int launch_trace(const TraceJob& job, cudaStream_t s)
 {
     if (job.n_items <= 0) return URCHIN_OK;
     const urchin_bvh* b = job.bvh;
     TraceParams P;
+    P.ktab = b->ktab;
     P.nodes = b->nodes;
     P.n_nodes = b->n_nodes;
     P.n = (int)b->n;
@@ -364,12 +602,13 @@ int launch_trace(const TraceJob& job, cudaStream_t s)
     if ((unsigned long long)P.n_chunks * (unsigned long long)job.R >= 0xffffffffull)
         return set_error(URCHIN_ERR_ARG, "trace: too many rays for one launch");
     URCHIN_TRY_CUDA(cudaMemsetAsync(job.counter, 0, sizeof(unsigned), s));
-    if (job.precision == URCHIN_F64) {
-        if (job.kernel == URCHIN_KERNEL_GT) return launch_one<double, URCHIN_KERNEL_GT>(P, s);
-        return launch_one<double, URCHIN_KERNEL_M4>(P, s);
-    }
-    if (job.kernel == URCHIN_KERNEL_GT) return launch_one<float, URCHIN_KERNEL_GT>(P, s);
-    return launch_one<float, URCHIN_KERNEL_M4>(P, s);
+    P.counts = job.counts;
+    P.row_ptr = job.row_ptr;
+    P.seg_col = job.seg_col;
+    P.seg_val = job.seg_val;
+    P.A32 = b->A32;
+    P.A64 = b->A64;
+    return dispatch_mode(P, job.precision, job.kernel, job.mode, s);
 }
 
 // w[s] = A[s] x[perm[s]]
@@ -427,9 +666,9 @@ extern "C" int urchin_trace_columns(const urchin_bvh* bvh, const double* x, cons
     if (precision != URCHIN_F32 && precision != URCHIN_F64)
         return set_error(URCHIN_ERR_ARG, "urchin_trace_columns: unknown precision %d", precision);
     if (n_orig < 0) return set_error(URCHIN_ERR_ARG, "urchin_trace_columns: n_orig < 0");
+    if (n_orig == 0) return URCHIN_OK;
     if (!origins && n_orig != bvh->n)
         return set_error(URCHIN_ERR_ARG, "urchin_trace_columns: origins NULL requires n_orig == n");
-    if (n_orig == 0) return URCHIN_OK;
     if (!tau_out) return set_error(URCHIN_ERR_ARG, "urchin_trace_columns: tau_out is NULL");
     for (int i = 0; i < 3 * R; ++i)
         if (!std::isfinite(dirs[i])) return set_error(URCHIN_ERR_ARG, "urchin_trace_columns: non-finite direction");

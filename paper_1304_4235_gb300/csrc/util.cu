@@ -90,12 +90,13 @@ constexpr int kScanThreads = 512;
 constexpr int kScanItems = 4;
 constexpr int kScanTile = kScanThreads * kScanItems;
 
-__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v)
+template <typename T>
+__device__ __forceinline__ T warp_incl_scan(T v)
 {
     const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
+        T t = __shfl_up_sync(0xffffffffu, v, o);
         if (lane >= o) v += t;
     }
     return v;
@@ -103,38 +104,39 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v)
 
 // Block-wide exclusive scan of one value per thread; returns the prefix and
 // writes the block total to *total.
-__device__ uint32_t block_excl_scan(uint32_t v, uint32_t* total)
+template <typename T>
+__device__ T block_excl_scan(T v, T* total)
 {
-    __shared__ uint32_t warp_sums[kScanThreads / 32];
+    __shared__ T warp_sums[kScanThreads / 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    uint32_t incl = warp_incl_scan(v);
+    T incl = warp_incl_scan(v);
     if (lane == 31) warp_sums[wid] = incl;
     __syncthreads();
     if (wid == 0) {
-        uint32_t ws = (lane < kScanThreads / 32) ? warp_sums[lane] : 0u;
-        uint32_t wi = warp_incl_scan(ws);
+        T ws = (lane < kScanThreads / 32) ? warp_sums[lane] : T(0);
+        T wi = warp_incl_scan(ws);
         if (lane < kScanThreads / 32) warp_sums[lane] = wi - ws;
         if (lane == kScanThreads / 32 - 1) *total = wi;
     }
     __syncthreads();
-    uint32_t r = incl - v + warp_sums[wid];
+    T r = incl - v + warp_sums[wid];
     __syncthreads();
     return r;
 }
 
-__global__ void k_scan_tiles(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tile_sums,
-                             uint32_t* total_dev)
+template <typename TIn, typename TOut>
+__global__ void k_scan_tiles(const TIn* in, TOut* out, int64_t n, TOut* tile_sums, TOut* total_dev)
 {
-    __shared__ uint32_t tot;
+    __shared__ TOut tot;
     int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
-    uint32_t v[kScanItems];
-    uint32_t sum = 0;
+    TOut v[kScanItems];
+    TOut sum = 0;
 #pragma unroll
     for (int i = 0; i < kScanItems; ++i) {
-        v[i] = (base + i < n) ? in[base + i] : 0u;
+        v[i] = (base + i < n) ? (TOut)in[base + i] : TOut(0);
         sum += v[i];
     }
-    uint32_t pre = block_excl_scan(sum, &tot);
+    TOut pre = block_excl_scan<TOut>(sum, &tot);
 #pragma unroll
     for (int i = 0; i < kScanItems; ++i) {
         if (base + i < n) out[base + i] = pre;
@@ -146,48 +148,65 @@ __global__ void k_scan_tiles(const uint32_t* in, uint32_t* out, int64_t n, uint3
     }
 }
 
-__global__ void k_scan_add(uint32_t* out, int64_t n, const uint32_t* tile_pre)
+template <typename T>
+__global__ void k_scan_add(T* out, int64_t n, const T* tile_pre)
 {
     int64_t base = (int64_t)blockIdx.x * kScanTile;
-    uint32_t add = tile_pre[blockIdx.x];
+    T add = tile_pre[blockIdx.x];
     for (int i = threadIdx.x; i < kScanTile; i += blockDim.x)
         if (base + i < n) out[base + i] += add;
 }
 
 static int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
-size_t scan_tmp_bytes(int64_t n)
+template <typename T>
+static size_t scan_tmp_bytes_t(int64_t n)
 {
     size_t bytes = 0;
     int64_t m = n;
     while (m > kScanTile) {
         m = ceil_div(m, kScanTile);
-        bytes += ((size_t)m * 4 + 255) & ~size_t(255);
+        bytes += ((size_t)m * sizeof(T) + 255) & ~size_t(255);
     }
     return bytes + 256;
+}
+
+size_t scan_tmp_bytes(int64_t n) { return scan_tmp_bytes_t<uint32_t>(n); }
+size_t scan64_tmp_bytes(int64_t n) { return scan_tmp_bytes_t<uint64_t>(n); }
+
+template <typename TIn, typename TOut>
+static int scan_t(const TIn* in, TOut* out, int64_t n, void* tmp, TOut* total_dev, cudaStream_t s)
+{
+    if (n <= 0) {
+        if (total_dev) URCHIN_TRY_CUDA(cudaMemsetAsync(total_dev, 0, sizeof(TOut), s));
+        return URCHIN_OK;
+    }
+    int64_t tiles = ceil_div(n, kScanTile);
+    if (tiles == 1) {
+        k_scan_tiles<TIn, TOut><<<1, kScanThreads, 0, s>>>(in, out, n, nullptr, total_dev);
+        URCHIN_TRY(launched());
+        return URCHIN_OK;
+    }
+    TOut* sums = static_cast<TOut*>(tmp);
+    void* rest = static_cast<char*>(tmp) + (((size_t)tiles * sizeof(TOut) + 255) & ~size_t(255));
+    k_scan_tiles<TIn, TOut><<<(unsigned)tiles, kScanThreads, 0, s>>>(in, out, n, sums, nullptr);
+    URCHIN_TRY(launched());
+    URCHIN_TRY((scan_t<TOut, TOut>(sums, sums, tiles, rest, total_dev, s)));
+    k_scan_add<TOut><<<(unsigned)tiles, kScanThreads, 0, s>>>(out, n, sums);
+    URCHIN_TRY(launched());
+    return URCHIN_OK;
 }
 
 int scan_exclusive_u32(const uint32_t* in, uint32_t* out, int64_t n, void* tmp, uint32_t* total_dev,
                        cudaStream_t s)
 {
-    if (n <= 0) {
-        if (total_dev) URCHIN_TRY_CUDA(cudaMemsetAsync(total_dev, 0, 4, s));
-        return URCHIN_OK;
-    }
-    int64_t tiles = ceil_div(n, kScanTile);
-    if (tiles == 1) {
-        k_scan_tiles<<<1, kScanThreads, 0, s>>>(in, out, n, nullptr, total_dev);
-        URCHIN_TRY(launched());
-        return URCHIN_OK;
-    }
-    uint32_t* sums = static_cast<uint32_t*>(tmp);
-    void* rest = static_cast<char*>(tmp) + (((size_t)tiles * 4 + 255) & ~size_t(255));
-    k_scan_tiles<<<(unsigned)tiles, kScanThreads, 0, s>>>(in, out, n, sums, nullptr);
-    URCHIN_TRY(launched());
-    URCHIN_TRY(scan_exclusive_u32(sums, sums, tiles, rest, total_dev, s));
-    k_scan_add<<<(unsigned)tiles, kScanThreads, 0, s>>>(out, n, sums);
-    URCHIN_TRY(launched());
-    return URCHIN_OK;
+    return scan_t<uint32_t, uint32_t>(in, out, n, tmp, total_dev, s);
+}
+
+int scan_counts_u64(const uint32_t* in, uint64_t* out, int64_t n, void* tmp, uint64_t* total_dev,
+                    cudaStream_t s)
+{
+    return scan_t<uint32_t, uint64_t>(in, out, n, tmp, total_dev, s);
 }
 
 // ---------------------------------------------------------------------------

@@ -296,3 +296,57 @@ def test_solve_full_size_halo_one_sweep_sampled():
     expect = np.where(te0 < 1e-4, x1[org], expect)
     err = rel_err(x2[org], expect)
     assert np.quantile(err, 0.99) < 1e-4
+
+
+# --------------------------------------------------------------------------
+# stored segments and Newton-Krylov (same fixed point, same sweep semantics)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("sweeps", [1, 3])
+def test_stored_segments_match_recompute_fp64(lattice, sweeps):
+    w, bvh, d = lattice
+    sg, so = spectra(w, torch)
+    xr, sr = _solve_gpu(w, bvh, d, sg, U.F64, tol=1e-300, max_iter=sweeps)
+    xs, ss = _solve_gpu(w, bvh, d, sg, U.F64, tol=1e-300, max_iter=sweeps, segments=U.SEG_STORE, profile=True)
+    assert ss["segments_stored"] == 1 and sr["segments_stored"] == 0
+    assert ss["nnz"] == ss["hits"] // 2          # the count and the fill pass each count every hit
+    assert ss["iterations"] == sr["iterations"] == sweeps
+    assert ss["rays"] == sr["rays"]
+    assert rel_err(xs, xr).max() < 1e-11
+    xo, fo, so_ = O.solve(w, so[0], so[1], O.healpix(1), sweeps=sweeps)
+    assert rel_err(xs, xo).max() < 1e-9
+
+
+def test_stored_segments_match_recompute_fp32(halo_small):
+    w, bvh, d = halo_small
+    sg, so = spectra(w, torch)
+    xr, sr = _solve_gpu(w, bvh, d, sg, U.F32, tol=1e-300, max_iter=4)
+    xs, ss = _solve_gpu(w, bvh, d, sg, U.F32, tol=1e-300, max_iter=4, segments=U.SEG_AUTO)
+    assert ss["segments_stored"] == 1
+    err = rel_err(xs, xr)
+    assert np.quantile(err, 0.999) < 1e-4
+
+
+def test_newton_reaches_plain_fixed_point_lattice(lattice):
+    w, bvh, d = lattice
+    sg, so = spectra(w, torch)
+    xp, sp = _solve_gpu(w, bvh, d, sg, U.F64, tol=1e-10, max_iter=300)
+    xn, sn = _solve_gpu(w, bvh, d, sg, U.F64, tol=1e-10, max_iter=60, method=U.METHOD_NEWTON, gmres_m=20)
+    assert sp["converged"] and sn["converged"]
+    assert rel_err(xn, xp).max() < 1e-8
+    xo, fo, st = O.solve(w, so[0], so[1], O.healpix(1), tol=1e-10, max_iter=300)
+    assert rel_err(xn, xo).max() < 1e-8
+
+
+@pytest.mark.parametrize("segments", [U.SEG_RECOMPUTE, U.SEG_STORE])
+def test_newton_halo_small_fp32(halo_small, segments):
+    """Newton-Krylov and plain Jacobi reach the same fixed point; Newton needs
+    far fewer evaluations of the column map."""
+    w, bvh, d = halo_small
+    sg, so = spectra(w, torch)
+    xp, sp = _solve_gpu(w, bvh, d, sg, U.F32, tol=1e-7, max_iter=2000, segments=U.SEG_STORE)
+    xn, sn = _solve_gpu(w, bvh, d, sg, U.F32, tol=1e-7, max_iter=100, method=U.METHOD_NEWTON, gmres_m=30,
+                        segments=segments)
+    assert sp["converged"] and sn["converged"], (sp, sn)
+    # both within ~tol / (1 - rho) of the fixed point; allow 1e-4
+    assert np.quantile(rel_err(xn, xp), 0.999) < 1e-4
+    assert sn["iterations"] < sp["iterations"]
