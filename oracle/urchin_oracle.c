@@ -402,7 +402,8 @@ double oracle_xeq(double Gamma, double nH, double T, double y, int caseB)
 }
 
 /* Case choice (Sec. 3.3.3 / Sec. 4): 0 = always A, 1 = always B,
- * 2 = B when tau_eff >= 1. */
+ * 2 = B when tau_eff >= 1.  In the iteration driver rule 2 is latched: a
+ * particle that has once had tau_eff >= 1 keeps case B (see oracle_solve). */
 static int use_caseB(int case_rule, double tau_eff)
 {
     if (case_rule == 0) return 0;
@@ -422,6 +423,12 @@ static int use_caseB(int case_rule, double tau_eff)
  *   from the previous sweep's x before any x changes;
  *   stop when max over non-frozen particles of |x_new - x| / x < tol, or
  *   after max_iter sweeps.
+ * The case rule "B when tau_eff >= 1" is applied as a latch: once a
+ * particle has reached tau_eff >= 1 in some sweep it keeps case B.  Read
+ * literally, the rule has no self-consistent state for particles whose
+ * case-A equilibrium is thick and case-B equilibrium thin, and the Jacobi
+ * iteration then alternates between the two forever; the latch settles
+ * them in case B.
  * If max_iter < 0 the run does exactly -max_iter sweeps (step-matched mode).
  * x_out[n] receives the final x, frozen_out[n] (optional) 1 for frozen
  * particles, stats[0] = sweeps done, stats[1] = last max |dx|/x,
@@ -440,6 +447,7 @@ int oracle_solve(int64_t n, const double* px, const double* py, const double* pz
     for (int j = 0; j < F; ++j) gthin += w[j];
     double* x = x_out;
     int* frozen = (int*)calloc((size_t)n, sizeof(int));
+    int* latchB = (int*)calloc((size_t)n, sizeof(int));
     double* tau = (double*)malloc(sizeof(double) * (size_t)n * R);
     double* G = (double*)malloc(sizeof(double) * (size_t)n);
     double* te = (double*)malloc(sizeof(double) * (size_t)n);
@@ -470,7 +478,9 @@ int oracle_solve(int64_t n, const double* px, const double* py, const double* pz
         maxrel = 0.0;
         for (int64_t o = 0; o < nact; ++o) {
             int64_t i = act[o];
-            xn[o] = oracle_xeq(G[o], nH[i], T[i], y, use_caseB(case_rule, te[o]));
+            int cb = use_caseB(case_rule, te[o]) || (case_rule == 2 && latchB[i]);
+            latchB[i] = cb;
+            xn[o] = oracle_xeq(G[o], nH[i], T[i], y, cb);
             double rel = fabs(xn[o] - x[i]) / x[i];
             if (rel > maxrel) maxrel = rel;
         }
@@ -480,7 +490,7 @@ int oracle_solve(int64_t n, const double* px, const double* py, const double* pz
     }
     if (frozen_out) for (int64_t i = 0; i < n; ++i) frozen_out[i] = frozen[i];
     if (stats) { stats[0] = sweeps; stats[1] = maxrel; stats[2] = rays; }
-    free(frozen); free(tau); free(G); free(te); free(xn); free(act);
+    free(frozen); free(latchB); free(tau); free(G); free(te); free(xn); free(act);
     return (fixed || converged) ? 0 : 1;
 }
 
