@@ -216,6 +216,10 @@ typedef struct {
     int             warm_start;   /* 0: start from x_thin; 1: from x_inout     */
     int             profile;      /* 1: time every traversal with CUDA events
                                      and count kernel-chord evaluations        */
+    double*         history_maxrel;      /* host [max_iter] or NULL: max |dx|/x
+                                            after each sweep / Newton step     */
+    int64_t*        history_unconverged; /* host [max_iter] or NULL: particles
+                                            with |dx|/x >= tol at that point   */
 } urchin_solve_params;
 
 typedef struct {

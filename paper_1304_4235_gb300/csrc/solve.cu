@@ -125,6 +125,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs A)
     const int k = threadIdx.x % A.R;
     const double gthin = sh[0], smin = sh[1];
     double my_max = 0.0;
+    unsigned long long my_above = 0;
     unsigned err = 0;
     for (int64_t row0 = (int64_t)blockIdx.x * rows_per_block; row0 < A.n_items;
          row0 += (int64_t)gridDim.x * rows_per_block) {
@@ -168,13 +169,17 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs A)
             if (A.gamma_out) A.gamma_out[row] = G;
             if (A.tau_eff_out) A.tau_eff_out[row] = (float)te;
             if (update) {
-                const bool caseB = A.case_rule == URCHIN_CASE_B || (A.case_rule == URCHIN_CASE_AUTO && te >= 1.0);
+                // case B iff tau_eff >= 1, latched once reached (see urchin_solve)
+                const bool caseB = A.case_rule == URCHIN_CASE_B ||
+                                   (A.case_rule == URCHIN_CASE_AUTO && (te >= 1.0 || A.latch[i]));
+                if (A.case_rule == URCHIN_CASE_AUTO) A.latch[i] = caseB ? 1 : 0;
                 const double alpha = caseB ? A.aB[i] : A.aA[i];
                 const double xo = A.x[i];
                 const double xn = x_equilibrium(G, A.nH[i], alpha, A.gc[i], A.y);
                 if (!isfinite(xn) || !(xn > 0.0)) err |= kStNonfinite;
                 const double rel = fabs(xn - xo) / xo;
                 my_max = fmax(my_max, rel);
+                if (rel >= A.tol) ++my_above;
                 if (A.want_tangent) {
                     // elasticity Gamma dE/dGamma / E and per-ray dGamma/dtau_k / Gamma
                     const double dEdG = dx_dgamma(xn, A.nH[i], alpha, A.gc[i], G, A.y);
@@ -198,10 +203,12 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs A)
     }
     for (int o = 16; o > 0; o >>= 1) {
         my_max = fmax(my_max, __shfl_xor_sync(0xffffffffu, my_max, o));
+        my_above += __shfl_xor_sync(0xffffffffu, my_above, o);
         err |= __shfl_xor_sync(0xffffffffu, err, o);
     }
     if ((threadIdx.x & 31) == 0) {
         if (my_max > 0.0) atomic_max_pos(A.maxrel, my_max);
+        if (my_above && A.n_above) atomicAdd(A.n_above, my_above);
         if (err) atomicOr(A.status, err);
     }
 }
@@ -234,6 +241,13 @@ __global__ void k_jv(const double* __restrict__ v, const double* __restrict__ ct
     }
 }
 
+__global__ void k_gather_x(const int32_t* __restrict__ items, int64_t n_act, const double* __restrict__ x,
+                           double* out)
+{
+    for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < n_act; a += (int64_t)gridDim.x * blockDim.x)
+        out[a] = x[items[a]];
+}
+
 // Newton residual -G_a = ln E_a - ln x_a
 __global__ void k_residual(const int32_t* __restrict__ items, int64_t n_act, const double* __restrict__ x,
                            const double* __restrict__ E, double* r)
@@ -245,8 +259,8 @@ __global__ void k_residual(const int32_t* __restrict__ items, int64_t n_act, con
 // x_a <- x_a exp(d_a) (step limited to a factor e^3, x <= 1), or x_a <- E_a
 // when E is given; refresh the tracer weights and the column-precision copy
 __global__ void k_set_x(const int32_t* __restrict__ items, int64_t n_act, const double* __restrict__ d,
-                        const double* __restrict__ E, double* x, const double* __restrict__ A64, float* w32,
-                        double* w64, float* xs32, double* xs64)
+                        double lam, const double* __restrict__ xbase, const double* __restrict__ E, double* x,
+                        const double* __restrict__ A64, float* w32, double* w64, float* xs32, double* xs64)
 {
     for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < n_act; a += (int64_t)gridDim.x * blockDim.x) {
         const int32_t i = items[a];
@@ -254,8 +268,8 @@ __global__ void k_set_x(const int32_t* __restrict__ items, int64_t n_act, const 
         if (E) {
             xn = E[a];
         } else {
-            const double step = fmin(fmax(d[a], -3.0), 3.0);
-            xn = fmin(1.0, x[i] * exp(step));
+            const double step = fmin(fmax(lam * d[a], -3.0), 3.0);
+            xn = fmin(1.0, xbase[a] * exp(step));
         }
         x[i] = xn;
         const double wv = A64[i] * xn;
@@ -308,6 +322,7 @@ int Solver::init(const urchin_bvh* bvh_, const urchin_solve_params* P_, double* 
     size_t o_w = lay.take(rsz * (size_t)n);
     size_t o_xs = lay.take(may_store ? rsz * (size_t)n : 0);
     size_t o_act = lay.take((size_t)n);
+    size_t o_latch = lay.take((size_t)n);
     size_t o_list = lay.take(sizeof(int32_t) * (size_t)n);
     size_t o_tau = lay.take(rsz * (size_t)rays);
     size_t o_comp = lay.take(compact_tmp_bytes(n));
@@ -332,6 +347,7 @@ int Solver::init(const urchin_bvh* bvh_, const urchin_solve_params* P_, double* 
         scan_tmp = scr.at<void>(o_st);
     }
     active = scr.at<uint8_t>(o_act);
+    latch = scr.at<uint8_t>(o_latch);
     list = scr.at<int32_t>(o_list);
     tau = scr.at<void>(o_tau);
     comp_tmp = scr.at<void>(o_comp);
@@ -339,6 +355,7 @@ int Solver::init(const urchin_bvh* bvh_, const urchin_solve_params* P_, double* 
     status = counter + 1;
     hits = P.profile ? misc + 3 : nullptr;
     URCHIN_TRY_CUDA(cudaMemsetAsync(misc, 0, 64, s));
+    URCHIN_TRY_CUDA(cudaMemsetAsync(latch, 0, (size_t)n, s));
     URCHIN_TRY_CUDA(cudaMemcpyAsync(dirs, P.dirs, sizeof(double) * 3 * (size_t)P.R, cudaMemcpyHostToDevice, s));
     std::vector<double> wh((size_t)P.spectrum.F);
     URCHIN_TRY_CUDA(cudaMemcpyAsync(wh.data(), P.spectrum.w, sizeof(double) * wh.size(), cudaMemcpyDeviceToHost, s));
@@ -550,30 +567,43 @@ SweepArgs Solver::sweep_args(const int32_t* items, int64_t n_items, int sweep0)
     A.tau_skip = P.tau_skip;
     A.sweep0 = sweep0;
     A.active = active;
+    A.latch = latch;
     A.maxrel = misc;
+    A.n_above = misc + 7;
+    A.tol = P.tol;
     A.status = status;
     return A;
 }
 
 int Solver::read_scalars(double* maxrel, unsigned* st)
 {
-    unsigned long long h[2];
+    unsigned long long h[8];
     URCHIN_TRY_CUDA(cudaMemcpyAsync(h, misc, sizeof(h), cudaMemcpyDeviceToHost, s));
     URCHIN_TRY_CUDA(cudaStreamSynchronize(s));
     double m;
     memcpy(&m, &h[0], sizeof(double));
     *maxrel = m;
     *st = (unsigned)(h[1] >> 32);
+    last_above = (int64_t)h[7];
     if (*st & kStNonfinite) return set_error(URCHIN_ERR_NONFINITE, "urchin_solve: non-finite neutral fraction");
     if (*st & (kStStack | kStVisit)) return set_error(URCHIN_ERR_CUDA, "urchin_solve: traversal stack/visit limit hit");
     if (*st & kStSegment) return set_error(URCHIN_ERR_CUDA, "urchin_solve: segment fill disagrees with its count");
     return URCHIN_OK;
 }
 
+void Solver::record(double maxrel)
+{
+    const int i = stats.iterations - 1;
+    if (i < 0 || i >= P.max_iter) return;
+    if (P.history_maxrel) P.history_maxrel[i] = maxrel;
+    if (P.history_unconverged) P.history_unconverged[i] = last_above;
+}
+
 int Solver::first_sweep()
 {
     // sweep 0: every particle traced; tau_eff < tau_skip freezes it
     URCHIN_TRY_CUDA(cudaMemsetAsync(misc, 0, sizeof(unsigned long long), s));
+        URCHIN_TRY_CUDA(cudaMemsetAsync(misc + 7, 0, sizeof(unsigned long long), s));
     URCHIN_TRY(columns(nullptr, n, 1));
     URCHIN_TRY(launch_sweep(sweep_args(nullptr, n, 1), s));
     uint32_t* cnt = reinterpret_cast<uint32_t*>(misc + 2);
@@ -588,6 +618,7 @@ int Solver::first_sweep()
     stats.particle_updates += n_act;
     stats.iterations = 1;
     stats.max_rel_dx = m;
+    record(m);
     return URCHIN_OK;
 }
 
@@ -600,6 +631,7 @@ int Solver::plain()
     }
     while (stats.iterations < P.max_iter) {
         URCHIN_TRY_CUDA(cudaMemsetAsync(misc, 0, sizeof(unsigned long long), s));
+        URCHIN_TRY_CUDA(cudaMemsetAsync(misc + 7, 0, sizeof(unsigned long long), s));
         URCHIN_TRY(columns(list, n_act, 0));
         URCHIN_TRY(launch_sweep(sweep_args(list, n_act, 0), s));
         double m;
@@ -608,6 +640,7 @@ int Solver::plain()
         stats.iterations += 1;
         stats.particle_updates += n_act;
         stats.max_rel_dx = m;
+        record(m);
         if (m < P.tol) {
             stats.converged = 1;
             break;
@@ -624,6 +657,46 @@ int Solver::plain()
 // Each step solves J d = -G by GMRES(m) to relative residual eta and sets
 // x <- x exp(d); it stops when max |E - x| / x < dx_tol and returns x <- E,
 // the same test and the same final update as the plain sweep.
+// One evaluation of the sweep map at the current x without updating it:
+// E = E(Gamma(x)), the tangent factors, max |E - x| / x, and the residual
+// r = ln E - ln x (into V0) with its 2-norm.
+int Solver::evaluate(double* V0, double* E, double* ctan, double* dtmp, double* hdev, double* maxrel, double* norm)
+{
+    const int64_t na = n_act;
+    const unsigned g1 = (unsigned)std::max<int64_t>(1, std::min<int64_t>((na + 255) / 256, 2048));
+    URCHIN_TRY_CUDA(cudaMemsetAsync(misc, 0, sizeof(unsigned long long), s));
+    URCHIN_TRY_CUDA(cudaMemsetAsync(misc + 7, 0, sizeof(unsigned long long), s));
+    URCHIN_TRY(columns(list, na, 0));
+    SweepArgs A = sweep_args(list, na, 0);
+    A.want_tangent = 1;
+    A.ctan = ctan;
+    A.xeq_out = E;
+    URCHIN_TRY(launch_sweep(A, s));
+    k_residual<<<g1, 256, 0, s>>>(list, na, x, E, V0);
+    URCHIN_TRY(launched());
+    URCHIN_TRY(launch_dots(V0, na, 1, V0, na, dtmp, hdev, s));
+    double r2 = 0.0;
+    URCHIN_TRY_CUDA(cudaMemcpyAsync(&r2, hdev, sizeof(double), cudaMemcpyDeviceToHost, s));
+    unsigned st;
+    URCHIN_TRY(read_scalars(maxrel, &st));
+    *norm = std::sqrt(std::max(r2, 0.0));
+    stats.iterations += 1;
+    stats.particle_updates += na;
+    stats.max_rel_dx = *maxrel;
+    record(*maxrel);
+    return URCHIN_OK;
+}
+
+// Newton-Krylov on the fixed point of the sweep map, in u = ln x over the
+// non-frozen particles: G(u) = u - ln E(Gamma(x)), with each particle's
+// recombination case held at its value in the evaluation.  J v = v - C dtau(x v)
+// where dtau is the column of the tangent vector (columns are linear in x)
+// and C holds c_ak = (1/E) dE/dGamma dGamma/dtau_k from the sweep kernel.
+// Each step solves J d = -G by GMRES(m) to relative residual eta
+// (Eisenstat-Walker), then backtracks x <- x exp(lam d), lam = 1, 1/2, ...,
+// until ||G||_2 decreases.  It stops when max |E - x| / x < dx_tol and returns
+// x <- E: the same test and the same final update as the plain sweep.  Every
+// evaluation of the sweep map counts as one iteration.
 int Solver::newton()
 {
     URCHIN_TRY(first_sweep());
@@ -639,6 +712,7 @@ int Solver::newton()
     size_t o_E = lay.take(sizeof(double) * (size_t)na);
     size_t o_c = lay.take(sizeof(double) * (size_t)na * P.R);
     size_t o_d = lay.take(sizeof(double) * (size_t)na);
+    size_t o_xb = lay.take(sizeof(double) * (size_t)na);
     size_t o_z = lay.take(rsz * (size_t)n);
     size_t o_wz = lay.take(stored ? 0 : rsz * (size_t)n);
     size_t o_dt = lay.take(dots_tmp_bytes(m + 1));
@@ -648,6 +722,7 @@ int Solver::newton()
     double* E = nk.at<double>(o_E);
     double* ctan = nk.at<double>(o_c);
     double* d = nk.at<double>(o_d);
+    double* xb = nk.at<double>(o_xb);
     float* z32 = f64 ? nullptr : nk.at<float>(o_z);
     double* z64 = f64 ? nk.at<double>(o_z) : nullptr;
     float* wz32 = (stored || f64) ? nullptr : nk.at<float>(o_wz);
@@ -657,42 +732,18 @@ int Solver::newton()
     const unsigned g1 = (unsigned)std::max<int64_t>(1, std::min<int64_t>((na + 255) / 256, 2048));
     std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1), hcol(m + 2), y(m);
     double eta = 0.1, prev_norm = -1.0;
-
-    while (stats.iterations < P.max_iter) {
-        // residual at the current x (no update), with the tangent factors
-        URCHIN_TRY_CUDA(cudaMemsetAsync(misc, 0, sizeof(unsigned long long), s));
-        URCHIN_TRY(columns(list, na, 0));
-        SweepArgs A = sweep_args(list, na, 0);
-        A.want_tangent = 1;
-        A.ctan = ctan;
-        A.xeq_out = E;
-        URCHIN_TRY(launch_sweep(A, s));
-        double mrel;
-        unsigned st;
-        URCHIN_TRY(read_scalars(&mrel, &st));
-        stats.iterations += 1;
-        stats.particle_updates += na;
-        stats.max_rel_dx = mrel;
-        if (mrel < P.tol) {
-            k_set_x<<<g1, 256, 0, s>>>(list, na, nullptr, E, x, bvh->A64, w32, w64, xs32, xs64);
+    double mrel = 0.0, norm = 0.0;
+    URCHIN_TRY(evaluate(V, E, ctan, dtmp, hdev, &mrel, &norm));
+    for (;;) {
+        if (mrel < P.tol || stats.iterations >= P.max_iter || norm == 0.0) {
+            // converged (or out of evaluations): finish with the plain update
+            k_set_x<<<g1, 256, 0, s>>>(list, na, nullptr, 0.0, nullptr, E, x, bvh->A64, w32, w64, xs32, xs64);
             URCHIN_TRY(launched());
-            stats.converged = 1;
+            if (mrel < P.tol) stats.converged = 1;
             break;
         }
-        if (stats.iterations >= P.max_iter) {
-            // out of steps: leave x at the last plain update, like the plain driver
-            k_set_x<<<g1, 256, 0, s>>>(list, na, nullptr, E, x, bvh->A64, w32, w64, xs32, xs64);
-            URCHIN_TRY(launched());
-            break;
-        }
-        // GMRES(m) for J d = -G, d0 = 0
-        k_residual<<<g1, 256, 0, s>>>(list, na, x, E, V);
-        URCHIN_TRY(launched());
-        URCHIN_TRY(launch_dots(V, na, 1, V, na, dtmp, hdev, s));
-        double beta2 = 0.0;
-        URCHIN_TRY_CUDA(cudaMemcpyAsync(&beta2, hdev, sizeof(double), cudaMemcpyDeviceToHost, s));
-        URCHIN_TRY_CUDA(cudaStreamSynchronize(s));
-        const double beta = std::sqrt(beta2);
+        // GMRES(m) for J d = r, r = -G already in V0, d0 = 0
+        const double beta = norm;
         if (prev_norm > 0.0) eta = std::min(0.1, std::max(1e-3, 0.9 * (beta / prev_norm) * (beta / prev_norm)));
         prev_norm = beta;
         URCHIN_TRY(launch_axpby(0.0, V, 1.0 / beta, V, na, s));
@@ -702,7 +753,6 @@ int Solver::newton()
         for (int j = 0; j < m; ++j) {
             double* vj = V + (size_t)j * na;
             double* w = V + (size_t)(j + 1) * na;
-            // w = J v_j
             if (z32) URCHIN_TRY_CUDA(cudaMemsetAsync(z32, 0, sizeof(float) * (size_t)n, s));
             if (z64) URCHIN_TRY_CUDA(cudaMemsetAsync(z64, 0, sizeof(double) * (size_t)n, s));
             if (wz32) URCHIN_TRY_CUDA(cudaMemsetAsync(wz32, 0, sizeof(float) * (size_t)n, s));
@@ -713,9 +763,8 @@ int Solver::newton()
             if (f64) k_jv<double><<<g1, 256, 0, s>>>(vj, ctan, static_cast<const double*>(tau), na, P.R, w);
             else k_jv<float><<<g1, 256, 0, s>>>(vj, ctan, static_cast<const float*>(tau), na, P.R, w);
             URCHIN_TRY(launched());
-            // classical Gram-Schmidt, twice
             std::fill(hcol.begin(), hcol.end(), 0.0);
-            for (int pass = 0; pass < 2; ++pass) {
+            for (int pass = 0; pass < 2; ++pass) {     // classical Gram-Schmidt, twice
                 URCHIN_TRY(launch_dots(V, na, j + 1, w, na, dtmp, hdev, s));
                 URCHIN_TRY(launch_subtract(w, V, na, j + 1, hdev, na, s));
                 std::vector<double> hh(j + 1);
@@ -730,8 +779,7 @@ int Solver::newton()
             const double hn = std::sqrt(std::max(hn2, 0.0));
             hcol[j + 1] = hn;
             if (hn > 0.0) URCHIN_TRY(launch_axpby(0.0, w, 1.0 / hn, w, na, s));
-            // Givens rotations on the new Hessenberg column
-            for (int i = 0; i < j; ++i) {
+            for (int i = 0; i < j; ++i) {              // earlier Givens rotations
                 const double a = cs[i] * hcol[i] + sn[i] * hcol[i + 1];
                 hcol[i + 1] = -sn[i] * hcol[i] + cs[i] * hcol[i + 1];
                 hcol[i] = a;
@@ -747,8 +795,7 @@ int Solver::newton()
             kdim = j + 1;
             if (std::fabs(gv[j + 1]) <= eta * beta || hn == 0.0) break;
         }
-        // y = H^-1 g (upper triangular), d = V y
-        for (int i = kdim - 1; i >= 0; --i) {
+        for (int i = kdim - 1; i >= 0; --i) {          // y = H^-1 g, d = V y
             double acc = gv[i];
             for (int k = i + 1; k < kdim; ++k) acc -= H[(size_t)i * m + k] * y[k];
             y[i] = H[(size_t)i * m + i] != 0.0 ? acc / H[(size_t)i * m + i] : 0.0;
@@ -757,8 +804,23 @@ int Solver::newton()
         URCHIN_TRY_CUDA(cudaMemcpyAsync(hdev, y.data(), sizeof(double) * kdim, cudaMemcpyHostToDevice, s));
         URCHIN_TRY_CUDA(cudaMemsetAsync(d, 0, sizeof(double) * (size_t)na, s));
         URCHIN_TRY(launch_subtract(d, V, na, kdim, hdev, na, s));
-        k_set_x<<<g1, 256, 0, s>>>(list, na, d, nullptr, x, bvh->A64, w32, w64, xs32, xs64);
+        // backtracking on ||G||_2
+        k_gather_x<<<g1, 256, 0, s>>>(list, na, x, xb);
         URCHIN_TRY(launched());
+        double lam = 1.0;
+        for (int ls = 0;; ++ls) {
+            k_set_x<<<g1, 256, 0, s>>>(list, na, d, lam, xb, nullptr, x, bvh->A64, w32, w64, xs32, xs64);
+            URCHIN_TRY(launched());
+            double mrel_t, norm_t;
+            URCHIN_TRY(evaluate(V, E, ctan, dtmp, hdev, &mrel_t, &norm_t));
+            const bool ok = norm_t <= (1.0 - 1e-4 * lam) * norm;
+            if (ok || ls >= 4 || stats.iterations >= P.max_iter || mrel_t < P.tol) {
+                mrel = mrel_t;
+                norm = norm_t;
+                break;
+            }
+            lam *= 0.5;
+        }
     }
     return URCHIN_OK;
 }

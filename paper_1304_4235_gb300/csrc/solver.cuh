@@ -33,7 +33,10 @@ struct SweepArgs {
     double tau_skip;
     int sweep0;
     uint8_t* active;           // written in sweep 0
+    uint8_t* latch;            // case B latched (CASE_AUTO), Morton order
     unsigned long long* maxrel;
+    unsigned long long* n_above;   // count of updated particles with |dx|/x >= tol
+    double tol;
     unsigned* status;
     double* gamma_out;         // [n_items] optional
     float* tau_eff_out;        // [n_items] optional
@@ -50,6 +53,7 @@ struct Solver {
     cudaStream_t s = nullptr;
     int64_t n = 0;
     int64_t n_act = 0;
+    int64_t last_above = 0;
     bool f64 = false;
     double gthin = 0.0;
     urchin_solve_stats stats{};
@@ -66,6 +70,7 @@ struct Solver {
     float* w32 = nullptr;
     double* w64 = nullptr;
     uint8_t* active = nullptr;
+    uint8_t* latch = nullptr;
     int32_t* list = nullptr;
     void* tau = nullptr;
     void* comp_tmp = nullptr;
@@ -89,11 +94,13 @@ struct Solver {
     int linear_columns(const int32_t* items, int64_t n_items, const float* z32, const double* z64,
                        float* wz32, double* wz64);
     int timed_trace(TraceJob& job);
+    int evaluate(double* V0, double* E, double* ctan, double* dtmp, double* hdev, double* maxrel, double* norm);
 
     int init(const urchin_bvh* bvh, const urchin_solve_params* P, double* x_inout, cudaStream_t s);
     int trace(const int32_t* items, int64_t n_items, const float* tw32, const double* tw64);
     SweepArgs sweep_args(const int32_t* items, int64_t n_items, int sweep0);
     int read_scalars(double* maxrel, unsigned* status);
+    void record(double maxrel);
     int first_sweep();
     int plain();
     int newton();

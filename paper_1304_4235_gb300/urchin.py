@@ -55,7 +55,8 @@ class urchin_solve_params(C.Structure):
                 ("tol", C.c_double), ("tau_skip", C.c_double), ("max_iter", C.c_int),
                 ("method", C.c_int), ("segments", C.c_int), ("gmres_m", C.c_int),
                 ("kernel", C.c_int), ("precision", C.c_int), ("case_rule", C.c_int),
-                ("warm_start", C.c_int), ("profile", C.c_int)]
+                ("warm_start", C.c_int), ("profile", C.c_int), ("history_maxrel", _vp),
+                ("history_unconverged", _vp)]
 
 
 class urchin_solve_stats(C.Structure):
@@ -265,7 +266,7 @@ def urchin_solve(bvh: Bvh, dirs, l_ray: float, s, w, nH, T, x=None, *, y: float 
                  method: int = METHOD_PLAIN, segments: int = SEG_RECOMPUTE, gmres_m: int = 10,
                  kernel: int = KERNEL_M4, precision: int = F32, case_rule: int = CASE_AUTO,
                  warm_start: bool = False, profile: bool = False, raise_not_converged: bool = True,
-                 stream=None):
+                 history: bool = False, stream=None):
     """Returns (x, stats dict).  x (float64 CUDA tensor, original order) is
     updated in place when given."""
     import torch
@@ -291,9 +292,20 @@ def urchin_solve(bvh: Bvh, dirs, l_ray: float, s, w, nH, T, x=None, *, y: float 
     P.case_rule = int(case_rule)
     P.warm_start = int(bool(warm_start))
     P.profile = int(bool(profile))
+    hist_max = hist_unc = None
+    if history:
+        hist_max = np.zeros(int(max_iter))
+        hist_unc = np.zeros(int(max_iter), dtype=np.int64)
+        P.history_maxrel = hist_max.ctypes.data_as(_vp)
+        P.history_unconverged = hist_unc.ctypes.data_as(_vp)
     st = urchin_solve_stats()
     rc = load().urchin_solve(bvh.handle, C.byref(P), _dev(x, torch.float64), C.byref(st), _stream(stream))
+    out = st.as_dict()
+    if history:
+        k = out["iterations"]
+        out["history_maxrel"] = hist_max[:k].tolist()
+        out["history_unconverged"] = hist_unc[:k].tolist()
     if rc == URCHIN_ERR_NOT_CONVERGED and not raise_not_converged:
-        return x, st.as_dict()
+        return x, out
     _check(rc)
-    return x, st.as_dict()
+    return x, out
