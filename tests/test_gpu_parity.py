@@ -359,6 +359,6 @@ def test_plain_solve_latched_case_matches_oracle(halo_small):
     where the unlatched rule would cycle."""
     w, bvh, d = halo_small
     sg, so = spectra(w, torch)
-    x, st = _solve_gpu(w, bvh, d, sg, U.F64, tol=1e-300, max_iter=40, segments=U.SEG_STORE)
-    xo, fo, so_ = O.solve(w, so[0], so[1], O.healpix(1), sweeps=40)
+    x, st = _solve_gpu(w, bvh, d, sg, U.F64, tol=1e-300, max_iter=15, segments=U.SEG_STORE)
+    xo, fo, so_ = O.solve(w, so[0], so[1], O.healpix(1), sweeps=15)
     assert rel_err(x, xo).max() < 1e-8
