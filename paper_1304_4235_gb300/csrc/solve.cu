@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs A)
     const int k = threadIdx.x % A.R;
     const double gthin = sh[0], smin = sh[1];
     double my_max = 0.0;
-    unsigned long long my_above = 0;
+    unsigned long long my_above = 0, my_switch = 0;
     unsigned err = 0;
     for (int64_t row0 = (int64_t)blockIdx.x * rows_per_block; row0 < A.n_items;
          row0 += (int64_t)gridDim.x * rows_per_block) {
@@ -170,9 +170,17 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs A)
             if (A.tau_eff_out) A.tau_eff_out[row] = (float)te;
             if (update) {
                 // case B iff tau_eff >= 1, latched once reached (see urchin_solve)
-                const bool caseB = A.case_rule == URCHIN_CASE_B ||
-                                   (A.case_rule == URCHIN_CASE_AUTO && (te >= 1.0 || A.latch[i]));
-                if (A.case_rule == URCHIN_CASE_AUTO) A.latch[i] = caseB ? 1 : 0;
+                bool caseB = A.case_rule == URCHIN_CASE_B;
+                if (A.case_rule == URCHIN_CASE_AUTO) {
+                    const bool latched = A.latch[i] != 0;
+                    if (A.latch_frozen) {
+                        caseB = latched;
+                        if (te >= 1.0 && !latched) ++my_switch;
+                    } else {
+                        caseB = latched || te >= 1.0;
+                        A.latch[i] = caseB ? 1 : 0;
+                    }
+                }
                 const double alpha = caseB ? A.aB[i] : A.aA[i];
                 const double xo = A.x[i];
                 const double xn = x_equilibrium(G, A.nH[i], alpha, A.gc[i], A.y);
@@ -204,11 +212,13 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs A)
     for (int o = 16; o > 0; o >>= 1) {
         my_max = fmax(my_max, __shfl_xor_sync(0xffffffffu, my_max, o));
         my_above += __shfl_xor_sync(0xffffffffu, my_above, o);
+        my_switch += __shfl_xor_sync(0xffffffffu, my_switch, o);
         err |= __shfl_xor_sync(0xffffffffu, err, o);
     }
     if ((threadIdx.x & 31) == 0) {
         if (my_max > 0.0) atomic_max_pos(A.maxrel, my_max);
         if (my_above && A.n_above) atomicAdd(A.n_above, my_above);
+        if (my_switch && A.n_switch) atomicAdd(A.n_switch, my_switch);
         if (err) atomicOr(A.status, err);
     }
 }
@@ -312,7 +322,7 @@ int Solver::init(const urchin_bvh* bvh_, const urchin_solve_params* P_, double* 
     const bool may_store = P.segments != URCHIN_SEG_RECOMPUTE;
     const int64_t rays = (int64_t)P.R * n;
     Layout lay;
-    size_t o_misc = lay.take(64);
+    size_t o_misc = lay.take(128);
     size_t o_dirs = lay.take(sizeof(double) * 3 * (size_t)P.R);
     size_t o_x = lay.take(sizeof(double) * (size_t)n);
     size_t o_nH = lay.take(sizeof(double) * (size_t)n);
@@ -354,7 +364,7 @@ int Solver::init(const urchin_bvh* bvh_, const urchin_solve_params* P_, double* 
     counter = reinterpret_cast<unsigned*>(misc + 1);
     status = counter + 1;
     hits = P.profile ? misc + 3 : nullptr;
-    URCHIN_TRY_CUDA(cudaMemsetAsync(misc, 0, 64, s));
+    URCHIN_TRY_CUDA(cudaMemsetAsync(misc, 0, 128, s));
     URCHIN_TRY_CUDA(cudaMemsetAsync(latch, 0, (size_t)n, s));
     URCHIN_TRY_CUDA(cudaMemcpyAsync(dirs, P.dirs, sizeof(double) * 3 * (size_t)P.R, cudaMemcpyHostToDevice, s));
     std::vector<double> wh((size_t)P.spectrum.F);
@@ -570,6 +580,7 @@ SweepArgs Solver::sweep_args(const int32_t* items, int64_t n_items, int sweep0)
     A.latch = latch;
     A.maxrel = misc;
     A.n_above = misc + 7;
+    A.n_switch = misc + 8;
     A.tol = P.tol;
     A.status = status;
     return A;
@@ -649,37 +660,34 @@ int Solver::plain()
     return URCHIN_OK;
 }
 
-// Newton-Krylov on the fixed point of the sweep map, in u = ln x over the
-// non-frozen particles: G(u) = u - ln E(Gamma(x)), with the recombination
-// case of each particle held at its current value.  J v = v - C dtau(x v)
-// where dtau is the column of the tangent vector (columns are linear in x)
-// and C holds c_ak = (1/E) dE/dGamma dGamma/dtau_k from the sweep kernel.
-// Each step solves J d = -G by GMRES(m) to relative residual eta and sets
-// x <- x exp(d); it stops when max |E - x| / x < dx_tol and returns x <- E,
-// the same test and the same final update as the plain sweep.
 // One evaluation of the sweep map at the current x without updating it:
 // E = E(Gamma(x)), the tangent factors, max |E - x| / x, and the residual
 // r = ln E - ln x (into V0) with its 2-norm.
-int Solver::evaluate(double* V0, double* E, double* ctan, double* dtmp, double* hdev, double* maxrel, double* norm)
+int Solver::evaluate(int frozen, double* V0, double* E, double* ctan, double* dtmp, double* hdev, double* maxrel,
+                     double* norm, int64_t* switches)
 {
     const int64_t na = n_act;
     const unsigned g1 = (unsigned)std::max<int64_t>(1, std::min<int64_t>((na + 255) / 256, 2048));
     URCHIN_TRY_CUDA(cudaMemsetAsync(misc, 0, sizeof(unsigned long long), s));
-    URCHIN_TRY_CUDA(cudaMemsetAsync(misc + 7, 0, sizeof(unsigned long long), s));
+    URCHIN_TRY_CUDA(cudaMemsetAsync(misc + 7, 0, 2 * sizeof(unsigned long long), s));
     URCHIN_TRY(columns(list, na, 0));
     SweepArgs A = sweep_args(list, na, 0);
     A.want_tangent = 1;
     A.ctan = ctan;
     A.xeq_out = E;
+    A.latch_frozen = frozen;
     URCHIN_TRY(launch_sweep(A, s));
     k_residual<<<g1, 256, 0, s>>>(list, na, x, E, V0);
     URCHIN_TRY(launched());
     URCHIN_TRY(launch_dots(V0, na, 1, V0, na, dtmp, hdev, s));
     double r2 = 0.0;
+    unsigned long long sw = 0;
     URCHIN_TRY_CUDA(cudaMemcpyAsync(&r2, hdev, sizeof(double), cudaMemcpyDeviceToHost, s));
+    URCHIN_TRY_CUDA(cudaMemcpyAsync(&sw, misc + 8, sizeof(sw), cudaMemcpyDeviceToHost, s));
     unsigned st;
     URCHIN_TRY(read_scalars(maxrel, &st));
     *norm = std::sqrt(std::max(r2, 0.0));
+    *switches = (int64_t)sw;
     stats.iterations += 1;
     stats.particle_updates += na;
     stats.max_rel_dx = *maxrel;
@@ -694,9 +702,13 @@ int Solver::evaluate(double* V0, double* E, double* ctan, double* dtmp, double* 
 // and C holds c_ak = (1/E) dE/dGamma dGamma/dtau_k from the sweep kernel.
 // Each step solves J d = -G by GMRES(m) to relative residual eta
 // (Eisenstat-Walker), then backtracks x <- x exp(lam d), lam = 1, 1/2, ...,
-// until ||G||_2 decreases.  It stops when max |E - x| / x < dx_tol and returns
-// x <- E: the same test and the same final update as the plain sweep.  Every
-// evaluation of the sweep map counts as one iteration.
+// until ||G||_2 decreases.  Within a step the recombination cases are held
+// at the latch of the step's base point, so G is smooth along the search;
+// when an accepted point has particles newly past tau_eff = 1 the latch is
+// updated there by a plain evaluation.  It stops when max |E - x| / x <
+// dx_tol with no case left to switch and returns x <- E: the same test and
+// the same final update as the plain sweep.  Every evaluation of the sweep
+// map counts as one iteration.
 int Solver::newton()
 {
     URCHIN_TRY(first_sweep());
@@ -733,7 +745,8 @@ int Solver::newton()
     std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1), hcol(m + 2), y(m);
     double eta = 0.1, prev_norm = -1.0;
     double mrel = 0.0, norm = 0.0;
-    URCHIN_TRY(evaluate(V, E, ctan, dtmp, hdev, &mrel, &norm));
+    int64_t sw = 0;
+    URCHIN_TRY(evaluate(0, V, E, ctan, dtmp, hdev, &mrel, &norm, &sw));
     for (;;) {
         if (mrel < P.tol || stats.iterations >= P.max_iter || norm == 0.0) {
             // converged (or out of evaluations): finish with the plain update
@@ -812,14 +825,20 @@ int Solver::newton()
             k_set_x<<<g1, 256, 0, s>>>(list, na, d, lam, xb, nullptr, x, bvh->A64, w32, w64, xs32, xs64);
             URCHIN_TRY(launched());
             double mrel_t, norm_t;
-            URCHIN_TRY(evaluate(V, E, ctan, dtmp, hdev, &mrel_t, &norm_t));
+            int64_t sw_t = 0;
+            URCHIN_TRY(evaluate(1, V, E, ctan, dtmp, hdev, &mrel_t, &norm_t, &sw_t));
             const bool ok = norm_t <= (1.0 - 1e-4 * lam) * norm;
-            if (ok || ls >= 4 || stats.iterations >= P.max_iter || mrel_t < P.tol) {
+            if (ok || ls >= 4 || stats.iterations >= P.max_iter) {
                 mrel = mrel_t;
                 norm = norm_t;
+                sw = sw_t;
                 break;
             }
             lam *= 0.5;
+        }
+        if (sw > 0 && stats.iterations < P.max_iter) {
+            // cases newly past tau_eff = 1: latch them and re-evaluate here
+            URCHIN_TRY(evaluate(0, V, E, ctan, dtmp, hdev, &mrel, &norm, &sw));
         }
     }
     return URCHIN_OK;

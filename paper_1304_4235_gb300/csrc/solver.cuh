@@ -34,6 +34,9 @@ struct SweepArgs {
     int sweep0;
     uint8_t* active;           // written in sweep 0
     uint8_t* latch;            // case B latched (CASE_AUTO), Morton order
+    int latch_frozen;          // 1: cases from the latch only, latch not written;
+                               //    count particles that would switch (n_switch)
+    unsigned long long* n_switch;
     unsigned long long* maxrel;
     unsigned long long* n_above;   // count of updated particles with |dx|/x >= tol
     double tol;
@@ -94,7 +97,8 @@ struct Solver {
     int linear_columns(const int32_t* items, int64_t n_items, const float* z32, const double* z64,
                        float* wz32, double* wz64);
     int timed_trace(TraceJob& job);
-    int evaluate(double* V0, double* E, double* ctan, double* dtmp, double* hdev, double* maxrel, double* norm);
+    int evaluate(int frozen, double* V0, double* E, double* ctan, double* dtmp, double* hdev, double* maxrel,
+                 double* norm, int64_t* switches);
 
     int init(const urchin_bvh* bvh, const urchin_solve_params* P, double* x_inout, cudaStream_t s);
     int trace(const int32_t* items, int64_t n_items, const float* tw32, const double* tw64);
