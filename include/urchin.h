@@ -238,6 +238,7 @@ typedef struct {
     int     trace_launches;       /* traversal kernel launches                 */
     int64_t sphere_tests;         /* ray-sphere tests at leaves (profile=1)    */
     int64_t node_visits;          /* internal nodes visited (profile=1)        */
+    int     newton_fallbacks;     /* Newton steps replaced by a plain sweep    */
 } urchin_solve_stats;
 
 /* Iterate to the equilibrium neutral fraction (Sec. 4): x starts at x_thin

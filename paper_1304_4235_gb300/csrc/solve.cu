@@ -266,7 +266,7 @@ __global__ void k_residual(const int32_t* __restrict__ items, int64_t n_act, con
         r[a] = log(E[a]) - log(x[items[a]]);
 }
 
-// x_a <- x_a exp(d_a) (step limited to a factor e^3, x <= 1), or x_a <- E_a
+// x_a <- x_a exp(lam d_a) (step limited to a factor e, x <= 1), or x_a <- E_a
 // when E is given; refresh the tracer weights and the column-precision copy
 __global__ void k_set_x(const int32_t* __restrict__ items, int64_t n_act, const double* __restrict__ d,
                         double lam, const double* __restrict__ xbase, const double* __restrict__ E, double* x,
@@ -278,7 +278,7 @@ __global__ void k_set_x(const int32_t* __restrict__ items, int64_t n_act, const 
         if (E) {
             xn = E[a];
         } else {
-            const double step = fmin(fmax(lam * d[a], -3.0), 3.0);
+            const double step = fmin(fmax(lam * d[a], -1.0), 1.0);
             xn = fmin(1.0, xbase[a] * exp(step));
         }
         x[i] = xn;
@@ -725,6 +725,7 @@ int Solver::newton()
     size_t o_c = lay.take(sizeof(double) * (size_t)na * P.R);
     size_t o_d = lay.take(sizeof(double) * (size_t)na);
     size_t o_xb = lay.take(sizeof(double) * (size_t)na);
+    size_t o_Eb = lay.take(sizeof(double) * (size_t)na);
     size_t o_z = lay.take(rsz * (size_t)n);
     size_t o_wz = lay.take(stored ? 0 : rsz * (size_t)n);
     size_t o_dt = lay.take(dots_tmp_bytes(m + 1));
@@ -735,6 +736,7 @@ int Solver::newton()
     double* ctan = nk.at<double>(o_c);
     double* d = nk.at<double>(o_d);
     double* xb = nk.at<double>(o_xb);
+    double* Eb = nk.at<double>(o_Eb);
     float* z32 = f64 ? nullptr : nk.at<float>(o_z);
     double* z64 = f64 ? nk.at<double>(o_z) : nullptr;
     float* wz32 = (stored || f64) ? nullptr : nk.at<float>(o_wz);
@@ -817,24 +819,35 @@ int Solver::newton()
         URCHIN_TRY_CUDA(cudaMemcpyAsync(hdev, y.data(), sizeof(double) * kdim, cudaMemcpyHostToDevice, s));
         URCHIN_TRY_CUDA(cudaMemsetAsync(d, 0, sizeof(double) * (size_t)na, s));
         URCHIN_TRY(launch_subtract(d, V, na, kdim, hdev, na, s));
-        // backtracking on ||G||_2
+        // backtracking on ||G||_2 from the base point (x, E saved); when no
+        // trial decreases it, take the plain step x <- E(Gamma(x)) instead
         k_gather_x<<<g1, 256, 0, s>>>(list, na, x, xb);
         URCHIN_TRY(launched());
+        URCHIN_TRY_CUDA(cudaMemcpyAsync(Eb, E, sizeof(double) * (size_t)na, cudaMemcpyDeviceToDevice, s));
         double lam = 1.0;
-        for (int ls = 0;; ++ls) {
+        bool accepted = false;
+        for (int ls = 0; ls < 3 && stats.iterations < P.max_iter; ++ls) {
             k_set_x<<<g1, 256, 0, s>>>(list, na, d, lam, xb, nullptr, x, bvh->A64, w32, w64, xs32, xs64);
             URCHIN_TRY(launched());
             double mrel_t, norm_t;
             int64_t sw_t = 0;
             URCHIN_TRY(evaluate(1, V, E, ctan, dtmp, hdev, &mrel_t, &norm_t, &sw_t));
-            const bool ok = norm_t <= (1.0 - 1e-4 * lam) * norm;
-            if (ok || ls >= 4 || stats.iterations >= P.max_iter) {
+            if (norm_t <= (1.0 - 1e-4 * lam) * norm) {
                 mrel = mrel_t;
                 norm = norm_t;
                 sw = sw_t;
+                accepted = true;
                 break;
             }
             lam *= 0.5;
+        }
+        if (!accepted) {
+            stats.newton_fallbacks += 1;
+            k_set_x<<<g1, 256, 0, s>>>(list, na, nullptr, 0.0, nullptr, Eb, x, bvh->A64, w32, w64, xs32, xs64);
+            URCHIN_TRY(launched());
+            if (stats.iterations >= P.max_iter) break;
+            URCHIN_TRY(evaluate(0, V, E, ctan, dtmp, hdev, &mrel, &norm, &sw));
+            continue;
         }
         if (sw > 0 && stats.iterations < P.max_iter) {
             // cases newly past tau_eff = 1: latch them and re-evaluate here

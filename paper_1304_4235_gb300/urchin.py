@@ -64,7 +64,8 @@ class urchin_solve_stats(C.Structure):
                 ("particle_updates", C.c_int64), ("n_active", C.c_int64), ("nnz", C.c_int64),
                 ("max_rel_dx", C.c_double), ("wall_s", C.c_double), ("converged", C.c_int),
                 ("segments_stored", C.c_int), ("hits", C.c_int64), ("trace_s", C.c_double),
-                ("trace_launches", C.c_int), ("sphere_tests", C.c_int64), ("node_visits", C.c_int64)]
+                ("trace_launches", C.c_int), ("sphere_tests", C.c_int64), ("node_visits", C.c_int64),
+                ("newton_fallbacks", C.c_int)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
