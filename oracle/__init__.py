@@ -80,7 +80,7 @@ def _load():
                 "oracle_rates": (None, [d, vp, vp, vp]),
                 "oracle_xeq": (d, [d, d, d, d, i]),
                 "oracle_solve": (i, [i64, vp, vp, vp, vp, vp, vp, vp, d, i, d, d,
-                                     vp, i, d, i, i, vp, vp, d, d, i, i, vp, vp, vp, vp]),
+                                     vp, i, d, i, i, vp, vp, d, d, i, i, i, vp, vp, vp, vp]),
                 "oracle_num_threads": (i, []),
             }
             for name, (res, args) in sig.items():
@@ -219,10 +219,11 @@ def xeq(Gamma, nH, T, y=0.0, caseB=False):
 
 # -- driver (Sec. 4) ---------------------------------------------------------
 def solve(w, s, wts, dirs, tol=1e-3, tau_skip=1e-4, max_iter=100, case_rule=CASE_AUTO,
-          kernel=KERNEL_M4, y=0.0, x_start=None, sweeps=None, l_ray=None):
-    """Jacobi iteration of Sec. 4.  ``sweeps`` = exact sweep count (step-matched
-    mode) instead of the tolerance test.  Returns (x, frozen, stats) with
-    stats = dict(sweeps, max_rel_dx, rays, converged)."""
+          kernel=KERNEL_M4, y=0.0, x_start=None, sweeps=None, l_ray=None, blocks=1):
+    """Iteration of Sec. 4: Jacobi (blocks=1) or the high-to-low density
+    update order in `blocks` blocks.  ``sweeps`` = exact sweep count
+    (step-matched mode) instead of the tolerance test.  Returns (x, frozen,
+    stats) with stats = dict(sweeps, max_rel_dx, rays, converged)."""
     px, py, pz, h, m = _particles(w)
     nH, T = _f64(w.nH), _f64(w.T)
     dirs = _f64(dirs).reshape(-1, 3)
@@ -237,7 +238,7 @@ def solve(w, s, wts, dirs, tol=1e-3, tau_skip=1e-4, max_iter=100, case_rule=CASE
                               _p(dirs), dirs.shape[0],
                               float(w.l_ray if l_ray is None else l_ray), kernel,
                               s.shape[0], _p(s), _p(wts), float(tol), float(tau_skip),
-                              mi, case_rule, _p(xs), _p(x), _p(frozen), _p(st))
+                              mi, case_rule, int(blocks), _p(xs), _p(x), _p(frozen), _p(st))
     return x, frozen.astype(bool), dict(sweeps=int(st[0]), max_rel_dx=float(st[1]),
                                         rays=float(st[2]), converged=(rc == 0))
 

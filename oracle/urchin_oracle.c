@@ -430,17 +430,33 @@ static int use_caseB(int case_rule, double tau_eff)
  * iteration then alternates between the two forever; the latch settles
  * them in case B.
  * If max_iter < 0 the run does exactly -max_iter sweeps (step-matched mode).
+ * blocks > 1 selects the update order of Sec. 4 instead of Jacobi: after
+ * sweep 0 the non-frozen particles are ordered from high to low density
+ * (n_H rounded to float, ties by particle index), cut into `blocks`
+ * contiguous blocks of sizes floor((b+1) m / blocks) - floor(b m / blocks),
+ * and each sweep updates block after block, every block's columns using the
+ * x of the blocks already updated in that sweep.
  * x_out[n] receives the final x, frozen_out[n] (optional) 1 for frozen
  * particles, stats[0] = sweeps done, stats[1] = last max |dx|/x,
  * stats[2] = rays traced.  x_start (optional) replaces x_thin as the start
  * (sweep 0 still applies the freeze rule).  Returns 0 when converged, 1 when
  * the sweep limit ended the run. */
+static const double* g_sort_nH;
+static int by_density(const void* a, const void* b)
+{
+    int64_t i = *(const int64_t*)a, j = *(const int64_t*)b;
+    float fi = (float)g_sort_nH[i], fj = (float)g_sort_nH[j];
+    if (fi > fj) return -1;
+    if (fi < fj) return 1;
+    return (i > j) - (i < j);
+}
+
 int oracle_solve(int64_t n, const double* px, const double* py, const double* pz,
                  const double* h, const double* mass_H, const double* nH, const double* T,
                  double y, int periodic, double L, double unit_cm,
                  const double* dirs, int R, double l_ray, int kernel,
                  int F, const double* s, const double* w,
-                 double tol, double tau_skip, int max_iter, int case_rule,
+                 double tol, double tau_skip, int max_iter, int case_rule, int blocks,
                  const double* x_start, double* x_out, int* frozen_out, double* stats)
 {
     double gthin = 0.0;
@@ -462,29 +478,57 @@ int oracle_solve(int64_t n, const double* px, const double* py, const double* pz
     int64_t nact = n;
     for (int64_t i = 0; i < n; ++i) act[i] = i;
     while (sweeps < limit) {
-        oracle_columns(n, px, py, pz, h, mass_H, x, periodic, L, unit_cm,
-                       act, nact, dirs, R, l_ray, kernel, tau);
-        oracle_gamma(tau, nact, R, F, s, w, G, te);
-        rays += (double)nact * R;
-        if (sweeps == 0) {
-            int64_t m = 0;
+        if (sweeps == 0 || blocks <= 1) {
+            oracle_columns(n, px, py, pz, h, mass_H, x, periodic, L, unit_cm,
+                           act, nact, dirs, R, l_ray, kernel, tau);
+            oracle_gamma(tau, nact, R, F, s, w, G, te);
+            rays += (double)nact * R;
+            if (sweeps == 0) {
+                int64_t m = 0;
+                for (int64_t o = 0; o < nact; ++o) {
+                    int64_t i = act[o];
+                    if (te[o] < tau_skip) { frozen[i] = 1; continue; }
+                    act[m] = i; G[m] = G[o]; te[m] = te[o]; ++m;
+                }
+                nact = m;
+            }
+            maxrel = 0.0;
             for (int64_t o = 0; o < nact; ++o) {
                 int64_t i = act[o];
-                if (te[o] < tau_skip) { frozen[i] = 1; continue; }
-                act[m] = i; G[m] = G[o]; te[m] = te[o]; ++m;
+                int cb = use_caseB(case_rule, te[o]) || (case_rule == 2 && latchB[i]);
+                latchB[i] = cb;
+                xn[o] = oracle_xeq(G[o], nH[i], T[i], y, cb);
+                double rel = fabs(xn[o] - x[i]) / x[i];
+                if (rel > maxrel) maxrel = rel;
             }
-            nact = m;
+            for (int64_t o = 0; o < nact; ++o) x[act[o]] = xn[o];
+            if (sweeps == 0 && blocks > 1) {
+                g_sort_nH = nH;
+                qsort(act, (size_t)nact, sizeof(int64_t), by_density);
+            }
+        } else {
+            maxrel = 0.0;
+            for (int b = 0; b < blocks; ++b) {
+                int64_t lo = (b * nact) / blocks;
+                int64_t hi = ((b + 1) * nact) / blocks;
+                int64_t m = hi - lo;
+                if (m <= 0) continue;
+                oracle_columns(n, px, py, pz, h, mass_H, x, periodic, L, unit_cm,
+                               act + lo, m, dirs, R, l_ray, kernel, tau);
+                oracle_gamma(tau, m, R, F, s, w, G, te);
+                rays += (double)m * R;
+                for (int64_t o = 0; o < m; ++o) {
+                    int64_t i = act[lo + o];
+                    int cb = use_caseB(case_rule, te[o]) || (case_rule == 2 && latchB[i]);
+                    latchB[i] = cb;
+                    double xv = oracle_xeq(G[o], nH[i], T[i], y, cb);
+                    double rel = fabs(xv - x[i]) / x[i];
+                    if (rel > maxrel) maxrel = rel;
+                    xn[o] = xv;
+                }
+                for (int64_t o = 0; o < m; ++o) x[act[lo + o]] = xn[o];
+            }
         }
-        maxrel = 0.0;
-        for (int64_t o = 0; o < nact; ++o) {
-            int64_t i = act[o];
-            int cb = use_caseB(case_rule, te[o]) || (case_rule == 2 && latchB[i]);
-            latchB[i] = cb;
-            xn[o] = oracle_xeq(G[o], nH[i], T[i], y, cb);
-            double rel = fabs(xn[o] - x[i]) / x[i];
-            if (rel > maxrel) maxrel = rel;
-        }
-        for (int64_t o = 0; o < nact; ++o) x[act[o]] = xn[o];
         ++sweeps;
         if (!fixed && maxrel < tol) { converged = 1; break; }
     }

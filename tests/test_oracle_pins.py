@@ -480,3 +480,43 @@ def test_driver_sweep_semantics():
     xe[idx] = O.xeq(g, w.nH[idx], w.T[idx], 0.0, te >= 1)
     assert np.allclose(x2, xe, rtol=1e-14, atol=0)
     assert st["rays"] == (w.n + act.sum()) * 12
+
+
+def test_density_ordered_blocks_semantics():
+    # two sweeps with the high-to-low density order in 3 blocks equal the
+    # composition of the primitives in that order (Sec. 4 update order)
+    w = _tiny_isolated(n=14)
+    w.mass_H = w.mass_H * 300
+    w.nH = np.linspace(1.0, 0.1, w.n)[::-1].copy()       # density rises with index
+    s, wts = _spec()
+    dirs = O.healpix(1)
+    x2, frozen, st = O.solve(w, s, wts, dirs, sweeps=2, blocks=3)
+    x0 = O.xeq(wts.sum(), w.nH, w.T, 0.0, False)
+    g, te = O.gamma(O.columns(w, x0, dirs), s, wts)
+    act = np.where(te >= 1e-4)[0]
+    x1 = x0.copy()
+    x1[act] = O.xeq(g[act], w.nH[act], w.T[act], 0.0, te[act] >= 1)
+    latch = np.zeros(w.n, bool)
+    latch[act] = te[act] >= 1
+    order = sorted(act, key=lambda i: (-np.float32(w.nH[i]), i))
+    m = len(order)
+    xe = x1.copy()
+    for b in range(3):
+        blk = np.array(order[(b * m) // 3:((b + 1) * m) // 3])
+        g, te = O.gamma(O.columns(w, xe, dirs, origins=blk), s, wts)
+        cb = (te >= 1) | latch[blk]
+        latch[blk] = cb
+        xe[blk] = O.xeq(g, w.nH[blk], w.T[blk], 0.0, cb)
+    assert np.allclose(x2, xe, rtol=1e-14, atol=0)
+
+
+def test_density_order_reaches_jacobi_fixed_point():
+    w = _tiny_isolated(n=14)
+    w.mass_H = w.mass_H * 300
+    s, wts = _spec()
+    dirs = O.healpix(1)
+    xj, _, sj = O.solve(w, s, wts, dirs, tol=1e-12, max_iter=2000, case_rule=O.CASE_A)
+    xb, _, sb = O.solve(w, s, wts, dirs, tol=1e-12, max_iter=2000, case_rule=O.CASE_A, blocks=4)
+    assert sj["converged"] and sb["converged"]
+    assert np.allclose(xj, xb, rtol=1e-9)
+    assert sb["sweeps"] <= sj["sweeps"]
