@@ -220,6 +220,18 @@ typedef struct {
                                             after each sweep / Newton step     */
     int64_t*        history_unconverged; /* host [max_iter] or NULL: particles
                                             with |dx|/x >= tol at that point   */
+    int             blocks;       /* update order after sweep 0 (plain method):
+                                     1 = Jacobi (all x from the previous
+                                     sweep); B > 1 = the Sec. 4 order, high to
+                                     low density, in B blocks updated in
+                                     sequence (float32 n_H descending, ties by
+                                     particle index; block b holds ranks
+                                     [b m / B, (b+1) m / B) of the m
+                                     non-frozen particles)                     */
+    double          newton_switch; /* NEWTON: plain sweeps run until at most this
+                                      fraction of the non-frozen particles has
+                                      |dx|/x >= tol, then Newton-Krylov takes
+                                      over (<= 0: 0.01)                        */
 } urchin_solve_params;
 
 typedef struct {
@@ -239,6 +251,7 @@ typedef struct {
     int64_t sphere_tests;         /* ray-sphere tests at leaves (profile=1)    */
     int64_t node_visits;          /* internal nodes visited (profile=1)        */
     int     newton_fallbacks;     /* Newton steps replaced by a plain sweep    */
+    int     newton_start;         /* iterations done before Newton took over   */
 } urchin_solve_stats;
 
 /* Iterate to the equilibrium neutral fraction (Sec. 4): x starts at x_thin
@@ -246,8 +259,10 @@ typedef struct {
  * freezes those with tau_eff < tau_skip at their current x; each later sweep
  * recomputes Gamma for all non-frozen particles from the previous sweep's x
  * (Jacobi) and updates them; the run stops when max |dx|/x < tol.
- * URCHIN_METHOD_NEWTON solves the same fixed point x = E(Gamma(x)) with a
- * Newton-Krylov iteration in ln x (GMRES, tangent columns).  x_inout is
+ * URCHIN_METHOD_NEWTON runs those sweeps until at most `newton_switch` of
+ * the non-frozen particles remain above tol, then solves the same fixed
+ * point x = E(Gamma(x)) with a Newton-Krylov iteration in ln x (GMRES with
+ * tangent columns, backtracking, plain-sweep fallback).  x_inout is
  * device [n] double in the original particle order.  `stats` may be NULL.
  * Synchronises `stream`.  Returns URCHIN_ERR_NOT_CONVERGED (x_inout then
  * holds the last iterate) when max_iter is reached first. */

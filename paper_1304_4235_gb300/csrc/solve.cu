@@ -290,6 +290,46 @@ __global__ void k_set_x(const int32_t* __restrict__ items, int64_t n_act, const 
     }
 }
 
+// density order: value = original index of each active item
+__global__ void k_orig_keys(const int32_t* __restrict__ list, const int32_t* __restrict__ perm, int64_t na,
+                            uint32_t* keys, int32_t* vals)
+{
+    for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < na; a += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t o = perm[list[a]];
+        keys[a] = (uint32_t)o;
+        vals[a] = o;
+    }
+}
+
+// key = bits of float(n_H) inverted, so an ascending sort is high to low density
+__global__ void k_density_keys(const int32_t* __restrict__ vals, const double* __restrict__ nH_orig, int64_t na,
+                               uint32_t* keys)
+{
+    for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < na; a += (int64_t)gridDim.x * blockDim.x)
+        keys[a] = ~__float_as_uint((float)nH_orig[vals[a]]);
+}
+
+// block of each density rank a: block b holds ranks [b na / B, (b+1) na / B)
+__global__ void k_block_of(const int32_t* __restrict__ vals, const int32_t* __restrict__ inv, int64_t na, int B,
+                           uint32_t* block_of_slot)
+{
+    for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < na; a += (int64_t)gridDim.x * blockDim.x) {
+        int64_t b = (a * B) / na;
+        while (b + 1 < B && ((b + 1) * na) / B <= a) ++b;
+        while (b > 0 && (b * na) / B > a) --b;
+        block_of_slot[inv[vals[a]]] = (uint32_t)b;
+    }
+}
+
+__global__ void k_block_keys(const int32_t* __restrict__ list, const uint32_t* __restrict__ block_of_slot, int64_t na,
+                             uint32_t* keys, int32_t* vals)
+{
+    for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < na; a += (int64_t)gridDim.x * blockDim.x) {
+        keys[a] = block_of_slot[list[a]];
+        vals[a] = list[a];
+    }
+}
+
 }  // namespace
 
 int launch_sweep(const SweepArgs& A, cudaStream_t s)
@@ -633,6 +673,50 @@ int Solver::first_sweep()
     return URCHIN_OK;
 }
 
+// Regroup the active list (Morton order) into the blocks of the high-to-low
+// density order; inside a block the items stay in Morton order (a block's
+// updates are simultaneous, so their order does not matter, and Morton
+// order keeps the block's rays coherent).
+int Solver::order_by_density()
+{
+    const int64_t na = n_act;
+    const int B = (int)std::min<int64_t>(P.blocks, std::max<int64_t>(na, 1));
+    block_lo.assign(1, 0);
+    if (B <= 1 || na == 0) {
+        block_lo.push_back(na);
+        return URCHIN_OK;
+    }
+    Layout lay;
+    size_t o_k = lay.take(sizeof(uint32_t) * (size_t)na);
+    size_t o_v = lay.take(sizeof(int32_t) * (size_t)na);
+    size_t o_b = lay.take(sizeof(uint32_t) * (size_t)n);
+    size_t o_t = lay.take(radix_tmp_bytes(na));
+    Scratch tmp;
+    URCHIN_TRY(tmp.alloc(lay.bytes, s));
+    uint32_t* keys = tmp.at<uint32_t>(o_k);
+    int32_t* vals = tmp.at<int32_t>(o_v);
+    uint32_t* blk = tmp.at<uint32_t>(o_b);
+    void* rt = tmp.at<void>(o_t);
+    const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>((na + 255) / 256, 4096));
+    k_orig_keys<<<g, 256, 0, s>>>(list, bvh->perm, na, keys, vals);
+    URCHIN_TRY(launched());
+    URCHIN_TRY(radix_sort_pairs(keys, vals, na, 30, rt, s));          // by particle index
+    k_density_keys<<<g, 256, 0, s>>>(vals, P.nH, na, keys);
+    URCHIN_TRY(launched());
+    URCHIN_TRY(radix_sort_pairs(keys, vals, na, 32, rt, s));          // stable: high to low density
+    k_block_of<<<g, 256, 0, s>>>(vals, bvh->inv, na, B, blk);
+    URCHIN_TRY(launched());
+    k_block_keys<<<g, 256, 0, s>>>(list, blk, na, keys, vals);
+    URCHIN_TRY(launched());
+    int bits = 1;
+    while ((1 << bits) < B) ++bits;
+    URCHIN_TRY(radix_sort_pairs(keys, vals, na, bits, rt, s));        // stable: Morton order inside blocks
+    URCHIN_TRY_CUDA(cudaMemcpyAsync(list, vals, sizeof(int32_t) * (size_t)na, cudaMemcpyDeviceToDevice, s));
+    tmp.release();
+    for (int b = 1; b <= B; ++b) block_lo.push_back(((int64_t)b * na) / B);
+    return URCHIN_OK;
+}
+
 int Solver::plain()
 {
     URCHIN_TRY(first_sweep());
@@ -640,11 +724,23 @@ int Solver::plain()
         stats.converged = 1;
         return URCHIN_OK;
     }
+    return plain_sweeps(-1.0);
+}
+
+// Sweeps after sweep 0 until converged, out of iterations, or (stop_fraction
+// >= 0) at most stop_fraction of the non-frozen particles above tol.
+int Solver::plain_sweeps(double stop_fraction)
+{
+    URCHIN_TRY(order_by_density());
     while (stats.iterations < P.max_iter) {
         URCHIN_TRY_CUDA(cudaMemsetAsync(misc, 0, sizeof(unsigned long long), s));
         URCHIN_TRY_CUDA(cudaMemsetAsync(misc + 7, 0, sizeof(unsigned long long), s));
-        URCHIN_TRY(columns(list, n_act, 0));
-        URCHIN_TRY(launch_sweep(sweep_args(list, n_act, 0), s));
+        for (size_t b = 0; b + 1 < block_lo.size(); ++b) {
+            const int64_t lo = block_lo[b], m = block_lo[b + 1] - block_lo[b];
+            if (m <= 0) continue;
+            URCHIN_TRY(columns(list + lo, m, 0));
+            URCHIN_TRY(launch_sweep(sweep_args(list + lo, m, 0), s));
+        }
         double m;
         unsigned st;
         URCHIN_TRY(read_scalars(&m, &st));
@@ -656,6 +752,7 @@ int Solver::plain()
             stats.converged = 1;
             break;
         }
+        if (stop_fraction >= 0.0 && (double)last_above <= stop_fraction * (double)n_act) break;
     }
     return URCHIN_OK;
 }
@@ -716,6 +813,10 @@ int Solver::newton()
         stats.converged = 1;
         return URCHIN_OK;
     }
+    // plain sweeps as the predictor until few particles are left above tol
+    URCHIN_TRY(plain_sweeps(P.newton_switch > 0.0 ? P.newton_switch : 0.01));
+    stats.newton_start = stats.iterations;
+    if (stats.converged || stats.iterations >= P.max_iter) return URCHIN_OK;
     const int m = P.gmres_m;
     const int64_t na = n_act;
     const size_t rsz = f64 ? sizeof(double) : sizeof(float);

@@ -106,7 +106,10 @@ struct Solver {
     int read_scalars(double* maxrel, unsigned* status);
     void record(double maxrel);
     int first_sweep();
+    int order_by_density();
+    std::vector<int64_t> block_lo;               // block b = list[block_lo[b], block_lo[b+1])
     int plain();
+    int plain_sweeps(double stop_fraction);
     int newton();
     int run() { return P.method == URCHIN_METHOD_NEWTON ? newton() : plain(); }
     int finish(double* x_inout);

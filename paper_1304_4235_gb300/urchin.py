@@ -56,7 +56,7 @@ class urchin_solve_params(C.Structure):
                 ("method", C.c_int), ("segments", C.c_int), ("gmres_m", C.c_int),
                 ("kernel", C.c_int), ("precision", C.c_int), ("case_rule", C.c_int),
                 ("warm_start", C.c_int), ("profile", C.c_int), ("history_maxrel", _vp),
-                ("history_unconverged", _vp)]
+                ("history_unconverged", _vp), ("blocks", C.c_int), ("newton_switch", C.c_double)]
 
 
 class urchin_solve_stats(C.Structure):
@@ -65,7 +65,7 @@ class urchin_solve_stats(C.Structure):
                 ("max_rel_dx", C.c_double), ("wall_s", C.c_double), ("converged", C.c_int),
                 ("segments_stored", C.c_int), ("hits", C.c_int64), ("trace_s", C.c_double),
                 ("trace_launches", C.c_int), ("sphere_tests", C.c_int64), ("node_visits", C.c_int64),
-                ("newton_fallbacks", C.c_int)]
+                ("newton_fallbacks", C.c_int), ("newton_start", C.c_int)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -267,7 +267,7 @@ def urchin_solve(bvh: Bvh, dirs, l_ray: float, s, w, nH, T, x=None, *, y: float 
                  method: int = METHOD_PLAIN, segments: int = SEG_RECOMPUTE, gmres_m: int = 10,
                  kernel: int = KERNEL_M4, precision: int = F32, case_rule: int = CASE_AUTO,
                  warm_start: bool = False, profile: bool = False, raise_not_converged: bool = True,
-                 history: bool = False, stream=None):
+                 history: bool = False, blocks: int = 1, newton_switch: float = 0.01, stream=None):
     """Returns (x, stats dict).  x (float64 CUDA tensor, original order) is
     updated in place when given."""
     import torch
@@ -293,6 +293,8 @@ def urchin_solve(bvh: Bvh, dirs, l_ray: float, s, w, nH, T, x=None, *, y: float 
     P.case_rule = int(case_rule)
     P.warm_start = int(bool(warm_start))
     P.profile = int(bool(profile))
+    P.blocks = int(blocks)
+    P.newton_switch = float(newton_switch)
     hist_max = hist_unc = None
     if history:
         hist_max = np.zeros(int(max_iter))

@@ -362,3 +362,24 @@ def test_plain_solve_latched_case_matches_oracle(halo_small):
     x, st = _solve_gpu(w, bvh, d, sg, U.F64, tol=1e-300, max_iter=15, segments=U.SEG_STORE)
     xo, fo, so_ = O.solve(w, so[0], so[1], O.healpix(1), sweeps=15)
     assert rel_err(x, xo).max() < 1e-8
+
+
+@pytest.mark.parametrize("blocks", [2, 8])
+def test_density_ordered_blocks_match_oracle(halo_small, blocks):
+    """The Sec. 4 high-to-low density update order, in blocks, step matched
+    against the oracle (FP64, stored segments)."""
+    w, bvh, d = halo_small
+    sg, so = spectra(w, torch)
+    x, st = _solve_gpu(w, bvh, d, sg, U.F64, tol=1e-300, max_iter=4, segments=U.SEG_STORE, blocks=blocks)
+    xo, fo, so_ = O.solve(w, so[0], so[1], O.healpix(1), sweeps=4, blocks=blocks)
+    assert st["iterations"] == 4 and st["rays"] == so_["rays"]
+    assert rel_err(x, xo).max() < 1e-8
+
+
+def test_density_ordered_blocks_converge_faster(halo_small):
+    w, bvh, d = halo_small
+    sg, so = spectra(w, torch)
+    xj, sj = _solve_gpu(w, bvh, d, sg, U.F32, tol=1e-3, max_iter=3000, segments=U.SEG_STORE)
+    xb, sb = _solve_gpu(w, bvh, d, sg, U.F32, tol=1e-3, max_iter=3000, segments=U.SEG_STORE, blocks=32)
+    assert sj["converged"] and sb["converged"]
+    assert sb["iterations"] < sj["iterations"]
