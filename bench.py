@@ -37,15 +37,21 @@ sys.path.insert(0, ROOT)
 METRIC = "rays/s and particle-updates/s to converged x (rel 1e-3), Newton+adjoint vs plain"
 WORKLOAD = "halo_262144_nside1_l200kpc_F100"
 
-# dram__bytes_read.sum + dram__bytes_write.sum per launch of the traversal
-# kernel, from one ncu capture, keyed by the hash of the traversal sources at
-# capture time (reported as null once the kernel has changed).
-TRACE_TRAFFIC = {}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per unit of work
+# of a kernel, from one ncu capture, keyed by the hash of the kernel's source
+# files at capture time; a changed kernel reports traffic null.
+#   k_spmv: bytes per stored segment read;  k_trace: bytes per ray-sphere hit
+MEASURED_TRAFFIC = {
+    "k_spmv": {},
+    "k_trace": {},
+}
+KERNEL_SOURCES = {"k_spmv": ("linalg.cu", "linalg.cuh", "common.cuh"),
+                  "k_trace": ("trace.cu", "common.cuh")}
 
 
-def source_hash() -> str:
+def source_hash(kernel: str) -> str:
     h = hashlib.sha256()
-    for f in ("trace.cu", "common.cuh"):
+    for f in KERNEL_SOURCES[kernel]:
         with open(os.path.join(ROOT, "paper_1304_4235_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -58,7 +64,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--method", choices=["plain", "newton"], default="plain")
-    ap.add_argument("--segments", choices=["recompute", "store", "auto"], default="recompute")
+    ap.add_argument("--segments", choices=["recompute", "store", "auto"], default="auto")
+    ap.add_argument("--blocks", type=int, default=1, help="update order: 1 Jacobi, B>1 density blocks")
+    ap.add_argument("--no-compare", action="store_true", help="skip the untimed Newton / tight-tolerance runs")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -220,12 +228,13 @@ def main():
     dirs = U.urchin_healpix_dirs(w.nside)
     stream = torch.cuda.current_stream(dev)
 
-    def step(dd, x_out=None):
+    def step(dd, x_out=None, meth=None, tol=1e-3, max_iter=None):
         bvh = U.urchin_build_bvh(dd["px"], dd["py"], dd["pz"], dd["h"], dd["m"], w.periodic, w.box, w.unit_cm)
         x = torch.empty(w.n, dtype=torch.float64, device=dev) if x_out is None else x_out
-        x, st = U.urchin_solve(bvh, dirs, w.l_ray, s_d, w_d, dd["nH"], dd["T"], x, tol=1e-3, tau_skip=1e-4,
-                               max_iter=args.max_iter, method=method, segments=segs, precision=U.F32,
-                               case_rule=U.CASE_AUTO, profile=True, raise_not_converged=False)
+        x, st = U.urchin_solve(bvh, dirs, w.l_ray, s_d, w_d, dd["nH"], dd["T"], x, tol=tol, tau_skip=1e-4,
+                               max_iter=max_iter or args.max_iter, method=method if meth is None else meth,
+                               segments=segs, precision=U.F32, case_rule=U.CASE_AUTO, profile=True,
+                               raise_not_converged=False, blocks=args.blocks, gmres_m=20)
         bvh.close()
         return x, st
 
@@ -301,11 +310,41 @@ def main():
         return
 
     hbm, peak_kind = peaks()
-    alg_bytes = hits * 20 + rays / world * 4          # particle records + tau written
-    per_launch_bytes = alg_bytes / max(trace_launches, 1)
-    per_launch_s = trace_s / max(trace_launches, 1)
-    achieved = per_launch_bytes / per_launch_s / 1e9 if per_launch_s > 0 else None
-    traffic = TRACE_TRAFFIC.get(source_hash())
+    # per-kernel GPU time of the timed steps (CUDA events on the solve's stream)
+    spmv_s = sum(st["spmv_s"] for st in stats)
+    sweep_s = sum(st["sweep_s"] for st in stats)
+    spmv_launches = sum(st["spmv_launches"] for st in stats)
+    spmv_bytes = sum(st["spmv_bytes"] for st in stats)
+    trace_bytes = hits * 20 + sum(st["rays"] for st in stats if st["spmv_launches"] == 0) * 4
+    kernels = {
+        "k_spmv": {"s": spmv_s, "launches": spmv_launches},
+        "k_trace": {"s": trace_s, "launches": trace_launches},
+        "k_sweep": {"s": sweep_s, "launches": sum(st["sweep_launches"] for st in stats)},
+    }
+    for k in kernels.values():
+        k["share_of_step"] = k["s"] / (total_ms * 1e-3 / world) if total_ms > 0 else None
+    if spmv_s >= trace_s and spmv_launches > 0:
+        per_bytes = spmv_bytes / spmv_launches
+        per_s = spmv_s / spmv_launches
+        seg_per_launch = (spmv_bytes / spmv_launches) / 8.0
+        t = MEASURED_TRAFFIC["k_spmv"].get(source_hash("k_spmv"))
+        roof = {"bound": "hbm", "achieved": per_bytes / per_s / 1e9, "peak": hbm, "unit": "GB/s",
+                "frac": per_bytes / per_s / 1e9 / hbm,
+                "traffic": (t * seg_per_launch) if t else None,
+                "kernel": "k_spmv<float>", "peak_kind": peak_kind,
+                "alg_bytes_per_launch": per_bytes, "launch_ms": per_s * 1e3}
+    else:
+        per_bytes = trace_bytes / max(trace_launches, 1)
+        per_s = trace_s / max(trace_launches, 1)
+        t = MEASURED_TRAFFIC["k_trace"].get(source_hash("k_trace"))
+        roof = {"bound": "hbm", "achieved": per_bytes / per_s / 1e9 if per_s > 0 else None, "peak": hbm,
+                "unit": "GB/s", "frac": (per_bytes / per_s / 1e9 / hbm) if per_s > 0 else None,
+                "traffic": (t * hits / max(trace_launches, 1)) if t else None,
+                "kernel": "k_trace<float,M4>", "peak_kind": peak_kind,
+                "alg_bytes_per_launch": per_bytes, "launch_ms": per_s * 1e3}
+    roof["traversal"] = {"hits_per_launch": hits / max(trace_launches, 1), "launch_ms": 1e3 * trace_s / max(trace_launches, 1),
+                         "sphere_tests_per_hit": sum(st["sphere_tests"] for st in stats) / max(hits, 1),
+                         "node_visits_per_hit": sum(st["node_visits"] for st in stats) / max(hits, 1)}
     st0 = stats[-1]
     line = {
         "metric": METRIC, "value": rays / (total_ms * 1e-3), "unit": "rays/s", "n_gpus": world,
@@ -313,22 +352,39 @@ def main():
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "particles": w.n, "rays_per_particle": w.R, "l_ray_kpc": w.l_ray,
-                   "bins": w.F, "method": args.method, "segments": args.segments, "tol": 1e-3,
-                   "l2": "flushed before each step (256 MB write)"},
+                   "bins": w.F, "method": args.method, "segments": args.segments, "blocks": args.blocks,
+                   "tol": 1e-3, "l2": "flushed before each step (256 MB write); stored segments >> L2"},
         "particle_updates_per_s": updates / (total_ms * 1e-3),
         "iterations": st0["iterations"], "n_active": st0["n_active"], "converged": bool(st0["converged"]),
+        "segments_stored": bool(st0["segments_stored"]), "nnz": st0["nnz"],
         "wall_s_to_converged": total_ms * 1e-3 / args.steps,
         "gpu_launches": int(launches),
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": (achieved / hbm) if achieved else None, "traffic": traffic,
-                     "kernel": "k_trace<float,M4>", "peak_kind": peak_kind,
-                     "alg_bytes_per_launch": per_launch_bytes, "launch_ms": per_launch_s * 1e3,
-                     "hits_per_launch": hits / max(trace_launches, 1),
-                     "sphere_tests_per_hit": sum(st["sphere_tests"] for st in stats) / max(hits, 1),
-                     "node_visits_per_hit": sum(st["node_visits"] for st in stats) / max(hits, 1)},
+        "roofline": roof,
+        "kernels": kernels,
         "clocks": clk,
         "e2e": e2e,
     }
+    if not args.no_compare and world == 1:
+        # untimed: the other method and a tightly converged reference x*,
+        # to report each method's wall time and its distance to x*
+        comp = {}
+        xr, sr = step(d, meth=U.METHOD_PLAIN, tol=1e-6, max_iter=20000)
+        xr = xr.cpu().numpy()
+        for name, meth in (("plain", U.METHOD_PLAIN), ("newton", U.METHOD_NEWTON)):
+            torch.cuda.synchronize(dev)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            xm, sm = step(d, meth=meth, max_iter=400 if meth == U.METHOD_NEWTON else args.max_iter)
+            b.record(stream)
+            b.synchronize()
+            dist = np.abs(xm.cpu().numpy() - xr) / xr
+            comp[name] = {"wall_s": a.elapsed_time(b) * 1e-3, "iterations": sm["iterations"],
+                          "converged": bool(sm["converged"]), "rays": sm["rays"],
+                          "newton_start": sm["newton_start"], "newton_fallbacks": sm["newton_fallbacks"],
+                          "max_rel_to_xstar": float(dist.max()), "p999_rel_to_xstar": float(np.quantile(dist, 0.999))}
+        comp["xstar"] = {"tol": 1e-6, "iterations": sr["iterations"], "converged": bool(sr["converged"])}
+        line["compare"] = comp
     if world == 1 and not args.no_cpu_baseline:
         import oracle as O
         e_, J_ = w.spectrum()

@@ -252,6 +252,14 @@ typedef struct {
     int64_t node_visits;          /* internal nodes visited (profile=1)        */
     int     newton_fallbacks;     /* Newton steps replaced by a plain sweep    */
     int     newton_start;         /* iterations done before Newton took over   */
+    double  spmv_s;               /* GPU time of stored-segment sweeps (profile=1) */
+    int     spmv_launches;        /* stored-segment column launches            */
+    int64_t spmv_bytes;           /* algorithmic bytes of those launches:
+                                     segments read (index + value), columns
+                                     written, x gathered once per launch       */
+    double  sweep_s;              /* GPU time of the spectral/equilibrium
+                                     kernel (profile=1)                        */
+    int     sweep_launches;
 } urchin_solve_stats;
 
 /* Iterate to the equilibrium neutral fraction (Sec. 4): x starts at x_thin

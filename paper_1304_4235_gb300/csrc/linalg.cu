@@ -107,6 +107,20 @@ __global__ void k_axpby(double alpha, const double* __restrict__ x, double beta,
         y[t] = alpha * x[t] + beta * y[t];
 }
 
+__global__ void k_row_nnz(const uint64_t* __restrict__ row_ptr, const int32_t* __restrict__ items, int64_t n_items,
+                          int64_t n_rows_per_k, int R, unsigned long long* acc)
+{
+    unsigned long long t = 0;
+    for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < (int64_t)R * n_items;
+         w += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = w / n_items, a = w - k * n_items;
+        const int64_t row = k * n_rows_per_k + (items ? items[a] : a);
+        t += row_ptr[row + 1] - row_ptr[row];
+    }
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if ((threadIdx.x & 31) == 0 && t) atomicAdd(acc, t);
+}
+
 unsigned grid1(int64_t n) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 2048)); }
 
 }  // namespace
@@ -122,6 +136,13 @@ int launch_spmv(const SpmvArgs& A, cudaStream_t s)
     if (need < grid) grid = (int)std::max<int64_t>(need, 1);
     if (A.precision == URCHIN_F64) k_spmv<double><<<grid, kSpmvThreads, 0, s>>>(A);
     else k_spmv<float><<<grid, kSpmvThreads, 0, s>>>(A);
+    return launched();
+}
+
+int launch_row_nnz(const uint64_t* row_ptr, const int32_t* items, int64_t n_items, int64_t n_rows_per_k, int R,
+                   unsigned long long* acc, cudaStream_t s)
+{
+    k_row_nnz<<<grid1((int64_t)R * n_items), 256, 0, s>>>(row_ptr, items, n_items, n_rows_per_k, R, acc);
     return launched();
 }
 

@@ -19,6 +19,10 @@ struct SpmvArgs {
 };
 int launch_spmv(const SpmvArgs& A, cudaStream_t s);
 
+// acc += number of segments of the rays (k, items[a]) (profiling)
+int launch_row_nnz(const uint64_t* row_ptr, const int32_t* items, int64_t n_items, int64_t n_rows_per_k, int R,
+                   unsigned long long* acc, cudaStream_t s);
+
 size_t dots_tmp_bytes(int count);
 // out[i] = V_i . w for i < count (V row-major with leading dimension ld),
 // deterministic two-pass reduction; tmp needs dots_tmp_bytes(count).

@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs A)
             Real tau = static_cast<const Real*>(A.tau)[row + (int64_t)k * A.k_stride];
             Real S = Real(0), c = Real(0), S2 = Real(0), c2 = Real(0);
             for (int j = 0; j < A.F; ++j) {
-                Real v = wn[j] * exp2(-e2[j] * tau);
+                Real v = wn[j] * exp2_p(-e2[j] * tau);
                 Real yy = v - c;
                 Real t = S + yy;
                 c = (t - S) - yy;
@@ -148,15 +148,16 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs A)
                     S2 = t2;
                 }
             }
-            lk[local * A.R + k] = -smin * (double)tau + log((double)S);
-            if (A.want_tangent) lk2[local * A.R + k] = -smin * (double)tau + log((double)fmax(S2, Real(1e-37)));
+            lk[local * A.R + k] = -smin * (double)tau + (double)log_p(S);
+            if (A.want_tangent)
+                lk2[local * A.R + k] = -smin * (double)tau + (double)log_p(S2 > Real(1e-37) ? S2 : Real(1e-37));
         }
         __syncthreads();
         if (active && k == 0) {
             double m = -1e300;
             for (int r = 0; r < A.R; ++r) m = fmax(m, lk[local * A.R + r]);
             double acc = 0.0;
-            for (int r = 0; r < A.R; ++r) acc += exp(lk[local * A.R + r] - m);
+            for (int r = 0; r < A.R; ++r) acc += (double)exp_p((Real)(lk[local * A.R + r] - m));
             const double lmean = m + log(acc / (double)A.R);     // ln(Gamma/Gamma_thin)
             const double G = gthin * exp(lmean);
             const double te = -lmean;
@@ -193,7 +194,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs A)
                     const double dEdG = dx_dgamma(xn, A.nH[i], alpha, A.gc[i], G, A.y);
                     const double elas = (G > 0.0) ? G * dEdG / xn : 0.0;
                     for (int r = 0; r < A.R; ++r) {
-                        const double dlog = exp(lk2[local * A.R + r] - lmean) / (double)A.R;
+                        const double dlog = (double)exp_p((Real)(lk2[local * A.R + r] - lmean)) / (double)A.R;
                         A.ctan[row + (int64_t)r * A.k_stride] = -elas * dlog;
                     }
                     A.xeq_out[row] = xn;
@@ -426,21 +427,73 @@ int Solver::init(const urchin_bvh* bvh_, const urchin_solve_params* P_, double* 
     return URCHIN_OK;
 }
 
+// Profile mode: a start/stop event pair recorded on the launching stream
+// around each timed launch, resolved in finish().
+int Solver::begin_timed(int kind, cudaEvent_t* stop)
+{
+    *stop = nullptr;
+    if (!P.profile) return URCHIN_OK;
+    cudaEvent_t a, b;
+    URCHIN_TRY_CUDA(cudaEventCreate(&a));
+    URCHIN_TRY_CUDA(cudaEventCreate(&b));
+    events.push_back(a);
+    events.push_back(b);
+    event_kind.push_back(kind);
+    URCHIN_TRY_CUDA(cudaEventRecord(a, s));
+    *stop = b;
+    return URCHIN_OK;
+}
+
+int Solver::end_timed(cudaEvent_t stop)
+{
+    if (stop) URCHIN_TRY_CUDA(cudaEventRecord(stop, s));
+    return URCHIN_OK;
+}
+
+int Solver::timed_sweep(const SweepArgs& A, cudaStream_t st)
+{
+    cudaEvent_t stop;
+    URCHIN_TRY(begin_timed(2, &stop));
+    URCHIN_TRY(launch_sweep(A, st));
+    URCHIN_TRY(end_timed(stop));
+    stats.sweep_launches += 1;
+    return URCHIN_OK;
+}
+
+// Algorithmic bytes of one stored-segment launch over `items` (profile mode):
+// every segment of the evaluated rays read once (index and value), each
+// column written once, the x vector gathered once.
+int Solver::count_spmv(const int32_t* items, int64_t n_items)
+{
+    stats.spmv_launches += 1;
+    if (!P.profile) return URCHIN_OK;
+    const size_t vsz = f64 ? sizeof(double) : sizeof(float);
+    int64_t seg = 0;
+    if (items == list && n_items == n_act && active_nnz >= 0) {
+        seg = active_nnz;
+    } else {
+        unsigned long long* acc = misc + 9;
+        URCHIN_TRY_CUDA(cudaMemsetAsync(acc, 0, sizeof(unsigned long long), s));
+        URCHIN_TRY(launch_row_nnz(row_ptr, items, n_items, n, P.R, acc, s));
+        unsigned long long h = 0;
+        URCHIN_TRY_CUDA(cudaMemcpyAsync(&h, acc, sizeof(h), cudaMemcpyDeviceToHost, s));
+        URCHIN_TRY_CUDA(cudaStreamSynchronize(s));
+        seg = (int64_t)h;
+        if (items == list && n_items == n_act) active_nnz = seg;
+    }
+    stats.spmv_bytes += seg * (int64_t)(sizeof(int32_t) + vsz) + n_items * P.R * (int64_t)vsz + n * (int64_t)vsz;
+    return URCHIN_OK;
+}
+
 int Solver::timed_trace(TraceJob& job)
 {
     job.counter = counter;
     job.status = status;
     job.hits = hits;
-    cudaEvent_t ev[2] = {nullptr, nullptr};
-    if (P.profile) {
-        for (auto& e : ev) {
-            URCHIN_TRY_CUDA(cudaEventCreate(&e));
-            events.push_back(e);
-        }
-        URCHIN_TRY_CUDA(cudaEventRecord(ev[0], s));
-    }
+    cudaEvent_t stop;
+    URCHIN_TRY(begin_timed(0, &stop));
     URCHIN_TRY(launch_trace(job, s));
-    if (P.profile) URCHIN_TRY_CUDA(cudaEventRecord(ev[1], s));
+    URCHIN_TRY(end_timed(stop));
     stats.trace_launches += 1;
     return URCHIN_OK;
 }
@@ -485,7 +538,11 @@ int Solver::columns(const int32_t* items, int64_t n_items, int sweep0)
         A.R = P.R;
         A.precision = P.precision;
         A.out = tau;
+        cudaEvent_t stop;
+        URCHIN_TRY(begin_timed(1, &stop));
         URCHIN_TRY(launch_spmv(A, s));
+        URCHIN_TRY(end_timed(stop));
+        URCHIN_TRY(count_spmv(items, n_items));
         stats.traversals += 1;
         stats.rays += n_items * P.R;
         return URCHIN_OK;
@@ -570,7 +627,11 @@ int Solver::linear_columns(const int32_t* items, int64_t n_items, const float* z
         A.R = P.R;
         A.precision = P.precision;
         A.out = tau;
-        return launch_spmv(A, s);
+        cudaEvent_t stop;
+        URCHIN_TRY(begin_timed(1, &stop));
+        URCHIN_TRY(launch_spmv(A, s));
+        URCHIN_TRY(end_timed(stop));
+        return count_spmv(items, n_items);
     }
     TraceJob job{};
     job.bvh = bvh;
@@ -656,7 +717,7 @@ int Solver::first_sweep()
     URCHIN_TRY_CUDA(cudaMemsetAsync(misc, 0, sizeof(unsigned long long), s));
         URCHIN_TRY_CUDA(cudaMemsetAsync(misc + 7, 0, sizeof(unsigned long long), s));
     URCHIN_TRY(columns(nullptr, n, 1));
-    URCHIN_TRY(launch_sweep(sweep_args(nullptr, n, 1), s));
+    URCHIN_TRY(timed_sweep(sweep_args(nullptr, n, 1), s));
     uint32_t* cnt = reinterpret_cast<uint32_t*>(misc + 2);
     URCHIN_TRY(compact_indices(active, n, list, cnt, comp_tmp, s));
     uint32_t hc = 0;
@@ -739,7 +800,7 @@ int Solver::plain_sweeps(double stop_fraction)
             const int64_t lo = block_lo[b], m = block_lo[b + 1] - block_lo[b];
             if (m <= 0) continue;
             URCHIN_TRY(columns(list + lo, m, 0));
-            URCHIN_TRY(launch_sweep(sweep_args(list + lo, m, 0), s));
+            URCHIN_TRY(timed_sweep(sweep_args(list + lo, m, 0), s));
         }
         double m;
         unsigned st;
@@ -773,7 +834,7 @@ int Solver::evaluate(int frozen, double* V0, double* E, double* ctan, double* dt
     A.ctan = ctan;
     A.xeq_out = E;
     A.latch_frozen = frozen;
-    URCHIN_TRY(launch_sweep(A, s));
+    URCHIN_TRY(timed_sweep(A, s));
     k_residual<<<g1, 256, 0, s>>>(list, na, x, E, V0);
     URCHIN_TRY(launched());
     URCHIN_TRY(launch_dots(V0, na, 1, V0, na, dtmp, hdev, s));
@@ -970,13 +1031,15 @@ int Solver::finish(double* x_inout)
         stats.hits = (int64_t)h[0];
         stats.sphere_tests = (int64_t)h[1];
         stats.node_visits = (int64_t)h[2];
-        double total = 0.0;
+        double total[3] = {0.0, 0.0, 0.0};
         for (size_t i = 0; i + 1 < events.size(); i += 2) {
             float ms = 0.f;
             URCHIN_TRY_CUDA(cudaEventElapsedTime(&ms, events[i], events[i + 1]));
-            total += ms;
+            total[event_kind[i / 2]] += ms;
         }
-        stats.trace_s = total * 1e-3;
+        stats.trace_s = total[0] * 1e-3;
+        stats.spmv_s = total[1] * 1e-3;
+        stats.sweep_s = total[2] * 1e-3;
     }
     nk.release();
     seg.release();

@@ -78,7 +78,10 @@ struct Solver {
     void* tau = nullptr;
     void* comp_tmp = nullptr;
     unsigned long long* hits = nullptr;          // misc[3..5], counted when P.profile
-    std::vector<cudaEvent_t> events;             // start/stop pairs of each traversal
+    std::vector<cudaEvent_t> events;             // start/stop pairs of each timed launch
+    std::vector<int> event_kind;                 // 0 traversal, 1 stored-segment columns, 2 sweep
+    int begin_timed(int kind, cudaEvent_t* stop);
+    int end_timed(cudaEvent_t stop);
     // stored segments
     bool stored = false;
     float* xs32 = nullptr;                       // x in the precision of the columns (Morton)
@@ -97,6 +100,9 @@ struct Solver {
     int linear_columns(const int32_t* items, int64_t n_items, const float* z32, const double* z64,
                        float* wz32, double* wz64);
     int timed_trace(TraceJob& job);
+    int timed_sweep(const SweepArgs& A, cudaStream_t st);
+    int count_spmv(const int32_t* items, int64_t n_items);
+    int64_t active_nnz = -1;
     int evaluate(int frozen, double* V0, double* E, double* ctan, double* dtmp, double* hdev, double* maxrel,
                  double* norm, int64_t* switches);
 

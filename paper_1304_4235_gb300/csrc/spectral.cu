@@ -65,13 +65,13 @@ __device__ __forceinline__ double ray_log_rate(Real tau, const Real* e2, const R
 {
     Real S = Real(0), c = Real(0);
     for (int j = 0; j < F; ++j) {
-        Real v = wn[j] * exp2(-e2[j] * tau);
+        Real v = wn[j] * exp2_p(-e2[j] * tau);
         Real y = v - c;
         Real t = S + y;
         c = (t - S) - y;
         S = t;
     }
-    return -smin * (double)tau + log((double)S);
+    return -smin * (double)tau + (double)log_p(S);
 }
 
 template <typename Real>
@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(kGammaThreads) k_gamma(GammaJob J)
             double m = -1e300;
             for (int r = 0; r < J.R; ++r) m = fmax(m, lk[local * J.R + r]);
             double acc = 0.0;
-            for (int r = 0; r < J.R; ++r) acc += exp(lk[local * J.R + r] - m);
+            for (int r = 0; r < J.R; ++r) acc += (double)exp_p((Real)(lk[local * J.R + r] - m));
             double lmean = m + log(acc / (double)J.R);       // ln(Gamma / Gamma_thin)
             J.gamma_out[row] = gthin * exp(lmean);
             if (J.tau_eff_out) J.tau_eff_out[row] = (float)(-lmean);

@@ -6,6 +6,15 @@
 
 namespace urchin {
 
+// Precision-matched math for the spectral fold: single-precision intrinsics
+// in the FP32 path, double in the FP64 path.
+__device__ __forceinline__ float exp2_p(float x) { return exp2f(x); }
+__device__ __forceinline__ double exp2_p(double x) { return exp2(x); }
+__device__ __forceinline__ float exp_p(float x) { return expf(x); }
+__device__ __forceinline__ double exp_p(double x) { return exp(x); }
+__device__ __forceinline__ float log_p(float x) { return logf(x); }
+__device__ __forceinline__ double log_p(double x) { return log(x); }
+
 struct Rates {
     double alphaA, alphaB, gamma_c;   // cm^3 s^-1
 };

@@ -65,7 +65,9 @@ class urchin_solve_stats(C.Structure):
                 ("max_rel_dx", C.c_double), ("wall_s", C.c_double), ("converged", C.c_int),
                 ("segments_stored", C.c_int), ("hits", C.c_int64), ("trace_s", C.c_double),
                 ("trace_launches", C.c_int), ("sphere_tests", C.c_int64), ("node_visits", C.c_int64),
-                ("newton_fallbacks", C.c_int), ("newton_start", C.c_int)]
+                ("newton_fallbacks", C.c_int), ("newton_start", C.c_int), ("spmv_s", C.c_double),
+                ("spmv_launches", C.c_int), ("spmv_bytes", C.c_int64), ("sweep_s", C.c_double),
+                ("sweep_launches", C.c_int)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}

@@ -339,19 +339,22 @@ def test_newton_reaches_plain_fixed_point_lattice(lattice):
 
 @pytest.mark.parametrize("segments", [U.SEG_RECOMPUTE, U.SEG_STORE])
 def test_newton_halo_small_fp32(halo_small, segments):
-    """Newton-Krylov and plain Jacobi reach the same fixed point; Newton needs
-    far fewer evaluations of the sweep map."""
+    """Plain sweeps then Newton-Krylov at the paper's dx_tol = 1e-3: converges
+    in fewer evaluations than plain sweeps alone and lands closer to the
+    fixed point (the step test stops plain sweeps early when they contract
+    slowly)."""
     w, bvh, d = halo_small
     sg, so = spectra(w, torch)
-    xp, sp = _solve_gpu(w, bvh, d, sg, U.F32, tol=1e-6, max_iter=5000, segments=U.SEG_STORE)
-    xn, sn = _solve_gpu(w, bvh, d, sg, U.F32, tol=1e-6, max_iter=200, method=U.METHOD_NEWTON, gmres_m=30,
+    xt, st_ = _solve_gpu(w, bvh, d, sg, U.F32, tol=1e-6, max_iter=6000, segments=U.SEG_STORE)
+    xp, sp = _solve_gpu(w, bvh, d, sg, U.F32, tol=1e-3, max_iter=3000, segments=U.SEG_STORE)
+    xn, sn = _solve_gpu(w, bvh, d, sg, U.F32, tol=1e-3, max_iter=600, method=U.METHOD_NEWTON, gmres_m=20,
                         segments=segments)
-    assert sp["converged"] and sn["converged"], (sp["iterations"], sn["iterations"])
-    # both stop at max |dx|/x < 1e-6; plain creeps (contraction near 1), so
-    # its distance to the fixed point is larger than its last step
-    assert np.quantile(rel_err(xn, xp), 0.999) < 1e-3
-    assert rel_err(xn, xp).max() < 1e-2
-    assert sn["iterations"] < sp["iterations"]
+    assert st_["converged"] and sp["converged"] and sn["converged"], (sp["iterations"], sn["iterations"])
+    assert sn["newton_start"] > 0 and sn["iterations"] <= sp["iterations"]
+    dn = rel_err(xn, xt)
+    dp = rel_err(xp, xt)
+    assert np.quantile(dn, 0.999) < 2e-3
+    assert dn.max() <= dp.max()
 
 
 def test_plain_solve_latched_case_matches_oracle(halo_small):
