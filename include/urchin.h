@@ -74,6 +74,8 @@ typedef struct CUstream_st* urchin_stream_t;
 
 #define URCHIN_MAX_RAYS       192     /* HEALPix N_side <= 4                    */
 #define URCHIN_MAX_BINS      4096     /* frequency bins                         */
+#define URCHIN_NOALLOC_SCRATCH_BYTES (16u << 20)   /* fixed work array of
+                                     urchin_trace_columns_noalloc (16 MiB)    */
 
 /* ---- data -------------------------------------------------------------- */
 
@@ -172,6 +174,32 @@ URCHIN_API int64_t urchin_bvh_size(const urchin_bvh* bvh);
 URCHIN_API int urchin_trace_columns(const urchin_bvh* bvh, const double* x, const double* dirs, int R,
                          double l_ray, const int32_t* origins, int64_t n_orig,
                          int kernel, int precision, void* tau_out, urchin_stream_t stream);
+
+/* Column tracing that allocates nothing (the paper has no counterpart: this
+ * is a deployment variant of urchin_trace_columns, with the same arguments,
+ * output and errors).  It is meant for callers that cannot call cudaMalloc
+ * or cudaMallocAsync: code running inside a framework whose caching
+ * allocator owns the device memory pool, services that pin a fixed memory
+ * budget, or setups that treat any allocation on the hot path as an error.
+ * Its work space (work-queue counter, status word, directions, per-particle
+ * weights, mapped origins) lives in one file-scope device array of
+ * URCHIN_NOALLOC_SCRATCH_BYTES that every GPU loading the library keeps
+ * until the process exits; the call makes no cudaMalloc, cudaFree or other
+ * allocating call.
+ *   - Size limit: 256 + 24 R + (4 or 8) n + 4 n_orig bytes (each part
+ *     rounded up to 256) must fit in the array; larger requests return
+ *     URCHIN_ERR_ARG and leave everything untouched.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) and caches it; make that first call before any
+ *     stream capture.
+ *   - Every call shares the one array and clears what must start at zero;
+ *     calls whose work overlaps on the GPU (other streams, other host
+ *     threads) race on it and must be serialised by the caller.
+ *   - Like urchin_trace_columns it synchronises `stream` to read its status. */
+URCHIN_API int urchin_trace_columns_noalloc(const urchin_bvh* bvh, const double* x, const double* dirs, int R,
+                                            double l_ray, const int32_t* origins, int64_t n_orig,
+                                            int kernel, int precision, void* tau_out,
+                                            urchin_stream_t stream);
 
 /* Shielded rate, Eq. gamma_shld: for each of n_orig particles with R columns
  * tau[o*R + k] (float for URCHIN_F32, double for URCHIN_F64),

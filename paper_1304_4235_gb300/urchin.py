@@ -92,6 +92,8 @@ SIGNATURES = {
     "urchin_bvh_size": (C.c_int64, [_vp]),
     "urchin_trace_columns": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_double, _vp, C.c_int64,
                                        C.c_int, C.c_int, _vp, _vp]),
+    "urchin_trace_columns_noalloc": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_double, _vp, C.c_int64,
+                                               C.c_int, C.c_int, _vp, _vp]),
     "urchin_gamma": (C.c_int, [_vp, C.c_int, C.c_int64, C.c_int, C.POINTER(urchin_spectrum),
                                _vp, _vp, _vp]),
     "urchin_equilibrium": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int64, C.c_int, C.c_double,
@@ -237,6 +239,24 @@ def urchin_trace_columns(bvh: Bvh, x, dirs, l_ray: float, origins=None, kernel: 
     _check(load().urchin_trace_columns(bvh.handle, _dev(x, torch.float64), dirs.ctypes.data_as(_vp), R,
                                        float(l_ray), _dev(origins, torch.int32), n_orig, int(kernel),
                                        int(precision), _dev(out, dt), _stream(stream)))
+    return out
+
+
+def urchin_trace_columns_noalloc(bvh: Bvh, x, dirs, l_ray: float, origins=None, kernel: int = KERNEL_M4,
+                                 precision: int = F32, out=None, stream=None):
+    """Same as urchin_trace_columns, but the library allocates nothing: its
+    work space is a fixed device array (see include/urchin.h for the size
+    limit and the sharing rules).  `out` may be preallocated by the caller."""
+    import torch
+    dirs = _host(dirs).reshape(-1, 3)
+    R = dirs.shape[0]
+    n_orig = bvh.n if origins is None else int(origins.numel())
+    dt = torch.float64 if precision == F64 else torch.float32
+    if out is None:
+        out = torch.empty((n_orig, R), dtype=dt, device=x.device)
+    _check(load().urchin_trace_columns_noalloc(bvh.handle, _dev(x, torch.float64), dirs.ctypes.data_as(_vp), R,
+                                               float(l_ray), _dev(origins, torch.int32), n_orig, int(kernel),
+                                               int(precision), _dev(out, dt), _stream(stream)))
     return out
 
 
