@@ -109,6 +109,11 @@ __device__ void sweep_spectrum(const double* s, const double* w, int F, Real* e2
 // One sweep's spectral fold + equilibrium update (see file comment).  With
 // want_tangent, also stores per ray c_tk = (1/E) dE/dGamma dGamma/dtau_k for
 // the Newton tangent (in log-safe form).
+//
+// Threads (local, k) fold ray k of particle `local` through the spectrum in
+// the columns' precision; the per-particle tail (the log-sum-exp over rays,
+// then the FP64 equilibrium) runs with one thread per particle packed into
+// the first lanes, so the FP64 work is not spread over mostly idle warps.
 template <typename Real>
 __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs A)
 {
@@ -116,59 +121,63 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs A)
     Real* e2 = reinterpret_cast<Real*>(smem_raw);
     Real* wn = e2 + A.F;
     Real* sj = wn + A.F;
-    double* lk = reinterpret_cast<double*>(smem_raw + ((3 * (size_t)A.F * sizeof(Real) + 15) & ~size_t(15)));
-    double* lk2 = lk + kSweepThreads;
+    Real* lk = reinterpret_cast<Real*>(smem_raw + ((3 * (size_t)A.F * sizeof(Real) + 15) & ~size_t(15)));
+    Real* lk2 = lk + kSweepThreads;
     __shared__ double sh[2];
     sweep_spectrum<Real>(A.s, A.w, A.F, e2, A.want_tangent ? sj : nullptr, wn, sh);
     const int rows_per_block = kSweepThreads / A.R;
     const int local = threadIdx.x / A.R;
     const int k = threadIdx.x % A.R;
-    const double gthin = sh[0], smin = sh[1];
+    const double gthin = sh[0];
+    const Real smin = (Real)sh[1];
     double my_max = 0.0;
     unsigned long long my_above = 0, my_switch = 0;
     unsigned err = 0;
     for (int64_t row0 = (int64_t)blockIdx.x * rows_per_block; row0 < A.n_items;
          row0 += (int64_t)gridDim.x * rows_per_block) {
         const int64_t row = row0 + local;
-        const bool active = local < rows_per_block && row < A.n_items;
-        if (active) {
-            Real tau = static_cast<const Real*>(A.tau)[row + (int64_t)k * A.k_stride];
+        if (local < rows_per_block && row < A.n_items) {
+            const Real tau = static_cast<const Real*>(A.tau)[row + (int64_t)k * A.k_stride];
             Real S = Real(0), c = Real(0), S2 = Real(0), c2 = Real(0);
             for (int j = 0; j < A.F; ++j) {
-                Real v = wn[j] * exp2_p(-e2[j] * tau);
-                Real yy = v - c;
-                Real t = S + yy;
+                const Real v = wn[j] * exp2_p(-e2[j] * tau);
+                const Real yy = v - c;
+                const Real t = S + yy;
                 c = (t - S) - yy;
                 S = t;
                 if (A.want_tangent) {
-                    Real v2 = v * sj[j];
-                    Real y2 = v2 - c2;
-                    Real t2 = S2 + y2;
+                    const Real v2 = v * sj[j];
+                    const Real y2 = v2 - c2;
+                    const Real t2 = S2 + y2;
                     c2 = (t2 - S2) - y2;
                     S2 = t2;
                 }
             }
-            lk[local * A.R + k] = -smin * (double)tau + (double)log_p(S);
-            if (A.want_tangent)
-                lk2[local * A.R + k] = -smin * (double)tau + (double)log_p(S2 > Real(1e-37) ? S2 : Real(1e-37));
+            // ln(Gamma_k / Gamma_thin) = -s_min tau_k + ln S_k
+            lk[local * A.R + k] = -smin * tau + log_p(S);
+            if (A.want_tangent) lk2[local * A.R + k] = -smin * tau + log_p(S2 > Real(1e-37) ? S2 : Real(1e-37));
         }
         __syncthreads();
-        if (active && k == 0) {
-            double m = -1e300;
-            for (int r = 0; r < A.R; ++r) m = fmax(m, lk[local * A.R + r]);
-            double acc = 0.0;
-            for (int r = 0; r < A.R; ++r) acc += (double)exp_p((Real)(lk[local * A.R + r] - m));
-            const double lmean = m + log(acc / (double)A.R);     // ln(Gamma/Gamma_thin)
+        const int p = threadIdx.x;
+        const int64_t prow = row0 + p;
+        if (p < rows_per_block && prow < A.n_items) {
+            const Real* l = lk + p * A.R;
+            Real m = l[0];
+            for (int r = 1; r < A.R; ++r) m = m > l[r] ? m : l[r];
+            Real acc = Real(0);
+            for (int r = 0; r < A.R; ++r) acc += exp_p(l[r] - m);
+            const Real lmean_r = m + log_p(acc / (Real)A.R);     // ln(Gamma/Gamma_thin)
+            const double lmean = (double)lmean_r;
             const double G = gthin * exp(lmean);
             const double te = -lmean;
-            const int32_t i = A.items ? A.items[row] : (int32_t)row;
+            const int32_t i = A.items ? A.items[prow] : (int32_t)prow;
             bool update = true;
             if (A.sweep0) {
                 update = !(te < A.tau_skip);
                 A.active[i] = update ? 1 : 0;
             }
-            if (A.gamma_out) A.gamma_out[row] = G;
-            if (A.tau_eff_out) A.tau_eff_out[row] = (float)te;
+            if (A.gamma_out) A.gamma_out[prow] = G;
+            if (A.tau_eff_out) A.tau_eff_out[prow] = (float)te;
             if (update) {
                 // case B iff tau_eff >= 1, latched once reached (see urchin_solve)
                 bool caseB = A.case_rule == URCHIN_CASE_B;
@@ -193,11 +202,12 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs A)
                     // elasticity Gamma dE/dGamma / E and per-ray dGamma/dtau_k / Gamma
                     const double dEdG = dx_dgamma(xn, A.nH[i], alpha, A.gc[i], G, A.y);
                     const double elas = (G > 0.0) ? G * dEdG / xn : 0.0;
+                    const Real* l2 = lk2 + p * A.R;
                     for (int r = 0; r < A.R; ++r) {
-                        const double dlog = (double)exp_p((Real)(lk2[local * A.R + r] - lmean)) / (double)A.R;
-                        A.ctan[row + (int64_t)r * A.k_stride] = -elas * dlog;
+                        const double dlog = (double)exp_p(l2[r] - lmean_r) / (double)A.R;
+                        A.ctan[prow + (int64_t)r * A.k_stride] = -elas * dlog;
                     }
-                    A.xeq_out[row] = xn;
+                    A.xeq_out[prow] = xn;
                 } else {
                     A.x[i] = xn;
                     const double wv = A.A64[i] * xn;
@@ -337,7 +347,7 @@ int launch_sweep(const SweepArgs& A, cudaStream_t s)
 {
     if (A.n_items <= 0) return URCHIN_OK;
     const size_t rsz = A.precision == URCHIN_F64 ? sizeof(double) : sizeof(float);
-    size_t smem = ((3 * (size_t)A.F * rsz + 15) & ~size_t(15)) + 2 * sizeof(double) * kSweepThreads;
+    size_t smem = ((3 * (size_t)A.F * rsz + 15) & ~size_t(15)) + 2 * rsz * kSweepThreads;
     const void* fn = A.precision == URCHIN_F64 ? (const void*)k_sweep<double> : (const void*)k_sweep<float>;
     if (smem > 48 * 1024)
         URCHIN_TRY_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

@@ -61,7 +61,7 @@ __device__ void load_spectrum(const double* s, const double* w, int F, Real* e2,
 }
 
 template <typename Real>
-__device__ __forceinline__ double ray_log_rate(Real tau, const Real* e2, const Real* wn, int F, double smin)
+__device__ __forceinline__ Real ray_log_rate(Real tau, const Real* e2, const Real* wn, int F, Real smin)
 {
     Real S = Real(0), c = Real(0);
     for (int j = 0; j < F; ++j) {
@@ -71,39 +71,44 @@ __device__ __forceinline__ double ray_log_rate(Real tau, const Real* e2, const R
         c = (t - S) - y;
         S = t;
     }
-    return -smin * (double)tau + (double)log_p(S);
+    return -smin * tau + log_p(S);
 }
 
+// Threads (local, k) fold ray k of row `local`; the per-row log-sum-exp runs
+// with one thread per row packed into the first lanes.
 template <typename Real>
 __global__ void __launch_bounds__(kGammaThreads) k_gamma(GammaJob J)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Real* e2 = reinterpret_cast<Real*>(smem_raw);
     Real* wn = e2 + J.F;
-    double* lk = reinterpret_cast<double*>(smem_raw + ((2 * (size_t)J.F * sizeof(Real) + 15) & ~size_t(15)));
+    Real* lk = reinterpret_cast<Real*>(smem_raw + ((2 * (size_t)J.F * sizeof(Real) + 15) & ~size_t(15)));
     __shared__ double sh[2];
     load_spectrum<Real>(J.s, J.w, J.F, e2, wn, sh);
     const int rows_per_block = kGammaThreads / J.R;
     const int local = threadIdx.x / J.R;
     const int k = threadIdx.x % J.R;
-    const double gthin = sh[0], smin = sh[1];
+    const double gthin = sh[0];
+    const Real smin = (Real)sh[1];
     for (int64_t row0 = (int64_t)blockIdx.x * rows_per_block; row0 < J.n_rows;
          row0 += (int64_t)gridDim.x * rows_per_block) {
-        int64_t row = row0 + local;
-        bool active = local < rows_per_block && row < J.n_rows;
-        if (active) {
-            Real tau = static_cast<const Real*>(J.tau)[row * J.row_stride + (int64_t)k * J.k_stride];
+        const int64_t row = row0 + local;
+        if (local < rows_per_block && row < J.n_rows) {
+            const Real tau = static_cast<const Real*>(J.tau)[row * J.row_stride + (int64_t)k * J.k_stride];
             lk[local * J.R + k] = ray_log_rate<Real>(tau, e2, wn, J.F, smin);
         }
         __syncthreads();
-        if (active && k == 0) {
-            double m = -1e300;
-            for (int r = 0; r < J.R; ++r) m = fmax(m, lk[local * J.R + r]);
-            double acc = 0.0;
-            for (int r = 0; r < J.R; ++r) acc += (double)exp_p((Real)(lk[local * J.R + r] - m));
-            double lmean = m + log(acc / (double)J.R);       // ln(Gamma / Gamma_thin)
-            J.gamma_out[row] = gthin * exp(lmean);
-            if (J.tau_eff_out) J.tau_eff_out[row] = (float)(-lmean);
+        const int p = threadIdx.x;
+        const int64_t prow = row0 + p;
+        if (p < rows_per_block && prow < J.n_rows) {
+            const Real* l = lk + p * J.R;
+            Real m = l[0];
+            for (int r = 1; r < J.R; ++r) m = m > l[r] ? m : l[r];
+            Real acc = Real(0);
+            for (int r = 0; r < J.R; ++r) acc += exp_p(l[r] - m);
+            const double lmean = (double)(m + log_p(acc / (Real)J.R));    // ln(Gamma / Gamma_thin)
+            J.gamma_out[prow] = gthin * exp(lmean);
+            if (J.tau_eff_out) J.tau_eff_out[prow] = (float)(-lmean);
         }
         __syncthreads();
     }
@@ -112,7 +117,7 @@ __global__ void __launch_bounds__(kGammaThreads) k_gamma(GammaJob J)
 template <typename Real>
 int launch_gamma_t(const GammaJob& J, cudaStream_t s)
 {
-    size_t smem = ((2 * (size_t)J.F * sizeof(Real) + 15) & ~size_t(15)) + sizeof(double) * kGammaThreads;
+    size_t smem = ((2 * (size_t)J.F * sizeof(Real) + 15) & ~size_t(15)) + sizeof(Real) * kGammaThreads;
     auto fn = k_gamma<Real>;
     if (smem > 48 * 1024)
         URCHIN_TRY_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
