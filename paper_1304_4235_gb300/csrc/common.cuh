@@ -170,8 +170,6 @@ struct TraceJob {
     unsigned int* counter;        // one device uint (work queue), zeroed here
     unsigned int* status;         // one device uint: error flags (may be NULL)
     unsigned long long* hits;     // chord evaluations (may be NULL)
-    const int32_t* order;         // [R * n_items] or NULL: processing order of the rays of
-                                  // direction k (item indices), see build_ray_order
     int mode;                     // 0: columns, 1: count hits per ray, 2: fill segments (+ columns)
     uint32_t* counts;             // mode 1: [R * n_items], index k * n_items + item
     const uint64_t* row_ptr;      // mode 2: [R * n_items + 1] offsets of each ray's segments
@@ -179,14 +177,6 @@ struct TraceJob {
     void* seg_val;                // mode 2: A_j * chord integral per segment (precision's type)
 };
 int launch_trace(const TraceJob& job, cudaStream_t s);
-
-// Coherent processing order of the rays: for each direction k, the items
-// sorted by the 2-D Morton code of their origin projected onto the plane
-// normal to n_k, so that a warp's rays are nearly coincident parallel lines.
-// order_out [R * n_items]; tmp needs ray_order_tmp_bytes(n_items).
-size_t ray_order_tmp_bytes(int64_t n_items);
-int build_ray_order(const urchin_bvh* bvh, const int32_t* items, int64_t n_items, const double* dirs_host, int R,
-                    int32_t* order_out, void* tmp, cudaStream_t s);
 
 // w = A * x gathered into Morton order: w[s] = A[s] * x[perm[s]]
 int launch_weights(const urchin_bvh* bvh, const double* x_orig, float* w32, double* w64,

@@ -77,11 +77,6 @@ struct Solver {
     int32_t* list = nullptr;
     void* tau = nullptr;
     void* comp_tmp = nullptr;
-    int32_t* ray_order = nullptr;                // [R * n] coherent ray order (see build_ray_order)
-    const int32_t* order_items = nullptr;        // items list the order was built for
-    int64_t order_n = -1;
-    void* order_tmp = nullptr;
-    const int32_t* order_for(const int32_t* items, int64_t n_items);
     unsigned long long* hits = nullptr;          // misc[3..5], counted when P.profile
     std::vector<cudaEvent_t> events;             // start/stop pairs of each timed launch
     std::vector<int> event_kind;                 // 0 traversal, 1 stored-segment columns, 2 sweep
@@ -124,7 +119,6 @@ struct Solver {
     int newton();
     int run() { return P.method == URCHIN_METHOD_NEWTON ? newton() : plain(); }
     int finish(double* x_inout);
-    int tangent(const double* v_orig, double* E_orig, double* dlnE_orig);
 };
 
 }  // namespace urchin

@@ -31,7 +31,6 @@ struct TraceParams {
     int R;
     double l_ray;
     const int32_t* items;
-    const int32_t* order;
     int64_t n_items;
     int64_t row_stride, k_stride;
     const int32_t* out_row;
@@ -457,9 +456,8 @@ __global__ void __launch_bounds__(256) k_trace(TraceParams P)
         if ((unsigned long long)task >= total) break;
         const int k = (int)(task / P.n_chunks);
         const int64_t chunk = (int64_t)(task % P.n_chunks);
-        const int64_t slot = chunk * 32 + lane;
-        if (slot < P.n_items) {
-            const int64_t item = P.order ? (int64_t)P.order[(int64_t)k * P.n_items + slot] : slot;
+        const int64_t item = chunk * 32 + lane;
+        if (item < P.n_items) {
             int32_t org = P.items ? P.items[item] : (int32_t)item;
             float4 o = __ldg(P.xyzh + org);
             Real dx = Real(s_dirs[3 * k]), dy = Real(s_dirs[3 * k + 1]), dz = Real(s_dirs[3 * k + 2]);
@@ -580,7 +578,6 @@ int launch_trace(const TraceJob& job, cudaStream_t s)
     P.R = job.R;
     P.l_ray = job.l_ray;
     P.items = job.items;
-    P.order = job.order;
     P.n_items = job.n_items;
     P.row_stride = job.row_stride;
     P.k_stride = job.k_stride;
@@ -650,73 +647,6 @@ __global__ void k_map_origins(const int32_t* __restrict__ origins, const int32_t
     }
 }
 
-__device__ __forceinline__ uint32_t spread16(uint32_t v)
-{
-    v &= 0xffffu;
-    v = (v | (v << 8)) & 0x00ff00ffu;
-    v = (v | (v << 4)) & 0x0f0f0f0fu;
-    v = (v | (v << 2)) & 0x33333333u;
-    v = (v | (v << 1)) & 0x55555555u;
-    return v;
-}
-
-// key = 2-D Morton code of the origin projected on (e1, e2), value = item
-__global__ void k_ray_keys(const float4* __restrict__ xyzh, const int32_t* __restrict__ items, int64_t n_items,
-                           double3 e1, double3 e2, double lo1, double lo2, double inv1, double inv2,
-                           uint32_t* keys, int32_t* vals)
-{
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n_items;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        const float4 p = xyzh[items ? items[t] : t];
-        const double a = (p.x * e1.x + p.y * e1.y + p.z * e1.z - lo1) * inv1;
-        const double b = (p.x * e2.x + p.y * e2.y + p.z * e2.z - lo2) * inv2;
-        const uint32_t qa = (uint32_t)fmin(fmax(a * 65536.0, 0.0), 65535.0);
-        const uint32_t qb = (uint32_t)fmin(fmax(b * 65536.0, 0.0), 65535.0);
-        keys[t] = (spread16(qa) << 1) | spread16(qb);
-        vals[t] = (int32_t)t;
-    }
-}
-
-size_t ray_order_tmp_bytes(int64_t n_items)
-{
-    return (((size_t)n_items * 4 + 255) & ~size_t(255)) + radix_tmp_bytes(n_items);
-}
-
-int build_ray_order(const urchin_bvh* bvh, const int32_t* items, int64_t n_items, const double* dirs, int R,
-                    int32_t* order_out, void* tmp, cudaStream_t s)
-{
-    if (n_items <= 0) return URCHIN_OK;
-    uint32_t* keys = static_cast<uint32_t*>(tmp);
-    void* rt = static_cast<char*>(tmp) + (((size_t)n_items * 4 + 255) & ~size_t(255));
-    const unsigned grid = (unsigned)std::min<int64_t>((n_items + 255) / 256, 4096);
-    for (int k = 0; k < R; ++k) {
-        const double* d = dirs + 3 * k;
-        // orthonormal e1, e2 perpendicular to d
-        double ax = std::fabs(d[0]) < 0.9 ? 1.0 : 0.0, ay = ax == 1.0 ? 0.0 : 1.0, az = 0.0;
-        double e1x = ay * d[2] - az * d[1], e1y = az * d[0] - ax * d[2], e1z = ax * d[1] - ay * d[0];
-        const double l1 = std::sqrt(e1x * e1x + e1y * e1y + e1z * e1z);
-        e1x /= l1; e1y /= l1; e1z /= l1;
-        const double e2x = d[1] * e1z - d[2] * e1y, e2y = d[2] * e1x - d[0] * e1z, e2z = d[0] * e1y - d[1] * e1x;
-        // projected extent of the root box
-        double lo1 = 1e300, hi1 = -1e300, lo2 = 1e300, hi2 = -1e300;
-        for (int c = 0; c < 8; ++c) {
-            const double px = (c & 1) ? bvh->root_hi[0] : bvh->root_lo[0];
-            const double py = (c & 2) ? bvh->root_hi[1] : bvh->root_lo[1];
-            const double pz = (c & 4) ? bvh->root_hi[2] : bvh->root_lo[2];
-            const double a = px * e1x + py * e1y + pz * e1z, b = px * e2x + py * e2y + pz * e2z;
-            lo1 = std::min(lo1, a); hi1 = std::max(hi1, a);
-            lo2 = std::min(lo2, b); hi2 = std::max(hi2, b);
-        }
-        const double inv1 = hi1 > lo1 ? 1.0 / (hi1 - lo1) : 0.0, inv2 = hi2 > lo2 ? 1.0 / (hi2 - lo2) : 0.0;
-        int32_t* vals = order_out + (int64_t)k * n_items;
-        k_ray_keys<<<grid, 256, 0, s>>>(bvh->xyzh, items, n_items, make_double3(e1x, e1y, e1z),
-                                        make_double3(e2x, e2y, e2z), lo1, lo2, inv1, inv2, keys, vals);
-        URCHIN_TRY(launched());
-        URCHIN_TRY(radix_sort_pairs(keys, vals, n_items, 32, rt, s));
-    }
-    return URCHIN_OK;
-}
-
 }  // namespace urchin
 
 extern "C" int urchin_trace_columns(const urchin_bvh* bvh, const double* x, const double* dirs, int R,
@@ -754,11 +684,6 @@ extern "C" int urchin_trace_columns(const urchin_bvh* bvh, const double* x, cons
     size_t o_dirs = lay.take(sizeof(double) * 3 * (size_t)R);
     size_t o_w = lay.take((f64 ? sizeof(double) : sizeof(float)) * (size_t)n);
     size_t o_items = lay.take(origins ? sizeof(int32_t) * (size_t)n_orig : 0);
-    // large requests: process each direction's rays in projected 2-D Morton
-    // order (outputs are unchanged, warps get nearly coincident rays)
-    const bool ordered = n_orig >= 4096;
-    size_t o_order = lay.take(ordered ? sizeof(int32_t) * (size_t)n_orig * R : 0);
-    size_t o_otmp = lay.take(ordered ? ray_order_tmp_bytes(n_orig) : 0);
     Scratch scr;
     URCHIN_TRY(scr.alloc(lay.bytes, s));
     unsigned* ctr = scr.at<unsigned>(o_ctr);
@@ -792,10 +717,6 @@ extern "C" int urchin_trace_columns(const urchin_bvh* bvh, const double* x, cons
         // all particles, in Morton order for coherence; row = original index
         job.items = nullptr;
         job.out_row = bvh->perm;
-    }
-    if (ordered) {
-        URCHIN_TRY(build_ray_order(bvh, job.items, n_orig, dirs, R, scr.at<int32_t>(o_order), scr.at<void>(o_otmp), s));
-        job.order = scr.at<int32_t>(o_order);
     }
     URCHIN_TRY(launch_trace(job, s));
     unsigned st = 0;
