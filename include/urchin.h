@@ -305,6 +305,21 @@ typedef struct {
 URCHIN_API int urchin_solve(const urchin_bvh* bvh, const urchin_solve_params* params,
                  double* x_inout, urchin_solve_stats* stats, urchin_stream_t stream);
 
+/* Tangent of the sweep map that Newton-Krylov linearises (Sec. 4 iteration,
+ * Eq. colden, Eq. gamma_shld, Eq. xroots): for the map x -> E(Gamma(x)) of
+ * one sweep over all particles, with each particle's recombination case
+ * taken from its tau_eff at x (params->case_rule, no latch), writes
+ *   E_out[i]    = E_i(x)                                   (device, may be NULL)
+ *   dlnE_out[i] = sum_j (d ln E_i / d ln x_j) v_j          (device)
+ *              = sum_k c_ik dtau_ik,  dtau = columns of the vector x v,
+ *     c_ik = (1/E_i) dE_i/dGamma_i dGamma_i/dtau_ik,
+ * i.e. the directional derivative in ln x.  x and v are device [n] double in
+ * the original particle order.  Uses params' R, dirs, l_ray, spectrum, nH, T,
+ * y, kernel, precision and case_rule; the columns are traced (no stored
+ * segments).  Synchronises `stream`.  Errors: as urchin_solve. */
+URCHIN_API int urchin_tangent(const urchin_bvh* bvh, const urchin_solve_params* params, const double* x,
+                              const double* v, double* E_out, double* dlnE_out, urchin_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

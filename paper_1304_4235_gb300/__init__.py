@@ -3,6 +3,6 @@
 and its thin Python binding (urchin.py)."""
 from .urchin import (  # noqa: F401
     Bvh, UrchinError, load, library_path, urchin_build_bvh, urchin_equilibrium, urchin_gamma,
-    urchin_healpix_dirs, urchin_kernel_launches, urchin_solve, urchin_spectrum_weights, urchin_trace_columns, urchin_trace_columns_noalloc,
+    urchin_healpix_dirs, urchin_kernel_launches, urchin_solve, urchin_tangent, urchin_spectrum_weights, urchin_trace_columns, urchin_trace_columns_noalloc,
     urchin_version,
 )

@@ -341,6 +341,30 @@ __global__ void k_block_keys(const int32_t* __restrict__ list, const uint32_t* _
     }
 }
 
+__global__ void k_iota(int32_t* out, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (int32_t)i;
+}
+
+// v_m[s] = v[perm[s]] (original -> Morton order)
+__global__ void k_to_morton(const int32_t* __restrict__ perm, const double* __restrict__ v, int64_t n, double* vm)
+{
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x)
+        vm[s] = v[perm[s]];
+}
+
+// out[perm[s]] = (v_m[s] - jv[s]) and E_out[perm[s]] = E[s]
+__global__ void k_tangent_out(const int32_t* __restrict__ perm, const double* __restrict__ vm,
+                              const double* __restrict__ jv, const double* __restrict__ E, int64_t n,
+                              double* dlnE_out, double* E_out)
+{
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
+        dlnE_out[perm[s]] = vm[s] - jv[s];
+        if (E_out) E_out[perm[s]] = E[s];
+    }
+}
+
 }  // namespace
 
 int launch_sweep(const SweepArgs& A, cudaStream_t s)
@@ -1029,6 +1053,57 @@ int Solver::newton()
     return URCHIN_OK;
 }
 
+// Sweep-map tangent at the current x (see urchin_tangent): one traversal for
+// E and the factors c_ik, one for the columns of x v.
+int Solver::tangent(const double* v_orig, double* E_orig, double* dlnE_orig)
+{
+    const size_t rsz = f64 ? sizeof(double) : sizeof(float);
+    Layout lay;
+    size_t o_E = lay.take(sizeof(double) * (size_t)n);
+    size_t o_c = lay.take(sizeof(double) * (size_t)n * P.R);
+    size_t o_v = lay.take(sizeof(double) * (size_t)n);
+    size_t o_jv = lay.take(sizeof(double) * (size_t)n);
+    size_t o_z = lay.take(rsz * (size_t)n);
+    size_t o_wz = lay.take(rsz * (size_t)n);
+    URCHIN_TRY(nk.alloc(lay.bytes, s));
+    double* E = nk.at<double>(o_E);
+    double* ctan = nk.at<double>(o_c);
+    double* vm = nk.at<double>(o_v);
+    double* jv = nk.at<double>(o_jv);
+    float* z32 = f64 ? nullptr : nk.at<float>(o_z);
+    double* z64 = f64 ? nk.at<double>(o_z) : nullptr;
+    float* wz32 = f64 ? nullptr : nk.at<float>(o_wz);
+    double* wz64 = f64 ? nk.at<double>(o_wz) : nullptr;
+    const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 4096));
+    k_iota<<<g, 256, 0, s>>>(list, n);
+    URCHIN_TRY(launched());
+    n_act = n;
+    URCHIN_TRY(trace(list, n, w32, w64));
+    URCHIN_TRY_CUDA(cudaMemsetAsync(misc, 0, sizeof(unsigned long long), s));
+    SweepArgs A = sweep_args(list, n, 0);
+    A.want_tangent = 1;
+    A.ctan = ctan;
+    A.xeq_out = E;
+    URCHIN_TRY(timed_sweep(A, s));
+    k_to_morton<<<g, 256, 0, s>>>(bvh->perm, v_orig, n, vm);
+    URCHIN_TRY(launched());
+    k_tangent_vector<<<g, 256, 0, s>>>(list, n, vm, x, bvh->A64, z32, z64, wz32, wz64);
+    URCHIN_TRY(launched());
+    URCHIN_TRY(linear_columns(list, n, z32, z64, wz32, wz64));
+    if (f64) k_jv<double><<<g, 256, 0, s>>>(vm, ctan, static_cast<const double*>(tau), n, P.R, jv);
+    else k_jv<float><<<g, 256, 0, s>>>(vm, ctan, static_cast<const float*>(tau), n, P.R, jv);
+    URCHIN_TRY(launched());
+    k_tangent_out<<<g, 256, 0, s>>>(bvh->perm, vm, jv, E, n, dlnE_orig, E_orig);
+    URCHIN_TRY(launched());
+    double m;
+    unsigned st;
+    URCHIN_TRY(read_scalars(&m, &st));
+    nk.release();
+    scr.release();
+    URCHIN_TRY_CUDA(cudaStreamSynchronize(s));
+    return URCHIN_OK;
+}
+
 int Solver::finish(double* x_inout)
 {
     unsigned grid = (unsigned)std::min<int64_t>((n + 255) / 256, 4096);
@@ -1064,6 +1139,45 @@ Solver::~Solver()
 }
 
 }  // namespace urchin
+
+extern "C" int urchin_tangent(const urchin_bvh* bvh, const urchin_solve_params* P, const double* x,
+                              const double* v, double* E_out, double* dlnE_out, urchin_stream_t stream)
+{
+    using namespace urchin;
+    clear_error();
+    if (!bvh || !P || !x || !v || !dlnE_out)
+        return set_error(URCHIN_ERR_ARG, "urchin_tangent: NULL bvh, params, x, v or dlnE_out");
+    if (P->R < 1 || P->R > URCHIN_MAX_RAYS || !P->dirs)
+        return set_error(URCHIN_ERR_ARG, "urchin_tangent: bad ray set (R = %d)", P->R);
+    for (int k = 0; k < P->R; ++k) {
+        const double* d = P->dirs + 3 * k;
+        double nn = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        if (!std::isfinite(nn) || std::fabs(nn - 1.0) > 1e-6)
+            return set_error(URCHIN_ERR_ARG, "urchin_tangent: direction %d is not a unit vector", k);
+    }
+    if (!(P->l_ray >= 0.0) || !std::isfinite(P->l_ray)) return set_error(URCHIN_ERR_ARG, "urchin_tangent: bad l_ray");
+    if (P->spectrum.F < 1 || P->spectrum.F > URCHIN_MAX_BINS || !P->spectrum.s || !P->spectrum.w)
+        return set_error(URCHIN_ERR_ARG, "urchin_tangent: bad spectrum");
+    if (!P->nH || !P->T || !(P->y >= 0.0)) return set_error(URCHIN_ERR_ARG, "urchin_tangent: bad nH, T or y");
+    if (P->kernel != URCHIN_KERNEL_M4 && P->kernel != URCHIN_KERNEL_GT)
+        return set_error(URCHIN_ERR_ARG, "urchin_tangent: unknown kernel");
+    if (P->precision != URCHIN_F32 && P->precision != URCHIN_F64)
+        return set_error(URCHIN_ERR_ARG, "urchin_tangent: unknown precision");
+    if (P->case_rule != URCHIN_CASE_A && P->case_rule != URCHIN_CASE_B && P->case_rule != URCHIN_CASE_AUTO)
+        return set_error(URCHIN_ERR_ARG, "urchin_tangent: unknown case_rule");
+    urchin_solve_params Q = *P;
+    Q.warm_start = 1;
+    Q.segments = URCHIN_SEG_RECOMPUTE;
+    Q.profile = 0;
+    Q.tol = Q.tol > 0.0 ? Q.tol : 1e-3;
+    Q.max_iter = 1;
+    cudaStream_t s = (cudaStream_t)stream;
+    Solver S;
+    int st = S.init(bvh, &Q, const_cast<double*>(x), s);
+    if (st == URCHIN_OK) st = S.tangent(v, E_out, dlnE_out);
+    if (st != URCHIN_OK) cudaStreamSynchronize(s);
+    return st;
+}
 
 extern "C" int urchin_solve(const urchin_bvh* bvh, const urchin_solve_params* P, double* x_inout,
                             urchin_solve_stats* stats, urchin_stream_t stream)

@@ -119,6 +119,7 @@ struct Solver {
     int newton();
     int run() { return P.method == URCHIN_METHOD_NEWTON ? newton() : plain(); }
     int finish(double* x_inout);
+    int tangent(const double* v_orig, double* E_orig, double* dlnE_orig);
 };
 
 }  // namespace urchin

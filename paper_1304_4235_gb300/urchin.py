@@ -100,6 +100,7 @@ SIGNATURES = {
                                      _vp, _vp]),
     "urchin_solve": (C.c_int, [_vp, C.POINTER(urchin_solve_params), _vp,
                                C.POINTER(urchin_solve_stats), _vp]),
+    "urchin_tangent": (C.c_int, [_vp, C.POINTER(urchin_solve_params), _vp, _vp, _vp, _vp, _vp]),
 }
 
 _lib = None
@@ -334,3 +335,30 @@ def urchin_solve(bvh: Bvh, dirs, l_ray: float, s, w, nH, T, x=None, *, y: float 
         return x, out
     _check(rc)
     return x, out
+
+
+def urchin_tangent(bvh: Bvh, dirs, l_ray: float, s, w, nH, T, x, v, *, y: float = 0.0,
+                   kernel: int = KERNEL_M4, precision: int = F32, case_rule: int = CASE_AUTO, stream=None):
+    """(E(x), d ln E / d ln x . v) of one sweep over all particles (float64
+    CUDA tensors, original order)."""
+    import torch
+    dirs = _host(dirs).reshape(-1, 3)
+    P = urchin_solve_params()
+    P.R = dirs.shape[0]
+    P.dirs = dirs.ctypes.data_as(_vp)
+    P.l_ray = float(l_ray)
+    P.spectrum = urchin_spectrum(int(s.numel()), _dev(s, torch.float64), _dev(w, torch.float64))
+    P.nH = _dev(nH, torch.float64)
+    P.T = _dev(T, torch.float64)
+    P.y = float(y)
+    P.tol = 1e-3
+    P.max_iter = 1
+    P.kernel = int(kernel)
+    P.precision = int(precision)
+    P.case_rule = int(case_rule)
+    E = torch.empty(bvh.n, dtype=torch.float64, device=x.device)
+    dl = torch.empty(bvh.n, dtype=torch.float64, device=x.device)
+    _check(load().urchin_tangent(bvh.handle, C.byref(P), _dev(x, torch.float64), _dev(v, torch.float64),
+                                 _dev(E), _dev(dl), _stream(stream)))
+    return E, dl
+

@@ -386,3 +386,68 @@ def test_density_ordered_blocks_converge_faster(halo_small):
     xb, sb = _solve_gpu(w, bvh, d, sg, U.F32, tol=1e-3, max_iter=3000, segments=U.SEG_STORE, blocks=32)
     assert sj["converged"] and sb["converged"]
     assert sb["iterations"] < sj["iterations"]
+
+
+# --------------------------------------------------------------------------
+# tangent of the sweep map (what Newton-Krylov linearises)
+# --------------------------------------------------------------------------
+def _oracle_lnE(w, so, x, case_rule):
+    g, te = O.gamma(O.columns(w, x, O.healpix(w.nside)), so[0], so[1])
+    cb = np.full(w.n, case_rule == U.CASE_B)
+    return np.log(O.xeq(g, w.nH, w.T, 0.0, cb))
+
+
+@pytest.mark.parametrize("case_rule", [U.CASE_A, U.CASE_B])
+def test_tangent_matches_finite_differences_fp64(lattice, case_rule):
+    """d ln E / d ln x . v from the library against central differences of the
+    library's own sweep map and of the FP64 oracle's (step 1e-4 in ln x)."""
+    w, bvh, d = lattice
+    sg, so = spectra(w, torch)
+    dirs = U.urchin_healpix_dirs(1)
+    # a partly shielded state: x_thin scaled by factors 0.5-2 (the lattice
+    # turns fully neutral within two sweeps, where every derivative vanishes)
+    rng = np.random.default_rng(31)
+    x = O.xeq(so[1].sum(), w.nH, w.T, 0.0, case_rule == U.CASE_B) * rng.uniform(0.5, 2.0, w.n)
+    v = rng.uniform(-1, 1, w.n)
+    eps = 1e-4
+    tg = lambda xx: U.urchin_tangent(bvh, dirs, w.l_ray, sg[0], sg[1], d["nH"], d["T"],
+                                     torch.from_numpy(xx).cuda(), torch.from_numpy(v).cuda(),
+                                     precision=U.F64, case_rule=case_rule)
+    E0, dl = tg(x)
+    dl = dl.cpu().numpy()
+    Ep, _ = tg(x * np.exp(eps * v))
+    Em, _ = tg(x * np.exp(-eps * v))
+    fd = (np.log(Ep.cpu().numpy()) - np.log(Em.cpu().numpy())) / (2 * eps)
+    scale = np.abs(fd).max()
+    assert scale > 1e-3
+    assert np.all(np.abs(dl - fd) <= 1e-6 * scale)
+    fdo = (_oracle_lnE(w, so, x * np.exp(eps * v), case_rule) - _oracle_lnE(w, so, x * np.exp(-eps * v), case_rule)) / (2 * eps)
+    assert np.all(np.abs(dl - fdo) <= 1e-6 * scale)
+    xe = O.xeq(O.gamma(O.columns(w, x, O.healpix(1)), so[0], so[1])[0], w.nH, w.T, 0.0,
+               np.full(w.n, case_rule == U.CASE_B))
+    assert rel_err(E0.cpu().numpy(), xe).max() < 1e-9
+
+
+def test_tangent_fp32_halo(halo_small):
+    w, bvh, d = halo_small
+    sg, so = spectra(w, torch)
+    dirs = U.urchin_healpix_dirs(1)
+    x, _ = _solve_gpu(w, bvh, d, sg, U.F32, tol=1e-300, max_iter=20, case_rule=U.CASE_A, segments=U.SEG_STORE)
+    x = np.minimum(x, 0.9)           # keep x e^(eps v) inside (0, 1]
+    rng = np.random.default_rng(32)
+    v = rng.uniform(-1, 1, w.n)
+    eps = 1e-3
+    tg = lambda xx: U.urchin_tangent(bvh, dirs, w.l_ray, sg[0], sg[1], d["nH"], d["T"],
+                                     torch.from_numpy(xx).cuda(), torch.from_numpy(v).cuda(),
+                                     precision=U.F64, case_rule=U.CASE_A)
+    E0, dl64 = tg(x)
+    _, dl32 = U.urchin_tangent(bvh, dirs, w.l_ray, sg[0], sg[1], d["nH"], d["T"], torch.from_numpy(x).cuda(),
+                               torch.from_numpy(v).cuda(), precision=U.F32, case_rule=U.CASE_A)
+    Ep, _ = tg(x * np.exp(eps * v))
+    Em, _ = tg(x * np.exp(-eps * v))
+    fd = (np.log(Ep.cpu().numpy()) - np.log(Em.cpu().numpy())) / (2 * eps)
+    dl64 = dl64.cpu().numpy()
+    dl32 = dl32.cpu().numpy()
+    scale = np.abs(fd).max()
+    assert np.quantile(np.abs(dl64 - fd), 0.999) <= 1e-4 * scale
+    assert np.quantile(np.abs(dl32 - dl64), 0.999) <= 1e-4 * scale
