@@ -134,6 +134,22 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def combine_ranks(total_ms: float, counts, device=None):
+    """Replicas: the job's time is the slowest rank's, its work the sum over
+    ranks.  Returns (max total_ms, [summed counts]); a no-op without a
+    process group."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return total_ms, list(counts)
+    t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    c = torch.tensor([float(v) for v in counts], dtype=torch.float64, device=device)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return float(t.item()), [float(v) for v in c.tolist()]
+
+
 def oracle_sample(w, s, wts, dirs, seconds: float):
     """The FP64 oracle on a bounded sample of the workload: one sweep (columns
     of every ray, Gamma and the equilibrium x) for a seeded sample of origins
@@ -273,13 +289,7 @@ def main():
     hits = sum(st["hits"] for st in stats)
     trace_s = sum(st["trace_s"] for st in stats)
     trace_launches = sum(st["trace_launches"] for st in stats)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        c = torch.tensor([float(rays), float(updates)], dtype=torch.float64, device=dev)
-        dist.all_reduce(c, op=dist.ReduceOp.SUM)
-        rays, updates = float(c[0].item()), float(c[1].item())
+    total_ms, (rays, updates) = combine_ranks(total_ms, (rays, updates), device=dev)
 
     # end to end through the public API with host buffers: pinned H2D of the
     # inputs, build, solve, D2H of x, all inside the timed region
