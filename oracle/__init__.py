@@ -14,6 +14,9 @@ Functions (FP64 throughout; each follows the passage named in the C source):
   gamma(...)                                      Eq. gamma_shld
   rates(T), xeq(...)                              App. C3, Eqs. xroots / xphys
   solve(...)                                      Sec. 4 iteration driver (Jacobi)
+  column_matrix(...)                              Eq. colden as tau = M x
+  gamma_partials(...), xeq_dgamma(...)            derivatives of Eq. gamma_shld, Eq. xroots
+  columns_vjp(...), solve_vjp(...)                reverse-mode derivatives (dense)
 """
 from __future__ import annotations
 
@@ -80,7 +83,10 @@ def _load():
                 "oracle_rates": (None, [d, vp, vp, vp]),
                 "oracle_xeq": (d, [d, d, d, d, i]),
                 "oracle_solve": (i, [i64, vp, vp, vp, vp, vp, vp, vp, d, i, d, d,
-                                     vp, i, d, i, i, vp, vp, d, d, i, i, i, vp, vp, vp, vp]),
+                                     vp, i, d, i, i, vp, vp, d, d, i, i, i, vp, vp, vp, vp, vp]),
+                "oracle_xeq_dgamma": (d, [d, d, d, d, i]),
+                "oracle_column_matrix": (None, [i64, vp, vp, vp, vp, vp, i, d, d,
+                                                vp, i64, vp, i, d, i, vp]),
                 "oracle_num_threads": (i, []),
             }
             for name, (res, args) in sig.items():
@@ -223,13 +229,15 @@ def solve(w, s, wts, dirs, tol=1e-3, tau_skip=1e-4, max_iter=100, case_rule=CASE
     """Iteration of Sec. 4: Jacobi (blocks=1) or the high-to-low density
     update order in `blocks` blocks.  ``sweeps`` = exact sweep count
     (step-matched mode) instead of the tolerance test.  Returns (x, frozen,
-    stats) with stats = dict(sweeps, max_rel_dx, rays, converged)."""
+    stats) with stats = dict(sweeps, max_rel_dx, rays, converged, caseB), caseB
+    the case of each particle's last update."""
     px, py, pz, h, m = _particles(w)
     nH, T = _f64(w.nH), _f64(w.T)
     dirs = _f64(dirs).reshape(-1, 3)
     s, wts = _f64(s), _f64(wts)
     x = np.zeros(w.n)
     frozen = np.zeros(w.n, dtype=np.int32)
+    caseB = np.zeros(w.n, dtype=np.int32)
     st = np.zeros(3)
     xs = None if x_start is None else _f64(x_start)
     mi = -int(sweeps) if sweeps is not None else int(max_iter)
@@ -238,9 +246,104 @@ def solve(w, s, wts, dirs, tol=1e-3, tau_skip=1e-4, max_iter=100, case_rule=CASE
                               _p(dirs), dirs.shape[0],
                               float(w.l_ray if l_ray is None else l_ray), kernel,
                               s.shape[0], _p(s), _p(wts), float(tol), float(tau_skip),
-                              mi, case_rule, int(blocks), _p(xs), _p(x), _p(frozen), _p(st))
+                              mi, case_rule, int(blocks), _p(xs), _p(x), _p(frozen), _p(caseB), _p(st))
     return x, frozen.astype(bool), dict(sweeps=int(st[0]), max_rel_dx=float(st[1]),
-                                        rays=float(st[2]), converged=(rc == 0))
+                                        rays=float(st[2]), converged=(rc == 0),
+                                        caseB=caseB.astype(bool))
+
+
+# -- derivatives (reverse mode, dense) ----------------------------------------
+def column_matrix(w, dirs, origins=None, l_ray=None, kernel=KERNEL_M4):
+    """M[o, k, j] with tau[o, k] = sum_j M[o, k, j] x_j (Eq. colden is linear
+    in x).  Dense: n_orig * R * n doubles."""
+    px, py, pz, h, m = _particles(w)
+    dirs = _f64(dirs).reshape(-1, 3)
+    R = dirs.shape[0]
+    org = None if origins is None else np.ascontiguousarray(origins, dtype=np.int64)
+    n_orig = w.n if org is None else org.shape[0]
+    M = np.zeros((n_orig, R, w.n))
+    _load().oracle_column_matrix(w.n, _p(px), _p(py), _p(pz), _p(h), _p(m),
+                                 int(w.periodic), float(w.box), float(w.unit_cm),
+                                 _p(org), n_orig, _p(dirs), R,
+                                 float(w.l_ray if l_ray is None else l_ray), kernel, _p(M))
+    return M
+
+
+def columns_vjp(w, dirs, tau_bar, origins=None, l_ray=None, kernel=KERNEL_M4, chunk=256):
+    """x_bar[j] = sum_{o,k} tau_bar[o, k] dtau[o, k]/dx_j = (M^T tau_bar)_j."""
+    tau_bar = _f64(tau_bar)
+    org = np.arange(w.n) if origins is None else np.asarray(origins, dtype=np.int64)
+    out = np.zeros(w.n)
+    for a in range(0, org.shape[0], chunk):
+        M = column_matrix(w, dirs, org[a:a + chunk], l_ray, kernel)
+        out += np.einsum("okj,ok->j", M, tau_bar[a:a + chunk])
+    return out
+
+
+def gamma_partials(tau, s, w):
+    """Partial derivatives of Eq. gamma_shld, Gamma_o = (1/R) sum_k sum_b
+    w_b exp(-s_b tau_ok):  dGamma_o/dtau_ok = -(1/R) sum_b w_b s_b
+    exp(-s_b tau_ok)  [n_orig, R]  and  dGamma_o/dw_b = (1/R) sum_k
+    exp(-s_b tau_ok)  [n_orig, F]."""
+    tau, s, w = _f64(tau), _f64(s), _f64(w)
+    R = tau.shape[1]
+    e = np.exp(-tau[:, :, None] * s[None, None, :])          # [n_orig, R, F]
+    dG_dtau = -(e * (w * s)[None, None, :]).sum(axis=2) / R
+    dG_dw = e.sum(axis=1) / R
+    return dG_dtau, dG_dw
+
+
+def xeq_dgamma(Gamma, nH, T, y=0.0, caseB=False):
+    """d x_- / d Gamma of the equilibrium root (App. C3)."""
+    lib = _load()
+    G, nH, T, cb = np.broadcast_arrays(np.atleast_1d(np.asarray(Gamma, dtype=np.float64)),
+                                       np.asarray(nH, dtype=np.float64),
+                                       np.asarray(T, dtype=np.float64),
+                                       np.asarray(caseB, dtype=bool))
+    return np.array([lib.oracle_xeq_dgamma(float(g), float(n), float(t), float(y), int(c))
+                     for g, n, t, c in zip(G, nH, T, cb)])
+
+
+def solve_vjp(w, s, wts, dirs, x_star, frozen, caseB, x_bar, case_rule=CASE_AUTO, y=0.0,
+              kernel=KERNEL_M4, l_ray=None, warm_start=False, chunk=256):
+    """Gradient of a loss L(x*) with respect to the spectrum weights w_b by
+    the implicit function theorem at the fixed point of Sec. 4.
+
+    Non-frozen particles a satisfy x_a = E_a(Gamma_a(x, w)) with their case
+    held (caseB); frozen particles f hold x_thin,f = E_f(Gamma_thin), with
+    Gamma_thin = sum_b w_b (constants when warm_start).  With
+    J[a, j] = dE_a/dGamma_a * sum_k dGamma_a/dtau_ak * M[a, k, j],
+        mu = (I - J[:, act])^{-T} x_bar[act],   Gamma_bar_a = mu_a dE_a/dGamma_a,
+        dL/dw_b = sum_a Gamma_bar_a dGamma_a/dw_b
+                  + sum_f (x_bar_f + (J^T mu)_f) dE_f/dGamma(Gamma_thin).
+    Everything is evaluated at the given x_star.  Returns (w_bar[F], mu[n_act])."""
+    s, wts, x_star, x_bar = _f64(s), _f64(wts), _f64(x_star), _f64(x_bar)
+    frozen = np.asarray(frozen, dtype=bool)
+    caseB = np.asarray(caseB, dtype=bool)
+    act = np.flatnonzero(~frozen)
+    fro = np.flatnonzero(frozen)
+    na = act.shape[0]
+    J = np.zeros((na, w.n))
+    dGdw = np.zeros((na, s.shape[0]))
+    dEdG = np.zeros(na)
+    for a in range(0, na, chunk):
+        ids = act[a:a + chunk]
+        M = column_matrix(w, dirs, ids, l_ray, kernel)
+        tau = np.einsum("okj,j->ok", M, x_star)
+        G, _ = gamma(tau, s, wts)
+        dG_dtau, dG_dw = gamma_partials(tau, s, wts)
+        e1 = xeq_dgamma(G, w.nH[ids], w.T[ids], y, caseB[ids])
+        J[a:a + len(ids)] = e1[:, None] * np.einsum("ok,okj->oj", dG_dtau, M)
+        dGdw[a:a + len(ids)] = dG_dw
+        dEdG[a:a + len(ids)] = e1
+    mu = np.linalg.solve((np.eye(na) - J[:, act]).T, x_bar[act])
+    w_bar = (mu * dEdG) @ dGdw
+    if fro.shape[0] and not warm_start:
+        gthin = float(wts.sum())
+        xbar_f = x_bar[fro] + J[:, fro].T @ mu
+        cb = np.full(fro.shape[0], case_rule == CASE_B)
+        w_bar = w_bar + float(xbar_f @ xeq_dgamma(gthin, w.nH[fro], w.T[fro], y, cb))
+    return w_bar, mu
 
 
 def num_threads() -> int:

@@ -401,6 +401,20 @@ double oracle_xeq(double Gamma, double nH, double T, double y, int caseB)
     return 2.0 * P / (-Q + sqrt(disc));
 }
 
+/* d x_- / d Gamma by implicit differentiation of f(x, Gamma) = R x^2 + Q x + P
+ * = 0, where only Q depends on Gamma (dQ/dGamma = -1):
+ *   dx/dGamma = -(df/dGamma) / (df/dx) = x / (2 R x + Q). */
+double oracle_xeq_dgamma(double Gamma, double nH, double T, double y, int caseB)
+{
+    double aA, aB, gc;
+    oracle_rates(T, &aA, &aB, &gc);
+    double alpha = caseB ? aB : aA;
+    double R = (gc + alpha) * nH;
+    double Q = -(Gamma + alpha * nH + R * (1.0 + y));
+    double x = oracle_xeq(Gamma, nH, T, y, caseB);
+    return x / (2.0 * R * x + Q);
+}
+
 /* Case choice (Sec. 3.3.3 / Sec. 4): 0 = always A, 1 = always B,
  * 2 = B when tau_eff >= 1.  In the iteration driver rule 2 is latched: a
  * particle that has once had tau_eff >= 1 keeps case B (see oracle_solve). */
@@ -437,7 +451,8 @@ static int use_caseB(int case_rule, double tau_eff)
  * and each sweep updates block after block, every block's columns using the
  * x of the blocks already updated in that sweep.
  * x_out[n] receives the final x, frozen_out[n] (optional) 1 for frozen
- * particles, stats[0] = sweeps done, stats[1] = last max |dx|/x,
+ * particles, caseB_out[n] (optional) 1 where the final update used case B,
+ * stats[0] = sweeps done, stats[1] = last max |dx|/x,
  * stats[2] = rays traced.  x_start (optional) replaces x_thin as the start
  * (sweep 0 still applies the freeze rule).  Returns 0 when converged, 1 when
  * the sweep limit ended the run. */
@@ -457,7 +472,7 @@ int oracle_solve(int64_t n, const double* px, const double* py, const double* pz
                  const double* dirs, int R, double l_ray, int kernel,
                  int F, const double* s, const double* w,
                  double tol, double tau_skip, int max_iter, int case_rule, int blocks,
-                 const double* x_start, double* x_out, int* frozen_out, double* stats)
+                 const double* x_start, double* x_out, int* frozen_out, int* caseB_out, double* stats)
 {
     double gthin = 0.0;
     for (int j = 0; j < F; ++j) gthin += w[j];
@@ -533,9 +548,54 @@ int oracle_solve(int64_t n, const double* px, const double* py, const double* pz
         if (!fixed && maxrel < tol) { converged = 1; break; }
     }
     if (frozen_out) for (int64_t i = 0; i < n; ++i) frozen_out[i] = frozen[i];
+    if (caseB_out) for (int64_t i = 0; i < n; ++i) caseB_out[i] = frozen[i] ? use_caseB(case_rule, 0.0) : latchB[i];
     if (stats) { stats[0] = sweeps; stats[1] = maxrel; stats[2] = rays; }
     free(frozen); free(latchB); free(tau); free(G); free(te); free(xn); free(act);
     return (fixed || converged) ? 0 : 1;
+}
+
+/* Columns are linear in x (Eq. colden): tau = M x with
+ *   M[(o R + k) n + j] = sigma_th (m_j / m_p) int_0^{l_ray} W(|r_o + t n_k - r_j| / h_j) dt,
+ * summed over the periodic images of j.  Brute force, like oracle_columns. */
+void oracle_column_matrix(int64_t n, const double* px, const double* py, const double* pz,
+                          const double* h, const double* mass_H,
+                          int periodic, double L, double unit_cm,
+                          const int64_t* origins, int64_t n_orig,
+                          const double* dirs, int R, double l_ray, int kernel, double* M)
+{
+    int nimg = image_range(periodic, L, n, h, l_ray);
+    int64_t total = n_orig * (int64_t)R;
+    double sth = oracle_sigma_th();
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t r = 0; r < total; ++r) {
+        int64_t o = r / R;
+        int k = (int)(r % R);
+        int64_t i = origins ? origins[o] : o;
+        const double* dir = dirs + 3 * k;
+        double* row = M + r * n;
+        for (int64_t j = 0; j < n; ++j) {
+            double hj = h[j], acc = 0.0;
+            for (int a = -nimg; a <= nimg; ++a)
+            for (int bb = -nimg; bb <= nimg; ++bb)
+            for (int c = -nimg; c <= nimg; ++c) {
+                double dx = px[j] + (periodic ? a * L : 0.0) - px[i];
+                double dy = py[j] + (periodic ? bb * L : 0.0) - py[i];
+                double dz = pz[j] + (periodic ? c * L : 0.0) - pz[i];
+                double tc = dx * dir[0] + dy * dir[1] + dz * dir[2];
+                double cx = dy * dir[2] - dz * dir[1];
+                double cy = dz * dir[0] - dx * dir[2];
+                double cz = dx * dir[1] - dy * dir[0];
+                double b2 = cx * cx + cy * cy + cz * cz;
+                if (b2 >= hj * hj) continue;
+                double half = sqrt(hj * hj - b2);
+                double t1 = fmax(0.0, tc - half), t2 = fmin(l_ray, tc + half);
+                if (t2 <= t1) continue;
+                acc += oracle_chord(kernel, sqrt(b2) / hj, (t1 - tc) / hj, (t2 - tc) / hj);
+            }
+            double hcm = hj * unit_cm;
+            row[j] = sth * mass_H[j] * (8.0 / OR_PI) / (hcm * hcm) * acc;
+        }
+    }
 }
 
 /* Directional derivative of the sweep map along v (for checking tangents):
