@@ -68,6 +68,7 @@ typedef struct CUstream_st* urchin_stream_t;
 #define URCHIN_XSEC_POWERLAW    2     /* sigma_th (nu/nu_th)^-3, Eq. sigma_pwr  */
 #define URCHIN_METHOD_PLAIN     0     /* Jacobi fixed point (Sec. 4)            */
 #define URCHIN_METHOD_NEWTON    1     /* Newton-Krylov on the same fixed point  */
+#define URCHIN_METHOD_ANDERSON  2     /* Anderson-accelerated sweeps            */
 #define URCHIN_SEG_RECOMPUTE    0     /* trace the BVH every sweep              */
 #define URCHIN_SEG_STORE        1     /* store per-ray segment lists once       */
 #define URCHIN_SEG_AUTO         2     /* store when the lists fit in memory     */
@@ -237,7 +238,8 @@ typedef struct {
     int             max_iter;     /* sweep limit (plain) / Newton step limit   */
     int             method;       /* URCHIN_METHOD_*                           */
     int             segments;     /* URCHIN_SEG_*                              */
-    int             gmres_m;      /* Krylov dimension per Newton step          */
+    int             gmres_m;      /* Krylov dimension per Newton step, or the
+                                     history depth of Anderson acceleration    */
     int             kernel;       /* URCHIN_KERNEL_*                           */
     int             precision;    /* URCHIN_F32 / URCHIN_F64 (columns, Gamma)  */
     int             case_rule;    /* URCHIN_CASE_*                             */
@@ -298,7 +300,10 @@ typedef struct {
  * URCHIN_METHOD_NEWTON runs those sweeps until at most `newton_switch` of
  * the non-frozen particles remain above tol, then solves the same fixed
  * point x = E(Gamma(x)) with a Newton-Krylov iteration in ln x (GMRES with
- * tangent columns, backtracking, plain-sweep fallback).  x_inout is
+ * tangent columns, backtracking, plain-sweep fallback).
+ * URCHIN_METHOD_ANDERSON accelerates the sweeps themselves: each iteration
+ * evaluates the sweep map once and combines it with the last gmres_m
+ * iterates (Anderson mixing in ln x, restarted when the residual grows).  x_inout is
  * device [n] double in the original particle order.  `stats` may be NULL.
  * Synchronises `stream`.  Returns URCHIN_ERR_NOT_CONVERGED (x_inout then
  * holds the last iterate) when max_iter is reached first. */

@@ -198,14 +198,16 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs A)
                 const double rel = fabs(xn - xo) / xo;
                 my_max = fmax(my_max, rel);
                 if (rel >= A.tol) ++my_above;
-                if (A.want_tangent) {
-                    // elasticity Gamma dE/dGamma / E and per-ray dGamma/dtau_k / Gamma
-                    const double dEdG = dx_dgamma(xn, A.nH[i], alpha, A.gc[i], G, A.y);
-                    const double elas = (G > 0.0) ? G * dEdG / xn : 0.0;
-                    const Real* l2 = lk2 + p * A.R;
-                    for (int r = 0; r < A.R; ++r) {
-                        const double dlog = (double)exp_p(l2[r] - lmean_r) / (double)A.R;
-                        A.ctan[prow + (int64_t)r * A.k_stride] = -elas * dlog;
+                if (A.xeq_out) {
+                    if (A.want_tangent) {
+                        // elasticity Gamma dE/dGamma / E and per-ray dGamma/dtau_k / Gamma
+                        const double dEdG = dx_dgamma(xn, A.nH[i], alpha, A.gc[i], G, A.y);
+                        const double elas = (G > 0.0) ? G * dEdG / xn : 0.0;
+                        const Real* l2 = lk2 + p * A.R;
+                        for (int r = 0; r < A.R; ++r) {
+                            const double dlog = (double)exp_p(l2[r] - lmean_r) / (double)A.R;
+                            A.ctan[prow + (int64_t)r * A.k_stride] = -elas * dlog;
+                        }
                     }
                     A.xeq_out[prow] = xn;
                 } else {
@@ -362,6 +364,36 @@ __global__ void k_tangent_out(const int32_t* __restrict__ perm, const double* __
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
         dlnE_out[perm[s]] = vm[s] - jv[s];
         if (E_out) E_out[perm[s]] = E[s];
+    }
+}
+
+// Anderson mixing: f = ln E - ln x (residual), g = ln E (map) on the active set
+__global__ void k_aa_fg(const int32_t* __restrict__ items, int64_t n_act, const double* __restrict__ x,
+                        const double* __restrict__ E, double* f, double* g)
+{
+    for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < n_act; a += (int64_t)gridDim.x * blockDim.x) {
+        const double lg = log(E[a]);
+        g[a] = lg;
+        f[a] = lg - log(x[items[a]]);
+    }
+}
+
+// x = exp(u), u kept within a factor e of the plain update g (and x <= 1);
+// refresh the tracer weights and x copies
+__global__ void k_set_x_from_u(const int32_t* __restrict__ items, int64_t n_act, const double* __restrict__ u,
+                               const double* __restrict__ g, double* x, const double* __restrict__ A64, float* w32,
+                               double* w64, float* xs32, double* xs64)
+{
+    for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < n_act; a += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t i = items[a];
+        const double ua = fmin(fmax(u[a], g[a] - 1.0), g[a] + 1.0);
+        const double xn = fmin(1.0, exp(ua));
+        x[i] = xn;
+        const double wv = A64[i] * xn;
+        if (w32) w32[i] = (float)wv;
+        if (w64) w64[i] = wv;
+        if (xs32) xs32[i] = (float)xn;
+        if (xs64) xs64[i] = xn;
     }
 }
 
@@ -856,7 +888,7 @@ int Solver::plain_sweeps(double stop_fraction)
 // E = E(Gamma(x)), the tangent factors, max |E - x| / x, and the residual
 // r = ln E - ln x (into V0) with its 2-norm.
 int Solver::evaluate(int frozen, double* V0, double* E, double* ctan, double* dtmp, double* hdev, double* maxrel,
-                     double* norm, int64_t* switches)
+                     double* norm, int64_t* switches, int tangent)
 {
     const int64_t na = n_act;
     const unsigned g1 = (unsigned)std::max<int64_t>(1, std::min<int64_t>((na + 255) / 256, 2048));
@@ -864,8 +896,8 @@ int Solver::evaluate(int frozen, double* V0, double* E, double* ctan, double* dt
     URCHIN_TRY_CUDA(cudaMemsetAsync(misc + 7, 0, 2 * sizeof(unsigned long long), s));
     URCHIN_TRY(columns(list, na, 0));
     SweepArgs A = sweep_args(list, na, 0);
-    A.want_tangent = 1;
-    A.ctan = ctan;
+    A.want_tangent = tangent;
+    A.ctan = tangent ? ctan : nullptr;
     A.xeq_out = E;
     A.latch_frozen = frozen;
     URCHIN_TRY(timed_sweep(A, s));
@@ -1053,6 +1085,131 @@ int Solver::newton()
     return URCHIN_OK;
 }
 
+// Anderson acceleration of the sweep map in u = ln x (Walker & Ni 2011 form):
+// with f_k = g(u_k) - u_k, g = ln E(Gamma(e^u)), and the last m differences
+// dF_i = f_{i+1} - f_i, dG_i = g_{i+1} - g_i, the next iterate is
+// u_{k+1} = g_k - sum_i gamma_i dG_i with gamma = argmin ||f_k - dF gamma||_2
+// (normal equations, Tikhonov-regularised), each u kept within a factor e of
+// g.  The history restarts when ||f|| grows by more than a factor 2 or a
+// recombination case switches.  Blocks do not apply: every evaluation
+// updates all non-frozen particles at once.  The stop
+// test and final update are the plain sweep's (x <- E when max |E - x|/x <
+// tol).  Every evaluation of the sweep map counts as one iteration.
+int Solver::anderson()
+{
+    URCHIN_TRY(first_sweep());
+    if (stats.max_rel_dx < P.tol || n_act == 0) {
+        stats.converged = 1;
+        return URCHIN_OK;
+    }
+    const int m = P.gmres_m;
+    const int64_t na = n_act;
+    Layout lay;
+    size_t o_dF = lay.take(sizeof(double) * (size_t)m * na);
+    size_t o_dG = lay.take(sizeof(double) * (size_t)m * na);
+    size_t o_f = lay.take(sizeof(double) * (size_t)na);
+    size_t o_g = lay.take(sizeof(double) * (size_t)na);
+    size_t o_fp = lay.take(sizeof(double) * (size_t)na);
+    size_t o_gp = lay.take(sizeof(double) * (size_t)na);
+    size_t o_E = lay.take(sizeof(double) * (size_t)na);
+    size_t o_V = lay.take(sizeof(double) * (size_t)na);
+    size_t o_dt = lay.take(dots_tmp_bytes(m + 1));
+    size_t o_h = lay.take(sizeof(double) * (size_t)(m + 2));
+    URCHIN_TRY(nk.alloc(lay.bytes, s));
+    double* dF = nk.at<double>(o_dF);
+    double* dG = nk.at<double>(o_dG);
+    double* f = nk.at<double>(o_f);
+    double* g = nk.at<double>(o_g);
+    double* fp = nk.at<double>(o_fp);
+    double* gp = nk.at<double>(o_gp);
+    double* E = nk.at<double>(o_E);
+    double* V0 = nk.at<double>(o_V);
+    double* dtmp = nk.at<double>(o_dt);
+    double* hdev = nk.at<double>(o_h);
+    const unsigned g1 = (unsigned)std::max<int64_t>(1, std::min<int64_t>((na + 255) / 256, 2048));
+    int hist = 0, head = 0;                         // valid history columns, next slot
+    double mrel = 0.0, norm = 0.0, prev_norm = -1.0;
+    int64_t sw = 0;
+    std::vector<double> M((size_t)m * m), rhs(m), gam(m);
+    URCHIN_TRY(evaluate(0, V0, E, nullptr, dtmp, hdev, &mrel, &norm, &sw, 0));
+    for (;;) {
+        if (mrel < P.tol || stats.iterations >= P.max_iter) {
+            k_set_x<<<g1, 256, 0, s>>>(list, na, nullptr, 0.0, nullptr, E, x, bvh->A64, w32, w64, xs32, xs64);
+            URCHIN_TRY(launched());
+            if (mrel < P.tol) stats.converged = 1;
+            break;
+        }
+        k_aa_fg<<<g1, 256, 0, s>>>(list, na, x, E, f, g);
+        URCHIN_TRY(launched());
+        if (prev_norm >= 0.0 && (norm > 2.0 * prev_norm || sw > 0)) {
+            hist = 0;                               // restart the history
+            head = 0;
+            stats.newton_fallbacks += 1;
+        } else if (prev_norm >= 0.0) {
+            double* dFs = dF + (size_t)head * na;
+            double* dGs = dG + (size_t)head * na;
+            URCHIN_TRY_CUDA(cudaMemcpyAsync(dFs, f, sizeof(double) * (size_t)na, cudaMemcpyDeviceToDevice, s));
+            URCHIN_TRY(launch_axpby(-1.0, fp, 1.0, dFs, na, s));
+            URCHIN_TRY_CUDA(cudaMemcpyAsync(dGs, g, sizeof(double) * (size_t)na, cudaMemcpyDeviceToDevice, s));
+            URCHIN_TRY(launch_axpby(-1.0, gp, 1.0, dGs, na, s));
+            head = (head + 1) % m;
+            hist = std::min(hist + 1, m);
+        }
+        URCHIN_TRY_CUDA(cudaMemcpyAsync(fp, f, sizeof(double) * (size_t)na, cudaMemcpyDeviceToDevice, s));
+        URCHIN_TRY_CUDA(cudaMemcpyAsync(gp, g, sizeof(double) * (size_t)na, cudaMemcpyDeviceToDevice, s));
+        prev_norm = norm;
+        if (hist > 0) {
+            // normal equations (dF^T dF + mu I) gamma = dF^T f over the valid slots 0..hist-1
+            for (int j = 0; j < hist; ++j) {
+                URCHIN_TRY(launch_dots(dF, na, hist, dF + (size_t)j * na, na, dtmp, hdev, s));
+                URCHIN_TRY_CUDA(cudaMemcpyAsync(M.data() + (size_t)j * m, hdev, sizeof(double) * hist,
+                                                cudaMemcpyDeviceToHost, s));
+            }
+            URCHIN_TRY(launch_dots(dF, na, hist, f, na, dtmp, hdev, s));
+            URCHIN_TRY_CUDA(cudaMemcpyAsync(rhs.data(), hdev, sizeof(double) * hist, cudaMemcpyDeviceToHost, s));
+            URCHIN_TRY_CUDA(cudaStreamSynchronize(s));
+            double tr = 0.0;
+            for (int j = 0; j < hist; ++j) tr += M[(size_t)j * m + j];
+            const double mu = 1e-10 * (tr > 0.0 ? tr : 1.0);
+            std::vector<double> Aq((size_t)hist * hist), bq(rhs.begin(), rhs.begin() + hist);
+            for (int r = 0; r < hist; ++r)
+                for (int c = 0; c < hist; ++c) Aq[(size_t)r * hist + c] = M[(size_t)c * m + r] + (r == c ? mu : 0.0);
+            for (int c = 0; c < hist; ++c) {        // Gaussian elimination with partial pivoting
+                int piv = c;
+                for (int r = c + 1; r < hist; ++r)
+                    if (std::fabs(Aq[(size_t)r * hist + c]) > std::fabs(Aq[(size_t)piv * hist + c])) piv = r;
+                if (piv != c) {
+                    for (int k2 = 0; k2 < hist; ++k2) std::swap(Aq[(size_t)c * hist + k2], Aq[(size_t)piv * hist + k2]);
+                    std::swap(bq[c], bq[piv]);
+                }
+                const double d = Aq[(size_t)c * hist + c];
+                if (d == 0.0) continue;
+                for (int r = c + 1; r < hist; ++r) {
+                    const double fct = Aq[(size_t)r * hist + c] / d;
+                    for (int k2 = c; k2 < hist; ++k2) Aq[(size_t)r * hist + k2] -= fct * Aq[(size_t)c * hist + k2];
+                    bq[r] -= fct * bq[c];
+                }
+            }
+            for (int r = hist - 1; r >= 0; --r) {
+                double acc = bq[r];
+                for (int c = r + 1; c < hist; ++c) acc -= Aq[(size_t)r * hist + c] * gam[c];
+                const double d = Aq[(size_t)r * hist + r];
+                gam[r] = d != 0.0 ? acc / d : 0.0;
+            }
+            // u = g - dG gamma
+            URCHIN_TRY_CUDA(cudaMemcpyAsync(hdev, gam.data(), sizeof(double) * hist, cudaMemcpyHostToDevice, s));
+            URCHIN_TRY_CUDA(cudaMemcpyAsync(V0, g, sizeof(double) * (size_t)na, cudaMemcpyDeviceToDevice, s));
+            URCHIN_TRY(launch_subtract(V0, dG, na, hist, hdev, na, s));
+            k_set_x_from_u<<<g1, 256, 0, s>>>(list, na, V0, g, x, bvh->A64, w32, w64, xs32, xs64);
+        } else {
+            k_set_x_from_u<<<g1, 256, 0, s>>>(list, na, g, g, x, bvh->A64, w32, w64, xs32, xs64);
+        }
+        URCHIN_TRY(launched());
+        URCHIN_TRY(evaluate(0, V0, E, nullptr, dtmp, hdev, &mrel, &norm, &sw, 0));
+    }
+    return URCHIN_OK;
+}
+
 // Sweep-map tangent at the current x (see urchin_tangent): one traversal for
 // E and the factors c_ik, one for the columns of x v.
 int Solver::tangent(const double* v_orig, double* E_orig, double* dlnE_orig)
@@ -1207,11 +1364,11 @@ extern "C" int urchin_solve(const urchin_bvh* bvh, const urchin_solve_params* P,
         return set_error(URCHIN_ERR_ARG, "urchin_solve: unknown precision");
     if (P->case_rule != URCHIN_CASE_A && P->case_rule != URCHIN_CASE_B && P->case_rule != URCHIN_CASE_AUTO)
         return set_error(URCHIN_ERR_ARG, "urchin_solve: unknown case_rule");
-    if (P->method != URCHIN_METHOD_PLAIN && P->method != URCHIN_METHOD_NEWTON)
+    if (P->method != URCHIN_METHOD_PLAIN && P->method != URCHIN_METHOD_NEWTON && P->method != URCHIN_METHOD_ANDERSON)
         return set_error(URCHIN_ERR_ARG, "urchin_solve: unknown method");
     if (P->segments != URCHIN_SEG_RECOMPUTE && P->segments != URCHIN_SEG_STORE && P->segments != URCHIN_SEG_AUTO)
         return set_error(URCHIN_ERR_ARG, "urchin_solve: unknown segments mode");
-    if (P->method == URCHIN_METHOD_NEWTON && (P->gmres_m < 1 || P->gmres_m > 64))
+    if (P->method != URCHIN_METHOD_PLAIN && (P->gmres_m < 1 || P->gmres_m > 64))
         return set_error(URCHIN_ERR_ARG, "urchin_solve: gmres_m must be in [1, 64]");
     cudaStream_t s = (cudaStream_t)stream;
     Solver S;

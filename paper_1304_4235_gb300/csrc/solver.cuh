@@ -104,7 +104,7 @@ struct Solver {
     int count_spmv(const int32_t* items, int64_t n_items);
     int64_t active_nnz = -1;
     int evaluate(int frozen, double* V0, double* E, double* ctan, double* dtmp, double* hdev, double* maxrel,
-                 double* norm, int64_t* switches);
+                 double* norm, int64_t* switches, int tangent = 1);
 
     int init(const urchin_bvh* bvh, const urchin_solve_params* P, double* x_inout, cudaStream_t s);
     int trace(const int32_t* items, int64_t n_items, const float* tw32, const double* tw64);
@@ -117,7 +117,13 @@ struct Solver {
     int plain();
     int plain_sweeps(double stop_fraction);
     int newton();
-    int run() { return P.method == URCHIN_METHOD_NEWTON ? newton() : plain(); }
+    int anderson();
+    int run()
+    {
+        if (P.method == URCHIN_METHOD_NEWTON) return newton();
+        if (P.method == URCHIN_METHOD_ANDERSON) return anderson();
+        return plain();
+    }
     int finish(double* x_inout);
     int tangent(const double* v_orig, double* E_orig, double* dlnE_orig);
 };

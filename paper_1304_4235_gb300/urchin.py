@@ -28,7 +28,7 @@ KERNEL_M4, KERNEL_GT = 0, 1
 F32, F64 = 0, 1
 CASE_A, CASE_B, CASE_AUTO = 0, 1, 2
 XSEC_VERNER, XSEC_HYDROGENIC, XSEC_POWERLAW = 0, 1, 2
-METHOD_PLAIN, METHOD_NEWTON = 0, 1
+METHOD_PLAIN, METHOD_NEWTON, METHOD_ANDERSON = 0, 1, 2
 SEG_RECOMPUTE, SEG_STORE, SEG_AUTO = 0, 1, 2
 MAX_RAYS = 192
 MAX_BINS = 4096

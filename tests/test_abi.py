@@ -135,3 +135,13 @@ def test_solve_params_validation():
     P.dirs = bad.ctypes.data_as(C.c_void_p)
     assert lib.urchin_solve(fake, C.byref(P), fake, C.byref(st), None) == U.URCHIN_ERR_ARG
     assert "unit" in lib.urchin_last_error().decode()
+    P.dirs = dirs.ctypes.data_as(C.c_void_p)
+    P.method = 3                                  # no such method
+    assert lib.urchin_solve(fake, C.byref(P), fake, C.byref(st), None) == U.URCHIN_ERR_ARG
+    assert "method" in lib.urchin_last_error().decode()
+    for method in (U.METHOD_NEWTON, U.METHOD_ANDERSON):
+        P.method = method
+        for m in (0, 65):                         # Krylov dimension / history depth out of range
+            P.gmres_m = m
+            assert lib.urchin_solve(fake, C.byref(P), fake, C.byref(st), None) == U.URCHIN_ERR_ARG
+            assert "gmres_m" in lib.urchin_last_error().decode()

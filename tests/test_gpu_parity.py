@@ -337,6 +337,18 @@ def test_newton_reaches_plain_fixed_point_lattice(lattice):
     assert rel_err(xn, xo).max() < 1e-8
 
 
+def test_anderson_reaches_plain_fixed_point_lattice(lattice):
+    """Anderson mixing of the sweep map converges to the plain iteration's
+    fixed point (FP64, stored segments)."""
+    w, bvh, d = lattice
+    sg, so = spectra(w, torch)
+    xp, sp = _solve_gpu(w, bvh, d, sg, U.F64, tol=1e-10, max_iter=300, segments=U.SEG_STORE)
+    xa, sa = _solve_gpu(w, bvh, d, sg, U.F64, tol=1e-10, max_iter=300, method=U.METHOD_ANDERSON, gmres_m=5,
+                        segments=U.SEG_STORE)
+    assert sp["converged"] and sa["converged"]
+    assert rel_err(xa, xp).max() < 1e-8
+
+
 @pytest.mark.parametrize("segments", [U.SEG_RECOMPUTE, U.SEG_STORE])
 def test_newton_halo_small_fp32(halo_small, segments):
     """Plain sweeps then Newton-Krylov at the paper's dx_tol = 1e-3: converges
