@@ -262,6 +262,11 @@ typedef struct {
                                       fraction of the non-frozen particles has
                                       |dx|/x >= tol, then Newton-Krylov takes
                                       over (<= 0: 0.01)                        */
+    unsigned char*  state;        /* device [n] or NULL, original order:
+                                     urchin_solve writes, urchin_solve_vjp
+                                     reads each particle's final state,
+                                     bit 0 = recombination case B,
+                                     bit 1 = frozen after sweep 0             */
 } urchin_solve_params;
 
 typedef struct {
@@ -324,6 +329,64 @@ URCHIN_API int urchin_solve(const urchin_bvh* bvh, const urchin_solve_params* pa
  * segments).  Synchronises `stream`.  Errors: as urchin_solve. */
 URCHIN_API int urchin_tangent(const urchin_bvh* bvh, const urchin_solve_params* params, const double* x,
                               const double* v, double* E_out, double* dlnE_out, urchin_stream_t stream);
+
+/* ---- Reverse mode (adjoints) -------------------------------------------
+ * Each *_vjp call is the transpose of the forward call of the same name:
+ * given the cotangent of the forward output it returns the cotangent of the
+ * inputs.  Accumulating outputs (+=) are marked; the caller zeroes them. */
+
+/* Transpose of Eq. colden: the columns are linear in x, tau = M x, so
+ *   x_bar[j] += sum_{o,k} tau_bar[o*R + k] sigma_th (m_j/m_p) int W dt
+ * over every ray (o, k) that crosses particle j (and its periodic images).
+ * Arguments as urchin_trace_columns; tau_bar has tau_out's layout and type
+ * (float for URCHIN_F32, double for URCHIN_F64); x_bar is device [n] double
+ * in the original order, accumulated with atomics (the order of the
+ * additions, hence the last bits, varies between runs).  Rays whose
+ * tau_bar is zero are not traced.  Synchronises `stream`.  Errors: as
+ * urchin_trace_columns. */
+URCHIN_API int urchin_trace_columns_vjp(const urchin_bvh* bvh, const double* dirs, int R, double l_ray,
+                                        const int32_t* origins, int64_t n_orig, int kernel, int precision,
+                                        const void* tau_bar, double* x_bar, urchin_stream_t stream);
+
+/* Transpose of Eq. gamma_shld, in double: with c_o = gamma_bar[o] / R,
+ *   tau_bar_out[o*R + k] = -c_o sum_b w_b s_b exp(-s_b tau_ok)      (overwritten;
+ *                          type of tau; may be NULL)
+ *   w_bar[b]            += sum_{o,k} c_o exp(-s_b tau_ok)           (device [F]; may be NULL)
+ * i.e. dL/dtau and dL/dw for the spectrum weights w (s held fixed).  One of
+ * the outputs must be given.  Errors: ERR_ARG, ERR_NOMEM, ERR_CUDA. */
+URCHIN_API int urchin_gamma_vjp(const void* tau, int precision, int64_t n_orig, int R,
+                                const urchin_spectrum* sp, const double* gamma_bar, void* tau_bar_out,
+                                double* w_bar, urchin_stream_t stream);
+
+/* Transpose of urchin_equilibrium: gamma_bar_out[i] = x_bar[i] dx_i/dGamma_i,
+ * dx/dGamma = x / (2 R x + Q) (implicit differentiation of the quadratic;
+ * the case choice is held).  Arguments as urchin_equilibrium.  Errors: ERR_ARG,
+ * ERR_CUDA. */
+URCHIN_API int urchin_equilibrium_vjp(const double* gamma, const float* tau_eff, const double* nH,
+                                      const double* T, int64_t n, int case_rule, double y,
+                                      const double* x_bar, double* gamma_bar_out, urchin_stream_t stream);
+
+/* Gradient of a loss L(x*) with respect to the spectrum weights w_b, where
+ * x* is the converged state of urchin_solve (implicit function theorem at
+ * the Sec. 4 fixed point; the paper has no derivatives, this is its
+ * adjoint).  Inputs: the same params as the forward solve, with
+ * params->state holding the state that solve wrote; x_star = its output;
+ * x_bar = dL/dx* (device [n] double, original order).  With the cases and
+ * the frozen set held, non-frozen particles satisfy x_a = E_a(Gamma_a(x, w))
+ * and (unless params->warm_start) frozen ones x_f = E_f(Gamma_thin), with
+ * Gamma_thin = sum_b w_b.  The call solves (I - J_u)^T nu = x_bar (.) x* for
+ * the sweep-map Jacobian in ln x by restarted GMRES(params->gmres_m), to
+ * relative residual params->tol in at most params->max_iter products (each
+ * one transposed column pass: scatter traversal, or the stored segments
+ * when params->segments allows), then
+ *   w_bar[b] += dL/dw_b                                  (device [F], accumulated).
+ * stats: iterations = products, max_rel_dx = final relative residual,
+ * converged, traversals, rays.  Synchronises `stream`.  Errors: as
+ * urchin_solve; ERR_NOT_CONVERGED when the residual target is not met
+ * (w_bar then holds the gradient of the last iterate). */
+URCHIN_API int urchin_solve_vjp(const urchin_bvh* bvh, const urchin_solve_params* params,
+                                const double* x_star, const double* x_bar, double* w_bar,
+                                urchin_solve_stats* stats, urchin_stream_t stream);
 
 #ifdef __cplusplus
 }

@@ -170,13 +170,21 @@ struct TraceJob {
     unsigned int* counter;        // one device uint (work queue), zeroed here
     unsigned int* status;         // one device uint: error flags (may be NULL)
     unsigned long long* hits;     // chord evaluations (may be NULL)
-    int mode;                     // 0: columns, 1: count hits per ray, 2: fill segments (+ columns)
+    int mode;                     // 0: columns, 1: count hits per ray, 2: fill segments (+ columns),
+                                  // 3: transpose (scatter coef * A_j * chord into xbar)
     uint32_t* counts;             // mode 1: [R * n_items], index k * n_items + item
     const uint64_t* row_ptr;      // mode 2: [R * n_items + 1] offsets of each ray's segments
     int32_t* seg_col;             // mode 2: Morton index of the particle per segment
     void* seg_val;                // mode 2: A_j * chord integral per segment (precision's type)
+    const void* coef;             // mode 3: per-ray coefficient (precision's type), indexed like out
+    double* xbar;                 // mode 3: [n] Morton order, accumulated with atomics
 };
 int launch_trace(const TraceJob& job, cudaStream_t s);
+
+// w_bar[b] += sum_r sg[r] exp(lc[r] - s_b tau[r]) over n_rays rays (tau in
+// the precision's type; the coefficient of ray r is sg[r] exp(lc[r]))
+int launch_wbar(const void* tau, int precision, int64_t n_rays, const double* lc, const double* sg, const double* s,
+                int F, double* w_bar, cudaStream_t st);
 
 // w = A * x gathered into Morton order: w[s] = A[s] * x[perm[s]]
 int launch_weights(const urchin_bvh* bvh, const double* x_orig, float* w32, double* w64,

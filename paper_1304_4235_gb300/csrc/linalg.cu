@@ -59,6 +59,29 @@ __global__ void __launch_bounds__(kSpmvThreads) k_spmv(SpmvArgs A)
     }
 }
 
+// One warp per ray: the ray's coefficient times each stored segment value is
+// added to z at the segment's particle.
+template <typename Real>
+__global__ void __launch_bounds__(kSpmvThreads) k_spmv_t(SpmvTArgs A)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (kSpmvThreads / 32);
+    const int64_t total = (int64_t)A.R * A.n_items;
+    const Real* val = static_cast<const Real*>(A.val);
+    const Real* coef = static_cast<const Real*>(A.coef);
+    for (int64_t w = (int64_t)blockIdx.x * (kSpmvThreads / 32) + (threadIdx.x >> 5); w < total; w += warps) {
+        const Real c = coef[w];
+        if (c == Real(0)) continue;
+        const int64_t k = w / A.n_items;
+        const int64_t a = w - k * A.n_items;
+        const int64_t i = A.items ? (int64_t)A.items[a] : a;
+        const int64_t row = k * A.n_rows_per_k + i;
+        const int64_t beg = (int64_t)A.row_ptr[row], end = (int64_t)A.row_ptr[row + 1];
+        for (int64_t e = beg + lane; e < end; e += 32)
+            atomicAdd(A.z + __ldcs(A.col + e), (double)(c * __ldcs(val + e)));
+    }
+}
+
 // partial[i * nb + b] = sum over block b's share of V_i . w
 __global__ void k_dots(const double* __restrict__ V, int64_t ld, int count, const double* __restrict__ w,
                        int64_t n, double* partial)
@@ -136,6 +159,20 @@ int launch_spmv(const SpmvArgs& A, cudaStream_t s)
     if (need < grid) grid = (int)std::max<int64_t>(need, 1);
     if (A.precision == URCHIN_F64) k_spmv<double><<<grid, kSpmvThreads, 0, s>>>(A);
     else k_spmv<float><<<grid, kSpmvThreads, 0, s>>>(A);
+    return launched();
+}
+
+int launch_spmv_t(const SpmvTArgs& A, cudaStream_t s)
+{
+    if (A.n_items <= 0) return URCHIN_OK;
+    int64_t warps = (int64_t)A.R * A.n_items;
+    int grid = 0;
+    const void* fn = A.precision == URCHIN_F64 ? (const void*)k_spmv_t<double> : (const void*)k_spmv_t<float>;
+    URCHIN_TRY(grid_for(fn, kSpmvThreads, 0, &grid));
+    int64_t need = (warps + 7) / 8;
+    if (need < grid) grid = (int)std::max<int64_t>(need, 1);
+    if (A.precision == URCHIN_F64) k_spmv_t<double><<<grid, kSpmvThreads, 0, s>>>(A);
+    else k_spmv_t<float><<<grid, kSpmvThreads, 0, s>>>(A);
     return launched();
 }
 

@@ -397,6 +397,152 @@ __global__ void k_set_x_from_u(const int32_t* __restrict__ items, int64_t n_act,
     }
 }
 
+// out[b] += *v
+__global__ void k_add_scalar(double* out, int F, const double* __restrict__ v)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < F) out[b] += *v;
+}
+
+// per-particle state (original order): bit 0 case B latched, bit 1 frozen
+__global__ void k_state_out(const int32_t* __restrict__ perm, const uint8_t* __restrict__ active,
+                            const uint8_t* __restrict__ latch, int64_t n, int case_rule, uint8_t* state)
+{
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
+        const bool caseB = case_rule == URCHIN_CASE_B || (case_rule == URCHIN_CASE_AUTO && latch[s]);
+        state[perm[s]] = (uint8_t)((caseB ? 1 : 0) | (active[s] ? 0 : 2));
+    }
+}
+
+__global__ void k_state_in(const int32_t* __restrict__ perm, const uint8_t* __restrict__ state, int64_t n,
+                           uint8_t* active, uint8_t* latch, unsigned* status)
+{
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
+        const uint8_t st = state[perm[s]];
+        if (st & ~3u) atomicOr(status, kStInput);
+        active[s] = (st & 2) ? 0 : 1;
+        latch[s] = st & 1;
+    }
+}
+
+// b_a = x_bar_i x_i (the cotangent in u = ln x), i = items[a]
+__global__ void k_adj_rhs(const int32_t* __restrict__ items, int64_t na, const int32_t* __restrict__ perm,
+                          const double* __restrict__ xbar_orig, const double* __restrict__ x, double* b)
+{
+    for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < na; a += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t i = items[a];
+        b[a] = xbar_orig[perm[i]] * x[i];
+    }
+}
+
+// ray coefficients of J_u^T nu: coef[k na + a] = nu_a (E_a / x_a) c_ak, where
+// c_ak = d ln E_a / d tau_ak from the sweep kernel
+template <typename Real>
+__global__ void k_adj_coef(const int32_t* __restrict__ items, int64_t na, int R, const double* __restrict__ nu,
+                           const double* __restrict__ E, const double* __restrict__ x, const double* __restrict__ ctan,
+                           Real* coef)
+{
+    const int64_t total = na * (int64_t)R;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < total; r += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t a = r % na;
+        coef[r] = (Real)(nu[a] * (E[a] / x[items[a]]) * ctan[r]);
+    }
+}
+
+// out_a = nu_a - x_i z_i: (I - J_u^T) nu from the scattered z = J^T (nu / x)
+__global__ void k_adj_apply(const int32_t* __restrict__ items, int64_t na, const double* __restrict__ nu,
+                            const double* __restrict__ x, const double* __restrict__ z, double* out)
+{
+    for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < na; a += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t i = items[a];
+        out[a] = nu[a] - x[i] * z[i];
+    }
+}
+
+// frozen particles f: t_f = (x_bar_f + z_f) dx_f/dGamma at Gamma_thin (their
+// x = x_thin depends on Gamma_thin = sum_b w_b); 0 for the others; one_s = 1
+__global__ void k_adj_frozen(const uint8_t* __restrict__ active, const int32_t* __restrict__ perm,
+                             const double* __restrict__ xbar_orig, const double* __restrict__ z,
+                             const double* __restrict__ x, const double* __restrict__ nH,
+                             const double* __restrict__ aA, const double* __restrict__ aB,
+                             const double* __restrict__ gc, int64_t n, double gthin, double y, int case_rule,
+                             double* t, double* one)
+{
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
+        one[s] = 1.0;
+        if (active[s]) {
+            t[s] = 0.0;
+            continue;
+        }
+        const double alpha = case_rule == URCHIN_CASE_B ? aB[s] : aA[s];
+        t[s] = (xbar_orig[perm[s]] + z[s]) * dx_dgamma(x[s], nH[s], alpha, gc[s], gthin, y);
+    }
+}
+
+// Per-ray coefficients of the active particles' w_bar term:
+//   w_bar_b += sum_a phi_a (1/R) sum_k exp(-s_b tau_ak) / Gamma_a,
+//   phi_a = nu_a (E_a / x_a) elas_a,  elas_a = Gamma_a (dE_a/dGamma_a) / E_a,
+// as lc = ln|phi_a / (R Gamma_thin)| - ln(Gamma_a / Gamma_thin), sg = sign
+// (Gamma_a recomputed in double from tau with the factored log-sum-exp).
+template <typename Real>
+__global__ void k_adj_wcoef(const int32_t* __restrict__ items, int64_t na, int R, const Real* __restrict__ tau,
+                            const double* __restrict__ sv, const double* __restrict__ wv, int F,
+                            const double* __restrict__ nu, const double* __restrict__ E, const double* __restrict__ x,
+                            const double* __restrict__ nH, const double* __restrict__ aA,
+                            const double* __restrict__ aB, const double* __restrict__ gc,
+                            const uint8_t* __restrict__ latch, int case_rule, double y, double* lc, double* sg)
+{
+    extern __shared__ double sm[];
+    double* ss = sm;
+    double* ws = sm + F;
+    __shared__ double sh[2];
+    if (threadIdx.x == 0) {
+        double g = 0.0, m = sv[0];
+        for (int b = 0; b < F; ++b) {
+            g += wv[b];
+            m = fmin(m, sv[b]);
+        }
+        sh[0] = g;
+        sh[1] = m;
+    }
+    __syncthreads();
+    const double gthin = sh[0], smin = sh[1];
+    for (int b = threadIdx.x; b < F; b += blockDim.x) {
+        ss[b] = sv[b] - smin;
+        ws[b] = wv[b] / gthin;
+    }
+    __syncthreads();
+    for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < na; a += (int64_t)gridDim.x * blockDim.x) {
+        double m = -INFINITY, acc = 0.0;
+        for (int k = 0; k < R; ++k) {            // streaming log-sum-exp over rays
+            const double t = (double)tau[a + (int64_t)k * na];
+            double S = 0.0;
+            for (int b = 0; b < F; ++b) S += ws[b] * exp(-ss[b] * t);
+            const double l = -smin * t + log(S);
+            if (!(l > -INFINITY)) continue;      // a ray with no transmitted flux adds nothing
+            if (l > m) {
+                acc = acc * exp(m - l) + 1.0;
+                m = l;
+            } else {
+                acc += exp(l - m);
+            }
+        }
+        const double lnr = m + log(acc / (double)R);      // ln(Gamma_a / Gamma_thin)
+        const int32_t i = items[a];
+        const double G = gthin * exp(lnr);
+        const bool caseB = case_rule == URCHIN_CASE_B || (case_rule == URCHIN_CASE_AUTO && latch[i]);
+        const double alpha = caseB ? aB[i] : aA[i];
+        const double elas = G > 0.0 ? G * dx_dgamma(E[a], nH[i], alpha, gc[i], G, y) / E[a] : 0.0;
+        const double phi = nu[a] * (E[a] / x[i]) * elas;
+        const double l0 = phi != 0.0 ? log(fabs(phi) / ((double)R * gthin)) - lnr : -INFINITY;
+        const double sgn = phi < 0.0 ? -1.0 : 1.0;
+        for (int k = 0; k < R; ++k) {
+            lc[a + (int64_t)k * na] = l0;
+            sg[a + (int64_t)k * na] = sgn;
+        }
+    }
+}
+
 }  // namespace
 
 int launch_sweep(const SweepArgs& A, cudaStream_t s)
@@ -1210,6 +1356,165 @@ int Solver::anderson()
     return URCHIN_OK;
 }
 
+// z[j] += sum over the active rays (k, a) of coef[k na + a] A_j K_ajk, for
+// every particle j (Morton): the transpose of the columns, by a scatter
+// traversal or over the stored segments.
+int Solver::transpose_columns(const void* coef, double* z)
+{
+    stats.traversals += 1;
+    stats.rays += n_act * P.R;
+    if (stored) {
+        SpmvTArgs A{};
+        A.row_ptr = row_ptr;
+        A.col = seg_col;
+        A.val = seg_val;
+        A.coef = coef;
+        A.items = list;
+        A.n_items = n_act;
+        A.n_rows_per_k = n;
+        A.R = P.R;
+        A.precision = P.precision;
+        A.z = z;
+        cudaEvent_t stop;
+        URCHIN_TRY(begin_timed(1, &stop));
+        URCHIN_TRY(launch_spmv_t(A, s));
+        return end_timed(stop);
+    }
+    TraceJob job{};
+    job.bvh = bvh;
+    job.dirs_dev = dirs;
+    job.R = P.R;
+    job.l_ray = P.l_ray;
+    job.items = list;
+    job.n_items = n_act;
+    job.row_stride = 1;
+    job.k_stride = n_act;
+    job.out_row = nullptr;
+    job.kernel = P.kernel;
+    job.precision = P.precision;
+    job.mode = 3;
+    job.coef = coef;
+    job.xbar = z;
+    return timed_trace(job);
+}
+
+// Reverse mode at a converged state x* (held in x): with the cases and the
+// frozen set of the forward solve (state), solve
+//   (I - J_u^T) nu = x_bar (.) x*        (J_u: sweep-map Jacobian in ln x)
+// by restarted GMRES, each product one transposed column pass, then
+//   w_bar_b += sum_a nu_a (E_a/x_a) elas_a dGamma_a/dw_b / Gamma_a
+//            + [cold start] sum_f (x_bar_f + (J^T mu)_f) dx_f/dGamma(Gamma_thin),
+// the frozen particles' x_thin depending on Gamma_thin = sum_b w_b.
+int Solver::adjoint(const uint8_t* state_orig, const double* xbar_orig, int cold_start, double* w_bar)
+{
+    const unsigned gn = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 4096));
+    k_state_in<<<gn, 256, 0, s>>>(bvh->perm, state_orig, n, active, latch, status);
+    URCHIN_TRY(launched());
+    uint32_t* cnt = reinterpret_cast<uint32_t*>(misc + 2);
+    URCHIN_TRY(compact_indices(active, n, list, cnt, comp_tmp, s));
+    uint32_t hc = 0;
+    URCHIN_TRY_CUDA(cudaMemcpyAsync(&hc, cnt, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    double mrel;
+    unsigned st;
+    URCHIN_TRY(read_scalars(&mrel, &st));
+    if (st & kStInput) return set_error(URCHIN_ERR_ARG, "urchin_solve_vjp: state values must be in 0..3");
+    n_act = hc;
+    stats.n_active = n_act;
+    if (P.segments != URCHIN_SEG_RECOMPUTE) URCHIN_TRY(columns(nullptr, n, 1));   // builds the stored segments
+    const int64_t na = n_act;
+    const int m = P.gmres_m;
+    const size_t rsz = f64 ? sizeof(double) : sizeof(float);
+    const int64_t nr = std::max<int64_t>(na * P.R, 1);
+    Layout lay;
+    size_t o_E = lay.take(sizeof(double) * (size_t)std::max<int64_t>(na, 1));
+    size_t o_c = lay.take(sizeof(double) * (size_t)nr);
+    size_t o_b = lay.take(sizeof(double) * (size_t)std::max<int64_t>(na, 1));
+    size_t o_nu = lay.take(sizeof(double) * (size_t)std::max<int64_t>(na, 1));
+    size_t o_V0 = lay.take(sizeof(double) * (size_t)std::max<int64_t>(na, 1));
+    size_t o_cf = lay.take(rsz * (size_t)nr);
+    size_t o_z = lay.take(sizeof(double) * (size_t)n);
+    size_t o_t = lay.take(sizeof(double) * (size_t)n);
+    size_t o_one = lay.take(sizeof(double) * (size_t)n);
+    size_t o_lc = lay.take(sizeof(double) * (size_t)nr);
+    size_t o_sg = lay.take(sizeof(double) * (size_t)nr);
+    size_t o_dt = lay.take(dots_tmp_bytes(2));
+    size_t o_h = lay.take(sizeof(double) * 4);
+    size_t o_g = lay.take(gmres_work_bytes(std::max<int64_t>(na, 1), m));
+    URCHIN_TRY(nk.alloc(lay.bytes, s));
+    double* E = nk.at<double>(o_E);
+    double* ctan = nk.at<double>(o_c);
+    double* b = nk.at<double>(o_b);
+    double* nu = nk.at<double>(o_nu);
+    double* V0 = nk.at<double>(o_V0);
+    void* coef = nk.at<void>(o_cf);
+    double* z = nk.at<double>(o_z);
+    double* t = nk.at<double>(o_t);
+    double* one = nk.at<double>(o_one);
+    double* lc = nk.at<double>(o_lc);
+    double* sg = nk.at<double>(o_sg);
+    double* dtmp = nk.at<double>(o_dt);
+    double* hdev = nk.at<double>(o_h);
+    void* gw = nk.at<void>(o_g);
+    const unsigned ga = (unsigned)std::max<int64_t>(1, std::min<int64_t>((na + 255) / 256, 2048));
+    const unsigned gr = (unsigned)std::max<int64_t>(1, std::min<int64_t>((nr + 255) / 256, 4096));
+    GmresResult gres;
+    if (na > 0) {
+        // E, c_ak and the columns at x*, cases held at the forward solve's
+        double norm;
+        int64_t sw;
+        URCHIN_TRY(evaluate(1, V0, E, ctan, dtmp, hdev, &mrel, &norm, &sw, 1));
+        k_adj_rhs<<<ga, 256, 0, s>>>(list, na, bvh->perm, xbar_orig, x, b);
+        URCHIN_TRY(launched());
+        auto matvec = [&](const double* v, double* out) -> int {
+            if (f64) k_adj_coef<double><<<gr, 256, 0, s>>>(list, na, P.R, v, E, x, ctan, static_cast<double*>(coef));
+            else k_adj_coef<float><<<gr, 256, 0, s>>>(list, na, P.R, v, E, x, ctan, static_cast<float*>(coef));
+            URCHIN_TRY(launched());
+            URCHIN_TRY_CUDA(cudaMemsetAsync(z, 0, sizeof(double) * (size_t)n, s));
+            URCHIN_TRY(transpose_columns(coef, z));
+            k_adj_apply<<<ga, 256, 0, s>>>(list, na, v, x, z, out);
+            return launched();
+        };
+        URCHIN_TRY(gmres_solve(matvec, b, nu, na, m, P.tol, P.max_iter, gw, &gres, s));
+        stats.iterations = gres.matvecs;
+        stats.max_rel_dx = gres.rel_residual;
+        stats.converged = gres.rel_residual <= P.tol ? 1 : 0;
+        // active particles: w_bar_b += sum_a phi_a rho_ab
+        const size_t smem = sizeof(double) * 2 * (size_t)P.spectrum.F;
+        const void* fw = f64 ? (const void*)k_adj_wcoef<double> : (const void*)k_adj_wcoef<float>;
+        if (smem > 48 * 1024)
+            URCHIN_TRY_CUDA(cudaFuncSetAttribute(fw, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        if (f64)
+            k_adj_wcoef<double><<<ga, 256, smem, s>>>(list, na, P.R, static_cast<const double*>(tau), P.spectrum.s,
+                                                      P.spectrum.w, P.spectrum.F, nu, E, x, nH, aA, aB, gc, latch,
+                                                      P.case_rule, P.y, lc, sg);
+        else
+            k_adj_wcoef<float><<<ga, 256, smem, s>>>(list, na, P.R, static_cast<const float*>(tau), P.spectrum.s,
+                                                     P.spectrum.w, P.spectrum.F, nu, E, x, nH, aA, aB, gc, latch,
+                                                     P.case_rule, P.y, lc, sg);
+        URCHIN_TRY(launched());
+        URCHIN_TRY(launch_wbar(tau, P.precision, na * P.R, lc, sg, P.spectrum.s, P.spectrum.F, w_bar, s));
+        // z = J^T mu over every particle, for the frozen term
+        if (f64) k_adj_coef<double><<<gr, 256, 0, s>>>(list, na, P.R, nu, E, x, ctan, static_cast<double*>(coef));
+        else k_adj_coef<float><<<gr, 256, 0, s>>>(list, na, P.R, nu, E, x, ctan, static_cast<float*>(coef));
+        URCHIN_TRY(launched());
+        URCHIN_TRY_CUDA(cudaMemsetAsync(z, 0, sizeof(double) * (size_t)n, s));
+        URCHIN_TRY(transpose_columns(coef, z));
+    } else {
+        URCHIN_TRY_CUDA(cudaMemsetAsync(z, 0, sizeof(double) * (size_t)n, s));
+        stats.converged = 1;
+    }
+    if (cold_start && na < n) {
+        k_adj_frozen<<<gn, 256, 0, s>>>(active, bvh->perm, xbar_orig, z, x, nH, aA, aB, gc, n, gthin, P.y,
+                                         P.case_rule, t, one);
+        URCHIN_TRY(launched());
+        URCHIN_TRY(launch_dots(t, n, 1, one, n, dtmp, hdev, s));
+        k_add_scalar<<<(P.spectrum.F + 255) / 256, 256, 0, s>>>(w_bar, P.spectrum.F, hdev);
+        URCHIN_TRY(launched());
+    }
+    URCHIN_TRY(read_scalars(&mrel, &st));
+    return URCHIN_OK;
+}
+
 // Sweep-map tangent at the current x (see urchin_tangent): one traversal for
 // E and the factors c_ik, one for the columns of x v.
 int Solver::tangent(const double* v_orig, double* E_orig, double* dlnE_orig)
@@ -1264,8 +1569,10 @@ int Solver::tangent(const double* v_orig, double* E_orig, double* dlnE_orig)
 int Solver::finish(double* x_inout)
 {
     unsigned grid = (unsigned)std::min<int64_t>((n + 255) / 256, 4096);
-    k_finish<<<grid, 256, 0, s>>>(bvh->perm, x, n, x_inout);
-    URCHIN_TRY(launched());
+    if (x_inout) {
+        k_finish<<<grid, 256, 0, s>>>(bvh->perm, x, n, x_inout);
+        URCHIN_TRY(launched());
+    }
     if (P.profile) {
         unsigned long long h[3] = {0, 0, 0};
         URCHIN_TRY_CUDA(cudaMemcpyAsync(h, hits, sizeof(h), cudaMemcpyDeviceToHost, s));
@@ -1336,6 +1643,42 @@ extern "C" int urchin_tangent(const urchin_bvh* bvh, const urchin_solve_params* 
     return st;
 }
 
+namespace urchin {
+namespace {
+
+int check_solve_params(const char* fn, const urchin_bvh* bvh, const urchin_solve_params* P, const void* x)
+{
+    if (!bvh || !P || !x) return set_error(URCHIN_ERR_ARG, "%s: NULL bvh, params or x", fn);
+    if (P->R < 1 || P->R > URCHIN_MAX_RAYS || !P->dirs)
+        return set_error(URCHIN_ERR_ARG, "%s: bad ray set (R = %d)", fn, P->R);
+    for (int k = 0; k < P->R; ++k) {
+        const double* d = P->dirs + 3 * k;
+        double nn = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        if (!std::isfinite(nn) || std::fabs(nn - 1.0) > 1e-6)
+            return set_error(URCHIN_ERR_ARG, "%s: direction %d is not a unit vector", fn, k);
+    }
+    if (!(P->l_ray >= 0.0) || !std::isfinite(P->l_ray)) return set_error(URCHIN_ERR_ARG, "%s: bad l_ray", fn);
+    if (P->spectrum.F < 1 || P->spectrum.F > URCHIN_MAX_BINS || !P->spectrum.s || !P->spectrum.w)
+        return set_error(URCHIN_ERR_ARG, "%s: bad spectrum", fn);
+    if (!P->nH || !P->T) return set_error(URCHIN_ERR_ARG, "%s: NULL nH or T", fn);
+    if (!(P->tol > 0.0) || !(P->tau_skip >= 0.0) || P->max_iter < 1 || !(P->y >= 0.0))
+        return set_error(URCHIN_ERR_ARG, "%s: need tol > 0, tau_skip >= 0, max_iter >= 1, y >= 0", fn);
+    if (P->kernel != URCHIN_KERNEL_M4 && P->kernel != URCHIN_KERNEL_GT)
+        return set_error(URCHIN_ERR_ARG, "%s: unknown kernel", fn);
+    if (P->precision != URCHIN_F32 && P->precision != URCHIN_F64)
+        return set_error(URCHIN_ERR_ARG, "%s: unknown precision", fn);
+    if (P->case_rule != URCHIN_CASE_A && P->case_rule != URCHIN_CASE_B && P->case_rule != URCHIN_CASE_AUTO)
+        return set_error(URCHIN_ERR_ARG, "%s: unknown case_rule", fn);
+    if (P->method != URCHIN_METHOD_PLAIN && P->method != URCHIN_METHOD_NEWTON && P->method != URCHIN_METHOD_ANDERSON)
+        return set_error(URCHIN_ERR_ARG, "%s: unknown method", fn);
+    if (P->segments != URCHIN_SEG_RECOMPUTE && P->segments != URCHIN_SEG_STORE && P->segments != URCHIN_SEG_AUTO)
+        return set_error(URCHIN_ERR_ARG, "%s: unknown segments mode", fn);
+    return URCHIN_OK;
+}
+
+}  // namespace
+}  // namespace urchin
+
 extern "C" int urchin_solve(const urchin_bvh* bvh, const urchin_solve_params* P, double* x_inout,
                             urchin_solve_stats* stats, urchin_stream_t stream)
 {
@@ -1343,37 +1686,18 @@ extern "C" int urchin_solve(const urchin_bvh* bvh, const urchin_solve_params* P,
     clear_error();
     auto t0 = std::chrono::steady_clock::now();
     if (stats) memset(stats, 0, sizeof(*stats));
-    if (!bvh || !P || !x_inout) return set_error(URCHIN_ERR_ARG, "urchin_solve: NULL bvh, params or x_inout");
-    if (P->R < 1 || P->R > URCHIN_MAX_RAYS || !P->dirs)
-        return set_error(URCHIN_ERR_ARG, "urchin_solve: bad ray set (R = %d)", P->R);
-    for (int k = 0; k < P->R; ++k) {
-        const double* d = P->dirs + 3 * k;
-        double nn = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-        if (!std::isfinite(nn) || std::fabs(nn - 1.0) > 1e-6)
-            return set_error(URCHIN_ERR_ARG, "urchin_solve: direction %d is not a unit vector", k);
-    }
-    if (!(P->l_ray >= 0.0) || !std::isfinite(P->l_ray)) return set_error(URCHIN_ERR_ARG, "urchin_solve: bad l_ray");
-    if (P->spectrum.F < 1 || P->spectrum.F > URCHIN_MAX_BINS || !P->spectrum.s || !P->spectrum.w)
-        return set_error(URCHIN_ERR_ARG, "urchin_solve: bad spectrum");
-    if (!P->nH || !P->T) return set_error(URCHIN_ERR_ARG, "urchin_solve: NULL nH or T");
-    if (!(P->tol > 0.0) || !(P->tau_skip >= 0.0) || P->max_iter < 1 || !(P->y >= 0.0))
-        return set_error(URCHIN_ERR_ARG, "urchin_solve: need tol > 0, tau_skip >= 0, max_iter >= 1, y >= 0");
-    if (P->kernel != URCHIN_KERNEL_M4 && P->kernel != URCHIN_KERNEL_GT)
-        return set_error(URCHIN_ERR_ARG, "urchin_solve: unknown kernel");
-    if (P->precision != URCHIN_F32 && P->precision != URCHIN_F64)
-        return set_error(URCHIN_ERR_ARG, "urchin_solve: unknown precision");
-    if (P->case_rule != URCHIN_CASE_A && P->case_rule != URCHIN_CASE_B && P->case_rule != URCHIN_CASE_AUTO)
-        return set_error(URCHIN_ERR_ARG, "urchin_solve: unknown case_rule");
-    if (P->method != URCHIN_METHOD_PLAIN && P->method != URCHIN_METHOD_NEWTON && P->method != URCHIN_METHOD_ANDERSON)
-        return set_error(URCHIN_ERR_ARG, "urchin_solve: unknown method");
-    if (P->segments != URCHIN_SEG_RECOMPUTE && P->segments != URCHIN_SEG_STORE && P->segments != URCHIN_SEG_AUTO)
-        return set_error(URCHIN_ERR_ARG, "urchin_solve: unknown segments mode");
+    URCHIN_TRY(check_solve_params("urchin_solve", bvh, P, x_inout));
     if (P->method != URCHIN_METHOD_PLAIN && (P->gmres_m < 1 || P->gmres_m > 64))
         return set_error(URCHIN_ERR_ARG, "urchin_solve: gmres_m must be in [1, 64]");
     cudaStream_t s = (cudaStream_t)stream;
     Solver S;
     int st = S.init(bvh, P, x_inout, s);
     if (st == URCHIN_OK) st = S.run();
+    if (st == URCHIN_OK && P->state) {
+        unsigned grid = (unsigned)std::min<int64_t>((S.n + 255) / 256, 4096);
+        k_state_out<<<grid, 256, 0, s>>>(bvh->perm, S.active, S.latch, S.n, P->case_rule, P->state);
+        st = launched();
+    }
     if (st == URCHIN_OK) st = S.finish(x_inout);
     else cudaStreamSynchronize(s);
     S.stats.wall_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -1381,6 +1705,38 @@ extern "C" int urchin_solve(const urchin_bvh* bvh, const urchin_solve_params* P,
     if (st != URCHIN_OK) return st;
     if (!S.stats.converged)
         return set_error(URCHIN_ERR_NOT_CONVERGED, "urchin_solve: max |dx|/x = %.3e after %d iterations",
+                         S.stats.max_rel_dx, S.stats.iterations);
+    return URCHIN_OK;
+}
+
+extern "C" int urchin_solve_vjp(const urchin_bvh* bvh, const urchin_solve_params* P, const double* x_star,
+                                const double* x_bar, double* w_bar, urchin_solve_stats* stats,
+                                urchin_stream_t stream)
+{
+    using namespace urchin;
+    clear_error();
+    auto t0 = std::chrono::steady_clock::now();
+    if (stats) memset(stats, 0, sizeof(*stats));
+    URCHIN_TRY(check_solve_params("urchin_solve_vjp", bvh, P, x_star));
+    if (!x_bar || !w_bar || !P->state)
+        return set_error(URCHIN_ERR_ARG, "urchin_solve_vjp: NULL x_bar, w_bar or params->state");
+    if (P->gmres_m < 1 || P->gmres_m > 64)
+        return set_error(URCHIN_ERR_ARG, "urchin_solve_vjp: gmres_m must be in [1, 64]");
+    urchin_solve_params Q = *P;
+    Q.warm_start = 1;                      // x = x*
+    Q.history_maxrel = nullptr;
+    Q.history_unconverged = nullptr;
+    cudaStream_t s = (cudaStream_t)stream;
+    Solver S;
+    int st = S.init(bvh, &Q, const_cast<double*>(x_star), s);
+    if (st == URCHIN_OK) st = S.adjoint(P->state, x_bar, P->warm_start ? 0 : 1, w_bar);
+    if (st == URCHIN_OK) st = S.finish(nullptr);
+    else cudaStreamSynchronize(s);
+    S.stats.wall_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (stats) *stats = S.stats;
+    if (st != URCHIN_OK) return st;
+    if (!S.stats.converged)
+        return set_error(URCHIN_ERR_NOT_CONVERGED, "urchin_solve_vjp: GMRES relative residual %.3e after %d products",
                          S.stats.max_rel_dx, S.stats.iterations);
     return URCHIN_OK;
 }

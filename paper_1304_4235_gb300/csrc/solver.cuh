@@ -126,6 +126,9 @@ struct Solver {
     }
     int finish(double* x_inout);
     int tangent(const double* v_orig, double* E_orig, double* dlnE_orig);
+    // reverse mode at a converged state (urchin_solve_vjp)
+    int adjoint(const uint8_t* state_orig, const double* xbar_orig, int cold_start, double* w_bar);
+    int transpose_columns(const void* coef, double* z);   // z[j] += sum_rays coef A_j K (Morton, all j)
 };
 
 }  // namespace urchin

@@ -144,7 +144,176 @@ __global__ void k_equilibrium(const double* __restrict__ gamma, const float* __r
     }
 }
 
+// Reverse mode of Eq. gamma_shld, in double.  With c_o = gamma_bar_o / R:
+//   tau_bar_ok = -c_o sum_b w_b s_b exp(-s_b tau_ok)
+//              = -sign(c_o) exp(ln|c_o| - s_min tau_ok + ln sum_b w_b s_b exp(-(s_b - s_min) tau_ok)),
+// written so that a large |c_o| (deeply shielded origins) does not overflow
+// where exp(-s_min tau) underflows.
+template <typename Real>
+__global__ void k_gamma_vjp_tau(const Real* __restrict__ tau, int64_t n_rays, int R, const double* __restrict__ sv,
+                                const double* __restrict__ wv, int F, const double* __restrict__ gbar, Real* tau_bar)
+{
+    extern __shared__ double sm[];
+    double* ss = sm;
+    double* ws = sm + F;
+    __shared__ double smin_s;
+    for (int b = threadIdx.x; b < F; b += blockDim.x) {
+        ss[b] = sv[b];
+        ws[b] = wv[b] * sv[b];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = ss[0];
+        for (int b = 1; b < F; ++b) m = fmin(m, ss[b]);
+        smin_s = m;
+    }
+    __syncthreads();
+    const double smin = smin_s;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n_rays; r += (int64_t)gridDim.x * blockDim.x) {
+        const double c = gbar[r / R] / (double)R;
+        const double t = (double)tau[r];
+        double S = 0.0;
+        for (int b = 0; b < F; ++b) S += ws[b] * exp(-(ss[b] - smin) * t);
+        double v = 0.0;
+        if (c != 0.0 && S > 0.0) v = -copysign(exp(log(fabs(c)) - smin * t + log(S)), c);
+        tau_bar[r] = (Real)v;
+    }
+}
+
+// w_bar_b partial sums over rays r with a coefficient c_r = sg_r exp(lc_r):
+// partial[block * F + b] = sum over the block's rays of sg_r exp(lc_r - s_b tau_r).
+// Rays are staged in tiles; each thread owns a set of bins, so no two
+// threads add to the same sum.
+constexpr int kWTile = 128;
+template <typename Real>
+__global__ void k_wbar_tiles(const Real* __restrict__ tau, int64_t n_rays, const double* __restrict__ lc_in,
+                             const double* __restrict__ sg_in, const double* __restrict__ sv, int F, double* partial)
+{
+    extern __shared__ double sm[];
+    double* ss = sm;
+    double* acc = sm + F;
+    double* tt = acc + F;
+    double* lc = tt + kWTile;
+    double* sg = lc + kWTile;
+    for (int b = threadIdx.x; b < F; b += blockDim.x) {
+        ss[b] = sv[b];
+        acc[b] = 0.0;
+    }
+    const int64_t tiles = (n_rays + kWTile - 1) / kWTile;
+    for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < kWTile; i += blockDim.x) {
+            const int64_t r = tile * kWTile + i;
+            const bool in = r < n_rays;
+            tt[i] = in ? (double)tau[r] : 0.0;
+            lc[i] = in ? lc_in[r] : -INFINITY;
+            sg[i] = in ? sg_in[r] : 0.0;
+        }
+        __syncthreads();
+        for (int b = threadIdx.x; b < F; b += blockDim.x) {
+            const double sb = ss[b];
+            double a = acc[b];
+            for (int i = 0; i < kWTile; ++i) a += sg[i] * exp(lc[i] - sb * tt[i]);
+            acc[b] = a;
+        }
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < F; b += blockDim.x) partial[(int64_t)blockIdx.x * F + b] = acc[b];
+}
+
+// per-ray coefficient of Eq. gamma_shld's reverse mode: c_r = gamma_bar_o / R
+__global__ void k_gamma_coef(int64_t n_rays, int R, const double* __restrict__ gbar, double* lc, double* sg)
+{
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n_rays; r += (int64_t)gridDim.x * blockDim.x) {
+        const double c = gbar[r / R] / (double)R;
+        lc[r] = c != 0.0 ? log(fabs(c)) : -INFINITY;
+        sg[r] = c < 0.0 ? -1.0 : 1.0;
+    }
+}
+
+// out[b] += sum over blocks of partial[block * F + b] (fixed order)
+__global__ void k_sum_partials(const double* __restrict__ partial, int nb, int F, double* out)
+{
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < F; b += gridDim.x * blockDim.x) {
+        double t = 0.0;
+        for (int q = 0; q < nb; ++q) t += partial[(int64_t)q * F + b];
+        out[b] += t;
+    }
+}
+
+// gamma_bar_i = x_bar_i dx_i/dGamma_i (App. C3 root, case as in k_equilibrium)
+__global__ void k_equilibrium_vjp(const double* __restrict__ gamma, const float* __restrict__ tau_eff,
+                                  const double* __restrict__ nH, const double* __restrict__ T, int64_t n,
+                                  int case_rule, double y, const double* __restrict__ x_bar, double* gamma_bar)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        Rates r = hg97_rates(T[i]);
+        bool caseB = case_rule == URCHIN_CASE_B ||
+                     (case_rule == URCHIN_CASE_AUTO && tau_eff[i] >= 1.0f);
+        const double alpha = caseB ? r.alphaB : r.alphaA;
+        const double x = x_equilibrium(gamma[i], nH[i], alpha, r.gamma_c, y);
+        gamma_bar[i] = x_bar[i] * dx_dgamma(x, nH[i], alpha, r.gamma_c, gamma[i], y);
+    }
+}
+
+template <typename Real>
+int gamma_vjp_t(const Real* tau, int64_t n_orig, int R, const urchin_spectrum* sp, const double* gbar,
+                Real* tau_bar, double* w_bar, cudaStream_t s)
+{
+    const int64_t n_rays = n_orig * (int64_t)R;
+    const int F = sp->F;
+    if (tau_bar) {
+        const size_t smem = sizeof(double) * 2 * (size_t)F;
+        auto fn = k_gamma_vjp_tau<Real>;
+        if (smem > 48 * 1024)
+            URCHIN_TRY_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int grid = 0;
+        URCHIN_TRY(grid_for((const void*)fn, 256, smem, &grid));
+        grid = (int)std::max<int64_t>(1, std::min<int64_t>(grid, (n_rays + 255) / 256));
+        fn<<<grid, 256, smem, s>>>(tau, n_rays, R, sp->s, sp->w, F, gbar, tau_bar);
+        URCHIN_TRY(launched());
+    }
+    if (w_bar) {
+        Scratch cf;
+        URCHIN_TRY(cf.alloc(2 * sizeof(double) * (size_t)n_rays + 256, s));
+        double* lc = cf.at<double>(0);
+        double* sg = lc + n_rays;
+        const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n_rays + 255) / 256, 4096));
+        k_gamma_coef<<<g, 256, 0, s>>>(n_rays, R, gbar, lc, sg);
+        URCHIN_TRY(launched());
+        URCHIN_TRY(launch_wbar(tau, sizeof(Real) == 8 ? URCHIN_F64 : URCHIN_F32, n_rays, lc, sg, sp->s, F, w_bar, s));
+        cf.release();
+    }
+    return URCHIN_OK;
+}
+
 }  // namespace
+
+int launch_wbar(const void* tau, int precision, int64_t n_rays, const double* lc, const double* sg, const double* sv,
+                int F, double* w_bar, cudaStream_t s)
+{
+    if (n_rays <= 0) return URCHIN_OK;
+    const size_t smem = sizeof(double) * (2 * (size_t)F + 3 * kWTile);
+    const void* fn = precision == URCHIN_F64 ? (const void*)k_wbar_tiles<double> : (const void*)k_wbar_tiles<float>;
+    if (smem > 48 * 1024)
+        URCHIN_TRY_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int64_t tiles = (n_rays + kWTile - 1) / kWTile;
+    const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, 608));
+    Scratch part;
+    URCHIN_TRY(part.alloc(sizeof(double) * (size_t)nb * F, s));
+    if (precision == URCHIN_F64)
+        k_wbar_tiles<double><<<nb, 256, smem, s>>>(static_cast<const double*>(tau), n_rays, lc, sg, sv, F,
+                                                   part.at<double>(0));
+    else
+        k_wbar_tiles<float><<<nb, 256, smem, s>>>(static_cast<const float*>(tau), n_rays, lc, sg, sv, F,
+                                                  part.at<double>(0));
+    URCHIN_TRY(launched());
+    k_sum_partials<<<(F + 255) / 256, 256, 0, s>>>(part.at<double>(0), nb, F, w_bar);
+    URCHIN_TRY(launched());
+    part.release();
+    return URCHIN_OK;
+}
 
 int launch_gamma(const GammaJob& J, cudaStream_t s)
 {
@@ -208,4 +377,48 @@ extern "C" int urchin_equilibrium(const double* gamma, const float* tau_eff, con
     if (case_rule == URCHIN_CASE_AUTO && !tau_eff)
         return set_error(URCHIN_ERR_ARG, "urchin_equilibrium: CASE_AUTO needs tau_eff");
     return launch_equilibrium(gamma, tau_eff, nH, T, n, case_rule, y, x_out, (cudaStream_t)stream);
+}
+
+extern "C" int urchin_gamma_vjp(const void* tau, int precision, int64_t n_orig, int R, const urchin_spectrum* sp,
+                                const double* gamma_bar, void* tau_bar_out, double* w_bar, urchin_stream_t stream)
+{
+    using namespace urchin;
+    clear_error();
+    if (precision != URCHIN_F32 && precision != URCHIN_F64)
+        return set_error(URCHIN_ERR_ARG, "urchin_gamma_vjp: unknown precision %d", precision);
+    if (R < 1 || R > URCHIN_MAX_RAYS) return set_error(URCHIN_ERR_ARG, "urchin_gamma_vjp: R = %d out of range", R);
+    if (n_orig < 0) return set_error(URCHIN_ERR_ARG, "urchin_gamma_vjp: n_orig < 0");
+    if (!sp || !sp->s || !sp->w) return set_error(URCHIN_ERR_ARG, "urchin_gamma_vjp: NULL spectrum");
+    if (sp->F < 1 || sp->F > URCHIN_MAX_BINS)
+        return set_error(URCHIN_ERR_ARG, "urchin_gamma_vjp: F = %d out of range [1, %d]", sp->F, URCHIN_MAX_BINS);
+    if (n_orig == 0) return URCHIN_OK;
+    if (!tau || !gamma_bar) return set_error(URCHIN_ERR_ARG, "urchin_gamma_vjp: NULL tau or gamma_bar");
+    if (!tau_bar_out && !w_bar) return set_error(URCHIN_ERR_ARG, "urchin_gamma_vjp: no output requested");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (precision == URCHIN_F64)
+        return gamma_vjp_t<double>(static_cast<const double*>(tau), n_orig, R, sp, gamma_bar,
+                                   static_cast<double*>(tau_bar_out), w_bar, s);
+    return gamma_vjp_t<float>(static_cast<const float*>(tau), n_orig, R, sp, gamma_bar,
+                              static_cast<float*>(tau_bar_out), w_bar, s);
+}
+
+extern "C" int urchin_equilibrium_vjp(const double* gamma, const float* tau_eff, const double* nH, const double* T,
+                                      int64_t n, int case_rule, double y, const double* x_bar, double* gamma_bar_out,
+                                      urchin_stream_t stream)
+{
+    using namespace urchin;
+    clear_error();
+    if (n < 0) return set_error(URCHIN_ERR_ARG, "urchin_equilibrium_vjp: n < 0");
+    if (case_rule != URCHIN_CASE_A && case_rule != URCHIN_CASE_B && case_rule != URCHIN_CASE_AUTO)
+        return set_error(URCHIN_ERR_ARG, "urchin_equilibrium_vjp: unknown case_rule %d", case_rule);
+    if (!(y >= 0.0) || !std::isfinite(y)) return set_error(URCHIN_ERR_ARG, "urchin_equilibrium_vjp: y must be >= 0");
+    if (n == 0) return URCHIN_OK;
+    if (!gamma || !nH || !T || !x_bar || !gamma_bar_out)
+        return set_error(URCHIN_ERR_ARG, "urchin_equilibrium_vjp: NULL array");
+    if (case_rule == URCHIN_CASE_AUTO && !tau_eff)
+        return set_error(URCHIN_ERR_ARG, "urchin_equilibrium_vjp: CASE_AUTO needs tau_eff");
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned grid = (unsigned)std::min<int64_t>((n + 255) / 256, 4096);
+    k_equilibrium_vjp<<<grid, 256, 0, s>>>(gamma, tau_eff, nH, T, n, case_rule, y, x_bar, gamma_bar_out);
+    return launched();
 }

@@ -51,9 +51,12 @@ struct TraceParams {
     void* seg_val;                // MODE_FILL: A_j * chord integral (float or double)
     const float* A32;
     const double* A64;
+    // transpose mode
+    const void* coef;             // MODE_SCATTER: coefficient of each ray, indexed like out
+    double* xbar;                 // MODE_SCATTER: xbar[j] += coef * A_j * chord integral (Morton)
 };
 
-constexpr int MODE_TAU = 0, MODE_COUNT = 1, MODE_FILL = 2;
+constexpr int MODE_TAU = 0, MODE_COUNT = 1, MODE_FILL = 2, MODE_SCATTER = 3;
 
 // Where a ray's hits go: the running column sum, and in MODE_FILL the
 // cursor into the ray's stored segment list.
@@ -62,6 +65,7 @@ struct Sink {
     Real sum, comp;
     unsigned nhit, ntest;
     int64_t pos, end;
+    Real coef;                    // MODE_SCATTER
 };
 
 template <typename Real> struct RealOps;
@@ -304,6 +308,10 @@ __device__ __forceinline__ void leaf_hits_f32(const TraceParams& P, const float2
             if (KERNEL == URCHIN_KERNEL_M4) F = m4_part_f(beta2, u1, u2);
             else F = gt_chord<float>(P, beta2, u1, u2);
         }
+        if (MODE == MODE_SCATTER) {
+            atomicAdd(P.xbar + j, (double)(k.coef * (__ldg(P.A32 + j) * F)));
+            continue;
+        }
         Kahan::add(k.sum, k.comp, __ldg(P.w32 + j) * F);
         if (MODE == MODE_FILL) {
             if (k.pos < k.end) {
@@ -349,6 +357,11 @@ __device__ __forceinline__ void leaf_hits(const TraceParams& P, int ref, int cnt
             Real u2 = (fmin(L, tc + ch) - tc) * ih;
             if (KERNEL == URCHIN_KERNEL_M4) F = m4_part(beta2, u1, u2);
             else F = gt_chord(P, beta2, u1, u2);
+        }
+        if (MODE == MODE_SCATTER) {
+            const Real A = sizeof(Real) == 4 ? Real(__ldg(P.A32 + j)) : Real(__ldg(P.A64 + j));
+            atomicAdd(P.xbar + j, (double)(k.coef * (A * F)));
+            continue;
         }
         Kahan::add(k.sum, k.comp, O::weight(P, j) * F);
         if (MODE == MODE_FILL) {
@@ -462,22 +475,26 @@ __global__ void __launch_bounds__(256) k_trace(TraceParams P)
             float4 o = __ldg(P.xyzh + org);
             Real dx = Real(s_dirs[3 * k]), dy = Real(s_dirs[3 * k + 1]), dz = Real(s_dirs[3 * k + 2]);
             unsigned nvisit = 0;
-            Sink<Real> sk{Real(0), Real(0), 0u, 0u, 0, 0};
+            Sink<Real> sk{Real(0), Real(0), 0u, 0u, 0, 0, Real(0)};
             const int64_t ray = (int64_t)k * P.n_items + item;
             if (MODE == MODE_FILL) {
                 sk.pos = (int64_t)P.row_ptr[ray];
                 sk.end = (int64_t)P.row_ptr[ray + 1];
             }
-            ray_column<Real, KERNEL, MODE>(P, s_tab, o, dx, dy, dz, sk, err, nvisit);
+            const int64_t orow = P.out_row ? (int64_t)P.out_row[item] : item;
+            if (MODE == MODE_SCATTER)
+                sk.coef = static_cast<const Real*>(P.coef)[orow * P.row_stride + (int64_t)k * P.k_stride];
+            // a ray with a zero coefficient adds nothing: skip its traversal
+            if (MODE != MODE_SCATTER || sk.coef != Real(0))
+                ray_column<Real, KERNEL, MODE>(P, s_tab, o, dx, dy, dz, sk, err, nvisit);
             hits += sk.nhit;
             tests += sk.ntest;
             visits += nvisit;
             if (MODE == MODE_COUNT) {
                 P.counts[ray] = sk.nhit;
-            } else {
+            } else if (MODE != MODE_SCATTER) {
                 if (MODE == MODE_FILL && sk.pos != sk.end) err |= kStSegment;
-                int64_t row = P.out_row ? (int64_t)P.out_row[item] : item;
-                static_cast<Real*>(P.out)[row * P.row_stride + (int64_t)k * P.k_stride] = sk.sum;
+                static_cast<Real*>(P.out)[orow * P.row_stride + (int64_t)k * P.k_stride] = sk.sum;
             }
         }
     }
@@ -517,6 +534,7 @@ int dispatch_k(const TraceParams& P, int mode, cudaStream_t s)
 {
     if (mode == MODE_COUNT) return launch_one<Real, KERNEL, MODE_COUNT>(P, s);
     if (mode == MODE_FILL) return launch_one<Real, KERNEL, MODE_FILL>(P, s);
+    if (mode == MODE_SCATTER) return launch_one<Real, KERNEL, MODE_SCATTER>(P, s);
     return launch_one<Real, KERNEL, MODE_TAU>(P, s);
 }
 
@@ -608,6 +626,8 @@ int launch_trace(const TraceJob& job, cudaStream_t s)
     P.seg_val = job.seg_val;
     P.A32 = b->A32;
     P.A64 = b->A64;
+    P.coef = job.coef;
+    P.xbar = job.xbar;
     return dispatch_mode(P, job.precision, job.kernel, job.mode, s);
 }
 
@@ -649,6 +669,47 @@ __global__ void k_map_origins(const int32_t* __restrict__ origins, const int32_t
 
 }  // namespace urchin
 
+namespace urchin {
+namespace {
+
+// Argument checks shared by the column entry points (status 1 = valid no-op)
+int check_trace_args(const char* fn, const urchin_bvh* bvh, const void* x, const double* dirs, int R, double l_ray,
+                     const int32_t* origins, int64_t n_orig, int kernel, int precision, const void* buf)
+{
+    if (!bvh || !x || !dirs) return set_error(URCHIN_ERR_ARG, "%s: NULL bvh, input or dirs", fn);
+    if (R < 1 || R > URCHIN_MAX_RAYS)
+        return set_error(URCHIN_ERR_ARG, "%s: R = %d out of range [1, %d]", fn, R, URCHIN_MAX_RAYS);
+    if (!(l_ray >= 0.0) || !std::isfinite(l_ray))
+        return set_error(URCHIN_ERR_ARG, "%s: l_ray must be finite and >= 0", fn);
+    if (kernel != URCHIN_KERNEL_M4 && kernel != URCHIN_KERNEL_GT)
+        return set_error(URCHIN_ERR_ARG, "%s: unknown kernel %d", fn, kernel);
+    if (precision != URCHIN_F32 && precision != URCHIN_F64)
+        return set_error(URCHIN_ERR_ARG, "%s: unknown precision %d", fn, precision);
+    if (n_orig < 0) return set_error(URCHIN_ERR_ARG, "%s: n_orig < 0", fn);
+    if (n_orig == 0) return 1;
+    if (!origins && n_orig != bvh->n) return set_error(URCHIN_ERR_ARG, "%s: origins NULL requires n_orig == n", fn);
+    if (!buf) return set_error(URCHIN_ERR_ARG, "%s: output or cotangent array is NULL", fn);
+    for (int i = 0; i < 3 * R; ++i)
+        if (!std::isfinite(dirs[i])) return set_error(URCHIN_ERR_ARG, "%s: non-finite direction", fn);
+    for (int k = 0; k < R; ++k) {
+        double nn = dirs[3 * k] * dirs[3 * k] + dirs[3 * k + 1] * dirs[3 * k + 1] + dirs[3 * k + 2] * dirs[3 * k + 2];
+        if (std::fabs(nn - 1.0) > 1e-6)
+            return set_error(URCHIN_ERR_ARG, "%s: direction %d is not a unit vector", fn, k);
+    }
+    return URCHIN_OK;
+}
+
+// x_bar[perm[s]] += xm[s]
+__global__ void k_unpermute_add(const int32_t* __restrict__ perm, const double* __restrict__ xm, int64_t n,
+                                double* x_bar)
+{
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x)
+        x_bar[perm[s]] += xm[s];
+}
+
+}  // namespace
+}  // namespace urchin
+
 extern "C" int urchin_trace_columns(const urchin_bvh* bvh, const double* x, const double* dirs, int R,
                                     double l_ray, const int32_t* origins, int64_t n_orig, int kernel,
                                     int precision, void* tau_out, urchin_stream_t stream)
@@ -656,26 +717,10 @@ extern "C" int urchin_trace_columns(const urchin_bvh* bvh, const double* x, cons
     using namespace urchin;
     clear_error();
     cudaStream_t s = (cudaStream_t)stream;
-    if (!bvh || !x || !dirs) return set_error(URCHIN_ERR_ARG, "urchin_trace_columns: NULL bvh, x or dirs");
-    if (R < 1 || R > URCHIN_MAX_RAYS)
-        return set_error(URCHIN_ERR_ARG, "urchin_trace_columns: R = %d out of range [1, %d]", R, URCHIN_MAX_RAYS);
-    if (!(l_ray >= 0.0) || !std::isfinite(l_ray))
-        return set_error(URCHIN_ERR_ARG, "urchin_trace_columns: l_ray must be finite and >= 0");
-    if (kernel != URCHIN_KERNEL_M4 && kernel != URCHIN_KERNEL_GT)
-        return set_error(URCHIN_ERR_ARG, "urchin_trace_columns: unknown kernel %d", kernel);
-    if (precision != URCHIN_F32 && precision != URCHIN_F64)
-        return set_error(URCHIN_ERR_ARG, "urchin_trace_columns: unknown precision %d", precision);
-    if (n_orig < 0) return set_error(URCHIN_ERR_ARG, "urchin_trace_columns: n_orig < 0");
-    if (n_orig == 0) return URCHIN_OK;
-    if (!origins && n_orig != bvh->n)
-        return set_error(URCHIN_ERR_ARG, "urchin_trace_columns: origins NULL requires n_orig == n");
-    if (!tau_out) return set_error(URCHIN_ERR_ARG, "urchin_trace_columns: tau_out is NULL");
-    for (int i = 0; i < 3 * R; ++i)
-        if (!std::isfinite(dirs[i])) return set_error(URCHIN_ERR_ARG, "urchin_trace_columns: non-finite direction");
-    for (int k = 0; k < R; ++k) {
-        double nn = dirs[3 * k] * dirs[3 * k] + dirs[3 * k + 1] * dirs[3 * k + 1] + dirs[3 * k + 2] * dirs[3 * k + 2];
-        if (std::fabs(nn - 1.0) > 1e-6)
-            return set_error(URCHIN_ERR_ARG, "urchin_trace_columns: direction %d is not a unit vector", k);
+    {
+        const int c = check_trace_args("urchin_trace_columns", bvh, x, dirs, R, l_ray, origins, n_orig, kernel,
+                                       precision, tau_out);
+        if (c != URCHIN_OK) return c > 0 ? URCHIN_OK : c;
     }
     const int64_t n = bvh->n;
     const bool f64 = precision == URCHIN_F64;
@@ -726,5 +771,72 @@ extern "C" int urchin_trace_columns(const urchin_bvh* bvh, const double* x, cons
     if (st & kStOrigin) return set_error(URCHIN_ERR_ARG, "urchin_trace_columns: origin index out of range");
     if (st & kStStack) return set_error(URCHIN_ERR_CUDA, "urchin_trace_columns: traversal stack overflow");
     if (st & kStVisit) return set_error(URCHIN_ERR_CUDA, "urchin_trace_columns: malformed tree (visit limit)");
+    return URCHIN_OK;
+}
+
+extern "C" int urchin_trace_columns_vjp(const urchin_bvh* bvh, const double* dirs, int R, double l_ray,
+                                        const int32_t* origins, int64_t n_orig, int kernel, int precision,
+                                        const void* tau_bar, double* x_bar, urchin_stream_t stream)
+{
+    using namespace urchin;
+    clear_error();
+    cudaStream_t s = (cudaStream_t)stream;
+    {
+        const int c = check_trace_args("urchin_trace_columns_vjp", bvh, tau_bar ? tau_bar : (const void*)dirs,
+                                       dirs, R, l_ray, origins, n_orig, kernel, precision, x_bar);
+        if (c != URCHIN_OK) return c > 0 ? URCHIN_OK : c;
+        if (!tau_bar) return set_error(URCHIN_ERR_ARG, "urchin_trace_columns_vjp: tau_bar is NULL");
+    }
+    const int64_t n = bvh->n;
+    Layout lay;
+    size_t o_ctr = lay.take(2 * sizeof(unsigned));
+    size_t o_dirs = lay.take(sizeof(double) * 3 * (size_t)R);
+    size_t o_xm = lay.take(sizeof(double) * (size_t)n);
+    size_t o_items = lay.take(origins ? sizeof(int32_t) * (size_t)n_orig : 0);
+    Scratch scr;
+    URCHIN_TRY(scr.alloc(lay.bytes, s));
+    unsigned* ctr = scr.at<unsigned>(o_ctr);
+    double* xm = scr.at<double>(o_xm);
+    URCHIN_TRY_CUDA(cudaMemsetAsync(ctr, 0, 2 * sizeof(unsigned), s));
+    URCHIN_TRY_CUDA(cudaMemsetAsync(xm, 0, sizeof(double) * (size_t)n, s));
+    URCHIN_TRY_CUDA(cudaMemcpyAsync(scr.at<double>(o_dirs), dirs, sizeof(double) * 3 * (size_t)R,
+                                    cudaMemcpyHostToDevice, s));
+    TraceJob job{};
+    job.bvh = bvh;
+    job.dirs_dev = scr.at<double>(o_dirs);
+    job.R = R;
+    job.l_ray = l_ray;
+    job.n_items = n_orig;
+    job.row_stride = R;
+    job.k_stride = 1;
+    job.kernel = kernel;
+    job.precision = precision;
+    job.counter = ctr;
+    job.status = ctr + 1;
+    job.mode = 3;
+    job.coef = tau_bar;
+    job.xbar = xm;
+    if (origins) {
+        int32_t* items = scr.at<int32_t>(o_items);
+        unsigned grid = (unsigned)std::min<int64_t>((n_orig + 255) / 256, 4096);
+        k_map_origins<<<grid, 256, 0, s>>>(origins, bvh->inv, n_orig, n, items, ctr + 1);
+        URCHIN_TRY(launched());
+        job.items = items;
+        job.out_row = nullptr;
+    } else {
+        job.items = nullptr;
+        job.out_row = bvh->perm;
+    }
+    URCHIN_TRY(launch_trace(job, s));
+    unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 4096));
+    k_unpermute_add<<<grid, 256, 0, s>>>(bvh->perm, xm, n, x_bar);
+    URCHIN_TRY(launched());
+    unsigned st = 0;
+    URCHIN_TRY_CUDA(cudaMemcpyAsync(&st, ctr + 1, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    scr.release();
+    URCHIN_TRY_CUDA(cudaStreamSynchronize(s));
+    if (st & kStOrigin) return set_error(URCHIN_ERR_ARG, "urchin_trace_columns_vjp: origin index out of range");
+    if (st & kStStack) return set_error(URCHIN_ERR_CUDA, "urchin_trace_columns_vjp: traversal stack overflow");
+    if (st & kStVisit) return set_error(URCHIN_ERR_CUDA, "urchin_trace_columns_vjp: malformed tree (visit limit)");
     return URCHIN_OK;
 }

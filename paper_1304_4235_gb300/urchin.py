@@ -56,7 +56,8 @@ class urchin_solve_params(C.Structure):
                 ("method", C.c_int), ("segments", C.c_int), ("gmres_m", C.c_int),
                 ("kernel", C.c_int), ("precision", C.c_int), ("case_rule", C.c_int),
                 ("warm_start", C.c_int), ("profile", C.c_int), ("history_maxrel", _vp),
-                ("history_unconverged", _vp), ("blocks", C.c_int), ("newton_switch", C.c_double)]
+                ("history_unconverged", _vp), ("blocks", C.c_int), ("newton_switch", C.c_double),
+                ("state", _vp)]
 
 
 class urchin_solve_stats(C.Structure):
@@ -101,6 +102,13 @@ SIGNATURES = {
     "urchin_solve": (C.c_int, [_vp, C.POINTER(urchin_solve_params), _vp,
                                C.POINTER(urchin_solve_stats), _vp]),
     "urchin_tangent": (C.c_int, [_vp, C.POINTER(urchin_solve_params), _vp, _vp, _vp, _vp, _vp]),
+    "urchin_trace_columns_vjp": (C.c_int, [_vp, _vp, C.c_int, C.c_double, _vp, C.c_int64, C.c_int, C.c_int,
+                                           _vp, _vp, _vp]),
+    "urchin_gamma_vjp": (C.c_int, [_vp, C.c_int, C.c_int64, C.c_int, C.POINTER(urchin_spectrum), _vp, _vp, _vp,
+                                   _vp]),
+    "urchin_equilibrium_vjp": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int64, C.c_int, C.c_double, _vp, _vp, _vp]),
+    "urchin_solve_vjp": (C.c_int, [_vp, C.POINTER(urchin_solve_params), _vp, _vp, _vp,
+                                   C.POINTER(urchin_solve_stats), _vp]),
 }
 
 _lib = None
@@ -290,9 +298,11 @@ def urchin_solve(bvh: Bvh, dirs, l_ray: float, s, w, nH, T, x=None, *, y: float 
                  method: int = METHOD_PLAIN, segments: int = SEG_RECOMPUTE, gmres_m: int = 10,
                  kernel: int = KERNEL_M4, precision: int = F32, case_rule: int = CASE_AUTO,
                  warm_start: bool = False, profile: bool = False, raise_not_converged: bool = True,
-                 history: bool = False, blocks: int = 1, newton_switch: float = 0.01, stream=None):
+                 history: bool = False, blocks: int = 1, newton_switch: float = 0.01, state=None,
+                 stream=None):
     """Returns (x, stats dict).  x (float64 CUDA tensor, original order) is
-    updated in place when given."""
+    updated in place when given.  `state` (uint8 CUDA tensor [n]) receives
+    each particle's final case / frozen flags for urchin_solve_vjp."""
     import torch
     dirs = _host(dirs).reshape(-1, 3)
     if x is None:
@@ -318,6 +328,7 @@ def urchin_solve(bvh: Bvh, dirs, l_ray: float, s, w, nH, T, x=None, *, y: float 
     P.profile = int(bool(profile))
     P.blocks = int(blocks)
     P.newton_switch = float(newton_switch)
+    P.state = _dev(state, torch.uint8)
     hist_max = hist_unc = None
     if history:
         hist_max = np.zeros(int(max_iter))
@@ -362,3 +373,89 @@ def urchin_tangent(bvh: Bvh, dirs, l_ray: float, s, w, nH, T, x, v, *, y: float 
                                  _dev(E), _dev(dl), _stream(stream)))
     return E, dl
 
+
+
+# ---------------------------------------------------------------------------
+# reverse mode
+def urchin_trace_columns_vjp(bvh: Bvh, dirs, l_ray: float, tau_bar, origins=None, kernel: int = KERNEL_M4,
+                             precision: int = None, x_bar=None, stream=None):
+    """x_bar[j] (+)= sum_{o,k} tau_bar[o, k] d tau[o, k] / d x_j (float64 CUDA
+    tensor [n], original order; accumulated into x_bar when given)."""
+    import torch
+    dirs = _host(dirs).reshape(-1, 3)
+    R = dirs.shape[0]
+    if precision is None:
+        precision = F64 if tau_bar.dtype == torch.float64 else F32
+    dt = torch.float64 if precision == F64 else torch.float32
+    n_orig = bvh.n if origins is None else int(origins.numel())
+    if tuple(tau_bar.shape) != (n_orig, R):
+        raise ValueError(f"tau_bar must have shape ({n_orig}, {R})")
+    if x_bar is None:
+        x_bar = torch.zeros(bvh.n, dtype=torch.float64, device=tau_bar.device)
+    _check(load().urchin_trace_columns_vjp(bvh.handle, dirs.ctypes.data_as(_vp), R, float(l_ray),
+                                           _dev(origins, torch.int32), n_orig, int(kernel), int(precision),
+                                           _dev(tau_bar, dt), _dev(x_bar, torch.float64), _stream(stream)))
+    return x_bar
+
+
+def urchin_gamma_vjp(tau, s, w, gamma_bar, want_tau: bool = True, want_w: bool = True, precision: int = None,
+                     stream=None):
+    """(tau_bar [n_orig, R] in tau's dtype or None, w_bar [F] float64 or None)."""
+    import torch
+    if precision is None:
+        precision = F64 if tau.dtype == torch.float64 else F32
+    n_orig, R = tau.shape
+    sp = urchin_spectrum(int(s.numel()), _dev(s, torch.float64), _dev(w, torch.float64))
+    tb = torch.empty_like(tau) if want_tau else None
+    wb = torch.zeros(int(s.numel()), dtype=torch.float64, device=tau.device) if want_w else None
+    _check(load().urchin_gamma_vjp(_dev(tau), int(precision), n_orig, R, C.byref(sp),
+                                   _dev(gamma_bar, torch.float64), _dev(tb), _dev(wb), _stream(stream)))
+    return tb, wb
+
+
+def urchin_equilibrium_vjp(gamma, tau_eff, nH, T, x_bar, case_rule: int = CASE_AUTO, y: float = 0.0,
+                           stream=None):
+    import torch
+    n = int(gamma.numel())
+    gb = torch.empty(n, dtype=torch.float64, device=gamma.device)
+    _check(load().urchin_equilibrium_vjp(_dev(gamma, torch.float64), _dev(tau_eff, torch.float32),
+                                         _dev(nH, torch.float64), _dev(T, torch.float64), n, int(case_rule),
+                                         float(y), _dev(x_bar, torch.float64), _dev(gb), _stream(stream)))
+    return gb
+
+
+def urchin_solve_vjp(bvh: Bvh, dirs, l_ray: float, s, w, nH, T, x_star, state, x_bar, *, y: float = 0.0,
+                     tau_skip: float = 1e-4, tol: float = 1e-10, max_iter: int = 2000, gmres_m: int = 30,
+                     segments: int = SEG_RECOMPUTE, kernel: int = KERNEL_M4, precision: int = F32,
+                     case_rule: int = CASE_AUTO, warm_start: bool = False, raise_not_converged: bool = True,
+                     stream=None):
+    """dL/dw (float64 CUDA tensor [F]) at the converged x* of urchin_solve
+    (whose `state` output must be passed), for x_bar = dL/dx*.  tol and
+    max_iter bound the adjoint GMRES solve; returns (w_bar, stats dict)."""
+    import torch
+    dirs = _host(dirs).reshape(-1, 3)
+    P = urchin_solve_params()
+    P.R = dirs.shape[0]
+    P.dirs = dirs.ctypes.data_as(_vp)
+    P.l_ray = float(l_ray)
+    P.spectrum = urchin_spectrum(int(s.numel()), _dev(s, torch.float64), _dev(w, torch.float64))
+    P.nH = _dev(nH, torch.float64)
+    P.T = _dev(T, torch.float64)
+    P.y = float(y)
+    P.tol = float(tol)
+    P.tau_skip = float(tau_skip)
+    P.max_iter = int(max_iter)
+    P.segments = int(segments)
+    P.gmres_m = int(gmres_m)
+    P.kernel = int(kernel)
+    P.precision = int(precision)
+    P.case_rule = int(case_rule)
+    P.warm_start = int(bool(warm_start))
+    P.state = _dev(state, torch.uint8)
+    wb = torch.zeros(int(s.numel()), dtype=torch.float64, device=x_star.device)
+    st = urchin_solve_stats()
+    rc = load().urchin_solve_vjp(bvh.handle, C.byref(P), _dev(x_star, torch.float64), _dev(x_bar, torch.float64),
+                                 _dev(wb), C.byref(st), _stream(stream))
+    if not (rc == URCHIN_ERR_NOT_CONVERGED and not raise_not_converged):
+        _check(rc)
+    return wb, st.as_dict()

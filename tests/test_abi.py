@@ -109,6 +109,16 @@ def test_device_entry_points_reject_bad_arguments_without_gpu_work():
     assert lib.urchin_equilibrium(C.c_void_p(16), None, C.c_void_p(16), C.c_void_p(16), 5, 2, 0.0,
                                   C.c_void_p(16), None) == U.URCHIN_ERR_ARG
     assert lib.urchin_solve(None, None, None, None, None) == U.URCHIN_ERR_ARG
+    # reverse-mode entry points
+    assert lib.urchin_trace_columns_vjp(None, dirs.ctypes.data_as(C.c_void_p), 1, 1.0, None, 5, 0, 0, None,
+                                        None, None) == U.URCHIN_ERR_ARG
+    assert lib.urchin_gamma_vjp(C.c_void_p(16), 0, 10, 12, C.byref(sp), C.c_void_p(16), None, None,
+                                None) == U.URCHIN_ERR_ARG                  # no output requested
+    assert lib.urchin_gamma_vjp(None, 5, 10, 12, C.byref(sp), None, None, None, None) == U.URCHIN_ERR_ARG
+    assert lib.urchin_equilibrium_vjp(None, None, None, None, 5, 9, 0.0, None, None, None) == U.URCHIN_ERR_ARG
+    assert lib.urchin_equilibrium_vjp(None, None, None, None, 0, 0, 0.0, None, None, None) == U.URCHIN_OK
+    assert lib.urchin_gamma_vjp(None, 0, 0, 12, C.byref(sp), None, None, None, None) == U.URCHIN_OK
+    assert lib.urchin_solve_vjp(None, None, None, None, None, None, None) == U.URCHIN_ERR_ARG
     # zero-size requests are no-ops
     assert lib.urchin_equilibrium(None, None, None, None, 0, 0, 0.0, None, None) == U.URCHIN_OK
     assert lib.urchin_gamma(None, 0, 0, 12, C.byref(sp), None, None, None) == U.URCHIN_OK
@@ -139,6 +149,11 @@ def test_solve_params_validation():
     P.method = 3                                  # no such method
     assert lib.urchin_solve(fake, C.byref(P), fake, C.byref(st), None) == U.URCHIN_ERR_ARG
     assert "method" in lib.urchin_last_error().decode()
+    P.method = U.METHOD_PLAIN
+    P.gmres_m = 10
+    xb = C.c_void_p(16)
+    assert lib.urchin_solve_vjp(fake, C.byref(P), fake, xb, xb, C.byref(st), None) == U.URCHIN_ERR_ARG
+    assert "state" in lib.urchin_last_error().decode()       # the forward state is required
     for method in (U.METHOD_NEWTON, U.METHOD_ANDERSON):
         P.method = method
         for m in (0, 65):                         # Krylov dimension / history depth out of range
