@@ -8,8 +8,13 @@
 //
 // Work distribution: a persistent grid; each warp takes tasks of 32
 // Morton-consecutive origins in one direction from an atomic queue, so the
-// 32 rays of a warp are parallel and start close together (coherent node
-// fetches).  Each lane walks its own ray with a private stack.
+// 32 rays of a warp are parallel and start close together.  The warp walks
+// the tree as one packet: a child is entered when any lane's segment crosses
+// its box (warp vote), so every lane follows the same path and stack and the
+// node fetches are broadcasts; at a leaf each lane tests its own segment
+// against the leaf's spheres.  The packet visits the union of the lanes'
+// nodes (a beam about as wide as the 32 origins' spread, comparable to h),
+// in exchange for uniform control flow.
 #include <algorithm>
 #include <cmath>
 
@@ -379,7 +384,7 @@ __device__ __forceinline__ void leaf_hits(const TraceParams& P, int ref, int cnt
 
 template <typename Real, int KERNEL, int MODE>
 __device__ void ray_column(const TraceParams& P, const float2* tab, float4 o, Real dx, Real dy, Real dz,
-                           Sink<Real>& sk, unsigned& err, unsigned& nvisit)
+                           bool live, Sink<Real>& sk, unsigned& err, unsigned& nvisit)
 {
     const Real L = Real(P.l_ray);
     const float Lf = (float)P.l_ray * 1.000001f + 1e-30f;
@@ -397,7 +402,7 @@ __device__ void ray_column(const TraceParams& P, const float2* tab, float4 o, Re
         Real sy = Real(o.y) - Real(ay) * Real(P.Lbox);
         Real sz = Real(o.z) - Real(az) * Real(P.Lbox);
         float fx = (float)sx, fy = (float)sy, fz = (float)sz;
-        if (!seg_box(fx, fy, fz, ix, iy, iz, Lf, rlo, rhi)) continue;
+        if (!__any_sync(0xffffffffu, live && seg_box(fx, fy, fz, ix, iy, iz, Lf, rlo, rhi))) continue;
         int sp = 0;
         int node = 0;
         // a traversal visits every internal node at most once; the cap only
@@ -417,20 +422,24 @@ __device__ void ray_column(const TraceParams& P, const float2* tab, float4 o, Re
             float4 a = __ldg(nd), b = __ldg(nd + 1), c = __ldg(nd + 2), d = __ldg(nd + 3);
             int lref = __float_as_int(a.w), lcnt = __float_as_int(b.w);
             int rref = __float_as_int(c.w), rcnt = __float_as_int(d.w);
-            bool hl = seg_box(fx, fy, fz, ix, iy, iz, Lf, a, b);
-            bool hr = rcnt >= 0 && seg_box(fx, fy, fz, ix, iy, iz, Lf, c, d);
+            bool hl = __any_sync(0xffffffffu, live && seg_box(fx, fy, fz, ix, iy, iz, Lf, a, b));
+            bool hr = __any_sync(0xffffffffu, live && rcnt >= 0 && seg_box(fx, fy, fz, ix, iy, iz, Lf, c, d));
             if (hl && lcnt > 0) {
-                if constexpr (sizeof(Real) == 4)
-                    leaf_hits_f32<KERNEL, MODE>(P, tab, lref, lcnt, sx, sy, sz, dx, dy, dz, L, sk, err);
-                else
-                    leaf_hits<Real, KERNEL, MODE>(P, lref, lcnt, sx, sy, sz, dx, dy, dz, L, sk, err);
+                if (live) {
+                    if constexpr (sizeof(Real) == 4)
+                        leaf_hits_f32<KERNEL, MODE>(P, tab, lref, lcnt, sx, sy, sz, dx, dy, dz, L, sk, err);
+                    else
+                        leaf_hits<Real, KERNEL, MODE>(P, lref, lcnt, sx, sy, sz, dx, dy, dz, L, sk, err);
+                }
                 hl = false;
             }
             if (hr && rcnt > 0) {
-                if constexpr (sizeof(Real) == 4)
-                    leaf_hits_f32<KERNEL, MODE>(P, tab, rref, rcnt, sx, sy, sz, dx, dy, dz, L, sk, err);
-                else
-                    leaf_hits<Real, KERNEL, MODE>(P, rref, rcnt, sx, sy, sz, dx, dy, dz, L, sk, err);
+                if (live) {
+                    if constexpr (sizeof(Real) == 4)
+                        leaf_hits_f32<KERNEL, MODE>(P, tab, rref, rcnt, sx, sy, sz, dx, dy, dz, L, sk, err);
+                    else
+                        leaf_hits<Real, KERNEL, MODE>(P, rref, rcnt, sx, sy, sz, dx, dy, dz, L, sk, err);
+                }
                 hr = false;
             }
             if (hl && hr) {
@@ -470,23 +479,27 @@ __global__ void __launch_bounds__(256) k_trace(TraceParams P)
         const int k = (int)(task / P.n_chunks);
         const int64_t chunk = (int64_t)(task % P.n_chunks);
         const int64_t item = chunk * 32 + lane;
+        // every lane takes part in the packet's votes; lanes past the end of
+        // the origin list (and, in the transpose, rays with a zero
+        // coefficient) are carried along without a segment
+        bool live = item < P.n_items;
+        const int32_t org = live ? (P.items ? P.items[item] : (int32_t)item) : 0;
+        float4 o = __ldg(P.xyzh + org);
+        Real dx = Real(s_dirs[3 * k]), dy = Real(s_dirs[3 * k + 1]), dz = Real(s_dirs[3 * k + 2]);
+        unsigned nvisit = 0;
+        Sink<Real> sk{Real(0), Real(0), 0u, 0u, 0, 0, Real(0)};
+        const int64_t ray = (int64_t)k * P.n_items + item;
+        const int64_t orow = live ? (P.out_row ? (int64_t)P.out_row[item] : item) : 0;
+        if (live && MODE == MODE_FILL) {
+            sk.pos = (int64_t)P.row_ptr[ray];
+            sk.end = (int64_t)P.row_ptr[ray + 1];
+        }
+        if (live && MODE == MODE_SCATTER) {
+            sk.coef = static_cast<const Real*>(P.coef)[orow * P.row_stride + (int64_t)k * P.k_stride];
+            live = sk.coef != Real(0);
+        }
+        ray_column<Real, KERNEL, MODE>(P, s_tab, o, dx, dy, dz, live, sk, err, nvisit);
         if (item < P.n_items) {
-            int32_t org = P.items ? P.items[item] : (int32_t)item;
-            float4 o = __ldg(P.xyzh + org);
-            Real dx = Real(s_dirs[3 * k]), dy = Real(s_dirs[3 * k + 1]), dz = Real(s_dirs[3 * k + 2]);
-            unsigned nvisit = 0;
-            Sink<Real> sk{Real(0), Real(0), 0u, 0u, 0, 0, Real(0)};
-            const int64_t ray = (int64_t)k * P.n_items + item;
-            if (MODE == MODE_FILL) {
-                sk.pos = (int64_t)P.row_ptr[ray];
-                sk.end = (int64_t)P.row_ptr[ray + 1];
-            }
-            const int64_t orow = P.out_row ? (int64_t)P.out_row[item] : item;
-            if (MODE == MODE_SCATTER)
-                sk.coef = static_cast<const Real*>(P.coef)[orow * P.row_stride + (int64_t)k * P.k_stride];
-            // a ray with a zero coefficient adds nothing: skip its traversal
-            if (MODE != MODE_SCATTER || sk.coef != Real(0))
-                ray_column<Real, KERNEL, MODE>(P, s_tab, o, dx, dy, dz, sk, err, nvisit);
             hits += sk.nhit;
             tests += sk.ntest;
             visits += nvisit;
