@@ -395,6 +395,27 @@ def main():
                           "newton_start": sm["newton_start"], "newton_fallbacks": sm["newton_fallbacks"],
                           "max_rel_to_xstar": float(dist.max()), "p999_rel_to_xstar": float(np.quantile(dist, 0.999))}
         comp["xstar"] = {"tol": 1e-6, "iterations": sr["iterations"], "converged": bool(sr["converged"])}
+        # reverse mode at the converged state: gradient of L = sum_i ln x*_i
+        # with respect to the spectrum weights (adjoint GMRES, one transposed
+        # column pass per product)
+        bvh = U.urchin_build_bvh(d["px"], d["py"], d["pz"], d["h"], d["m"], w.periodic, w.box, w.unit_cm)
+        state = torch.empty(w.n, dtype=torch.uint8, device=dev)
+        xs, ss = U.urchin_solve(bvh, dirs, w.l_ray, s_d, w_d, d["nH"], d["T"], tol=1e-3, tau_skip=1e-4,
+                                max_iter=args.max_iter, segments=segs, precision=U.F32, state=state,
+                                raise_not_converged=False)
+        torch.cuda.synchronize(dev)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        wb, vs = U.urchin_solve_vjp(bvh, dirs, w.l_ray, s_d, w_d, d["nH"], d["T"], xs, state, 1.0 / xs,
+                                    tol=1e-6, max_iter=600, gmres_m=30, segments=segs, precision=U.F32,
+                                    raise_not_converged=False)
+        b.record(stream)
+        b.synchronize()
+        comp["adjoint"] = {"loss": "sum ln x*", "wall_s": a.elapsed_time(b) * 1e-3, "products": vs["iterations"],
+                           "rel_residual": vs["max_rel_dx"], "converged": bool(vs["converged"]),
+                           "rays": vs["rays"], "grad_norm": float(wb.norm())}
+        bvh.close()
         line["compare"] = comp
     if world == 1 and not args.no_cpu_baseline:
         import oracle as O

@@ -143,12 +143,12 @@ constexpr unsigned kStWarm = 16u;       // warm-start x outside (0, 1]
 constexpr unsigned kStVisit = 32u;      // traversal visit limit (malformed tree)
 constexpr unsigned kStSegment = 64u;    // stored-segment fill disagrees with its count
 
-constexpr int kLeafMax = 4;
+constexpr int kLeafMax = 4;       // subtrees with <= kLeafMax particles become leaves
 constexpr int kKTab = 2048;       // intervals of the full-chord M4 table in t = b^2/h^2
 
 // Full-chord M4 integral K(t) = int_{-c}^{c} shape(sqrt(t + u^2)) du, c = sqrt(1-t),
 // tabulated at t_i = i / kKTab as (K(t_i), dK/dt(t_i) / kKTab), host side.
-void m4_full_table(float2* out /* [kKTab + 1] */);       // subtrees with <= kLeafMax particles become leaves
+void m4_full_table(float2* out /* [kKTab + 1] */);
 constexpr int kStackMax = 64;     // traversal stack (tree depth <= 62 for 30-bit codes)
 
 // Column tracing shared by urchin_trace_columns and urchin_solve.
@@ -178,8 +178,25 @@ struct TraceJob {
     void* seg_val;                // mode 2: A_j * chord integral per segment (precision's type)
     const void* coef;             // mode 3: per-ray coefficient (precision's type), indexed like out
     double* xbar;                 // mode 3: [n] Morton order, accumulated with atomics
+    const int32_t* order;         // [R * n_items] or NULL: order[k * n_items + i] = the item that the
+                                  // i-th lane slot of direction k traces (ray_order)
 };
 int launch_trace(const TraceJob& job, cudaStream_t s);
+
+// Per-direction traversal order of the items: for each direction k the
+// origins sorted by a Morton code in the frame (e1, e2, d_k) with the axis
+// along d_k compressed, so that 32 consecutive origins form a thin beam
+// along the ray direction.  order needs R * n_items int32; tmp needs
+// ray_order_tmp_bytes(n_items).
+// Measured on the 262144-particle halo (F32 columns, all origins): no order
+// 70 ms, E = 1: 68.6, E = 4: 63.7, E = 16: 60.7, E = 64 and 256: 60.8 ms;
+// on the 4096-particle lattice the order costs more (sort launches, and
+// 9.1 instead of 7.4 sphere tests per hit), so short lists keep item order.
+constexpr double kRayOrderElongation = 16.0;
+constexpr int64_t kRayOrderMinItems = 16384;
+size_t ray_order_tmp_bytes(int64_t n_items);
+int ray_order(const urchin_bvh* bvh, const int32_t* items, int64_t n_items, const double* dirs_host, int R,
+              int32_t* order, void* tmp, cudaStream_t s);
 
 // w_bar[b] += sum_r sg[r] exp(lc[r] - s_b tau[r]) over n_rays rays (tau in
 // the precision's type; the coefficient of ray r is sg[r] exp(lc[r]))

@@ -710,6 +710,35 @@ int Solver::timed_trace(TraceJob& job)
     return URCHIN_OK;
 }
 
+int Solver::order_for(const int32_t* items, int64_t n_items, const int32_t** out)
+{
+    *out = nullptr;
+    if (n_items <= 0) return URCHIN_OK;
+    for (const OrderEntry& e : orders)
+        if (e.items == items && e.n == n_items) {
+            *out = e.order;
+            return URCHIN_OK;
+        }
+    if (!ord_base) {
+        ord_cap = 2 * (int64_t)P.R * n;
+        Layout lay;
+        const size_t o_o = lay.take(sizeof(int32_t) * (size_t)ord_cap);
+        const size_t o_t = lay.take(ray_order_tmp_bytes(n));
+        URCHIN_TRY(ord.alloc(lay.bytes, s));
+        ord_base = ord.at<int32_t>(o_o);
+        ord_tmp = ord.at<void>(o_t);
+    }
+    const int64_t need = (int64_t)P.R * n_items;
+    if (n_items > n || n_items < kRayOrderMinItems) return URCHIN_OK;   // item order
+    if (ord_used + need > ord_cap) items_changed();
+    int32_t* o = ord_base + ord_used;
+    URCHIN_TRY(ray_order(bvh, items, n_items, P.dirs, P.R, o, ord_tmp, s));
+    ord_used += need;
+    orders.push_back(OrderEntry{items, n_items, o});
+    *out = o;
+    return URCHIN_OK;
+}
+
 int Solver::trace(const int32_t* items, int64_t n_items, const float* tw32, const double* tw64)
 {
     TraceJob job{};
@@ -728,6 +757,7 @@ int Solver::trace(const int32_t* items, int64_t n_items, const float* tw32, cons
     job.kernel = P.kernel;
     job.precision = P.precision;
     job.mode = 0;
+    URCHIN_TRY(order_for(items, n_items, &job.order));
     URCHIN_TRY(timed_trace(job));
     stats.traversals += 1;
     stats.rays += n_items * P.R;
@@ -777,6 +807,7 @@ int Solver::columns(const int32_t* items, int64_t n_items, int sweep0)
     job.precision = P.precision;
     job.mode = 1;
     job.counts = counts;
+    URCHIN_TRY(order_for(items, n_items, &job.order));
     URCHIN_TRY(timed_trace(job));
     const int64_t rays = (int64_t)P.R * n_items;
     uint64_t* total = reinterpret_cast<uint64_t*>(misc + 6);
@@ -860,6 +891,7 @@ int Solver::linear_columns(const int32_t* items, int64_t n_items, const float* z
     job.kernel = P.kernel;
     job.precision = P.precision;
     job.mode = 0;
+    URCHIN_TRY(order_for(items, n_items, &job.order));
     return timed_trace(job);
 }
 
@@ -932,6 +964,7 @@ int Solver::first_sweep()
     URCHIN_TRY(timed_sweep(sweep_args(nullptr, n, 1), s));
     uint32_t* cnt = reinterpret_cast<uint32_t*>(misc + 2);
     URCHIN_TRY(compact_indices(active, n, list, cnt, comp_tmp, s));
+    items_changed();
     uint32_t hc = 0;
     URCHIN_TRY_CUDA(cudaMemcpyAsync(&hc, cnt, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     double m;
@@ -985,6 +1018,7 @@ int Solver::order_by_density()
     while ((1 << bits) < B) ++bits;
     URCHIN_TRY(radix_sort_pairs(keys, vals, na, bits, rt, s));        // stable: Morton order inside blocks
     URCHIN_TRY_CUDA(cudaMemcpyAsync(list, vals, sizeof(int32_t) * (size_t)na, cudaMemcpyDeviceToDevice, s));
+    items_changed();
     tmp.release();
     for (int b = 1; b <= B; ++b) block_lo.push_back(((int64_t)b * na) / B);
     return URCHIN_OK;
@@ -1395,6 +1429,7 @@ int Solver::transpose_columns(const void* coef, double* z)
     job.mode = 3;
     job.coef = coef;
     job.xbar = z;
+    URCHIN_TRY(order_for(list, n_act, &job.order));
     return timed_trace(job);
 }
 
@@ -1412,6 +1447,7 @@ int Solver::adjoint(const uint8_t* state_orig, const double* xbar_orig, int cold
     URCHIN_TRY(launched());
     uint32_t* cnt = reinterpret_cast<uint32_t*>(misc + 2);
     URCHIN_TRY(compact_indices(active, n, list, cnt, comp_tmp, s));
+    items_changed();
     uint32_t hc = 0;
     URCHIN_TRY_CUDA(cudaMemcpyAsync(&hc, cnt, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     double mrel;
@@ -1539,6 +1575,7 @@ int Solver::tangent(const double* v_orig, double* E_orig, double* dlnE_orig)
     const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 4096));
     k_iota<<<g, 256, 0, s>>>(list, n);
     URCHIN_TRY(launched());
+    items_changed();
     n_act = n;
     URCHIN_TRY(trace(list, n, w32, w64));
     URCHIN_TRY_CUDA(cudaMemsetAsync(misc, 0, sizeof(unsigned long long), s));
@@ -1592,6 +1629,7 @@ int Solver::finish(double* x_inout)
     }
     nk.release();
     seg.release();
+    ord.release();
     scr.release();
     URCHIN_TRY_CUDA(cudaStreamSynchronize(s));
     return URCHIN_OK;

@@ -92,6 +92,24 @@ struct Solver {
     int32_t* seg_col = nullptr;
     void* seg_val = nullptr;
     Scratch seg;
+    // per-direction traversal orders, cached per item list (any permutation
+    // is correct; a stale one only costs coherence)
+    Scratch ord;
+    int32_t* ord_base = nullptr;
+    void* ord_tmp = nullptr;
+    int64_t ord_cap = 0, ord_used = 0;
+    struct OrderEntry {
+        const int32_t* items;
+        int64_t n;
+        int32_t* order;
+    };
+    std::vector<OrderEntry> orders;
+    int order_for(const int32_t* items, int64_t n_items, const int32_t** out);
+    void items_changed()
+    {
+        orders.clear();
+        ord_used = 0;
+    }
     // Newton-Krylov
     Scratch nk;
 

@@ -59,6 +59,7 @@ struct TraceParams {
     // transpose mode
     const void* coef;             // MODE_SCATTER: coefficient of each ray, indexed like out
     double* xbar;                 // MODE_SCATTER: xbar[j] += coef * A_j * chord integral (Morton)
+    const int32_t* order;         // [R * n_items] per-direction item order, or NULL
 };
 
 constexpr int MODE_TAU = 0, MODE_COUNT = 1, MODE_FILL = 2, MODE_SCATTER = 3;
@@ -478,11 +479,12 @@ __global__ void __launch_bounds__(256) k_trace(TraceParams P)
         if ((unsigned long long)task >= total) break;
         const int k = (int)(task / P.n_chunks);
         const int64_t chunk = (int64_t)(task % P.n_chunks);
-        const int64_t item = chunk * 32 + lane;
+        const int64_t slot = chunk * 32 + lane;
         // every lane takes part in the packet's votes; lanes past the end of
         // the origin list (and, in the transpose, rays with a zero
         // coefficient) are carried along without a segment
-        bool live = item < P.n_items;
+        bool live = slot < P.n_items;
+        const int64_t item = !live ? 0 : (P.order ? (int64_t)P.order[(int64_t)k * P.n_items + slot] : slot);
         const int32_t org = live ? (P.items ? P.items[item] : (int32_t)item) : 0;
         float4 o = __ldg(P.xyzh + org);
         Real dx = Real(s_dirs[3 * k]), dy = Real(s_dirs[3 * k + 1]), dz = Real(s_dirs[3 * k + 2]);
@@ -499,7 +501,7 @@ __global__ void __launch_bounds__(256) k_trace(TraceParams P)
             live = sk.coef != Real(0);
         }
         ray_column<Real, KERNEL, MODE>(P, s_tab, o, dx, dy, dz, live, sk, err, nvisit);
-        if (item < P.n_items) {
+        if (slot < P.n_items) {
             hits += sk.nhit;
             tests += sk.ntest;
             visits += nvisit;
@@ -530,8 +532,8 @@ template <typename Real, int KERNEL, int MODE>
 int launch_one(const TraceParams& P, cudaStream_t s)
 {
     const void* fn = (const void*)k_trace<Real, KERNEL, MODE>;
-    size_t smem = sizeof(double) * 3 * (size_t)P.R +
-                  ((sizeof(Real) == 4 && KERNEL == URCHIN_KERNEL_M4) ? sizeof(float2) * (kKTab + 1) : 0);
+    const size_t smem = sizeof(double) * 3 * (size_t)P.R +
+                        ((sizeof(Real) == 4 && KERNEL == URCHIN_KERNEL_M4) ? sizeof(float2) * (kKTab + 1) : 0);
     int grid = 0;
     URCHIN_TRY(grid_for(fn, 256, smem, &grid));
     int64_t tasks = P.n_chunks * P.R;
@@ -641,7 +643,94 @@ int launch_trace(const TraceJob& job, cudaStream_t s)
     P.A64 = b->A64;
     P.coef = job.coef;
     P.xbar = job.xbar;
+    P.order = job.order;
     return dispatch_mode(P, job.precision, job.kernel, job.mode, s);
+}
+
+namespace {
+
+__device__ __forceinline__ uint32_t spread10(uint32_t v)
+{
+    v &= 0x3ffu;
+    v = (v | (v << 16)) & 0x030000ffu;
+    v = (v | (v << 8)) & 0x0300f00fu;
+    v = (v | (v << 4)) & 0x030c30c3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+
+__device__ __forceinline__ uint32_t quant10(float f)
+{
+    return (uint32_t)fminf(fmaxf(f * 1024.f, 0.f), 1023.f);
+}
+
+// keys of the items for one direction: Morton code of (u, v, t / E) in the
+// frame (e1, e2, d), coordinates relative to c scaled by inv into [0, 1)
+__global__ void k_ray_keys(const float4* __restrict__ xyzh, const int32_t* __restrict__ items, int64_t n_items,
+                           float3 e1, float3 e2, float3 d, float3 c, float inv, float inv_E, uint32_t* keys,
+                           int32_t* vals)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_items;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float4 p = __ldg(xyzh + (items ? items[i] : (int32_t)i));
+        const float rx = p.x - c.x, ry = p.y - c.y, rz = p.z - c.z;
+        const float u = (rx * e1.x + ry * e1.y + rz * e1.z) * inv + 0.5f;
+        const float v = (rx * e2.x + ry * e2.y + rz * e2.z) * inv + 0.5f;
+        const float t = (rx * d.x + ry * d.y + rz * d.z) * inv * inv_E + 0.5f;
+        keys[i] = (spread10(quant10(u)) << 2) | (spread10(quant10(v)) << 1) | spread10(quant10(t));
+        vals[i] = (int32_t)i;
+    }
+}
+
+}  // namespace
+
+size_t ray_order_tmp_bytes(int64_t n_items)
+{
+    Layout lay;
+    lay.take(sizeof(uint32_t) * (size_t)n_items);
+    lay.take(radix_tmp_bytes(n_items));
+    return lay.bytes;
+}
+
+int ray_order(const urchin_bvh* b, const int32_t* items, int64_t n_items, const double* dirs, int R,
+              int32_t* order, void* tmp, cudaStream_t s)
+{
+    if (n_items <= 0) return URCHIN_OK;
+    Layout lay;
+    const size_t o_k = lay.take(sizeof(uint32_t) * (size_t)n_items);
+    const size_t o_t = lay.take(radix_tmp_bytes(n_items));
+    uint32_t* keys = reinterpret_cast<uint32_t*>(static_cast<char*>(tmp) + o_k);
+    void* rt = static_cast<char*>(tmp) + o_t;
+    const double E = kRayOrderElongation;
+    const float3 c = make_float3(0.5f * (b->root_lo[0] + b->root_hi[0]), 0.5f * (b->root_lo[1] + b->root_hi[1]),
+                                 0.5f * (b->root_lo[2] + b->root_hi[2]));
+    const double ex = b->root_hi[0] - b->root_lo[0], ey = b->root_hi[1] - b->root_lo[1],
+                 ez = b->root_hi[2] - b->root_lo[2];
+    const double diam = std::sqrt(ex * ex + ey * ey + ez * ez);
+    const float inv = (float)(1.0 / std::max(diam, 1e-30));
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n_items + 255) / 256, 4096));
+    for (int k = 0; k < R; ++k) {
+        const double dx = dirs[3 * k], dy = dirs[3 * k + 1], dz = dirs[3 * k + 2];
+        // e1 perpendicular to d, from the coordinate axis least aligned with it
+        double ax = 0, ay = 0, az = 0;
+        if (std::fabs(dx) <= std::fabs(dy) && std::fabs(dx) <= std::fabs(dz)) ax = 1;
+        else if (std::fabs(dy) <= std::fabs(dz)) ay = 1;
+        else az = 1;
+        double e1x = dy * az - dz * ay, e1y = dz * ax - dx * az, e1z = dx * ay - dy * ax;
+        const double nn = std::sqrt(e1x * e1x + e1y * e1y + e1z * e1z);
+        e1x /= nn;
+        e1y /= nn;
+        e1z /= nn;
+        const double e2x = dy * e1z - dz * e1y, e2y = dz * e1x - dx * e1z, e2z = dx * e1y - dy * e1x;
+        int32_t* vals = order + (size_t)k * n_items;
+        k_ray_keys<<<grid, 256, 0, s>>>(b->xyzh, items, n_items, make_float3((float)e1x, (float)e1y, (float)e1z),
+                                        make_float3((float)e2x, (float)e2y, (float)e2z),
+                                        make_float3((float)dx, (float)dy, (float)dz), c, inv, (float)(1.0 / E),
+                                        keys, vals);
+        URCHIN_TRY(launched());
+        URCHIN_TRY(radix_sort_pairs(keys, vals, n_items, 30, rt, s));
+    }
+    return URCHIN_OK;
 }
 
 // w[s] = A[s] x[perm[s]]
@@ -742,6 +831,9 @@ extern "C" int urchin_trace_columns(const urchin_bvh* bvh, const double* x, cons
     size_t o_dirs = lay.take(sizeof(double) * 3 * (size_t)R);
     size_t o_w = lay.take((f64 ? sizeof(double) : sizeof(float)) * (size_t)n);
     size_t o_items = lay.take(origins ? sizeof(int32_t) * (size_t)n_orig : 0);
+    const bool ordered = n_orig >= kRayOrderMinItems;
+    size_t o_ord = lay.take(ordered ? sizeof(int32_t) * (size_t)R * (size_t)n_orig : 0);
+    size_t o_otmp = lay.take(ordered ? ray_order_tmp_bytes(n_orig) : 0);
     Scratch scr;
     URCHIN_TRY(scr.alloc(lay.bytes, s));
     unsigned* ctr = scr.at<unsigned>(o_ctr);
@@ -775,6 +867,10 @@ extern "C" int urchin_trace_columns(const urchin_bvh* bvh, const double* x, cons
         // all particles, in Morton order for coherence; row = original index
         job.items = nullptr;
         job.out_row = bvh->perm;
+    }
+    if (n_orig >= kRayOrderMinItems) {
+        URCHIN_TRY(ray_order(bvh, job.items, n_orig, dirs, R, scr.at<int32_t>(o_ord), scr.at<void>(o_otmp), s));
+        job.order = scr.at<int32_t>(o_ord);
     }
     URCHIN_TRY(launch_trace(job, s));
     unsigned st = 0;
