@@ -143,7 +143,7 @@ constexpr unsigned kStWarm = 16u;       // warm-start x outside (0, 1]
 constexpr unsigned kStVisit = 32u;      // traversal visit limit (malformed tree)
 constexpr unsigned kStSegment = 64u;    // stored-segment fill disagrees with its count
 
-constexpr int kLeafMax = 4;       // subtrees with <= kLeafMax particles become leaves
+constexpr int kLeafMax = 16;      // subtrees with <= kLeafMax particles become leaves
 constexpr int kKTab = 2048;       // intervals of the full-chord M4 table in t = b^2/h^2
 
 // Full-chord M4 integral K(t) = int_{-c}^{c} shape(sqrt(t + u^2)) du, c = sqrt(1-t),
