@@ -262,6 +262,8 @@ typedef struct {
                                       fraction of the non-frozen particles has
                                       |dx|/x >= tol, then Newton-Krylov takes
                                       over (<= 0: 0.01)                        */
+    double          newton_eta;   /* NEWTON: GMRES relative residual per step
+                                     (<= 0: Eisenstat-Walker, 0.1 ... 1e-3)   */
     unsigned char*  state;        /* device [n] or NULL, original order:
                                      urchin_solve writes, urchin_solve_vjp
                                      reads each particle's final state,

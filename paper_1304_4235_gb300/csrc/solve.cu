@@ -1153,7 +1153,7 @@ int Solver::newton()
     double* hdev = nk.at<double>(o_h);
     const unsigned g1 = (unsigned)std::max<int64_t>(1, std::min<int64_t>((na + 255) / 256, 2048));
     std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1), hcol(m + 2), y(m);
-    double eta = 0.1, prev_norm = -1.0;
+    double eta = P.newton_eta > 0.0 ? P.newton_eta : 0.1, prev_norm = -1.0;
     double mrel = 0.0, norm = 0.0;
     int64_t sw = 0;
     URCHIN_TRY(evaluate(0, V, E, ctan, dtmp, hdev, &mrel, &norm, &sw));
@@ -1167,7 +1167,8 @@ int Solver::newton()
         }
         // GMRES(m) for J d = r, r = -G already in V0, d0 = 0
         const double beta = norm;
-        if (prev_norm > 0.0) eta = std::min(0.1, std::max(1e-3, 0.9 * (beta / prev_norm) * (beta / prev_norm)));
+        if (P.newton_eta > 0.0) eta = P.newton_eta;
+        else if (prev_norm > 0.0) eta = std::min(0.1, std::max(1e-3, 0.9 * (beta / prev_norm) * (beta / prev_norm)));
         prev_norm = beta;
         URCHIN_TRY(launch_axpby(0.0, V, 1.0 / beta, V, na, s));
         std::fill(gv.begin(), gv.end(), 0.0);
@@ -1711,6 +1712,8 @@ int check_solve_params(const char* fn, const urchin_bvh* bvh, const urchin_solve
         return set_error(URCHIN_ERR_ARG, "%s: unknown method", fn);
     if (P->segments != URCHIN_SEG_RECOMPUTE && P->segments != URCHIN_SEG_STORE && P->segments != URCHIN_SEG_AUTO)
         return set_error(URCHIN_ERR_ARG, "%s: unknown segments mode", fn);
+    if (!std::isfinite(P->newton_eta) || !(P->newton_eta < 1.0))
+        return set_error(URCHIN_ERR_ARG, "%s: newton_eta must be finite and < 1", fn);
     return URCHIN_OK;
 }
 

@@ -57,7 +57,7 @@ class urchin_solve_params(C.Structure):
                 ("kernel", C.c_int), ("precision", C.c_int), ("case_rule", C.c_int),
                 ("warm_start", C.c_int), ("profile", C.c_int), ("history_maxrel", _vp),
                 ("history_unconverged", _vp), ("blocks", C.c_int), ("newton_switch", C.c_double),
-                ("state", _vp)]
+                ("newton_eta", C.c_double), ("state", _vp)]
 
 
 class urchin_solve_stats(C.Structure):
@@ -298,8 +298,8 @@ def urchin_solve(bvh: Bvh, dirs, l_ray: float, s, w, nH, T, x=None, *, y: float 
                  method: int = METHOD_PLAIN, segments: int = SEG_RECOMPUTE, gmres_m: int = 10,
                  kernel: int = KERNEL_M4, precision: int = F32, case_rule: int = CASE_AUTO,
                  warm_start: bool = False, profile: bool = False, raise_not_converged: bool = True,
-                 history: bool = False, blocks: int = 1, newton_switch: float = 0.01, state=None,
-                 stream=None):
+                 history: bool = False, blocks: int = 1, newton_switch: float = 0.01, newton_eta: float = 0.0,
+                 state=None, stream=None):
     """Returns (x, stats dict).  x (float64 CUDA tensor, original order) is
     updated in place when given.  `state` (uint8 CUDA tensor [n]) receives
     each particle's final case / frozen flags for urchin_solve_vjp."""
@@ -328,6 +328,7 @@ def urchin_solve(bvh: Bvh, dirs, l_ray: float, s, w, nH, T, x=None, *, y: float 
     P.profile = int(bool(profile))
     P.blocks = int(blocks)
     P.newton_switch = float(newton_switch)
+    P.newton_eta = float(newton_eta)
     P.state = _dev(state, torch.uint8)
     hist_max = hist_unc = None
     if history:

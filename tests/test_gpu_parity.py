@@ -369,6 +369,26 @@ def test_newton_halo_small_fp32(halo_small, segments):
     assert dn.max() <= dp.max()
 
 
+def test_newton_full_halo_reaches_xstar_in_fewer_evaluations():
+    """Benchmark-size halo: Newton-Krylov started once the sweeps are in
+    their linear regime (at most 1 % of the particles moving by >= 1e-5),
+    with GMRES(60) to relative residual 1e-4, converges quadratically and
+    lands within rel 1e-5 of x* (plain sweeps to dx_tol 1e-6); plain sweeps
+    need dx_tol 1e-5 and more evaluations to get within rel 1e-3 of x*."""
+    w = W.halo()
+    bvh, d = build(w, torch)
+    sg, so = spectra(w, torch)
+    xs, ss = _solve_gpu(w, bvh, d, sg, U.F32, tol=1e-6, max_iter=5000, segments=U.SEG_STORE)
+    assert ss["converged"]
+    xp, sp = _solve_gpu(w, bvh, d, sg, U.F32, tol=1e-5, max_iter=5000, segments=U.SEG_STORE)
+    xn, sn = _solve_gpu(w, bvh, d, sg, U.F32, tol=1e-5, max_iter=1000, segments=U.SEG_STORE,
+                        method=U.METHOD_NEWTON, gmres_m=60, newton_eta=1e-4, newton_switch=0.01)
+    assert sp["converged"] and sn["converged"] and sn["newton_start"] > 0
+    assert sn["iterations"] < sp["iterations"]
+    assert rel_err(xn, xs).max() < 1e-4
+    assert rel_err(xp, xs).max() < 1e-3
+
+
 def test_plain_solve_latched_case_matches_oracle(halo_small):
     """The latched case switch, step matched against the oracle on a halo
     where the unlatched rule would cycle."""

@@ -143,7 +143,7 @@ def gaussian_random_field(ng: int, slope: float, rng) -> np.ndarray:
     nz = k > 0
     amp[nz] = k[nz] ** (0.5 * slope)
     noise = rng.standard_normal((ng, ng, ng))
-    field = np.fft.irfftn(np.fft.rfftn(noise) * amp, s=(ng, ng, ng))
+    field = np.fft.irfftn(np.fft.rfftn(noise) * amp, s=(ng, ng, ng), axes=(0, 1, 2))
     field -= field.mean()
     return field / field.std()
 
