@@ -83,7 +83,11 @@ def _load():
                 "oracle_rates": (None, [d, vp, vp, vp]),
                 "oracle_xeq": (d, [d, d, d, d, i]),
                 "oracle_solve": (i, [i64, vp, vp, vp, vp, vp, vp, vp, d, i, d, d,
-                                     vp, i, d, i, i, vp, vp, d, d, i, i, i, vp, vp, vp, vp, vp]),
+                                     vp, i, d, i, i, vp, vp, d, d, i, i, i, i, vp, vp, vp, vp, vp]),
+                "oracle_columns_nearfar": (None, [i64, vp, vp, vp, vp, vp, vp, i, d, d,
+                                                  vp, i64, vp, i, d, i, vp, vp]),
+                "oracle_slab_lngamma": (d, [d, d, d, i, d]),
+                "oracle_gamma_nearfar": (None, [vp, vp, i64, i, i, vp, vp, vp, vp, vp, vp, vp]),
                 "oracle_xeq_dgamma": (d, [d, d, d, d, i]),
                 "oracle_column_matrix": (None, [i64, vp, vp, vp, vp, vp, i, d, d,
                                                 vp, i64, vp, i, d, i, vp]),
@@ -225,7 +229,7 @@ def xeq(Gamma, nH, T, y=0.0, caseB=False):
 
 # -- driver (Sec. 4) ---------------------------------------------------------
 def solve(w, s, wts, dirs, tol=1e-3, tau_skip=1e-4, max_iter=100, case_rule=CASE_AUTO,
-          kernel=KERNEL_M4, y=0.0, x_start=None, sweeps=None, l_ray=None, blocks=1):
+          kernel=KERNEL_M4, y=0.0, x_start=None, sweeps=None, l_ray=None, blocks=1, near_far=False):
     """Iteration of Sec. 4: Jacobi (blocks=1) or the high-to-low density
     update order in `blocks` blocks.  ``sweeps`` = exact sweep count
     (step-matched mode) instead of the tolerance test.  Returns (x, frozen,
@@ -246,10 +250,57 @@ def solve(w, s, wts, dirs, tol=1e-3, tau_skip=1e-4, max_iter=100, case_rule=CASE
                               _p(dirs), dirs.shape[0],
                               float(w.l_ray if l_ray is None else l_ray), kernel,
                               s.shape[0], _p(s), _p(wts), float(tol), float(tau_skip),
-                              mi, case_rule, int(blocks), _p(xs), _p(x), _p(frozen), _p(caseB), _p(st))
+                              mi, case_rule, int(blocks), int(bool(near_far)), _p(xs), _p(x), _p(frozen),
+                              _p(caseB), _p(st))
+    if rc == 2:
+        raise ValueError("near_far needs blocks <= 1")
     return x, frozen.astype(bool), dict(sweeps=int(st[0]), max_rel_dx=float(st[1]),
                                         rays=float(st[2]), converged=(rc == 0),
                                         caseB=caseB.astype(bool))
+
+
+# -- near/far split and the slab solution (Sec. 3.3.3, App. slab) -----------
+def columns_nearfar(w, x, dirs, origins=None, l_ray=None, kernel=KERNEL_M4):
+    """(tau_far, tau_near) [n_orig, R]: far particles weighted by x, near
+    particles (whose smoothing sphere holds the origin) with x = 1."""
+    px, py, pz, h, m = _particles(w)
+    x = _f64(x)
+    dirs = _f64(dirs).reshape(-1, 3)
+    R = dirs.shape[0]
+    org = None if origins is None else np.ascontiguousarray(origins, dtype=np.int64)
+    n_orig = w.n if org is None else org.shape[0]
+    tf = np.zeros((n_orig, R))
+    tn = np.zeros((n_orig, R))
+    _load().oracle_columns_nearfar(w.n, _p(px), _p(py), _p(pz), _p(h), _p(m), _p(x),
+                                   int(w.periodic), float(w.box), float(w.unit_cm),
+                                   _p(org), n_orig, _p(dirs), R,
+                                   float(w.l_ray if l_ray is None else l_ray), kernel, _p(tf), _p(tn))
+    return tf, tn
+
+
+def slab_lngamma(Gamma0, nH, T, caseB, tau_near):
+    """ln Gamma at the bottom of the uniform slab (monochromatic, y = 0)."""
+    lib = _load()
+    G, nH, T, cb, tn = np.broadcast_arrays(np.atleast_1d(np.asarray(Gamma0, dtype=np.float64)),
+                                           np.asarray(nH, dtype=np.float64), np.asarray(T, dtype=np.float64),
+                                           np.asarray(caseB, dtype=bool), np.asarray(tau_near, dtype=np.float64))
+    return np.array([lib.oracle_slab_lngamma(float(g), float(a), float(t), int(c), float(u))
+                     for g, a, t, c, u in zip(G, nH, T, cb, tn)])
+
+
+def gamma_nearfar(tau_far, tau_near, s, w, nH, T, caseB):
+    """(ln(Gamma/Gamma_thin), Gamma) per origin with the slab solution."""
+    tf, tn = _f64(tau_far), _f64(tau_near)
+    n_orig, R = tf.shape
+    s, w = _f64(s), _f64(w)
+    nH = _f64(np.broadcast_to(nH, (n_orig,)))
+    T = _f64(np.broadcast_to(T, (n_orig,)))
+    cb = np.ascontiguousarray(np.broadcast_to(caseB, (n_orig,)), dtype=np.int32)
+    lr = np.zeros(n_orig)
+    g = np.zeros(n_orig)
+    _load().oracle_gamma_nearfar(_p(tf), _p(tn), n_orig, R, s.shape[0], _p(s), _p(w), _p(nH), _p(T),
+                                 _p(cb), _p(lr), _p(g))
+    return lr, g
 
 
 # -- derivatives (reverse mode, dense) ----------------------------------------

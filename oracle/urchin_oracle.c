@@ -290,6 +290,61 @@ void oracle_columns(int64_t n, const double* px, const double* py, const double*
     free(pts);
 }
 
+/* Near/far split of Sec. 3.3.3 (self-contribution to self-shielding in
+ * SPH): on the ray from particle i, a crossed particle j (periodic image
+ * r_j + a L) is near when r_i lies inside its smoothing sphere,
+ * |r_j + a L - r_i| < h_j, i.e. j contributes to the density at r_i in
+ * Eq. nhi (the particle itself included); every other crossed particle is
+ * far.  For origins[o] (NULL = all particles) and direction k:
+ *   tau_far[o*R+k]  = sigma_th sum_far  (m_j x_j / m_p) int_0^l W dl
+ *   tau_near[o*R+k] = sigma_th sum_near (m_j / m_p) int_0^l W dl   (neutral
+ *                     fractions set to one: the slab thickness tau_H^near). */
+void oracle_columns_nearfar(int64_t n, const double* px, const double* py, const double* pz,
+                            const double* h, const double* mass_H, const double* x,
+                            int periodic, double L, double unit_cm,
+                            const int64_t* origins, int64_t n_orig,
+                            const double* dirs, int R, double l_ray, int kernel,
+                            double* tau_far, double* tau_near)
+{
+    int nimg = image_range(periodic, L, n, h, l_ray);
+    int64_t total = n_orig * (int64_t)R;
+    double sth = oracle_sigma_th();
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t r = 0; r < total; ++r) {
+        int64_t o = r / R;
+        int k = (int)(r % R);
+        int64_t i = origins ? origins[o] : o;
+        const double* dir = dirs + 3 * k;
+        double far = 0.0, near = 0.0;
+        for (int64_t j = 0; j < n; ++j) {
+            double hj = h[j];
+            for (int a = -nimg; a <= nimg; ++a)
+            for (int bb = -nimg; bb <= nimg; ++bb)
+            for (int c = -nimg; c <= nimg; ++c) {
+                double dx = px[j] + (periodic ? a * L : 0.0) - px[i];
+                double dy = py[j] + (periodic ? bb * L : 0.0) - py[i];
+                double dz = pz[j] + (periodic ? c * L : 0.0) - pz[i];
+                double tc = dx * dir[0] + dy * dir[1] + dz * dir[2];
+                double cx = dy * dir[2] - dz * dir[1];
+                double cy = dz * dir[0] - dx * dir[2];
+                double cz = dx * dir[1] - dy * dir[0];
+                double b2 = cx * cx + cy * cy + cz * cz;
+                if (b2 >= hj * hj) continue;
+                double half = sqrt(hj * hj - b2);
+                double t1 = fmax(0.0, tc - half), t2 = fmin(l_ray, tc + half);
+                if (t2 <= t1) continue;
+                double F = oracle_chord(kernel, sqrt(b2) / hj, (t1 - tc) / hj, (t2 - tc) / hj);
+                double hcm = hj * unit_cm;
+                double col = mass_H[j] * (8.0 / OR_PI) / (hcm * hcm) * F;
+                if (dx * dx + dy * dy + dz * dz < hj * hj) near += col;
+                else far += col * x[j];
+            }
+        }
+        tau_far[r] = sth * far;
+        tau_near[r] = sth * near;
+    }
+}
+
 /* ------------------------------------------------------------------------ */
 /* HEALPix ray directions (Sec. 3.2; Gorski et al. 2005 ring scheme).       */
 /* ------------------------------------------------------------------------ */
@@ -415,6 +470,79 @@ double oracle_xeq_dgamma(double Gamma, double nH, double T, double y, int caseB)
     return x / (2.0 * R * x + Q);
 }
 
+/* Photoionisation rate at the far side of a uniform hydrogen slab (App.
+ * "Neutral fraction in a plane parallel slab", y = 0): monochromatic
+ * radiation at the threshold with rate Gamma0 at the surface, density nH,
+ * temperature T, recombination case caseB, slab thickness
+ * tau_near = N_H sigma_th (all hydrogen, neutral or not).  In equilibrium
+ * Gamma(z) x = nH X(x), X = alpha (1-x)^2 - gamma (1-x) x, and the depth at
+ * which the neutral fraction is x obeys
+ *   z nH sigma = (1/x0 - 1/x) + ln[x (1-x0) / (x0 (1-x))]
+ *                + (1/x_ce) ln[x (x_ce - x0) / (x0 (x_ce - x))],
+ * with x0 = x(0) (equilibrium with Gamma0) and x_ce = alpha/(alpha+gamma).
+ * Solved for the bottom value x_b at z nH sigma = tau_near by bisection in
+ * v = ln(x_ce - x), then Gamma_b = nH X(x_b) / x_b, written as
+ * nH (1-x_b) (alpha+gamma) (x_ce - x_b) / x_b.  Returns ln Gamma_b
+ * (-inf for Gamma0 = 0). */
+double oracle_slab_lngamma(double Gamma0, double nH, double T, int caseB, double tau_near)
+{
+    if (!(Gamma0 > 0.0)) return -INFINITY;
+    if (tau_near <= 0.0) return log(Gamma0);
+    double aA, aB, gc;
+    oracle_rates(T, &aA, &aB, &gc);
+    double alpha = caseB ? aB : aA;
+    double ag = alpha + gc;
+    double xce = alpha / ag;
+    double x0 = oracle_xeq(Gamma0, nH, T, 0.0, caseB);
+    /* x_ce - x0 from the equilibrium at the surface, Gamma0 x0 = nH (1-x0) (alpha+gamma) (x_ce - x0) */
+    double d0 = Gamma0 * x0 / (nH * (1.0 - x0) * ag);
+    double vhi = log(d0);                          /* x = x0: depth 0 */
+    double vlo = vhi - (xce * tau_near + 50.0);    /* deeper than the slab */
+    for (int it = 0; it < 400; ++it) {
+        double v = 0.5 * (vlo + vhi);
+        double e = exp(v);
+        double x = xce - e;
+        double depth = (1.0 / x0 - 1.0 / x) + log(x * (1.0 - x0) / (x0 * (1.0 - x)))
+                       + (1.0 / xce) * (log(x / x0) + log(d0) - v);
+        if (depth > tau_near) vlo = v;
+        else vhi = v;
+    }
+    double v = 0.5 * (vlo + vhi);
+    double x = xce - exp(v);
+    return log(nH) + log(1.0 - x) + log(ag) + v - log(x);
+}
+
+/* Shielded rate with the near/far split (Sec. 3.3.3, Eqs. gammafar,
+ * gammashldk, gammashld): per ray Gamma_far = sum_j w_j exp(-s_j tau_far),
+ * Gamma_shld,k = G(Gamma_far, nH, T, tau_near) with G the slab solution
+ * above, Gamma = (1/R) sum_k Gamma_shld,k (the 4 pi / N_ray absorbed in w).
+ * caseB[o] is the recombination case used inside the slab.  Writes
+ * ln(Gamma / Gamma_thin) per origin (log-sum-exp over rays, finite where
+ * Gamma underflows) and Gamma. */
+void oracle_gamma_nearfar(const double* tau_far, const double* tau_near, int64_t n_orig, int R, int F,
+                          const double* s, const double* w, const double* nH, const double* T,
+                          const int* caseB, double* lnratio_out, double* gamma_out)
+{
+    double gthin = 0.0;
+    for (int j = 0; j < F; ++j) gthin += w[j];
+#pragma omp parallel for schedule(static)
+    for (int64_t o = 0; o < n_orig; ++o) {
+        double lk[512];
+        double m = -INFINITY;
+        for (int k = 0; k < R; ++k) {
+            double gf = 0.0;
+            for (int j = 0; j < F; ++j) gf += w[j] * exp(-s[j] * tau_far[o * R + k]);
+            lk[k] = oracle_slab_lngamma(gf, nH[o], T[o], caseB[o], tau_near[o * R + k]) - log(gthin);
+            if (lk[k] > m) m = lk[k];
+        }
+        double acc = 0.0;
+        for (int k = 0; k < R; ++k) acc += exp(lk[k] - m);
+        double lr = m + log(acc / (double)R);
+        lnratio_out[o] = lr;
+        gamma_out[o] = gthin * exp(lr);
+    }
+}
+
 /* Case choice (Sec. 3.3.3 / Sec. 4): 0 = always A, 1 = always B,
  * 2 = B when tau_eff >= 1.  In the iteration driver rule 2 is latched: a
  * particle that has once had tau_eff >= 1 keeps case B (see oracle_solve). */
@@ -450,6 +578,11 @@ static int use_caseB(int case_rule, double tau_eff)
  * contiguous blocks of sizes floor((b+1) m / blocks) - floor(b m / blocks),
  * and each sweep updates block after block, every block's columns using the
  * x of the blocks already updated in that sweep.
+ * near_far = 1 replaces the columns and Gamma by the near/far split of
+ * Sec. 3.3.3 (oracle_columns_nearfar, oracle_gamma_nearfar): the slab of
+ * near particles uses each particle's case before the sweep (its latch, or
+ * the forced case), then tau_eff = -ln(Gamma/Gamma_thin) decides the case
+ * of the update as above.  It needs blocks <= 1 (returns 2 otherwise).
  * x_out[n] receives the final x, frozen_out[n] (optional) 1 for frozen
  * particles, caseB_out[n] (optional) 1 where the final update used case B,
  * stats[0] = sweeps done, stats[1] = last max |dx|/x,
@@ -471,15 +604,20 @@ int oracle_solve(int64_t n, const double* px, const double* py, const double* pz
                  double y, int periodic, double L, double unit_cm,
                  const double* dirs, int R, double l_ray, int kernel,
                  int F, const double* s, const double* w,
-                 double tol, double tau_skip, int max_iter, int case_rule, int blocks,
+                 double tol, double tau_skip, int max_iter, int case_rule, int blocks, int near_far,
                  const double* x_start, double* x_out, int* frozen_out, int* caseB_out, double* stats)
 {
+    if (near_far && blocks > 1) return 2;
     double gthin = 0.0;
     for (int j = 0; j < F; ++j) gthin += w[j];
     double* x = x_out;
     int* frozen = (int*)calloc((size_t)n, sizeof(int));
     int* latchB = (int*)calloc((size_t)n, sizeof(int));
     double* tau = (double*)malloc(sizeof(double) * (size_t)n * R);
+    double* tau_nr = near_far ? (double*)malloc(sizeof(double) * (size_t)n * R) : NULL;
+    double* nH_o = near_far ? (double*)malloc(sizeof(double) * (size_t)n) : NULL;
+    double* T_o = near_far ? (double*)malloc(sizeof(double) * (size_t)n) : NULL;
+    int* cb_o = near_far ? (int*)malloc(sizeof(int) * (size_t)n) : NULL;
     double* G = (double*)malloc(sizeof(double) * (size_t)n);
     double* te = (double*)malloc(sizeof(double) * (size_t)n);
     double* xn = (double*)malloc(sizeof(double) * (size_t)n);
@@ -494,9 +632,22 @@ int oracle_solve(int64_t n, const double* px, const double* py, const double* pz
     for (int64_t i = 0; i < n; ++i) act[i] = i;
     while (sweeps < limit) {
         if (sweeps == 0 || blocks <= 1) {
-            oracle_columns(n, px, py, pz, h, mass_H, x, periodic, L, unit_cm,
-                           act, nact, dirs, R, l_ray, kernel, tau);
-            oracle_gamma(tau, nact, R, F, s, w, G, te);
+            if (near_far) {
+                oracle_columns_nearfar(n, px, py, pz, h, mass_H, x, periodic, L, unit_cm,
+                                       act, nact, dirs, R, l_ray, kernel, tau, tau_nr);
+                for (int64_t o = 0; o < nact; ++o) {
+                    int64_t i = act[o];
+                    nH_o[o] = nH[i];
+                    T_o[o] = T[i];
+                    cb_o[o] = use_caseB(case_rule, 0.0) || (case_rule == 2 && latchB[i]);
+                }
+                oracle_gamma_nearfar(tau, tau_nr, nact, R, F, s, w, nH_o, T_o, cb_o, te, G);
+                for (int64_t o = 0; o < nact; ++o) te[o] = -te[o];
+            } else {
+                oracle_columns(n, px, py, pz, h, mass_H, x, periodic, L, unit_cm,
+                               act, nact, dirs, R, l_ray, kernel, tau);
+                oracle_gamma(tau, nact, R, F, s, w, G, te);
+            }
             rays += (double)nact * R;
             if (sweeps == 0) {
                 int64_t m = 0;
@@ -551,6 +702,7 @@ int oracle_solve(int64_t n, const double* px, const double* py, const double* pz
     if (caseB_out) for (int64_t i = 0; i < n; ++i) caseB_out[i] = frozen[i] ? use_caseB(case_rule, 0.0) : latchB[i];
     if (stats) { stats[0] = sweeps; stats[1] = maxrel; stats[2] = rays; }
     free(frozen); free(latchB); free(tau); free(G); free(te); free(xn); free(act);
+    free(tau_nr); free(nH_o); free(T_o); free(cb_o);
     return (fixed || converged) ? 0 : 1;
 }
 

@@ -1,0 +1,111 @@
+"""Pins of the oracle's near/far split and slab solution (Sec. 3.3.3 and
+the appendix on a plane-parallel slab), CPU only."""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+scipy_integrate = pytest.importorskip("scipy.integrate")
+
+
+def _slab_by_ode(G0, nH, T, caseB, tau_near):
+    """ln Gamma at depth tau_near by integrating the slab equations directly:
+    with t = sigma_th nH z, dtau_HI/dt = x(t), x(t) the equilibrium neutral
+    fraction at Gamma(t) = G0 exp(-tau_HI(t)) (monochromatic at threshold)."""
+    def rhs(t, y):
+        return [O.xeq(G0 * np.exp(-y[0]), nH, T, 0.0, caseB)[0]]
+    sol = scipy_integrate.solve_ivp(rhs, (0.0, tau_near), [0.0], method="LSODA", rtol=1e-11, atol=1e-13)
+    return np.log(G0) - sol.y[0, -1]
+
+
+@pytest.mark.parametrize("caseB", [False, True])
+@pytest.mark.parametrize("ratio", [1e-3, 1.0, 30.0])
+@pytest.mark.parametrize("tau_near", [0.1, 3.0, 40.0])
+def test_slab_solution_matches_direct_integration(caseB, ratio, tau_near):
+    nH, T = 1e-3, 1e4
+    aA, aB, gc = O.rates(T)
+    G0 = ratio * (aB if caseB else aA) * nH
+    got = O.slab_lngamma(G0, nH, T, caseB, tau_near)[0]
+    ref = _slab_by_ode(G0, nH, T, caseB, tau_near)
+    assert abs(got - ref) <= 1e-7 * max(1.0, abs(ref))
+
+
+def test_slab_limits():
+    nH, T = 1e-2, 1e4
+    aA, aB, gc = O.rates(T)
+    G0 = 5.0 * aA * nH
+    assert O.slab_lngamma(G0, nH, T, False, 0.0)[0] == np.log(G0)
+    assert O.slab_lngamma(0.0, nH, T, False, 5.0)[0] == -np.inf
+    # deep in the slab the gas is at x_ce: Gamma falls as exp(-x_ce dtau)
+    xce = aA / (aA + gc)
+    l1 = O.slab_lngamma(G0, nH, T, False, 400.0)[0]
+    l2 = O.slab_lngamma(G0, nH, T, False, 500.0)[0]
+    assert abs((l2 - l1) / 100.0 + xce) < 1e-9
+    # thicker slabs shield more
+    vals = O.slab_lngamma(G0, nH, T, False, np.array([0.01, 0.1, 1.0, 10.0]))
+    assert np.all(np.diff(vals) < 0)
+
+
+def test_near_far_columns_partition_the_column():
+    """With every x = 1 the far and near columns add up to the full column,
+    and the origin itself is always near (periodic lattice and halo)."""
+    for w in (W.lattice_box(n_side=6, box_kpc=375.0, l_ray=250.0), W.halo(n=300, seed=3)):
+        dirs = O.healpix(1)
+        org = np.arange(0, w.n, 5)
+        one = np.ones(w.n)
+        tf, tn = O.columns_nearfar(w, one, dirs, origins=org)
+        tot = O.columns(w, one, dirs, origins=org)
+        np.testing.assert_allclose(tf + tn, tot, rtol=1e-12, atol=0)
+        assert (tn > 0).all()
+        # far columns scale with x, near columns do not
+        tf2, tn2 = O.columns_nearfar(w, 0.25 * one, dirs, origins=org)
+        np.testing.assert_allclose(tf2, 0.25 * tf, rtol=1e-13, atol=0)
+        np.testing.assert_allclose(tn2, tn, rtol=0, atol=0)
+
+
+def test_near_set_is_the_scatter_neighbourhood():
+    """A particle is near for origin i exactly when it contributes to the
+    density at r_i in Eq. nhi: two particles, the second placed just inside
+    and just outside the first's... own smoothing radius of the second."""
+    base = W.halo(n=2, seed=1)
+    for inside, expect_near in ((0.99, True), (1.01, False)):
+        pos = np.array([[0.0, 0.0, 0.0], [inside * 2.0, 0.0, 0.0]], dtype=np.float32)
+        w = W.subset(base, np.arange(2))
+        w = w.__class__(**{**w.__dict__, "pos": pos, "h": np.array([1.0, 2.0], dtype=np.float32),
+                           "l_ray": 10.0})
+        d = np.array([[1.0, 0.0, 0.0]])
+        tf, tn = O.columns_nearfar(w, np.ones(2), d, origins=[0])
+        tot = O.columns(w, np.ones(2), d, origins=[0])
+        self_only = O.columns(W.subset(w, np.arange(1)), np.ones(1), d, origins=[0])
+        if expect_near:
+            assert tf[0, 0] == 0.0 and abs(tn[0, 0] - tot[0, 0]) <= 1e-12 * tot[0, 0]
+        else:
+            assert abs(tn[0, 0] - self_only[0, 0]) <= 1e-12 * self_only[0, 0]
+            assert abs(tf[0, 0] + tn[0, 0] - tot[0, 0]) <= 1e-12 * tot[0, 0]
+
+
+def test_gamma_nearfar_without_near_column_is_the_plain_rate():
+    rng = np.random.default_rng(4)
+    w = W.halo(n=10, seed=1)
+    e, J = w.spectrum()
+    s, wts = O.spectrum(e, J, w.gamma_thin)
+    tau = np.exp(rng.uniform(np.log(1e-3), np.log(20.0), (6, 12)))
+    lr, g = O.gamma_nearfar(tau, np.zeros_like(tau), s, wts, 1e-3, 1e4, False)
+    g0, te0 = O.gamma(tau, s, wts)
+    np.testing.assert_allclose(g, g0, rtol=1e-12)
+    np.testing.assert_allclose(-lr, te0, rtol=1e-11, atol=1e-14)
+
+
+def test_near_far_iteration_converges_faster_than_the_plain_scheme():
+    """Sec. 3.3.3: with the near particles modelled as a slab, Gamma of a
+    particle no longer depends on its own and its neighbours' x, which
+    removes the slow growth of neutral regions of the plain scheme."""
+    w = W.halo(n=400, seed=7, n0=0.3, F=20)
+    e, J = w.spectrum()
+    s, wts = O.spectrum(e, J, w.gamma_thin)
+    dirs = O.healpix(1)
+    xp, fp, sp = O.solve(w, s, wts, dirs, tol=1e-8, max_iter=3000)
+    xn, fn, sn = O.solve(w, s, wts, dirs, tol=1e-8, max_iter=3000, near_far=True)
+    assert sp["converged"] and sn["converged"]
+    assert sn["sweeps"] < sp["sweeps"]
