@@ -481,9 +481,16 @@ double oracle_xeq_dgamma(double Gamma, double nH, double T, double y, int caseB)
  *                + (1/x_ce) ln[x (x_ce - x0) / (x0 (x_ce - x))],
  * with x0 = x(0) (equilibrium with Gamma0) and x_ce = alpha/(alpha+gamma).
  * Solved for the bottom value x_b at z nH sigma = tau_near by bisection in
- * v = ln(x_ce - x), then Gamma_b = nH X(x_b) / x_b, written as
- * nH (1-x_b) (alpha+gamma) (x_ce - x_b) / x_b.  Returns ln Gamma_b
- * (-inf for Gamma0 = 0). */
+ * y = ln[x / (x_ce - x)], which resolves both a strongly ionised bottom
+ * (x << x_ce) and a neutral one (x_ce - x below double resolution); then
+ * Gamma_b = nH X(x_b) / x_b = nH (1-x_b) (alpha+gamma) (x_ce - x_b) / x_b.
+ * Every 1 - x is formed as c + (x_ce - x), c = 1 - x_ce = gamma/(alpha+gamma),
+ * and x_ce - x0 from the surface equilibrium D (c + D) = Gamma0 x0 /
+ * (nH (alpha+gamma)) (exact rewrites that do not cancel in cold, nearly
+ * neutral gas where x_ce rounds to 1).  Returns ln Gamma_b (-inf for
+ * Gamma0 = 0). */
+static double log1pexp(double y) { return y > 0.0 ? y + log1p(exp(-y)) : log1p(exp(y)); }
+
 double oracle_slab_lngamma(double Gamma0, double nH, double T, int caseB, double tau_near)
 {
     if (!(Gamma0 > 0.0)) return -INFINITY;
@@ -493,23 +500,24 @@ double oracle_slab_lngamma(double Gamma0, double nH, double T, int caseB, double
     double alpha = caseB ? aB : aA;
     double ag = alpha + gc;
     double xce = alpha / ag;
+    double c = gc / ag;                            /* 1 - x_ce */
     double x0 = oracle_xeq(Gamma0, nH, T, 0.0, caseB);
-    /* x_ce - x0 from the equilibrium at the surface, Gamma0 x0 = nH (1-x0) (alpha+gamma) (x_ce - x0) */
-    double d0 = Gamma0 * x0 / (nH * (1.0 - x0) * ag);
-    double vhi = log(d0);                          /* x = x0: depth 0 */
-    double vlo = vhi - (xce * tau_near + 50.0);    /* deeper than the slab */
+    double K = Gamma0 * x0 / (nH * ag);
+    double d0 = 2.0 * K / (c + sqrt(c * c + 4.0 * K));   /* x_ce - x0 */
+    double ylo = log(x0) - log(d0);                /* depth 0 */
+    double yhi = log(xce) - log(d0) + xce * tau_near + 50.0;   /* deeper than the slab */
     for (int it = 0; it < 400; ++it) {
-        double v = 0.5 * (vlo + vhi);
-        double e = exp(v);
-        double x = xce - e;
-        double depth = (1.0 / x0 - 1.0 / x) + log(x * (1.0 - x0) / (x0 * (1.0 - x)))
-                       + (1.0 / xce) * (log(x / x0) + log(d0) - v);
-        if (depth > tau_near) vlo = v;
-        else vhi = v;
+        double y = 0.5 * (ylo + yhi);
+        double lx = log(xce) - log1pexp(-y), le = log(xce) - log1pexp(y);
+        double x = exp(lx), e = exp(le);
+        double depth = (1.0 / x0 - 1.0 / x) + (lx - log(x0)) + log(c + d0) - log(c + e)
+                       + (1.0 / xce) * (lx - log(x0) + log(d0) - le);
+        if (depth > tau_near) yhi = y;
+        else ylo = y;
     }
-    double v = 0.5 * (vlo + vhi);
-    double x = xce - exp(v);
-    return log(nH) + log(1.0 - x) + log(ag) + v - log(x);
+    double y = 0.5 * (ylo + yhi);
+    double lx = log(xce) - log1pexp(-y), le = log(xce) - log1pexp(y);
+    return log(nH) + log(c + exp(le)) + log(ag) + le - lx;
 }
 
 /* Shielded rate with the near/far split (Sec. 3.3.3, Eqs. gammafar,
