@@ -202,6 +202,33 @@ URCHIN_API int urchin_trace_columns_noalloc(const urchin_bvh* bvh, const double*
                                             int kernel, int precision, void* tau_out,
                                             urchin_stream_t stream);
 
+/* Columns with the near/far split of Sec. 3.3.3: for the ray (o, k), a
+ * crossed particle j is near when the origin lies inside j's smoothing
+ * sphere (|r_j - r_o| < h_j, j contributes to the density at r_o in
+ * Eq. nhi; the origin itself is always near) and far otherwise:
+ *   tau_far_out[o*R + k]  = sigma_th sum_far  (m_j x_j / m_p) int W dt
+ *   tau_near_out[o*R + k] = sigma_th sum_near (m_j / m_p) int W dt   (x = 1)
+ * The near test is made in double from the float positions.  Arguments,
+ * layouts and errors as urchin_trace_columns. */
+URCHIN_API int urchin_trace_columns_nearfar(const urchin_bvh* bvh, const double* x, const double* dirs, int R,
+                                            double l_ray, const int32_t* origins, int64_t n_orig, int kernel,
+                                            int precision, void* tau_far_out, void* tau_near_out,
+                                            urchin_stream_t stream);
+
+/* Shielded rate with the near/far split (Eqs. gammafar, gammashldk,
+ * gammashld): per ray the far rate Gamma_far,k = sum_j w_j exp(-s_j tau_far,k)
+ * lights a uniform hydrogen slab of thickness tau_near,k with the origin's
+ * nH and T (device [n_orig] double) and recombination case (caseB device
+ * [n_orig], nonzero = case B; NULL = case A); the slab solution of the
+ * appendix (monochromatic at the threshold, y = 0) gives the rate at its far
+ * side, and gamma_out[o] = (1/R) sum_k of those.  tau_eff_out as in
+ * urchin_gamma (may be NULL).  tau_far / tau_near as written by
+ * urchin_trace_columns_nearfar.  Errors: ERR_ARG, ERR_CUDA. */
+URCHIN_API int urchin_gamma_nearfar(const void* tau_far, const void* tau_near, int precision, int64_t n_orig,
+                                    int R, const urchin_spectrum* sp, const double* nH, const double* T,
+                                    const unsigned char* caseB, double* gamma_out, float* tau_eff_out,
+                                    urchin_stream_t stream);
+
 /* Shielded rate, Eq. gamma_shld: for each of n_orig particles with R columns
  * tau[o*R + k] (float for URCHIN_F32, double for URCHIN_F64),
  *   gamma_out[o]   = (1/R) sum_k sum_j w_j exp(-s_j tau_ok)     (device, double)
@@ -269,6 +296,16 @@ typedef struct {
                                      reads each particle's final state,
                                      bit 0 = recombination case B,
                                      bit 1 = frozen after sweep 0             */
+    int             near_far;     /* 1: the near/far split of Sec. 3.3.3 (plain
+                                     method, blocks <= 1, y = 0): far
+                                     particles give tau_far, the origin's
+                                     near particles (those whose smoothing
+                                     sphere holds it) a slab of thickness
+                                     tau_near (x = 1); each ray's rate is the
+                                     slab solution at the far-attenuated
+                                     surface rate (monochromatic slab at the
+                                     threshold, the slab appendix), in the
+                                     particle's case before the sweep        */
 } urchin_solve_params;
 
 typedef struct {

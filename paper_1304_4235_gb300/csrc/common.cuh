@@ -180,6 +180,11 @@ struct TraceJob {
     double* xbar;                 // mode 3: [n] Morton order, accumulated with atomics
     const int32_t* order;         // [R * n_items] or NULL: order[k * n_items + i] = the item that the
                                   // i-th lane slot of direction k traces (ray_order)
+    int near_far;                 // 1: split near / far particles (Sec. 3.3.3): out (and the stored
+                                  //    segments, and the hit counts) take far particles only
+    void* out_near;               // near_far: hydrogen column (x = 1) of the near particles, in tau units,
+                                  //    at [origin's Morton slot + k * near_k_stride] (modes 0 and 2)
+    int64_t near_k_stride;
 };
 int launch_trace(const TraceJob& job, cudaStream_t s);
 

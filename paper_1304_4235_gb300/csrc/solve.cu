@@ -139,6 +139,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs A)
         if (local < rows_per_block && row < A.n_items) {
             const Real tau = static_cast<const Real*>(A.tau)[row + (int64_t)k * A.k_stride];
             Real S = Real(0), c = Real(0), S2 = Real(0), c2 = Real(0);
+            // (near/far: tau is the far column; the slab of near particles is applied below)
             for (int j = 0; j < A.F; ++j) {
                 const Real v = wn[j] * exp2_p(-e2[j] * tau);
                 const Real yy = v - c;
@@ -154,7 +155,16 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs A)
                 }
             }
             // ln(Gamma_k / Gamma_thin) = -s_min tau_k + ln S_k
-            lk[local * A.R + k] = -smin * tau + log_p(S);
+            Real lkv = -smin * tau + log_p(S);
+            if (A.near_far) {
+                // Eq. gammashldk: the far rate enters the slab of near particles, in the
+                // particle's recombination case before this sweep
+                const int32_t ir = A.items ? A.items[row] : (int32_t)row;
+                const bool cB = A.case_rule == URCHIN_CASE_B || (A.case_rule == URCHIN_CASE_AUTO && A.latch[ir]);
+                const double tn = (double)static_cast<const Real*>(A.tau_near)[ir + (int64_t)k * A.near_k_stride];
+                lkv = (Real)slab_lnratio((double)lkv, gthin, tn, A.nH[ir], cB ? A.aB[ir] : A.aA[ir], A.gc[ir]);
+            }
+            lk[local * A.R + k] = lkv;
             if (A.want_tangent) lk2[local * A.R + k] = -smin * tau + log_p(S2 > Real(1e-37) ? S2 : Real(1e-37));
         }
         __syncthreads();
@@ -588,6 +598,7 @@ int Solver::init(const urchin_bvh* bvh_, const urchin_solve_params* P_, double* 
     size_t o_latch = lay.take((size_t)n);
     size_t o_list = lay.take(sizeof(int32_t) * (size_t)n);
     size_t o_tau = lay.take(rsz * (size_t)rays);
+    size_t o_tn = lay.take(P.near_far ? rsz * (size_t)rays : 0);
     size_t o_comp = lay.take(compact_tmp_bytes(n));
     size_t o_cnt = lay.take(may_store ? sizeof(uint32_t) * (size_t)rays : 0);
     size_t o_rp = lay.take(may_store ? sizeof(uint64_t) * (size_t)(rays + 1) : 0);
@@ -613,6 +624,7 @@ int Solver::init(const urchin_bvh* bvh_, const urchin_solve_params* P_, double* 
     latch = scr.at<uint8_t>(o_latch);
     list = scr.at<int32_t>(o_list);
     tau = scr.at<void>(o_tau);
+    tau_near = P.near_far ? scr.at<void>(o_tn) : nullptr;
     comp_tmp = scr.at<void>(o_comp);
     counter = reinterpret_cast<unsigned*>(misc + 1);
     status = counter + 1;
@@ -757,6 +769,9 @@ int Solver::trace(const int32_t* items, int64_t n_items, const float* tw32, cons
     job.kernel = P.kernel;
     job.precision = P.precision;
     job.mode = 0;
+    job.near_far = P.near_far;
+    job.out_near = tau_near;
+    job.near_k_stride = n;
     URCHIN_TRY(order_for(items, n_items, &job.order));
     URCHIN_TRY(timed_trace(job));
     stats.traversals += 1;
@@ -807,6 +822,9 @@ int Solver::columns(const int32_t* items, int64_t n_items, int sweep0)
     job.precision = P.precision;
     job.mode = 1;
     job.counts = counts;
+    job.near_far = P.near_far;
+    job.out_near = tau_near;
+    job.near_k_stride = n;
     URCHIN_TRY(order_for(items, n_items, &job.order));
     URCHIN_TRY(timed_trace(job));
     const int64_t rays = (int64_t)P.R * n_items;
@@ -928,6 +946,9 @@ SweepArgs Solver::sweep_args(const int32_t* items, int64_t n_items, int sweep0)
     A.n_switch = misc + 8;
     A.tol = P.tol;
     A.status = status;
+    A.near_far = P.near_far;
+    A.tau_near = tau_near;
+    A.near_k_stride = n;
     return A;
 }
 
@@ -1668,6 +1689,7 @@ extern "C" int urchin_tangent(const urchin_bvh* bvh, const urchin_solve_params* 
         return set_error(URCHIN_ERR_ARG, "urchin_tangent: unknown precision");
     if (P->case_rule != URCHIN_CASE_A && P->case_rule != URCHIN_CASE_B && P->case_rule != URCHIN_CASE_AUTO)
         return set_error(URCHIN_ERR_ARG, "urchin_tangent: unknown case_rule");
+    if (P->near_far) return set_error(URCHIN_ERR_ARG, "urchin_tangent: no tangent of the near/far split");
     urchin_solve_params Q = *P;
     Q.warm_start = 1;
     Q.segments = URCHIN_SEG_RECOMPUTE;
@@ -1730,6 +1752,9 @@ extern "C" int urchin_solve(const urchin_bvh* bvh, const urchin_solve_params* P,
     URCHIN_TRY(check_solve_params("urchin_solve", bvh, P, x_inout));
     if (P->method != URCHIN_METHOD_PLAIN && (P->gmres_m < 1 || P->gmres_m > 64))
         return set_error(URCHIN_ERR_ARG, "urchin_solve: gmres_m must be in [1, 64]");
+    if (P->near_far != 0 && P->near_far != 1) return set_error(URCHIN_ERR_ARG, "urchin_solve: near_far must be 0 or 1");
+    if (P->near_far && (P->method != URCHIN_METHOD_PLAIN || P->blocks > 1 || P->y != 0.0))
+        return set_error(URCHIN_ERR_ARG, "urchin_solve: the near/far split needs the plain Jacobi method and y = 0");
     cudaStream_t s = (cudaStream_t)stream;
     Solver S;
     int st = S.init(bvh, P, x_inout, s);
@@ -1761,6 +1786,7 @@ extern "C" int urchin_solve_vjp(const urchin_bvh* bvh, const urchin_solve_params
     URCHIN_TRY(check_solve_params("urchin_solve_vjp", bvh, P, x_star));
     if (!x_bar || !w_bar || !P->state)
         return set_error(URCHIN_ERR_ARG, "urchin_solve_vjp: NULL x_bar, w_bar or params->state");
+    if (P->near_far) return set_error(URCHIN_ERR_ARG, "urchin_solve_vjp: no adjoint of the near/far split");
     if (P->gmres_m < 1 || P->gmres_m > 64)
         return set_error(URCHIN_ERR_ARG, "urchin_solve_vjp: gmres_m must be in [1, 64]");
     urchin_solve_params Q = *P;

@@ -43,6 +43,9 @@ struct SweepArgs {
     unsigned* status;
     double* gamma_out;         // [n_items] optional
     float* tau_eff_out;        // [n_items] optional
+    int near_far;              // Sec. 3.3.3 split: tau holds the far columns; the near
+    const void* tau_near;      //   columns (x = 1) are at tau_near[i + k * near_k_stride]
+    int64_t near_k_stride;     //   (i the Morton slot) and enter through the slab solution
     int want_tangent;          // Newton: keep x, emit E and tangent factors
     double* ctan;              // [n_items * R] (k-major, stride k_stride)
     double* xeq_out;           // [n_items]
@@ -76,6 +79,7 @@ struct Solver {
     uint8_t* latch = nullptr;
     int32_t* list = nullptr;
     void* tau = nullptr;
+    void* tau_near = nullptr;                    // near/far: [R * n] near columns, Morton slot + k n
     void* comp_tmp = nullptr;
     unsigned long long* hits = nullptr;          // misc[3..5], counted when P.profile
     std::vector<cudaEvent_t> events;             // start/stop pairs of each timed launch

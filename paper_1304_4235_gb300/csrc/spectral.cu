@@ -257,6 +257,58 @@ __global__ void k_equilibrium_vjp(const double* __restrict__ gamma, const float*
     }
 }
 
+// Near/far rate per origin (Eqs. gammafar, gammashldk, gammashld), one
+// thread per origin, in double: ln(Gamma_far,k / Gamma_thin) by the factored
+// fold, the slab solution per ray, then a log-sum-exp over the rays.
+template <typename Real>
+__global__ void k_gamma_nearfar(const Real* __restrict__ tf, const Real* __restrict__ tn, int64_t n_orig, int R,
+                                const double* __restrict__ sv, const double* __restrict__ wv, int F,
+                                const double* __restrict__ nH, const double* __restrict__ T,
+                                const uint8_t* __restrict__ caseB, double* gamma_out, float* tau_eff_out)
+{
+    extern __shared__ double sm[];
+    double* ss = sm;
+    double* ws = sm + F;
+    __shared__ double sh[2];
+    if (threadIdx.x == 0) {
+        double g = 0.0, m = sv[0];
+        for (int b = 0; b < F; ++b) {
+            g += wv[b];
+            m = fmin(m, sv[b]);
+        }
+        sh[0] = g;
+        sh[1] = m;
+    }
+    __syncthreads();
+    const double gthin = sh[0], smin = sh[1];
+    for (int b = threadIdx.x; b < F; b += blockDim.x) {
+        ss[b] = sv[b] - smin;
+        ws[b] = wv[b] / gthin;
+    }
+    __syncthreads();
+    for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < n_orig; o += (int64_t)gridDim.x * blockDim.x) {
+        const Rates r = hg97_rates(T[o]);
+        const double alpha = (caseB && caseB[o]) ? r.alphaB : r.alphaA;
+        double m = -INFINITY, acc = 0.0;
+        for (int k = 0; k < R; ++k) {
+            const double t = (double)tf[o * R + k];
+            double S = 0.0;
+            for (int b = 0; b < F; ++b) S += ws[b] * exp(-ss[b] * t);
+            const double l = slab_lnratio(-smin * t + log(S), gthin, (double)tn[o * R + k], nH[o], alpha, r.gamma_c);
+            if (!(l > -INFINITY)) continue;
+            if (l > m) {
+                acc = acc * exp(m - l) + 1.0;
+                m = l;
+            } else {
+                acc += exp(l - m);
+            }
+        }
+        const double lr = m + log(acc / (double)R);
+        gamma_out[o] = gthin * exp(lr);
+        if (tau_eff_out) tau_eff_out[o] = (float)(-lr);
+    }
+}
+
 template <typename Real>
 int gamma_vjp_t(const Real* tau, int64_t n_orig, int R, const urchin_spectrum* sp, const double* gbar,
                 Real* tau_bar, double* w_bar, cudaStream_t s)
@@ -420,5 +472,43 @@ extern "C" int urchin_equilibrium_vjp(const double* gamma, const float* tau_eff,
     cudaStream_t s = (cudaStream_t)stream;
     unsigned grid = (unsigned)std::min<int64_t>((n + 255) / 256, 4096);
     k_equilibrium_vjp<<<grid, 256, 0, s>>>(gamma, tau_eff, nH, T, n, case_rule, y, x_bar, gamma_bar_out);
+    return launched();
+}
+
+extern "C" int urchin_gamma_nearfar(const void* tau_far, const void* tau_near, int precision, int64_t n_orig, int R,
+                                    const urchin_spectrum* sp, const double* nH, const double* T,
+                                    const unsigned char* caseB, double* gamma_out, float* tau_eff_out,
+                                    urchin_stream_t stream)
+{
+    using namespace urchin;
+    clear_error();
+    if (precision != URCHIN_F32 && precision != URCHIN_F64)
+        return set_error(URCHIN_ERR_ARG, "urchin_gamma_nearfar: unknown precision %d", precision);
+    if (R < 1 || R > URCHIN_MAX_RAYS) return set_error(URCHIN_ERR_ARG, "urchin_gamma_nearfar: R = %d out of range", R);
+    if (n_orig < 0) return set_error(URCHIN_ERR_ARG, "urchin_gamma_nearfar: n_orig < 0");
+    if (!sp || !sp->s || !sp->w) return set_error(URCHIN_ERR_ARG, "urchin_gamma_nearfar: NULL spectrum");
+    if (sp->F < 1 || sp->F > URCHIN_MAX_BINS)
+        return set_error(URCHIN_ERR_ARG, "urchin_gamma_nearfar: F = %d out of range [1, %d]", sp->F, URCHIN_MAX_BINS);
+    if (n_orig == 0) return URCHIN_OK;
+    if (!tau_far || !tau_near || !nH || !T || !gamma_out)
+        return set_error(URCHIN_ERR_ARG, "urchin_gamma_nearfar: NULL tau_far, tau_near, nH, T or gamma_out");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t smem = sizeof(double) * 2 * (size_t)sp->F;
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n_orig + 127) / 128, 4096));
+    if (precision == URCHIN_F64) {
+        if (smem > 48 * 1024)
+            URCHIN_TRY_CUDA(cudaFuncSetAttribute(k_gamma_nearfar<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)smem));
+        k_gamma_nearfar<double><<<grid, 128, smem, s>>>(static_cast<const double*>(tau_far),
+                                                        static_cast<const double*>(tau_near), n_orig, R, sp->s,
+                                                        sp->w, sp->F, nH, T, caseB, gamma_out, tau_eff_out);
+    } else {
+        if (smem > 48 * 1024)
+            URCHIN_TRY_CUDA(cudaFuncSetAttribute(k_gamma_nearfar<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)smem));
+        k_gamma_nearfar<float><<<grid, 128, smem, s>>>(static_cast<const float*>(tau_far),
+                                                       static_cast<const float*>(tau_near), n_orig, R, sp->s,
+                                                       sp->w, sp->F, nH, T, caseB, gamma_out, tau_eff_out);
+    }
     return launched();
 }

@@ -63,4 +63,73 @@ __device__ __forceinline__ double dx_dgamma(double x, double nH, double alpha, d
     return x / (2.0 * Rc * x + Q);
 }
 
+// Near/far split (Sec. 3.3.3): the near particles of a ray's origin are
+// modelled as a uniform hydrogen slab of thickness tau_near = N_H sigma_th
+// (all hydrogen, x = 1), with the origin's density and temperature, lit by
+// the far-attenuated radiation with rate Gamma_far at its surface.  For
+// radiation at the threshold (the slab appendix, y = 0) the depth at which
+// the equilibrium neutral fraction is x obeys
+//   z nH sigma = (1/x0 - 1/x) + ln[x (1-x0) / (x0 (1-x))]
+//                + (1/x_ce) ln[x (x_ce - x0) / (x0 (x_ce - x))],
+// x0 the equilibrium at Gamma_far, x_ce = alpha / (alpha + gamma_c), and the
+// rate at depth x is nH (1-x)(alpha+gamma_c)(x_ce - x) / x.  Returns
+// ln(Gamma_bottom / Gamma_thin) from ln(Gamma_far / Gamma_thin): Newton's
+// method on y = ln[x / (x_ce - x)] (which resolves both a strongly ionised
+// bottom, x << x_ce, and a neutral one, x_ce - x below double resolution),
+// kept inside a bracket (bisection when a step leaves it).  Every 1 - x is
+// formed as c + (x_ce - x), c = 1 - x_ce = gamma_c / (alpha + gamma_c), and
+// x_ce - x0 from the surface equilibrium D (c + D) = Gamma_far x0 /
+// (nH (alpha + gamma_c)): no cancellation in cold, nearly neutral gas where
+// x_ce rounds to 1.
+__device__ __forceinline__ double log1pexp(double y) { return y > 0.0 ? y + log1p(exp(-y)) : log1p(exp(y)); }
+
+__device__ __forceinline__ double slab_lnratio(double lnr_far, double gthin, double tau_near, double nH,
+                                               double alpha, double gamma_c)
+{
+    if (!(tau_near > 0.0)) return lnr_far;
+    const double ag = alpha + gamma_c;
+    const double xce = alpha / ag;
+    const double G0 = gthin * exp(lnr_far);
+    if (!(G0 > 0.0)) return lnr_far - xce * tau_near;   // no ionised layer: neutral attenuation
+    const double c = gamma_c / ag;                      // 1 - x_ce
+    const double x0 = x_equilibrium(G0, nH, alpha, gamma_c, 0.0);
+    const double K = G0 * x0 / (nH * ag);
+    const double d0 = 2.0 * K / (c + sqrt(c * c + 4.0 * K));   // x_ce - x0
+    const double lxce = log(xce), lx0 = log(x0), ld0 = log(d0);
+    // depth(y) - tau_near = c0 - 1/x + lx - log(c + e) + (lx - le) / x_ce - tau_near
+    const double c0 = 1.0 / x0 - lx0 + log(c + d0) + (ld0 - lx0) / xce;
+    double ylo = lx0 - ld0, yhi = lxce - ld0 + xce * tau_near + 50.0;
+    // first guess from the dominant terms: an ionised bottom where
+    // 1/x ~ 1/x0 - tau_near, else a neutral layer attenuating like x_ce
+    const double q = 1.0 / x0 - tau_near;
+    double y;
+    if (q * xce > 1.5) {
+        const double xg = 1.0 / q;
+        y = log(xg) - log(xce - xg);
+    } else {
+        y = lxce - ld0 + xce * (tau_near - (1.0 / x0 - 1.0 / xce));
+    }
+    y = fmin(yhi, fmax(ylo, y));
+    for (int it = 0; it < 100; ++it) {
+        const double lx = lxce - log1pexp(-y), le = lxce - log1pexp(y);
+        const double x = exp(lx), e = exp(le);
+        const double f = c0 - 1.0 / x + lx - log(c + e) + (lx - le) / xce - tau_near;
+        if (f > 0.0) yhi = y;                            // too deep
+        else ylo = y;
+        // d depth / dy with dx/dy = x e / x_ce (and x + e = x_ce)
+        const double fp = (e / x + e + x * e / (c + e) + 1.0) / xce;
+        double yn = y - f / fp;
+        if (fabs(yn - y) <= 1e-15 * (1.0 + fabs(y))) {   // converged (rounding may put it a hair
+            y = yn;                                        // outside the bracket)
+            break;
+        }
+        if (!(yn > ylo && yn < yhi)) yn = 0.5 * (ylo + yhi);
+        const bool done = yhi - ylo <= 1e-15 * (1.0 + fabs(y));
+        y = yn;
+        if (done) break;
+    }
+    const double lx = lxce - log1pexp(-y), le = lxce - log1pexp(y);
+    return log(nH) + log(c + exp(le)) + log(ag) + le - lx - log(gthin);
+}
+
 }  // namespace urchin

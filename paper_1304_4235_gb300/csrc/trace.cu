@@ -60,6 +60,9 @@ struct TraceParams {
     const void* coef;             // MODE_SCATTER: coefficient of each ray, indexed like out
     double* xbar;                 // MODE_SCATTER: xbar[j] += coef * A_j * chord integral (Morton)
     const int32_t* order;         // [R * n_items] per-direction item order, or NULL
+    // near/far split
+    void* out_near;               // [slot + k * near_k_stride] near column (x = 1)
+    int64_t near_k_stride;
 };
 
 constexpr int MODE_TAU = 0, MODE_COUNT = 1, MODE_FILL = 2, MODE_SCATTER = 3;
@@ -72,7 +75,21 @@ struct Sink {
     unsigned nhit, ntest;
     int64_t pos, end;
     Real coef;                    // MODE_SCATTER
+    Real near, near_c;            // near/far: near column and its compensation
+    double ox, oy, oz;            // near/far: shifted origin in double (the near test)
 };
+
+// Near/far split (Sec. 3.3.3): particle j is near the ray's origin when the
+// origin lies inside j's smoothing sphere.  Evaluated in double from the
+// float positions (the differences are exact), like the reference
+// definition, so both sides classify every pair the same way.
+template <typename Real>
+__device__ __forceinline__ bool is_near(const Sink<Real>& k, float4 q)
+{
+    const double ex = (double)q.x - k.ox, ey = (double)q.y - k.oy, ez = (double)q.z - k.oz;
+    const double hh = (double)q.w;
+    return ex * ex + ey * ey + ez * ez < hh * hh;
+}
 
 template <typename Real> struct RealOps;
 template <> struct RealOps<float> {
@@ -279,7 +296,7 @@ __device__ __forceinline__ float safe_inv(double d)
 
 // FP32 hit evaluation: cheap rejection, then the impact parameter from an
 // error-free cross product, then the tabulated / piecewise chord integral.
-template <int KERNEL, int MODE>
+template <int KERNEL, int MODE, bool NF>
 __device__ __forceinline__ void leaf_hits_f32(const TraceParams& P, const float2* tab, int ref, int cnt,
                                               float sx, float sy, float sz, float dx, float dy, float dz,
                                               float L, Sink<float>& k, unsigned& err)
@@ -300,7 +317,8 @@ __device__ __forceinline__ void leaf_hits_f32(const TraceParams& P, const float2
         float tc = ex * dx + ey * dy + ez * dz;
         float ch = sqrtf(h2 - b2);
         if (tc + ch <= 0.f || tc - ch >= L) continue;
-        ++k.nhit;
+        const bool near = NF && is_near(k, q);
+        if (!near) ++k.nhit;
         if (MODE == MODE_COUNT) continue;
         float ih = 1.f / q.w;
         float beta2 = b2 * ih * ih;
@@ -318,6 +336,10 @@ __device__ __forceinline__ void leaf_hits_f32(const TraceParams& P, const float2
             atomicAdd(P.xbar + j, (double)(k.coef * (__ldg(P.A32 + j) * F)));
             continue;
         }
+        if (near) {
+            Kahan::add(k.near, k.near_c, __ldg(P.A32 + j) * F);
+            continue;
+        }
         Kahan::add(k.sum, k.comp, __ldg(P.w32 + j) * F);
         if (MODE == MODE_FILL) {
             if (k.pos < k.end) {
@@ -331,7 +353,7 @@ __device__ __forceinline__ void leaf_hits_f32(const TraceParams& P, const float2
     }
 }
 
-template <typename Real, int KERNEL, int MODE>
+template <typename Real, int KERNEL, int MODE, bool NF>
 __device__ __forceinline__ void leaf_hits(const TraceParams& P, int ref, int cnt, Real sx, Real sy, Real sz,
                                           Real dx, Real dy, Real dz, Real L, Sink<Real>& k, unsigned& err)
 {
@@ -349,7 +371,8 @@ __device__ __forceinline__ void leaf_hits(const TraceParams& P, int ref, int cnt
         if (b2 >= h2) continue;
         Real ch = O::sqrt_(h2 - b2);
         if (tc + ch <= Real(0) || tc - ch >= L) continue;
-        ++k.nhit;
+        const bool near = NF && is_near(k, q);
+        if (!near) ++k.nhit;
         if (MODE == MODE_COUNT) continue;
         Real ih = Real(1) / h;
         Real beta2 = b2 * ih * ih;
@@ -369,6 +392,11 @@ __device__ __forceinline__ void leaf_hits(const TraceParams& P, int ref, int cnt
             atomicAdd(P.xbar + j, (double)(k.coef * (A * F)));
             continue;
         }
+        if (near) {
+            const Real A = sizeof(Real) == 4 ? Real(__ldg(P.A32 + j)) : Real(__ldg(P.A64 + j));
+            Kahan::add(k.near, k.near_c, A * F);
+            continue;
+        }
         Kahan::add(k.sum, k.comp, O::weight(P, j) * F);
         if (MODE == MODE_FILL) {
             if (k.pos < k.end) {
@@ -383,7 +411,7 @@ __device__ __forceinline__ void leaf_hits(const TraceParams& P, int ref, int cnt
     }
 }
 
-template <typename Real, int KERNEL, int MODE>
+template <typename Real, int KERNEL, int MODE, bool NF>
 __device__ void ray_column(const TraceParams& P, const float2* tab, float4 o, Real dx, Real dy, Real dz,
                            bool live, Sink<Real>& sk, unsigned& err, unsigned& nvisit)
 {
@@ -404,6 +432,11 @@ __device__ void ray_column(const TraceParams& P, const float2* tab, float4 o, Re
         Real sz = Real(o.z) - Real(az) * Real(P.Lbox);
         float fx = (float)sx, fy = (float)sy, fz = (float)sz;
         if (!__any_sync(0xffffffffu, live && seg_box(fx, fy, fz, ix, iy, iz, Lf, rlo, rhi))) continue;
+        if (NF) {
+            sk.ox = (double)o.x - (double)ax * P.Lbox;
+            sk.oy = (double)o.y - (double)ay * P.Lbox;
+            sk.oz = (double)o.z - (double)az * P.Lbox;
+        }
         int sp = 0;
         int node = 0;
         // a traversal visits every internal node at most once; the cap only
@@ -428,18 +461,18 @@ __device__ void ray_column(const TraceParams& P, const float2* tab, float4 o, Re
             if (hl && lcnt > 0) {
                 if (live) {
                     if constexpr (sizeof(Real) == 4)
-                        leaf_hits_f32<KERNEL, MODE>(P, tab, lref, lcnt, sx, sy, sz, dx, dy, dz, L, sk, err);
+                        leaf_hits_f32<KERNEL, MODE, NF>(P, tab, lref, lcnt, sx, sy, sz, dx, dy, dz, L, sk, err);
                     else
-                        leaf_hits<Real, KERNEL, MODE>(P, lref, lcnt, sx, sy, sz, dx, dy, dz, L, sk, err);
+                        leaf_hits<Real, KERNEL, MODE, NF>(P, lref, lcnt, sx, sy, sz, dx, dy, dz, L, sk, err);
                 }
                 hl = false;
             }
             if (hr && rcnt > 0) {
                 if (live) {
                     if constexpr (sizeof(Real) == 4)
-                        leaf_hits_f32<KERNEL, MODE>(P, tab, rref, rcnt, sx, sy, sz, dx, dy, dz, L, sk, err);
+                        leaf_hits_f32<KERNEL, MODE, NF>(P, tab, rref, rcnt, sx, sy, sz, dx, dy, dz, L, sk, err);
                     else
-                        leaf_hits<Real, KERNEL, MODE>(P, rref, rcnt, sx, sy, sz, dx, dy, dz, L, sk, err);
+                        leaf_hits<Real, KERNEL, MODE, NF>(P, rref, rcnt, sx, sy, sz, dx, dy, dz, L, sk, err);
                 }
                 hr = false;
             }
@@ -459,7 +492,7 @@ __device__ void ray_column(const TraceParams& P, const float2* tab, float4 o, Re
     }
 }
 
-template <typename Real, int KERNEL, int MODE>
+template <typename Real, int KERNEL, int MODE, bool NF>
 __global__ void __launch_bounds__(256) k_trace(TraceParams P)
 {
     extern __shared__ double s_dirs[];
@@ -489,7 +522,7 @@ __global__ void __launch_bounds__(256) k_trace(TraceParams P)
         float4 o = __ldg(P.xyzh + org);
         Real dx = Real(s_dirs[3 * k]), dy = Real(s_dirs[3 * k + 1]), dz = Real(s_dirs[3 * k + 2]);
         unsigned nvisit = 0;
-        Sink<Real> sk{Real(0), Real(0), 0u, 0u, 0, 0, Real(0)};
+        Sink<Real> sk{Real(0), Real(0), 0u, 0u, 0, 0, Real(0), Real(0), Real(0), 0.0, 0.0, 0.0};
         const int64_t ray = (int64_t)k * P.n_items + item;
         const int64_t orow = live ? (P.out_row ? (int64_t)P.out_row[item] : item) : 0;
         if (live && MODE == MODE_FILL) {
@@ -500,7 +533,7 @@ __global__ void __launch_bounds__(256) k_trace(TraceParams P)
             sk.coef = static_cast<const Real*>(P.coef)[orow * P.row_stride + (int64_t)k * P.k_stride];
             live = sk.coef != Real(0);
         }
-        ray_column<Real, KERNEL, MODE>(P, s_tab, o, dx, dy, dz, live, sk, err, nvisit);
+        ray_column<Real, KERNEL, MODE, NF>(P, s_tab, o, dx, dy, dz, live, sk, err, nvisit);
         if (slot < P.n_items) {
             hits += sk.nhit;
             tests += sk.ntest;
@@ -510,6 +543,11 @@ __global__ void __launch_bounds__(256) k_trace(TraceParams P)
             } else if (MODE != MODE_SCATTER) {
                 if (MODE == MODE_FILL && sk.pos != sk.end) err |= kStSegment;
                 static_cast<Real*>(P.out)[orow * P.row_stride + (int64_t)k * P.k_stride] = sk.sum;
+                if (NF) {
+                    const int64_t at = P.near_k_stride > 0 ? (int64_t)org + (int64_t)k * P.near_k_stride
+                                                           : orow * P.row_stride + (int64_t)k * P.k_stride;
+                    static_cast<Real*>(P.out_near)[at] = sk.near;
+                }
             }
         }
     }
@@ -528,10 +566,10 @@ __global__ void __launch_bounds__(256) k_trace(TraceParams P)
     }
 }
 
-template <typename Real, int KERNEL, int MODE>
+template <typename Real, int KERNEL, int MODE, bool NF>
 int launch_one(const TraceParams& P, cudaStream_t s)
 {
-    const void* fn = (const void*)k_trace<Real, KERNEL, MODE>;
+    const void* fn = (const void*)k_trace<Real, KERNEL, MODE, NF>;
     const size_t smem = sizeof(double) * 3 * (size_t)P.R +
                         ((sizeof(Real) == 4 && KERNEL == URCHIN_KERNEL_M4) ? sizeof(float2) * (kKTab + 1) : 0);
     int grid = 0;
@@ -539,28 +577,34 @@ int launch_one(const TraceParams& P, cudaStream_t s)
     int64_t tasks = P.n_chunks * P.R;
     int64_t need = (tasks + 7) / 8;       // 8 warps per block
     if (need < grid) grid = (int)std::max<int64_t>(need, 1);
-    k_trace<Real, KERNEL, MODE><<<grid, 256, smem, s>>>(P);
+    k_trace<Real, KERNEL, MODE, NF><<<grid, 256, smem, s>>>(P);
     URCHIN_TRY(launched());
     return URCHIN_OK;
 }
 
 template <typename Real, int KERNEL>
-int dispatch_k(const TraceParams& P, int mode, cudaStream_t s)
+int dispatch_k(const TraceParams& P, int mode, bool nf, cudaStream_t s)
 {
-    if (mode == MODE_COUNT) return launch_one<Real, KERNEL, MODE_COUNT>(P, s);
-    if (mode == MODE_FILL) return launch_one<Real, KERNEL, MODE_FILL>(P, s);
-    if (mode == MODE_SCATTER) return launch_one<Real, KERNEL, MODE_SCATTER>(P, s);
-    return launch_one<Real, KERNEL, MODE_TAU>(P, s);
+    if (nf) {
+        if (mode == MODE_COUNT) return launch_one<Real, KERNEL, MODE_COUNT, true>(P, s);
+        if (mode == MODE_FILL) return launch_one<Real, KERNEL, MODE_FILL, true>(P, s);
+        if (mode == MODE_SCATTER) return set_error(URCHIN_ERR_ARG, "trace: no transpose with the near/far split");
+        return launch_one<Real, KERNEL, MODE_TAU, true>(P, s);
+    }
+    if (mode == MODE_COUNT) return launch_one<Real, KERNEL, MODE_COUNT, false>(P, s);
+    if (mode == MODE_FILL) return launch_one<Real, KERNEL, MODE_FILL, false>(P, s);
+    if (mode == MODE_SCATTER) return launch_one<Real, KERNEL, MODE_SCATTER, false>(P, s);
+    return launch_one<Real, KERNEL, MODE_TAU, false>(P, s);
 }
 
-int dispatch_mode(const TraceParams& P, int precision, int kernel, int mode, cudaStream_t s)
+int dispatch_mode(const TraceParams& P, int precision, int kernel, int mode, bool nf, cudaStream_t s)
 {
     if (precision == URCHIN_F64) {
-        if (kernel == URCHIN_KERNEL_GT) return dispatch_k<double, URCHIN_KERNEL_GT>(P, mode, s);
-        return dispatch_k<double, URCHIN_KERNEL_M4>(P, mode, s);
+        if (kernel == URCHIN_KERNEL_GT) return dispatch_k<double, URCHIN_KERNEL_GT>(P, mode, nf, s);
+        return dispatch_k<double, URCHIN_KERNEL_M4>(P, mode, nf, s);
     }
-    if (kernel == URCHIN_KERNEL_GT) return dispatch_k<float, URCHIN_KERNEL_GT>(P, mode, s);
-    return dispatch_k<float, URCHIN_KERNEL_M4>(P, mode, s);
+    if (kernel == URCHIN_KERNEL_GT) return dispatch_k<float, URCHIN_KERNEL_GT>(P, mode, nf, s);
+    return dispatch_k<float, URCHIN_KERNEL_M4>(P, mode, nf, s);
 }
 
 }  // namespace
@@ -644,7 +688,11 @@ int launch_trace(const TraceJob& job, cudaStream_t s)
     P.coef = job.coef;
     P.xbar = job.xbar;
     P.order = job.order;
-    return dispatch_mode(P, job.precision, job.kernel, job.mode, s);
+    P.out_near = job.out_near;
+    P.near_k_stride = job.near_k_stride;
+    if (job.near_far && !job.out_near && job.mode != MODE_COUNT)
+        return set_error(URCHIN_ERR_ARG, "trace: near/far split without a near-column output");
+    return dispatch_mode(P, job.precision, job.kernel, job.mode, job.near_far != 0, s);
 }
 
 namespace {
@@ -812,16 +860,15 @@ __global__ void k_unpermute_add(const int32_t* __restrict__ perm, const double* 
 }  // namespace
 }  // namespace urchin
 
-extern "C" int urchin_trace_columns(const urchin_bvh* bvh, const double* x, const double* dirs, int R,
-                                    double l_ray, const int32_t* origins, int64_t n_orig, int kernel,
-                                    int precision, void* tau_out, urchin_stream_t stream)
+namespace urchin {
+namespace {
+
+int trace_columns_impl(const char* fn, const urchin_bvh* bvh, const double* x, const double* dirs, int R,
+                       double l_ray, const int32_t* origins, int64_t n_orig, int kernel, int precision,
+                       void* tau_out, void* near_out, cudaStream_t s)
 {
-    using namespace urchin;
-    clear_error();
-    cudaStream_t s = (cudaStream_t)stream;
     {
-        const int c = check_trace_args("urchin_trace_columns", bvh, x, dirs, R, l_ray, origins, n_orig, kernel,
-                                       precision, tau_out);
+        const int c = check_trace_args(fn, bvh, x, dirs, R, l_ray, origins, n_orig, kernel, precision, tau_out);
         if (c != URCHIN_OK) return c > 0 ? URCHIN_OK : c;
     }
     const int64_t n = bvh->n;
@@ -872,15 +919,42 @@ extern "C" int urchin_trace_columns(const urchin_bvh* bvh, const double* x, cons
         URCHIN_TRY(ray_order(bvh, job.items, n_orig, dirs, R, scr.at<int32_t>(o_ord), scr.at<void>(o_otmp), s));
         job.order = scr.at<int32_t>(o_ord);
     }
+    job.near_far = near_out ? 1 : 0;
+    job.out_near = near_out;
+    job.near_k_stride = 0;                      // same layout as tau_out
     URCHIN_TRY(launch_trace(job, s));
     unsigned st = 0;
     URCHIN_TRY_CUDA(cudaMemcpyAsync(&st, ctr + 1, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
     scr.release();
     URCHIN_TRY_CUDA(cudaStreamSynchronize(s));
-    if (st & kStOrigin) return set_error(URCHIN_ERR_ARG, "urchin_trace_columns: origin index out of range");
-    if (st & kStStack) return set_error(URCHIN_ERR_CUDA, "urchin_trace_columns: traversal stack overflow");
-    if (st & kStVisit) return set_error(URCHIN_ERR_CUDA, "urchin_trace_columns: malformed tree (visit limit)");
+    if (st & kStOrigin) return set_error(URCHIN_ERR_ARG, "%s: origin index out of range", fn);
+    if (st & kStStack) return set_error(URCHIN_ERR_CUDA, "%s: traversal stack overflow", fn);
+    if (st & kStVisit) return set_error(URCHIN_ERR_CUDA, "%s: malformed tree (visit limit)", fn);
     return URCHIN_OK;
+}
+
+}  // namespace
+}  // namespace urchin
+
+extern "C" int urchin_trace_columns(const urchin_bvh* bvh, const double* x, const double* dirs, int R,
+                                    double l_ray, const int32_t* origins, int64_t n_orig, int kernel,
+                                    int precision, void* tau_out, urchin_stream_t stream)
+{
+    urchin::clear_error();
+    return urchin::trace_columns_impl("urchin_trace_columns", bvh, x, dirs, R, l_ray, origins, n_orig, kernel,
+                                      precision, tau_out, nullptr, (cudaStream_t)stream);
+}
+
+extern "C" int urchin_trace_columns_nearfar(const urchin_bvh* bvh, const double* x, const double* dirs, int R,
+                                            double l_ray, const int32_t* origins, int64_t n_orig, int kernel,
+                                            int precision, void* tau_far_out, void* tau_near_out,
+                                            urchin_stream_t stream)
+{
+    urchin::clear_error();
+    if (n_orig > 0 && !tau_near_out)
+        return urchin::set_error(URCHIN_ERR_ARG, "urchin_trace_columns_nearfar: tau_near_out is NULL");
+    return urchin::trace_columns_impl("urchin_trace_columns_nearfar", bvh, x, dirs, R, l_ray, origins, n_orig,
+                                      kernel, precision, tau_far_out, tau_near_out, (cudaStream_t)stream);
 }
 
 extern "C" int urchin_trace_columns_vjp(const urchin_bvh* bvh, const double* dirs, int R, double l_ray,

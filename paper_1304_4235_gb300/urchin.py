@@ -57,7 +57,7 @@ class urchin_solve_params(C.Structure):
                 ("kernel", C.c_int), ("precision", C.c_int), ("case_rule", C.c_int),
                 ("warm_start", C.c_int), ("profile", C.c_int), ("history_maxrel", _vp),
                 ("history_unconverged", _vp), ("blocks", C.c_int), ("newton_switch", C.c_double),
-                ("newton_eta", C.c_double), ("state", _vp)]
+                ("newton_eta", C.c_double), ("state", _vp), ("near_far", C.c_int)]
 
 
 class urchin_solve_stats(C.Structure):
@@ -109,6 +109,10 @@ SIGNATURES = {
     "urchin_equilibrium_vjp": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int64, C.c_int, C.c_double, _vp, _vp, _vp]),
     "urchin_solve_vjp": (C.c_int, [_vp, C.POINTER(urchin_solve_params), _vp, _vp, _vp,
                                    C.POINTER(urchin_solve_stats), _vp]),
+    "urchin_trace_columns_nearfar": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_double, _vp, C.c_int64,
+                                               C.c_int, C.c_int, _vp, _vp, _vp]),
+    "urchin_gamma_nearfar": (C.c_int, [_vp, _vp, C.c_int, C.c_int64, C.c_int, C.POINTER(urchin_spectrum),
+                                       _vp, _vp, _vp, _vp, _vp, _vp]),
 }
 
 _lib = None
@@ -269,6 +273,37 @@ def urchin_trace_columns_noalloc(bvh: Bvh, x, dirs, l_ray: float, origins=None, 
     return out
 
 
+def urchin_trace_columns_nearfar(bvh: Bvh, x, dirs, l_ray: float, origins=None, kernel: int = KERNEL_M4,
+                                 precision: int = F32, stream=None):
+    """(tau_far, tau_near) [n_orig, R] with the near/far split of Sec. 3.3.3."""
+    import torch
+    dirs = _host(dirs).reshape(-1, 3)
+    R = dirs.shape[0]
+    n_orig = bvh.n if origins is None else int(origins.numel())
+    dt = torch.float64 if precision == F64 else torch.float32
+    tf = torch.empty((n_orig, R), dtype=dt, device=x.device)
+    tn = torch.empty((n_orig, R), dtype=dt, device=x.device)
+    _check(load().urchin_trace_columns_nearfar(bvh.handle, _dev(x, torch.float64), dirs.ctypes.data_as(_vp), R,
+                                               float(l_ray), _dev(origins, torch.int32), n_orig, int(kernel),
+                                               int(precision), _dev(tf, dt), _dev(tn, dt), _stream(stream)))
+    return tf, tn
+
+
+def urchin_gamma_nearfar(tau_far, tau_near, s, w, nH, T, caseB=None, stream=None):
+    """(Gamma float64, tau_eff float32) per origin with the slab solution for
+    the near particles; caseB: uint8 CUDA tensor or None (case A)."""
+    import torch
+    precision = F64 if tau_far.dtype == torch.float64 else F32
+    n_orig, R = tau_far.shape
+    sp = urchin_spectrum(int(s.numel()), _dev(s, torch.float64), _dev(w, torch.float64))
+    g = torch.empty(n_orig, dtype=torch.float64, device=tau_far.device)
+    te = torch.empty(n_orig, dtype=torch.float32, device=tau_far.device)
+    _check(load().urchin_gamma_nearfar(_dev(tau_far), _dev(tau_near, tau_far.dtype), int(precision), n_orig, R,
+                                       C.byref(sp), _dev(nH, torch.float64), _dev(T, torch.float64),
+                                       _dev(caseB, torch.uint8), _dev(g), _dev(te), _stream(stream)))
+    return g, te
+
+
 def urchin_gamma(tau, s, w, precision: int = None, stream=None):
     """Gamma (float64) and tau_eff (float32) per row of tau [n_orig, R]."""
     import torch
@@ -299,7 +334,7 @@ def urchin_solve(bvh: Bvh, dirs, l_ray: float, s, w, nH, T, x=None, *, y: float 
                  kernel: int = KERNEL_M4, precision: int = F32, case_rule: int = CASE_AUTO,
                  warm_start: bool = False, profile: bool = False, raise_not_converged: bool = True,
                  history: bool = False, blocks: int = 1, newton_switch: float = 0.01, newton_eta: float = 0.0,
-                 state=None, stream=None):
+                 state=None, near_far: bool = False, stream=None):
     """Returns (x, stats dict).  x (float64 CUDA tensor, original order) is
     updated in place when given.  `state` (uint8 CUDA tensor [n]) receives
     each particle's final case / frozen flags for urchin_solve_vjp."""
@@ -330,6 +365,7 @@ def urchin_solve(bvh: Bvh, dirs, l_ray: float, s, w, nH, T, x=None, *, y: float 
     P.newton_switch = float(newton_switch)
     P.newton_eta = float(newton_eta)
     P.state = _dev(state, torch.uint8)
+    P.near_far = int(bool(near_far))
     hist_max = hist_unc = None
     if history:
         hist_max = np.zeros(int(max_iter))

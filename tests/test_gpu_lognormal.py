@@ -1,5 +1,7 @@
-"""Parity on the periodic log-normal box (cosmological-like workload: 48
-HEALPix rays per particle with periodic wrapping, 200 bins, T ~ rho^0.6).
+"""Parity on the periodic log-normal boxes (cosmological-like workloads: 48
+HEALPix rays per particle with periodic wrapping, 200 bins, T ~ rho^0.6;
+and the large 256^3 box, sigma_ln 2.5, 12 rays, 400 bins, recomputed
+columns).
 Columns FP32 rel 1e-5 and FP64 rel 1e-11 against the oracle at sampled
 origins; the full 128^3 box is checked at a seeded sample of origins after
 the GPU traces all of its 1.0e8 rays, and one solver sweep is checked
@@ -105,3 +107,34 @@ def test_solve_full_box_converges(box128):
     fz = np.flatnonzero(frozen)[:50]
     x_thin = O.xeq(so[1].sum(), w.nH[fz], w.T[fz], 0.0, False)
     assert rel_err(xa[fz], x_thin).max() < 1e-12
+
+
+def test_large_box_columns_and_recomputed_sweep_sampled():
+    """The large log-normal box (256^3 = 1.68e7 particles, sigma_ln 2.5,
+    8 Mpc, 12 rays of 100 kpc, 400 bins): all 2.0e8 rays traced in one call
+    (FP32), 4 seeded origins compared with the oracle; then two sweeps in
+    recompute mode, the second checked at the same origins against the
+    oracle's update of the GPU's first-sweep state."""
+    w = W.lognormal_box(n_side=256, box_kpc=8000.0, sigma_ln=2.5, nside=1, F=400)
+    bvh, d = build(w, torch)
+    dirs = U.urchin_healpix_dirs(1)
+    x = _x(w.n, 7)
+    tau = U.urchin_trace_columns(bvh, torch.from_numpy(x).cuda(), dirs, w.l_ray, precision=U.F32)
+    org = W.random_origins(w.n, 4, 8)
+    ref = O.columns(w, x, O.healpix(1), origins=org)
+    assert rel_err(tau.double().cpu().numpy()[org], ref).max() < 1e-5
+    del tau
+    sg, so = spectra(w, torch)
+    state = torch.zeros(w.n, dtype=torch.uint8, device="cuda")
+    x1, st1 = U.urchin_solve(bvh, dirs, w.l_ray, sg[0], sg[1], d["nH"], d["T"], tol=1e-300, max_iter=1,
+                             segments=U.SEG_RECOMPUTE, precision=U.F32, raise_not_converged=False, state=state)
+    x2, st2 = U.urchin_solve(bvh, dirs, w.l_ray, sg[0], sg[1], d["nH"], d["T"], tol=1e-300, max_iter=2,
+                             segments=U.SEG_RECOMPUTE, precision=U.F32, raise_not_converged=False)
+    assert st2["segments_stored"] == 0
+    stt = state.cpu().numpy()
+    x1, x2 = x1.cpu().numpy(), x2.cpu().numpy()
+    act = np.flatnonzero((stt & 2) == 0)
+    org = np.sort(np.random.default_rng(9).choice(act, size=min(4, act.size), replace=False))
+    g1, te1 = O.gamma(O.columns(w, x1, O.healpix(1), origins=org), so[0], so[1])
+    e2 = O.xeq(g1, w.nH[org], w.T[org], 0.0, (te1 >= 1) | ((stt[org] & 1) > 0))
+    assert np.quantile(rel_err(e2, x2[org]), 0.5) < 1e-4
