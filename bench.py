@@ -43,7 +43,7 @@ WORKLOAD = "halo_262144_nside1_l200kpc_F100"
 #   k_spmv: bytes per stored segment read;  k_trace: bytes per ray-sphere hit
 MEASURED_TRAFFIC = {
     # 65536-particle halo: 2.584e9 DRAM bytes for 3.208e8 segments in one launch
-    "k_spmv": {"6305d580bab9b06c": 8.055},
+    "k_spmv": {"77b81bd81f3631b0": 8.055},
     "k_trace": {},
 }
 KERNEL_SOURCES = {"k_spmv": ("linalg.cu", "linalg.cuh"),
