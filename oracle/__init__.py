@@ -87,7 +87,8 @@ def _load():
                 "oracle_columns_nearfar": (None, [i64, vp, vp, vp, vp, vp, vp, i, d, d,
                                                   vp, i64, vp, i, d, i, vp, vp]),
                 "oracle_slab_lngamma": (d, [d, d, d, i, d]),
-                "oracle_gamma_nearfar": (None, [vp, vp, i64, i, i, vp, vp, vp, vp, vp, vp, vp]),
+                "oracle_gamma_nearfar": (None, [vp, vp, i64, i, i, vp, vp, vp, vp, vp, i, vp, vp]),
+                "oracle_slab_poly_lngamma": (d, [i, vp, vp, d, d, d, i, d]),
                 "oracle_xeq_dgamma": (d, [d, d, d, d, i]),
                 "oracle_column_matrix": (None, [i64, vp, vp, vp, vp, vp, i, d, d,
                                                 vp, i64, vp, i, d, i, vp]),
@@ -229,7 +230,7 @@ def xeq(Gamma, nH, T, y=0.0, caseB=False):
 
 # -- driver (Sec. 4) ---------------------------------------------------------
 def solve(w, s, wts, dirs, tol=1e-3, tau_skip=1e-4, max_iter=100, case_rule=CASE_AUTO,
-          kernel=KERNEL_M4, y=0.0, x_start=None, sweeps=None, l_ray=None, blocks=1, near_far=False):
+          kernel=KERNEL_M4, y=0.0, x_start=None, sweeps=None, l_ray=None, blocks=1, near_far=0):
     """Iteration of Sec. 4: Jacobi (blocks=1) or the high-to-low density
     update order in `blocks` blocks.  ``sweeps`` = exact sweep count
     (step-matched mode) instead of the tolerance test.  Returns (x, frozen,
@@ -250,7 +251,7 @@ def solve(w, s, wts, dirs, tol=1e-3, tau_skip=1e-4, max_iter=100, case_rule=CASE
                               _p(dirs), dirs.shape[0],
                               float(w.l_ray if l_ray is None else l_ray), kernel,
                               s.shape[0], _p(s), _p(wts), float(tol), float(tau_skip),
-                              mi, case_rule, int(blocks), int(bool(near_far)), _p(xs), _p(x), _p(frozen),
+                              mi, case_rule, int(blocks), int(near_far), _p(xs), _p(x), _p(frozen),
                               _p(caseB), _p(st))
     if rc == 2:
         raise ValueError("near_far needs blocks <= 1")
@@ -288,8 +289,21 @@ def slab_lngamma(Gamma0, nH, T, caseB, tau_near):
                      for g, a, t, c, u in zip(G, nH, T, cb, tn)])
 
 
-def gamma_nearfar(tau_far, tau_near, s, w, nH, T, caseB):
-    """(ln(Gamma/Gamma_thin), Gamma) per origin with the slab solution."""
+def slab_poly_lngamma(s, w, tau_far, nH, T, caseB, tau_near):
+    """ln Gamma at the bottom of the slab for the binned spectrum (s, w)
+    attenuated by tau_far (the numerical slab solution)."""
+    s, w = _f64(s), _f64(w)
+    lib = _load()
+    tf, nH, T, cb, tn = np.broadcast_arrays(np.atleast_1d(np.asarray(tau_far, dtype=np.float64)),
+                                            np.asarray(nH, dtype=np.float64), np.asarray(T, dtype=np.float64),
+                                            np.asarray(caseB, dtype=bool), np.asarray(tau_near, dtype=np.float64))
+    return np.array([lib.oracle_slab_poly_lngamma(s.shape[0], _p(s), _p(w), float(a), float(b), float(c), int(e),
+                                                  float(f)) for a, b, c, e, f in zip(tf, nH, T, cb, tn)])
+
+
+def gamma_nearfar(tau_far, tau_near, s, w, nH, T, caseB, poly=False):
+    """(ln(Gamma/Gamma_thin), Gamma) per origin with the slab solution
+    (analytic at the threshold, or polychromatic when poly)."""
     tf, tn = _f64(tau_far), _f64(tau_near)
     n_orig, R = tf.shape
     s, w = _f64(s), _f64(w)
@@ -299,7 +313,7 @@ def gamma_nearfar(tau_far, tau_near, s, w, nH, T, caseB):
     lr = np.zeros(n_orig)
     g = np.zeros(n_orig)
     _load().oracle_gamma_nearfar(_p(tf), _p(tn), n_orig, R, s.shape[0], _p(s), _p(w), _p(nH), _p(T),
-                                 _p(cb), _p(lr), _p(g))
+                                 _p(cb), int(bool(poly)), _p(lr), _p(g))
     return lr, g
 
 

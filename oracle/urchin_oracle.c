@@ -520,16 +520,83 @@ double oracle_slab_lngamma(double Gamma0, double nH, double T, int caseB, double
     return log(nH) + log(c + exp(le)) + log(ag) + le - lx;
 }
 
+/* ln sum_b w_b exp(-s_b tau), factored so that it does not underflow. */
+static double ln_spec_rate(int F, const double* s, const double* w, double tau)
+{
+    double smin = s[0];
+    for (int b = 1; b < F; ++b) smin = fmin(smin, s[b]);
+    double acc = 0.0;
+    for (int b = 0; b < F; ++b) acc += w[b] * exp(-(s[b] - smin) * tau);
+    return -smin * tau + log(acc);
+}
+
+/* The same slab for a polychromatic spectrum (the numerical slab solution
+ * the paper tabulates for Eq. gammashldk; y = 0): the slab of thickness
+ * tau_near = N_H sigma_th, density nH and temperature T is lit by the
+ * spectrum (s_b = sigma_b / sigma_th, w_b) already attenuated by the far
+ * column tau_far (at threshold).  With t = sigma_th nH z and tau_HI(t) the
+ * neutral column inside the slab (at threshold),
+ *   dtau_HI/dt = x(t),  x(t) = x_eq(Gamma(t)),
+ *   Gamma(t) = sum_b w_b exp(-s_b (tau_far + tau_HI(t))),
+ * integrated over t in [0, tau_near] with the Dormand-Prince 5(4) pair
+ * (adaptive steps, relative tolerance 1e-11).  Returns
+ * ln Gamma(tau_near) = ln sum_b w_b exp(-s_b (tau_far + tau_HI(tau_near))). */
+static double slab_rhs(int F, const double* s, const double* w, double tau_far, double nH, double T, int caseB,
+                       double u)
+{
+    double lg = ln_spec_rate(F, s, w, tau_far + u);
+    return oracle_xeq(exp(lg), nH, T, 0.0, caseB);
+}
+
+double oracle_slab_poly_lngamma(int F, const double* s, const double* w, double tau_far, double nH, double T,
+                                int caseB, double tau_near)
+{
+    static const double a21 = 1.0 / 5, a31 = 3.0 / 40, a32 = 9.0 / 40, a41 = 44.0 / 45, a42 = -56.0 / 15,
+                        a43 = 32.0 / 9, a51 = 19372.0 / 6561, a52 = -25360.0 / 2187, a53 = 64448.0 / 6561,
+                        a54 = -212.0 / 729, a61 = 9017.0 / 3168, a62 = -355.0 / 33, a63 = 46732.0 / 5247,
+                        a64 = 49.0 / 176, a65 = -5103.0 / 18656, b1 = 35.0 / 384, b3 = 500.0 / 1113,
+                        b4 = 125.0 / 192, b5 = -2187.0 / 6784, b6 = 11.0 / 84, e1 = 71.0 / 57600,
+                        e3 = -71.0 / 16695, e4 = 71.0 / 1920, e5 = -17253.0 / 339200, e6 = 22.0 / 525,
+                        e7 = -1.0 / 40;
+    double t = 0.0, u = 0.0;
+    double h = fmin(tau_near, 1e-3);
+    double k1 = slab_rhs(F, s, w, tau_far, nH, T, caseB, u);
+    int guard = 0;
+    while (t < tau_near && guard++ < 10000000) {
+        if (t + h > tau_near) h = tau_near - t;
+        double k2 = slab_rhs(F, s, w, tau_far, nH, T, caseB, u + h * a21 * k1);
+        double k3 = slab_rhs(F, s, w, tau_far, nH, T, caseB, u + h * (a31 * k1 + a32 * k2));
+        double k4 = slab_rhs(F, s, w, tau_far, nH, T, caseB, u + h * (a41 * k1 + a42 * k2 + a43 * k3));
+        double k5 = slab_rhs(F, s, w, tau_far, nH, T, caseB, u + h * (a51 * k1 + a52 * k2 + a53 * k3 + a54 * k4));
+        double k6 = slab_rhs(F, s, w, tau_far, nH, T, caseB,
+                             u + h * (a61 * k1 + a62 * k2 + a63 * k3 + a64 * k4 + a65 * k5));
+        double un = u + h * (b1 * k1 + b3 * k3 + b4 * k4 + b5 * k5 + b6 * k6);
+        double k7 = slab_rhs(F, s, w, tau_far, nH, T, caseB, un);
+        double err = h * fabs(e1 * k1 + e3 * k3 + e4 * k4 + e5 * k5 + e6 * k6 + e7 * k7);
+        double tol = 1e-11 * fmax(fabs(un), 1e-3 * h) + 1e-300;
+        if (err <= tol) {
+            t += h;
+            u = un;
+            k1 = k7;
+        }
+        double fac = err > 0.0 ? 0.9 * pow(tol / err, 0.2) : 5.0;
+        h *= fmin(5.0, fmax(0.2, fac));
+    }
+    return ln_spec_rate(F, s, w, tau_far + u);
+}
+
 /* Shielded rate with the near/far split (Sec. 3.3.3, Eqs. gammafar,
  * gammashldk, gammashld): per ray Gamma_far = sum_j w_j exp(-s_j tau_far),
  * Gamma_shld,k = G(Gamma_far, nH, T, tau_near) with G the slab solution
  * above, Gamma = (1/R) sum_k Gamma_shld,k (the 4 pi / N_ray absorbed in w).
- * caseB[o] is the recombination case used inside the slab.  Writes
+ * caseB[o] is the recombination case used inside the slab; poly = 0 takes
+ * the analytic slab (radiation at the threshold with the far rate), poly = 1
+ * the polychromatic slab (oracle_slab_poly_lngamma).  Writes
  * ln(Gamma / Gamma_thin) per origin (log-sum-exp over rays, finite where
  * Gamma underflows) and Gamma. */
 void oracle_gamma_nearfar(const double* tau_far, const double* tau_near, int64_t n_orig, int R, int F,
                           const double* s, const double* w, const double* nH, const double* T,
-                          const int* caseB, double* lnratio_out, double* gamma_out)
+                          const int* caseB, int poly, double* lnratio_out, double* gamma_out)
 {
     double gthin = 0.0;
     for (int j = 0; j < F; ++j) gthin += w[j];
@@ -538,9 +605,14 @@ void oracle_gamma_nearfar(const double* tau_far, const double* tau_near, int64_t
         double lk[512];
         double m = -INFINITY;
         for (int k = 0; k < R; ++k) {
-            double gf = 0.0;
-            for (int j = 0; j < F; ++j) gf += w[j] * exp(-s[j] * tau_far[o * R + k]);
-            lk[k] = oracle_slab_lngamma(gf, nH[o], T[o], caseB[o], tau_near[o * R + k]) - log(gthin);
+            if (poly) {
+                lk[k] = oracle_slab_poly_lngamma(F, s, w, tau_far[o * R + k], nH[o], T[o], caseB[o],
+                                                 tau_near[o * R + k]) - log(gthin);
+            } else {
+                double gf = 0.0;
+                for (int j = 0; j < F; ++j) gf += w[j] * exp(-s[j] * tau_far[o * R + k]);
+                lk[k] = oracle_slab_lngamma(gf, nH[o], T[o], caseB[o], tau_near[o * R + k]) - log(gthin);
+            }
             if (lk[k] > m) m = lk[k];
         }
         double acc = 0.0;
@@ -586,8 +658,9 @@ static int use_caseB(int case_rule, double tau_eff)
  * contiguous blocks of sizes floor((b+1) m / blocks) - floor(b m / blocks),
  * and each sweep updates block after block, every block's columns using the
  * x of the blocks already updated in that sweep.
- * near_far = 1 replaces the columns and Gamma by the near/far split of
- * Sec. 3.3.3 (oracle_columns_nearfar, oracle_gamma_nearfar): the slab of
+ * near_far = 1 (analytic slab) or 2 (polychromatic slab) replaces the
+ * columns and Gamma by the near/far split of Sec. 3.3.3
+ * (oracle_columns_nearfar, oracle_gamma_nearfar): the slab of
  * near particles uses each particle's case before the sweep (its latch, or
  * the forced case), then tau_eff = -ln(Gamma/Gamma_thin) decides the case
  * of the update as above.  It needs blocks <= 1 (returns 2 otherwise).
@@ -649,7 +722,7 @@ int oracle_solve(int64_t n, const double* px, const double* py, const double* pz
                     T_o[o] = T[i];
                     cb_o[o] = use_caseB(case_rule, 0.0) || (case_rule == 2 && latchB[i]);
                 }
-                oracle_gamma_nearfar(tau, tau_nr, nact, R, F, s, w, nH_o, T_o, cb_o, te, G);
+                oracle_gamma_nearfar(tau, tau_nr, nact, R, F, s, w, nH_o, T_o, cb_o, near_far == 2, te, G);
                 for (int64_t o = 0; o < nact; ++o) te[o] = -te[o];
             } else {
                 oracle_columns(n, px, py, pz, h, mass_H, x, periodic, L, unit_cm,

@@ -109,3 +109,49 @@ def test_near_far_iteration_converges_faster_than_the_plain_scheme():
     xn, fn, sn = O.solve(w, s, wts, dirs, tol=1e-8, max_iter=3000, near_far=True)
     assert sp["converged"] and sn["converged"]
     assert sn["sweeps"] < sp["sweeps"]
+
+
+# -- the polychromatic slab (numerical slab solution) --------------------------
+@pytest.mark.parametrize("caseB", [False, True])
+@pytest.mark.parametrize("tau_far", [0.0, 2.0])
+@pytest.mark.parametrize("tau_near", [0.05, 5.0, 60.0])
+def test_poly_slab_reduces_to_the_analytic_slab_for_one_bin(caseB, tau_far, tau_near):
+    """A single bin at the threshold (s = 1) is monochromatic radiation: the
+    numerical slab integration must give the appendix's analytic solution."""
+    nH, T = 3e-3, 1.2e4
+    aA, aB, gc = O.rates(T)
+    w = np.array([20.0 * (aB if caseB else aA) * nH])
+    s = np.array([1.0])
+    got = O.slab_poly_lngamma(s, w, tau_far, nH, T, caseB, tau_near)[0]
+    ref = O.slab_lngamma(w[0] * np.exp(-tau_far), nH, T, caseB, tau_near)[0]
+    assert abs(got - ref) <= 1e-8 * max(1.0, abs(ref))
+
+
+def test_poly_slab_limits_and_hardening():
+    w_ = W.halo(n=10, seed=1, F=50)
+    e, J = w_.spectrum()
+    s, wts = O.spectrum(e, J, w_.gamma_thin)
+    nH, T = 1e-2, 1e4
+    for tf in (0.0, 3.0):
+        lgf = np.log((wts * np.exp(-s * tf)).sum())
+        assert abs(O.slab_poly_lngamma(s, wts, tf, nH, T, False, 0.0)[0] - lgf) < 1e-14 * max(1, abs(lgf))
+        # every bin at or above the threshold has s <= 1: the slab is at least
+        # as transparent as one lit at the threshold with the same rate
+        for tn in (0.1, 3.0, 30.0, 300.0):
+            poly = O.slab_poly_lngamma(s, wts, tf, nH, T, False, tn)[0]
+            mono = O.slab_lngamma(np.exp(lgf), nH, T, False, tn)[0]
+            assert poly >= mono - 1e-10
+        vals = O.slab_poly_lngamma(s, wts, tf, nH, T, False, np.array([0.01, 0.1, 1.0, 10.0, 100.0]))
+        assert np.all(np.diff(vals) < 0)
+
+
+def test_poly_near_far_iteration_converges():
+    w = W.halo(n=400, seed=7, n0=0.3, F=20)
+    e, J = w.spectrum()
+    s, wts = O.spectrum(e, J, w.gamma_thin)
+    dirs = O.healpix(1)
+    x1, f1, s1 = O.solve(w, s, wts, dirs, tol=1e-8, max_iter=300, near_far=1)
+    x2, f2, s2 = O.solve(w, s, wts, dirs, tol=1e-8, max_iter=300, near_far=2)
+    assert s1["converged"] and s2["converged"]
+    # the hardened spectrum penetrates the near slab further: less neutral gas
+    assert np.median(x2 / x1) <= 1.0 + 1e-12
