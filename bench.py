@@ -417,22 +417,25 @@ def main():
         t = comp["to_rel_1e-3_of_xstar"]
         t["newton_speedup"] = (t["plain_wall_s"] / t["newton_wall_s"]) if (t["plain_wall_s"] and t["newton_wall_s"]) else None
         # the near/far split of the paper (a different model of the near
-        # particles, so its x is not compared with the plain scheme's x*)
-        bvh = U.urchin_build_bvh(d["px"], d["py"], d["pz"], d["h"], d["m"], w.periodic, w.box, w.unit_cm)
-        torch.cuda.synchronize(dev)
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        xnf, snf = U.urchin_solve(bvh, dirs, w.l_ray, s_d, w_d, d["nH"], d["T"], tol=1e-3, tau_skip=1e-4,
-                                  max_iter=args.max_iter, segments=segs, precision=U.F32, near_far=True,
-                                  raise_not_converged=False)
-        b.record(stream)
-        b.synchronize()
-        bvh.close()
-        xnf = xnf.cpu().numpy()
-        comp["near_far"] = {"wall_s_incl_build": a.elapsed_time(b) * 1e-3, "dx_tol": 1e-3,
-                            "iterations": snf["iterations"], "converged": bool(snf["converged"]),
-                            "rays": snf["rays"], "median_x_over_plain_xstar": float(np.median(xnf / xr))}
+        # particles, so its x is not compared with the plain scheme's x*),
+        # with the analytic (threshold) and the numerical (spectrum) slab
+        for name, slab in (("near_far_threshold", U.SLAB_THRESHOLD), ("near_far_spectrum", U.SLAB_SPECTRUM)):
+            bvh = U.urchin_build_bvh(d["px"], d["py"], d["pz"], d["h"], d["m"], w.periodic, w.box, w.unit_cm)
+            torch.cuda.synchronize(dev)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            xnf, snf = U.urchin_solve(bvh, dirs, w.l_ray, s_d, w_d, d["nH"], d["T"], tol=1e-3, tau_skip=1e-4,
+                                      max_iter=args.max_iter, segments=segs, precision=U.F32, near_far=slab,
+                                      raise_not_converged=False, profile=True)
+            b.record(stream)
+            b.synchronize()
+            bvh.close()
+            xnf = xnf.cpu().numpy()
+            comp[name] = {"wall_s": a.elapsed_time(b) * 1e-3, "dx_tol": 1e-3, "iterations": snf["iterations"],
+                          "converged": bool(snf["converged"]), "rays": snf["rays"],
+                          "trace_s": snf["trace_s"], "spmv_s": snf["spmv_s"], "sweep_s": snf["sweep_s"],
+                          "median_x_over_plain_xstar": float(np.median(xnf / xr))}
         # reverse mode at the converged state: gradient of L = sum_i ln x*_i
         # with respect to the spectrum weights (adjoint GMRES, one transposed
         # column pass per product)

@@ -69,6 +69,10 @@ typedef struct CUstream_st* urchin_stream_t;
 #define URCHIN_METHOD_PLAIN     0     /* Jacobi fixed point (Sec. 4)            */
 #define URCHIN_METHOD_NEWTON    1     /* Newton-Krylov on the same fixed point  */
 #define URCHIN_METHOD_ANDERSON  2     /* Anderson-accelerated sweeps            */
+
+/* Slab model for the near particles of the near/far split (Sec. 3.3.3) */
+#define URCHIN_SLAB_THRESHOLD   1     /* analytic slab, radiation at threshold   */
+#define URCHIN_SLAB_SPECTRUM    2     /* numerical slab, the binned spectrum     */
 #define URCHIN_SEG_RECOMPUTE    0     /* trace the BVH every sweep              */
 #define URCHIN_SEG_STORE        1     /* store per-ray segment lists once       */
 #define URCHIN_SEG_AUTO         2     /* store when the lists fit in memory     */
@@ -219,14 +223,20 @@ URCHIN_API int urchin_trace_columns_nearfar(const urchin_bvh* bvh, const double*
  * gammashld): per ray the far rate Gamma_far,k = sum_j w_j exp(-s_j tau_far,k)
  * lights a uniform hydrogen slab of thickness tau_near,k with the origin's
  * nH and T (device [n_orig] double) and recombination case (caseB device
- * [n_orig], nonzero = case B; NULL = case A); the slab solution of the
- * appendix (monochromatic at the threshold, y = 0) gives the rate at its far
- * side, and gamma_out[o] = (1/R) sum_k of those.  tau_eff_out as in
- * urchin_gamma (may be NULL).  tau_far / tau_near as written by
- * urchin_trace_columns_nearfar.  Errors: ERR_ARG, ERR_CUDA. */
+ * [n_orig], nonzero = case B; NULL = case A); the slab solution (y = 0)
+ * gives the rate at its far side, and gamma_out[o] = (1/R) sum_k of those.
+ *   slab = URCHIN_SLAB_THRESHOLD: the appendix's analytic solution for
+ *          radiation at the threshold, lit with the far rate;
+ *   slab = URCHIN_SLAB_SPECTRUM: the numerical slab solution for the binned
+ *          spectrum hardened by tau_far (dtau_HI/dt = x_eq(Gamma(tau_far +
+ *          tau_HI)) over the slab, t = N_H sigma_th depth), the paper's
+ *          polychromatic G computed per ray instead of tabulated.
+ * tau_eff_out as in urchin_gamma (may be NULL).  tau_far / tau_near as
+ * written by urchin_trace_columns_nearfar.  Errors: ERR_ARG, ERR_NOMEM,
+ * ERR_CUDA. */
 URCHIN_API int urchin_gamma_nearfar(const void* tau_far, const void* tau_near, int precision, int64_t n_orig,
                                     int R, const urchin_spectrum* sp, const double* nH, const double* T,
-                                    const unsigned char* caseB, double* gamma_out, float* tau_eff_out,
+                                    const unsigned char* caseB, int slab, double* gamma_out, float* tau_eff_out,
                                     urchin_stream_t stream);
 
 /* Shielded rate, Eq. gamma_shld: for each of n_orig particles with R columns
@@ -296,16 +306,17 @@ typedef struct {
                                      reads each particle's final state,
                                      bit 0 = recombination case B,
                                      bit 1 = frozen after sweep 0             */
-    int             near_far;     /* 1: the near/far split of Sec. 3.3.3 (plain
-                                     method, blocks <= 1, y = 0): far
-                                     particles give tau_far, the origin's
-                                     near particles (those whose smoothing
-                                     sphere holds it) a slab of thickness
-                                     tau_near (x = 1); each ray's rate is the
-                                     slab solution at the far-attenuated
-                                     surface rate (monochromatic slab at the
-                                     threshold, the slab appendix), in the
-                                     particle's case before the sweep        */
+    int             near_far;     /* 0: off; URCHIN_SLAB_THRESHOLD or
+                                     URCHIN_SLAB_SPECTRUM: the near/far split
+                                     of Sec. 3.3.3 (plain method, blocks <= 1,
+                                     y = 0): far particles give tau_far, the
+                                     origin's near particles (those whose
+                                     smoothing sphere holds it) a slab of
+                                     thickness tau_near (x = 1); each ray's
+                                     rate is that slab's solution (see
+                                     urchin_gamma_nearfar) lit by the far-
+                                     attenuated radiation, in the particle's
+                                     case before the sweep                    */
 } urchin_solve_params;
 
 typedef struct {

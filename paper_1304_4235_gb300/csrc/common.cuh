@@ -208,6 +208,13 @@ int ray_order(const urchin_bvh* bvh, const int32_t* items, int64_t n_items, cons
 int launch_wbar(const void* tau, int precision, int64_t n_rays, const double* lc, const double* sg, const double* s,
                 int F, double* w_bar, cudaStream_t st);
 
+// Table of ln sum_b w_b exp(-s_b tau) on u = ln(1 + tau) for the
+// polychromatic slab (spectral_device.cuh, SpecTable): kSpecTab intervals
+// up to tau = kSpecTauMax; tab needs kSpecTab + 1 double2 (value, d/du).
+constexpr int kSpecTab = 4096;
+constexpr double kSpecTauMax = 1e7;
+int build_spec_table(const double* s, const double* w, int F, double2* tab, double* smin_out, cudaStream_t st);
+
 // w = A * x gathered into Morton order: w[s] = A[s] * x[perm[s]]
 int launch_weights(const urchin_bvh* bvh, const double* x_orig, float* w32, double* w64,
                    cudaStream_t s);

@@ -140,7 +140,8 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs A)
             const Real tau = static_cast<const Real*>(A.tau)[row + (int64_t)k * A.k_stride];
             Real S = Real(0), c = Real(0), S2 = Real(0), c2 = Real(0);
             // (near/far: tau is the far column; the slab of near particles is applied below)
-            for (int j = 0; j < A.F; ++j) {
+            const int nspec = A.near_far == URCHIN_SLAB_SPECTRUM ? 0 : A.F;
+            for (int j = 0; j < nspec; ++j) {
                 const Real v = wn[j] * exp2_p(-e2[j] * tau);
                 const Real yy = v - c;
                 const Real t = S + yy;
@@ -155,14 +156,18 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs A)
                 }
             }
             // ln(Gamma_k / Gamma_thin) = -s_min tau_k + ln S_k
-            Real lkv = -smin * tau + log_p(S);
+            Real lkv = nspec ? -smin * tau + log_p(S) : Real(0);
             if (A.near_far) {
-                // Eq. gammashldk: the far rate enters the slab of near particles, in the
-                // particle's recombination case before this sweep
+                // Eq. gammashldk: the far radiation enters the slab of near particles, in
+                // the particle's recombination case before this sweep
                 const int32_t ir = A.items ? A.items[row] : (int32_t)row;
                 const bool cB = A.case_rule == URCHIN_CASE_B || (A.case_rule == URCHIN_CASE_AUTO && A.latch[ir]);
                 const double tn = (double)static_cast<const Real*>(A.tau_near)[ir + (int64_t)k * A.near_k_stride];
-                lkv = (Real)slab_lnratio((double)lkv, gthin, tn, A.nH[ir], cB ? A.aB[ir] : A.aA[ir], A.gc[ir]);
+                const double al = cB ? A.aB[ir] : A.aA[ir];
+                if (A.near_far == URCHIN_SLAB_SPECTRUM)
+                    lkv = (Real)slab_poly_lnratio(A.poly, gthin, (double)tau, tn, A.nH[ir], al, A.gc[ir]);
+                else
+                    lkv = (Real)slab_lnratio((double)lkv, gthin, tn, A.nH[ir], al, A.gc[ir]);
             }
             lk[local * A.R + k] = lkv;
             if (A.want_tangent) lk2[local * A.R + k] = -smin * tau + log_p(S2 > Real(1e-37) ? S2 : Real(1e-37));
@@ -599,6 +604,7 @@ int Solver::init(const urchin_bvh* bvh_, const urchin_solve_params* P_, double* 
     size_t o_list = lay.take(sizeof(int32_t) * (size_t)n);
     size_t o_tau = lay.take(rsz * (size_t)rays);
     size_t o_tn = lay.take(P.near_far ? rsz * (size_t)rays : 0);
+    size_t o_pt = lay.take(P.near_far == URCHIN_SLAB_SPECTRUM ? sizeof(double2) * (kSpecTab + 1) + 64 : 0);
     size_t o_comp = lay.take(compact_tmp_bytes(n));
     size_t o_cnt = lay.take(may_store ? sizeof(uint32_t) * (size_t)rays : 0);
     size_t o_rp = lay.take(may_store ? sizeof(uint64_t) * (size_t)(rays + 1) : 0);
@@ -625,6 +631,15 @@ int Solver::init(const urchin_bvh* bvh_, const urchin_solve_params* P_, double* 
     list = scr.at<int32_t>(o_list);
     tau = scr.at<void>(o_tau);
     tau_near = P.near_far ? scr.at<void>(o_tn) : nullptr;
+    if (P.near_far == URCHIN_SLAB_SPECTRUM) {
+        double2* tab = scr.at<double2>(o_pt);
+        double* smin = reinterpret_cast<double*>(tab + kSpecTab + 1);
+        URCHIN_TRY(build_spec_table(P.spectrum.s, P.spectrum.w, P.spectrum.F, tab, smin, s));
+        double hs = 0.0;
+        URCHIN_TRY_CUDA(cudaMemcpyAsync(&hs, smin, sizeof(double), cudaMemcpyDeviceToHost, s));
+        URCHIN_TRY_CUDA(cudaStreamSynchronize(s));
+        poly = SpecTable{tab, kSpecTab, log1p(kSpecTauMax), hs};
+    }
     comp_tmp = scr.at<void>(o_comp);
     counter = reinterpret_cast<unsigned*>(misc + 1);
     status = counter + 1;
@@ -949,6 +964,7 @@ SweepArgs Solver::sweep_args(const int32_t* items, int64_t n_items, int sweep0)
     A.near_far = P.near_far;
     A.tau_near = tau_near;
     A.near_k_stride = n;
+    A.poly = poly;
     return A;
 }
 
@@ -1752,7 +1768,8 @@ extern "C" int urchin_solve(const urchin_bvh* bvh, const urchin_solve_params* P,
     URCHIN_TRY(check_solve_params("urchin_solve", bvh, P, x_inout));
     if (P->method != URCHIN_METHOD_PLAIN && (P->gmres_m < 1 || P->gmres_m > 64))
         return set_error(URCHIN_ERR_ARG, "urchin_solve: gmres_m must be in [1, 64]");
-    if (P->near_far != 0 && P->near_far != 1) return set_error(URCHIN_ERR_ARG, "urchin_solve: near_far must be 0 or 1");
+    if (P->near_far != 0 && P->near_far != URCHIN_SLAB_THRESHOLD && P->near_far != URCHIN_SLAB_SPECTRUM)
+        return set_error(URCHIN_ERR_ARG, "urchin_solve: near_far must be 0, URCHIN_SLAB_THRESHOLD or URCHIN_SLAB_SPECTRUM");
     if (P->near_far && (P->method != URCHIN_METHOD_PLAIN || P->blocks > 1 || P->y != 0.0))
         return set_error(URCHIN_ERR_ARG, "urchin_solve: the near/far split needs the plain Jacobi method and y = 0");
     cudaStream_t s = (cudaStream_t)stream;

@@ -5,6 +5,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "spectral_device.cuh"
 
 namespace urchin {
 
@@ -46,6 +47,7 @@ struct SweepArgs {
     int near_far;              // Sec. 3.3.3 split: tau holds the far columns; the near
     const void* tau_near;      //   columns (x = 1) are at tau_near[i + k * near_k_stride]
     int64_t near_k_stride;     //   (i the Morton slot) and enter through the slab solution
+    SpecTable poly;            // near_far == URCHIN_SLAB_SPECTRUM: ln Gamma_spec(tau) table
     int want_tangent;          // Newton: keep x, emit E and tangent factors
     double* ctan;              // [n_items * R] (k-major, stride k_stride)
     double* xeq_out;           // [n_items]
@@ -80,6 +82,7 @@ struct Solver {
     int32_t* list = nullptr;
     void* tau = nullptr;
     void* tau_near = nullptr;                    // near/far: [R * n] near columns, Morton slot + k n
+    SpecTable poly{nullptr, 0, 0.0, 0.0};        // near/far with the polychromatic slab
     void* comp_tmp = nullptr;
     unsigned long long* hits = nullptr;          // misc[3..5], counted when P.profile
     std::vector<cudaEvent_t> events;             // start/stop pairs of each timed launch

@@ -264,7 +264,8 @@ template <typename Real>
 __global__ void k_gamma_nearfar(const Real* __restrict__ tf, const Real* __restrict__ tn, int64_t n_orig, int R,
                                 const double* __restrict__ sv, const double* __restrict__ wv, int F,
                                 const double* __restrict__ nH, const double* __restrict__ T,
-                                const uint8_t* __restrict__ caseB, double* gamma_out, float* tau_eff_out)
+                                const uint8_t* __restrict__ caseB, SpecTable poly, double* gamma_out,
+                                float* tau_eff_out)
 {
     extern __shared__ double sm[];
     double* ss = sm;
@@ -292,9 +293,14 @@ __global__ void k_gamma_nearfar(const Real* __restrict__ tf, const Real* __restr
         double m = -INFINITY, acc = 0.0;
         for (int k = 0; k < R; ++k) {
             const double t = (double)tf[o * R + k];
-            double S = 0.0;
-            for (int b = 0; b < F; ++b) S += ws[b] * exp(-ss[b] * t);
-            const double l = slab_lnratio(-smin * t + log(S), gthin, (double)tn[o * R + k], nH[o], alpha, r.gamma_c);
+            double l;
+            if (poly.tab) {
+                l = slab_poly_lnratio(poly, gthin, t, (double)tn[o * R + k], nH[o], alpha, r.gamma_c);
+            } else {
+                double S = 0.0;
+                for (int b = 0; b < F; ++b) S += ws[b] * exp(-ss[b] * t);
+                l = slab_lnratio(-smin * t + log(S), gthin, (double)tn[o * R + k], nH[o], alpha, r.gamma_c);
+            }
             if (!(l > -INFINITY)) continue;
             if (l > m) {
                 acc = acc * exp(m - l) + 1.0;
@@ -306,6 +312,28 @@ __global__ void k_gamma_nearfar(const Real* __restrict__ tf, const Real* __restr
         const double lr = m + log(acc / (double)R);
         gamma_out[o] = gthin * exp(lr);
         if (tau_eff_out) tau_eff_out[o] = (float)(-lr);
+    }
+}
+
+// tab[i] = (ln sum_b w_b e^{-s_b tau_i}, d/du), tau_i = e^{u_i} - 1, u_i = i umax / nt,
+// in double with the factored sum; smin_out[0] = min_b s_b
+__global__ void k_spec_table(const double* __restrict__ sv, const double* __restrict__ wv, int F, int nt,
+                             double umax, double2* tab, double* smin_out)
+{
+    double smin = sv[0];
+    for (int b = 1; b < F; ++b) smin = fmin(smin, sv[b]);
+    if (blockIdx.x == 0 && threadIdx.x == 0) smin_out[0] = smin;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= nt; i += gridDim.x * blockDim.x) {
+        const double u = umax * (double)i / (double)nt;
+        const double tau = expm1(u);
+        double S = 0.0, S1 = 0.0;
+        for (int b = 0; b < F; ++b) {
+            const double e = wv[b] * exp(-(sv[b] - smin) * tau);
+            S += e;
+            S1 += sv[b] * e;
+        }
+        // d/du = (d/dtau)(1 + tau), d ln Gamma / d tau = -S1 / S
+        tab[i] = make_double2(-smin * tau + log(S), -(S1 / S) * (1.0 + tau));
     }
 }
 
@@ -341,6 +369,12 @@ int gamma_vjp_t(const Real* tau, int64_t n_orig, int R, const urchin_spectrum* s
 }
 
 }  // namespace
+
+int build_spec_table(const double* s, const double* w, int F, double2* tab, double* smin_out, cudaStream_t st)
+{
+    k_spec_table<<<(kSpecTab + 256) / 256, 256, 0, st>>>(s, w, F, kSpecTab, log1p(kSpecTauMax), tab, smin_out);
+    return launched();
+}
 
 int launch_wbar(const void* tau, int precision, int64_t n_rays, const double* lc, const double* sg, const double* sv,
                 int F, double* w_bar, cudaStream_t s)
@@ -477,7 +511,7 @@ extern "C" int urchin_equilibrium_vjp(const double* gamma, const float* tau_eff,
 
 extern "C" int urchin_gamma_nearfar(const void* tau_far, const void* tau_near, int precision, int64_t n_orig, int R,
                                     const urchin_spectrum* sp, const double* nH, const double* T,
-                                    const unsigned char* caseB, double* gamma_out, float* tau_eff_out,
+                                    const unsigned char* caseB, int slab, double* gamma_out, float* tau_eff_out,
                                     urchin_stream_t stream)
 {
     using namespace urchin;
@@ -490,9 +524,24 @@ extern "C" int urchin_gamma_nearfar(const void* tau_far, const void* tau_near, i
     if (sp->F < 1 || sp->F > URCHIN_MAX_BINS)
         return set_error(URCHIN_ERR_ARG, "urchin_gamma_nearfar: F = %d out of range [1, %d]", sp->F, URCHIN_MAX_BINS);
     if (n_orig == 0) return URCHIN_OK;
+    if (slab != URCHIN_SLAB_THRESHOLD && slab != URCHIN_SLAB_SPECTRUM)
+        return set_error(URCHIN_ERR_ARG, "urchin_gamma_nearfar: unknown slab model %d", slab);
     if (!tau_far || !tau_near || !nH || !T || !gamma_out)
         return set_error(URCHIN_ERR_ARG, "urchin_gamma_nearfar: NULL tau_far, tau_near, nH, T or gamma_out");
     cudaStream_t s = (cudaStream_t)stream;
+    Scratch tb;
+    SpecTable poly{nullptr, kSpecTab, log1p(kSpecTauMax), 0.0};
+    if (slab == URCHIN_SLAB_SPECTRUM) {
+        URCHIN_TRY(tb.alloc(sizeof(double2) * (kSpecTab + 1) + 256, s));
+        double2* tab = tb.at<double2>(0);
+        double* smin = reinterpret_cast<double*>(tab + kSpecTab + 1);
+        URCHIN_TRY(build_spec_table(sp->s, sp->w, sp->F, tab, smin, s));
+        double hs = 0.0;
+        URCHIN_TRY_CUDA(cudaMemcpyAsync(&hs, smin, sizeof(double), cudaMemcpyDeviceToHost, s));
+        URCHIN_TRY_CUDA(cudaStreamSynchronize(s));
+        poly.tab = tab;
+        poly.smin = hs;
+    }
     const size_t smem = sizeof(double) * 2 * (size_t)sp->F;
     const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n_orig + 127) / 128, 4096));
     if (precision == URCHIN_F64) {
@@ -501,14 +550,16 @@ extern "C" int urchin_gamma_nearfar(const void* tau_far, const void* tau_near, i
                                                  (int)smem));
         k_gamma_nearfar<double><<<grid, 128, smem, s>>>(static_cast<const double*>(tau_far),
                                                         static_cast<const double*>(tau_near), n_orig, R, sp->s,
-                                                        sp->w, sp->F, nH, T, caseB, gamma_out, tau_eff_out);
+                                                        sp->w, sp->F, nH, T, caseB, poly, gamma_out, tau_eff_out);
     } else {
         if (smem > 48 * 1024)
             URCHIN_TRY_CUDA(cudaFuncSetAttribute(k_gamma_nearfar<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)smem));
         k_gamma_nearfar<float><<<grid, 128, smem, s>>>(static_cast<const float*>(tau_far),
                                                        static_cast<const float*>(tau_near), n_orig, R, sp->s,
-                                                       sp->w, sp->F, nH, T, caseB, gamma_out, tau_eff_out);
+                                                       sp->w, sp->F, nH, T, caseB, poly, gamma_out, tau_eff_out);
     }
-    return launched();
+    URCHIN_TRY(launched());
+    tb.release();
+    return URCHIN_OK;
 }

@@ -132,4 +132,109 @@ __device__ __forceinline__ double slab_lnratio(double lnr_far, double gthin, dou
     return log(nH) + log(c + exp(le)) + log(ag) + le - lx - log(gthin);
 }
 
+// ---- polychromatic slab ---------------------------------------------------
+// ln Gamma_spec(tau) = ln sum_b w_b exp(-s_b tau) tabulated on u = ln(1 + tau)
+// in [0, umax] (nt intervals): tab[i] = (value, d value / du), evaluated by
+// cubic Hermite interpolation; past umax the tail is linear in tau with
+// slope -s_min (the hardest bin dominates).
+struct SpecTable {
+    const double2* tab;
+    int nt;
+    double umax;
+    double smin;
+};
+
+__device__ __forceinline__ double spec_lnrate(const SpecTable& S, double tau)
+{
+    const double u = log1p(tau);
+    if (u >= S.umax) {
+        const double tm = expm1(S.umax);
+        return S.tab[S.nt].x - S.smin * (tau - tm);
+    }
+    const double pos = u / S.umax * (double)S.nt;
+    int i = (int)pos;
+    i = i < 0 ? 0 : (i >= S.nt ? S.nt - 1 : i);
+    const double h = S.umax / (double)S.nt;
+    const double f = pos - (double)i;
+    const double2 a = S.tab[i], b = S.tab[i + 1];
+    const double f2 = f * f, f3 = f2 * f;
+    return (2.0 * f3 - 3.0 * f2 + 1.0) * a.x + (f3 - 2.0 * f2 + f) * h * a.y + (3.0 * f2 - 2.0 * f3) * b.x +
+           (f3 - f2) * h * b.y;
+}
+
+// d ln Gamma_spec / d tau = -(mean s weighted by the attenuated spectrum)
+__device__ __forceinline__ double spec_slope(const SpecTable& S, double tau)
+{
+    const double u = log1p(tau);
+    if (u >= S.umax) return -S.smin;
+    const double pos = u / S.umax * (double)S.nt;
+    int i = (int)pos;
+    i = i < 0 ? 0 : (i >= S.nt ? S.nt - 1 : i);
+    const double f = pos - (double)i;
+    return ((1.0 - f) * S.tab[i].y + f * S.tab[i + 1].y) / (1.0 + tau);
+}
+
+// The slab of near particles lit by the polychromatic spectrum after the far
+// column tau_far (the numerical slab solution for Eq. gammashldk, y = 0):
+// with t = sigma_th nH z, dtau_HI/dt = x_eq(Gamma_spec(tau_far + tau_HI)),
+// equivalently t(tau_HI) = int_0^tau_HI dv / x(v).  The integral is summed
+// over panels in v whose width keeps the change of ln Gamma below 1/2
+// (|d ln x / d ln Gamma| <= 1, so x changes by at most e^(1/2) per panel),
+// each by 4-point Gauss-Legendre; the panel where t reaches tau_near is
+// solved by Newton's method on its own quadrature.  Once x is within 1e-10
+// of x_ce the rest of the slab is uniform (1/x = 1/x_ce).  Returns
+// ln(Gamma_bottom / Gamma_thin).
+__device__ __forceinline__ double slab_x(const SpecTable& S, double tau, double nH, double alpha, double gc)
+{
+    return x_equilibrium(exp(spec_lnrate(S, tau)), nH, alpha, gc, 0.0);
+}
+
+__device__ __forceinline__ double slab_panel(const SpecTable& S, double tf, double a, double b, double nH,
+                                             double alpha, double gc)
+{
+    // 4-point Gauss-Legendre of 1/x over [a, b]
+    const double g1 = 0.3399810435848563, g2 = 0.8611363115940526;
+    const double w1 = 0.6521451548625461, w2 = 0.3478548451374538;
+    const double m = 0.5 * (a + b), r = 0.5 * (b - a);
+    return r * (w1 / slab_x(S, tf + m - r * g1, nH, alpha, gc) + w1 / slab_x(S, tf + m + r * g1, nH, alpha, gc) +
+                w2 / slab_x(S, tf + m - r * g2, nH, alpha, gc) + w2 / slab_x(S, tf + m + r * g2, nH, alpha, gc));
+}
+
+__device__ __forceinline__ double slab_poly_lnratio(const SpecTable& S, double gthin, double tau_far,
+                                                    double tau_near, double nH, double alpha, double gc)
+{
+    if (!(tau_near > 0.0)) return spec_lnrate(S, tau_far) - log(gthin);
+    const double xce = alpha / (alpha + gc);
+    double v = 0.0, t = 0.0;
+    for (int panel = 0; panel < 100000; ++panel) {
+        const double xv = slab_x(S, tau_far + v, nH, alpha, gc);
+        if (xv >= xce * (1.0 - 1e-10)) {            // neutral plateau: the rest is uniform
+            v += (tau_near - t) * xce;
+            break;
+        }
+        const double sl = -spec_slope(S, tau_far + v);
+        const double dv = 0.5 / fmax(sl, 1e-300);
+        const double dt = slab_panel(S, tau_far, v, v + dv, nH, alpha, gc);
+        if (t + dt < tau_near) {
+            t += dt;
+            v += dv;
+            continue;
+        }
+        // t(v + e) = t + int_v^{v+e} 1/x = tau_near: Newton from the linear guess
+        double e = dv * (tau_near - t) / dt;
+        for (int it = 0; it < 30; ++it) {
+            const double g = t + slab_panel(S, tau_far, v, v + e, nH, alpha, gc) - tau_near;
+            const double step = g * slab_x(S, tau_far + v + e, nH, alpha, gc);
+            double en = e - step;
+            en = fmin(fmax(en, 0.0), dv);
+            const bool done = fabs(en - e) <= 1e-14 * (v + dv);
+            e = en;
+            if (done) break;
+        }
+        v += e;
+        break;
+    }
+    return spec_lnrate(S, tau_far + v) - log(gthin);
+}
+
 }  // namespace urchin

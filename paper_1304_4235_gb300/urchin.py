@@ -29,6 +29,7 @@ F32, F64 = 0, 1
 CASE_A, CASE_B, CASE_AUTO = 0, 1, 2
 XSEC_VERNER, XSEC_HYDROGENIC, XSEC_POWERLAW = 0, 1, 2
 METHOD_PLAIN, METHOD_NEWTON, METHOD_ANDERSON = 0, 1, 2
+SLAB_THRESHOLD, SLAB_SPECTRUM = 1, 2
 SEG_RECOMPUTE, SEG_STORE, SEG_AUTO = 0, 1, 2
 MAX_RAYS = 192
 MAX_BINS = 4096
@@ -112,7 +113,7 @@ SIGNATURES = {
     "urchin_trace_columns_nearfar": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_double, _vp, C.c_int64,
                                                C.c_int, C.c_int, _vp, _vp, _vp]),
     "urchin_gamma_nearfar": (C.c_int, [_vp, _vp, C.c_int, C.c_int64, C.c_int, C.POINTER(urchin_spectrum),
-                                       _vp, _vp, _vp, _vp, _vp, _vp]),
+                                       _vp, _vp, _vp, C.c_int, _vp, _vp, _vp]),
 }
 
 _lib = None
@@ -289,9 +290,10 @@ def urchin_trace_columns_nearfar(bvh: Bvh, x, dirs, l_ray: float, origins=None, 
     return tf, tn
 
 
-def urchin_gamma_nearfar(tau_far, tau_near, s, w, nH, T, caseB=None, stream=None):
+def urchin_gamma_nearfar(tau_far, tau_near, s, w, nH, T, caseB=None, slab: int = SLAB_THRESHOLD, stream=None):
     """(Gamma float64, tau_eff float32) per origin with the slab solution for
-    the near particles; caseB: uint8 CUDA tensor or None (case A)."""
+    the near particles; caseB: uint8 CUDA tensor or None (case A); slab:
+    SLAB_THRESHOLD (analytic) or SLAB_SPECTRUM (numerical, binned spectrum)."""
     import torch
     precision = F64 if tau_far.dtype == torch.float64 else F32
     n_orig, R = tau_far.shape
@@ -300,7 +302,7 @@ def urchin_gamma_nearfar(tau_far, tau_near, s, w, nH, T, caseB=None, stream=None
     te = torch.empty(n_orig, dtype=torch.float32, device=tau_far.device)
     _check(load().urchin_gamma_nearfar(_dev(tau_far), _dev(tau_near, tau_far.dtype), int(precision), n_orig, R,
                                        C.byref(sp), _dev(nH, torch.float64), _dev(T, torch.float64),
-                                       _dev(caseB, torch.uint8), _dev(g), _dev(te), _stream(stream)))
+                                       _dev(caseB, torch.uint8), int(slab), _dev(g), _dev(te), _stream(stream)))
     return g, te
 
 
@@ -334,7 +336,7 @@ def urchin_solve(bvh: Bvh, dirs, l_ray: float, s, w, nH, T, x=None, *, y: float 
                  kernel: int = KERNEL_M4, precision: int = F32, case_rule: int = CASE_AUTO,
                  warm_start: bool = False, profile: bool = False, raise_not_converged: bool = True,
                  history: bool = False, blocks: int = 1, newton_switch: float = 0.01, newton_eta: float = 0.0,
-                 state=None, near_far: bool = False, stream=None):
+                 state=None, near_far: int = 0, stream=None):
     """Returns (x, stats dict).  x (float64 CUDA tensor, original order) is
     updated in place when given.  `state` (uint8 CUDA tensor [n]) receives
     each particle's final case / frozen flags for urchin_solve_vjp."""
@@ -365,7 +367,7 @@ def urchin_solve(bvh: Bvh, dirs, l_ray: float, s, w, nH, T, x=None, *, y: float 
     P.newton_switch = float(newton_switch)
     P.newton_eta = float(newton_eta)
     P.state = _dev(state, torch.uint8)
-    P.near_far = int(bool(near_far))
+    P.near_far = int(near_far)
     hist_max = hist_unc = None
     if history:
         hist_max = np.zeros(int(max_iter))
