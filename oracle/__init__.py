@@ -89,6 +89,8 @@ def _load():
                 "oracle_slab_lngamma": (d, [d, d, d, i, d]),
                 "oracle_gamma_nearfar": (None, [vp, vp, i64, i, i, vp, vp, vp, vp, vp, i, vp, vp]),
                 "oracle_slab_poly_lngamma": (d, [i, vp, vp, d, d, d, i, d]),
+                "oracle_ns_slab": (d, [i, vp, vp, d, d, i, d, i64, vp]),
+                "oracle_ns_slab2": (d, [i, vp, vp, d, d, i, d, i64, d, i, vp]),
                 "oracle_xeq_dgamma": (d, [d, d, d, d, i]),
                 "oracle_column_matrix": (None, [i64, vp, vp, vp, vp, vp, i, d, d,
                                                 vp, i64, vp, i, d, i, vp]),
@@ -299,6 +301,25 @@ def slab_poly_lngamma(s, w, tau_far, nH, T, caseB, tau_near):
                                             np.asarray(caseB, dtype=bool), np.asarray(tau_near, dtype=np.float64))
     return np.array([lib.oracle_slab_poly_lngamma(s.shape[0], _p(s), _p(w), float(a), float(b), float(c), int(e),
                                                   float(f)) for a, b, c, e, f in zip(tf, nH, T, cb, tn)])
+
+
+def ns_slab(s, w, nH, T, caseB, tau_total, n_slices):
+    """Test 1's slab solver: (x per slice from the lit surface, N_HI sigma_th
+    through the slab) for plane-parallel radiation with rates w_b."""
+    s, w = _f64(s), _f64(w)
+    x = np.zeros(int(n_slices))
+    t = _load().oracle_ns_slab(s.shape[0], _p(s), _p(w), float(nH), float(T), int(bool(caseB)), float(tau_total),
+                               int(n_slices), _p(x))
+    return x, t
+
+
+def ns_slab2(s, w, nH, T, caseB, tau_total, n_slices, tol=1e-8, max_pass=100000):
+    """Test 3's slab solver (lit from both sides, half the rate each)."""
+    s, w = _f64(s), _f64(w)
+    x = np.zeros(int(n_slices))
+    t = _load().oracle_ns_slab2(s.shape[0], _p(s), _p(w), float(nH), float(T), int(bool(caseB)), float(tau_total),
+                                int(n_slices), float(tol), int(max_pass), _p(x))
+    return x, t
 
 
 def gamma_nearfar(tau_far, tau_near, s, w, nH, T, caseB, poly=False):

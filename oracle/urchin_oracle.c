@@ -585,10 +585,83 @@ double oracle_slab_poly_lngamma(int F, const double* s, const double* w, double 
     return ln_spec_rate(F, s, w, tau_far + u);
 }
 
+/* The numerical slab solver of Test 1 (NS): plane-parallel radiation with
+ * the binned spectrum (s_b, w_b = its rate contributions at the surface)
+ * onto a uniform hydrogen slab of total thickness tau_total = N_H sigma_th,
+ * density nH, temperature T, recombination case caseB, y = 0.  The slab is
+ * cut into n_slices equal slices; going down from the surface, each slice
+ * takes the neutral column above it, tau = sum over the slices above of
+ * x dtau_H, the rate Gamma = sum_b w_b exp(-s_b tau), and x = x_eq(Gamma)
+ * (Eq. xroots).  Writes x of every slice (x_out, may be NULL) and returns
+ * the neutral column through the slab, N_HI sigma_th = sum x dtau_H. */
+double oracle_ns_slab(int F, const double* s, const double* w, double nH, double T, int caseB, double tau_total,
+                      int64_t n_slices, double* x_out)
+{
+    double dt = tau_total / (double)n_slices;
+    double tau = 0.0;
+    for (int64_t i = 0; i < n_slices; ++i) {
+        double g = exp(ln_spec_rate(F, s, w, tau));
+        double x = oracle_xeq(g, nH, T, 0.0, caseB);
+        if (x_out) x_out[i] = x;
+        tau += x * dt;
+    }
+    return tau;
+}
+
+/* NS for Test 3: the same slab lit from both sides, each side with half of
+ * the rate (w_b / 2 per side, so that thin gas keeps sum_b w_b).  Starting
+ * from the optically thin x, every slice takes the neutral columns above
+ * and below it from the previous pass, Gamma = (1/2) sum_b w_b
+ * [exp(-s_b tau_above) + exp(-s_b tau_below)], x = x_eq(Gamma); passes
+ * repeat until no slice changes by more than tol (relative) or max_pass.
+ * Writes x per slice and returns the total N_HI sigma_th. */
+double oracle_ns_slab2(int F, const double* s, const double* w, double nH, double T, int caseB, double tau_total,
+                       int64_t n_slices, double tol, int max_pass, double* x_out)
+{
+    double dt = tau_total / (double)n_slices;
+    double* x = (double*)malloc(sizeof(double) * (size_t)n_slices);
+    double* xn = (double*)malloc(sizeof(double) * (size_t)n_slices);
+    double* above = (double*)malloc(sizeof(double) * (size_t)n_slices);
+    double g0 = 0.0;
+    for (int b = 0; b < F; ++b) g0 += w[b];
+    for (int64_t i = 0; i < n_slices; ++i) x[i] = oracle_xeq(g0, nH, T, 0.0, caseB);
+    for (int pass = 0; pass < max_pass; ++pass) {
+        double acc = 0.0, total = 0.0;
+        for (int64_t i = 0; i < n_slices; ++i) total += x[i] * dt;
+        double maxrel = 0.0;
+        for (int64_t i = 0; i < n_slices; ++i) {
+            above[i] = acc;
+            acc += x[i] * dt;
+        }
+        for (int64_t i = 0; i < n_slices; ++i) {
+            double below = total - above[i] - x[i] * dt;
+            double g = 0.5 * (exp(ln_spec_rate(F, s, w, above[i])) + exp(ln_spec_rate(F, s, w, below)));
+            xn[i] = oracle_xeq(g, nH, T, 0.0, caseB);
+            double rel = fabs(xn[i] - x[i]) / x[i];
+            if (rel > maxrel) maxrel = rel;
+        }
+        memcpy(x, xn, sizeof(double) * (size_t)n_slices);
+        if (maxrel < tol) break;
+    }
+    double tot = 0.0;
+    for (int64_t i = 0; i < n_slices; ++i) {
+        tot += x[i] * dt;
+        if (x_out) x_out[i] = x[i];
+    }
+    free(x); free(xn); free(above);
+    return tot;
+}
+
 /* Shielded rate with the near/far split (Sec. 3.3.3, Eqs. gammafar,
- * gammashldk, gammashld): per ray Gamma_far = sum_j w_j exp(-s_j tau_far),
- * Gamma_shld,k = G(Gamma_far, nH, T, tau_near) with G the slab solution
- * above, Gamma = (1/R) sum_k Gamma_shld,k (the 4 pi / N_ray absorbed in w).
+ * gammashldk, gammashld).  Ray k carries the share 4 pi / N_ray of the
+ * radiation, here (1/R) of the spectrum weights w (sum_j w_j = Gamma_thin);
+ * its slab of near particles is lit by that share attenuated by the far
+ * column, Gamma_far,k = (1/R) sum_j w_j exp(-s_j tau_far,k), and the
+ * particle's rate is the sum of the slabs' bottom rates,
+ * Gamma = sum_k G(Gamma_far,k, nH, T, tau_near,k).  Reading: a slab lit by
+ * its ray's share reproduces the one-sided slab test exactly (one ray) and
+ * makes each slab miss the other directions' radiation, the shortcoming the
+ * paper gives for its two-sided slab test.
  * caseB[o] is the recombination case used inside the slab; poly = 0 takes
  * the analytic slab (radiation at the threshold with the far rate), poly = 1
  * the polychromatic slab (oracle_slab_poly_lngamma).  Writes
@@ -600,27 +673,30 @@ void oracle_gamma_nearfar(const double* tau_far, const double* tau_near, int64_t
 {
     double gthin = 0.0;
     for (int j = 0; j < F; ++j) gthin += w[j];
+    double* wsh = (double*)malloc(sizeof(double) * (size_t)F);   /* one ray's share */
+    for (int j = 0; j < F; ++j) wsh[j] = w[j] / (double)R;
 #pragma omp parallel for schedule(static)
     for (int64_t o = 0; o < n_orig; ++o) {
         double lk[512];
         double m = -INFINITY;
         for (int k = 0; k < R; ++k) {
             if (poly) {
-                lk[k] = oracle_slab_poly_lngamma(F, s, w, tau_far[o * R + k], nH[o], T[o], caseB[o],
+                lk[k] = oracle_slab_poly_lngamma(F, s, wsh, tau_far[o * R + k], nH[o], T[o], caseB[o],
                                                  tau_near[o * R + k]) - log(gthin);
             } else {
                 double gf = 0.0;
-                for (int j = 0; j < F; ++j) gf += w[j] * exp(-s[j] * tau_far[o * R + k]);
+                for (int j = 0; j < F; ++j) gf += wsh[j] * exp(-s[j] * tau_far[o * R + k]);
                 lk[k] = oracle_slab_lngamma(gf, nH[o], T[o], caseB[o], tau_near[o * R + k]) - log(gthin);
             }
             if (lk[k] > m) m = lk[k];
         }
         double acc = 0.0;
         for (int k = 0; k < R; ++k) acc += exp(lk[k] - m);
-        double lr = m + log(acc / (double)R);
+        double lr = m + log(acc);
         lnratio_out[o] = lr;
         gamma_out[o] = gthin * exp(lr);
     }
+    free(wsh);
 }
 
 /* Case choice (Sec. 3.3.3 / Sec. 4): 0 = always A, 1 = always B,

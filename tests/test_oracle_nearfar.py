@@ -155,3 +155,67 @@ def test_poly_near_far_iteration_converges():
     assert s1["converged"] and s2["converged"]
     # the hardened spectrum penetrates the near slab further: less neutral gas
     assert np.median(x2 / x1) <= 1.0 + 1e-12
+
+
+# -- Test 1's slab solver (NS) ---------------------------------------------------
+def test_ns_slab_matches_the_slab_solutions():
+    """The slice-by-slice slab solver converges (first order in the slice
+    thickness) to the integrated slab equations, and for one threshold bin to
+    the analytic solution."""
+    w_ = W.halo(n=10, seed=1, F=50)
+    e, J = w_.spectrum()
+    s, wts = O.spectrum(e, J, 1e-12)
+    sth = O.sigma_th()
+    for nH in (1.1e-3, 1.3e-3):
+        tot = sth * nH * 200.0 * 3.0856775814913673e21
+        x, t = O.ns_slab(s, wts, nH, 1e4, False, tot, 200000)
+        lg = O.slab_poly_lngamma(s, wts, 0.0, nH, 1e4, False, tot)[0]
+        xb = O.xeq(np.exp(lg), nH, 1e4, 0.0, False)[0]
+        assert abs(x[-1] / xb - 1) < 1e-3
+        x2, t2 = O.ns_slab(s, wts, nH, 1e4, False, tot, 100000)
+        assert abs(t2 / t - 1) < 1e-3
+    aA, aB, gc = O.rates(1e4)
+    one_s, one_w = np.array([1.0]), np.array([30.0 * aA * 1e-3])
+    x, t = O.ns_slab(one_s, one_w, 1e-3, 1e4, False, 20.0, 400000)
+    xa = O.xeq(np.exp(O.slab_lngamma(one_w[0], 1e-3, 1e4, False, 20.0)[0]), 1e-3, 1e4, 0.0, False)[0]
+    assert abs(x[-1] / xa - 1) < 1e-3
+
+
+def test_ns_slab_two_sided():
+    """Test 3's solver: symmetric about the mid-plane, equal to the one-sided
+    solver in the optically thin limit, and, when thick, holding less neutral
+    gas than the slab lit from one side with the whole rate (which in turn
+    holds less than with half of it)."""
+    w_ = W.halo(n=10, seed=1, F=50)
+    e, J = w_.spectrum()
+    s, wts = O.spectrum(e, J, 1e-12)
+    sth = O.sigma_th()
+    L = 200.0 * 3.0856775814913673e21
+    x, t = O.ns_slab2(s, wts, 1e-4, 1e4, False, sth * 1e-4 * L, 2000)
+    x1, t1 = O.ns_slab(s, wts, 1e-4, 1e4, False, sth * 1e-4 * L, 2000)
+    assert abs(t / t1 - 1) < 2e-3
+    x, t = O.ns_slab2(s, wts, 1.3e-3, 1e4, False, sth * 1.3e-3 * L, 4000)
+    np.testing.assert_allclose(x, x[::-1], rtol=1e-9)
+    _, t_full = O.ns_slab(s, wts, 1.3e-3, 1e4, False, sth * 1.3e-3 * L, 4000)
+    _, t_half = O.ns_slab(s, 0.5 * wts, 1.3e-3, 1e4, False, sth * 1.3e-3 * L, 4000)
+    assert t < t_full < t_half
+
+
+def test_each_ray_slab_takes_its_share_of_the_radiation():
+    """Eq. gammashld: ray k carries 4 pi / N_ray of the radiation, so its
+    slab is lit by (1/R) of the far-attenuated rate and the slabs' bottom
+    rates add up: with R identical rays the rate is R G(Gamma_far / R)."""
+    w_ = W.halo(n=10, seed=1, F=30)
+    e, J = w_.spectrum()
+    s, wts = O.spectrum(e, J, w_.gamma_thin)
+    nH, T = 2e-3, 1e4
+    for R in (1, 2, 12):
+        tf = np.full((1, R), 0.7)
+        tn = np.full((1, R), 4.0)
+        lr, g = O.gamma_nearfar(tf, tn, s, wts, nH, T, False)
+        gfar = (wts * np.exp(-s * 0.7)).sum()
+        ref = R * np.exp(O.slab_lngamma(gfar / R, nH, T, False, 4.0)[0])
+        assert abs(g[0] / ref - 1) < 1e-12
+        lrp, gp = O.gamma_nearfar(tf, tn, s, wts, nH, T, False, poly=True)
+        refp = R * np.exp(O.slab_poly_lngamma(s, wts / R, 0.7, nH, T, False, 4.0)[0])
+        assert abs(gp[0] / refp - 1) < 1e-12

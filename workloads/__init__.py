@@ -75,8 +75,9 @@ def smoothing_lengths(pos: np.ndarray, n_ngb: int, box: float | None) -> np.ndar
         tree = cKDTree(p, boxsize=box)
     else:
         tree = cKDTree(p)
-    d, _ = tree.query(p, k=n_ngb + 1, workers=-1)
-    return d[:, n_ngb].astype(np.float32)
+    # only the (n_ngb + 1)-th nearest (the particle itself is the first)
+    d, _ = tree.query(p, k=[n_ngb + 1], workers=-1)
+    return d[:, 0].astype(np.float32)
 
 
 def powerlaw_spectrum(F: int, e_lo: float, e_hi: float, alpha: float = 1.5):
@@ -177,6 +178,34 @@ def lognormal_box(n_side: int = 128, box_kpc: float = 4000.0, sigma_ln: float = 
                     1.0e-12, seed)
 
 
+def slab(n_z: int = 16, slab_kpc: float = 200.0, nH: float = 1.2e-3, T: float = 1.0e4, jitter: float = 0.1,
+         n_ngb: int = 32, seed: int = 1307, F: int = 50, box_factor: int = 3) -> Workload:
+    """Uniform isothermal slab z in [0, slab_kpc] (the SPH slabs of the
+    paper's Tests 2-3): a jittered lattice of spacing slab_kpc / n_z, laterally
+    periodic in a cubic box of side box_factor * slab_kpc (the rest of the box
+    is empty, so a ray of length slab_kpc never wraps back into the slab).
+    One ray per particle toward the lit surface z = 0 is the caller's choice
+    of directions."""
+    rng = np.random.default_rng(seed)
+    d = slab_kpc / n_z
+    box = box_factor * slab_kpc
+    nxy = box_factor * n_z
+    gx = (np.arange(nxy) + 0.5) * d
+    gz = (np.arange(n_z) + 0.5) * d
+    X, Y, Z = np.meshgrid(gx, gx, gz, indexing="ij")
+    p = np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1)
+    p += rng.uniform(-jitter * d, jitter * d, size=p.shape)
+    p[:, :2] = np.mod(p[:, :2], box)
+    p = p.astype(np.float32)
+    p[p >= np.float32(box)] = 0.0
+    n = p.shape[0]
+    h = smoothing_lengths(p, n_ngb, box)
+    vol_cm3 = (box * KPC_CM) ** 2 * (slab_kpc * KPC_CM)
+    mass = np.full(n, nH * vol_cm3 / n, dtype=np.float64)
+    return Workload("slab", p, h, mass, np.full(n, nH), np.full(n, T), True, box, KPC_CM, 1, slab_kpc, F,
+                    13.6, 54.4, 1.0e-12, seed)
+
+
 def subset(w: Workload, idx: np.ndarray, name: str | None = None) -> Workload:
     """Particles ``idx`` of a workload (e.g. a small isolated cut-out)."""
     return dataclasses.replace(
@@ -196,4 +225,5 @@ CONFIGS = {
     "lattice_box": lattice_box,
     "halo": halo,
     "lognormal_box": lognormal_box,
+    "slab": slab,
 }
