@@ -164,10 +164,14 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs A)
                 const bool cB = A.case_rule == URCHIN_CASE_B || (A.case_rule == URCHIN_CASE_AUTO && A.latch[ir]);
                 const double tn = (double)static_cast<const Real*>(A.tau_near)[ir + (int64_t)k * A.near_k_stride];
                 const double al = cB ? A.aB[ir] : A.aA[ir];
+                // each slab is lit by its ray's share (1/R) of the radiation and the
+                // particle's rate is the sum of the slabs' bottom rates: scale by 1/R
+                // into the slab and by R out of it (the ray combination below is a mean)
+                const double lnR = log((double)A.R);
                 if (A.near_far == URCHIN_SLAB_SPECTRUM)
-                    lkv = (Real)slab_poly_lnratio(A.poly, gthin, (double)tau, tn, A.nH[ir], al, A.gc[ir]);
+                    lkv = (Real)(slab_poly_lnratio(A.poly, gthin, (double)tau, tn, A.nH[ir], al, A.gc[ir], -lnR) + lnR);
                 else
-                    lkv = (Real)slab_lnratio((double)lkv, gthin, tn, A.nH[ir], al, A.gc[ir]);
+                    lkv = (Real)(slab_lnratio((double)lkv - lnR, gthin, tn, A.nH[ir], al, A.gc[ir]) + lnR);
             }
             lk[local * A.R + k] = lkv;
             if (A.want_tangent) lk2[local * A.R + k] = -smin * tau + log_p(S2 > Real(1e-37) ? S2 : Real(1e-37));

@@ -294,12 +294,15 @@ __global__ void k_gamma_nearfar(const Real* __restrict__ tf, const Real* __restr
         for (int k = 0; k < R; ++k) {
             const double t = (double)tf[o * R + k];
             double l;
+            // the ray's share (1/R) of the radiation lights its slab; rates add over rays
+            const double lnR = log((double)R);
             if (poly.tab) {
-                l = slab_poly_lnratio(poly, gthin, t, (double)tn[o * R + k], nH[o], alpha, r.gamma_c);
+                l = slab_poly_lnratio(poly, gthin, t, (double)tn[o * R + k], nH[o], alpha, r.gamma_c, -lnR) + lnR;
             } else {
                 double S = 0.0;
                 for (int b = 0; b < F; ++b) S += ws[b] * exp(-ss[b] * t);
-                l = slab_lnratio(-smin * t + log(S), gthin, (double)tn[o * R + k], nH[o], alpha, r.gamma_c);
+                l = slab_lnratio(-smin * t + log(S) - lnR, gthin, (double)tn[o * R + k], nH[o], alpha, r.gamma_c) +
+                    lnR;
             }
             if (!(l > -INFINITY)) continue;
             if (l > m) {

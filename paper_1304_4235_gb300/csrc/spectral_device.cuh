@@ -66,7 +66,9 @@ __device__ __forceinline__ double dx_dgamma(double x, double nH, double alpha, d
 // Near/far split (Sec. 3.3.3): the near particles of a ray's origin are
 // modelled as a uniform hydrogen slab of thickness tau_near = N_H sigma_th
 // (all hydrogen, x = 1), with the origin's density and temperature, lit by
-// the far-attenuated radiation with rate Gamma_far at its surface.  For
+// the far-attenuated radiation of that ray's direction, i.e. its share
+// (1/N_ray) of the rate, Gamma_far at the slab's surface; the particle's
+// rate is the sum over rays of the slabs' bottom rates (Eq. gammashld).  For
 // radiation at the threshold (the slab appendix, y = 0) the depth at which
 // the equilibrium neutral fraction is x obeys
 //   z nH sigma = (1/x0 - 1/x) + ln[x (1-x0) / (x0 (1-x))]
@@ -184,37 +186,40 @@ __device__ __forceinline__ double spec_slope(const SpecTable& S, double tau)
 // solved by Newton's method on its own quadrature.  Once x is within 1e-10
 // of x_ce the rest of the slab is uniform (1/x = 1/x_ce).  Returns
 // ln(Gamma_bottom / Gamma_thin).
-__device__ __forceinline__ double slab_x(const SpecTable& S, double tau, double nH, double alpha, double gc)
+__device__ __forceinline__ double slab_x(const SpecTable& S, double tau, double lnscale, double nH, double alpha,
+                                         double gc)
 {
-    return x_equilibrium(exp(spec_lnrate(S, tau)), nH, alpha, gc, 0.0);
+    return x_equilibrium(exp(spec_lnrate(S, tau) + lnscale), nH, alpha, gc, 0.0);
 }
 
-__device__ __forceinline__ double slab_panel(const SpecTable& S, double tf, double a, double b, double nH,
-                                             double alpha, double gc)
+__device__ __forceinline__ double slab_panel(const SpecTable& S, double tf, double ls, double a, double b,
+                                             double nH, double alpha, double gc)
 {
     // 4-point Gauss-Legendre of 1/x over [a, b]
     const double g1 = 0.3399810435848563, g2 = 0.8611363115940526;
     const double w1 = 0.6521451548625461, w2 = 0.3478548451374538;
     const double m = 0.5 * (a + b), r = 0.5 * (b - a);
-    return r * (w1 / slab_x(S, tf + m - r * g1, nH, alpha, gc) + w1 / slab_x(S, tf + m + r * g1, nH, alpha, gc) +
-                w2 / slab_x(S, tf + m - r * g2, nH, alpha, gc) + w2 / slab_x(S, tf + m + r * g2, nH, alpha, gc));
+    return r * (w1 / slab_x(S, tf + m - r * g1, ls, nH, alpha, gc) + w1 / slab_x(S, tf + m + r * g1, ls, nH, alpha, gc) +
+                w2 / slab_x(S, tf + m - r * g2, ls, nH, alpha, gc) + w2 / slab_x(S, tf + m + r * g2, ls, nH, alpha, gc));
 }
 
 __device__ __forceinline__ double slab_poly_lnratio(const SpecTable& S, double gthin, double tau_far,
-                                                    double tau_near, double nH, double alpha, double gc)
+                                                    double tau_near, double nH, double alpha, double gc,
+                                                    double lnscale)
 {
-    if (!(tau_near > 0.0)) return spec_lnrate(S, tau_far) - log(gthin);
+    // the slab is lit by the tabulated spectrum scaled by e^lnscale (a ray's share)
+    if (!(tau_near > 0.0)) return spec_lnrate(S, tau_far) + lnscale - log(gthin);
     const double xce = alpha / (alpha + gc);
     double v = 0.0, t = 0.0;
     for (int panel = 0; panel < 100000; ++panel) {
-        const double xv = slab_x(S, tau_far + v, nH, alpha, gc);
+        const double xv = slab_x(S, tau_far + v, lnscale, nH, alpha, gc);
         if (xv >= xce * (1.0 - 1e-10)) {            // neutral plateau: the rest is uniform
             v += (tau_near - t) * xce;
             break;
         }
         const double sl = -spec_slope(S, tau_far + v);
         const double dv = 0.5 / fmax(sl, 1e-300);
-        const double dt = slab_panel(S, tau_far, v, v + dv, nH, alpha, gc);
+        const double dt = slab_panel(S, tau_far, lnscale, v, v + dv, nH, alpha, gc);
         if (t + dt < tau_near) {
             t += dt;
             v += dv;
@@ -223,8 +228,8 @@ __device__ __forceinline__ double slab_poly_lnratio(const SpecTable& S, double g
         // t(v + e) = t + int_v^{v+e} 1/x = tau_near: Newton from the linear guess
         double e = dv * (tau_near - t) / dt;
         for (int it = 0; it < 30; ++it) {
-            const double g = t + slab_panel(S, tau_far, v, v + e, nH, alpha, gc) - tau_near;
-            const double step = g * slab_x(S, tau_far + v + e, nH, alpha, gc);
+            const double g = t + slab_panel(S, tau_far, lnscale, v, v + e, nH, alpha, gc) - tau_near;
+            const double step = g * slab_x(S, tau_far + v + e, lnscale, nH, alpha, gc);
             double en = e - step;
             en = fmin(fmax(en, 0.0), dv);
             const bool done = fabs(en - e) <= 1e-14 * (v + dv);
@@ -234,7 +239,7 @@ __device__ __forceinline__ double slab_poly_lnratio(const SpecTable& S, double g
         v += e;
         break;
     }
-    return spec_lnrate(S, tau_far + v) - log(gthin);
+    return spec_lnrate(S, tau_far + v) + lnscale - log(gthin);
 }
 
 }  // namespace urchin

@@ -80,12 +80,17 @@ struct Sink {
 };
 
 // Near/far split (Sec. 3.3.3): particle j is near the ray's origin when the
-// origin lies inside j's smoothing sphere.  Evaluated in double from the
-// float positions (the differences are exact), like the reference
-// definition, so both sides classify every pair the same way.
+// origin lies inside j's smoothing sphere.  For a crossed sphere that is the
+// case exactly when its chord starts before the origin, tc - ch < 0 (the
+// origin at distance^2 = tc^2 + b^2 < h^2); that test decides unless the
+// origin sits within rounding of the sphere's surface, where the distance is
+// compared in double from the float positions (the differences are exact),
+// like the reference definition, so both sides classify every pair alike.
 template <typename Real>
-__device__ __forceinline__ bool is_near(const Sink<Real>& k, float4 q)
+__device__ __forceinline__ bool is_near(const Sink<Real>& k, float4 q, Real tc, Real ch)
 {
+    const Real gap = tc - ch;
+    if (fabs((double)gap) > 1e-4 * (double)q.w) return gap < Real(0);
     const double ex = (double)q.x - k.ox, ey = (double)q.y - k.oy, ez = (double)q.z - k.oz;
     const double hh = (double)q.w;
     return ex * ex + ey * ey + ez * ez < hh * hh;
@@ -317,7 +322,7 @@ __device__ __forceinline__ void leaf_hits_f32(const TraceParams& P, const float2
         float tc = ex * dx + ey * dy + ez * dz;
         float ch = sqrtf(h2 - b2);
         if (tc + ch <= 0.f || tc - ch >= L) continue;
-        const bool near = NF && is_near(k, q);
+        const bool near = NF && is_near(k, q, tc, ch);
         if (!near) ++k.nhit;
         if (MODE == MODE_COUNT) continue;
         float ih = 1.f / q.w;
@@ -371,7 +376,7 @@ __device__ __forceinline__ void leaf_hits(const TraceParams& P, int ref, int cnt
         if (b2 >= h2) continue;
         Real ch = O::sqrt_(h2 - b2);
         if (tc + ch <= Real(0) || tc - ch >= L) continue;
-        const bool near = NF && is_near(k, q);
+        const bool near = NF && is_near(k, q, tc, ch);
         if (!near) ++k.nhit;
         if (MODE == MODE_COUNT) continue;
         Real ih = Real(1) / h;
