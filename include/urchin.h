@@ -66,6 +66,7 @@ typedef struct CUstream_st* urchin_stream_t;
 #define URCHIN_XSEC_VERNER      0     /* Verner et al. 1996 fit, App. C1        */
 #define URCHIN_XSEC_HYDROGENIC  1     /* exact hydrogenic, Eq. sigma_ana        */
 #define URCHIN_XSEC_POWERLAW    2     /* sigma_th (nu/nu_th)^-3, Eq. sigma_pwr  */
+#define URCHIN_XSEC_HEII        3     /* He II: exact hydrogenic, Z = 2 (54.4 eV) */
 #define URCHIN_METHOD_PLAIN     0     /* Jacobi fixed point (Sec. 4)            */
 #define URCHIN_METHOD_NEWTON    1     /* Newton-Krylov on the same fixed point  */
 #define URCHIN_METHOD_ANDERSON  2     /* Anderson-accelerated sweeps            */
@@ -105,12 +106,21 @@ typedef struct {
 } urchin_box;
 
 /* Binned UV-background spectrum (Eq. gamma_shld, Sec. 3.3.3):
- * Gamma/Gamma_thin = (1/N_ray) sum_k sum_j w_j exp(-s_j tau_k) / sum_j w_j. */
+ * Gamma/Gamma_thin = (1/N_ray) sum_k sum_j w_j exp(-s_j tau_k) / sum_j w_j.
+ * Optional helium (the paper treats hydrogen only): the bins' He I and He II
+ * cross sections in the same units; the exponent then becomes
+ * s_j tau_k + s_he1_j tau_he1_k + s_he2_j tau_he2_k with the helium columns
+ * tau_he (N_He sigma_th).  Only urchin_gamma_he and the plain urchin_solve
+ * accept a spectrum with helium cross sections; the other calls return
+ * URCHIN_ERR_ARG for it. */
 typedef struct {
     int           F;        /* bins, 1..URCHIN_MAX_BINS                        */
     const double* s;        /* device [F] sigma(nu_j) / sigma_th, >= 0         */
     const double* w;        /* device [F] rate weights (s^-1), >= 0, with
                                sum_j w_j = Gamma_thin > 0                      */
+    const double* s_he1;    /* device [F] sigma_HeI(nu_j) / sigma_th, or NULL  */
+    const double* s_he2;    /* device [F] sigma_HeII(nu_j) / sigma_th, or NULL
+                               (both or neither)                               */
 } urchin_spectrum;
 
 /* Opaque bounding-volume hierarchy over the particles' smoothing spheres
@@ -145,6 +155,14 @@ URCHIN_API int urchin_healpix_dirs(int nside, double* dirs_out);
  * `xsec` selects the cross section (URCHIN_XSEC_*).  Errors: ERR_ARG. */
 URCHIN_API int urchin_spectrum_weights(int F, const double* E_edges, const double* J, int xsec,
                             double gamma_thin, double* s_out, double* w_out);
+
+/* Cross-section ratios for the bins (host only): s_out[j] =
+ * sigma(E_j) / sigma_th at the geometric bin centres E_j of the F+1 edges
+ * (eV, increasing), zero below the species' threshold.  xsec:
+ * URCHIN_XSEC_VERNER / _HYDROGENIC / _POWERLAW (H I, App. C1) or
+ * URCHIN_XSEC_HEII (He II, the exact hydrogenic form with Z = 2, for the
+ * helium columns, which the paper does not treat).  Errors: ERR_ARG. */
+URCHIN_API int urchin_cross_section_ratio(int F, const double* E_edges, int xsec, double* s_out);
 
 /* Build the BVH (no counterpart in the paper, which does not describe its
  * search structure): Morton codes of the sphere centres, radix sort, binary
@@ -250,6 +268,18 @@ URCHIN_API int urchin_gamma(const void* tau, int precision, int64_t n_orig, int 
                  const urchin_spectrum* sp, double* gamma_out, float* tau_eff_out,
                  urchin_stream_t stream);
 
+/* The rate behind hydrogen and helium columns (helium is not in the paper,
+ * which treats hydrogen only): with the spectrum's s, s_he1, s_he2,
+ *   gamma_out[o] = (1/R) sum_k sum_j w_j exp(-(s_j tau + s_he1_j tau_he1
+ *                                               + s_he2_j tau_he2)[o*R + k]),
+ * tau_eff_out as in urchin_gamma.  tau, tau_he1, tau_he2 device
+ * [n_orig*R] of the precision's type (helium columns in units of N_He
+ * sigma_th).  Errors: ERR_ARG (also when the spectrum lacks s_he1 / s_he2),
+ * ERR_CUDA. */
+URCHIN_API int urchin_gamma_he(const void* tau, const void* tau_he1, const void* tau_he2, int precision,
+                               int64_t n_orig, int R, const urchin_spectrum* sp, double* gamma_out,
+                               float* tau_eff_out, urchin_stream_t stream);
+
 /* Ionisation equilibrium, App. C3 (Eqs. dxdt, xroots): the physical root
  * x_- of R x^2 + Q x + P = 0 with R = (gamma_c + alpha) n_H,
  * Q = -[Gamma + alpha n_H + R (1+y)], P = alpha n_H (1+y), in FP64, where
@@ -306,6 +336,11 @@ typedef struct {
                                      reads each particle's final state,
                                      bit 0 = recombination case B,
                                      bit 1 = frozen after sweep 0             */
+    const double*   he1;          /* device [n] or NULL: He I atoms per H atom of
+                                     each particle (n_He/n_H times the He I
+                                     fraction, fixed), original order; needed
+                                     when the spectrum has s_he1 / s_he2      */
+    const double*   he2;          /* device [n] or NULL: He II atoms per H atom */
     int             near_far;     /* 0: off; URCHIN_SLAB_THRESHOLD or
                                      URCHIN_SLAB_SPECTRUM: the near/far split
                                      of Sec. 3.3.3 (plain method, blocks <= 1,
@@ -356,6 +391,10 @@ typedef struct {
  * the non-frozen particles remain above tol, then solves the same fixed
  * point x = E(Gamma(x)) with a Newton-Krylov iteration in ln x (GMRES with
  * tangent columns, backtracking, plain-sweep fallback).
+ * With helium (spectrum s_he1 / s_he2, params he1 / he2; plain method,
+ * no near/far split, blocks <= 1) the fixed He I and He II columns of every
+ * ray are traced once, with weights he1 / he2, and attenuate the spectrum in
+ * every sweep.
  * URCHIN_METHOD_ANDERSON accelerates the sweeps themselves: each iteration
  * evaluates the sweep map once and combines it with the last gmres_m
  * iterates (Anderson mixing in ln x, restarted when the residual grows).  x_inout is

@@ -83,7 +83,9 @@ def _load():
                 "oracle_rates": (None, [d, vp, vp, vp]),
                 "oracle_xeq": (d, [d, d, d, d, i]),
                 "oracle_solve": (i, [i64, vp, vp, vp, vp, vp, vp, vp, d, i, d, d,
-                                     vp, i, d, i, i, vp, vp, d, d, i, i, i, i, vp, vp, vp, vp, vp]),
+                                     vp, i, d, i, i, vp, vp, d, d, i, i, i, i, vp, vp, vp, vp,
+                                     vp, vp, vp, vp, vp]),
+                "oracle_gamma_he": (None, [vp, vp, vp, i64, i, i, vp, vp, vp, vp, vp, vp]),
                 "oracle_columns_nearfar": (None, [i64, vp, vp, vp, vp, vp, vp, i, d, d,
                                                   vp, i64, vp, i, d, i, vp, vp]),
                 "oracle_slab_lngamma": (d, [d, d, d, i, d]),
@@ -232,12 +234,13 @@ def xeq(Gamma, nH, T, y=0.0, caseB=False):
 
 # -- driver (Sec. 4) ---------------------------------------------------------
 def solve(w, s, wts, dirs, tol=1e-3, tau_skip=1e-4, max_iter=100, case_rule=CASE_AUTO,
-          kernel=KERNEL_M4, y=0.0, x_start=None, sweeps=None, l_ray=None, blocks=1, near_far=0):
+          kernel=KERNEL_M4, y=0.0, x_start=None, sweeps=None, l_ray=None, blocks=1, near_far=0, he=None):
     """Iteration of Sec. 4: Jacobi (blocks=1) or the high-to-low density
     update order in `blocks` blocks.  ``sweeps`` = exact sweep count
     (step-matched mode) instead of the tolerance test.  Returns (x, frozen,
     stats) with stats = dict(sweeps, max_rel_dx, rays, converged, caseB), caseB
-    the case of each particle's last update."""
+    the case of each particle's last update.  he = dict(tau1, tau2 [n, R],
+    s1, s2 [F]) adds fixed He I / He II columns (gamma_he)."""
     px, py, pz, h, m = _particles(w)
     nH, T = _f64(w.nH), _f64(w.T)
     dirs = _f64(dirs).reshape(-1, 3)
@@ -248,15 +251,19 @@ def solve(w, s, wts, dirs, tol=1e-3, tau_skip=1e-4, max_iter=100, case_rule=CASE
     st = np.zeros(3)
     xs = None if x_start is None else _f64(x_start)
     mi = -int(sweeps) if sweeps is not None else int(max_iter)
+    h1 = h2 = hs1 = hs2 = None
+    if he is not None:
+        h1, h2 = _f64(he["tau1"]).reshape(-1), _f64(he["tau2"]).reshape(-1)
+        hs1, hs2 = _f64(he["s1"]), _f64(he["s2"])
     rc = _load().oracle_solve(w.n, _p(px), _p(py), _p(pz), _p(h), _p(m), _p(nH), _p(T),
                               float(y), int(w.periodic), float(w.box), float(w.unit_cm),
                               _p(dirs), dirs.shape[0],
                               float(w.l_ray if l_ray is None else l_ray), kernel,
                               s.shape[0], _p(s), _p(wts), float(tol), float(tau_skip),
-                              mi, case_rule, int(blocks), int(near_far), _p(xs), _p(x), _p(frozen),
-                              _p(caseB), _p(st))
+                              mi, case_rule, int(blocks), int(near_far), _p(h1), _p(h2), _p(hs1), _p(hs2),
+                              _p(xs), _p(x), _p(frozen), _p(caseB), _p(st))
     if rc == 2:
-        raise ValueError("near_far needs blocks <= 1")
+        raise ValueError("near_far needs blocks <= 1, helium needs near_far = 0 and blocks <= 1")
     return x, frozen.astype(bool), dict(sweeps=int(st[0]), max_rel_dx=float(st[1]),
                                         rays=float(st[2]), converged=(rc == 0),
                                         caseB=caseB.astype(bool))
@@ -430,6 +437,19 @@ def solve_vjp(w, s, wts, dirs, x_star, frozen, caseB, x_bar, case_rule=CASE_AUTO
         cb = np.full(fro.shape[0], case_rule == CASE_B)
         w_bar = w_bar + float(xbar_f @ xeq_dgamma(gthin, w.nH[fro], w.T[fro], y, cb))
     return w_bar, mu
+
+
+# -- helium columns (not in the paper: hydrogen only) --------------------------
+def gamma_he(tau, tau1, tau2, s, s1, s2, w):
+    """(Gamma, tau_eff) behind H I, He I and He II columns (threshold units)."""
+    tau, tau1, tau2 = _f64(tau), _f64(tau1), _f64(tau2)
+    n_orig, R = tau.shape
+    s, s1, s2, w = _f64(s), _f64(s1), _f64(s2), _f64(w)
+    g = np.zeros(n_orig)
+    te = np.zeros(n_orig)
+    _load().oracle_gamma_he(_p(tau), _p(tau1), _p(tau2), n_orig, R, s.shape[0], _p(s), _p(s1), _p(s2), _p(w),
+                            _p(g), _p(te))
+    return g, te
 
 
 def num_threads() -> int:

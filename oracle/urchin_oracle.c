@@ -412,6 +412,31 @@ void oracle_gamma(const double* tau, int64_t n_orig, int R, int F,
     }
 }
 
+/* Hydrogen photoionisation rate behind columns of H I, He I and He II (the
+ * paper treats hydrogen only; helium columns attenuate the same spectrum):
+ * tau, tau1, tau2 are the three columns in units of the H I threshold cross
+ * section (N sigma_th) and s, s1, s2 the cross sections of each species in
+ * the bins in the same units (zero below a species' threshold):
+ *   Gamma_o = (1/R) sum_k sum_j w_j exp(-(s_j tau_ok + s1_j tau1_ok + s2_j tau2_ok)). */
+void oracle_gamma_he(const double* tau, const double* tau1, const double* tau2, int64_t n_orig, int R, int F,
+                     const double* s, const double* s1, const double* s2, const double* w,
+                     double* gamma_out, double* tau_eff_out)
+{
+    double gthin = 0.0;
+    for (int j = 0; j < F; ++j) gthin += w[j];
+#pragma omp parallel for schedule(static)
+    for (int64_t o = 0; o < n_orig; ++o) {
+        double g = 0.0;
+        for (int k = 0; k < R; ++k) {
+            int64_t r = o * R + k;
+            for (int j = 0; j < F; ++j) g += w[j] * exp(-(s[j] * tau[r] + s1[j] * tau1[r] + s2[j] * tau2[r]));
+        }
+        g /= (double)R;
+        gamma_out[o] = g;
+        if (tau_eff_out) tau_eff_out[o] = -log(g / gthin);
+    }
+}
+
 /* ------------------------------------------------------------------------ */
 /* Rate coefficients (App. C3 refers to published fits; Hui & Gnedin 1997). */
 /* ------------------------------------------------------------------------ */
@@ -740,6 +765,9 @@ static int use_caseB(int case_rule, double tau_eff)
  * near particles uses each particle's case before the sweep (its latch, or
  * the forced case), then tau_eff = -ln(Gamma/Gamma_thin) decides the case
  * of the update as above.  It needs blocks <= 1 (returns 2 otherwise).
+ * he_tau1 / he_tau2 (optional, [n*R] per particle and ray, fixed) are He I
+ * and He II columns that attenuate the spectrum with the bin cross sections
+ * he_s1 / he_s2 (oracle_gamma_he); they need near_far = 0 and blocks <= 1.
  * x_out[n] receives the final x, frozen_out[n] (optional) 1 for frozen
  * particles, caseB_out[n] (optional) 1 where the final update used case B,
  * stats[0] = sweeps done, stats[1] = last max |dx|/x,
@@ -762,8 +790,10 @@ int oracle_solve(int64_t n, const double* px, const double* py, const double* pz
                  const double* dirs, int R, double l_ray, int kernel,
                  int F, const double* s, const double* w,
                  double tol, double tau_skip, int max_iter, int case_rule, int blocks, int near_far,
+                 const double* he_tau1, const double* he_tau2, const double* he_s1, const double* he_s2,
                  const double* x_start, double* x_out, int* frozen_out, int* caseB_out, double* stats)
 {
+    if (he_tau1 && (near_far || blocks > 1)) return 2;
     if (near_far && blocks > 1) return 2;
     double gthin = 0.0;
     for (int j = 0; j < F; ++j) gthin += w[j];
@@ -775,6 +805,8 @@ int oracle_solve(int64_t n, const double* px, const double* py, const double* pz
     double* nH_o = near_far ? (double*)malloc(sizeof(double) * (size_t)n) : NULL;
     double* T_o = near_far ? (double*)malloc(sizeof(double) * (size_t)n) : NULL;
     int* cb_o = near_far ? (int*)malloc(sizeof(int) * (size_t)n) : NULL;
+    double* he1_o = he_tau1 ? (double*)malloc(sizeof(double) * (size_t)n * R) : NULL;
+    double* he2_o = he_tau1 ? (double*)malloc(sizeof(double) * (size_t)n * R) : NULL;
     double* G = (double*)malloc(sizeof(double) * (size_t)n);
     double* te = (double*)malloc(sizeof(double) * (size_t)n);
     double* xn = (double*)malloc(sizeof(double) * (size_t)n);
@@ -800,6 +832,15 @@ int oracle_solve(int64_t n, const double* px, const double* py, const double* pz
                 }
                 oracle_gamma_nearfar(tau, tau_nr, nact, R, F, s, w, nH_o, T_o, cb_o, near_far == 2, te, G);
                 for (int64_t o = 0; o < nact; ++o) te[o] = -te[o];
+            } else if (he_tau1) {
+                oracle_columns(n, px, py, pz, h, mass_H, x, periodic, L, unit_cm,
+                               act, nact, dirs, R, l_ray, kernel, tau);
+                for (int64_t o = 0; o < nact; ++o)
+                    for (int k = 0; k < R; ++k) {
+                        he1_o[o * R + k] = he_tau1[act[o] * R + k];
+                        he2_o[o * R + k] = he_tau2[act[o] * R + k];
+                    }
+                oracle_gamma_he(tau, he1_o, he2_o, nact, R, F, s, he_s1, he_s2, w, G, te);
             } else {
                 oracle_columns(n, px, py, pz, h, mass_H, x, periodic, L, unit_cm,
                                act, nact, dirs, R, l_ray, kernel, tau);
@@ -859,7 +900,7 @@ int oracle_solve(int64_t n, const double* px, const double* py, const double* pz
     if (caseB_out) for (int64_t i = 0; i < n; ++i) caseB_out[i] = frozen[i] ? use_caseB(case_rule, 0.0) : latchB[i];
     if (stats) { stats[0] = sweeps; stats[1] = maxrel; stats[2] = rays; }
     free(frozen); free(latchB); free(tau); free(G); free(te); free(xn); free(act);
-    free(tau_nr); free(nH_o); free(T_o); free(cb_o);
+    free(tau_nr); free(nH_o); free(T_o); free(cb_o); free(he1_o); free(he2_o);
     return (fixed || converged) ? 0 : 1;
 }
 

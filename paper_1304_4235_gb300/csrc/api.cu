@@ -20,16 +20,18 @@ double sigma_verner(double E)
     return 5.475e-14 * xm1 * xm1 * std::pow(x, 0.5 * P - 5.5) * std::pow(1.0 + std::sqrt(x / 32.88), -P);
 }
 
-double sigma_hydrogenic(double E)
+double sigma_hydrogenic(double E, double Z = 1.0)
 {
-    // exact hydrogenic (Z = 1): sigma_th (nu_th/nu)^4 e^(4 - 4 atan(eps)/eps) / (1 - e^(-2 pi/eps)),
-    // eps = sqrt(nu/nu_th - 1); the bracket tends to 1 at threshold
-    if (E < kRydbergEV) return 0.0;
-    const double r = E / kRydbergEV;
+    // exact hydrogenic ion of charge Z (App. C1 for Z = 1; He II for Z = 2):
+    // (sigma_th / Z^2) (nu_th/nu)^4 e^(4 - 4 atan(eps)/eps) / (1 - e^(-2 pi/eps)),
+    // nu_th = Z^2 x 13.6 eV, eps = sqrt(nu/nu_th - 1); the bracket tends to 1 at threshold
+    const double Eth = Z * Z * kRydbergEV;
+    if (E < Eth) return 0.0;
+    const double r = E / Eth;
     const double eps = std::sqrt(r - 1.0);
     double f = 1.0;
     if (eps > 1e-6) f = std::exp(4.0 - 4.0 * std::atan(eps) / eps) / (-std::expm1(-2.0 * kPi / eps));
-    return sigma_th_cm2() * f / (r * r * r * r);
+    return sigma_th_cm2() / (Z * Z) * f / (r * r * r * r);
 }
 
 double sigma_powerlaw(double E)
@@ -119,5 +121,29 @@ extern "C" int urchin_spectrum_weights(int F, const double* E_edges, const doubl
     if (!(total > 0.0)) return set_error(URCHIN_ERR_ARG, "urchin_spectrum_weights: zero total rate");
     const double scale = gamma_thin / total;
     for (int j = 0; j < F; ++j) w_out[j] *= scale;
+    return URCHIN_OK;
+}
+
+extern "C" int urchin_cross_section_ratio(int F, const double* E_edges, int xsec, double* s_out)
+{
+    using namespace urchin;
+    clear_error();
+    if (F < 1 || F > URCHIN_MAX_BINS) return set_error(URCHIN_ERR_ARG, "urchin_cross_section_ratio: F = %d", F);
+    if (!E_edges || !s_out) return set_error(URCHIN_ERR_ARG, "urchin_cross_section_ratio: NULL array");
+    if (xsec != URCHIN_XSEC_VERNER && xsec != URCHIN_XSEC_HYDROGENIC && xsec != URCHIN_XSEC_POWERLAW &&
+        xsec != URCHIN_XSEC_HEII)
+        return set_error(URCHIN_ERR_ARG, "urchin_cross_section_ratio: unknown cross section %d", xsec);
+    for (int j = 0; j <= F; ++j)
+        if (!std::isfinite(E_edges[j]) || !(E_edges[j] > 0.0) || (j > 0 && !(E_edges[j] > E_edges[j - 1])))
+            return set_error(URCHIN_ERR_ARG, "urchin_cross_section_ratio: edges must be positive and increase");
+    const double sth = sigma_th_cm2();
+    for (int j = 0; j < F; ++j) {
+        const double Ec = std::sqrt(E_edges[j] * E_edges[j + 1]);
+        const double sig = xsec == URCHIN_XSEC_HYDROGENIC ? sigma_hydrogenic(Ec)
+                         : xsec == URCHIN_XSEC_HEII       ? sigma_hydrogenic(Ec, 2.0)
+                         : xsec == URCHIN_XSEC_POWERLAW   ? sigma_powerlaw(Ec)
+                                                          : sigma_verner(Ec);
+        s_out[j] = sig / sth;
+    }
     return URCHIN_OK;
 }

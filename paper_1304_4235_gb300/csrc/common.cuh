@@ -208,6 +208,9 @@ int ray_order(const urchin_bvh* bvh, const int32_t* items, int64_t n_items, cons
 int launch_wbar(const void* tau, int precision, int64_t n_rays, const double* lc, const double* sg, const double* s,
                 int F, double* w_bar, cudaStream_t st);
 
+// A spectrum with helium cross sections (urchin_gamma_he, plain urchin_solve)
+inline bool spectrum_has_he(const urchin_spectrum* sp) { return sp && (sp->s_he1 || sp->s_he2); }
+
 // Table of ln sum_b w_b exp(-s_b tau) on u = ln(1 + tau) for the
 // polychromatic slab (spectral_device.cuh, SpecTable): kSpecTab intervals
 // up to tau = kSpecTauMax; tab needs kSpecTab + 1 double2 (value, d/du).

@@ -121,10 +121,20 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs A)
     Real* e2 = reinterpret_cast<Real*>(smem_raw);
     Real* wn = e2 + A.F;
     Real* sj = wn + A.F;
-    Real* lk = reinterpret_cast<Real*>(smem_raw + ((3 * (size_t)A.F * sizeof(Real) + 15) & ~size_t(15)));
+    Real* sh1 = sj + A.F;                       // helium cross sections (A.he)
+    Real* sh2 = sh1 + A.F;
+    const int narr = A.he ? 5 : 3;
+    Real* lk = reinterpret_cast<Real*>(smem_raw + ((narr * (size_t)A.F * sizeof(Real) + 15) & ~size_t(15)));
     Real* lk2 = lk + kSweepThreads;
     __shared__ double sh[2];
-    sweep_spectrum<Real>(A.s, A.w, A.F, e2, A.want_tangent ? sj : nullptr, wn, sh);
+    sweep_spectrum<Real>(A.s, A.w, A.F, e2, (A.want_tangent || A.he) ? sj : nullptr, wn, sh);
+    if (A.he) {
+        for (int j = threadIdx.x; j < A.F; j += blockDim.x) {
+            sh1[j] = (Real)A.s_he1[j];
+            sh2[j] = (Real)A.s_he2[j];
+        }
+        __syncthreads();
+    }
     const int rows_per_block = kSweepThreads / A.R;
     const int local = threadIdx.x / A.R;
     const int k = threadIdx.x % A.R;
@@ -140,7 +150,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs A)
             const Real tau = static_cast<const Real*>(A.tau)[row + (int64_t)k * A.k_stride];
             Real S = Real(0), c = Real(0), S2 = Real(0), c2 = Real(0);
             // (near/far: tau is the far column; the slab of near particles is applied below)
-            const int nspec = A.near_far == URCHIN_SLAB_SPECTRUM ? 0 : A.F;
+            const int nspec = (A.near_far == URCHIN_SLAB_SPECTRUM || A.he) ? 0 : A.F;
             for (int j = 0; j < nspec; ++j) {
                 const Real v = wn[j] * exp2_p(-e2[j] * tau);
                 const Real yy = v - c;
@@ -157,6 +167,27 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs A)
             }
             // ln(Gamma_k / Gamma_thin) = -s_min tau_k + ln S_k
             Real lkv = nspec ? -smin * tau + log_p(S) : Real(0);
+            if (A.he) {
+                // H I, He I and He II columns: E_j = s_j tau + s1_j tau1 + s2_j tau2, the
+                // smallest E_j factored out of the sum
+                const int32_t ir = A.items ? A.items[row] : (int32_t)row;
+                const Real t1 = static_cast<const Real*>(A.tau_he1)[ir + (int64_t)k * A.near_k_stride];
+                const Real t2 = static_cast<const Real*>(A.tau_he2)[ir + (int64_t)k * A.near_k_stride];
+                Real emin = sj[0] * tau + sh1[0] * t1 + sh2[0] * t2;
+                for (int j = 1; j < A.F; ++j) {
+                    const Real e = sj[j] * tau + sh1[j] * t1 + sh2[j] * t2;
+                    emin = e < emin ? e : emin;
+                }
+                Real Sh = Real(0), ch = Real(0);
+                for (int j = 0; j < A.F; ++j) {
+                    const Real v = wn[j] * exp_p(emin - (sj[j] * tau + sh1[j] * t1 + sh2[j] * t2));
+                    const Real yy = v - ch;
+                    const Real t = Sh + yy;
+                    ch = (t - Sh) - yy;
+                    Sh = t;
+                }
+                lkv = -emin + log_p(Sh);
+            }
             if (A.near_far) {
                 // Eq. gammashldk: the far radiation enters the slab of near particles, in
                 // the particle's recombination case before this sweep
@@ -568,7 +599,7 @@ int launch_sweep(const SweepArgs& A, cudaStream_t s)
 {
     if (A.n_items <= 0) return URCHIN_OK;
     const size_t rsz = A.precision == URCHIN_F64 ? sizeof(double) : sizeof(float);
-    size_t smem = ((3 * (size_t)A.F * rsz + 15) & ~size_t(15)) + 2 * rsz * kSweepThreads;
+    size_t smem = (((A.he ? 5 : 3) * (size_t)A.F * rsz + 15) & ~size_t(15)) + 2 * rsz * kSweepThreads;
     const void* fn = A.precision == URCHIN_F64 ? (const void*)k_sweep<double> : (const void*)k_sweep<float>;
     if (smem > 48 * 1024)
         URCHIN_TRY_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -609,6 +640,9 @@ int Solver::init(const urchin_bvh* bvh_, const urchin_solve_params* P_, double* 
     size_t o_tau = lay.take(rsz * (size_t)rays);
     size_t o_tn = lay.take(P.near_far ? rsz * (size_t)rays : 0);
     size_t o_pt = lay.take(P.near_far == URCHIN_SLAB_SPECTRUM ? sizeof(double2) * (kSpecTab + 1) + 64 : 0);
+    const bool he = spectrum_has_he(&P.spectrum);
+    size_t o_h1 = lay.take(he ? rsz * (size_t)rays : 0);
+    size_t o_h2 = lay.take(he ? rsz * (size_t)rays : 0);
     size_t o_comp = lay.take(compact_tmp_bytes(n));
     size_t o_cnt = lay.take(may_store ? sizeof(uint32_t) * (size_t)rays : 0);
     size_t o_rp = lay.take(may_store ? sizeof(uint64_t) * (size_t)(rays + 1) : 0);
@@ -635,6 +669,8 @@ int Solver::init(const urchin_bvh* bvh_, const urchin_solve_params* P_, double* 
     list = scr.at<int32_t>(o_list);
     tau = scr.at<void>(o_tau);
     tau_near = P.near_far ? scr.at<void>(o_tn) : nullptr;
+    tau_he1 = he ? scr.at<void>(o_h1) : nullptr;
+    tau_he2 = he ? scr.at<void>(o_h2) : nullptr;
     if (P.near_far == URCHIN_SLAB_SPECTRUM) {
         double2* tab = scr.at<double2>(o_pt);
         double* smin = reinterpret_cast<double*>(tab + kSpecTab + 1);
@@ -969,6 +1005,11 @@ SweepArgs Solver::sweep_args(const int32_t* items, int64_t n_items, int sweep0)
     A.tau_near = tau_near;
     A.near_k_stride = n;
     A.poly = poly;
+    A.he = tau_he1 ? 1 : 0;
+    A.tau_he1 = tau_he1;
+    A.tau_he2 = tau_he2;
+    A.s_he1 = P.spectrum.s_he1;
+    A.s_he2 = P.spectrum.s_he2;
     return A;
 }
 
@@ -1065,8 +1106,48 @@ int Solver::order_by_density()
     return URCHIN_OK;
 }
 
+// The fixed helium columns of every ray (all particles, [i + k n]): one
+// traversal per species with tracer weights A_j he_j (the columns are linear
+// in the weights; the helium fractions do not change during the solve).
+int Solver::he_columns()
+{
+    if (!tau_he1) return URCHIN_OK;
+    const size_t rsz = f64 ? sizeof(double) : sizeof(float);
+    Scratch wt;
+    URCHIN_TRY(wt.alloc(rsz * (size_t)n, s));
+    float* hw32 = f64 ? nullptr : wt.at<float>(0);
+    double* hw64 = f64 ? wt.at<double>(0) : nullptr;
+    const double* src[2] = {P.he1, P.he2};
+    void* dst[2] = {tau_he1, tau_he2};
+    for (int q = 0; q < 2; ++q) {
+        URCHIN_TRY(launch_weights(bvh, src[q], hw32, hw64, s));
+        TraceJob job{};
+        job.bvh = bvh;
+        job.w32 = hw32;
+        job.w64 = hw64;
+        job.dirs_dev = dirs;
+        job.R = P.R;
+        job.l_ray = P.l_ray;
+        job.items = nullptr;
+        job.n_items = n;
+        job.row_stride = 1;
+        job.k_stride = n;
+        job.out_row = nullptr;
+        job.out = dst[q];
+        job.kernel = P.kernel;
+        job.precision = P.precision;
+        job.mode = 0;
+        URCHIN_TRY(order_for(nullptr, n, &job.order));
+        URCHIN_TRY(timed_trace(job));
+        stats.traversals += 1;
+    }
+    wt.release();
+    return URCHIN_OK;
+}
+
 int Solver::plain()
 {
+    URCHIN_TRY(he_columns());
     URCHIN_TRY(first_sweep());
     if (stats.max_rel_dx < P.tol) {
         stats.converged = 1;
@@ -1710,6 +1791,7 @@ extern "C" int urchin_tangent(const urchin_bvh* bvh, const urchin_solve_params* 
     if (P->case_rule != URCHIN_CASE_A && P->case_rule != URCHIN_CASE_B && P->case_rule != URCHIN_CASE_AUTO)
         return set_error(URCHIN_ERR_ARG, "urchin_tangent: unknown case_rule");
     if (P->near_far) return set_error(URCHIN_ERR_ARG, "urchin_tangent: no tangent of the near/far split");
+    if (spectrum_has_he(&P->spectrum)) return set_error(URCHIN_ERR_ARG, "urchin_tangent: no helium in the tangent");
     urchin_solve_params Q = *P;
     Q.warm_start = 1;
     Q.segments = URCHIN_SEG_RECOMPUTE;
@@ -1756,6 +1838,8 @@ int check_solve_params(const char* fn, const urchin_bvh* bvh, const urchin_solve
         return set_error(URCHIN_ERR_ARG, "%s: unknown segments mode", fn);
     if (!std::isfinite(P->newton_eta) || !(P->newton_eta < 1.0))
         return set_error(URCHIN_ERR_ARG, "%s: newton_eta must be finite and < 1", fn);
+    if (spectrum_has_he(&P->spectrum) && (!P->spectrum.s_he1 || !P->spectrum.s_he2 || !P->he1 || !P->he2))
+        return set_error(URCHIN_ERR_ARG, "%s: helium needs spectrum s_he1 and s_he2 and params he1 and he2", fn);
     return URCHIN_OK;
 }
 
@@ -1776,6 +1860,8 @@ extern "C" int urchin_solve(const urchin_bvh* bvh, const urchin_solve_params* P,
         return set_error(URCHIN_ERR_ARG, "urchin_solve: near_far must be 0, URCHIN_SLAB_THRESHOLD or URCHIN_SLAB_SPECTRUM");
     if (P->near_far && (P->method != URCHIN_METHOD_PLAIN || P->blocks > 1 || P->y != 0.0))
         return set_error(URCHIN_ERR_ARG, "urchin_solve: the near/far split needs the plain Jacobi method and y = 0");
+    if (spectrum_has_he(&P->spectrum) && (P->method != URCHIN_METHOD_PLAIN || P->blocks > 1 || P->near_far))
+        return set_error(URCHIN_ERR_ARG, "urchin_solve: helium needs the plain Jacobi method without near/far split");
     cudaStream_t s = (cudaStream_t)stream;
     Solver S;
     int st = S.init(bvh, P, x_inout, s);
@@ -1808,6 +1894,7 @@ extern "C" int urchin_solve_vjp(const urchin_bvh* bvh, const urchin_solve_params
     if (!x_bar || !w_bar || !P->state)
         return set_error(URCHIN_ERR_ARG, "urchin_solve_vjp: NULL x_bar, w_bar or params->state");
     if (P->near_far) return set_error(URCHIN_ERR_ARG, "urchin_solve_vjp: no adjoint of the near/far split");
+    if (spectrum_has_he(&P->spectrum)) return set_error(URCHIN_ERR_ARG, "urchin_solve_vjp: no helium in reverse mode");
     if (P->gmres_m < 1 || P->gmres_m > 64)
         return set_error(URCHIN_ERR_ARG, "urchin_solve_vjp: gmres_m must be in [1, 64]");
     urchin_solve_params Q = *P;

@@ -48,6 +48,11 @@ struct SweepArgs {
     const void* tau_near;      //   columns (x = 1) are at tau_near[i + k * near_k_stride]
     int64_t near_k_stride;     //   (i the Morton slot) and enter through the slab solution
     SpecTable poly;            // near_far == URCHIN_SLAB_SPECTRUM: ln Gamma_spec(tau) table
+    int he;                    // helium: fixed columns tau_he1/2[i + k * near_k_stride] (Morton
+    const void* tau_he1;       //   slot i) attenuate the bins with the cross sections s_he1/2
+    const void* tau_he2;
+    const double* s_he1;
+    const double* s_he2;
     int want_tangent;          // Newton: keep x, emit E and tangent factors
     double* ctan;              // [n_items * R] (k-major, stride k_stride)
     double* xeq_out;           // [n_items]
@@ -83,6 +88,9 @@ struct Solver {
     void* tau = nullptr;
     void* tau_near = nullptr;                    // near/far: [R * n] near columns, Morton slot + k n
     SpecTable poly{nullptr, 0, 0.0, 0.0};        // near/far with the polychromatic slab
+    void* tau_he1 = nullptr;                     // helium: [R * n] fixed columns, Morton slot + k n
+    void* tau_he2 = nullptr;
+    int he_columns();
     void* comp_tmp = nullptr;
     unsigned long long* hits = nullptr;          // misc[3..5], counted when P.profile
     std::vector<cudaEvent_t> events;             // start/stop pairs of each timed launch

@@ -340,6 +340,58 @@ __global__ void k_spec_table(const double* __restrict__ sv, const double* __rest
     }
 }
 
+// Rate behind H I, He I and He II columns, one thread per origin in double:
+// per ray E_j = s_j tau + s1_j tau1 + s2_j tau2, ln sum_j w^_j exp(-E_j) with
+// the smallest E_j factored out, then a log-sum-exp over the rays.
+template <typename Real>
+__global__ void k_gamma_he(const Real* __restrict__ t0, const Real* __restrict__ t1, const Real* __restrict__ t2,
+                           int64_t n_orig, int R, const double* __restrict__ sv, const double* __restrict__ s1v,
+                           const double* __restrict__ s2v, const double* __restrict__ wv, int F, double* gamma_out,
+                           float* tau_eff_out)
+{
+    extern __shared__ double sm[];
+    double* ss = sm;
+    double* s1 = sm + F;
+    double* s2 = sm + 2 * F;
+    double* ws = sm + 3 * F;
+    __shared__ double gsh;
+    if (threadIdx.x == 0) {
+        double g = 0.0;
+        for (int b = 0; b < F; ++b) g += wv[b];
+        gsh = g;
+    }
+    __syncthreads();
+    const double gthin = gsh;
+    for (int b = threadIdx.x; b < F; b += blockDim.x) {
+        ss[b] = sv[b];
+        s1[b] = s1v[b];
+        s2[b] = s2v[b];
+        ws[b] = wv[b] / gthin;
+    }
+    __syncthreads();
+    for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < n_orig; o += (int64_t)gridDim.x * blockDim.x) {
+        double m = -INFINITY, acc = 0.0;
+        for (int k = 0; k < R; ++k) {
+            const double a = (double)t0[o * R + k], b1 = (double)t1[o * R + k], b2 = (double)t2[o * R + k];
+            double emin = INFINITY;
+            for (int b = 0; b < F; ++b) emin = fmin(emin, ss[b] * a + s1[b] * b1 + s2[b] * b2);
+            double S = 0.0;
+            for (int b = 0; b < F; ++b) S += ws[b] * exp(-(ss[b] * a + s1[b] * b1 + s2[b] * b2 - emin));
+            const double l = -emin + log(S);
+            if (!(l > -INFINITY)) continue;
+            if (l > m) {
+                acc = acc * exp(m - l) + 1.0;
+                m = l;
+            } else {
+                acc += exp(l - m);
+            }
+        }
+        const double lr = m + log(acc / (double)R);
+        gamma_out[o] = gthin * exp(lr);
+        if (tau_eff_out) tau_eff_out[o] = (float)(-lr);
+    }
+}
+
 template <typename Real>
 int gamma_vjp_t(const Real* tau, int64_t n_orig, int R, const urchin_spectrum* sp, const double* gbar,
                 Real* tau_bar, double* w_bar, cudaStream_t s)
@@ -435,6 +487,7 @@ extern "C" int urchin_gamma(const void* tau, int precision, int64_t n_orig, int 
     if (!sp || !sp->s || !sp->w) return set_error(URCHIN_ERR_ARG, "urchin_gamma: NULL spectrum");
     if (sp->F < 1 || sp->F > URCHIN_MAX_BINS)
         return set_error(URCHIN_ERR_ARG, "urchin_gamma: F = %d out of range [1, %d]", sp->F, URCHIN_MAX_BINS);
+    if (spectrum_has_he(sp)) return set_error(URCHIN_ERR_ARG, "urchin_gamma: helium spectrum (use urchin_gamma_he)");
     if (n_orig == 0) return URCHIN_OK;
     if (!tau || !gamma_out) return set_error(URCHIN_ERR_ARG, "urchin_gamma: NULL tau or gamma_out");
     GammaJob J{};
@@ -480,6 +533,7 @@ extern "C" int urchin_gamma_vjp(const void* tau, int precision, int64_t n_orig, 
     if (!sp || !sp->s || !sp->w) return set_error(URCHIN_ERR_ARG, "urchin_gamma_vjp: NULL spectrum");
     if (sp->F < 1 || sp->F > URCHIN_MAX_BINS)
         return set_error(URCHIN_ERR_ARG, "urchin_gamma_vjp: F = %d out of range [1, %d]", sp->F, URCHIN_MAX_BINS);
+    if (spectrum_has_he(sp)) return set_error(URCHIN_ERR_ARG, "urchin_gamma_vjp: no helium columns in reverse mode");
     if (n_orig == 0) return URCHIN_OK;
     if (!tau || !gamma_bar) return set_error(URCHIN_ERR_ARG, "urchin_gamma_vjp: NULL tau or gamma_bar");
     if (!tau_bar_out && !w_bar) return set_error(URCHIN_ERR_ARG, "urchin_gamma_vjp: no output requested");
@@ -529,6 +583,7 @@ extern "C" int urchin_gamma_nearfar(const void* tau_far, const void* tau_near, i
     if (n_orig == 0) return URCHIN_OK;
     if (slab != URCHIN_SLAB_THRESHOLD && slab != URCHIN_SLAB_SPECTRUM)
         return set_error(URCHIN_ERR_ARG, "urchin_gamma_nearfar: unknown slab model %d", slab);
+    if (spectrum_has_he(sp)) return set_error(URCHIN_ERR_ARG, "urchin_gamma_nearfar: the slab is hydrogen only");
     if (!tau_far || !tau_near || !nH || !T || !gamma_out)
         return set_error(URCHIN_ERR_ARG, "urchin_gamma_nearfar: NULL tau_far, tau_near, nH, T or gamma_out");
     cudaStream_t s = (cudaStream_t)stream;
@@ -565,4 +620,42 @@ extern "C" int urchin_gamma_nearfar(const void* tau_far, const void* tau_near, i
     URCHIN_TRY(launched());
     tb.release();
     return URCHIN_OK;
+}
+
+extern "C" int urchin_gamma_he(const void* tau, const void* tau_he1, const void* tau_he2, int precision,
+                               int64_t n_orig, int R, const urchin_spectrum* sp, double* gamma_out,
+                               float* tau_eff_out, urchin_stream_t stream)
+{
+    using namespace urchin;
+    clear_error();
+    if (precision != URCHIN_F32 && precision != URCHIN_F64)
+        return set_error(URCHIN_ERR_ARG, "urchin_gamma_he: unknown precision %d", precision);
+    if (R < 1 || R > URCHIN_MAX_RAYS) return set_error(URCHIN_ERR_ARG, "urchin_gamma_he: R = %d out of range", R);
+    if (n_orig < 0) return set_error(URCHIN_ERR_ARG, "urchin_gamma_he: n_orig < 0");
+    if (!sp || !sp->s || !sp->w || !sp->s_he1 || !sp->s_he2)
+        return set_error(URCHIN_ERR_ARG, "urchin_gamma_he: the spectrum needs s, w, s_he1 and s_he2");
+    if (sp->F < 1 || sp->F > URCHIN_MAX_BINS)
+        return set_error(URCHIN_ERR_ARG, "urchin_gamma_he: F = %d out of range [1, %d]", sp->F, URCHIN_MAX_BINS);
+    if (n_orig == 0) return URCHIN_OK;
+    if (!tau || !tau_he1 || !tau_he2 || !gamma_out)
+        return set_error(URCHIN_ERR_ARG, "urchin_gamma_he: NULL column or gamma_out");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t smem = sizeof(double) * 4 * (size_t)sp->F;
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n_orig + 127) / 128, 4096));
+    if (precision == URCHIN_F64) {
+        if (smem > 48 * 1024)
+            URCHIN_TRY_CUDA(cudaFuncSetAttribute(k_gamma_he<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)smem));
+        k_gamma_he<double><<<grid, 128, smem, s>>>(static_cast<const double*>(tau), static_cast<const double*>(tau_he1),
+                                                   static_cast<const double*>(tau_he2), n_orig, R, sp->s, sp->s_he1,
+                                                   sp->s_he2, sp->w, sp->F, gamma_out, tau_eff_out);
+    } else {
+        if (smem > 48 * 1024)
+            URCHIN_TRY_CUDA(cudaFuncSetAttribute(k_gamma_he<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)smem));
+        k_gamma_he<float><<<grid, 128, smem, s>>>(static_cast<const float*>(tau), static_cast<const float*>(tau_he1),
+                                                  static_cast<const float*>(tau_he2), n_orig, R, sp->s, sp->s_he1,
+                                                  sp->s_he2, sp->w, sp->F, gamma_out, tau_eff_out);
+    }
+    return launched();
 }

@@ -27,7 +27,7 @@ URCHIN_ERR_NONFINITE = -5
 KERNEL_M4, KERNEL_GT = 0, 1
 F32, F64 = 0, 1
 CASE_A, CASE_B, CASE_AUTO = 0, 1, 2
-XSEC_VERNER, XSEC_HYDROGENIC, XSEC_POWERLAW = 0, 1, 2
+XSEC_VERNER, XSEC_HYDROGENIC, XSEC_POWERLAW, XSEC_HEII = 0, 1, 2, 3
 METHOD_PLAIN, METHOD_NEWTON, METHOD_ANDERSON = 0, 1, 2
 SLAB_THRESHOLD, SLAB_SPECTRUM = 1, 2
 SEG_RECOMPUTE, SEG_STORE, SEG_AUTO = 0, 1, 2
@@ -47,7 +47,7 @@ class urchin_box(C.Structure):
 
 
 class urchin_spectrum(C.Structure):
-    _fields_ = [("F", C.c_int), ("s", _vp), ("w", _vp)]
+    _fields_ = [("F", C.c_int), ("s", _vp), ("w", _vp), ("s_he1", _vp), ("s_he2", _vp)]
 
 
 class urchin_solve_params(C.Structure):
@@ -58,7 +58,7 @@ class urchin_solve_params(C.Structure):
                 ("kernel", C.c_int), ("precision", C.c_int), ("case_rule", C.c_int),
                 ("warm_start", C.c_int), ("profile", C.c_int), ("history_maxrel", _vp),
                 ("history_unconverged", _vp), ("blocks", C.c_int), ("newton_switch", C.c_double),
-                ("newton_eta", C.c_double), ("state", _vp), ("near_far", C.c_int)]
+                ("newton_eta", C.c_double), ("state", _vp), ("he1", _vp), ("he2", _vp), ("near_far", C.c_int)]
 
 
 class urchin_solve_stats(C.Structure):
@@ -110,6 +110,9 @@ SIGNATURES = {
     "urchin_equilibrium_vjp": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int64, C.c_int, C.c_double, _vp, _vp, _vp]),
     "urchin_solve_vjp": (C.c_int, [_vp, C.POINTER(urchin_solve_params), _vp, _vp, _vp,
                                    C.POINTER(urchin_solve_stats), _vp]),
+    "urchin_gamma_he": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_int64, C.c_int, C.POINTER(urchin_spectrum),
+                                  _vp, _vp, _vp]),
+    "urchin_cross_section_ratio": (C.c_int, [C.c_int, _vp, C.c_int, _vp]),
     "urchin_trace_columns_nearfar": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_double, _vp, C.c_int64,
                                                C.c_int, C.c_int, _vp, _vp, _vp]),
     "urchin_gamma_nearfar": (C.c_int, [_vp, _vp, C.c_int, C.c_int64, C.c_int, C.POINTER(urchin_spectrum),
@@ -198,6 +201,15 @@ def urchin_spectrum_weights(edges, J, gamma_thin: float, xsec: int = XSEC_VERNER
                                           int(xsec), float(gamma_thin), s.ctypes.data_as(_vp),
                                           w.ctypes.data_as(_vp)))
     return s, w
+
+
+def urchin_cross_section_ratio(edges, xsec: int) -> np.ndarray:
+    """sigma(E_j) / sigma_th at the geometric bin centres (XSEC_HEII: He II)."""
+    edges = _host(edges)
+    F = edges.shape[0] - 1
+    out = np.zeros(F)
+    _check(load().urchin_cross_section_ratio(F, edges.ctypes.data_as(_vp), int(xsec), out.ctypes.data_as(_vp)))
+    return out
 
 
 class Bvh:
@@ -306,6 +318,20 @@ def urchin_gamma_nearfar(tau_far, tau_near, s, w, nH, T, caseB=None, slab: int =
     return g, te
 
 
+def urchin_gamma_he(tau, tau_he1, tau_he2, s, w, s_he1, s_he2, stream=None):
+    """(Gamma float64, tau_eff float32) behind H I, He I and He II columns."""
+    import torch
+    precision = F64 if tau.dtype == torch.float64 else F32
+    n_orig, R = tau.shape
+    sp = urchin_spectrum(int(s.numel()), _dev(s, torch.float64), _dev(w, torch.float64),
+                         _dev(s_he1, torch.float64), _dev(s_he2, torch.float64))
+    g = torch.empty(n_orig, dtype=torch.float64, device=tau.device)
+    te = torch.empty(n_orig, dtype=torch.float32, device=tau.device)
+    _check(load().urchin_gamma_he(_dev(tau), _dev(tau_he1, tau.dtype), _dev(tau_he2, tau.dtype), int(precision),
+                                  n_orig, R, C.byref(sp), _dev(g), _dev(te), _stream(stream)))
+    return g, te
+
+
 def urchin_gamma(tau, s, w, precision: int = None, stream=None):
     """Gamma (float64) and tau_eff (float32) per row of tau [n_orig, R]."""
     import torch
@@ -336,10 +362,12 @@ def urchin_solve(bvh: Bvh, dirs, l_ray: float, s, w, nH, T, x=None, *, y: float 
                  kernel: int = KERNEL_M4, precision: int = F32, case_rule: int = CASE_AUTO,
                  warm_start: bool = False, profile: bool = False, raise_not_converged: bool = True,
                  history: bool = False, blocks: int = 1, newton_switch: float = 0.01, newton_eta: float = 0.0,
-                 state=None, near_far: int = 0, stream=None):
+                 state=None, near_far: int = 0, s_he1=None, s_he2=None, he1=None, he2=None, stream=None):
     """Returns (x, stats dict).  x (float64 CUDA tensor, original order) is
     updated in place when given.  `state` (uint8 CUDA tensor [n]) receives
-    each particle's final case / frozen flags for urchin_solve_vjp."""
+    each particle's final case / frozen flags for urchin_solve_vjp.  Helium:
+    s_he1 / s_he2 (bin cross sections / sigma_th) with he1 / he2 (He I / He II
+    atoms per H atom of each particle)."""
     import torch
     dirs = _host(dirs).reshape(-1, 3)
     if x is None:
@@ -348,7 +376,10 @@ def urchin_solve(bvh: Bvh, dirs, l_ray: float, s, w, nH, T, x=None, *, y: float 
     P.R = dirs.shape[0]
     P.dirs = dirs.ctypes.data_as(_vp)
     P.l_ray = float(l_ray)
-    P.spectrum = urchin_spectrum(int(s.numel()), _dev(s, torch.float64), _dev(w, torch.float64))
+    P.spectrum = urchin_spectrum(int(s.numel()), _dev(s, torch.float64), _dev(w, torch.float64),
+                                 _dev(s_he1, torch.float64), _dev(s_he2, torch.float64))
+    P.he1 = _dev(he1, torch.float64)
+    P.he2 = _dev(he2, torch.float64)
     P.nH = _dev(nH, torch.float64)
     P.T = _dev(T, torch.float64)
     P.y = float(y)

@@ -65,6 +65,20 @@ def _err(fn, *args):
     return rc, U.load().urchin_last_error().decode()
 
 
+def test_heii_cross_section_is_hydrogenic_with_charge_two():
+    """URCHIN_XSEC_HEII: the exact hydrogenic form with Z = 2 (threshold
+    54.4 eV), against the oracle's hydrogenic cross section."""
+    edges = np.exp(np.linspace(np.log(13.6), np.log(136.0), 201))
+    got = U.urchin_cross_section_ratio(edges, U.XSEC_HEII)
+    Ec = np.sqrt(edges[:-1] * edges[1:])
+    ref = np.array([O.sigma_hydrogenic(E, 2.0) for E in Ec]).ravel() / O.sigma_th()
+    np.testing.assert_allclose(got, ref, rtol=1e-12, atol=0)
+    assert got[Ec < 54.4].max() == 0.0 and got[Ec > 55].min() > 0.0
+    hi = U.urchin_cross_section_ratio(edges, U.XSEC_HYDROGENIC)
+    ref1 = np.array([O.sigma_hydrogenic(E, 1.0) for E in Ec]).ravel() / O.sigma_th()
+    np.testing.assert_allclose(hi, ref1, rtol=1e-12, atol=0)
+
+
 def test_host_argument_errors():
     lib = U.load()
     rc, msg = _err(lib.urchin_healpix_dirs, 0, None)

@@ -1,0 +1,111 @@
+"""Helium columns on the GPU against the oracle (not in the paper, which
+treats hydrogen only: fixed He I and He II columns attenuate the spectrum).
+The He II cross section is the exact hydrogenic one with Z = 2; He I has
+no fit in the paper, so these tests use a stand-in shape (zero below
+24.59 eV, 1.2 (24.59 eV / E)^2 of sigma_th above), which only has to be the
+same on both sides.  Tolerances: rate on identical inputs rel 1e-12 (FP64),
+solver step-matched FP64 rel 1e-9, FP32 99.9 % rel 1e-4."""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from gpu_helpers import build, rel_err
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1304_4235_gb300 import urchin as U  # noqa: E402
+
+
+def _he_spectrum(w, e_hi=136.0, F=None):
+    F = F or w.F
+    edges = np.exp(np.linspace(np.log(13.6), np.log(e_hi), F + 1))
+    centres = np.sqrt(edges[:-1] * edges[1:])
+    J = (centres / 13.6) ** -1.5
+    s, wts = U.urchin_spectrum_weights(edges, J, w.gamma_thin)
+    s2 = U.urchin_cross_section_ratio(edges, U.XSEC_HEII)
+    s1 = np.where(centres >= 24.59, 1.2 * (24.59 / centres) ** 2, 0.0)
+    return s, wts, s1, s2
+
+
+def _he_fractions(w, seed):
+    rng = np.random.default_rng(seed)
+    y = 0.079                                     # n_He / n_H for X = 0.76
+    f1 = rng.uniform(0.0, 0.3, w.n)               # He I fraction
+    f2 = rng.uniform(0.0, 0.5, w.n) * (1 - f1)    # He II fraction
+    return y * f1, y * f2
+
+
+def test_gamma_he_matches_oracle():
+    rng = np.random.default_rng(4)
+    w = W.halo(n=10, seed=1, F=120)
+    s, wts, s1, s2 = _he_spectrum(w)
+    tau = np.exp(rng.uniform(np.log(1e-4), np.log(60.0), (600, 12)))
+    t1 = np.exp(rng.uniform(np.log(1e-4), np.log(20.0), (600, 12)))
+    t2 = np.exp(rng.uniform(np.log(1e-4), np.log(20.0), (600, 12)))
+    c = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    g, te = U.urchin_gamma_he(c(tau), c(t1), c(t2), c(s), c(wts), c(s1), c(s2))
+    go, teo = O.gamma_he(tau, t1, t2, s, s1, s2, wts)
+    assert rel_err(g.cpu().numpy(), go).max() < 1e-12
+    # a helium spectrum is refused by the hydrogen-only rate
+    with pytest.raises(U.UrchinError):
+        sp = U.urchin_spectrum(int(s.size), U._dev(c(s)), U._dev(c(wts)), U._dev(c(s1)), U._dev(c(s2)))
+        U._check(U.load().urchin_gamma(U._dev(c(tau)), U.F64, 600, 12, U.C.byref(sp), U._dev(c(tau[:, 0])), None,
+                                       None))
+
+
+@pytest.mark.parametrize("precision", [U.F64, U.F32])
+def test_solve_with_helium_step_matched(precision):
+    w = W.halo(n=2000, seed=9, n0=0.3, F=60)
+    bvh, d = build(w, torch)
+    s, wts, s1, s2 = _he_spectrum(w)
+    he1, he2 = _he_fractions(w, 5)
+    c = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    dirs = O.healpix(1)
+    he = dict(tau1=O.columns(w, he1, dirs), tau2=O.columns(w, he2, dirs), s1=s1, s2=s2)
+    for sweeps in (1, 3):
+        x, st = U.urchin_solve(bvh, U.urchin_healpix_dirs(1), w.l_ray, c(s), c(wts), d["nH"], d["T"], tol=1e-300,
+                               max_iter=sweeps, precision=precision, raise_not_converged=False, s_he1=c(s1),
+                               s_he2=c(s2), he1=c(he1), he2=c(he2), segments=U.SEG_STORE)
+        xo, fo, so_ = O.solve(w, s, wts, dirs, sweeps=sweeps, he=he)
+        err = rel_err(x.cpu().numpy(), xo)
+        if precision == U.F64:
+            assert err.max() < 1e-9, sweeps
+        else:
+            assert np.quantile(err, 0.999) < 1e-4, sweeps
+    # helium lowers the rate: the solve is at least as neutral as without it
+    xh, sh = U.urchin_solve(bvh, U.urchin_healpix_dirs(1), w.l_ray, c(s), c(wts), d["nH"], d["T"], tol=1e-6,
+                            max_iter=3000, precision=precision, s_he1=c(s1), s_he2=c(s2), he1=c(he1), he2=c(he2))
+    x0, s0 = U.urchin_solve(bvh, U.urchin_healpix_dirs(1), w.l_ray, c(s), c(wts), d["nH"], d["T"], tol=1e-6,
+                            max_iter=3000, precision=precision)
+    assert np.median(xh.cpu().numpy() / x0.cpu().numpy()) >= 1.0
+
+
+def test_lognormal_box_hydrogen_and_helium_columns():
+    """The cosmological-like box with 200 bins over 13.6-136 eV and H I, He I
+    and He II columns, in miniature (32^3 particles, 1 Mpc, 48 rays, periodic):
+    two FP64 sweeps against the oracle at sampled particles."""
+    w = W.lognormal_box(n_side=32, box_kpc=1000.0, e_hi=136.0)
+    bvh, d = build(w, torch)
+    s, wts, s1, s2 = _he_spectrum(w, e_hi=136.0, F=200)
+    he1, he2 = _he_fractions(w, 6)
+    c = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    x1, st1 = U.urchin_solve(bvh, U.urchin_healpix_dirs(2), w.l_ray, c(s), c(wts), d["nH"], d["T"], tol=1e-300,
+                             max_iter=1, precision=U.F64, raise_not_converged=False, s_he1=c(s1), s_he2=c(s2),
+                             he1=c(he1), he2=c(he2))
+    x2, st2 = U.urchin_solve(bvh, U.urchin_healpix_dirs(2), w.l_ray, c(s), c(wts), d["nH"], d["T"], tol=1e-300,
+                             max_iter=2, precision=U.F64, raise_not_converged=False, s_he1=c(s1), s_he2=c(s2),
+                             he1=c(he1), he2=c(he2))
+    x1, x2 = x1.cpu().numpy(), x2.cpu().numpy()
+    org = W.random_origins(w.n, 60, 7)
+    dirs = O.healpix(2)
+    t1, t2 = O.columns(w, he1, dirs, origins=org), O.columns(w, he2, dirs, origins=org)
+    x0 = O.xeq(wts.sum(), w.nH, w.T, 0.0, False)
+    g0, te0 = O.gamma_he(O.columns(w, x0, dirs, origins=org), t1, t2, s, s1, s2, wts)
+    g1, te1 = O.gamma_he(O.columns(w, x1, dirs, origins=org), t1, t2, s, s1, s2, wts)
+    frozen = te0 < 1e-4
+    e1 = O.xeq(g0, w.nH[org], w.T[org], 0.0, te0 >= 1)
+    e2 = O.xeq(g1, w.nH[org], w.T[org], 0.0, (te1 >= 1) | (te0 >= 1))
+    assert rel_err(np.where(frozen, x0[org], e1), x1[org]).max() < 1e-9
+    assert rel_err(np.where(frozen, x1[org], e2), x2[org]).max() < 1e-9
