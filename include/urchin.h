@@ -291,6 +291,18 @@ URCHIN_API int urchin_equilibrium(const double* gamma, const float* tau_eff, con
                        const double* T, int64_t n, int case_rule, double y,
                        double* x_out, urchin_stream_t stream);
 
+/* Time-dependent neutral fraction, App. C3: with Gamma, nH, T and y held
+ * over a step t (seconds), dx/dt = R (x - x_eq)(x - x_+) (Eq. dxdt) has the
+ * closed-form solution
+ *   x(t) = x_eq + (x0 - x_eq)(x_+ - x_eq) F / [(x_+ - x0) + (x0 - x_eq) F],
+ *   F = exp(-(x_+ - x_eq) t / t_rc),  t_rc = 1 / ((alpha + gamma_c) nH),
+ * x_eq the equilibrium of urchin_equilibrium, x_+ the other root.  Arguments
+ * as urchin_equilibrium plus x0 (device [n], the start) and t >= 0; x_out
+ * may alias x0.  Errors: ERR_ARG, ERR_CUDA. */
+URCHIN_API int urchin_evolve(const double* gamma, const float* tau_eff, const double* nH, const double* T,
+                             int64_t n, int case_rule, double y, const double* x0, double t, double* x_out,
+                             urchin_stream_t stream);
+
 typedef struct {
     int             R;            /* rays per particle                         */
     const double*   dirs;         /* host [R*3]                                */

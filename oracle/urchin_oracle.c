@@ -481,6 +481,25 @@ double oracle_xeq(double Gamma, double nH, double T, double y, int caseB)
     return 2.0 * P / (-Q + sqrt(disc));
 }
 
+/* Time-dependent neutral fraction (App. C3): with T, nH, y and Gamma held,
+ * dx/dt = R (x - x_eq)(x - x_+) and
+ *   x(t) = x_eq + (x0 - x_eq)(x_+ - x_eq) F / [(x_+ - x0) + (x0 - x_eq) F],
+ *   F = exp(-(x_+ - x_eq) t / t_rc),  t_rc = 1 / ((alpha + gamma) nH),
+ * x_eq = x_- the physical root (oracle_xeq) and x_+ = P / (R x_-) the other
+ * root (Vieta). */
+double oracle_xt(double Gamma, double nH, double T, double y, int caseB, double x0, double t)
+{
+    double aA, aB, gc;
+    oracle_rates(T, &aA, &aB, &gc);
+    double alpha = caseB ? aB : aA;
+    double R = (gc + alpha) * nH;
+    double P = alpha * nH * (1.0 + y);
+    double xeq = oracle_xeq(Gamma, nH, T, y, caseB);
+    double xp = P / (R * xeq);
+    double F = exp(-(xp - xeq) * t * R);
+    return xeq + (x0 - xeq) * (xp - xeq) * F / ((xp - x0) + (x0 - xeq) * F);
+}
+
 /* d x_- / d Gamma by implicit differentiation of f(x, Gamma) = R x^2 + Q x + P
  * = 0, where only Q depends on Gamma (dQ/dGamma = -1):
  *   dx/dGamma = -(df/dGamma) / (df/dx) = x / (2 R x + Q). */

@@ -392,6 +392,32 @@ __global__ void k_gamma_he(const Real* __restrict__ t0, const Real* __restrict__
     }
 }
 
+// x after time t from x0 with Gamma, nH, T, y held (App. C3): dx/dt =
+// R (x - x_eq)(x - x_+), solved in closed form with d = x_+ - x_eq =
+// sqrt(Q^2 - 4PR) / R (the same non-cancelling discriminant as the root):
+//   x(t) = x_eq + (x0 - x_eq) d F / (d - (x0 - x_eq)(1 - F)),  F = e^{-R d t}.
+__global__ void k_evolve(const double* __restrict__ gamma, const float* __restrict__ tau_eff,
+                         const double* __restrict__ nH, const double* __restrict__ T, int64_t n, int case_rule,
+                         double y, const double* __restrict__ x0, double t, double* x_out)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const Rates r = hg97_rates(T[i]);
+        const bool caseB = case_rule == URCHIN_CASE_B || (case_rule == URCHIN_CASE_AUTO && tau_eff[i] >= 1.0f);
+        const double alpha = caseB ? r.alphaB : r.alphaA;
+        const double G = gamma[i], n_ = nH[i];
+        const double an = alpha * n_;
+        const double Rc = (r.gamma_c + alpha) * n_;
+        const double e = an * y + r.gamma_c * n_ * (1.0 + y);
+        const double sq = sqrt((G + e) * (G + e) + 4.0 * G * an);
+        const double xe = x_equilibrium(G, n_, alpha, r.gamma_c, y);
+        const double d = sq / Rc;
+        const double F = exp(-sq * t);
+        const double omf = -expm1(-sq * t);
+        const double d0 = x0[i] - xe;
+        x_out[i] = xe + d0 * d * F / (d - d0 * omf);
+    }
+}
+
 template <typename Real>
 int gamma_vjp_t(const Real* tau, int64_t n_orig, int R, const urchin_spectrum* sp, const double* gbar,
                 Real* tau_bar, double* w_bar, cudaStream_t s)
@@ -657,5 +683,26 @@ extern "C" int urchin_gamma_he(const void* tau, const void* tau_he1, const void*
                                                   static_cast<const float*>(tau_he2), n_orig, R, sp->s, sp->s_he1,
                                                   sp->s_he2, sp->w, sp->F, gamma_out, tau_eff_out);
     }
+    return launched();
+}
+
+extern "C" int urchin_evolve(const double* gamma, const float* tau_eff, const double* nH, const double* T, int64_t n,
+                             int case_rule, double y, const double* x0, double t, double* x_out,
+                             urchin_stream_t stream)
+{
+    using namespace urchin;
+    clear_error();
+    if (n < 0) return set_error(URCHIN_ERR_ARG, "urchin_evolve: n < 0");
+    if (case_rule != URCHIN_CASE_A && case_rule != URCHIN_CASE_B && case_rule != URCHIN_CASE_AUTO)
+        return set_error(URCHIN_ERR_ARG, "urchin_evolve: unknown case_rule %d", case_rule);
+    if (!(y >= 0.0) || !std::isfinite(y)) return set_error(URCHIN_ERR_ARG, "urchin_evolve: y must be >= 0");
+    if (!(t >= 0.0) || !std::isfinite(t)) return set_error(URCHIN_ERR_ARG, "urchin_evolve: t must be finite and >= 0");
+    if (n == 0) return URCHIN_OK;
+    if (!gamma || !nH || !T || !x0 || !x_out) return set_error(URCHIN_ERR_ARG, "urchin_evolve: NULL array");
+    if (case_rule == URCHIN_CASE_AUTO && !tau_eff)
+        return set_error(URCHIN_ERR_ARG, "urchin_evolve: CASE_AUTO needs tau_eff");
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned grid = (unsigned)std::min<int64_t>((n + 255) / 256, 4096);
+    k_evolve<<<grid, 256, 0, s>>>(gamma, tau_eff, nH, T, n, case_rule, y, x0, t, x_out);
     return launched();
 }

@@ -110,6 +110,7 @@ SIGNATURES = {
     "urchin_equilibrium_vjp": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int64, C.c_int, C.c_double, _vp, _vp, _vp]),
     "urchin_solve_vjp": (C.c_int, [_vp, C.POINTER(urchin_solve_params), _vp, _vp, _vp,
                                    C.POINTER(urchin_solve_stats), _vp]),
+    "urchin_evolve": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int64, C.c_int, C.c_double, _vp, C.c_double, _vp, _vp]),
     "urchin_gamma_he": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_int64, C.c_int, C.POINTER(urchin_spectrum),
                                   _vp, _vp, _vp]),
     "urchin_cross_section_ratio": (C.c_int, [C.c_int, _vp, C.c_int, _vp]),
@@ -353,6 +354,17 @@ def urchin_equilibrium(gamma, tau_eff, nH, T, case_rule: int = CASE_AUTO, y: flo
     _check(load().urchin_equilibrium(_dev(gamma, torch.float64), _dev(tau_eff, torch.float32),
                                      _dev(nH, torch.float64), _dev(T, torch.float64), n,
                                      int(case_rule), float(y), _dev(x), _stream(stream)))
+    return x
+
+
+def urchin_evolve(gamma, tau_eff, nH, T, x0, t: float, case_rule: int = CASE_AUTO, y: float = 0.0, stream=None):
+    """x after time t (s) from x0 at fixed Gamma, nH, T (App. C3)."""
+    import torch
+    n = int(gamma.numel())
+    x = torch.empty(n, dtype=torch.float64, device=gamma.device)
+    _check(load().urchin_evolve(_dev(gamma, torch.float64), _dev(tau_eff, torch.float32), _dev(nH, torch.float64),
+                                _dev(T, torch.float64), n, int(case_rule), float(y), _dev(x0, torch.float64),
+                                float(t), _dev(x), _stream(stream)))
     return x
 
 

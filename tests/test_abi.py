@@ -131,6 +131,8 @@ def test_device_entry_points_reject_bad_arguments_without_gpu_work():
     assert lib.urchin_gamma_vjp(None, 5, 10, 12, C.byref(sp), None, None, None, None) == U.URCHIN_ERR_ARG
     assert lib.urchin_equilibrium_vjp(None, None, None, None, 5, 9, 0.0, None, None, None) == U.URCHIN_ERR_ARG
     assert lib.urchin_equilibrium_vjp(None, None, None, None, 0, 0, 0.0, None, None, None) == U.URCHIN_OK
+    assert lib.urchin_evolve(None, None, None, None, 5, 0, 0.0, None, -1.0, None, None) == U.URCHIN_ERR_ARG
+    assert lib.urchin_evolve(None, None, None, None, 0, 0, 0.0, None, 1.0, None, None) == U.URCHIN_OK
     assert lib.urchin_gamma_vjp(None, 0, 0, 12, C.byref(sp), None, None, None, None) == U.URCHIN_OK
     assert lib.urchin_solve_vjp(None, None, None, None, None, None, None) == U.URCHIN_ERR_ARG
     # zero-size requests are no-ops

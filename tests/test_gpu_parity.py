@@ -220,6 +220,24 @@ def test_equilibrium_matches_oracle(case_rule):
     assert rel_err(x, ref).max() < 1e-12
 
 
+@pytest.mark.parametrize("case_rule", [U.CASE_A, U.CASE_B, U.CASE_AUTO])
+def test_evolve_matches_oracle(case_rule):
+    """Time-dependent x (App. C3) on identical FP64 inputs: rel 1e-12."""
+    rng = np.random.default_rng(12)
+    n = 1500
+    G = np.exp(rng.uniform(np.log(1e-17), np.log(1e-11), n))
+    nH = np.exp(rng.uniform(np.log(1e-5), np.log(10.0), n))
+    T = rng.uniform(5e3, 3e4, n)
+    te = rng.uniform(0, 2, n).astype(np.float32)
+    x0 = np.exp(rng.uniform(np.log(1e-6), 0.0, n))
+    c = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    caseB = {U.CASE_A: np.zeros(n, bool), U.CASE_B: np.ones(n, bool), U.CASE_AUTO: te >= 1}[case_rule]
+    for t in (0.0, 3e12, 3e14, 3e17):
+        x = U.urchin_evolve(c(G), c(te), c(nH), c(T), c(x0), t, case_rule).cpu().numpy()
+        ref = O.xt(G, nH, T, x0, t, 0.0, caseB)
+        assert rel_err(x, ref).max() < 1e-12, t
+
+
 # --------------------------------------------------------------------------
 # iteration driver (Sec. 4)
 # --------------------------------------------------------------------------
