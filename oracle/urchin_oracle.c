@@ -485,19 +485,24 @@ double oracle_xeq(double Gamma, double nH, double T, double y, int caseB)
  * dx/dt = R (x - x_eq)(x - x_+) and
  *   x(t) = x_eq + (x0 - x_eq)(x_+ - x_eq) F / [(x_+ - x0) + (x0 - x_eq) F],
  *   F = exp(-(x_+ - x_eq) t / t_rc),  t_rc = 1 / ((alpha + gamma) nH),
- * x_eq = x_- the physical root (oracle_xeq) and x_+ = P / (R x_-) the other
- * root (Vieta). */
+ * x_eq = x_- the physical root (oracle_xeq).  From Eq. xroots the roots
+ * differ by x_+ - x_- = sqrt(Q^2 - 4PR) / R, taken with the discriminant in
+ * its non-cancelling form (as in oracle_xeq), and x_+ - x0 = (x_+ - x_eq) -
+ * (x0 - x_eq); subtracting the two roots directly loses the difference when
+ * x_+ and x_eq both approach 1 (neutral, cold gas). */
 double oracle_xt(double Gamma, double nH, double T, double y, int caseB, double x0, double t)
 {
     double aA, aB, gc;
     oracle_rates(T, &aA, &aB, &gc);
     double alpha = caseB ? aB : aA;
     double R = (gc + alpha) * nH;
-    double P = alpha * nH * (1.0 + y);
+    double excess = alpha * nH * y + gc * nH * (1.0 + y);
+    double disc = (Gamma + excess) * (Gamma + excess) + 4.0 * Gamma * alpha * nH;
+    double d = sqrt(disc) / R;                     /* x_+ - x_eq */
     double xeq = oracle_xeq(Gamma, nH, T, y, caseB);
-    double xp = P / (R * xeq);
-    double F = exp(-(xp - xeq) * t * R);
-    return xeq + (x0 - xeq) * (xp - xeq) * F / ((xp - x0) + (x0 - xeq) * F);
+    double F = exp(-d * t * R);
+    double d0 = x0 - xeq;
+    return xeq + d0 * d * F / ((d - d0) + d0 * F);
 }
 
 /* d x_- / d Gamma by implicit differentiation of f(x, Gamma) = R x^2 + Q x + P

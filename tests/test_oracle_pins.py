@@ -543,3 +543,29 @@ def test_time_dependent_x_matches_direct_integration():
             assert abs(got - ref) <= 1e-8 * ref, (G, nH, f)
         assert O.xt(G, nH, T, x0, 0.0, y, cb)[0] == pytest.approx(x0, rel=1e-15)
         assert O.xt(G, nH, T, x0, 1e4 * trc, y, cb)[0] == pytest.approx(O.xeq(G, nH, T, y, cb)[0], rel=1e-14)
+
+
+def test_time_dependent_x_against_50_digit_arithmetic():
+    """The closed form evaluated in 50-digit arithmetic from the roots of Eq.
+    xroots (the rate coefficients taken from the oracle): agreement to 1e-11,
+    including neutral, cold gas where x_+ and x_eq both approach 1."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 50
+    rng = np.random.default_rng(12)
+    for _ in range(200):
+        G = float(np.exp(rng.uniform(np.log(1e-18), np.log(1e-11))))
+        nH = float(np.exp(rng.uniform(np.log(1e-5), np.log(10.0))))
+        T = float(rng.uniform(5e3, 3e4))
+        x0 = float(np.exp(rng.uniform(np.log(1e-6), 0.0)))
+        t = float(10 ** rng.uniform(11, 18))
+        aA, aB, gc = O.rates(T)
+        a, g, n_, GG = mp.mpf(aA), mp.mpf(gc), mp.mpf(nH), mp.mpf(G)
+        R = (g + a) * n_
+        Q = -(GG + a * n_ + R)
+        P = a * n_
+        sq = mp.sqrt(Q * Q - 4 * P * R)
+        xm, xp = (-Q - sq) / (2 * R), (-Q + sq) / (2 * R)
+        F = mp.e ** (-(xp - xm) * mp.mpf(t) * R)
+        X0 = mp.mpf(x0)
+        ref = xm + (X0 - xm) * (xp - xm) * F / ((xp - X0) + (X0 - xm) * F)
+        assert abs(O.xt(G, nH, T, x0, t)[0] / float(ref) - 1) < 1e-11
