@@ -486,10 +486,13 @@ double oracle_xeq(double Gamma, double nH, double T, double y, int caseB)
  *   x(t) = x_eq + (x0 - x_eq)(x_+ - x_eq) F / [(x_+ - x0) + (x0 - x_eq) F],
  *   F = exp(-(x_+ - x_eq) t / t_rc),  t_rc = 1 / ((alpha + gamma) nH),
  * x_eq = x_- the physical root (oracle_xeq).  From Eq. xroots the roots
- * differ by x_+ - x_- = sqrt(Q^2 - 4PR) / R, taken with the discriminant in
- * its non-cancelling form (as in oracle_xeq), and x_+ - x0 = (x_+ - x_eq) -
- * (x0 - x_eq); subtracting the two roots directly loses the difference when
- * x_+ and x_eq both approach 1 (neutral, cold gas). */
+ * differ by d = x_+ - x_- = sqrt(Q^2 - 4PR) / R, taken with the
+ * discriminant in its non-cancelling form (as in oracle_xeq); subtracting
+ * the two roots directly loses d when x_+ and x_eq both approach 1
+ * (neutral, cold gas).  The closed form is evaluated over one denominator,
+ *   x(t) = [(1 - F) x_eq (x_+ - x0) + d F x0] / [(x_+ - x0) + (x0 - x_eq) F],
+ * a sum of non-negative terms that gives x0 at t = 0 and x_eq as t -> inf
+ * to rounding (x_eq + (x0 - x_eq) ... loses x0 << x_eq at small t). */
 double oracle_xt(double Gamma, double nH, double T, double y, int caseB, double x0, double t)
 {
     double aA, aB, gc;
@@ -501,8 +504,10 @@ double oracle_xt(double Gamma, double nH, double T, double y, int caseB, double 
     double d = sqrt(disc) / R;                     /* x_+ - x_eq */
     double xeq = oracle_xeq(Gamma, nH, T, y, caseB);
     double F = exp(-d * t * R);
+    double omf = -expm1(-d * t * R);               /* 1 - F */
     double d0 = x0 - xeq;
-    return xeq + d0 * d * F / ((d - d0) + d0 * F);
+    double up = d - d0;                            /* x_+ - x0 */
+    return (omf * xeq * up + d * F * x0) / (up + d0 * F);
 }
 
 /* d x_- / d Gamma by implicit differentiation of f(x, Gamma) = R x^2 + Q x + P

@@ -394,8 +394,10 @@ __global__ void k_gamma_he(const Real* __restrict__ t0, const Real* __restrict__
 
 // x after time t from x0 with Gamma, nH, T, y held (App. C3): dx/dt =
 // R (x - x_eq)(x - x_+), solved in closed form with d = x_+ - x_eq =
-// sqrt(Q^2 - 4PR) / R (the same non-cancelling discriminant as the root):
-//   x(t) = x_eq + (x0 - x_eq) d F / (d - (x0 - x_eq)(1 - F)),  F = e^{-R d t}.
+// sqrt(Q^2 - 4PR) / R (the same non-cancelling discriminant as the root)
+// and F = e^{-R d t}, over one denominator:
+//   x(t) = [(1 - F) x_eq (x_+ - x0) + d F x0] / [(x_+ - x0) + (x0 - x_eq) F],
+// non-negative terms that give x0 at t = 0 and x_eq at t -> inf to rounding.
 __global__ void k_evolve(const double* __restrict__ gamma, const float* __restrict__ tau_eff,
                          const double* __restrict__ nH, const double* __restrict__ T, int64_t n, int case_rule,
                          double y, const double* __restrict__ x0, double t, double* x_out)
@@ -414,7 +416,8 @@ __global__ void k_evolve(const double* __restrict__ gamma, const float* __restri
         const double F = exp(-sq * t);
         const double omf = -expm1(-sq * t);
         const double d0 = x0[i] - xe;
-        x_out[i] = xe + d0 * d * F / (d - d0 * omf);
+        const double up = d - d0;                       // x_+ - x0
+        x_out[i] = (omf * xe * up + d * F * x0[i]) / (up + d0 * F);
     }
 }
 
