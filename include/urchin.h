@@ -296,7 +296,10 @@ URCHIN_API int urchin_equilibrium(const double* gamma, const float* tau_eff, con
  * closed-form solution
  *   x(t) = x_eq + (x0 - x_eq)(x_+ - x_eq) F / [(x_+ - x0) + (x0 - x_eq) F],
  *   F = exp(-(x_+ - x_eq) t / t_rc),  t_rc = 1 / ((alpha + gamma_c) nH),
- * x_eq the equilibrium of urchin_equilibrium, x_+ the other root.  Arguments
+ * x_eq the equilibrium of urchin_equilibrium, x_+ the other root.  It is
+ * evaluated over one denominator, [(1 - F) x_eq (x_+ - x0) + d F x0] /
+ * [(x_+ - x0) + (x0 - x_eq) F] with d = x_+ - x_eq = sqrt(Q^2 - 4PR)/R,
+ * which is exact at t = 0 and t -> inf to rounding.  Arguments
  * as urchin_equilibrium plus x0 (device [n], the start) and t >= 0; x_out
  * may alias x0.  Errors: ERR_ARG, ERR_CUDA. */
 URCHIN_API int urchin_evolve(const double* gamma, const float* tau_eff, const double* nH, const double* T,
