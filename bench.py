@@ -42,8 +42,9 @@ WORKLOAD = "halo_262144_nside1_l200kpc_F100"
 # files at capture time; a changed kernel reports traffic null.
 #   k_spmv: bytes per stored segment read;  k_trace: bytes per ray-sphere hit
 MEASURED_TRAFFIC = {
-    # 65536-particle halo: 2.584e9 DRAM bytes for 3.208e8 segments in one launch
-    "k_spmv": {"77b81bd81f3631b0": 8.055},
+    # 65536-particle halo: 2.5945e9 DRAM bytes for 3.2202e8 segments (rays padded
+    # to multiples of 4) in one launch of the 4-segments-per-lane kernel
+    "k_spmv": {"b44318fd4381a7d4": 8.057},
     "k_trace": {},
 }
 KERNEL_SOURCES = {"k_spmv": ("linalg.cu", "linalg.cuh"),
@@ -345,6 +346,8 @@ def main():
     if spmv_s >= trace_s and spmv_launches > 0:
         per_bytes = spmv_bytes / spmv_launches
         per_s = spmv_s / spmv_launches
+        # 4-byte index + 4-byte value per segment; the per-ray output and
+        # per-particle gather bytes are ~0.1 % of a launch
         seg_per_launch = (spmv_bytes / spmv_launches) / 8.0
         t = MEASURED_TRAFFIC["k_spmv"].get(source_hash("k_spmv"))
         roof = {"bound": "hbm", "achieved": per_bytes / per_s / 1e9, "peak": hbm, "unit": "GB/s",
@@ -445,17 +448,20 @@ def main():
                                 max_iter=args.max_iter, segments=segs, precision=U.F32, state=state,
                                 raise_not_converged=False)
         torch.cuda.synchronize(dev)
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        wb, vs = U.urchin_solve_vjp(bvh, dirs, w.l_ray, s_d, w_d, d["nH"], d["T"], xs, state, 1.0 / xs,
-                                    tol=1e-6, max_iter=600, gmres_m=30, segments=segs, precision=U.F32,
-                                    raise_not_converged=False)
-        b.record(stream)
-        b.synchronize()
-        comp["adjoint"] = {"loss": "sum ln x*", "wall_s": a.elapsed_time(b) * 1e-3, "products": vs["iterations"],
-                           "rel_residual": vs["max_rel_dx"], "converged": bool(vs["converged"]),
-                           "rays": vs["rays"], "grad_norm": float(wb.norm())}
+        # the first call after the forward solve, then the same call again
+        for name in ("adjoint", "adjoint_repeat"):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            wb, vs = U.urchin_solve_vjp(bvh, dirs, w.l_ray, s_d, w_d, d["nH"], d["T"], xs, state, 1.0 / xs,
+                                        tol=1e-6, max_iter=600, gmres_m=30, segments=segs, precision=U.F32,
+                                        raise_not_converged=False, profile=True)
+            b.record(stream)
+            b.synchronize()
+            comp[name] = {"loss": "sum ln x*", "wall_s": a.elapsed_time(b) * 1e-3, "products": vs["iterations"],
+                          "rel_residual": vs["max_rel_dx"], "converged": bool(vs["converged"]),
+                          "rays": vs["rays"], "grad_norm": float(wb.norm()), "trace_s": vs["trace_s"],
+                          "spmv_s": vs["spmv_s"]}
         bvh.close()
         line["compare"] = comp
     if world == 1 and not args.no_cpu_baseline:

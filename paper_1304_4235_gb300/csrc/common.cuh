@@ -144,6 +144,8 @@ constexpr unsigned kStVisit = 32u;      // traversal visit limit (malformed tree
 constexpr unsigned kStSegment = 64u;    // stored-segment fill disagrees with its count
 
 constexpr int kLeafMax = 16;      // subtrees with <= kLeafMax particles become leaves
+constexpr int kSegPad = 4;        // stored rays are padded to a multiple of kSegPad segments (zero
+                                  // values, particle 0) so the SpMV reads 4 segments per lane
 constexpr int kKTab = 2048;       // intervals of the full-chord M4 table in t = b^2/h^2
 
 // Full-chord M4 integral K(t) = int_{-c}^{c} shape(sqrt(t + u^2)) du, c = sqrt(1-t),
@@ -172,7 +174,8 @@ struct TraceJob {
     unsigned long long* hits;     // chord evaluations (may be NULL)
     int mode;                     // 0: columns, 1: count hits per ray, 2: fill segments (+ columns),
                                   // 3: transpose (scatter coef * A_j * chord into xbar)
-    uint32_t* counts;             // mode 1: [R * n_items], index k * n_items + item
+    uint32_t* counts;             // mode 1: [R * n_items], index k * n_items + item: hits rounded
+                                  //    up to a multiple of kSegPad
     const uint64_t* row_ptr;      // mode 2: [R * n_items + 1] offsets of each ray's segments
     int32_t* seg_col;             // mode 2: Morton index of the particle per segment
     void* seg_val;                // mode 2: A_j * chord integral per segment (precision's type)

@@ -9,9 +9,9 @@
 namespace urchin {
 
 struct SpmvArgs {
-    const uint64_t* row_ptr;     // [R * n_rows_per_k + 1]
-    const int32_t* col;          // [nnz] Morton particle index
-    const void* val;             // [nnz] A_j * chord integral (float or double)
+    const uint64_t* row_ptr;     // [R * n_rows_per_k + 1], multiples of kSegPad
+    const int32_t* col;          // [nnz] Morton particle index (padding: 0)
+    const void* val;             // [nnz] A_j * chord integral (float or double; padding: 0)
     const void* xvec;            // [n] vector the columns are linear in (Morton order, same type)
     const int32_t* items;        // [n_items] Morton particle of each evaluated ray origin (NULL = identity)
     int64_t n_items;

@@ -106,6 +106,11 @@ __device__ void sweep_spectrum(const double* s, const double* w, int F, Real* e2
     __syncthreads();
 }
 
+// Instantiations of the sweep: the plain fold, the near/far split (slab of the
+// near particles), the helium columns.  Separate so that the plain sweep keeps
+// the register footprint (and occupancy) of the fold alone.
+constexpr int kSweepPlain = 0, kSweepNearFar = 1, kSweepHelium = 2;
+
 // One sweep's spectral fold + equilibrium update (see file comment).  With
 // want_tangent, also stores per ray c_tk = (1/E) dE/dGamma dGamma/dtau_k for
 // the Newton tangent (in log-safe form).
@@ -114,21 +119,23 @@ __device__ void sweep_spectrum(const double* s, const double* w, int F, Real* e2
 // the columns' precision; the per-particle tail (the log-sum-exp over rays,
 // then the FP64 equilibrium) runs with one thread per particle packed into
 // the first lanes, so the FP64 work is not spread over mostly idle warps.
-template <typename Real>
+template <typename Real, int VAR>
 __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs A)
 {
+    constexpr bool kHe = VAR == kSweepHelium;
+    constexpr bool kNF = VAR == kSweepNearFar;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Real* e2 = reinterpret_cast<Real*>(smem_raw);
     Real* wn = e2 + A.F;
     Real* sj = wn + A.F;
-    Real* sh1 = sj + A.F;                       // helium cross sections (A.he)
+    Real* sh1 = sj + A.F;                       // helium cross sections (kHe)
     Real* sh2 = sh1 + A.F;
-    const int narr = A.he ? 5 : 3;
+    const int narr = kHe ? 5 : 3;
     Real* lk = reinterpret_cast<Real*>(smem_raw + ((narr * (size_t)A.F * sizeof(Real) + 15) & ~size_t(15)));
     Real* lk2 = lk + kSweepThreads;
     __shared__ double sh[2];
-    sweep_spectrum<Real>(A.s, A.w, A.F, e2, (A.want_tangent || A.he) ? sj : nullptr, wn, sh);
-    if (A.he) {
+    sweep_spectrum<Real>(A.s, A.w, A.F, e2, (A.want_tangent || kHe) ? sj : nullptr, wn, sh);
+    if (kHe) {
         for (int j = threadIdx.x; j < A.F; j += blockDim.x) {
             sh1[j] = (Real)A.s_he1[j];
             sh2[j] = (Real)A.s_he2[j];
@@ -150,7 +157,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs A)
             const Real tau = static_cast<const Real*>(A.tau)[row + (int64_t)k * A.k_stride];
             Real S = Real(0), c = Real(0), S2 = Real(0), c2 = Real(0);
             // (near/far: tau is the far column; the slab of near particles is applied below)
-            const int nspec = (A.near_far == URCHIN_SLAB_SPECTRUM || A.he) ? 0 : A.F;
+            const int nspec = ((kNF && A.near_far == URCHIN_SLAB_SPECTRUM) || kHe) ? 0 : A.F;
             for (int j = 0; j < nspec; ++j) {
                 const Real v = wn[j] * exp2_p(-e2[j] * tau);
                 const Real yy = v - c;
@@ -167,7 +174,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs A)
             }
             // ln(Gamma_k / Gamma_thin) = -s_min tau_k + ln S_k
             Real lkv = nspec ? -smin * tau + log_p(S) : Real(0);
-            if (A.he) {
+            if (kHe) {
                 // H I, He I and He II columns: E_j = s_j tau + s1_j tau1 + s2_j tau2, the
                 // smallest E_j factored out of the sum
                 const int32_t ir = A.items ? A.items[row] : (int32_t)row;
@@ -188,7 +195,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs A)
                 }
                 lkv = -emin + log_p(Sh);
             }
-            if (A.near_far) {
+            if (kNF) {
                 // Eq. gammashldk: the far radiation enters the slab of near particles, in
                 // the particle's recombination case before this sweep
                 const int32_t ir = A.items ? A.items[row] : (int32_t)row;
@@ -600,7 +607,14 @@ int launch_sweep(const SweepArgs& A, cudaStream_t s)
     if (A.n_items <= 0) return URCHIN_OK;
     const size_t rsz = A.precision == URCHIN_F64 ? sizeof(double) : sizeof(float);
     size_t smem = (((A.he ? 5 : 3) * (size_t)A.F * rsz + 15) & ~size_t(15)) + 2 * rsz * kSweepThreads;
-    const void* fn = A.precision == URCHIN_F64 ? (const void*)k_sweep<double> : (const void*)k_sweep<float>;
+    const bool f64 = A.precision == URCHIN_F64;
+    const int var = A.he ? kSweepHelium : (A.near_far ? kSweepNearFar : kSweepPlain);
+    const void* fns[2][3] = {
+        {(const void*)k_sweep<float, kSweepPlain>, (const void*)k_sweep<float, kSweepNearFar>,
+         (const void*)k_sweep<float, kSweepHelium>},
+        {(const void*)k_sweep<double, kSweepPlain>, (const void*)k_sweep<double, kSweepNearFar>,
+         (const void*)k_sweep<double, kSweepHelium>}};
+    const void* fn = fns[f64 ? 1 : 0][var];
     if (smem > 48 * 1024)
         URCHIN_TRY_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int rows_per_block = kSweepThreads / A.R;
@@ -608,8 +622,8 @@ int launch_sweep(const SweepArgs& A, cudaStream_t s)
     int grid = 0;
     URCHIN_TRY(grid_for(fn, kSweepThreads, smem, &grid));
     if (need < grid) grid = (int)std::max<int64_t>(need, 1);
-    if (A.precision == URCHIN_F64) k_sweep<double><<<grid, kSweepThreads, smem, s>>>(A);
-    else k_sweep<float><<<grid, kSweepThreads, smem, s>>>(A);
+    void* args[] = {const_cast<SweepArgs*>(&A)};
+    URCHIN_TRY_CUDA(cudaLaunchKernel(fn, dim3(grid), dim3(kSweepThreads), args, smem, s));
     URCHIN_TRY(launched());
     return URCHIN_OK;
 }

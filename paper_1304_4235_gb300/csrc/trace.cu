@@ -544,9 +544,17 @@ __global__ void __launch_bounds__(256) k_trace(TraceParams P)
             tests += sk.ntest;
             visits += nvisit;
             if (MODE == MODE_COUNT) {
-                P.counts[ray] = sk.nhit;
+                P.counts[ray] = (sk.nhit + (unsigned)kSegPad - 1u) / (unsigned)kSegPad * (unsigned)kSegPad;
             } else if (MODE != MODE_SCATTER) {
-                if (MODE == MODE_FILL && sk.pos != sk.end) err |= kStSegment;
+                if (MODE == MODE_FILL) {
+                    // the padding (fewer than kSegPad entries) holds zero values
+                    if (sk.end - sk.pos >= kSegPad || sk.pos > sk.end) err |= kStSegment;
+                    else
+                        for (int64_t q = sk.pos; q < sk.end; ++q) {
+                            P.seg_col[q] = 0;
+                            static_cast<Real*>(P.seg_val)[q] = Real(0);
+                        }
+                }
                 static_cast<Real*>(P.out)[orow * P.row_stride + (int64_t)k * P.k_stride] = sk.sum;
                 if (NF) {
                     const int64_t at = P.near_k_stride > 0 ? (int64_t)org + (int64_t)k * P.near_k_stride

@@ -510,10 +510,11 @@ def urchin_solve_vjp(bvh: Bvh, dirs, l_ray: float, s, w, nH, T, x_star, state, x
                      tau_skip: float = 1e-4, tol: float = 1e-10, max_iter: int = 2000, gmres_m: int = 30,
                      segments: int = SEG_RECOMPUTE, kernel: int = KERNEL_M4, precision: int = F32,
                      case_rule: int = CASE_AUTO, warm_start: bool = False, raise_not_converged: bool = True,
-                     stream=None):
+                     profile: bool = False, stream=None):
     """dL/dw (float64 CUDA tensor [F]) at the converged x* of urchin_solve
     (whose `state` output must be passed), for x_bar = dL/dx*.  tol and
-    max_iter bound the adjoint GMRES solve; returns (w_bar, stats dict)."""
+    max_iter bound the adjoint GMRES solve; profile times the column passes
+    (trace_s, spmv_s).  Returns (w_bar, stats dict)."""
     import torch
     dirs = _host(dirs).reshape(-1, 3)
     P = urchin_solve_params()
@@ -533,6 +534,7 @@ def urchin_solve_vjp(bvh: Bvh, dirs, l_ray: float, s, w, nH, T, x_star, state, x
     P.precision = int(precision)
     P.case_rule = int(case_rule)
     P.warm_start = int(bool(warm_start))
+    P.profile = int(bool(profile))
     P.state = _dev(state, torch.uint8)
     wb = torch.zeros(int(s.numel()), dtype=torch.float64, device=x_star.device)
     st = urchin_solve_stats()

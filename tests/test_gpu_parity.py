@@ -300,14 +300,18 @@ def test_solve_not_converged_and_bad_inputs(halo_small):
     assert e.value.status == U.URCHIN_ERR_ARG
 
 
-def test_solve_full_size_halo_one_sweep_sampled():
+@pytest.mark.parametrize("segments", [U.SEG_RECOMPUTE, U.SEG_AUTO])
+def test_solve_full_size_halo_one_sweep_sampled(segments):
     """Benchmark-size halo: the GPU's sweep-2 x at sampled particles equals
-    the oracle's update computed from the GPU's sweep-1 state."""
+    the oracle's update computed from the GPU's sweep-1 state.  With stored
+    segments (the benchmark's launch configuration) sweep 2 reads its
+    columns from the padded segment lists (16-byte loads of 4 segments)."""
     w = W.halo()
     bvh, d = build(w, torch)
     sg, so = spectra(w, torch)
-    x1, st1 = _solve_gpu(w, bvh, d, sg, U.F32, tol=1e-300, max_iter=1)
-    x2, st2 = _solve_gpu(w, bvh, d, sg, U.F32, tol=1e-300, max_iter=2)
+    x1, st1 = _solve_gpu(w, bvh, d, sg, U.F32, tol=1e-300, max_iter=1, segments=segments)
+    x2, st2 = _solve_gpu(w, bvh, d, sg, U.F32, tol=1e-300, max_iter=2, segments=segments)
+    assert bool(st2["segments_stored"]) == (segments == U.SEG_AUTO)
     x0 = O.xeq(so[1].sum(), w.nH, w.T, 0.0, False)
     org = W.random_origins(w.n, 200, 10)
     # freeze decision of sweep 0 at the sample, from x0
@@ -330,7 +334,10 @@ def test_stored_segments_match_recompute_fp64(lattice, sweeps):
     xr, sr = _solve_gpu(w, bvh, d, sg, U.F64, tol=1e-300, max_iter=sweeps)
     xs, ss = _solve_gpu(w, bvh, d, sg, U.F64, tol=1e-300, max_iter=sweeps, segments=U.SEG_STORE, profile=True)
     assert ss["segments_stored"] == 1 and sr["segments_stored"] == 0
-    assert ss["nnz"] == ss["hits"] // 2          # the count and the fill pass each count every hit
+    # the count and the fill pass each count every hit; each of the n R rays is
+    # padded with fewer than 4 zero segments to a multiple of 4
+    hits = ss["hits"] // 2
+    assert ss["nnz"] % 4 == 0 and hits <= ss["nnz"] < hits + 4 * w.n * 12
     assert ss["iterations"] == sr["iterations"] == sweeps
     assert ss["rays"] == sr["rays"]
     assert rel_err(xs, xr).max() < 1e-11
