@@ -462,6 +462,34 @@ def main():
                           "rel_residual": vs["max_rel_dx"], "converged": bool(vs["converged"]),
                           "rays": vs["rays"], "grad_norm": float(wb.norm()), "trace_s": vs["trace_s"],
                           "spmv_s": vs["spmv_s"]}
+        # the differentiation workload on the same halo: 200 bins, loss = sum over
+        # all rays of (log10 N_HI - log10 N_target)^2, the target from seeded
+        # +-20 % bin weights; x* by Newton-Krylov, gradient by autograd (adjoint
+        # solve + column transpose)
+        from paper_1304_4235_gb300 import autograd as UA
+        e2, J2 = W.powerlaw_spectrum(200, w.e_lo, w.e_hi)
+        s2h, w2h = U.urchin_spectrum_weights(e2, J2, w.gamma_thin)
+        s2, w2 = torch.from_numpy(s2h).to(dev), torch.from_numpy(w2h).to(dev)
+        kw = dict(tol=1e-5, tau_skip=1e-4, max_iter=args.max_iter, method=U.METHOD_NEWTON, gmres_m=60,
+                  newton_eta=1e-4, segments=segs, precision=U.F32, raise_not_converged=False)
+        w2t = w2 * torch.from_numpy(np.random.default_rng(1308).uniform(0.8, 1.2, 200)).to(dev)
+        xt, _ = U.urchin_solve(bvh, dirs, w.l_ray, s2, w2t, d["nH"], d["T"], **kw)
+        target = torch.log10(U.urchin_trace_columns(bvh, xt, dirs, w.l_ray).double())
+        wv = w2.clone().requires_grad_(True)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record(stream)
+        xg = UA.converged_x(wv, bvh, dirs, w.l_ray, s2, d["nH"], d["T"], solve_kw=kw,
+                            vjp_kw=dict(tol=1e-6, max_iter=600, gmres_m=30, raise_not_converged=False))
+        L = ((torch.log10(UA.columns(xg, bvh, dirs, w.l_ray).double()) - target) ** 2).sum()
+        ev[1].record(stream)
+        L.backward()
+        ev[2].record(stream)
+        ev[2].synchronize()
+        comp["gradient_column_misfit_200_bins"] = {
+            "loss": float(L.detach()), "forward_s": ev[0].elapsed_time(ev[1]) * 1e-3,
+            "backward_s": ev[1].elapsed_time(ev[2]) * 1e-3, "grad_norm": float(wv.grad.norm()),
+            "forward": "Newton-Krylov to dx_tol 1e-5 + columns of x*",
+            "backward": "adjoint GMRES(30) to 1e-6 + column transpose"}
         bvh.close()
         line["compare"] = comp
     if world == 1 and not args.no_cpu_baseline:

@@ -195,6 +195,44 @@ def test_autograd_column_misfit_gradient_matches_finite_differences():
         assert abs(g[b] - fd) <= 1e-4 * abs(fd) + 1e-6 * np.abs(g).max(), (b, g[b], fd)
 
 
+def test_c4_column_misfit_gradient_200_bins():
+    """The column-misfit gradient of the differentiation workload (the halo's
+    density law, 200 bins, loss = sum over all rays of (log10 N_HI -
+    log10 N_target)^2 with the target from seeded +-20 % bin weights) on a
+    4000-particle halo, FP64 stored segments: autograd against central
+    differences of the forward solve at four seeded bins."""
+    w = W.halo(n=4000, seed=41, F=200)
+    bvh, d = build(w, torch)
+    sg, so = spectra(w, torch)
+    dirs = U.urchin_healpix_dirs(1)
+    kw = dict(tol=1e-12, max_iter=20000, precision=U.F64, segments=U.SEG_STORE)
+    rng = np.random.default_rng(42)
+    w_t = sg[1] * torch.from_numpy(rng.uniform(0.8, 1.2, sg[1].numel())).cuda()
+    x_t, st_t = U.urchin_solve(bvh, dirs, w.l_ray, sg[0], w_t, d["nH"], d["T"], **kw)
+    target = torch.log10(U.urchin_trace_columns(bvh, x_t, dirs, w.l_ray, precision=U.F64))
+
+    def loss_of(wv, grad):
+        wv = wv.clone().requires_grad_(grad)
+        x = UA.converged_x(wv, bvh, dirs, w.l_ray, sg[0], d["nH"], d["T"], solve_kw=kw,
+                           vjp_kw=dict(tol=1e-12, max_iter=5000, gmres_m=40))
+        tau = UA.columns(x, bvh, dirs, w.l_ray, precision=U.F64)
+        L = ((torch.log10(tau) - target) ** 2).sum()
+        if grad:
+            L.backward()
+            return L.item(), wv.grad.cpu().numpy()
+        return L.item(), None
+
+    L0, g = loss_of(sg[1], True)
+    assert np.isfinite(g).all() and np.abs(g).max() > 0
+    for b in np.sort(rng.choice(sg[1].numel(), size=4, replace=False)):
+        dw = 1e-4 * float(sg[1][b])
+        wp, wm = sg[1].clone(), sg[1].clone()
+        wp[b] += dw
+        wm[b] -= dw
+        fd = (loss_of(wp, False)[0] - loss_of(wm, False)[0]) / (2 * dw)
+        assert abs(g[b] - fd) <= 1e-4 * abs(fd) + 1e-6 * np.abs(g).max(), (b, g[b], fd)
+
+
 def test_autograd_rate_gradient_in_x_matches_oracle():
     """d(sum_i a_i Gamma_i)/dx through columns and the spectral fold: the
     per-particle dGamma/dx products of the adjoint."""
