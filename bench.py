@@ -42,9 +42,9 @@ WORKLOAD = "halo_262144_nside1_l200kpc_F100"
 # files at capture time; a changed kernel reports traffic null.
 #   k_spmv: bytes per stored segment read;  k_trace: bytes per ray-sphere hit
 MEASURED_TRAFFIC = {
-    # 65536-particle halo: 2.5945e9 DRAM bytes for 3.2202e8 segments (rays padded
-    # to multiples of 4) in one launch of the 4-segments-per-lane kernel
-    "k_spmv": {"b44318fd4381a7d4": 8.057},
+    # 65536-particle halo: 2.2773e9 DRAM bytes for 3.2360e8 segments (rays padded
+    # to multiples of 8) in one launch of k_spmv8 (7 algorithmic bytes per segment)
+    "k_spmv": {"41377b11515427e3": 7.038},
     "k_trace": {},
 }
 KERNEL_SOURCES = {"k_spmv": ("linalg.cu", "linalg.cuh"),
@@ -346,14 +346,14 @@ def main():
     if spmv_s >= trace_s and spmv_launches > 0:
         per_bytes = spmv_bytes / spmv_launches
         per_s = spmv_s / spmv_launches
-        # 4-byte index + 4-byte value per segment; the per-ray output and
-        # per-particle gather bytes are ~0.1 % of a launch
-        seg_per_launch = (spmv_bytes / spmv_launches) / 8.0
+        # 4-byte value + 3-byte split particle index per FP32 segment (n <= 2^24);
+        # the per-ray output and per-particle gather bytes are ~0.1 % of a launch
+        seg_per_launch = (spmv_bytes / spmv_launches) / (7.0 if w.n <= (1 << 24) else 8.0)
         t = MEASURED_TRAFFIC["k_spmv"].get(source_hash("k_spmv"))
         roof = {"bound": "hbm", "achieved": per_bytes / per_s / 1e9, "peak": hbm, "unit": "GB/s",
                 "frac": per_bytes / per_s / 1e9 / hbm,
                 "traffic": (t * seg_per_launch) if t else None,
-                "kernel": "k_spmv<float>", "peak_kind": peak_kind,
+                "kernel": "k_spmv8 (FP32 stored segments)", "peak_kind": peak_kind,
                 "alg_bytes_per_launch": per_bytes, "launch_ms": per_s * 1e3}
     else:
         per_bytes = trace_bytes / max(trace_launches, 1)

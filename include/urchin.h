@@ -376,7 +376,7 @@ typedef struct {
     int64_t particle_updates;     /* x updates of non-frozen particles         */
     int64_t n_active;             /* particles not frozen after sweep 0        */
     int64_t nnz;                  /* stored segments, each ray padded to a
-                                     multiple of 4 (0 in recompute mode)       */
+                                     multiple of 8 (0 in recompute mode)       */
     double  max_rel_dx;           /* last max |dx|/x over non-frozen particles */
     double  wall_s;               /* host wall time of the call                */
     int     converged;            /* 1 if max_rel_dx < tol                     */

@@ -144,8 +144,8 @@ constexpr unsigned kStVisit = 32u;      // traversal visit limit (malformed tree
 constexpr unsigned kStSegment = 64u;    // stored-segment fill disagrees with its count
 
 constexpr int kLeafMax = 16;      // subtrees with <= kLeafMax particles become leaves
-constexpr int kSegPad = 4;        // stored rays are padded to a multiple of kSegPad segments (zero
-                                  // values, particle 0) so the SpMV reads 4 segments per lane
+constexpr int kSegPad = 8;        // stored rays are padded to a multiple of kSegPad segments (zero
+                                  // values, particle 0) so the SpMV reads 8 segments per lane
 constexpr int kKTab = 2048;       // intervals of the full-chord M4 table in t = b^2/h^2
 
 // Full-chord M4 integral K(t) = int_{-c}^{c} shape(sqrt(t + u^2)) du, c = sqrt(1-t),
@@ -177,7 +177,9 @@ struct TraceJob {
     uint32_t* counts;             // mode 1: [R * n_items], index k * n_items + item: hits rounded
                                   //    up to a multiple of kSegPad
     const uint64_t* row_ptr;      // mode 2: [R * n_items + 1] offsets of each ray's segments
-    int32_t* seg_col;             // mode 2: Morton index of the particle per segment
+    int32_t* seg_col;             // mode 2: Morton index of the particle per segment, or NULL:
+    uint16_t* seg_lo;             //    its low 16 bits and
+    uint8_t* seg_hi;              //    its high 8 bits (FP32 segments, every index below 2^24)
     void* seg_val;                // mode 2: A_j * chord integral per segment (precision's type)
     const void* coef;             // mode 3: per-ray coefficient (precision's type), indexed like out
     double* xbar;                 // mode 3: [n] Morton order, accumulated with atomics

@@ -3,8 +3,8 @@
 //
 // With the per-ray segment lists stored once (column j, value A_j * chord
 // integral), a sweep's columns are tau_r = sum_e val_e x_{col_e}: a stream
-// over the segment arrays (8 bytes per segment in FP32) with a gather of x
-// from L2.  Rows are indexed k * n + particle (direction-major), as written by
+// over the segment arrays (7 bytes per segment in FP32: value + 24-bit
+// particle index split into 16 + 8 bits) with a gather of x from L2.  Rows are indexed k * n + particle (direction-major), as written by
 // the fill traversal.
 #include <algorithm>
 
@@ -16,7 +16,8 @@ namespace {
 
 constexpr int kSpmvThreads = 256;
 
-// One warp per ray; lanes stride the ray's segments four at a time (FP64).
+// One warp per ray; lanes stride the ray's segments four at a time (int32
+// indices: FP64, and FP32 beyond 2^24 particles).
 template <typename Real>
 __global__ void __launch_bounds__(kSpmvThreads) k_spmv(SpmvArgs A)
 {
@@ -59,11 +60,16 @@ __global__ void __launch_bounds__(kSpmvThreads) k_spmv(SpmvArgs A)
     }
 }
 
-// FP32: rays are padded to a multiple of kSegPad = 4 segments, so each lane
-// takes 4 consecutive segments with one 16-byte load of indices and one of
-// values (a quarter of the load instructions of the strided loop; measured on
-// the 262144-particle halo: 2.55 ms per sweep against 2.65 ms).
-__global__ void __launch_bounds__(kSpmvThreads) k_spmv4(SpmvArgs A)
+// FP32 with the split index (every particle index below 2^24): rays padded
+// to a multiple of 8 segments, each lane takes 8 consecutive segments with two
+// 16-byte value loads, one 16-byte load of the eight low halves and one
+// 8-byte load of the eight high bytes of the indices.  Measured on the
+// 262144-particle halo, ms per sweep: int32 indices with strided 4-byte loads
+// 2.72, with 16-byte loads of 4 segments per lane 2.55-2.62; split indices
+// with strided loads 3.13, with 4 segments per lane 2.64, with 8 segments per
+// lane (this loop: as many load requests as the int32 16-byte loop, 7 bytes
+// per segment instead of 8) 2.47.
+__global__ void __launch_bounds__(kSpmvThreads) k_spmv8(SpmvArgs A)
 {
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (kSpmvThreads / 32);
@@ -78,10 +84,21 @@ __global__ void __launch_bounds__(kSpmvThreads) k_spmv4(SpmvArgs A)
         const int64_t row = k * A.n_rows_per_k + i;
         const int64_t beg = (int64_t)A.row_ptr[row], end = (int64_t)A.row_ptr[row + 1];
         float s = 0.f, c = 0.f;
-        for (int64_t e = beg + 4 * lane; e < end; e += 128) {
-            const float4 v = __ldcs(reinterpret_cast<const float4*>(val + e));
-            const int4 j = __ldcs(reinterpret_cast<const int4*>(A.col + e));
-            const float t = (v.x * __ldg(xv + j.x) + v.y * __ldg(xv + j.y)) + (v.z * __ldg(xv + j.z) + v.w * __ldg(xv + j.w));
+        for (int64_t e = beg + 8 * lane; e < end; e += 256) {
+            const float4 v0 = __ldcs(reinterpret_cast<const float4*>(val + e));
+            const float4 v1 = __ldcs(reinterpret_cast<const float4*>(val + e + 4));
+            const uint4 l = __ldcs(reinterpret_cast<const uint4*>(A.lo + e));
+            const uint2 h = __ldcs(reinterpret_cast<const uint2*>(A.hi + e));
+            const int j0 = (int)((l.x & 0xffffu) | ((h.x & 0xffu) << 16));
+            const int j1 = (int)((l.x >> 16) | ((h.x & 0xff00u) << 8));
+            const int j2 = (int)((l.y & 0xffffu) | (h.x & 0xff0000u));
+            const int j3 = (int)((l.y >> 16) | ((h.x >> 24) << 16));
+            const int j4 = (int)((l.z & 0xffffu) | ((h.y & 0xffu) << 16));
+            const int j5 = (int)((l.z >> 16) | ((h.y & 0xff00u) << 8));
+            const int j6 = (int)((l.w & 0xffffu) | (h.y & 0xff0000u));
+            const int j7 = (int)((l.w >> 16) | ((h.y >> 24) << 16));
+            const float t = ((v0.x * __ldg(xv + j0) + v0.y * __ldg(xv + j1)) + (v0.z * __ldg(xv + j2) + v0.w * __ldg(xv + j3))) +
+                            ((v1.x * __ldg(xv + j4) + v1.y * __ldg(xv + j5)) + (v1.z * __ldg(xv + j6) + v1.w * __ldg(xv + j7)));
             const float y = t - c;
             const float u = s + y;
             c = (u - s) - y;
@@ -114,7 +131,10 @@ __global__ void __launch_bounds__(kSpmvThreads) k_spmv_t(SpmvTArgs A)
         const int64_t beg = (int64_t)A.row_ptr[row], end = (int64_t)A.row_ptr[row + 1];
         for (int64_t e = beg + lane; e < end; e += 32) {
             const Real v = __ldcs(val + e);
-            if (v != Real(0)) atomicAdd(A.z + __ldcs(A.col + e), (double)(c * v));   // padding is zero
+            if (v != Real(0)) {   // padding is zero
+                const int32_t j = A.col ? __ldcs(A.col + e) : (int32_t)__ldcs(A.lo + e) | ((int32_t)__ldcs(A.hi + e) << 16);
+                atomicAdd(A.z + j, (double)(c * v));
+            }
         }
     }
 }
@@ -190,12 +210,16 @@ int launch_spmv(const SpmvArgs& A, cudaStream_t s)
     if (A.n_items <= 0) return URCHIN_OK;
     int64_t warps = (int64_t)A.R * A.n_items;
     int grid = 0;
-    const void* fn = A.precision == URCHIN_F64 ? (const void*)k_spmv<double> : (const void*)k_spmv4;
+    // FP32 takes the split-index loop (the solver splits indices whenever n <=
+    // 2^24); the strided loop serves FP64 and FP32 with int32 indices
+    const void* fn = A.precision == URCHIN_F64 ? (const void*)k_spmv<double>
+                                               : (A.col ? (const void*)k_spmv<float> : (const void*)k_spmv8);
+    if (A.precision == URCHIN_F64 && !A.col) return set_error(URCHIN_ERR_ARG, "spmv: FP64 segments need int32 indices");
     URCHIN_TRY(grid_for(fn, kSpmvThreads, 0, &grid));
     int64_t need = (warps + 7) / 8;
     if (need < grid) grid = (int)std::max<int64_t>(need, 1);
-    if (A.precision == URCHIN_F64) k_spmv<double><<<grid, kSpmvThreads, 0, s>>>(A);
-    else k_spmv4<<<grid, kSpmvThreads, 0, s>>>(A);
+    void* args[] = {const_cast<SpmvArgs*>(&A)};
+    URCHIN_TRY_CUDA(cudaLaunchKernel(fn, dim3(grid), dim3(kSpmvThreads), args, 0, s));
     return launched();
 }
 

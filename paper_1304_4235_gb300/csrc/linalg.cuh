@@ -10,7 +10,9 @@ namespace urchin {
 
 struct SpmvArgs {
     const uint64_t* row_ptr;     // [R * n_rows_per_k + 1], multiples of kSegPad
-    const int32_t* col;          // [nnz] Morton particle index (padding: 0)
+    const int32_t* col;          // [nnz] Morton particle index (padding: 0), or NULL:
+    const uint16_t* lo;          //   its low 16 bits
+    const uint8_t* hi;           //   and high 8 bits (FP32 only)
     const void* val;             // [nnz] A_j * chord integral (float or double; padding: 0)
     const void* xvec;            // [n] vector the columns are linear in (Morton order, same type)
     const int32_t* items;        // [n_items] Morton particle of each evaluated ray origin (NULL = identity)
@@ -27,7 +29,9 @@ int launch_spmv(const SpmvArgs& A, cudaStream_t s);
 // accumulated with atomics; coef has the precision's type.
 struct SpmvTArgs {
     const uint64_t* row_ptr;
-    const int32_t* col;
+    const int32_t* col;          // as SpmvArgs
+    const uint16_t* lo;
+    const uint8_t* hi;
     const void* val;
     const void* coef;            // [R * n_items]
     const int32_t* items;        // NULL = identity

@@ -864,7 +864,8 @@ int Solver::count_spmv(const int32_t* items, int64_t n_items)
         seg = (int64_t)h;
         if (items == list && n_items == n_act) active_nnz = seg;
     }
-    stats.spmv_bytes += seg * (int64_t)(sizeof(int32_t) + vsz) + n_items * P.R * (int64_t)vsz + n * (int64_t)vsz;
+    const int64_t isz = seg_col ? (int64_t)sizeof(int32_t) : (int64_t)(sizeof(uint16_t) + sizeof(uint8_t));
+    stats.spmv_bytes += seg * (isz + (int64_t)vsz) + n_items * P.R * (int64_t)vsz + n * (int64_t)vsz;
     return URCHIN_OK;
 }
 
@@ -946,6 +947,8 @@ int Solver::columns(const int32_t* items, int64_t n_items, int sweep0)
         SpmvArgs A{};
         A.row_ptr = row_ptr;
         A.col = seg_col;
+        A.lo = seg_lo;
+        A.hi = seg_hi;
         A.val = seg_val;
         A.xvec = f64 ? (const void*)xs64 : (const void*)xs32;
         A.items = items;
@@ -994,7 +997,10 @@ int Solver::columns(const int32_t* items, int64_t n_items, int sweep0)
     URCHIN_TRY_CUDA(cudaMemcpyAsync(&nnz, total, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
     URCHIN_TRY_CUDA(cudaStreamSynchronize(s));
     const size_t vsz = f64 ? sizeof(double) : sizeof(float);
-    const size_t need = (size_t)nnz * (sizeof(int32_t) + vsz) + 1024;
+    // FP32 segments keep the particle index as 16 + 8 bits (7 bytes per segment)
+    const bool split = !f64 && n <= (int64_t(1) << 24);
+    const size_t isz = split ? sizeof(uint16_t) + sizeof(uint8_t) : sizeof(int32_t);
+    const size_t need = (size_t)nnz * (isz + vsz) + 1024;
     bool fits = true;
     if (P.segments == URCHIN_SEG_AUTO) {
         size_t free_b = 0, total_b = 0;
@@ -1003,7 +1009,9 @@ int Solver::columns(const int32_t* items, int64_t n_items, int sweep0)
     }
     if (fits) {
         Layout lay;
-        size_t o_col = lay.take(sizeof(int32_t) * (size_t)nnz);
+        size_t o_col = split ? 0 : lay.take(sizeof(int32_t) * (size_t)nnz);
+        size_t o_lo = split ? lay.take(sizeof(uint16_t) * (size_t)nnz) : 0;
+        size_t o_hi = split ? lay.take(sizeof(uint8_t) * (size_t)nnz) : 0;
         size_t o_val = lay.take(vsz * (size_t)nnz);
         int st = seg.alloc(lay.bytes, s);
         if (st != URCHIN_OK) {
@@ -1011,7 +1019,9 @@ int Solver::columns(const int32_t* items, int64_t n_items, int sweep0)
             fits = false;
             clear_error();
         } else {
-            seg_col = seg.at<int32_t>(o_col);
+            seg_col = split ? nullptr : seg.at<int32_t>(o_col);
+            seg_lo = split ? seg.at<uint16_t>(o_lo) : nullptr;
+            seg_hi = split ? seg.at<uint8_t>(o_hi) : nullptr;
             seg_val = seg.at<void>(o_val);
         }
     }
@@ -1022,6 +1032,8 @@ int Solver::columns(const int32_t* items, int64_t n_items, int sweep0)
     job.mode = 2;
     job.row_ptr = row_ptr;
     job.seg_col = seg_col;
+    job.seg_lo = seg_lo;
+    job.seg_hi = seg_hi;
     job.seg_val = seg_val;
     URCHIN_TRY(timed_trace(job));
     stats.traversals += 2;
@@ -1039,6 +1051,8 @@ int Solver::linear_columns(const int32_t* items, int64_t n_items, const float* z
         SpmvArgs A{};
         A.row_ptr = row_ptr;
         A.col = seg_col;
+        A.lo = seg_lo;
+        A.hi = seg_hi;
         A.val = seg_val;
         A.xvec = f64 ? (const void*)z64 : (const void*)z32;
         A.items = items;
@@ -1628,6 +1642,8 @@ int Solver::transpose_columns(const void* coef, double* z)
         SpmvTArgs A{};
         A.row_ptr = row_ptr;
         A.col = seg_col;
+        A.lo = seg_lo;
+        A.hi = seg_hi;
         A.val = seg_val;
         A.coef = coef;
         A.items = list;

@@ -104,7 +104,9 @@ struct Solver {
     uint32_t* counts = nullptr;
     uint64_t* row_ptr = nullptr;
     void* scan_tmp = nullptr;
-    int32_t* seg_col = nullptr;
+    int32_t* seg_col = nullptr;                  // particle index per segment, or NULL when
+    uint16_t* seg_lo = nullptr;                  // split into 16 + 8 bits (FP32 segments,
+    uint8_t* seg_hi = nullptr;                   // n <= 2^24: 7 bytes per segment instead of 8)
     void* seg_val = nullptr;
     Scratch seg;
     // per-direction traversal orders, cached per item list (any permutation

@@ -52,7 +52,9 @@ struct TraceParams {
     // stored-segment modes
     uint32_t* counts;             // MODE_COUNT: hits per ray, index k * n_items + item
     const uint64_t* row_ptr;      // MODE_FILL: first segment of each ray (same index), size + 1
-    int32_t* seg_col;             // MODE_FILL: Morton index of the particle
+    int32_t* seg_col;             // MODE_FILL: Morton index of the particle, or NULL:
+    uint16_t* seg_lo;             //   its low 16 bits
+    uint8_t* seg_hi;              //   and high 8 bits (indices below 2^24)
     void* seg_val;                // MODE_FILL: A_j * chord integral (float or double)
     const float* A32;
     const double* A64;
@@ -299,6 +301,17 @@ __device__ __forceinline__ float safe_inv(double d)
     return fabs(d) > 1e-20 ? (float)(1.0 / d) : copysignf(1e30f, (float)d);
 }
 
+// particle index of a stored segment (int32, or split 16 + 8 bits)
+__device__ __forceinline__ void store_index(const TraceParams& P, int64_t pos, int j)
+{
+    if (P.seg_col) {
+        P.seg_col[pos] = j;
+    } else {
+        P.seg_lo[pos] = (uint16_t)(j & 0xffff);
+        P.seg_hi[pos] = (uint8_t)(j >> 16);
+    }
+}
+
 // FP32 hit evaluation: cheap rejection, then the impact parameter from an
 // error-free cross product, then the tabulated / piecewise chord integral.
 template <int KERNEL, int MODE, bool NF>
@@ -348,7 +361,7 @@ __device__ __forceinline__ void leaf_hits_f32(const TraceParams& P, const float2
         Kahan::add(k.sum, k.comp, __ldg(P.w32 + j) * F);
         if (MODE == MODE_FILL) {
             if (k.pos < k.end) {
-                P.seg_col[k.pos] = j;
+                store_index(P, k.pos, j);
                 static_cast<float*>(P.seg_val)[k.pos] = __ldg(P.A32 + j) * F;
                 ++k.pos;
             } else {
@@ -405,7 +418,7 @@ __device__ __forceinline__ void leaf_hits(const TraceParams& P, int ref, int cnt
         Kahan::add(k.sum, k.comp, O::weight(P, j) * F);
         if (MODE == MODE_FILL) {
             if (k.pos < k.end) {
-                P.seg_col[k.pos] = j;
+                store_index(P, k.pos, j);
                 const Real A = sizeof(Real) == 4 ? Real(__ldg(P.A32 + j)) : Real(__ldg(P.A64 + j));
                 static_cast<Real*>(P.seg_val)[k.pos] = A * F;
                 ++k.pos;
@@ -551,7 +564,7 @@ __global__ void __launch_bounds__(256) k_trace(TraceParams P)
                     if (sk.end - sk.pos >= kSegPad || sk.pos > sk.end) err |= kStSegment;
                     else
                         for (int64_t q = sk.pos; q < sk.end; ++q) {
-                            P.seg_col[q] = 0;
+                            store_index(P, q, 0);
                             static_cast<Real*>(P.seg_val)[q] = Real(0);
                         }
                 }
@@ -695,6 +708,8 @@ int launch_trace(const TraceJob& job, cudaStream_t s)
     P.counts = job.counts;
     P.row_ptr = job.row_ptr;
     P.seg_col = job.seg_col;
+    P.seg_lo = job.seg_lo;
+    P.seg_hi = job.seg_hi;
     P.seg_val = job.seg_val;
     P.A32 = b->A32;
     P.A64 = b->A64;
@@ -705,6 +720,8 @@ int launch_trace(const TraceJob& job, cudaStream_t s)
     P.near_k_stride = job.near_k_stride;
     if (job.near_far && !job.out_near && job.mode != MODE_COUNT)
         return set_error(URCHIN_ERR_ARG, "trace: near/far split without a near-column output");
+    if (job.mode == MODE_FILL && !job.seg_col && !(job.seg_lo && job.seg_hi && b->n <= (int64_t(1) << 24)))
+        return set_error(URCHIN_ERR_ARG, "trace: segment fill without a particle-index array");
     return dispatch_mode(P, job.precision, job.kernel, job.mode, job.near_far != 0, s);
 }
 
