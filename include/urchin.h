@@ -24,10 +24,13 @@
  *     `unit_cm` converts it to cm.  Columns are returned as threshold
  *     optical depth tau = sigma_th N_HI with sigma_th = 2^9 pi/(3 e^4)
  *     alpha_fs pi a_0^2 = 6.3043e-18 cm^2 (App. C1, Eq. sigma_ana).
- *   - Work arrays the library needs are taken from the stream-ordered
- *     allocator of the calling device (cudaMallocAsync) and released on the
- *     same stream before the call returns; urchin_build_bvh's result holds
- *     device memory until urchin_free_bvh.
+ *   - Work arrays the library needs are taken from a stream-ordered memory
+ *     pool the library keeps per device (cudaMallocFromPoolAsync) and
+ *     released on the same stream before the call returns.  Released memory
+ *     stays reserved in that pool for later calls (mapping and unmapping the
+ *     14 GB of stored segments of a 262144-particle solve costs ~30 ms);
+ *     urchin_trim_memory returns it to the device.  urchin_build_bvh's
+ *     result holds device memory until urchin_free_bvh.
  */
 #ifndef URCHIN_H
 #define URCHIN_H
@@ -138,6 +141,15 @@ URCHIN_API const char* urchin_version(void);
 /* Number of CUDA kernels this library has launched in this process
  * (instrumentation for benchmarks; no counterpart in the paper). */
 URCHIN_API int64_t urchin_kernel_launches(void);
+
+/* Return the device memory held by the library's work-array pool of
+ * `device` (-1: every device the library has used) to the device, except
+ * blocks still in use or whose stream-ordered release has not completed
+ * (synchronise the streams of earlier calls first).  *reserved_out (may be
+ * NULL) receives the bytes the pool(s) still reserve afterwards.  No
+ * counterpart in the paper.  Errors: ERR_ARG (device out of range),
+ * ERR_CUDA. */
+URCHIN_API int urchin_trim_memory(int device, uint64_t* reserved_out);
 
 /* HEALPix ray directions (Sec. 3.2; App. A: N_pix = 12 N_side^2): the unit
  * vectors to the pixel centres of the ring scheme of Gorski et al. (2005),

@@ -78,6 +78,11 @@ struct Layout {
 
 int grid_for(const void* kernel, int block, size_t smem, int* grid_out);
 
+// The calling device's work-array pool (created on first use, keeps freed
+// memory reserved), and the bytes it holds reserved but unused.
+int library_pool(cudaMemPool_t* out);
+size_t pool_idle_bytes();
+
 // Check the launch just made and count it (urchin_kernel_launches).
 int launched();
 

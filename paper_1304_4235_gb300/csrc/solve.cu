@@ -1005,7 +1005,8 @@ int Solver::columns(const int32_t* items, int64_t n_items, int sweep0)
     if (P.segments == URCHIN_SEG_AUTO) {
         size_t free_b = 0, total_b = 0;
         URCHIN_TRY_CUDA(cudaMemGetInfo(&free_b, &total_b));
-        fits = need < (size_t)(0.85 * (double)free_b);
+        // memory the library's pool keeps reserved from earlier calls is available too
+        fits = need < (size_t)(0.85 * (double)(free_b + pool_idle_bytes()));
     }
     if (fits) {
         Layout lay;

@@ -86,6 +86,7 @@ SIGNATURES = {
     "urchin_last_error": (C.c_char_p, []),
     "urchin_version": (C.c_char_p, []),
     "urchin_kernel_launches": (C.c_int64, []),
+    "urchin_trim_memory": (C.c_int, [C.c_int, C.POINTER(C.c_uint64)]),
     "urchin_healpix_dirs": (C.c_int, [C.c_int, _vp]),
     "urchin_spectrum_weights": (C.c_int, [C.c_int, _vp, _vp, C.c_int, C.c_double, _vp, _vp]),
     "urchin_build_bvh": (C.c_int, [C.POINTER(urchin_particles), C.POINTER(urchin_box),
@@ -183,6 +184,14 @@ def urchin_version() -> str:
 
 def urchin_kernel_launches() -> int:
     return int(load().urchin_kernel_launches())
+
+
+def urchin_trim_memory(device: int = -1) -> int:
+    """Return the library pool's unused device memory (all devices for -1);
+    the bytes still reserved afterwards."""
+    left = C.c_uint64(0)
+    _check(load().urchin_trim_memory(int(device), C.byref(left)))
+    return int(left.value)
 
 
 def urchin_healpix_dirs(nside: int) -> np.ndarray:

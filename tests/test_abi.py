@@ -135,6 +135,10 @@ def test_device_entry_points_reject_bad_arguments_without_gpu_work():
     assert lib.urchin_evolve(None, None, None, None, 0, 0, 0.0, None, 1.0, None, None) == U.URCHIN_OK
     assert lib.urchin_gamma_vjp(None, 0, 0, 12, C.byref(sp), None, None, None, None) == U.URCHIN_OK
     assert lib.urchin_solve_vjp(None, None, None, None, None, None, None) == U.URCHIN_ERR_ARG
+    # the memory pool: bad device; nothing to trim before any GPU work
+    assert lib.urchin_trim_memory(-2, None) == U.URCHIN_ERR_ARG
+    left = C.c_uint64(7)
+    assert lib.urchin_trim_memory(-1, C.byref(left)) == U.URCHIN_OK and left.value == 0
     # zero-size requests are no-ops
     assert lib.urchin_equilibrium(None, None, None, None, 0, 0, 0.0, None, None) == U.URCHIN_OK
     assert lib.urchin_gamma(None, 0, 0, 12, C.byref(sp), None, None, None) == U.URCHIN_OK

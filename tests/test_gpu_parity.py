@@ -419,6 +419,21 @@ def test_newton_full_halo_reaches_xstar_in_fewer_evaluations():
     assert rel_err(xp, xs).max() < 1e-3
 
 
+def test_memory_pool_keeps_and_trims(halo_small):
+    """Work arrays come from a pool that keeps freed memory: a second solve
+    reuses it (same result), and urchin_trim_memory returns it."""
+    w, bvh, d = halo_small
+    sg, so = spectra(w, torch)
+    x1, s1 = _solve_gpu(w, bvh, d, sg, U.F32, tol=1e-300, max_iter=5, segments=U.SEG_STORE)
+    torch.cuda.synchronize()
+    held = U.urchin_trim_memory(-1)
+    x2, s2 = _solve_gpu(w, bvh, d, sg, U.F32, tol=1e-300, max_iter=5, segments=U.SEG_STORE)
+    torch.cuda.synchronize()
+    assert held == 0 and s1["nnz"] == s2["nnz"] > 0
+    np.testing.assert_allclose(x2, x1, rtol=1e-6, atol=0)
+    assert U.urchin_trim_memory(torch.cuda.current_device()) == 0
+
+
 def test_plain_solve_latched_case_matches_oracle(halo_small):
     """The latched case switch, step matched against the oracle on a halo
     where the unlatched rule would cycle."""
