@@ -79,6 +79,7 @@ struct Sink {
     Real coef;                    // MODE_SCATTER
     Real near, near_c;            // near/far: near column and its compensation
     double ox, oy, oz;            // near/far: shifted origin in double (the near test)
+    uint32_t lo_pend, hi_pend;    // MODE_FILL, split indices: halves / bytes of the current word
 };
 
 // Near/far split (Sec. 3.3.3): particle j is near the ray's origin when the
@@ -301,15 +302,23 @@ __device__ __forceinline__ float safe_inv(double d)
     return fabs(d) > 1e-20 ? (float)(1.0 / d) : copysignf(1e30f, (float)d);
 }
 
-// particle index of a stored segment (int32, or split 16 + 8 bits)
-__device__ __forceinline__ void store_index(const TraceParams& P, int64_t pos, int j)
+// Particle index of stored segment pos: an int32, or split into 16 + 8 bits.
+// A lane writes its ray's segments at consecutive positions from a multiple
+// of 8 to a multiple of 8 (the padding), so the split halves and bytes are
+// gathered in the sink and written as whole 32-bit words.
+template <typename Real>
+__device__ __forceinline__ void store_index(const TraceParams& P, Sink<Real>& k, int64_t pos, int j)
 {
     if (P.seg_col) {
         P.seg_col[pos] = j;
-    } else {
-        P.seg_lo[pos] = (uint16_t)(j & 0xffff);
-        P.seg_hi[pos] = (uint8_t)(j >> 16);
+        return;
     }
+    const uint32_t lo = (uint32_t)j & 0xffffu, hi = ((uint32_t)j >> 16) & 0xffu;
+    if (pos & 1) reinterpret_cast<uint32_t*>(P.seg_lo)[pos >> 1] = k.lo_pend | (lo << 16);
+    else k.lo_pend = lo;
+    const int sh = (int)(pos & 3) * 8;
+    k.hi_pend = (sh == 0 ? 0u : k.hi_pend) | (hi << sh);
+    if ((pos & 3) == 3) reinterpret_cast<uint32_t*>(P.seg_hi)[pos >> 2] = k.hi_pend;
 }
 
 // FP32 hit evaluation: cheap rejection, then the impact parameter from an
@@ -361,7 +370,7 @@ __device__ __forceinline__ void leaf_hits_f32(const TraceParams& P, const float2
         Kahan::add(k.sum, k.comp, __ldg(P.w32 + j) * F);
         if (MODE == MODE_FILL) {
             if (k.pos < k.end) {
-                store_index(P, k.pos, j);
+                store_index(P, k, k.pos, j);
                 static_cast<float*>(P.seg_val)[k.pos] = __ldg(P.A32 + j) * F;
                 ++k.pos;
             } else {
@@ -418,7 +427,7 @@ __device__ __forceinline__ void leaf_hits(const TraceParams& P, int ref, int cnt
         Kahan::add(k.sum, k.comp, O::weight(P, j) * F);
         if (MODE == MODE_FILL) {
             if (k.pos < k.end) {
-                store_index(P, k.pos, j);
+                store_index(P, k, k.pos, j);
                 const Real A = sizeof(Real) == 4 ? Real(__ldg(P.A32 + j)) : Real(__ldg(P.A64 + j));
                 static_cast<Real*>(P.seg_val)[k.pos] = A * F;
                 ++k.pos;
@@ -564,7 +573,7 @@ __global__ void __launch_bounds__(256) k_trace(TraceParams P)
                     if (sk.end - sk.pos >= kSegPad || sk.pos > sk.end) err |= kStSegment;
                     else
                         for (int64_t q = sk.pos; q < sk.end; ++q) {
-                            store_index(P, q, 0);
+                            store_index(P, sk, q, 0);
                             static_cast<Real*>(P.seg_val)[q] = Real(0);
                         }
                 }
