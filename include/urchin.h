@@ -80,6 +80,9 @@ typedef struct CUstream_st* urchin_stream_t;
 #define URCHIN_SEG_RECOMPUTE    0     /* trace the BVH every sweep              */
 #define URCHIN_SEG_STORE        1     /* store per-ray segment lists once       */
 #define URCHIN_SEG_AUTO         2     /* store when the lists fit in memory     */
+/* A stored segment is the FP32 value and the particle's Morton index split
+ * into 16 + 8 bits (7 bytes; n <= 2^24), or FP64 value and int32 index (12
+ * bytes); each ray's list is padded with zero entries to a multiple of 8. */
 
 #define URCHIN_MAX_RAYS       192     /* HEALPix N_side <= 4                    */
 #define URCHIN_MAX_BINS      4096     /* frequency bins                         */
