@@ -4,8 +4,9 @@
 // With the per-ray segment lists stored once (column j, value A_j * chord
 // integral), a sweep's columns are tau_r = sum_e val_e x_{col_e}: a stream
 // over the segment arrays (7 bytes per segment in FP32: value + 24-bit
-// particle index split into 16 + 8 bits) with a gather of x from L2.  Rows are indexed k * n + particle (direction-major), as written by
-// the fill traversal.
+// particle index split into 16 + 8 bits) with a gather of x from L2.  Rows
+// are indexed k * n + particle (direction-major), as written by the fill
+// traversal.
 #include <algorithm>
 
 #include "linalg.cuh"
