@@ -223,10 +223,13 @@ inline bool spectrum_has_he(const urchin_spectrum* sp) { return sp && (sp->s_he1
 
 // Table of ln sum_b w_b exp(-s_b tau) on u = ln(1 + tau) for the
 // polychromatic slab (spectral_device.cuh, SpecTable): kSpecTab intervals
-// up to tau = kSpecTauMax; tab needs kSpecTab + 1 double2 (value, d/du).
+// up to tau = kSpecTauMax, in double and (relative to Gamma_thin) in float.
+// buf needs spec_table_bytes() of device memory; synchronises st.
 constexpr int kSpecTab = 4096;
 constexpr double kSpecTauMax = 1e7;
-int build_spec_table(const double* s, const double* w, int F, double2* tab, double* smin_out, cudaStream_t st);
+struct SpecTable;
+size_t spec_table_bytes();
+int build_spec_table(const double* s, const double* w, int F, void* buf, SpecTable* out, cudaStream_t st);
 
 // w = A * x gathered into Morton order: w[s] = A[s] * x[perm[s]]
 int launch_weights(const urchin_bvh* bvh, const double* x_orig, float* w32, double* w64,

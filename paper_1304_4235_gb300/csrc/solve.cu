@@ -332,7 +332,11 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs A)
                 // into the slab and by R out of it (the ray combination below is a mean)
                 const double lnR = log((double)A.R);
                 if (A.near_far == URCHIN_SLAB_SPECTRUM)
-                    lkv = (Real)(slab_poly_lnratio(A.poly, gthin, (double)tau, tn, A.nH[ir], al, A.gc[ir], -lnR) + lnR);
+                    // FP32 sweep: the slab's table and x_eq in FP32 (slab_poly_lnratio32)
+                    lkv = (Real)((sizeof(Real) == 4
+                                      ? slab_poly_lnratio32(A.poly, gthin, (double)tau, tn, A.nH[ir], al, A.gc[ir], -lnR)
+                                      : slab_poly_lnratio(A.poly, gthin, (double)tau, tn, A.nH[ir], al, A.gc[ir], -lnR)) +
+                                 lnR);
                 else
                     lkv = (Real)(slab_lnratio((double)lkv - lnR, gthin, tn, A.nH[ir], al, A.gc[ir]) + lnR);
             }
@@ -743,7 +747,7 @@ int Solver::init(const urchin_bvh* bvh_, const urchin_solve_params* P_, double* 
     size_t o_list = lay.take(sizeof(int32_t) * (size_t)n);
     size_t o_tau = lay.take(rsz * (size_t)rays);
     size_t o_tn = lay.take(P.near_far ? rsz * (size_t)rays : 0);
-    size_t o_pt = lay.take(P.near_far == URCHIN_SLAB_SPECTRUM ? sizeof(double2) * (kSpecTab + 1) + 64 : 0);
+    size_t o_pt = lay.take(P.near_far == URCHIN_SLAB_SPECTRUM ? spec_table_bytes() : 0);
     const bool he = spectrum_has_he(&P.spectrum);
     size_t o_h1 = lay.take(he ? rsz * (size_t)rays : 0);
     size_t o_h2 = lay.take(he ? rsz * (size_t)rays : 0);
@@ -775,15 +779,8 @@ int Solver::init(const urchin_bvh* bvh_, const urchin_solve_params* P_, double* 
     tau_near = P.near_far ? scr.at<void>(o_tn) : nullptr;
     tau_he1 = he ? scr.at<void>(o_h1) : nullptr;
     tau_he2 = he ? scr.at<void>(o_h2) : nullptr;
-    if (P.near_far == URCHIN_SLAB_SPECTRUM) {
-        double2* tab = scr.at<double2>(o_pt);
-        double* smin = reinterpret_cast<double*>(tab + kSpecTab + 1);
-        URCHIN_TRY(build_spec_table(P.spectrum.s, P.spectrum.w, P.spectrum.F, tab, smin, s));
-        double hs = 0.0;
-        URCHIN_TRY_CUDA(cudaMemcpyAsync(&hs, smin, sizeof(double), cudaMemcpyDeviceToHost, s));
-        URCHIN_TRY_CUDA(cudaStreamSynchronize(s));
-        poly = SpecTable{tab, kSpecTab, log1p(kSpecTauMax), hs};
-    }
+    if (P.near_far == URCHIN_SLAB_SPECTRUM)
+        URCHIN_TRY(build_spec_table(P.spectrum.s, P.spectrum.w, P.spectrum.F, scr.at<void>(o_pt), &poly, s));
     comp_tmp = scr.at<void>(o_comp);
     counter = reinterpret_cast<unsigned*>(misc + 1);
     status = counter + 1;

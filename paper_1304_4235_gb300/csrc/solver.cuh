@@ -87,7 +87,7 @@ struct Solver {
     int32_t* list = nullptr;
     void* tau = nullptr;
     void* tau_near = nullptr;                    // near/far: [R * n] near columns, Morton slot + k n
-    SpecTable poly{nullptr, 0, 0.0, 0.0};        // near/far with the polychromatic slab
+    SpecTable poly{nullptr, 0, 0.0, 0.0, nullptr, 0.0};   // near/far with the polychromatic slab
     void* tau_he1 = nullptr;                     // helium: [R * n] fixed columns, Morton slot + k n
     void* tau_he2 = nullptr;
     int he_columns();

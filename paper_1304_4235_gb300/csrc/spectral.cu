@@ -297,7 +297,12 @@ __global__ void k_gamma_nearfar(const Real* __restrict__ tf, const Real* __restr
             // the ray's share (1/R) of the radiation lights its slab; rates add over rays
             const double lnR = log((double)R);
             if (poly.tab) {
-                l = slab_poly_lnratio(poly, gthin, t, (double)tn[o * R + k], nH[o], alpha, r.gamma_c, -lnR) + lnR;
+                // FP32 columns: the slab's table and x_eq in FP32 (see slab_poly_lnratio32)
+                l = (sizeof(Real) == 4 ? slab_poly_lnratio32(poly, gthin, t, (double)tn[o * R + k], nH[o], alpha,
+                                                             r.gamma_c, -lnR)
+                                       : slab_poly_lnratio(poly, gthin, t, (double)tn[o * R + k], nH[o], alpha,
+                                                           r.gamma_c, -lnR)) +
+                    lnR;
             } else {
                 double S = 0.0;
                 for (int b = 0; b < F; ++b) S += ws[b] * exp(-ss[b] * t);
@@ -321,11 +326,16 @@ __global__ void k_gamma_nearfar(const Real* __restrict__ tf, const Real* __restr
 // tab[i] = (ln sum_b w_b e^{-s_b tau_i}, d/du), tau_i = e^{u_i} - 1, u_i = i umax / nt,
 // in double with the factored sum; smin_out[0] = min_b s_b
 __global__ void k_spec_table(const double* __restrict__ sv, const double* __restrict__ wv, int F, int nt,
-                             double umax, double2* tab, double* smin_out)
+                             double umax, double2* tab, float2* tab32, double* smin_out)
 {
-    double smin = sv[0];
+    double smin = sv[0], gthin = 0.0;
     for (int b = 1; b < F; ++b) smin = fmin(smin, sv[b]);
-    if (blockIdx.x == 0 && threadIdx.x == 0) smin_out[0] = smin;
+    for (int b = 0; b < F; ++b) gthin += wv[b];
+    const double lnthin = log(gthin);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        smin_out[0] = smin;
+        smin_out[1] = lnthin;
+    }
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= nt; i += gridDim.x * blockDim.x) {
         const double u = umax * (double)i / (double)nt;
         const double tau = expm1(u);
@@ -337,6 +347,7 @@ __global__ void k_spec_table(const double* __restrict__ sv, const double* __rest
         }
         // d/du = (d/dtau)(1 + tau), d ln Gamma / d tau = -S1 / S
         tab[i] = make_double2(-smin * tau + log(S), -(S1 / S) * (1.0 + tau));
+        tab32[i] = make_float2((float)(-smin * tau + log(S) - lnthin), (float)(-(S1 / S) * (1.0 + tau)));
     }
 }
 
@@ -454,10 +465,20 @@ int gamma_vjp_t(const Real* tau, int64_t n_orig, int R, const urchin_spectrum* s
 
 }  // namespace
 
-int build_spec_table(const double* s, const double* w, int F, double2* tab, double* smin_out, cudaStream_t st)
+size_t spec_table_bytes() { return sizeof(double2) * (kSpecTab + 1) + 64 + sizeof(float2) * (kSpecTab + 1); }
+
+int build_spec_table(const double* s, const double* w, int F, void* buf, SpecTable* out, cudaStream_t st)
 {
-    k_spec_table<<<(kSpecTab + 256) / 256, 256, 0, st>>>(s, w, F, kSpecTab, log1p(kSpecTauMax), tab, smin_out);
-    return launched();
+    double2* tab = static_cast<double2*>(buf);
+    double* sc = reinterpret_cast<double*>(tab + kSpecTab + 1);          // smin, ln Gamma_thin
+    float2* tab32 = reinterpret_cast<float2*>(reinterpret_cast<char*>(sc) + 64);
+    k_spec_table<<<(kSpecTab + 256) / 256, 256, 0, st>>>(s, w, F, kSpecTab, log1p(kSpecTauMax), tab, tab32, sc);
+    URCHIN_TRY(launched());
+    double h[2] = {0.0, 0.0};
+    URCHIN_TRY_CUDA(cudaMemcpyAsync(h, sc, sizeof(h), cudaMemcpyDeviceToHost, st));
+    URCHIN_TRY_CUDA(cudaStreamSynchronize(st));
+    *out = SpecTable{tab, kSpecTab, log1p(kSpecTauMax), h[0], tab32, h[1]};
+    return URCHIN_OK;
 }
 
 int launch_wbar(const void* tau, int precision, int64_t n_rays, const double* lc, const double* sg, const double* sv,
@@ -617,17 +638,10 @@ extern "C" int urchin_gamma_nearfar(const void* tau_far, const void* tau_near, i
         return set_error(URCHIN_ERR_ARG, "urchin_gamma_nearfar: NULL tau_far, tau_near, nH, T or gamma_out");
     cudaStream_t s = (cudaStream_t)stream;
     Scratch tb;
-    SpecTable poly{nullptr, kSpecTab, log1p(kSpecTauMax), 0.0};
+    SpecTable poly{nullptr, kSpecTab, log1p(kSpecTauMax), 0.0, nullptr, 0.0};
     if (slab == URCHIN_SLAB_SPECTRUM) {
-        URCHIN_TRY(tb.alloc(sizeof(double2) * (kSpecTab + 1) + 256, s));
-        double2* tab = tb.at<double2>(0);
-        double* smin = reinterpret_cast<double*>(tab + kSpecTab + 1);
-        URCHIN_TRY(build_spec_table(sp->s, sp->w, sp->F, tab, smin, s));
-        double hs = 0.0;
-        URCHIN_TRY_CUDA(cudaMemcpyAsync(&hs, smin, sizeof(double), cudaMemcpyDeviceToHost, s));
-        URCHIN_TRY_CUDA(cudaStreamSynchronize(s));
-        poly.tab = tab;
-        poly.smin = hs;
+        URCHIN_TRY(tb.alloc(spec_table_bytes(), s));
+        URCHIN_TRY(build_spec_table(sp->s, sp->w, sp->F, tb.at<void>(0), &poly, s));
     }
     const size_t smem = sizeof(double) * 2 * (size_t)sp->F;
     const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n_orig + 127) / 128, 4096));
