@@ -35,7 +35,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "rays/s and particle-updates/s to converged x (rel 1e-3), Newton+adjoint vs plain"
-WORKLOAD = "halo_262144_nside1_l200kpc_F100"
+def workload_name(w) -> str:
+    """The halo as benchmarked: particles, HEALPix N_side, ray length, bins."""
+    return f"halo_{w.n}_nside{w.nside}_l{w.l_ray:g}kpc_F{w.F}"
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per unit of work
 # of a kernel, from one ncu capture, keyed by the hash of the kernel's source
@@ -197,7 +199,7 @@ def reference_arm(args, w):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
+        "data": "synthetic", "config": {"workload": workload_name(w), "l2": "n/a (CPU)"},
         "particle_updates_per_s": sum(r["origins"] for r in runs) / secs,
         "cpu_baseline": {"value": value, "unit": "rays/s", "cores": runs[0]["cores"], "kind": "oracle",
                          "sample": f"{runs[0]['origins']} seeded origins x {dirs.shape[0]} rays, one sweep "
@@ -375,7 +377,7 @@ def main():
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "particles": w.n, "rays_per_particle": w.R, "l_ray_kpc": w.l_ray,
+        "config": {"workload": workload_name(w), "particles": w.n, "rays_per_particle": w.R, "l_ray_kpc": w.l_ray,
                    "bins": w.F, "method": args.method, "segments": args.segments, "blocks": args.blocks,
                    "tol": timed["tol"], "l2": "flushed before each step (256 MB write); stored segments >> L2"},
         "particle_updates_per_s": updates / (total_ms * 1e-3),
