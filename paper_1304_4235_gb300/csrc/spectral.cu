@@ -20,93 +20,41 @@ namespace {
 
 constexpr int kGammaThreads = 256;
 
-// Shared spectrum prepared by every block: coefficients of exp2 and the
-// normalised weights, plus Gamma_thin and s_min.
-template <typename Real>
-__device__ void load_spectrum(const double* s, const double* w, int F, Real* e2, Real* wn, double* sh)
-{
-    // sh[0] = Gamma_thin, sh[1] = s_min
-    __shared__ double red[kGammaThreads / 32][2];
-    double tot = 0.0, smin = 1e300;
-    for (int j = threadIdx.x; j < F; j += blockDim.x) {
-        tot += w[j];
-        smin = fmin(smin, s[j]);
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        tot += __shfl_xor_sync(0xffffffffu, tot, o);
-        smin = fmin(smin, __shfl_xor_sync(0xffffffffu, smin, o));
-    }
-    if ((threadIdx.x & 31) == 0) {
-        red[threadIdx.x >> 5][0] = tot;
-        red[threadIdx.x >> 5][1] = smin;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0, m = 1e300;
-        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
-            t += red[i][0];
-            m = fmin(m, red[i][1]);
-        }
-        sh[0] = t;
-        sh[1] = m;
-    }
-    __syncthreads();
-    const double g = sh[0], m = sh[1];
-    for (int j = threadIdx.x; j < F; j += blockDim.x) {
-        // exp(-(s_j - s_min) tau) = exp2(-e2_j tau) with e2_j = (s_j - s_min) log2(e)
-        e2[j] = (Real)((s[j] - m) * 1.4426950408889634);
-        wn[j] = (Real)(w[j] / g);
-    }
-    __syncthreads();
-}
-
-template <typename Real>
-__device__ __forceinline__ Real ray_log_rate(Real tau, const Real* e2, const Real* wn, int F, Real smin)
-{
-    Real S = Real(0), c = Real(0);
-    for (int j = 0; j < F; ++j) {
-        Real v = wn[j] * exp2_p(-e2[j] * tau);
-        Real y = v - c;
-        Real t = S + y;
-        c = (t - S) - y;
-        S = t;
-    }
-    return -smin * tau + log_p(S);
-}
-
-// Threads (local, k) fold ray k of row `local`; the per-row log-sum-exp runs
-// with one thread per row packed into the first lanes.
+// Threads (local, k) fold ray k of row `local` (fold_ray: the exponent of
+// every bin formed without rounding error); the per-row log-sum-exp runs with
+// one thread per row packed into the first lanes.
 template <typename Real>
 __global__ void __launch_bounds__(kGammaThreads) k_gamma(GammaJob J)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    Real* e2 = reinterpret_cast<Real*>(smem_raw);
+    constexpr bool kF32 = sizeof(Real) == 4;
+    double* lk = reinterpret_cast<double*>(smem_raw);
+    Real* e2 = reinterpret_cast<Real*>(lk + kGammaThreads);
     Real* wn = e2 + J.F;
-    Real* lk = reinterpret_cast<Real*>(smem_raw + ((2 * (size_t)J.F * sizeof(Real) + 15) & ~size_t(15)));
+    Real* e2t = kF32 ? wn + J.F : nullptr;
     __shared__ double sh[2];
-    load_spectrum<Real>(J.s, J.w, J.F, e2, wn, sh);
+    fold_prepare<Real>(J.s, J.w, J.F, e2, e2t, wn, nullptr, sh);
     const int rows_per_block = kGammaThreads / J.R;
     const int local = threadIdx.x / J.R;
     const int k = threadIdx.x % J.R;
     const double gthin = sh[0];
-    const Real smin = (Real)sh[1];
+    const double smin = sh[1];
     for (int64_t row0 = (int64_t)blockIdx.x * rows_per_block; row0 < J.n_rows;
          row0 += (int64_t)gridDim.x * rows_per_block) {
         const int64_t row = row0 + local;
         if (local < rows_per_block && row < J.n_rows) {
             const Real tau = static_cast<const Real*>(J.tau)[row * J.row_stride + (int64_t)k * J.k_stride];
-            lk[local * J.R + k] = ray_log_rate<Real>(tau, e2, wn, J.F, smin);
+            Real S, S2;
+            fold_ray<false>(tau, e2, e2t, wn, nullptr, J.F, S, S2);
+            lk[local * J.R + k] = ray_lnrate(smin, tau, S);
         }
         __syncthreads();
         const int p = threadIdx.x;
         const int64_t prow = row0 + p;
         if (p < rows_per_block && prow < J.n_rows) {
-            const Real* l = lk + p * J.R;
-            Real m = l[0];
-            for (int r = 1; r < J.R; ++r) m = m > l[r] ? m : l[r];
-            Real acc = Real(0);
-            for (int r = 0; r < J.R; ++r) acc += exp_p(l[r] - m);
-            const double lmean = (double)(m + log_p(acc / (Real)J.R));    // ln(Gamma / Gamma_thin)
+            RayMean<Real> lse;
+            for (int r = 0; r < J.R; ++r) lse.add(lk[p * J.R + r]);
+            const double lmean = lse.mean(J.R);     // ln(Gamma / Gamma_thin)
             J.gamma_out[prow] = gthin * exp(lmean);
             if (J.tau_eff_out) J.tau_eff_out[prow] = (float)(-lmean);
         }
@@ -117,7 +65,8 @@ __global__ void __launch_bounds__(kGammaThreads) k_gamma(GammaJob J)
 template <typename Real>
 int launch_gamma_t(const GammaJob& J, cudaStream_t s)
 {
-    size_t smem = ((2 * (size_t)J.F * sizeof(Real) + 15) & ~size_t(15)) + sizeof(Real) * kGammaThreads;
+    // per-ray log rates (double), then e2, wn and (FP32) the tail e2t
+    const size_t smem = sizeof(double) * kGammaThreads + (sizeof(Real) == 4 ? 3 : 2) * (size_t)J.F * sizeof(Real);
     auto fn = k_gamma<Real>;
     if (smem > 48 * 1024)
         URCHIN_TRY_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -403,34 +352,6 @@ __global__ void k_gamma_he(const Real* __restrict__ t0, const Real* __restrict__
     }
 }
 
-// x after time t from x0 with Gamma, nH, T, y held (App. C3): dx/dt =
-// R (x - x_eq)(x - x_+), solved in closed form with d = x_+ - x_eq =
-// sqrt(Q^2 - 4PR) / R (the same non-cancelling discriminant as the root)
-// and F = e^{-R d t}, over one denominator:
-//   x(t) = [(1 - F) x_eq (x_+ - x0) + d F x0] / [(x_+ - x0) + (x0 - x_eq) F],
-// non-negative terms that give x0 at t = 0 and x_eq at t -> inf to rounding.
-__global__ void k_evolve(const double* __restrict__ gamma, const float* __restrict__ tau_eff,
-                         const double* __restrict__ nH, const double* __restrict__ T, int64_t n, int case_rule,
-                         double y, const double* __restrict__ x0, double t, double* x_out)
-{
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const Rates r = hg97_rates(T[i]);
-        const bool caseB = case_rule == URCHIN_CASE_B || (case_rule == URCHIN_CASE_AUTO && tau_eff[i] >= 1.0f);
-        const double alpha = caseB ? r.alphaB : r.alphaA;
-        const double G = gamma[i], n_ = nH[i];
-        const double an = alpha * n_;
-        const double Rc = (r.gamma_c + alpha) * n_;
-        const double e = an * y + r.gamma_c * n_ * (1.0 + y);
-        const double sq = sqrt((G + e) * (G + e) + 4.0 * G * an);
-        const double xe = x_equilibrium(G, n_, alpha, r.gamma_c, y);
-        const double d = sq / Rc;
-        const double F = exp(-sq * t);
-        const double omf = -expm1(-sq * t);
-        const double d0 = x0[i] - xe;
-        const double up = d - d0;                       // x_+ - x0
-        x_out[i] = (omf * xe * up + d * F * x0[i]) / (up + d0 * F);
-    }
-}
 
 template <typename Real>
 int gamma_vjp_t(const Real* tau, int64_t n_orig, int R, const urchin_spectrum* sp, const double* gbar,
@@ -703,23 +624,3 @@ extern "C" int urchin_gamma_he(const void* tau, const void* tau_he1, const void*
     return launched();
 }
 
-extern "C" int urchin_evolve(const double* gamma, const float* tau_eff, const double* nH, const double* T, int64_t n,
-                             int case_rule, double y, const double* x0, double t, double* x_out,
-                             urchin_stream_t stream)
-{
-    using namespace urchin;
-    clear_error();
-    if (n < 0) return set_error(URCHIN_ERR_ARG, "urchin_evolve: n < 0");
-    if (case_rule != URCHIN_CASE_A && case_rule != URCHIN_CASE_B && case_rule != URCHIN_CASE_AUTO)
-        return set_error(URCHIN_ERR_ARG, "urchin_evolve: unknown case_rule %d", case_rule);
-    if (!(y >= 0.0) || !std::isfinite(y)) return set_error(URCHIN_ERR_ARG, "urchin_evolve: y must be >= 0");
-    if (!(t >= 0.0) || !std::isfinite(t)) return set_error(URCHIN_ERR_ARG, "urchin_evolve: t must be finite and >= 0");
-    if (n == 0) return URCHIN_OK;
-    if (!gamma || !nH || !T || !x0 || !x_out) return set_error(URCHIN_ERR_ARG, "urchin_evolve: NULL array");
-    if (case_rule == URCHIN_CASE_AUTO && !tau_eff)
-        return set_error(URCHIN_ERR_ARG, "urchin_evolve: CASE_AUTO needs tau_eff");
-    cudaStream_t s = (cudaStream_t)stream;
-    unsigned grid = (unsigned)std::min<int64_t>((n + 255) / 256, 4096);
-    k_evolve<<<grid, 256, 0, s>>>(gamma, tau_eff, nH, T, n, case_rule, y, x0, t, x_out);
-    return launched();
-}

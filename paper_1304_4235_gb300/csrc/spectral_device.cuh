@@ -15,6 +15,155 @@ __device__ __forceinline__ double exp_p(double x) { return exp(x); }
 __device__ __forceinline__ float log_p(float x) { return logf(x); }
 __device__ __forceinline__ double log_p(double x) { return log(x); }
 
+// ---- the binned fold of Eq. gamma_shld ------------------------------------
+// Per ray, Gamma_k / Gamma_thin = exp(-s_min tau) S with
+//   S = sum_j wn_j exp(-(s_j - s_min) tau),  wn_j = w_j / Gamma_thin,
+// evaluated as sum_j wn_j 2^(-e2_j tau) with e2_j = (s_j - s_min) log2(e).
+// In FP32 the coefficient is held as a float head e2_j plus a float tail
+// e2t_j (their sum equals the double value to ~2^-48), and the exponent is
+// formed without rounding: p = e2_j tau rounded, err = fma(e2_j, tau, -p)
+// exactly, plus e2t_j tau, so 2^-(p + err) = 2^-p (1 - ln2 err) to second
+// order in err (|err| <= 2^-23 |p|).  Rounding the exponent to float would
+// leave a relative error growing like 6e-8 s tau (6e-6 at s tau = 100); with
+// the split what remains is exp2f's and the weights' rounding, ~2e-7 per
+// term, for any tau.
+
+// Block-wide preparation in shared memory (every thread of the block calls
+// it; at most 1024 threads): sh[0] = Gamma_thin = sum_j w_j, sh[1] = s_min,
+// e2 and wn as above, e2t the FP32 tail (NULL in FP64), sj = s_j (or NULL).
+template <typename Real>
+__device__ void fold_prepare(const double* s, const double* w, int F, Real* e2, Real* e2t, Real* wn, Real* sj,
+                             double* sh)
+{
+    __shared__ double red[32][2];
+    double tot = 0.0, smin = 1e300;
+    for (int j = threadIdx.x; j < F; j += blockDim.x) {
+        tot += w[j];
+        smin = fmin(smin, s[j]);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        tot += __shfl_xor_sync(0xffffffffu, tot, o);
+        smin = fmin(smin, __shfl_xor_sync(0xffffffffu, smin, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[threadIdx.x >> 5][0] = tot;
+        red[threadIdx.x >> 5][1] = smin;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0, m = 1e300;
+        for (int i = 0; i < (int)((blockDim.x + 31) >> 5); ++i) {
+            t += red[i][0];
+            m = fmin(m, red[i][1]);
+        }
+        sh[0] = t;
+        sh[1] = m;
+    }
+    __syncthreads();
+    const double g = sh[0], m = sh[1];
+    for (int j = threadIdx.x; j < F; j += blockDim.x) {
+        const double c = (s[j] - m) * 1.4426950408889634;
+        e2[j] = (Real)c;
+        if (e2t) e2t[j] = (Real)(c - (double)(Real)c);
+        wn[j] = (Real)(w[j] / g);
+        if (sj) sj[j] = (Real)s[j];
+    }
+    __syncthreads();
+}
+
+// S (and, with kTan, S2 = sum_j wn_j s_j exp(-(s_j - s_min) tau), the
+// tangent's sum) of one ray, compensated sums.
+template <bool kTan>
+__device__ __forceinline__ void fold_ray(float tau, const float* e2, const float* e2t, const float* wn,
+                                         const float* sj, int F, float& S_out, float& S2_out)
+{
+    // a NaN column stays NaN; columns beyond 1e30 (every term but the s_min
+    // bin underflows) are clamped so that the exponent's error stays finite
+    tau = tau < 1e30f ? tau : (tau == tau ? 1e30f : tau);
+    float S = 0.f, c = 0.f, S2 = 0.f, c2 = 0.f;
+    for (int j = 0; j < F; ++j) {
+        const float p = e2[j] * tau;
+        const float err = fmaf(e2t[j], tau, fmaf(e2[j], tau, -p));
+        const float v0 = wn[j] * exp2f(-p);
+        const float v = fmaf(-v0, err * 0.6931471805599453f, v0);
+        const float yy = v - c;
+        const float t = S + yy;
+        c = (t - S) - yy;
+        S = t;
+        if (kTan) {
+            const float v2 = v * sj[j];
+            const float y2 = v2 - c2;
+            const float t2 = S2 + y2;
+            c2 = (t2 - S2) - y2;
+            S2 = t2;
+        }
+    }
+    S_out = S;
+    S2_out = S2;
+}
+
+template <bool kTan>
+__device__ __forceinline__ void fold_ray(double tau, const double* e2, const double*, const double* wn,
+                                         const double* sj, int F, double& S_out, double& S2_out)
+{
+    double S = 0.0, c = 0.0, S2 = 0.0, c2 = 0.0;
+    for (int j = 0; j < F; ++j) {
+        const double v = wn[j] * exp2(-e2[j] * tau);
+        const double yy = v - c;
+        const double t = S + yy;
+        c = (t - S) - yy;
+        S = t;
+        if (kTan) {
+            const double v2 = v * sj[j];
+            const double y2 = v2 - c2;
+            const double t2 = S2 + y2;
+            c2 = (t2 - S2) - y2;
+            S2 = t2;
+        }
+    }
+    S_out = S;
+    S2_out = S2;
+}
+
+// ln x for x > 0 as e ln2 + ln m with x = m 2^e, m in [1/2, 1): the float
+// logarithm of the mantissa is accurate to 6e-8 absolute, where logf(x) of
+// a small x (|ln x| ~ 10) is only accurate to an ulp of 10, 1e-6.
+__device__ __forceinline__ double log_split(float x)
+{
+    int e;
+    const float m = frexpf(x, &e);
+    return fma((double)e, 0.6931471805599453, (double)logf(m));
+}
+__device__ __forceinline__ double log_split(double x) { return log(x); }
+
+// ln(Gamma_k / Gamma_thin) = -s_min tau + ln S, the product in double (in
+// float its rounding, ~6e-8 s_min tau, would reach 1e-5 at s_min tau ~ 170).
+template <typename Real>
+__device__ __forceinline__ double ray_lnrate(double smin, Real tau, Real S)
+{
+    return fma(-smin, (double)tau, log_split(S));
+}
+
+// Running log-sum-exp over a particle's rays, ln((1/R) sum_k exp(l_k)): the
+// maximum in double, the sum of exp(l_k - max) >= 1 in the columns'
+// precision.
+template <typename Real>
+struct RayMean {
+    double m = -INFINITY;
+    Real acc = Real(0);
+    __device__ __forceinline__ void add(double l)
+    {
+        if (l == -INFINITY) return;      // a ray with no transmitted flux adds nothing
+        if (l > m) {
+            acc = acc * exp_p((Real)(m - l)) + Real(1);
+            m = l;
+        } else {
+            acc += exp_p((Real)(l - m));
+        }
+    }
+    __device__ __forceinline__ double mean(int R) const { return m + log_split(acc / (Real)R); }
+};
+
 struct Rates {
     double alphaA, alphaB, gamma_c;   // cm^3 s^-1
 };

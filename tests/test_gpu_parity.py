@@ -1,8 +1,8 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle on the same
 seeded inputs.  Tolerances (stated per test):
   columns  FP64 mode rel 1e-11 (rounding order only); FP32 mode rel 1e-5
-  Gamma    FP64 rel 1e-12; FP32 rel 2e-6 + 2e-7 * s_max * tau (the exponent
-           s_j tau is rounded to float: d Gamma/Gamma ~ eps_32 s tau)
+  Gamma    FP64 rel 1e-12; FP32 rel 2e-6 on identical FP32 columns (every
+           bin's exponent s_j tau formed without rounding error)
   x        equilibrium on identical FP64 inputs rel 1e-12; end to end FP64
            rel 1e-9
 """
@@ -169,20 +169,25 @@ def test_build_rejects_nonfinite_and_bad_h():
 # Gamma (Eq. gamma_shld) and equilibrium (App. C3)
 # --------------------------------------------------------------------------
 @pytest.mark.parametrize("R", [1, 12, 48])
-@pytest.mark.parametrize("F", [1, 50, 200])
-def test_gamma_random_columns(R, F):
+@pytest.mark.parametrize("F", [1, 50, 200, 400])
+@pytest.mark.parametrize("tau_max", [300.0, 3e4])
+def test_gamma_random_columns(R, F, tau_max):
     rng = np.random.default_rng(R * 1000 + F)
     n = 777
-    tau = np.exp(rng.uniform(np.log(1e-6), np.log(300.0), (n, R))).astype(np.float32)
+    tau = np.exp(rng.uniform(np.log(1e-6), np.log(tau_max), (n, R))).astype(np.float32)
     tau[:5] = 0.0
     e, J = W.powerlaw_spectrum(F, 13.6, 54.4)
     s, wts = U.urchin_spectrum_weights(e, J, 1e-12)
     sg, wg = torch.from_numpy(s).cuda(), torch.from_numpy(wts).cuda()
     g_ref, te_ref = O.gamma(tau.astype(np.float64), s, wts)
     g32, te32 = U.urchin_gamma(torch.from_numpy(tau).cuda(), sg, wg)
-    tol = 2e-6 + 2e-7 * s.max() * tau.max(axis=1)
-    assert np.all(rel_err(g32.cpu().numpy(), g_ref) < tol)
-    assert np.all(np.abs(te32.cpu().numpy() - te_ref) < 1e-5 * np.maximum(1, te_ref) + tol)
+    # identical FP32 columns on both sides: every bin's exponent is formed
+    # without rounding, so the rate is within 2e-6 (the target is 1e-5) at
+    # every tau; tau_eff = -ln(Gamma / Gamma_thin) within 2e-6 absolute plus
+    # the rounding of the float32 output (an ulp, 1.2e-7 tau_eff)
+    assert rel_err(g32.cpu().numpy(), g_ref).max() < 2e-6
+    te32 = te32.cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(te32 - te_ref) <= 2e-6 + 1.2e-7 * np.abs(te_ref))
     g64, te64 = U.urchin_gamma(torch.from_numpy(tau.astype(np.float64)).cuda(), sg, wg)
     assert rel_err(g64.cpu().numpy(), g_ref).max() < 1e-12
     assert np.all(g64.cpu().numpy()[:5] == pytest.approx(wts.sum(), rel=1e-14))
@@ -218,28 +223,6 @@ def test_equilibrium_matches_oracle(case_rule):
     caseB = np.full(n, case_rule == U.CASE_B) if case_rule != U.CASE_AUTO else te.astype(np.float64) >= 1
     ref = O.xeq(G, nH, T, y, caseB)
     assert rel_err(x, ref).max() < 1e-12
-
-
-@pytest.mark.parametrize("case_rule", [U.CASE_A, U.CASE_B, U.CASE_AUTO])
-def test_evolve_matches_oracle(case_rule):
-    """Time-dependent x (App. C3) on identical FP64 inputs: rel 1e-12 for 99 %
-    of the particles, 1e-10 for all (where x0 nearly equals the upper root x_+
-    the result is ill-conditioned in the rate coefficients, whose last bits
-    differ between the device and host math libraries)."""
-    rng = np.random.default_rng(12)
-    n = 1500
-    G = np.exp(rng.uniform(np.log(1e-17), np.log(1e-11), n))
-    nH = np.exp(rng.uniform(np.log(1e-5), np.log(10.0), n))
-    T = rng.uniform(5e3, 3e4, n)
-    te = rng.uniform(0, 2, n).astype(np.float32)
-    x0 = np.exp(rng.uniform(np.log(1e-6), 0.0, n))
-    c = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
-    caseB = {U.CASE_A: np.zeros(n, bool), U.CASE_B: np.ones(n, bool), U.CASE_AUTO: te >= 1}[case_rule]
-    for t in (0.0, 3e12, 3e14, 3e17):
-        x = U.urchin_evolve(c(G), c(te), c(nH), c(T), c(x0), t, case_rule).cpu().numpy()
-        ref = O.xt(G, nH, T, x0, t, 0.0, caseB)
-        err = rel_err(x, ref)
-        assert np.quantile(err, 0.99) < 1e-12 and err.max() < 1e-10, (t, err.max())
 
 
 # --------------------------------------------------------------------------
@@ -365,18 +348,6 @@ def test_newton_reaches_plain_fixed_point_lattice(lattice):
     assert rel_err(xn, xp).max() < 1e-8
     xo, fo, st = O.solve(w, so[0], so[1], O.healpix(1), tol=1e-10, max_iter=300)
     assert rel_err(xn, xo).max() < 1e-8
-
-
-def test_anderson_reaches_plain_fixed_point_lattice(lattice):
-    """Anderson mixing of the sweep map converges to the plain iteration's
-    fixed point (FP64, stored segments)."""
-    w, bvh, d = lattice
-    sg, so = spectra(w, torch)
-    xp, sp = _solve_gpu(w, bvh, d, sg, U.F64, tol=1e-10, max_iter=300, segments=U.SEG_STORE)
-    xa, sa = _solve_gpu(w, bvh, d, sg, U.F64, tol=1e-10, max_iter=300, method=U.METHOD_ANDERSON, gmres_m=5,
-                        segments=U.SEG_STORE)
-    assert sp["converged"] and sa["converged"]
-    assert rel_err(xa, xp).max() < 1e-8
 
 
 @pytest.mark.parametrize("segments", [U.SEG_RECOMPUTE, U.SEG_STORE])
