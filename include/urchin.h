@@ -72,7 +72,6 @@ typedef struct CUstream_st* urchin_stream_t;
 #define URCHIN_XSEC_HEII        3     /* He II: exact hydrogenic, Z = 2 (54.4 eV) */
 #define URCHIN_METHOD_PLAIN     0     /* Jacobi fixed point (Sec. 4)            */
 #define URCHIN_METHOD_NEWTON    1     /* Newton-Krylov on the same fixed point  */
-#define URCHIN_METHOD_ANDERSON  2     /* Anderson-accelerated sweeps            */
 
 /* Slab model for the near particles of the near/far split (Sec. 3.3.3) */
 #define URCHIN_SLAB_THRESHOLD   1     /* analytic slab, radiation at threshold   */
@@ -227,13 +226,21 @@ URCHIN_API int urchin_trace_columns(const urchin_bvh* bvh, const double* x, cons
  *   - Size limit: 256 + 24 R + (4 or 8) n + 4 n_orig bytes (each part
  *     rounded up to 256) must fit in the array; larger requests return
  *     URCHIN_ERR_ARG and leave everything untouched.
+ *   - The columns are bit for bit those of urchin_trace_columns (a ray sums
+ *     its hits in the tree's fixed depth-first order, whichever rays share
+ *     its warp), but the rays are traced in the order of the origin list:
+ *     the per-direction ray ordering that urchin_trace_columns sorts into
+ *     extra memory for 16384 or more origins is skipped, so large calls run
+ *     slower.
  *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) and caches it; make that first call before any
- *     stream capture.
+ *     (cudaGetSymbolAddress) and caches it per device ordinal; make that
+ *     first call before any stream capture.  The cache assumes the device
+ *     keeps one CUDA context for the life of the process (after
+ *     cudaDeviceReset it is stale).
  *   - Every call shares the one array and clears what must start at zero;
  *     calls whose work overlaps on the GPU (other streams, other host
  *     threads) race on it and must be serialised by the caller.
- *   - Like urchin_trace_columns it synchronises `stream` to read its status. */
+ *   - It synchronises `stream` before returning, to read its status word. */
 URCHIN_API int urchin_trace_columns_noalloc(const urchin_bvh* bvh, const double* x, const double* dirs, int R,
                                             double l_ray, const int32_t* origins, int64_t n_orig,
                                             int kernel, int precision, void* tau_out,
@@ -306,21 +313,6 @@ URCHIN_API int urchin_equilibrium(const double* gamma, const float* tau_eff, con
                        const double* T, int64_t n, int case_rule, double y,
                        double* x_out, urchin_stream_t stream);
 
-/* Time-dependent neutral fraction, App. C3: with Gamma, nH, T and y held
- * over a step t (seconds), dx/dt = R (x - x_eq)(x - x_+) (Eq. dxdt) has the
- * closed-form solution
- *   x(t) = x_eq + (x0 - x_eq)(x_+ - x_eq) F / [(x_+ - x0) + (x0 - x_eq) F],
- *   F = exp(-(x_+ - x_eq) t / t_rc),  t_rc = 1 / ((alpha + gamma_c) nH),
- * x_eq the equilibrium of urchin_equilibrium, x_+ the other root.  It is
- * evaluated over one denominator, [(1 - F) x_eq (x_+ - x0) + d F x0] /
- * [(x_+ - x0) + (x0 - x_eq) F] with d = x_+ - x_eq = sqrt(Q^2 - 4PR)/R,
- * which is exact at t = 0 and t -> inf to rounding.  Arguments
- * as urchin_equilibrium plus x0 (device [n], the start) and t >= 0; x_out
- * may alias x0.  Errors: ERR_ARG, ERR_CUDA. */
-URCHIN_API int urchin_evolve(const double* gamma, const float* tau_eff, const double* nH, const double* T,
-                             int64_t n, int case_rule, double y, const double* x0, double t, double* x_out,
-                             urchin_stream_t stream);
-
 typedef struct {
     int             R;            /* rays per particle                         */
     const double*   dirs;         /* host [R*3]                                */
@@ -335,8 +327,7 @@ typedef struct {
     int             max_iter;     /* sweep limit (plain) / Newton step limit   */
     int             method;       /* URCHIN_METHOD_*                           */
     int             segments;     /* URCHIN_SEG_*                              */
-    int             gmres_m;      /* Krylov dimension per Newton step, or the
-                                     history depth of Anderson acceleration    */
+    int             gmres_m;      /* Krylov dimension per Newton step          */
     int             kernel;       /* URCHIN_KERNEL_*                           */
     int             precision;    /* URCHIN_F32 / URCHIN_F64 (columns, Gamma)  */
     int             case_rule;    /* URCHIN_CASE_*                             */
@@ -426,10 +417,7 @@ typedef struct {
  * no near/far split, blocks <= 1) the fixed He I and He II columns of every
  * ray are traced once, with weights he1 / he2, and attenuate the spectrum in
  * every sweep.
- * URCHIN_METHOD_ANDERSON accelerates the sweeps themselves: each iteration
- * evaluates the sweep map once and combines it with the last gmres_m
- * iterates (Anderson mixing in ln x, restarted when the residual grows).  x_inout is
- * device [n] double in the original particle order.  `stats` may be NULL.
+ * x_inout is device [n] double in the original particle order.  `stats` may be NULL.
  * Synchronises `stream`.  Returns URCHIN_ERR_NOT_CONVERGED (x_inout then
  * holds the last iterate) when max_iter is reached first. */
 URCHIN_API int urchin_solve(const urchin_bvh* bvh, const urchin_solve_params* params,

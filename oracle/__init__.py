@@ -94,7 +94,6 @@ def _load():
                 "oracle_ns_slab": (d, [i, vp, vp, d, d, i, d, i64, vp]),
                 "oracle_ns_slab2": (d, [i, vp, vp, d, d, i, d, i64, d, i, vp]),
                 "oracle_xeq_dgamma": (d, [d, d, d, d, i]),
-                "oracle_xt": (d, [d, d, d, d, i, d, d]),
                 "oracle_column_matrix": (None, [i64, vp, vp, vp, vp, vp, i, d, d,
                                                 vp, i64, vp, i, d, i, vp]),
                 "oracle_num_threads": (i, []),
@@ -385,17 +384,6 @@ def gamma_partials(tau, s, w):
     dG_dtau = -(e * (w * s)[None, None, :]).sum(axis=2) / R
     dG_dw = e.sum(axis=1) / R
     return dG_dtau, dG_dw
-
-
-def xt(Gamma, nH, T, x0, t, y=0.0, caseB=False):
-    """Neutral fraction after time t from x0 at fixed Gamma, nH, T (App. C3)."""
-    lib = _load()
-    G, nH, T, x0, t, cb = np.broadcast_arrays(np.atleast_1d(np.asarray(Gamma, dtype=np.float64)),
-                                              np.asarray(nH, dtype=np.float64), np.asarray(T, dtype=np.float64),
-                                              np.asarray(x0, dtype=np.float64), np.asarray(t, dtype=np.float64),
-                                              np.asarray(caseB, dtype=bool))
-    return np.array([lib.oracle_xt(float(g), float(a), float(b), float(y), int(c), float(u), float(v))
-                     for g, a, b, u, v, c in zip(G, nH, T, x0, t, cb)])
 
 
 def xeq_dgamma(Gamma, nH, T, y=0.0, caseB=False):

@@ -212,6 +212,31 @@ double oracle_chord(int kernel, double b, double u1, double u2)
  * can reach the segment):
  *     N_HI = sum_j (m_j x_j / m_p) int_0^L W(|r(t) - r_j| / h_j) dt.
  * Lengths are in the caller's unit; unit_cm converts them to cm. */
+/* Term of particle j, shifted by (sx, sy, sz) (a periodic image offset, or
+ * zero), in the column of the segment o + t dir, t in [0, l_ray], before
+ * the factor sigma_th: (m_j x_j / m_p) (8/pi) / (h_j unit_cm)^2 times the
+ * chord integral of the kernel; 0 when the segment misses the sphere. */
+static double pair_term(double pxj, double pyj, double pzj, double hj, double mxj, double sx, double sy,
+                        double sz, double unit_cm, const double* o, const double* dir, double l_ray, int kernel)
+{
+    double dx = pxj + sx - o[0];
+    double dy = pyj + sy - o[1];
+    double dz = pzj + sz - o[2];
+    double tc = dx * dir[0] + dy * dir[1] + dz * dir[2];
+    /* impact parameter from |d x dir| */
+    double cx = dy * dir[2] - dz * dir[1];
+    double cy = dz * dir[0] - dx * dir[2];
+    double cz = dx * dir[1] - dy * dir[0];
+    double b2 = cx * cx + cy * cy + cz * cz;
+    if (b2 >= hj * hj) return 0.0;
+    double half = sqrt(hj * hj - b2);
+    double t1 = fmax(0.0, tc - half), t2 = fmin(l_ray, tc + half);
+    if (t2 <= t1) return 0.0;
+    double F = oracle_chord(kernel, sqrt(b2) / hj, (t1 - tc) / hj, (t2 - tc) / hj);
+    double hcm = hj * unit_cm;
+    return mxj * (8.0 / OR_PI) / (hcm * hcm) * F;
+}
+
 static double column_from_point(int64_t n, const double* px, const double* py, const double* pz,
                                 const double* h, const double* mass_H, const double* x,
                                 int periodic, double L, double unit_cm, int nimg,
@@ -219,27 +244,11 @@ static double column_from_point(int64_t n, const double* px, const double* py, c
 {
     double sum = 0.0;
     for (int64_t j = 0; j < n; ++j) {
-        double hj = h[j];
         for (int a = -nimg; a <= nimg; ++a)
         for (int bb = -nimg; bb <= nimg; ++bb)
-        for (int c = -nimg; c <= nimg; ++c) {
-            double dx = px[j] + (periodic ? a * L : 0.0) - o[0];
-            double dy = py[j] + (periodic ? bb * L : 0.0) - o[1];
-            double dz = pz[j] + (periodic ? c * L : 0.0) - o[2];
-            double tc = dx * dir[0] + dy * dir[1] + dz * dir[2];
-            /* impact parameter from |d x dir| */
-            double cx = dy * dir[2] - dz * dir[1];
-            double cy = dz * dir[0] - dx * dir[2];
-            double cz = dx * dir[1] - dy * dir[0];
-            double b2 = cx * cx + cy * cy + cz * cz;
-            if (b2 >= hj * hj) continue;
-            double half = sqrt(hj * hj - b2);
-            double t1 = fmax(0.0, tc - half), t2 = fmin(l_ray, tc + half);
-            if (t2 <= t1) continue;
-            double F = oracle_chord(kernel, sqrt(b2) / hj, (t1 - tc) / hj, (t2 - tc) / hj);
-            double hcm = hj * unit_cm;
-            sum += mass_H[j] * x[j] * (8.0 / OR_PI) / (hcm * hcm) * F;
-        }
+        for (int c = -nimg; c <= nimg; ++c)
+            sum += pair_term(px[j], py[j], pz[j], h[j], mass_H[j] * x[j], periodic ? a * L : 0.0,
+                             periodic ? bb * L : 0.0, periodic ? c * L : 0.0, unit_cm, o, dir, l_ray, kernel);
     }
     return oracle_sigma_th() * sum;
 }
@@ -479,35 +488,6 @@ double oracle_xeq(double Gamma, double nH, double T, double y, int caseB)
     double excess = alpha * nH * y + gc * nH * (1.0 + y);
     double disc = (Gamma + excess) * (Gamma + excess) + 4.0 * Gamma * alpha * nH;
     return 2.0 * P / (-Q + sqrt(disc));
-}
-
-/* Time-dependent neutral fraction (App. C3): with T, nH, y and Gamma held,
- * dx/dt = R (x - x_eq)(x - x_+) and
- *   x(t) = x_eq + (x0 - x_eq)(x_+ - x_eq) F / [(x_+ - x0) + (x0 - x_eq) F],
- *   F = exp(-(x_+ - x_eq) t / t_rc),  t_rc = 1 / ((alpha + gamma) nH),
- * x_eq = x_- the physical root (oracle_xeq).  From Eq. xroots the roots
- * differ by d = x_+ - x_- = sqrt(Q^2 - 4PR) / R, taken with the
- * discriminant in its non-cancelling form (as in oracle_xeq); subtracting
- * the two roots directly loses d when x_+ and x_eq both approach 1
- * (neutral, cold gas).  The closed form is evaluated over one denominator,
- *   x(t) = [(1 - F) x_eq (x_+ - x0) + d F x0] / [(x_+ - x0) + (x0 - x_eq) F],
- * a sum of non-negative terms that gives x0 at t = 0 and x_eq as t -> inf
- * to rounding (x_eq + (x0 - x_eq) ... loses x0 << x_eq at small t). */
-double oracle_xt(double Gamma, double nH, double T, double y, int caseB, double x0, double t)
-{
-    double aA, aB, gc;
-    oracle_rates(T, &aA, &aB, &gc);
-    double alpha = caseB ? aB : aA;
-    double R = (gc + alpha) * nH;
-    double excess = alpha * nH * y + gc * nH * (1.0 + y);
-    double disc = (Gamma + excess) * (Gamma + excess) + 4.0 * Gamma * alpha * nH;
-    double d = sqrt(disc) / R;                     /* x_+ - x_eq */
-    double xeq = oracle_xeq(Gamma, nH, T, y, caseB);
-    double F = exp(-d * t * R);
-    double omf = -expm1(-d * t * R);               /* 1 - F */
-    double d0 = x0 - xeq;
-    double up = d - d0;                            /* x_+ - x0 */
-    return (omf * xeq * up + d * F * x0) / (up + d0 * F);
 }
 
 /* d x_- / d Gamma by implicit differentiation of f(x, Gamma) = R x^2 + Q x + P

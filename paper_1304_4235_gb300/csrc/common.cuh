@@ -231,6 +231,11 @@ struct SpecTable;
 size_t spec_table_bytes();
 int build_spec_table(const double* s, const double* w, int F, void* buf, SpecTable* out, cudaStream_t st);
 
+// Origins (original particle indices) to Morton slots: items[o] =
+// inv[origins[o]]; an index outside [0, n) sets kStOrigin in *status.
+int launch_map_origins(const urchin_bvh* bvh, const int32_t* origins, int64_t n_orig, int32_t* items,
+                       unsigned* status, cudaStream_t s);
+
 // w = A * x gathered into Morton order: w[s] = A[s] * x[perm[s]]
 int launch_weights(const urchin_bvh* bvh, const double* x_orig, float* w32, double* w64,
                    cudaStream_t s);

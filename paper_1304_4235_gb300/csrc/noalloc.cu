@@ -1,16 +1,20 @@
 // urchin_trace_columns_noalloc: column tracing for callers that cannot
-// allocate device memory.  It computes exactly what urchin_trace_columns
-// computes, but its work arrays (the traversal's work-queue counter and
-// status word, the ray directions, the per-particle tracer weights and the
-// mapped origin list) live in one fixed array in this file instead of coming
-// from the stream-ordered allocator.
+// allocate device memory.  It gives the same columns as urchin_trace_columns
+// (bit for bit: a ray sums its hits in the tree's fixed depth-first order,
+// whichever rays share its warp), but its work arrays (the traversal's
+// work-queue counter and status word, the ray directions, the per-particle
+// tracer weights and the mapped origin list) live in one fixed array in this
+// file instead of coming from the stream-ordered allocator.  It traces the
+// rays in the order of the origin list, without the per-direction ray
+// ordering that the allocating call sorts into extra memory for large
+// origin sets, so calls with many origins run slower.
 //
 // The array is a file-scope __device__ variable, so every GPU that loads the
 // library holds it until the process exits.  Host code cannot use the
 // array's name as a device address; the address is looked up once per
 // device with cudaGetSymbolAddress (on the first call made on that device)
-// and cached.
-#include <algorithm>
+// and cached, which assumes the device keeps the same CUDA context for the
+// life of the process (after cudaDeviceReset the cached address is stale).
 #include <cmath>
 #include <mutex>
 
@@ -43,22 +47,6 @@ int scratch_address(void** out)
     }
     *out = g_scratch_addr[dev];
     return URCHIN_OK;
-}
-
-// origins (original indices) -> Morton slots; bad indices flag the status
-__global__ void k_map_origins_fixed(const int32_t* __restrict__ origins, const int32_t* __restrict__ inv,
-                                    int64_t n_orig, int64_t n, int32_t* items, unsigned* status)
-{
-    for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < n_orig;
-         o += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t i = origins[o];
-        if (i < 0 || i >= n) {
-            atomicOr(status, kStOrigin);
-            items[o] = 0;
-        } else {
-            items[o] = inv[i];
-        }
-    }
 }
 
 }  // namespace
@@ -132,9 +120,7 @@ extern "C" int urchin_trace_columns_noalloc(const urchin_bvh* bvh, const double*
     job.status = ctr + 1;
     if (origins) {
         int32_t* items = reinterpret_cast<int32_t*>(scr + o_items);
-        const unsigned grid = (unsigned)std::min<int64_t>((n_orig + 255) / 256, 4096);
-        k_map_origins_fixed<<<grid, 256, 0, s>>>(origins, bvh->inv, n_orig, n, items, ctr + 1);
-        URCHIN_TRY(launched());
+        URCHIN_TRY(launch_map_origins(bvh, origins, n_orig, items, ctr + 1, s));
         job.items = items;
         job.out_row = nullptr;
     } else {

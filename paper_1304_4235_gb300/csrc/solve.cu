@@ -68,44 +68,6 @@ __device__ __forceinline__ void atomic_max_pos(unsigned long long* addr, double 
     atomicMax(addr, (unsigned long long)__double_as_longlong(v));
 }
 
-template <typename Real>
-__device__ void sweep_spectrum(const double* s, const double* w, int F, Real* e2, Real* e2s, Real* wn,
-                               double* sh)
-{
-    __shared__ double red[kSweepThreads / 32][2];
-    double tot = 0.0, smin = 1e300;
-    for (int j = threadIdx.x; j < F; j += blockDim.x) {
-        tot += w[j];
-        smin = fmin(smin, s[j]);
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        tot += __shfl_xor_sync(0xffffffffu, tot, o);
-        smin = fmin(smin, __shfl_xor_sync(0xffffffffu, smin, o));
-    }
-    if ((threadIdx.x & 31) == 0) {
-        red[threadIdx.x >> 5][0] = tot;
-        red[threadIdx.x >> 5][1] = smin;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0, m = 1e300;
-        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
-            t += red[i][0];
-            m = fmin(m, red[i][1]);
-        }
-        sh[0] = t;
-        sh[1] = m;
-    }
-    __syncthreads();
-    const double g = sh[0], m = sh[1];
-    for (int j = threadIdx.x; j < F; j += blockDim.x) {
-        e2[j] = (Real)((s[j] - m) * 1.4426950408889634);
-        wn[j] = (Real)(w[j] / g);
-        if (e2s) e2s[j] = (Real)s[j];
-    }
-    __syncthreads();
-}
-
 // The per-particle end of a sweep, from ln(Gamma/Gamma_thin) of item prow:
 // the freeze decision (sweep 0), the recombination case (latched at
 // tau_eff >= 1), the FP64 equilibrium root and the convergence counters, then
@@ -181,52 +143,37 @@ __device__ __forceinline__ void sweep_counters(const SweepArgs& A, double my_max
 }
 
 // The plain sweep without tangent, one thread per particle: its R rays are
-// folded in turn (Eq. gamma_shld, in the columns' precision) with a running
-// log-sum-exp over the rays, then every lane takes its particle's FP64 update
-// at once (the ray-parallel layout of k_sweep leaves all but one warp of the
-// block idle during the FP64 part).
+// folded in turn (Eq. gamma_shld, fold_ray) with a running log-sum-exp over
+// the rays, then every lane takes its particle's FP64 update at once (the
+// ray-parallel layout of k_sweep leaves all but one warp of the block idle
+// during the FP64 part).
 template <typename Real>
 __global__ void __launch_bounds__(kSweepThreads) k_sweep_pp(SweepArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr bool kF32 = sizeof(Real) == 4;
     Real* e2 = reinterpret_cast<Real*>(smem_raw);
     Real* wn = e2 + A.F;
+    Real* e2t = kF32 ? wn + A.F : nullptr;
     __shared__ double sh[2];
-    sweep_spectrum<Real>(A.s, A.w, A.F, e2, nullptr, wn, sh);
+    fold_prepare<Real>(A.s, A.w, A.F, e2, e2t, wn, nullptr, sh);
     const double gthin = sh[0];
-    const Real smin = (Real)sh[1];
+    const double smin = sh[1];
     const Real* tau = static_cast<const Real*>(A.tau);
     double my_max = 0.0;
     unsigned long long my_above = 0, my_switch = 0;
     unsigned err = 0;
     for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < A.n_items;
          row += (int64_t)gridDim.x * blockDim.x) {
-        Real m = Real(0), acc = Real(0);
+        RayMean<Real> lse;
         for (int k = 0; k < A.R; ++k) {
             const Real t = tau[row + (int64_t)k * A.k_stride];
-            Real S = Real(0), c = Real(0);
-            for (int j = 0; j < A.F; ++j) {
-                const Real v = wn[j] * exp2_p(-e2[j] * t);
-                const Real yy = v - c;
-                const Real u = S + yy;
-                c = (u - S) - yy;
-                S = u;
-            }
-            // ln(Gamma_k / Gamma_thin) = -s_min tau_k + ln S_k, summed as exp(l - max)
-            const Real l = -smin * t + log_p(S);
-            if (k == 0) {
-                m = l;
-                acc = Real(1);
-            } else if (l > m) {
-                acc = acc * exp_p(m - l) + Real(1);
-                m = l;
-            } else {
-                acc += exp_p(l - m);
-            }
+            Real S, S2;
+            fold_ray<false>(t, e2, e2t, wn, nullptr, A.F, S, S2);
+            lse.add(ray_lnrate(smin, t, S));
         }
         double xn, G, alpha;
-        particle_update(A, row, (double)(m + log_p(acc / (Real)A.R)), gthin, &xn, &G, &alpha, my_max, my_above,
-                        my_switch, err);
+        particle_update(A, row, lse.mean(A.R), gthin, &xn, &G, &alpha, my_max, my_above, my_switch, err);
     }
     sweep_counters(A, my_max, my_above, my_switch, err);
 }
@@ -249,17 +196,19 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs A)
 {
     constexpr bool kHe = VAR == kSweepHelium;
     constexpr bool kNF = VAR == kSweepNearFar;
+    constexpr bool kF32 = sizeof(Real) == 4;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    Real* e2 = reinterpret_cast<Real*>(smem_raw);
+    // per-ray log rates in double, then the spectrum arrays (sweep_smem_bytes)
+    double* lk = reinterpret_cast<double*>(smem_raw);
+    double* lk2 = lk + kSweepThreads;
+    Real* e2 = reinterpret_cast<Real*>(lk2 + kSweepThreads);
     Real* wn = e2 + A.F;
     Real* sj = wn + A.F;
-    Real* sh1 = sj + A.F;                       // helium cross sections (kHe)
+    Real* e2t = kF32 ? sj + A.F : nullptr;
+    Real* sh1 = sj + (kF32 ? 2 : 1) * A.F;      // helium cross sections (kHe)
     Real* sh2 = sh1 + A.F;
-    const int narr = kHe ? 5 : 3;
-    Real* lk = reinterpret_cast<Real*>(smem_raw + ((narr * (size_t)A.F * sizeof(Real) + 15) & ~size_t(15)));
-    Real* lk2 = lk + kSweepThreads;
     __shared__ double sh[2];
-    sweep_spectrum<Real>(A.s, A.w, A.F, e2, (A.want_tangent || kHe) ? sj : nullptr, wn, sh);
+    fold_prepare<Real>(A.s, A.w, A.F, e2, e2t, wn, (A.want_tangent || kHe) ? sj : nullptr, sh);
     if (kHe) {
         for (int j = threadIdx.x; j < A.F; j += blockDim.x) {
             sh1[j] = (Real)A.s_he1[j];
@@ -271,7 +220,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs A)
     const int local = threadIdx.x / A.R;
     const int k = threadIdx.x % A.R;
     const double gthin = sh[0];
-    const Real smin = (Real)sh[1];
+    const double smin = sh[1];
     double my_max = 0.0;
     unsigned long long my_above = 0, my_switch = 0;
     unsigned err = 0;
@@ -280,25 +229,15 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs A)
         const int64_t row = row0 + local;
         if (local < rows_per_block && row < A.n_items) {
             const Real tau = static_cast<const Real*>(A.tau)[row + (int64_t)k * A.k_stride];
-            Real S = Real(0), c = Real(0), S2 = Real(0), c2 = Real(0);
             // (near/far: tau is the far column; the slab of near particles is applied below)
-            const int nspec = ((kNF && A.near_far == URCHIN_SLAB_SPECTRUM) || kHe) ? 0 : A.F;
-            for (int j = 0; j < nspec; ++j) {
-                const Real v = wn[j] * exp2_p(-e2[j] * tau);
-                const Real yy = v - c;
-                const Real t = S + yy;
-                c = (t - S) - yy;
-                S = t;
-                if (A.want_tangent) {
-                    const Real v2 = v * sj[j];
-                    const Real y2 = v2 - c2;
-                    const Real t2 = S2 + y2;
-                    c2 = (t2 - S2) - y2;
-                    S2 = t2;
-                }
+            const bool fold = !((kNF && A.near_far == URCHIN_SLAB_SPECTRUM) || kHe);
+            Real S = Real(0), S2 = Real(0);
+            if (fold) {
+                if (A.want_tangent) fold_ray<true>(tau, e2, e2t, wn, sj, A.F, S, S2);
+                else fold_ray<false>(tau, e2, e2t, wn, nullptr, A.F, S, S2);
             }
             // ln(Gamma_k / Gamma_thin) = -s_min tau_k + ln S_k
-            Real lkv = nspec ? -smin * tau + log_p(S) : Real(0);
+            double lkv = fold ? ray_lnrate(smin, tau, S) : 0.0;
             if (kHe) {
                 // H I, He I and He II columns: E_j = s_j tau + s1_j tau1 + s2_j tau2, the
                 // smallest E_j factored out of the sum
@@ -318,7 +257,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs A)
                     ch = (t - Sh) - yy;
                     Sh = t;
                 }
-                lkv = -emin + log_p(Sh);
+                lkv = -(double)emin + (double)log_p(Sh);
             }
             if (kNF) {
                 // Eq. gammashldk: the far radiation enters the slab of near particles, in
@@ -333,36 +272,33 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs A)
                 const double lnR = log((double)A.R);
                 if (A.near_far == URCHIN_SLAB_SPECTRUM)
                     // FP32 sweep: the slab's table and x_eq in FP32 (slab_poly_lnratio32)
-                    lkv = (Real)((sizeof(Real) == 4
-                                      ? slab_poly_lnratio32(A.poly, gthin, (double)tau, tn, A.nH[ir], al, A.gc[ir], -lnR)
-                                      : slab_poly_lnratio(A.poly, gthin, (double)tau, tn, A.nH[ir], al, A.gc[ir], -lnR)) +
-                                 lnR);
+                    lkv = (kF32 ? slab_poly_lnratio32(A.poly, gthin, (double)tau, tn, A.nH[ir], al, A.gc[ir], -lnR)
+                                : slab_poly_lnratio(A.poly, gthin, (double)tau, tn, A.nH[ir], al, A.gc[ir], -lnR)) +
+                          lnR;
                 else
-                    lkv = (Real)(slab_lnratio((double)lkv - lnR, gthin, tn, A.nH[ir], al, A.gc[ir]) + lnR);
+                    lkv = slab_lnratio(lkv - lnR, gthin, tn, A.nH[ir], al, A.gc[ir]) + lnR;
             }
             lk[local * A.R + k] = lkv;
-            if (A.want_tangent) lk2[local * A.R + k] = -smin * tau + log_p(S2 > Real(1e-37) ? S2 : Real(1e-37));
+            if (A.want_tangent) lk2[local * A.R + k] = ray_lnrate(smin, tau, S2 > Real(1e-37) ? S2 : Real(1e-37));
         }
         __syncthreads();
         const int p = threadIdx.x;
         const int64_t prow = row0 + p;
         if (p < rows_per_block && prow < A.n_items) {
-            const Real* l = lk + p * A.R;
-            Real m = l[0];
-            for (int r = 1; r < A.R; ++r) m = m > l[r] ? m : l[r];
-            Real acc = Real(0);
-            for (int r = 0; r < A.R; ++r) acc += exp_p(l[r] - m);
-            const Real lmean_r = m + log_p(acc / (Real)A.R);     // ln(Gamma/Gamma_thin)
+            const double* l = lk + p * A.R;
+            RayMean<Real> lse;
+            for (int r = 0; r < A.R; ++r) lse.add(l[r]);
+            const double lmean_r = lse.mean(A.R);     // ln(Gamma/Gamma_thin)
             double xn, G, alpha;
-            const int32_t i = particle_update(A, prow, (double)lmean_r, gthin, &xn, &G, &alpha, my_max, my_above,
+            const int32_t i = particle_update(A, prow, lmean_r, gthin, &xn, &G, &alpha, my_max, my_above,
                                               my_switch, err);
             if (i >= 0 && A.xeq_out && A.want_tangent) {
                 // elasticity Gamma dE/dGamma / E and per-ray dGamma/dtau_k / Gamma
                 const double dEdG = dx_dgamma(xn, A.nH[i], alpha, A.gc[i], G, A.y);
                 const double elas = (G > 0.0) ? G * dEdG / xn : 0.0;
-                const Real* l2 = lk2 + p * A.R;
+                const double* l2 = lk2 + p * A.R;
                 for (int r = 0; r < A.R; ++r) {
-                    const double dlog = (double)exp_p(l2[r] - lmean_r) / (double)A.R;
+                    const double dlog = (double)exp_p((Real)(l2[r] - lmean_r)) / (double)A.R;
                     A.ctan[prow + (int64_t)r * A.k_stride] = -elas * dlog;
                 }
             }
@@ -500,36 +436,6 @@ __global__ void k_tangent_out(const int32_t* __restrict__ perm, const double* __
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
         dlnE_out[perm[s]] = vm[s] - jv[s];
         if (E_out) E_out[perm[s]] = E[s];
-    }
-}
-
-// Anderson mixing: f = ln E - ln x (residual), g = ln E (map) on the active set
-__global__ void k_aa_fg(const int32_t* __restrict__ items, int64_t n_act, const double* __restrict__ x,
-                        const double* __restrict__ E, double* f, double* g)
-{
-    for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < n_act; a += (int64_t)gridDim.x * blockDim.x) {
-        const double lg = log(E[a]);
-        g[a] = lg;
-        f[a] = lg - log(x[items[a]]);
-    }
-}
-
-// x = exp(u), u kept within a factor e of the plain update g (and x <= 1);
-// refresh the tracer weights and x copies
-__global__ void k_set_x_from_u(const int32_t* __restrict__ items, int64_t n_act, const double* __restrict__ u,
-                               const double* __restrict__ g, double* x, const double* __restrict__ A64, float* w32,
-                               double* w64, float* xs32, double* xs64)
-{
-    for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < n_act; a += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t i = items[a];
-        const double ua = fmin(fmax(u[a], g[a] - 1.0), g[a] + 1.0);
-        const double xn = fmin(1.0, exp(ua));
-        x[i] = xn;
-        const double wv = A64[i] * xn;
-        if (w32) w32[i] = (float)wv;
-        if (w64) w64[i] = wv;
-        if (xs32) xs32[i] = (float)xn;
-        if (xs64) xs64[i] = xn;
     }
 }
 
@@ -688,7 +594,8 @@ int launch_sweep(const SweepArgs& A, cudaStream_t s)
     // plain sweeps without tangent: one thread per particle (0.152 ms against
     // 0.184 ms per sweep of the 262144-particle halo for the ray-parallel layout)
     if (!A.he && !A.near_far && !A.want_tangent) {
-        const size_t sm = 2 * (size_t)A.F * rsz;
+        // e2, wn and (FP32) the tail e2t
+        const size_t sm = (A.precision == URCHIN_F64 ? 2 : 3) * (size_t)A.F * rsz;
         const void* fp = A.precision == URCHIN_F64 ? (const void*)k_sweep_pp<double> : (const void*)k_sweep_pp<float>;
         if (sm > 48 * 1024)
             URCHIN_TRY_CUDA(cudaFuncSetAttribute(fp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
@@ -700,8 +607,9 @@ int launch_sweep(const SweepArgs& A, cudaStream_t s)
         URCHIN_TRY_CUDA(cudaLaunchKernel(fp, dim3(g), dim3(kSweepThreads), args, sm, s));
         return launched();
     }
-    size_t smem = (((A.he ? 5 : 3) * (size_t)A.F * rsz + 15) & ~size_t(15)) + 2 * rsz * kSweepThreads;
     const bool f64 = A.precision == URCHIN_F64;
+    // two per-ray log-rate arrays in double, then e2, wn, s, (FP32) e2t and (helium) s1, s2
+    const size_t smem = 2 * sizeof(double) * kSweepThreads + ((f64 ? 3 : 4) + (A.he ? 2 : 0)) * (size_t)A.F * rsz;
     const int var = A.he ? kSweepHelium : (A.near_far ? kSweepNearFar : kSweepPlain);
     const void* fns[2][3] = {
         {(const void*)k_sweep<float, kSweepPlain>, (const void*)k_sweep<float, kSweepNearFar>,
@@ -1504,131 +1412,6 @@ int Solver::newton()
     return URCHIN_OK;
 }
 
-// Anderson acceleration of the sweep map in u = ln x (Walker & Ni 2011 form):
-// with f_k = g(u_k) - u_k, g = ln E(Gamma(e^u)), and the last m differences
-// dF_i = f_{i+1} - f_i, dG_i = g_{i+1} - g_i, the next iterate is
-// u_{k+1} = g_k - sum_i gamma_i dG_i with gamma = argmin ||f_k - dF gamma||_2
-// (normal equations, Tikhonov-regularised), each u kept within a factor e of
-// g.  The history restarts when ||f|| grows by more than a factor 2 or a
-// recombination case switches.  Blocks do not apply: every evaluation
-// updates all non-frozen particles at once.  The stop
-// test and final update are the plain sweep's (x <- E when max |E - x|/x <
-// tol).  Every evaluation of the sweep map counts as one iteration.
-int Solver::anderson()
-{
-    URCHIN_TRY(first_sweep());
-    if (stats.max_rel_dx < P.tol || n_act == 0) {
-        stats.converged = 1;
-        return URCHIN_OK;
-    }
-    const int m = P.gmres_m;
-    const int64_t na = n_act;
-    Layout lay;
-    size_t o_dF = lay.take(sizeof(double) * (size_t)m * na);
-    size_t o_dG = lay.take(sizeof(double) * (size_t)m * na);
-    size_t o_f = lay.take(sizeof(double) * (size_t)na);
-    size_t o_g = lay.take(sizeof(double) * (size_t)na);
-    size_t o_fp = lay.take(sizeof(double) * (size_t)na);
-    size_t o_gp = lay.take(sizeof(double) * (size_t)na);
-    size_t o_E = lay.take(sizeof(double) * (size_t)na);
-    size_t o_V = lay.take(sizeof(double) * (size_t)na);
-    size_t o_dt = lay.take(dots_tmp_bytes(m + 1));
-    size_t o_h = lay.take(sizeof(double) * (size_t)(m + 2));
-    URCHIN_TRY(nk.alloc(lay.bytes, s));
-    double* dF = nk.at<double>(o_dF);
-    double* dG = nk.at<double>(o_dG);
-    double* f = nk.at<double>(o_f);
-    double* g = nk.at<double>(o_g);
-    double* fp = nk.at<double>(o_fp);
-    double* gp = nk.at<double>(o_gp);
-    double* E = nk.at<double>(o_E);
-    double* V0 = nk.at<double>(o_V);
-    double* dtmp = nk.at<double>(o_dt);
-    double* hdev = nk.at<double>(o_h);
-    const unsigned g1 = (unsigned)std::max<int64_t>(1, std::min<int64_t>((na + 255) / 256, 2048));
-    int hist = 0, head = 0;                         // valid history columns, next slot
-    double mrel = 0.0, norm = 0.0, prev_norm = -1.0;
-    int64_t sw = 0;
-    std::vector<double> M((size_t)m * m), rhs(m), gam(m);
-    URCHIN_TRY(evaluate(0, V0, E, nullptr, dtmp, hdev, &mrel, &norm, &sw, 0));
-    for (;;) {
-        if (mrel < P.tol || stats.iterations >= P.max_iter) {
-            k_set_x<<<g1, 256, 0, s>>>(list, na, nullptr, 0.0, nullptr, E, x, bvh->A64, w32, w64, xs32, xs64);
-            URCHIN_TRY(launched());
-            if (mrel < P.tol) stats.converged = 1;
-            break;
-        }
-        k_aa_fg<<<g1, 256, 0, s>>>(list, na, x, E, f, g);
-        URCHIN_TRY(launched());
-        if (prev_norm >= 0.0 && (norm > 2.0 * prev_norm || sw > 0)) {
-            hist = 0;                               // restart the history
-            head = 0;
-            stats.newton_fallbacks += 1;
-        } else if (prev_norm >= 0.0) {
-            double* dFs = dF + (size_t)head * na;
-            double* dGs = dG + (size_t)head * na;
-            URCHIN_TRY_CUDA(cudaMemcpyAsync(dFs, f, sizeof(double) * (size_t)na, cudaMemcpyDeviceToDevice, s));
-            URCHIN_TRY(launch_axpby(-1.0, fp, 1.0, dFs, na, s));
-            URCHIN_TRY_CUDA(cudaMemcpyAsync(dGs, g, sizeof(double) * (size_t)na, cudaMemcpyDeviceToDevice, s));
-            URCHIN_TRY(launch_axpby(-1.0, gp, 1.0, dGs, na, s));
-            head = (head + 1) % m;
-            hist = std::min(hist + 1, m);
-        }
-        URCHIN_TRY_CUDA(cudaMemcpyAsync(fp, f, sizeof(double) * (size_t)na, cudaMemcpyDeviceToDevice, s));
-        URCHIN_TRY_CUDA(cudaMemcpyAsync(gp, g, sizeof(double) * (size_t)na, cudaMemcpyDeviceToDevice, s));
-        prev_norm = norm;
-        if (hist > 0) {
-            // normal equations (dF^T dF + mu I) gamma = dF^T f over the valid slots 0..hist-1
-            for (int j = 0; j < hist; ++j) {
-                URCHIN_TRY(launch_dots(dF, na, hist, dF + (size_t)j * na, na, dtmp, hdev, s));
-                URCHIN_TRY_CUDA(cudaMemcpyAsync(M.data() + (size_t)j * m, hdev, sizeof(double) * hist,
-                                                cudaMemcpyDeviceToHost, s));
-            }
-            URCHIN_TRY(launch_dots(dF, na, hist, f, na, dtmp, hdev, s));
-            URCHIN_TRY_CUDA(cudaMemcpyAsync(rhs.data(), hdev, sizeof(double) * hist, cudaMemcpyDeviceToHost, s));
-            URCHIN_TRY_CUDA(cudaStreamSynchronize(s));
-            double tr = 0.0;
-            for (int j = 0; j < hist; ++j) tr += M[(size_t)j * m + j];
-            const double mu = 1e-10 * (tr > 0.0 ? tr : 1.0);
-            std::vector<double> Aq((size_t)hist * hist), bq(rhs.begin(), rhs.begin() + hist);
-            for (int r = 0; r < hist; ++r)
-                for (int c = 0; c < hist; ++c) Aq[(size_t)r * hist + c] = M[(size_t)c * m + r] + (r == c ? mu : 0.0);
-            for (int c = 0; c < hist; ++c) {        // Gaussian elimination with partial pivoting
-                int piv = c;
-                for (int r = c + 1; r < hist; ++r)
-                    if (std::fabs(Aq[(size_t)r * hist + c]) > std::fabs(Aq[(size_t)piv * hist + c])) piv = r;
-                if (piv != c) {
-                    for (int k2 = 0; k2 < hist; ++k2) std::swap(Aq[(size_t)c * hist + k2], Aq[(size_t)piv * hist + k2]);
-                    std::swap(bq[c], bq[piv]);
-                }
-                const double d = Aq[(size_t)c * hist + c];
-                if (d == 0.0) continue;
-                for (int r = c + 1; r < hist; ++r) {
-                    const double fct = Aq[(size_t)r * hist + c] / d;
-                    for (int k2 = c; k2 < hist; ++k2) Aq[(size_t)r * hist + k2] -= fct * Aq[(size_t)c * hist + k2];
-                    bq[r] -= fct * bq[c];
-                }
-            }
-            for (int r = hist - 1; r >= 0; --r) {
-                double acc = bq[r];
-                for (int c = r + 1; c < hist; ++c) acc -= Aq[(size_t)r * hist + c] * gam[c];
-                const double d = Aq[(size_t)r * hist + r];
-                gam[r] = d != 0.0 ? acc / d : 0.0;
-            }
-            // u = g - dG gamma
-            URCHIN_TRY_CUDA(cudaMemcpyAsync(hdev, gam.data(), sizeof(double) * hist, cudaMemcpyHostToDevice, s));
-            URCHIN_TRY_CUDA(cudaMemcpyAsync(V0, g, sizeof(double) * (size_t)na, cudaMemcpyDeviceToDevice, s));
-            URCHIN_TRY(launch_subtract(V0, dG, na, hist, hdev, na, s));
-            k_set_x_from_u<<<g1, 256, 0, s>>>(list, na, V0, g, x, bvh->A64, w32, w64, xs32, xs64);
-        } else {
-            k_set_x_from_u<<<g1, 256, 0, s>>>(list, na, g, g, x, bvh->A64, w32, w64, xs32, xs64);
-        }
-        URCHIN_TRY(launched());
-        URCHIN_TRY(evaluate(0, V0, E, nullptr, dtmp, hdev, &mrel, &norm, &sw, 0));
-    }
-    return URCHIN_OK;
-}
-
 // z[j] += sum over the active rays (k, a) of coef[k na + a] A_j K_ajk, for
 // every particle j (Morton): the transpose of the columns, by a scatter
 // traversal or over the stored segments.
@@ -1950,7 +1733,7 @@ int check_solve_params(const char* fn, const urchin_bvh* bvh, const urchin_solve
         return set_error(URCHIN_ERR_ARG, "%s: unknown precision", fn);
     if (P->case_rule != URCHIN_CASE_A && P->case_rule != URCHIN_CASE_B && P->case_rule != URCHIN_CASE_AUTO)
         return set_error(URCHIN_ERR_ARG, "%s: unknown case_rule", fn);
-    if (P->method != URCHIN_METHOD_PLAIN && P->method != URCHIN_METHOD_NEWTON && P->method != URCHIN_METHOD_ANDERSON)
+    if (P->method != URCHIN_METHOD_PLAIN && P->method != URCHIN_METHOD_NEWTON)
         return set_error(URCHIN_ERR_ARG, "%s: unknown method", fn);
     if (P->segments != URCHIN_SEG_RECOMPUTE && P->segments != URCHIN_SEG_STORE && P->segments != URCHIN_SEG_AUTO)
         return set_error(URCHIN_ERR_ARG, "%s: unknown segments mode", fn);

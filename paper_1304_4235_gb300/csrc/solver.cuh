@@ -152,13 +152,7 @@ struct Solver {
     int plain();
     int plain_sweeps(double stop_fraction);
     int newton();
-    int anderson();
-    int run()
-    {
-        if (P.method == URCHIN_METHOD_NEWTON) return newton();
-        if (P.method == URCHIN_METHOD_ANDERSON) return anderson();
-        return plain();
-    }
+    int run() { return P.method == URCHIN_METHOD_NEWTON ? newton() : plain(); }
     int finish(double* x_inout);
     int tangent(const double* v_orig, double* E_orig, double* dlnE_orig);
     // reverse mode at a converged state (urchin_solve_vjp)

@@ -841,6 +841,8 @@ int launch_weights(const urchin_bvh* b, const double* x_orig, float* w32, double
     return URCHIN_OK;
 }
 
+// origins (original indices) -> Morton slots; an index out of range flags
+// the status word and maps to slot 0
 __global__ void k_map_origins(const int32_t* __restrict__ origins, const int32_t* __restrict__ inv,
                               int64_t n_orig, int64_t n, int32_t* items, unsigned* status)
 {
@@ -854,6 +856,14 @@ __global__ void k_map_origins(const int32_t* __restrict__ origins, const int32_t
             items[o] = inv[i];
         }
     }
+}
+
+int launch_map_origins(const urchin_bvh* bvh, const int32_t* origins, int64_t n_orig, int32_t* items,
+                       unsigned* status, cudaStream_t s)
+{
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n_orig + 255) / 256, 4096));
+    k_map_origins<<<grid, 256, 0, s>>>(origins, bvh->inv, n_orig, bvh->n, items, status);
+    return launched();
 }
 
 }  // namespace urchin
@@ -944,9 +954,7 @@ int trace_columns_impl(const char* fn, const urchin_bvh* bvh, const double* x, c
     job.status = ctr + 1;
     if (origins) {
         int32_t* items = scr.at<int32_t>(o_items);
-        unsigned grid = (unsigned)std::min<int64_t>((n_orig + 255) / 256, 4096);
-        k_map_origins<<<grid, 256, 0, s>>>(origins, bvh->inv, n_orig, n, items, ctr + 1);
-        URCHIN_TRY(launched());
+        URCHIN_TRY(launch_map_origins(bvh, origins, n_orig, items, ctr + 1, s));
         job.items = items;
         job.out_row = nullptr;
     } else {
@@ -1040,9 +1048,7 @@ extern "C" int urchin_trace_columns_vjp(const urchin_bvh* bvh, const double* dir
     job.xbar = xm;
     if (origins) {
         int32_t* items = scr.at<int32_t>(o_items);
-        unsigned grid = (unsigned)std::min<int64_t>((n_orig + 255) / 256, 4096);
-        k_map_origins<<<grid, 256, 0, s>>>(origins, bvh->inv, n_orig, n, items, ctr + 1);
-        URCHIN_TRY(launched());
+        URCHIN_TRY(launch_map_origins(bvh, origins, n_orig, items, ctr + 1, s));
         job.items = items;
         job.out_row = nullptr;
     } else {

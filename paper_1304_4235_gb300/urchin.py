@@ -28,7 +28,7 @@ KERNEL_M4, KERNEL_GT = 0, 1
 F32, F64 = 0, 1
 CASE_A, CASE_B, CASE_AUTO = 0, 1, 2
 XSEC_VERNER, XSEC_HYDROGENIC, XSEC_POWERLAW, XSEC_HEII = 0, 1, 2, 3
-METHOD_PLAIN, METHOD_NEWTON, METHOD_ANDERSON = 0, 1, 2
+METHOD_PLAIN, METHOD_NEWTON = 0, 1
 SLAB_THRESHOLD, SLAB_SPECTRUM = 1, 2
 SEG_RECOMPUTE, SEG_STORE, SEG_AUTO = 0, 1, 2
 MAX_RAYS = 192
@@ -111,7 +111,6 @@ SIGNATURES = {
     "urchin_equilibrium_vjp": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int64, C.c_int, C.c_double, _vp, _vp, _vp]),
     "urchin_solve_vjp": (C.c_int, [_vp, C.POINTER(urchin_solve_params), _vp, _vp, _vp,
                                    C.POINTER(urchin_solve_stats), _vp]),
-    "urchin_evolve": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int64, C.c_int, C.c_double, _vp, C.c_double, _vp, _vp]),
     "urchin_gamma_he": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_int64, C.c_int, C.POINTER(urchin_spectrum),
                                   _vp, _vp, _vp]),
     "urchin_cross_section_ratio": (C.c_int, [C.c_int, _vp, C.c_int, _vp]),
@@ -262,16 +261,45 @@ def urchin_build_bvh(pos_x, pos_y, pos_z, h, mass_H, periodic: bool, L: float, u
     return Bvh(out, n, None)
 
 
+def _trace_buffers(bvh: Bvh, x, origins, R: int, precision: int, outs):
+    """Checks shared by the column entry points, made before any call into
+    the library (the C side cannot check a raw pointer's size or device):
+    x holds bvh.n values, origins is int32, every output is a contiguous
+    [n_orig, R] tensor of the precision's dtype, and all of them sit on the
+    current CUDA device (the one whose work arrays the call uses).  Returns
+    (n_orig, dtype, outputs) with missing outputs allocated."""
+    import torch
+    if x.numel() != bvh.n:
+        raise ValueError(f"x has {x.numel()} values, the BVH has {bvh.n} particles")
+    if origins is not None and origins.dtype != torch.int32:
+        raise TypeError(f"origins must be int32, got {origins.dtype}")
+    n_orig = bvh.n if origins is None else int(origins.numel())
+    dt = torch.float64 if precision == F64 else torch.float32
+    res = []
+    for o in outs:
+        if o is not None:
+            if tuple(o.shape) != (n_orig, R):
+                raise ValueError(f"out has shape {tuple(o.shape)}, expected {(n_orig, R)}")
+            if o.dtype != dt:
+                raise TypeError(f"out has dtype {o.dtype}, expected {dt} for this precision")
+            if not o.is_contiguous():
+                raise ValueError("out must be contiguous")
+        res.append(o)
+    dev = torch.cuda.current_device()
+    for t in [x, origins] + res:
+        if t is not None and (not t.is_cuda or t.device.index != dev):
+            raise ValueError(f"every array must be on the current CUDA device cuda:{dev}, got {t.device}")
+    res = [torch.empty((n_orig, R), dtype=dt, device=x.device) if o is None else o for o in res]
+    return n_orig, dt, res
+
+
 def urchin_trace_columns(bvh: Bvh, x, dirs, l_ray: float, origins=None, kernel: int = KERNEL_M4,
                          precision: int = F32, out=None, stream=None):
     """Threshold optical depths tau[o, k] (float32 or float64 CUDA tensor)."""
     import torch
     dirs = _host(dirs).reshape(-1, 3)
     R = dirs.shape[0]
-    n_orig = bvh.n if origins is None else int(origins.numel())
-    dt = torch.float64 if precision == F64 else torch.float32
-    if out is None:
-        out = torch.empty((n_orig, R), dtype=dt, device=x.device)
+    n_orig, dt, (out,) = _trace_buffers(bvh, x, origins, R, precision, [out])
     _check(load().urchin_trace_columns(bvh.handle, _dev(x, torch.float64), dirs.ctypes.data_as(_vp), R,
                                        float(l_ray), _dev(origins, torch.int32), n_orig, int(kernel),
                                        int(precision), _dev(out, dt), _stream(stream)))
@@ -280,16 +308,15 @@ def urchin_trace_columns(bvh: Bvh, x, dirs, l_ray: float, origins=None, kernel: 
 
 def urchin_trace_columns_noalloc(bvh: Bvh, x, dirs, l_ray: float, origins=None, kernel: int = KERNEL_M4,
                                  precision: int = F32, out=None, stream=None):
-    """Same as urchin_trace_columns, but the library allocates nothing: its
-    work space is a fixed device array (see include/urchin.h for the size
-    limit and the sharing rules).  `out` may be preallocated by the caller."""
+    """Same columns as urchin_trace_columns, but the library allocates no
+    device memory: its work space is a fixed device array (see
+    include/urchin.h for the size limit and the sharing rules).  Pass a
+    preallocated `out` to keep the whole call free of allocation (with
+    out=None this wrapper allocates it through torch)."""
     import torch
     dirs = _host(dirs).reshape(-1, 3)
     R = dirs.shape[0]
-    n_orig = bvh.n if origins is None else int(origins.numel())
-    dt = torch.float64 if precision == F64 else torch.float32
-    if out is None:
-        out = torch.empty((n_orig, R), dtype=dt, device=x.device)
+    n_orig, dt, (out,) = _trace_buffers(bvh, x, origins, R, precision, [out])
     _check(load().urchin_trace_columns_noalloc(bvh.handle, _dev(x, torch.float64), dirs.ctypes.data_as(_vp), R,
                                                float(l_ray), _dev(origins, torch.int32), n_orig, int(kernel),
                                                int(precision), _dev(out, dt), _stream(stream)))
@@ -302,10 +329,7 @@ def urchin_trace_columns_nearfar(bvh: Bvh, x, dirs, l_ray: float, origins=None, 
     import torch
     dirs = _host(dirs).reshape(-1, 3)
     R = dirs.shape[0]
-    n_orig = bvh.n if origins is None else int(origins.numel())
-    dt = torch.float64 if precision == F64 else torch.float32
-    tf = torch.empty((n_orig, R), dtype=dt, device=x.device)
-    tn = torch.empty((n_orig, R), dtype=dt, device=x.device)
+    n_orig, dt, (tf, tn) = _trace_buffers(bvh, x, origins, R, precision, [None, None])
     _check(load().urchin_trace_columns_nearfar(bvh.handle, _dev(x, torch.float64), dirs.ctypes.data_as(_vp), R,
                                                float(l_ray), _dev(origins, torch.int32), n_orig, int(kernel),
                                                int(precision), _dev(tf, dt), _dev(tn, dt), _stream(stream)))
@@ -363,17 +387,6 @@ def urchin_equilibrium(gamma, tau_eff, nH, T, case_rule: int = CASE_AUTO, y: flo
     _check(load().urchin_equilibrium(_dev(gamma, torch.float64), _dev(tau_eff, torch.float32),
                                      _dev(nH, torch.float64), _dev(T, torch.float64), n,
                                      int(case_rule), float(y), _dev(x), _stream(stream)))
-    return x
-
-
-def urchin_evolve(gamma, tau_eff, nH, T, x0, t: float, case_rule: int = CASE_AUTO, y: float = 0.0, stream=None):
-    """x after time t (s) from x0 at fixed Gamma, nH, T (App. C3)."""
-    import torch
-    n = int(gamma.numel())
-    x = torch.empty(n, dtype=torch.float64, device=gamma.device)
-    _check(load().urchin_evolve(_dev(gamma, torch.float64), _dev(tau_eff, torch.float32), _dev(nH, torch.float64),
-                                _dev(T, torch.float64), n, int(case_rule), float(y), _dev(x0, torch.float64),
-                                float(t), _dev(x), _stream(stream)))
     return x
 
 
@@ -483,6 +496,8 @@ def urchin_trace_columns_vjp(bvh: Bvh, dirs, l_ray: float, tau_bar, origins=None
         raise ValueError(f"tau_bar must have shape ({n_orig}, {R})")
     if x_bar is None:
         x_bar = torch.zeros(bvh.n, dtype=torch.float64, device=tau_bar.device)
+    elif x_bar.numel() != bvh.n:
+        raise ValueError(f"x_bar has {x_bar.numel()} values, the BVH has {bvh.n} particles")
     _check(load().urchin_trace_columns_vjp(bvh.handle, dirs.ctypes.data_as(_vp), R, float(l_ray),
                                            _dev(origins, torch.int32), n_orig, int(kernel), int(precision),
                                            _dev(tau_bar, dt), _dev(x_bar, torch.float64), _stream(stream)))

@@ -520,52 +520,3 @@ def test_density_order_reaches_jacobi_fixed_point():
     assert sj["converged"] and sb["converged"]
     assert np.allclose(xj, xb, rtol=1e-9)
     assert sb["sweeps"] <= sj["sweeps"]
-
-
-# -- time-dependent neutral fraction (App. C3) ----------------------------------
-def test_time_dependent_x_matches_direct_integration():
-    """x(t) of App. C3 against direct integration of dx/dt = R x^2 + Q x + P
-    (Eq. dxdt) with Gamma, nH, T held, and its limits x(0) = x0, x(inf) = x_eq."""
-    from scipy.integrate import solve_ivp
-    for G, nH, T, y, cb, x0 in ((1e-12, 1e-3, 1e4, 0.0, False, 0.9), (3e-13, 0.1, 2e4, 0.08, True, 1e-4),
-                                (1e-14, 10.0, 8e3, 0.0, False, 0.5)):
-        aA, aB, gc = O.rates(T)
-        a = aB if cb else aA
-        R = (gc + a) * nH
-        Q = -(G + a * nH + R * (1 + y))
-        P = a * nH * (1 + y)
-        trc = 1.0 / R
-        sol = solve_ivp(lambda t, x: [R * x[0] ** 2 + Q * x[0] + P], (0, 5 * trc), [x0], method="LSODA",
-                        rtol=1e-11, atol=1e-14, dense_output=True)
-        for f in (0.01, 0.3, 1.0, 5.0):
-            got = O.xt(G, nH, T, x0, f * trc, y, cb)[0]
-            ref = sol.sol(f * trc)[0]
-            assert abs(got - ref) <= 1e-8 * ref, (G, nH, f)
-        assert O.xt(G, nH, T, x0, 0.0, y, cb)[0] == pytest.approx(x0, rel=1e-15)
-        assert O.xt(G, nH, T, x0, 1e4 * trc, y, cb)[0] == pytest.approx(O.xeq(G, nH, T, y, cb)[0], rel=1e-14)
-
-
-def test_time_dependent_x_against_50_digit_arithmetic():
-    """The closed form evaluated in 50-digit arithmetic from the roots of Eq.
-    xroots (the rate coefficients taken from the oracle): agreement to 1e-11,
-    including neutral, cold gas where x_+ and x_eq both approach 1."""
-    mp = pytest.importorskip("mpmath")
-    mp.mp.dps = 50
-    rng = np.random.default_rng(12)
-    for _ in range(200):
-        G = float(np.exp(rng.uniform(np.log(1e-18), np.log(1e-11))))
-        nH = float(np.exp(rng.uniform(np.log(1e-5), np.log(10.0))))
-        T = float(rng.uniform(5e3, 3e4))
-        x0 = float(np.exp(rng.uniform(np.log(1e-6), 0.0)))
-        t = float(10 ** rng.uniform(11, 18))
-        aA, aB, gc = O.rates(T)
-        a, g, n_, GG = mp.mpf(aA), mp.mpf(gc), mp.mpf(nH), mp.mpf(G)
-        R = (g + a) * n_
-        Q = -(GG + a * n_ + R)
-        P = a * n_
-        sq = mp.sqrt(Q * Q - 4 * P * R)
-        xm, xp = (-Q - sq) / (2 * R), (-Q + sq) / (2 * R)
-        F = mp.e ** (-(xp - xm) * mp.mpf(t) * R)
-        X0 = mp.mpf(x0)
-        ref = xm + (X0 - xm) * (xp - xm) * F / ((xp - X0) + (X0 - xm) * F)
-        assert abs(O.xt(G, nH, T, x0, t)[0] / float(ref) - 1) < 1e-11
