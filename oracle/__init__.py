@@ -10,6 +10,7 @@ Functions (FP64 throughout; each follows the passage named in the C source):
   sigma_th, sigma(E, which), spectrum(...)        App. C1, Eq. gamma
   m4_shape(q), gt_shape(q), chord(kernel, b,u1,u2) Eq. spline, Eq. Gt, I(h,b,z1,z2)
   columns(...), columns_points(...)               Eq. nhi, Eq. colden (brute force)
+  Grid(w, cell).columns(...)                      the same sums from a uniform-grid candidate search
   healpix(nside)                                  Sec. 3.2 (Gorski et al. 2005)
   gamma(...)                                      Eq. gamma_shld
   rates(T), xeq(...)                              App. C3, Eqs. xroots / xphys
@@ -84,7 +85,11 @@ def _load():
                 "oracle_xeq": (d, [d, d, d, d, i]),
                 "oracle_solve": (i, [i64, vp, vp, vp, vp, vp, vp, vp, d, i, d, d,
                                      vp, i, d, i, i, vp, vp, d, d, i, i, i, i, vp, vp, vp, vp,
-                                     vp, vp, vp, vp, vp]),
+                                     vp, vp, vp, vp, vp, d]),
+                "oracle_grid_build": (vp, [i64, vp, vp, vp, vp, i, d, d]),
+                "oracle_grid_free": (None, [vp]),
+                "oracle_grid_entries": (i64, [vp]),
+                "oracle_grid_columns": (None, [vp, vp, vp, vp, vp, vp, vp, d, vp, i64, vp, i, d, i, vp]),
                 "oracle_gamma_he": (None, [vp, vp, vp, i64, i, i, vp, vp, vp, vp, vp, vp]),
                 "oracle_columns_nearfar": (None, [i64, vp, vp, vp, vp, vp, vp, i, d, d,
                                                   vp, i64, vp, i, d, i, vp, vp]),
@@ -181,6 +186,50 @@ def columns(w, x, dirs, origins=None, l_ray=None, kernel=KERNEL_M4):
     return out
 
 
+class Grid:
+    """Uniform-grid candidate search over a workload's particles (positions
+    and h only): every particle listed in each cell its sphere's bounding box
+    overlaps, rays walking the cells their segments cross.  columns() then
+    gives the brute-force sums of Eq. colden up to the order of the sum."""
+
+    def __init__(self, w, cell: float):
+        self.w = w
+        px, py, pz, h, _ = _particles(w)
+        self._keep = (px, py, pz, h)
+        self._g = _load().oracle_grid_build(w.n, _p(px), _p(py), _p(pz), _p(h), int(w.periodic), float(w.box),
+                                            float(cell))
+        if not self._g:
+            raise ValueError("grid query: a periodic sphere spans the box at this cell size")
+
+    @property
+    def entries(self) -> int:
+        return int(_load().oracle_grid_entries(self._g))
+
+    def columns(self, x, dirs, origins=None, l_ray=None, kernel=KERNEL_M4):
+        w = self.w
+        px, py, pz, h, m = _particles(w)
+        x = _f64(x)
+        dirs = _f64(dirs).reshape(-1, 3)
+        org = None if origins is None else np.ascontiguousarray(origins, dtype=np.int64)
+        n_orig = w.n if org is None else org.shape[0]
+        out = np.zeros((n_orig, dirs.shape[0]))
+        _load().oracle_grid_columns(self._g, _p(px), _p(py), _p(pz), _p(h), _p(m), _p(x), float(w.unit_cm),
+                                    _p(org), n_orig, _p(dirs), dirs.shape[0],
+                                    float(w.l_ray if l_ray is None else l_ray), kernel, _p(out))
+        return out
+
+    def close(self):
+        if self._g:
+            _load().oracle_grid_free(self._g)
+            self._g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def columns_points(w, x, points, dirs, l_ray, kernel=KERNEL_M4):
     px, py, pz, h, m = _particles(w)
     x = _f64(x)
@@ -234,13 +283,16 @@ def xeq(Gamma, nH, T, y=0.0, caseB=False):
 
 # -- driver (Sec. 4) ---------------------------------------------------------
 def solve(w, s, wts, dirs, tol=1e-3, tau_skip=1e-4, max_iter=100, case_rule=CASE_AUTO,
-          kernel=KERNEL_M4, y=0.0, x_start=None, sweeps=None, l_ray=None, blocks=1, near_far=0, he=None):
+          kernel=KERNEL_M4, y=0.0, x_start=None, sweeps=None, l_ray=None, blocks=1, near_far=0, he=None,
+          grid_cell=0.0):
     """Iteration of Sec. 4: Jacobi (blocks=1) or the high-to-low density
     update order in `blocks` blocks.  ``sweeps`` = exact sweep count
     (step-matched mode) instead of the tolerance test.  Returns (x, frozen,
     stats) with stats = dict(sweeps, max_rel_dx, rays, converged, caseB), caseB
     the case of each particle's last update.  he = dict(tau1, tau2 [n, R],
-    s1, s2 [F]) adds fixed He I / He II columns (gamma_he)."""
+    s1, s2 [F]) adds fixed He I / He II columns (gamma_he).  grid_cell > 0
+    takes the columns from the uniform-grid query (Grid) instead of brute
+    force (not with near_far)."""
     px, py, pz, h, m = _particles(w)
     nH, T = _f64(w.nH), _f64(w.T)
     dirs = _f64(dirs).reshape(-1, 3)
@@ -261,9 +313,11 @@ def solve(w, s, wts, dirs, tol=1e-3, tau_skip=1e-4, max_iter=100, case_rule=CASE
                               float(w.l_ray if l_ray is None else l_ray), kernel,
                               s.shape[0], _p(s), _p(wts), float(tol), float(tau_skip),
                               mi, case_rule, int(blocks), int(near_far), _p(h1), _p(h2), _p(hs1), _p(hs2),
-                              _p(xs), _p(x), _p(frozen), _p(caseB), _p(st))
+                              _p(xs), _p(x), _p(frozen), _p(caseB), _p(st), float(grid_cell))
     if rc == 2:
         raise ValueError("near_far needs blocks <= 1, helium needs near_far = 0 and blocks <= 1")
+    if rc == 3:
+        raise ValueError("grid query: a periodic sphere spans the box at this cell size")
     return x, frozen.astype(bool), dict(sweeps=int(st[0]), max_rel_dx=float(st[1]),
                                         rays=float(st[2]), converged=(rc == 0),
                                         caseB=caseB.astype(bool))

@@ -299,6 +299,201 @@ void oracle_columns(int64_t n, const double* px, const double* py, const double*
     free(pts);
 }
 
+/* ------------------------------------------------------------------------ */
+/* Columns by a uniform-grid query: the same sum as oracle_columns          */
+/* (Eq. colden), with the candidate particles of a ray taken from the grid  */
+/* cells its segment passes through instead of from all n particles.        */
+/* ------------------------------------------------------------------------ */
+
+/* Every particle is listed in each cell of the box of cells that its
+ * sphere's bounding box overlaps ("cell range" [lo, hi] per axis, in
+ * unwrapped cell indices; a periodic grid stores cell i at i mod G).  A ray
+ * walks the cells its segment crosses in order (3-D DDA in unwrapped
+ * indices).  A candidate j met in unwrapped cell c belongs to the periodic
+ * image a of j whose unwrapped range [lo + a G, hi + a G] contains c; that
+ * image is evaluated once, in the first cell of the walk inside its range
+ * (the cells of a range that a straight segment crosses are consecutive in
+ * the walk, as the range is a box).  Every image whose sphere the segment
+ * crosses has a crossed cell in its range, so the set of non-zero terms is
+ * the brute force's; only the order of the sum differs. */
+typedef struct {
+    int periodic;
+    double L, c;            /* box side, cell size */
+    double lo[3];           /* grid origin */
+    int64_t G[3];           /* cells per axis */
+    int64_t* start;         /* [ncell + 1] first entry of each cell */
+    int64_t* idx;           /* particle index per entry */
+    int64_t* rlo;           /* [3 n] unwrapped cell range of each particle */
+    int64_t* rhi;
+    int64_t n;
+} oracle_grid;
+
+static int64_t floor_div(int64_t a, int64_t b) { int64_t q = a / b; return (a % b != 0 && (a < 0) != (b < 0)) ? q - 1 : q; }
+static int64_t pos_mod(int64_t a, int64_t b) { int64_t r = a % b; return r < 0 ? r + b : r; }
+
+void oracle_grid_free(oracle_grid* g)
+{
+    if (!g) return;
+    free(g->start); free(g->idx); free(g->rlo); free(g->rhi); free(g);
+}
+
+/* Build the grid with cells of about `cell` (length unit).  Returns NULL when
+ * a periodic sphere's cell range spans the whole box (2 h_j close to L),
+ * where the image of a candidate would not be unique. */
+oracle_grid* oracle_grid_build(int64_t n, const double* px, const double* py, const double* pz,
+                               const double* h, int periodic, double L, double cell)
+{
+    oracle_grid* g = (oracle_grid*)calloc(1, sizeof(oracle_grid));
+    const double* p[3] = {px, py, pz};
+    g->periodic = periodic;
+    g->L = L;
+    g->n = n;
+    if (periodic) {
+        int64_t G = (int64_t)floor(L / cell);
+        if (G < 1) G = 1;
+        g->c = L / (double)G;
+        for (int a = 0; a < 3; ++a) { g->lo[a] = 0.0; g->G[a] = G; }
+    } else {
+        g->c = cell;
+        for (int a = 0; a < 3; ++a) {
+            double mn = 1e300, mx = -1e300;
+            for (int64_t j = 0; j < n; ++j) {
+                mn = fmin(mn, p[a][j] - h[j]);
+                mx = fmax(mx, p[a][j] + h[j]);
+            }
+            g->lo[a] = mn;
+            g->G[a] = (int64_t)floor((mx - mn) / cell) + 1;
+        }
+    }
+    g->rlo = (int64_t*)malloc(sizeof(int64_t) * 3 * (size_t)n);
+    g->rhi = (int64_t*)malloc(sizeof(int64_t) * 3 * (size_t)n);
+    for (int64_t j = 0; j < n; ++j)
+        for (int a = 0; a < 3; ++a) {
+            int64_t l = (int64_t)floor((p[a][j] - h[j] - g->lo[a]) / g->c);
+            int64_t u = (int64_t)floor((p[a][j] + h[j] - g->lo[a]) / g->c);
+            if (!periodic) {
+                if (l < 0) l = 0;
+                if (u > g->G[a] - 1) u = g->G[a] - 1;
+            } else if (u - l + 1 >= g->G[a]) {
+                oracle_grid_free(g);
+                return NULL;
+            }
+            g->rlo[3 * j + a] = l;
+            g->rhi[3 * j + a] = u;
+        }
+    const int64_t ncell = g->G[0] * g->G[1] * g->G[2];
+    g->start = (int64_t*)calloc((size_t)ncell + 1, sizeof(int64_t));
+    for (int pass = 0; pass < 2; ++pass) {
+        int64_t* fill = NULL;
+        if (pass == 1) {
+            for (int64_t q = 0; q < ncell; ++q) g->start[q + 1] += g->start[q];
+            g->idx = (int64_t*)malloc(sizeof(int64_t) * (size_t)(g->start[ncell] > 0 ? g->start[ncell] : 1));
+            fill = (int64_t*)malloc(sizeof(int64_t) * (size_t)ncell);
+            memcpy(fill, g->start, sizeof(int64_t) * (size_t)ncell);
+        }
+        for (int64_t j = 0; j < n; ++j)
+            for (int64_t i = g->rlo[3 * j]; i <= g->rhi[3 * j]; ++i)
+                for (int64_t k = g->rlo[3 * j + 1]; k <= g->rhi[3 * j + 1]; ++k)
+                    for (int64_t m = g->rlo[3 * j + 2]; m <= g->rhi[3 * j + 2]; ++m) {
+                        const int64_t q = (pos_mod(i, g->G[0]) * g->G[1] + pos_mod(k, g->G[1])) * g->G[2] +
+                                          pos_mod(m, g->G[2]);
+                        if (pass == 0) g->start[q + 1]++;
+                        else g->idx[fill[q]++] = j;
+                    }
+        free(fill);
+    }
+    return g;
+}
+
+int64_t oracle_grid_entries(const oracle_grid* g) { return g ? g->start[g->G[0] * g->G[1] * g->G[2]] : -1; }
+
+/* The column of the segment o + t dir, t in [0, l_ray], from the grid (the
+ * factor sigma_th left out, as in column_from_point). */
+static double grid_column(const oracle_grid* g, const double* px, const double* py, const double* pz,
+                          const double* h, const double* mass_H, const double* x, double unit_cm,
+                          const double* o, const double* dir, double l_ray, int kernel)
+{
+    int64_t cur[3], step[3], prev[3] = {0, 0, 0};
+    double tmax[3], tdelta[3];
+    for (int a = 0; a < 3; ++a) {
+        cur[a] = (int64_t)floor((o[a] - g->lo[a]) / g->c);
+        if (dir[a] > 0.0) {
+            step[a] = 1;
+            tmax[a] = ((double)(cur[a] + 1) * g->c + g->lo[a] - o[a]) / dir[a];
+            tdelta[a] = g->c / dir[a];
+        } else if (dir[a] < 0.0) {
+            step[a] = -1;
+            tmax[a] = ((double)cur[a] * g->c + g->lo[a] - o[a]) / dir[a];
+            tdelta[a] = -g->c / dir[a];
+        } else {
+            step[a] = 0;
+            tmax[a] = INFINITY;
+            tdelta[a] = INFINITY;
+        }
+    }
+    int have_prev = 0;
+    double sum = 0.0;
+    for (;;) {
+        int inside = 1;
+        int64_t s[3];
+        for (int a = 0; a < 3; ++a) {
+            if (g->periodic) s[a] = pos_mod(cur[a], g->G[a]);
+            else {
+                s[a] = cur[a];
+                if (cur[a] < 0 || cur[a] >= g->G[a]) inside = 0;
+            }
+        }
+        if (inside) {
+            const int64_t q = (s[0] * g->G[1] + s[1]) * g->G[2] + s[2];
+            for (int64_t e = g->start[q]; e < g->start[q + 1]; ++e) {
+                const int64_t j = g->idx[e];
+                int64_t img[3];
+                int prev_in = have_prev;
+                for (int a = 0; a < 3; ++a) {
+                    const int64_t l = g->rlo[3 * j + a], u = g->rhi[3 * j + a];
+                    /* the image whose unwrapped range holds the current cell */
+                    img[a] = g->periodic ? floor_div(cur[a] - (l + pos_mod(s[a] - l, g->G[a])), g->G[a]) : 0;
+                    const int64_t lo = l + img[a] * g->G[a], hi = u + img[a] * g->G[a];
+                    if (prev[a] < lo || prev[a] > hi) prev_in = 0;
+                }
+                if (prev_in) continue;       /* met in an earlier cell of this walk */
+                sum += pair_term(px[j], py[j], pz[j], h[j], mass_H[j] * x[j], g->periodic ? img[0] * g->L : 0.0,
+                                 g->periodic ? img[1] * g->L : 0.0, g->periodic ? img[2] * g->L : 0.0, unit_cm, o,
+                                 dir, l_ray, kernel);
+            }
+        }
+        int ax = 0;
+        if (tmax[1] < tmax[ax]) ax = 1;
+        if (tmax[2] < tmax[ax]) ax = 2;
+        if (!(tmax[ax] <= l_ray)) break;
+        for (int a = 0; a < 3; ++a) prev[a] = cur[a];
+        have_prev = 1;
+        cur[ax] += step[ax];
+        tmax[ax] += tdelta[ax];
+    }
+    return sum;
+}
+
+/* Columns of rays from particle centres (origins as in oracle_columns) by
+ * the grid query: tau_out[o*R + k], the same values as oracle_columns up
+ * to the order of the sum. */
+void oracle_grid_columns(const oracle_grid* g, const double* px, const double* py, const double* pz,
+                         const double* h, const double* mass_H, const double* x, double unit_cm,
+                         const int64_t* origins, int64_t n_orig, const double* dirs, int R, double l_ray,
+                         int kernel, double* tau_out)
+{
+    const double sth = oracle_sigma_th();
+    const int64_t total = n_orig * (int64_t)R;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t r = 0; r < total; ++r) {
+        const int64_t o = r / R;
+        const int k = (int)(r % R);
+        const int64_t i = origins ? origins[o] : o;
+        const double pt[3] = {px[i], py[i], pz[i]};
+        tau_out[r] = sth * grid_column(g, px, py, pz, h, mass_H, x, unit_cm, pt, dirs + 3 * k, l_ray, kernel);
+    }
+}
+
 /* Near/far split of Sec. 3.3.3 (self-contribution to self-shielding in
  * SPH): on the ray from particle i, a crossed particle j (periodic image
  * r_j + a L) is near when r_i lies inside its smoothing sphere,
@@ -781,8 +976,10 @@ static int use_caseB(int case_rule, double tau_eff)
  * particles, caseB_out[n] (optional) 1 where the final update used case B,
  * stats[0] = sweeps done, stats[1] = last max |dx|/x,
  * stats[2] = rays traced.  x_start (optional) replaces x_thin as the start
- * (sweep 0 still applies the freeze rule).  Returns 0 when converged, 1 when
- * the sweep limit ended the run. */
+ * (sweep 0 still applies the freeze rule).  grid_cell > 0 takes the columns
+ * from the uniform-grid query with cells of about that size (not with the
+ * near/far split).  Returns 0 when converged, 1 when the sweep limit ended
+ * the run, 3 when the grid cannot be built (a sphere spanning the box). */
 static const double* g_sort_nH;
 static int by_density(const void* a, const void* b)
 {
@@ -793,6 +990,19 @@ static int by_density(const void* a, const void* b)
     return (i > j) - (i < j);
 }
 
+/* Columns for the driver: brute force, or the grid query when a grid is given. */
+static void solve_columns(const oracle_grid* grid, int64_t n, const double* px, const double* py,
+                          const double* pz, const double* h, const double* mass_H, const double* x, int periodic,
+                          double L, double unit_cm, const int64_t* origins, int64_t n_orig, const double* dirs,
+                          int R, double l_ray, int kernel, double* tau)
+{
+    if (grid)
+        oracle_grid_columns(grid, px, py, pz, h, mass_H, x, unit_cm, origins, n_orig, dirs, R, l_ray, kernel, tau);
+    else
+        oracle_columns(n, px, py, pz, h, mass_H, x, periodic, L, unit_cm, origins, n_orig, dirs, R, l_ray, kernel,
+                       tau);
+}
+
 int oracle_solve(int64_t n, const double* px, const double* py, const double* pz,
                  const double* h, const double* mass_H, const double* nH, const double* T,
                  double y, int periodic, double L, double unit_cm,
@@ -800,10 +1010,19 @@ int oracle_solve(int64_t n, const double* px, const double* py, const double* pz
                  int F, const double* s, const double* w,
                  double tol, double tau_skip, int max_iter, int case_rule, int blocks, int near_far,
                  const double* he_tau1, const double* he_tau2, const double* he_s1, const double* he_s2,
-                 const double* x_start, double* x_out, int* frozen_out, int* caseB_out, double* stats)
+                 const double* x_start, double* x_out, int* frozen_out, int* caseB_out, double* stats,
+                 double grid_cell)
 {
     if (he_tau1 && (near_far || blocks > 1)) return 2;
     if (near_far && blocks > 1) return 2;
+    /* grid_cell > 0: columns by the uniform-grid query (oracle_grid_columns)
+     * instead of brute force; the grid holds positions only, so one build
+     * serves every sweep */
+    oracle_grid* grid = NULL;
+    if (grid_cell > 0.0 && !near_far) {
+        grid = oracle_grid_build(n, px, py, pz, h, periodic, L, grid_cell);
+        if (!grid) return 3;
+    }
     double gthin = 0.0;
     for (int j = 0; j < F; ++j) gthin += w[j];
     double* x = x_out;
@@ -842,8 +1061,8 @@ int oracle_solve(int64_t n, const double* px, const double* py, const double* pz
                 oracle_gamma_nearfar(tau, tau_nr, nact, R, F, s, w, nH_o, T_o, cb_o, near_far == 2, te, G);
                 for (int64_t o = 0; o < nact; ++o) te[o] = -te[o];
             } else if (he_tau1) {
-                oracle_columns(n, px, py, pz, h, mass_H, x, periodic, L, unit_cm,
-                               act, nact, dirs, R, l_ray, kernel, tau);
+                solve_columns(grid, n, px, py, pz, h, mass_H, x, periodic, L, unit_cm,
+                              act, nact, dirs, R, l_ray, kernel, tau);
                 for (int64_t o = 0; o < nact; ++o)
                     for (int k = 0; k < R; ++k) {
                         he1_o[o * R + k] = he_tau1[act[o] * R + k];
@@ -851,8 +1070,8 @@ int oracle_solve(int64_t n, const double* px, const double* py, const double* pz
                     }
                 oracle_gamma_he(tau, he1_o, he2_o, nact, R, F, s, he_s1, he_s2, w, G, te);
             } else {
-                oracle_columns(n, px, py, pz, h, mass_H, x, periodic, L, unit_cm,
-                               act, nact, dirs, R, l_ray, kernel, tau);
+                solve_columns(grid, n, px, py, pz, h, mass_H, x, periodic, L, unit_cm,
+                              act, nact, dirs, R, l_ray, kernel, tau);
                 oracle_gamma(tau, nact, R, F, s, w, G, te);
             }
             rays += (double)nact * R;
@@ -886,8 +1105,8 @@ int oracle_solve(int64_t n, const double* px, const double* py, const double* pz
                 int64_t hi = ((b + 1) * nact) / blocks;
                 int64_t m = hi - lo;
                 if (m <= 0) continue;
-                oracle_columns(n, px, py, pz, h, mass_H, x, periodic, L, unit_cm,
-                               act + lo, m, dirs, R, l_ray, kernel, tau);
+                solve_columns(grid, n, px, py, pz, h, mass_H, x, periodic, L, unit_cm,
+                              act + lo, m, dirs, R, l_ray, kernel, tau);
                 oracle_gamma(tau, m, R, F, s, w, G, te);
                 rays += (double)m * R;
                 for (int64_t o = 0; o < m; ++o) {
@@ -910,6 +1129,7 @@ int oracle_solve(int64_t n, const double* px, const double* py, const double* pz
     if (stats) { stats[0] = sweeps; stats[1] = maxrel; stats[2] = rays; }
     free(frozen); free(latchB); free(tau); free(G); free(te); free(xn); free(act);
     free(tau_nr); free(nH_o); free(T_o); free(cb_o); free(he1_o); free(he2_o);
+    oracle_grid_free(grid);
     return (fixed || converged) ? 0 : 1;
 }
 

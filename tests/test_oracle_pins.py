@@ -520,3 +520,49 @@ def test_density_order_reaches_jacobi_fixed_point():
     assert sj["converged"] and sb["converged"]
     assert np.allclose(xj, xb, rtol=1e-9)
     assert sb["sweeps"] <= sj["sweeps"]
+
+
+# -- uniform-grid query (the timed CPU baseline) -------------------------------
+@pytest.mark.parametrize("case", ["lattice", "halo", "small_box_long_rays"])
+def test_grid_columns_equal_brute_force(case):
+    """The grid query changes only how the candidate particles of a ray are
+    found: its columns equal the brute-force sum over all particles (and
+    all periodic images) of Eq. colden to rounding order, rel 1e-12, for
+    periodic and isolated sets, both kernels, N_side 1 and 2, and rays
+    longer than half a small periodic box (several images of a particle on
+    one ray)."""
+    if case == "lattice":
+        w, cells = W.lattice_box(), (40.0, 130.0, 300.0)
+    elif case == "halo":
+        w, cells = W.halo(n=4096, seed=1405), (2.0, 8.0, 30.0)
+    else:
+        w, cells = W.lattice_box(n_side=6, box_kpc=100.0, seed=21), (8.0, 10.0)
+        w.l_ray = 90.0
+    rng = np.random.default_rng(3)
+    x = np.exp(rng.uniform(np.log(1e-4), 0.0, w.n))
+    org = W.random_origins(w.n, 200, 4)
+    for nside, kernel in ((1, O.KERNEL_M4), (2, O.KERNEL_GT)):
+        dirs = O.healpix(nside)
+        ref = O.columns(w, x, dirs, origins=org, kernel=kernel)
+        for cell in cells:
+            got = O.Grid(w, cell).columns(x, dirs, origins=org, kernel=kernel)
+            assert np.all(np.abs(got - ref) <= 1e-12 * np.abs(ref)), (case, nside, cell)
+
+
+def test_grid_refuses_a_sphere_spanning_the_box():
+    w = W.lattice_box(n_side=6, box_kpc=100.0, seed=21)
+    with pytest.raises(ValueError):
+        O.Grid(w, 60.0)
+
+
+def test_grid_solve_step_matched_equals_brute_force():
+    """The Sec. 4 driver with grid columns takes the brute-force driver's
+    steps (same freeze and case decisions, x to 1e-12)."""
+    w = W.halo(n=3000, seed=1406)
+    e, J = w.spectrum()
+    s, wts = O.spectrum(e, J, w.gamma_thin)
+    dirs = O.healpix(1)
+    xb, fb, sb = O.solve(w, s, wts, dirs, sweeps=4)
+    xg, fg, sg = O.solve(w, s, wts, dirs, sweeps=4, grid_cell=5.0)
+    assert np.array_equal(fb, fg) and np.array_equal(sb["caseB"], sg["caseB"])
+    assert np.all(np.abs(xg - xb) <= 1e-12 * xb)
