@@ -124,6 +124,7 @@ struct urchin_bvh {
     double L = 0.0;
     double unit_cm = 1.0;
     float hmax = 0.f;
+    float hgeo = 0.f;             // geometric mean of h
     float root_lo[3] = {0, 0, 0};
     float root_hi[3] = {0, 0, 0};
     int device = 0;
@@ -179,9 +180,9 @@ struct TraceJob {
     unsigned long long* hits;     // chord evaluations (may be NULL)
     int mode;                     // 0: columns, 1: count hits per ray, 2: fill segments (+ columns),
                                   // 3: transpose (scatter coef * A_j * chord into xbar)
-    uint32_t* counts;             // mode 1: [R * n_items], index k * n_items + item: hits rounded
-                                  //    up to a multiple of kSegPad
-    const uint64_t* row_ptr;      // mode 2: [R * n_items + 1] offsets of each ray's segments
+    uint32_t* counts;             // mode 1 (and mode 0 when not NULL): [R * n], index k * n + the origin's
+                                  //    Morton slot: hits rounded up to a multiple of kSegPad
+    const uint64_t* row_ptr;      // mode 2: [R * n + 1] offsets of each ray's segments (same index)
     int32_t* seg_col;             // mode 2: Morton index of the particle per segment, or NULL:
     uint16_t* seg_lo;             //    its low 16 bits and
     uint8_t* seg_hi;              //    its high 8 bits (FP32 segments, every index below 2^24)
@@ -199,19 +200,23 @@ struct TraceJob {
 int launch_trace(const TraceJob& job, cudaStream_t s);
 
 // Per-direction traversal order of the items: for each direction k the
-// origins sorted by a Morton code in the frame (e1, e2, d_k) with the axis
-// along d_k compressed, so that 32 consecutive origins form a thin beam
-// along the ray direction.  order needs R * n_items int32; tmp needs
+// origins sorted by a 63-bit Morton code in the frame (e1, e2, d_k) with the
+// axis along d_k compressed by a factor E, so that 32 consecutive origins
+// form a beam along the ray direction, about E times longer than wide.
+// Rays share their sphere crossings when the beam is narrow against h and
+// short against l_ray, so E = l_ray / (2 h_geo), h_geo the geometric mean of
+// h, clamped to [1, 64].  Measured traversal of all rays: 262144-particle
+// halo (l_ray / 2h_geo ~ 20) E = 16: 43 ms, 4: 51, 1: 58; the 256^3
+// log-normal box (~2) E = 16: 1.06 s, 4: 0.90, 1: 0.87 (30-bit keys, E = 16:
+// 1.34 s).  On the 4096-particle lattice the order costs more than it saves
+// (sort launches, and 9.1 instead of 7.4 sphere tests per hit), so short
+// lists keep item order.  order needs R * n_items int32; tmp needs
 // ray_order_tmp_bytes(n_items).
-// Measured on the 262144-particle halo (F32 columns, all origins): no order
-// 70 ms, E = 1: 68.6, E = 4: 63.7, E = 16: 60.7, E = 64 and 256: 60.8 ms;
-// on the 4096-particle lattice the order costs more (sort launches, and
-// 9.1 instead of 7.4 sphere tests per hit), so short lists keep item order.
-constexpr double kRayOrderElongation = 16.0;
 constexpr int64_t kRayOrderMinItems = 16384;
+double ray_order_elongation(const urchin_bvh* bvh, double l_ray);
 size_t ray_order_tmp_bytes(int64_t n_items);
 int ray_order(const urchin_bvh* bvh, const int32_t* items, int64_t n_items, const double* dirs_host, int R,
-              int32_t* order, void* tmp, cudaStream_t s);
+              double l_ray, int32_t* order, void* tmp, cudaStream_t s);
 
 // w_bar[b] += sum_r sg[r] exp(lc[r] - s_b tau[r]) over n_rays rays (tau in
 // the precision's type; the coefficient of ray r is sg[r] exp(lc[r]))

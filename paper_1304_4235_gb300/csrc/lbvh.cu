@@ -39,13 +39,16 @@ __host__ __device__ __forceinline__ float ord2f(unsigned u)
 
 // bounds[0..2] min centre, [3..5] max centre, [6] max h (ordered encoding);
 // bounds[7] error bits: 1 = non-finite, 2 = h <= 0 or mass < 0
+// logh_sum accumulates sum ln h (the geometric mean of h sets the shape of
+// the traversal's ray packets)
 __global__ void k_bounds(const float* __restrict__ x, const float* __restrict__ y,
                          const float* __restrict__ z, const float* __restrict__ h,
-                         const double* __restrict__ m, int64_t n, unsigned* bounds)
+                         const double* __restrict__ m, int64_t n, unsigned* bounds, double* logh_sum)
 {
     unsigned mn[3] = {0xffffffffu, 0xffffffffu, 0xffffffffu};
     unsigned mx[4] = {0u, 0u, 0u, 0u};
     unsigned err = 0;
+    double lsum = 0.0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         float c[3] = {x[i], y[i], z[i]};
@@ -54,6 +57,7 @@ __global__ void k_bounds(const float* __restrict__ x, const float* __restrict__ 
         bool fin = isfinite(c[0]) && isfinite(c[1]) && isfinite(c[2]) && isfinite(hi) && isfinite(mi);
         if (!fin) { err |= 1u; continue; }
         if (!(hi > 0.f) || mi < 0.0) err |= 2u;
+        else lsum += (double)logf(hi);
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             unsigned o = f2ord(c[a]);
@@ -71,6 +75,7 @@ __global__ void k_bounds(const float* __restrict__ x, const float* __restrict__ 
         }
         mx[3] = max(mx[3], __shfl_xor_sync(0xffffffffu, mx[3], off));
         err |= __shfl_xor_sync(0xffffffffu, err, off);
+        lsum += __shfl_xor_sync(0xffffffffu, lsum, off);
     }
     if ((threadIdx.x & 31) == 0) {
         for (int a = 0; a < 3; ++a) {
@@ -79,6 +84,7 @@ __global__ void k_bounds(const float* __restrict__ x, const float* __restrict__ 
         }
         atomicMax(&bounds[6], mx[3]);
         if (err) atomicOr(&bounds[7], err);
+        atomicAdd(logh_sum, lsum);
     }
 }
 
@@ -340,6 +346,7 @@ int build(const urchin_particles* p, const urchin_box* box, urchin_bvh* b, cudaS
     const int64_t ni = std::max<int64_t>(1, n - 1);
     Layout lay;
     size_t o_bounds = lay.take(8 * sizeof(unsigned));
+    size_t o_logh = lay.take(sizeof(double));
     size_t o_codes = lay.take((size_t)n * 4);
     size_t o_idx = lay.take((size_t)n * 4);
     size_t o_radix = lay.take(radix_tmp_bytes(n));
@@ -359,12 +366,17 @@ int build(const urchin_particles* p, const urchin_box* box, urchin_bvh* b, cudaS
 
     unsigned init[8] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0u, 0u, 0u, 0u, 0u};
     URCHIN_TRY_CUDA(cudaMemcpyAsync(bounds, init, sizeof(init), cudaMemcpyHostToDevice, s));
+    double* logh = scr.at<double>(o_logh);
+    URCHIN_TRY_CUDA(cudaMemsetAsync(logh, 0, sizeof(double), s));
     unsigned grid = (unsigned)std::min<int64_t>((n + 255) / 256, 2048);
-    k_bounds<<<grid, 256, 0, s>>>(p->pos_x, p->pos_y, p->pos_z, p->h, p->mass_H, n, bounds);
+    k_bounds<<<grid, 256, 0, s>>>(p->pos_x, p->pos_y, p->pos_z, p->h, p->mass_H, n, bounds, logh);
     URCHIN_TRY(launched());
     unsigned hb[8];
+    double lh = 0.0;
     URCHIN_TRY_CUDA(cudaMemcpyAsync(hb, bounds, sizeof(hb), cudaMemcpyDeviceToHost, s));
+    URCHIN_TRY_CUDA(cudaMemcpyAsync(&lh, logh, sizeof(double), cudaMemcpyDeviceToHost, s));
     URCHIN_TRY_CUDA(cudaStreamSynchronize(s));
+    b->hgeo = (float)std::exp(lh / (double)n);
     if (hb[7] & 1u) return set_error(URCHIN_ERR_NONFINITE, "urchin_build_bvh: NaN/Inf in positions, h or mass_H");
     if (hb[7] & 2u) return set_error(URCHIN_ERR_ARG, "urchin_build_bvh: h must be > 0 and mass_H >= 0");
     b->hmax = ord2f(hb[6]);

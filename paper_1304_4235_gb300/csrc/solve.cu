@@ -809,7 +809,7 @@ int Solver::order_for(const int32_t* items, int64_t n_items, const int32_t** out
     if (n_items > n || n_items < kRayOrderMinItems) return URCHIN_OK;   // item order
     if (ord_used + need > ord_cap) items_changed();
     int32_t* o = ord_base + ord_used;
-    URCHIN_TRY(ray_order(bvh, items, n_items, P.dirs, P.R, o, ord_tmp, s));
+    URCHIN_TRY(ray_order(bvh, items, n_items, P.dirs, P.R, P.l_ray, o, ord_tmp, s));
     ord_used += need;
     orders.push_back(OrderEntry{items, n_items, o});
     *out = o;
@@ -844,9 +844,29 @@ int Solver::trace(const int32_t* items, int64_t n_items, const float* tw32, cons
     return URCHIN_OK;
 }
 
-// Columns of the current x for the rays of `items` into tau (k-major).
-// Sweep 0 (all particles) also decides and builds the stored segments.
-int Solver::columns(const int32_t* items, int64_t n_items, int sweep0)
+// rows of the stored segments (direction-major, Morton slot) of particles
+// that are not active are emptied before the lists are built
+__global__ void k_clear_inactive_rows(const uint8_t* __restrict__ active, int64_t n, int R, uint32_t* counts)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n * R; i += (int64_t)gridDim.x * blockDim.x)
+        if (!active[i % n]) counts[i] = 0u;
+}
+
+// Columns of the current x for the rays of `items` into tau (k-major), from
+// the stored segments once they exist.  The segment lists (SEG_STORE, or
+// SEG_AUTO where they fit in memory) come from per-ray hit counts and one
+// filling traversal, which also gives that sweep's columns:
+//   * SEG_STORE (and SEG_AUTO with density blocks, or `build`): a counting
+//     and a filling traversal at once;
+//   * SEG_AUTO otherwise: sweep 0 traces recomputed columns and counts every
+//     ray's hits on the way, sweep 1 recomputes too, and the lists are built
+//     in sweep 2, for the particles still active: a solve that converges in
+//     two sweeps (an optically thin box) never writes them, one that goes on
+//     pays one traversal more than storing at once (262144-particle halo:
+//     292 sweeps, 0.86 s; one traversal 0.04 s).
+constexpr int kAutoStoreSweep = 2;
+
+int Solver::columns(const int32_t* items, int64_t n_items, int sweep0, bool build)
 {
     if (!sweep0 && stored) {
         SpmvArgs A{};
@@ -871,8 +891,8 @@ int Solver::columns(const int32_t* items, int64_t n_items, int sweep0)
         stats.rays += n_items * P.R;
         return URCHIN_OK;
     }
-    if (!sweep0 || P.segments == URCHIN_SEG_RECOMPUTE) return trace(items, n_items, w32, w64);
-    // count every ray's hits, then decide whether the lists fit
+    if (P.segments == URCHIN_SEG_RECOMPUTE || store_declined || (stored && sweep0))
+        return trace(items, n_items, w32, w64);
     TraceJob job{};
     job.bvh = bvh;
     job.w32 = w32;
@@ -887,14 +907,37 @@ int Solver::columns(const int32_t* items, int64_t n_items, int sweep0)
     job.out = tau;
     job.kernel = P.kernel;
     job.precision = P.precision;
-    job.mode = 1;
     job.counts = counts;
     job.near_far = P.near_far;
     job.out_near = tau_near;
     job.near_k_stride = n;
     URCHIN_TRY(order_for(items, n_items, &job.order));
-    URCHIN_TRY(timed_trace(job));
-    const int64_t rays = (int64_t)P.R * n_items;
+    const int64_t rays = (int64_t)P.R * n;
+    const bool deferred = P.segments == URCHIN_SEG_AUTO && !build && P.blocks <= 1;
+    if (deferred && !counts_ready) {
+        // recomputed columns, every ray's hits counted on the way
+        URCHIN_TRY_CUDA(cudaMemsetAsync(counts, 0, sizeof(uint32_t) * (size_t)rays, s));
+        job.mode = 0;
+        URCHIN_TRY(timed_trace(job));
+        counts_ready = true;
+        counted_all = items == nullptr && n_items == n;
+        stats.traversals += 1;
+        stats.rays += n_items * P.R;
+        return URCHIN_OK;
+    }
+    if (deferred && stats.iterations < kAutoStoreSweep) return trace(items, n_items, w32, w64);
+    if (!counts_ready || (!counted_all && items == nullptr)) {
+        URCHIN_TRY_CUDA(cudaMemsetAsync(counts, 0, sizeof(uint32_t) * (size_t)rays, s));
+        job.mode = 1;
+        URCHIN_TRY(timed_trace(job));
+        stats.traversals += 1;
+    } else if (items != nullptr) {
+        // counts from a traversal of every particle: keep the active rows only
+        const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>((rays + 255) / 256, 4096));
+        k_clear_inactive_rows<<<g, 256, 0, s>>>(active, n, P.R, counts);
+        URCHIN_TRY(launched());
+    }
+    counts_ready = true;
     uint64_t* total = reinterpret_cast<uint64_t*>(misc + 6);
     URCHIN_TRY(scan_counts_u64(counts, row_ptr, rays, scan_tmp, total, s));
     URCHIN_TRY_CUDA(cudaMemcpyAsync(row_ptr + rays, total, sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
@@ -931,10 +974,14 @@ int Solver::columns(const int32_t* items, int64_t n_items, int sweep0)
             seg_val = seg.at<void>(o_val);
         }
     }
-    if (!fits) return trace(items, n_items, w32, w64);
+    if (!fits) {
+        store_declined = true;
+        return trace(items, n_items, w32, w64);
+    }
     stored = true;
     stats.segments_stored = 1;
     stats.nnz = (int64_t)nnz;
+    job.counts = nullptr;
     job.mode = 2;
     job.row_ptr = row_ptr;
     job.seg_col = seg_col;
@@ -942,7 +989,7 @@ int Solver::columns(const int32_t* items, int64_t n_items, int sweep0)
     job.seg_hi = seg_hi;
     job.seg_val = seg_val;
     URCHIN_TRY(timed_trace(job));
-    stats.traversals += 2;
+    stats.traversals += 1;
     stats.rays += n_items * P.R;
     return URCHIN_OK;
 }
@@ -1480,7 +1527,7 @@ int Solver::adjoint(const uint8_t* state_orig, const double* xbar_orig, int cold
     if (st & kStInput) return set_error(URCHIN_ERR_ARG, "urchin_solve_vjp: state values must be in 0..3");
     n_act = hc;
     stats.n_active = n_act;
-    if (P.segments != URCHIN_SEG_RECOMPUTE) URCHIN_TRY(columns(nullptr, n, 1));   // builds the stored segments
+    if (P.segments != URCHIN_SEG_RECOMPUTE) URCHIN_TRY(columns(nullptr, n, 1, true));   // builds the stored segments
     const int64_t na = n_act;
     const int m = P.gmres_m;
     const size_t rsz = f64 ? sizeof(double) : sizeof(float);

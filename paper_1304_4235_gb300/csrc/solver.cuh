@@ -131,7 +131,10 @@ struct Solver {
     Scratch nk;
 
     ~Solver();
-    int columns(const int32_t* items, int64_t n_items, int sweep0);
+    int columns(const int32_t* items, int64_t n_items, int sweep0, bool build = false);
+    bool counts_ready = false;                   // counts[] hold every ray's hits (rows by Morton slot)
+    bool counted_all = false;                    // ... counted over all n particles
+    bool store_declined = false;                 // SEG_AUTO: the lists did not fit
     int linear_columns(const int32_t* items, int64_t n_items, const float* z32, const double* z64,
                        float* wz32, double* wz64);
     int timed_trace(TraceJob& job);

@@ -73,7 +73,8 @@ constexpr int MODE_TAU = 0, MODE_COUNT = 1, MODE_FILL = 2, MODE_SCATTER = 3;
 // cursor into the ray's stored segment list.
 template <typename Real>
 struct Sink {
-    Real sum, comp;
+    Real sum, comp;               // full chords, in traversal order
+    Real psum, pcomp;             // partial chords (FP32 queue), in the ray's queue order
     unsigned nhit, ntest;
     int64_t pos, end;
     Real coef;                    // MODE_SCATTER
@@ -96,8 +97,13 @@ __device__ __forceinline__ bool is_near(const Sink<Real>& k, float4 q, Real tc, 
     if (fabs((double)gap) > 1e-4 * (double)q.w) return gap < Real(0);
     const double ex = (double)q.x - k.ox, ey = (double)q.y - k.oy, ez = (double)q.z - k.oz;
     const double hh = (double)q.w;
-    return ex * ex + ey * ey + ez * ez < hh * hh;
+    return fma(ez, ez, fma(ey, ey, __dmul_rn(ex, ex))) < __dmul_rn(hh, hh);
 }
+
+// Rounded arithmetic the compiler may not contract into multiply-adds.
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
 
 template <typename Real> struct RealOps;
 template <> struct RealOps<float> {
@@ -259,10 +265,73 @@ __device__ __forceinline__ float m4_part_f(float b2, float u1, float u2)
     return t;
 }
 
+// int_{a1}^{a2} M4shape(sqrt(b2 + u^2)) du for 0 <= a1 <= a2 <= sqrt(1 - b2):
+// the inner piece (q <= 1/2) by its antiderivative Fi (Fi(0) = 0), the
+// outer piece by 6-point Gauss-Legendre quadrature of 2(1 - q)^3 (within
+// 6e-8 of the integral for every b2 and interval; K(0) = 0.75).  Integrating
+// over the interval itself keeps a short piece's relative accuracy (as a
+// difference of antiderivatives from 0 it would lose it).
+__constant__ float kGL6x[6] = {-0.9324695142031521f, -0.6612093864662645f, -0.2386191860831969f,
+                               0.2386191860831969f,  0.6612093864662645f,  0.9324695142031521f};
+__constant__ float kGL6w[6] = {0.1713244923791704f, 0.3607615730481386f, 0.4679139345726910f,
+                               0.4679139345726910f, 0.3607615730481386f, 0.1713244923791704f};
+
+__device__ __forceinline__ float m4_inner_fi(float b2, float rb, float a)
+{
+    const float q = sqrtf(fmaf(a, a, b2));
+    const float L = b2 > 0.f ? logf((a + q) * rb) : 0.f;
+    return a * (1.f - 6.f * b2 - 2.f * a * a) + 1.5f * a * q * q * q + 2.25f * b2 * a * q + 2.25f * b2 * b2 * L;
+}
+
+__device__ __forceinline__ float m4_seg_f(float b2, float a1, float a2)
+{
+    const float s = b2 < 0.25f ? sqrtf(0.25f - b2) : 0.f;
+    const float rb = b2 > 0.f ? rsqrtf(b2) : 0.f;
+    float r = 0.f;
+    if (a1 < s) {
+        r = m4_inner_fi(b2, rb, fminf(a2, s));
+        if (a1 > 0.f) r -= m4_inner_fi(b2, rb, a1);
+    }
+    const float lo = fmaxf(a1, s);
+    if (a2 > lo) {
+        const float m = 0.5f * (lo + a2), h = 0.5f * (a2 - lo);
+        float acc = 0.f;
+#pragma unroll
+        for (int g = 0; g < 6; ++g) {
+            const float u = fmaf(h, kGL6x[g], m);
+            const float v = 1.f - sqrtf(fmaf(u, u, b2));
+            acc = fmaf(kGL6w[g], v * v * v, acc);
+        }
+        r += 2.f * h * acc;
+    }
+    return r;
+}
+
+// Partial M4 chord over [u1, u2] (units of h, -c <= u1 < u2 <= c).  A chord
+// that straddles the closest approach (u1 < 0 < u2) is the sum of its two
+// halves, and a half that the segment does not clip is K(b2)/2 from the
+// full-chord table, so a chord clipped at one end costs one piece; a chord
+// on one side (the segment starts past the closest approach, or ends
+// before it) is integrated over its own interval.
+__device__ __forceinline__ float m4_part_q(const float2* tab, float b2, float u1, float u2, bool clip_lo,
+                                           bool clip_hi)
+{
+    const bool straddle = u1 < 0.f && u2 > 0.f;
+    // the first piece: the clipped half of a straddling chord, or the chord
+    float a1 = straddle ? 0.f : fminf(fabsf(u1), fabsf(u2));
+    float a2 = straddle ? (clip_hi ? u2 : -u1) : fmaxf(fabsf(u1), fabsf(u2));
+    float F = m4_seg_f(b2, a1, a2);
+    if (straddle) {
+        if (clip_hi && clip_lo) F += m4_seg_f(b2, 0.f, -u1);
+        else F += 0.5f * m4_full_tab(tab, b2);
+    }
+    return F;
+}
+
 // a*b - c*d with one rounding (Kahan's difference of products via FMA)
 __device__ __forceinline__ float dop(float a, float b, float c, float d)
 {
-    float w = c * d;
+    float w = __fmul_rn(c, d);
     float e = fmaf(-c, d, w);
     float f = fmaf(a, b, -w);
     return f + e;
@@ -302,6 +371,110 @@ __device__ __forceinline__ float safe_inv(double d)
     return fabs(d) > 1e-20 ? (float)(1.0 / d) : copysignf(1e30f, (float)d);
 }
 
+// ---- the packet's beam ------------------------------------------------------
+// The 32 rays of a packet are parallel (one direction d).  In a frame
+// (e1, e2, d) anchored at one live lane's origin B, a lane's segment is the
+// point (u_i, v_i) across the direction and the depth interval
+// [t_i, t_i + l_ray] along it; the beam is the box [u_lo, u_hi] x [v_lo, v_hi]
+// of the live lanes' points and the depth range [t_lo, t_hi + l_ray].  A
+// particle can only be crossed by some lane if its sphere reaches that box:
+// lateral distance from (u_j, v_j) to the box below h_j and depth range
+// [t_j - h_j, t_j + h_j] overlapping.  At a leaf, lanes 0..cnt-1 test one
+// particle each against the beam (one warp instruction stream for the whole
+// leaf) and only the particles that pass are tested per lane.  The test is
+// made conservative by a margin of a few float roundings of the coordinates,
+// so it never drops a crossing: every lane's hits, and the order in which it
+// sums them, are those of the unfiltered loop.
+struct Beam {
+    float bx, by, bz;             // anchor B
+    float e1x, e1y, e1z, e2x, e2y, e2z, dx, dy, dz;
+    float ulo, uhi, vlo, vhi, tlo, thi;
+    float eps;                    // absolute margin of the projections
+};
+
+__device__ __forceinline__ float wmin(float v)
+{
+    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ float wmax(float v)
+{
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Called by all 32 lanes with the same direction; (fx, fy, fz) is the
+// lane's (shifted) origin.  Writes the warp's beam to shared memory (out,
+// one per warp) and returns false when no lane is live.
+__device__ __forceinline__ bool make_beam(Beam* out, bool live, float fx, float fy, float fz, float dx, float dy,
+                                          float dz, float L)
+{
+    const unsigned lv = __ballot_sync(0xffffffffu, live);
+    if (!lv) return false;
+    Beam B;
+    const int a = __ffs(lv) - 1;
+    B.bx = __shfl_sync(0xffffffffu, fx, a);
+    B.by = __shfl_sync(0xffffffffu, fy, a);
+    B.bz = __shfl_sync(0xffffffffu, fz, a);
+    B.dx = dx;
+    B.dy = dy;
+    B.dz = dz;
+    // e1 perpendicular to d, from the coordinate axis least aligned with it
+    float ax = 0.f, ay = 0.f, az = 0.f;
+    if (fabsf(dx) <= fabsf(dy) && fabsf(dx) <= fabsf(dz)) ax = 1.f;
+    else if (fabsf(dy) <= fabsf(dz)) ay = 1.f;
+    else az = 1.f;
+    float e1x = dy * az - dz * ay, e1y = dz * ax - dx * az, e1z = dx * ay - dy * ax;
+    const float inv = rsqrtf(e1x * e1x + e1y * e1y + e1z * e1z);
+    e1x *= inv;
+    e1y *= inv;
+    e1z *= inv;
+    B.e1x = e1x;
+    B.e1y = e1y;
+    B.e1z = e1z;
+    B.e2x = dy * e1z - dz * e1y;
+    B.e2y = dz * e1x - dx * e1z;
+    B.e2z = dx * e1y - dy * e1x;
+    const float rx = fx - B.bx, ry = fy - B.by, rz = fz - B.bz;
+    const float u = rx * B.e1x + ry * B.e1y + rz * B.e1z;
+    const float v = rx * B.e2x + ry * B.e2y + rz * B.e2z;
+    const float t = rx * dx + ry * dy + rz * dz;
+    B.ulo = wmin(live ? u : INFINITY);
+    B.uhi = wmax(live ? u : -INFINITY);
+    B.vlo = wmin(live ? v : INFINITY);
+    B.vhi = wmax(live ? v : -INFINITY);
+    B.tlo = wmin(live ? t : INFINITY);
+    B.thi = wmax(live ? t : -INFINITY) + L;
+    // roundings of the projections: a few ulp of the coordinates' magnitude
+    const float span = fmaxf(fmaxf(B.uhi - B.ulo, B.vhi - B.vlo), B.thi - B.tlo);
+    B.eps = 1e-5f * (span + fabsf(B.bx) + fabsf(B.by) + fabsf(B.bz));
+    __syncwarp();                    // the previous beam's readers are done
+    if ((threadIdx.x & 31) == 0) *out = B;
+    __syncwarp();
+    return true;
+}
+
+// Mask of the leaf's particles (bit l for particle ref + l) that the beam can
+// reach.  Every lane calls it; lanes 0..cnt-1 test one particle each.
+__device__ __forceinline__ unsigned beam_mask(const TraceParams& P, const Beam& B, int ref, int cnt)
+{
+    const int lane = threadIdx.x & 31;
+    bool pass = false;
+    if (lane < cnt && ref >= 0 && cnt <= kLeafMax && ref + cnt <= P.n) {
+        const float4 q = __ldg(P.xyzh + ref + lane);
+        const float rx = q.x - B.bx, ry = q.y - B.by, rz = q.z - B.bz;
+        const float u = rx * B.e1x + ry * B.e1y + rz * B.e1z;
+        const float v = rx * B.e2x + ry * B.e2y + rz * B.e2z;
+        const float t = rx * B.dx + ry * B.dy + rz * B.dz;
+        const float hh = q.w * 1.00001f + B.eps + 1e-5f * (fabsf(rx) + fabsf(ry) + fabsf(rz));
+        const float du = fmaxf(fmaxf(B.ulo - u, u - B.uhi), 0.f);
+        const float dv = fmaxf(fmaxf(B.vlo - v, v - B.vhi), 0.f);
+        pass = du * du + dv * dv < hh * hh && t + hh > B.tlo && t - hh < B.thi;
+    }
+    return __ballot_sync(0xffffffffu, pass);
+}
+static_assert(kLeafMax <= 32, "a leaf's particles are filtered one per lane");
+
 // Particle index of stored segment pos: an int32, or split into 16 + 8 bits.
 // A lane writes its ray's segments at consecutive positions from a multiple
 // of 8 to a multiple of 8 (the padding), so the split halves and bytes are
@@ -321,90 +494,219 @@ __device__ __forceinline__ void store_index(const TraceParams& P, Sink<Real>& k,
     if ((pos & 3) == 3) reinterpret_cast<uint32_t*>(P.seg_hi)[pos >> 2] = k.hi_pend;
 }
 
+// ---- deferred partial chords ------------------------------------------------
+// A partial chord (a sphere cut by the segment's start or end) takes the
+// piecewise evaluation of m4_part_f, an order of magnitude more arithmetic
+// than a full chord's table lookup, and with rays of a few smoothing lengths
+// most hits are partial (every sphere holding the origin or the end point).
+// Evaluated where it is met, a warp would run that code for the few lanes
+// whose ray met one.  Instead the warp appends its partial chords to a queue
+// in shared memory and evaluates them 32 at a time, one per lane; every ray
+// then adds its own results in queue order (the lanes of one ray's items
+// found with a match), so the sums stay deterministic.
+constexpr int kPQ = 64;           // queue capacity per warp; a round takes 32
+constexpr int kPQNear = 32;       // owner flag: a near particle (near/far split)
+constexpr int kPQClipLo = 64;     // owner flag: the segment's start cuts the chord
+constexpr int kPQClipHi = 128;    // owner flag: the segment's end cuts the chord
+struct PartItem {
+    float beta2, u1, u2;          // chord in units of h: b^2/h^2 and [u1, u2]
+    int j;                        // particle (Morton slot)
+    int owner;                    // lane of the ray | kPQNear | kPQClipLo | kPQClipHi
+    float coef;                   // MODE_SCATTER: the ray's coefficient
+    int64_t pos;                  // MODE_FILL: the segment's position
+};
+struct PartQueue {
+    PartItem item[kPQ];
+    float val[32];                // results of the round being flushed
+    unsigned own[64];             // per owner (lane, lane + kPQNear): items of the round
+};
+
+// Byte offset of the queues in k_trace's dynamic shared memory: after the
+// directions (double[3R]) and the FP32 M4 table, 16-byte aligned.
+__host__ __device__ __forceinline__ size_t trace_queue_offset(int R, int kernel)
+{
+    const size_t b = sizeof(double) * 3 * (size_t)R + (kernel == URCHIN_KERNEL_M4 ? sizeof(float2) * (kKTab + 1) : 0);
+    return (b + 15) & ~size_t(15);
+}
+
+// Evaluate the first n (<= 32) queued chords, one per lane, and move the
+// rest to the front.  Every lane of the warp calls it.
+template <int KERNEL, int MODE, bool NF>
+__device__ __noinline__ void flush_partials(const TraceParams& P, const float2* tab, PartQueue* pq, int& count, int n,
+                                            Sink<float>& k)
+{
+    const int lane = threadIdx.x & 31;
+    int owner = -1;
+    float v = 0.f;
+    if (lane < n) {
+        const PartItem it = pq->item[lane];
+        const float F = KERNEL == URCHIN_KERNEL_M4
+                            ? m4_part_q(tab, it.beta2, it.u1, it.u2, (it.owner & kPQClipLo) != 0,
+                                        (it.owner & kPQClipHi) != 0)
+                            : gt_chord<float>(P, it.beta2, it.u1, it.u2);
+        const float A = __ldg(P.A32 + it.j);
+        if (MODE == MODE_SCATTER) {
+            atomicAdd(P.xbar + it.j, (double)(it.coef * (A * F)));
+        } else {
+            const bool near = NF && (it.owner & kPQNear);
+            v = near ? A * F : __ldg(P.w32 + it.j) * F;
+            if (MODE == MODE_FILL && !near) static_cast<float*>(P.seg_val)[it.pos] = A * F;
+            owner = it.owner & (31 | kPQNear);
+        }
+    }
+    if (MODE != MODE_SCATTER) {
+        pq->val[lane] = v;
+        const unsigned same = __match_any_sync(0xffffffffu, owner);
+        if (owner >= 0 && (same & ((1u << lane) - 1u)) == 0u) pq->own[owner] = same;
+        __syncwarp();
+        for (unsigned m = pq->own[lane]; m; m &= m - 1) Kahan::add(k.psum, k.pcomp, pq->val[__ffs(m) - 1]);
+        if (NF)
+            for (unsigned m = pq->own[lane + kPQNear]; m; m &= m - 1)
+                Kahan::add(k.near, k.near_c, pq->val[__ffs(m) - 1]);
+        __syncwarp();
+        pq->own[lane] = 0u;
+        pq->own[lane + kPQNear] = 0u;
+    }
+    const int rest = count - n;
+    PartItem tail;
+    if (lane < rest) tail = pq->item[n + lane];
+    __syncwarp();
+    if (lane < rest) pq->item[lane] = tail;
+    __syncwarp();
+    count = rest;
+}
+
 // FP32 hit evaluation: cheap rejection, then the impact parameter from an
 // error-free cross product, then the tabulated / piecewise chord integral.
+// FP32 hit evaluation: cheap rejection, then the impact parameter from an
+// error-free cross product; full chords from the table at once, partial
+// chords queued for flush_partials.  Every lane of the warp calls it (the
+// queue is shared); lanes that are not live only take part in the queue.
 template <int KERNEL, int MODE, bool NF>
-__device__ __forceinline__ void leaf_hits_f32(const TraceParams& P, const float2* tab, int ref, int cnt,
-                                              float sx, float sy, float sz, float dx, float dy, float dz,
-                                              float L, Sink<float>& k, unsigned& err)
+__device__ __forceinline__ void leaf_hits_f32(const TraceParams& P, const float2* tab, PartQueue* pq, int& pq_count,
+                                              int ref, int cnt, unsigned mask, bool live, float sx, float sy,
+                                              float sz, float dx, float dy, float dz, float L, Sink<float>& k,
+                                              unsigned& err)
 {
     if (ref < 0 || cnt > kLeafMax || ref + cnt > P.n) return;   // never true for a well-formed tree
-    k.ntest += (unsigned)cnt;
-    for (int j = ref; j < ref + cnt; ++j) {
-        float4 q = __ldg(P.xyzh + j);
-        float ex = q.x - sx, ey = q.y - sy, ez = q.z - sz;
-        float cx = ey * dz - ez * dy, cy = ez * dx - ex * dz, cz = ex * dy - ey * dx;
-        float h2 = q.w * q.w;
-        if (cx * cx + cy * cy + cz * cz >= 1.0001f * h2) continue;
-        cx = dop(ey, dz, ez, dy);
-        cy = dop(ez, dx, ex, dz);
-        cz = dop(ex, dy, ey, dx);
-        float b2 = cx * cx + cy * cy + cz * cz;
-        if (b2 >= h2) continue;
-        float tc = ex * dx + ey * dy + ez * dz;
-        float ch = sqrtf(h2 - b2);
-        if (tc + ch <= 0.f || tc - ch >= L) continue;
-        const bool near = NF && is_near(k, q, tc, ch);
-        if (!near) ++k.nhit;
-        if (MODE == MODE_COUNT) continue;
-        float ih = 1.f / q.w;
-        float beta2 = b2 * ih * ih;
-        float F;
-        if (tc - ch >= 0.f && tc + ch <= L) {
-            if (KERNEL == URCHIN_KERNEL_M4) F = m4_full_tab(tab, beta2);
-            else F = gt_chord<float>(P, beta2, -ch * ih, ch * ih);
-        } else {
-            float u1 = (fmaxf(0.f, tc - ch) - tc) * ih;
-            float u2 = (fminf(L, tc + ch) - tc) * ih;
-            if (KERNEL == URCHIN_KERNEL_M4) F = m4_part_f(beta2, u1, u2);
-            else F = gt_chord<float>(P, beta2, u1, u2);
-        }
-        if (MODE == MODE_SCATTER) {
-            atomicAdd(P.xbar + j, (double)(k.coef * (__ldg(P.A32 + j) * F)));
-            continue;
-        }
-        if (near) {
-            Kahan::add(k.near, k.near_c, __ldg(P.A32 + j) * F);
-            continue;
-        }
-        Kahan::add(k.sum, k.comp, __ldg(P.w32 + j) * F);
-        if (MODE == MODE_FILL) {
-            if (k.pos < k.end) {
-                store_index(P, k, k.pos, j);
-                static_cast<float*>(P.seg_val)[k.pos] = __ldg(P.A32 + j) * F;
-                ++k.pos;
-            } else {
-                err |= kStSegment;
+    if (live) k.ntest += (unsigned)__popc(mask);
+    const int lane = threadIdx.x & 31;
+    for (unsigned m = mask; m; m &= m - 1) {
+        const int j = ref + __ffs(m) - 1;
+        bool part = false, near = false;
+        int clip = 0;
+        float beta2 = 0.f, u1 = 0.f, u2 = 0.f;
+        int64_t spos = 0;
+        if (live) {
+            // The hit decision is written with explicit roundings (no
+            // multiply-add contraction left to the compiler), so that the
+            // counting and the filling traversal, separate instantiations,
+            // find exactly the same hits.
+            const float4 q = __ldg(P.xyzh + j);
+            const float ex = q.x - sx, ey = q.y - sy, ez = q.z - sz;
+            float cx = __fsub_rn(__fmul_rn(ey, dz), __fmul_rn(ez, dy));
+            float cy = __fsub_rn(__fmul_rn(ez, dx), __fmul_rn(ex, dz));
+            float cz = __fsub_rn(__fmul_rn(ex, dy), __fmul_rn(ey, dx));
+            const float h2 = __fmul_rn(q.w, q.w);
+            bool hit = fmaf(cz, cz, fmaf(cy, cy, __fmul_rn(cx, cx))) < __fmul_rn(1.0001f, h2);
+            float b2 = 0.f, tc = 0.f, ch = 0.f;
+            if (hit) {
+                cx = dop(ey, dz, ez, dy);
+                cy = dop(ez, dx, ex, dz);
+                cz = dop(ex, dy, ey, dx);
+                b2 = fmaf(cz, cz, fmaf(cy, cy, __fmul_rn(cx, cx)));
+                hit = b2 < h2;
+            }
+            if (hit) {
+                tc = fmaf(ez, dz, fmaf(ey, dy, __fmul_rn(ex, dx)));
+                ch = sqrtf(__fsub_rn(h2, b2));
+                hit = __fadd_rn(tc, ch) > 0.f && __fsub_rn(tc, ch) < L;
+            }
+            if (hit) {
+                near = NF && is_near(k, q, tc, ch);
+                if (!near) ++k.nhit;
+                if (MODE != MODE_COUNT) {
+                    const float ih = 1.f / q.w;
+                    beta2 = b2 * ih * ih;
+                    if (MODE == MODE_FILL && !near) {
+                        // the index is written now, in order; a partial chord's value at the flush
+                        if (k.pos < k.end) {
+                            store_index(P, k, k.pos, j);
+                            spos = k.pos++;
+                        } else {
+                            err |= kStSegment;
+                            hit = false;
+                        }
+                    }
+                    if (hit && __fsub_rn(tc, ch) >= 0.f && __fadd_rn(tc, ch) <= L) {
+                        const float F = KERNEL == URCHIN_KERNEL_M4 ? m4_full_tab(tab, beta2)
+                                                                   : gt_chord<float>(P, beta2, -ch * ih, ch * ih);
+                        const float A = __ldg(P.A32 + j);
+                        if (MODE == MODE_SCATTER) {
+                            atomicAdd(P.xbar + j, (double)(k.coef * (A * F)));
+                        } else if (near) {
+                            Kahan::add(k.near, k.near_c, A * F);
+                        } else {
+                            Kahan::add(k.sum, k.comp, __ldg(P.w32 + j) * F);
+                            if (MODE == MODE_FILL) static_cast<float*>(P.seg_val)[spos] = A * F;
+                        }
+                    } else if (hit) {
+                        part = true;
+                        clip = (__fsub_rn(tc, ch) < 0.f ? kPQClipLo : 0) | (__fadd_rn(tc, ch) > L ? kPQClipHi : 0);
+                        u1 = (fmaxf(0.f, tc - ch) - tc) * ih;
+                        u2 = (fminf(L, tc + ch) - tc) * ih;
+                    }
+                }
             }
         }
+        if (MODE == MODE_COUNT) continue;
+        const unsigned pb = __ballot_sync(0xffffffffu, part);
+        if (!pb) continue;
+        if (part) {
+            PartItem& it = pq->item[pq_count + __popc(pb & ((1u << lane) - 1u))];
+            it.beta2 = beta2;
+            it.u1 = u1;
+            it.u2 = u2;
+            it.j = j;
+            it.owner = lane | (near ? kPQNear : 0) | clip;
+            it.coef = MODE == MODE_SCATTER ? k.coef : 0.f;
+            it.pos = spos;
+        }
+        pq_count += __popc(pb);
+        __syncwarp();
+        if (pq_count >= 32) flush_partials<KERNEL, MODE, NF>(P, tab, pq, pq_count, 32, k);
     }
 }
 
 template <typename Real, int KERNEL, int MODE, bool NF>
-__device__ __forceinline__ void leaf_hits(const TraceParams& P, int ref, int cnt, Real sx, Real sy, Real sz,
-                                          Real dx, Real dy, Real dz, Real L, Sink<Real>& k, unsigned& err)
+__device__ __forceinline__ void leaf_hits(const TraceParams& P, int ref, int cnt, unsigned mask, Real sx, Real sy,
+                                          Real sz, Real dx, Real dy, Real dz, Real L, Sink<Real>& k, unsigned& err)
 {
     using O = RealOps<Real>;
     if (ref < 0 || cnt > kLeafMax || ref + cnt > P.n) return;   // never true for a well-formed tree
-    k.ntest += (unsigned)cnt;
-    for (int j = ref; j < ref + cnt; ++j) {
+    k.ntest += (unsigned)__popc(mask);
+    for (unsigned m = mask; m; m &= m - 1) {
+        const int j = ref + __ffs(m) - 1;
+        // explicit roundings in the hit decision, as in leaf_hits_f32
         float4 q = __ldg(P.xyzh + j);
         Real ex = Real(q.x) - sx, ey = Real(q.y) - sy, ez = Real(q.z) - sz;
-        Real tc = ex * dx + ey * dy + ez * dz;
-        Real cx = ey * dz - ez * dy, cy = ez * dx - ex * dz, cz = ex * dy - ey * dx;
-        Real b2 = cx * cx + cy * cy + cz * cz;
+        Real tc = fma(ez, dz, fma(ey, dy, mul_rn(ex, dx)));
+        Real cx = sub_rn(mul_rn(ey, dz), mul_rn(ez, dy));
+        Real cy = sub_rn(mul_rn(ez, dx), mul_rn(ex, dz));
+        Real cz = sub_rn(mul_rn(ex, dy), mul_rn(ey, dx));
+        Real b2 = fma(cz, cz, fma(cy, cy, mul_rn(cx, cx)));
         Real h = Real(q.w);
-        Real h2 = h * h;
+        Real h2 = mul_rn(h, h);
         if (b2 >= h2) continue;
-        Real ch = O::sqrt_(h2 - b2);
-        if (tc + ch <= Real(0) || tc - ch >= L) continue;
+        Real ch = O::sqrt_(sub_rn(h2, b2));
+        if (add_rn(tc, ch) <= Real(0) || sub_rn(tc, ch) >= L) continue;
         const bool near = NF && is_near(k, q, tc, ch);
         if (!near) ++k.nhit;
         if (MODE == MODE_COUNT) continue;
         Real ih = Real(1) / h;
         Real beta2 = b2 * ih * ih;
         Real F;
-        if (tc - ch >= Real(0) && tc + ch <= L) {
+        if (sub_rn(tc, ch) >= Real(0) && add_rn(tc, ch) <= L) {
             Real c = ch * ih;
             if (KERNEL == URCHIN_KERNEL_M4) F = m4_full(beta2, c);
             else F = gt_chord(P, beta2, -c, c);
@@ -439,8 +741,9 @@ __device__ __forceinline__ void leaf_hits(const TraceParams& P, int ref, int cnt
 }
 
 template <typename Real, int KERNEL, int MODE, bool NF>
-__device__ void ray_column(const TraceParams& P, const float2* tab, float4 o, Real dx, Real dy, Real dz,
-                           bool live, Sink<Real>& sk, unsigned& err, unsigned& nvisit)
+__device__ void ray_column(const TraceParams& P, const float2* tab, Beam* beam, PartQueue* pq, int& pq_count,
+                           float4 o, Real dx, Real dy, Real dz, bool live, Sink<Real>& sk, unsigned& err,
+                           unsigned& nvisit)
 {
     const Real L = Real(P.l_ray);
     const float Lf = (float)P.l_ray * 1.000001f + 1e-30f;
@@ -459,6 +762,7 @@ __device__ void ray_column(const TraceParams& P, const float2* tab, float4 o, Re
         Real sz = Real(o.z) - Real(az) * Real(P.Lbox);
         float fx = (float)sx, fy = (float)sy, fz = (float)sz;
         if (!__any_sync(0xffffffffu, live && seg_box(fx, fy, fz, ix, iy, iz, Lf, rlo, rhi))) continue;
+        if (!make_beam(beam, live, fx, fy, fz, (float)dx, (float)dy, (float)dz, Lf)) continue;
         if (NF) {
             sk.ox = (double)o.x - (double)ax * P.Lbox;
             sk.oy = (double)o.y - (double)ay * P.Lbox;
@@ -485,24 +789,22 @@ __device__ void ray_column(const TraceParams& P, const float2* tab, float4 o, Re
             int rref = __float_as_int(c.w), rcnt = __float_as_int(d.w);
             bool hl = __any_sync(0xffffffffu, live && seg_box(fx, fy, fz, ix, iy, iz, Lf, a, b));
             bool hr = __any_sync(0xffffffffu, live && rcnt >= 0 && seg_box(fx, fy, fz, ix, iy, iz, Lf, c, d));
-            if (hl && lcnt > 0) {
-                if (live) {
+            // leaf children: left then right, through one call site
+            const bool leaf_l = hl && lcnt > 0, leaf_r = hr && rcnt > 0;
+#pragma unroll 1
+            for (int q = leaf_l ? 0 : 1; q < (leaf_r ? 2 : 1); ++q) {
+                const int ref = q == 0 ? lref : rref, cnt = q == 0 ? lcnt : rcnt;
+                const unsigned mask = beam_mask(P, *beam, ref, cnt);
+                if (mask) {
                     if constexpr (sizeof(Real) == 4)
-                        leaf_hits_f32<KERNEL, MODE, NF>(P, tab, lref, lcnt, sx, sy, sz, dx, dy, dz, L, sk, err);
-                    else
-                        leaf_hits<Real, KERNEL, MODE, NF>(P, lref, lcnt, sx, sy, sz, dx, dy, dz, L, sk, err);
+                        leaf_hits_f32<KERNEL, MODE, NF>(P, tab, pq, pq_count, ref, cnt, mask, live, sx, sy, sz, dx,
+                                                        dy, dz, L, sk, err);
+                    else if (live)
+                        leaf_hits<Real, KERNEL, MODE, NF>(P, ref, cnt, mask, sx, sy, sz, dx, dy, dz, L, sk, err);
                 }
-                hl = false;
             }
-            if (hr && rcnt > 0) {
-                if (live) {
-                    if constexpr (sizeof(Real) == 4)
-                        leaf_hits_f32<KERNEL, MODE, NF>(P, tab, rref, rcnt, sx, sy, sz, dx, dy, dz, L, sk, err);
-                    else
-                        leaf_hits<Real, KERNEL, MODE, NF>(P, rref, rcnt, sx, sy, sz, dx, dy, dz, L, sk, err);
-                }
-                hr = false;
-            }
+            hl = hl && !leaf_l;
+            hr = hr && !leaf_r;
             if (hl && hr) {
                 if (sp < kStackMax) stack[sp++] = rref;
                 else err |= kStStack;
@@ -520,10 +822,21 @@ __device__ void ray_column(const TraceParams& P, const float2* tab, float4 o, Re
 }
 
 template <typename Real, int KERNEL, int MODE, bool NF>
-__global__ void __launch_bounds__(256) k_trace(TraceParams P)
+__global__ void __launch_bounds__(256, 4) k_trace(TraceParams P)
 {
     extern __shared__ double s_dirs[];
     float2* s_tab = reinterpret_cast<float2*>(s_dirs + 3 * P.R);
+    __shared__ Beam s_beam[256 / 32];
+    // the warps' partial-chord queues (FP32 modes that evaluate chords), after the table
+    constexpr bool kQueue = sizeof(Real) == 4 && MODE != MODE_COUNT;
+    PartQueue* pq = nullptr;
+    if (kQueue) {
+        const size_t off = trace_queue_offset(P.R, KERNEL);
+        pq = reinterpret_cast<PartQueue*>(reinterpret_cast<unsigned char*>(s_dirs) + off) + (threadIdx.x >> 5);
+        pq->own[threadIdx.x & 31] = 0u;
+        pq->own[(threadIdx.x & 31) + kPQNear] = 0u;
+    }
+    int pq_count = 0;
     for (int t = threadIdx.x; t < 3 * P.R; t += blockDim.x) s_dirs[t] = P.dirs[t];
     if (sizeof(Real) == 4 && KERNEL == URCHIN_KERNEL_M4)
         for (int t = threadIdx.x; t <= kKTab; t += blockDim.x) s_tab[t] = P.ktab[t];
@@ -549,8 +862,10 @@ __global__ void __launch_bounds__(256) k_trace(TraceParams P)
         float4 o = __ldg(P.xyzh + org);
         Real dx = Real(s_dirs[3 * k]), dy = Real(s_dirs[3 * k + 1]), dz = Real(s_dirs[3 * k + 2]);
         unsigned nvisit = 0;
-        Sink<Real> sk{Real(0), Real(0), 0u, 0u, 0, 0, Real(0), Real(0), Real(0), 0.0, 0.0, 0.0};
-        const int64_t ray = (int64_t)k * P.n_items + item;
+        Sink<Real> sk{Real(0), Real(0), Real(0), Real(0), 0u, 0u, 0, 0, Real(0), Real(0), Real(0), 0.0, 0.0, 0.0};
+        // stored-segment rows are indexed by direction and Morton slot (rows
+        // of particles not in the item list stay empty)
+        const int64_t ray = (int64_t)k * P.n + org;
         const int64_t orow = live ? (P.out_row ? (int64_t)P.out_row[item] : item) : 0;
         if (live && MODE == MODE_FILL) {
             sk.pos = (int64_t)P.row_ptr[ray];
@@ -560,14 +875,18 @@ __global__ void __launch_bounds__(256) k_trace(TraceParams P)
             sk.coef = static_cast<const Real*>(P.coef)[orow * P.row_stride + (int64_t)k * P.k_stride];
             live = sk.coef != Real(0);
         }
-        ray_column<Real, KERNEL, MODE, NF>(P, s_tab, o, dx, dy, dz, live, sk, err, nvisit);
+        ray_column<Real, KERNEL, MODE, NF>(P, s_tab, s_beam + (threadIdx.x >> 5), pq, pq_count, o, dx, dy, dz, live,
+                                           sk, err, nvisit);
+        if constexpr (kQueue) {
+            if (pq_count > 0) flush_partials<KERNEL, MODE, NF>(P, s_tab, pq, pq_count, pq_count, sk);
+        }
         if (slot < P.n_items) {
             hits += sk.nhit;
             tests += sk.ntest;
             visits += nvisit;
-            if (MODE == MODE_COUNT) {
+            if (MODE == MODE_COUNT || (MODE == MODE_TAU && P.counts))
                 P.counts[ray] = (sk.nhit + (unsigned)kSegPad - 1u) / (unsigned)kSegPad * (unsigned)kSegPad;
-            } else if (MODE != MODE_SCATTER) {
+            if (MODE != MODE_COUNT && MODE != MODE_SCATTER) {
                 if (MODE == MODE_FILL) {
                     // the padding (fewer than kSegPad entries) holds zero values
                     if (sk.end - sk.pos >= kSegPad || sk.pos > sk.end) err |= kStSegment;
@@ -577,7 +896,10 @@ __global__ void __launch_bounds__(256) k_trace(TraceParams P)
                             static_cast<Real*>(P.seg_val)[q] = Real(0);
                         }
                 }
-                static_cast<Real*>(P.out)[orow * P.row_stride + (int64_t)k * P.k_stride] = sk.sum;
+                // full and partial chords are summed apart, each in an order that
+                // depends on the ray alone (not on the rays sharing its warp)
+                static_cast<Real*>(P.out)[orow * P.row_stride + (int64_t)k * P.k_stride] =
+                    (sk.sum + sk.psum) - (sk.comp + sk.pcomp);
                 if (NF) {
                     const int64_t at = P.near_k_stride > 0 ? (int64_t)org + (int64_t)k * P.near_k_stride
                                                            : orow * P.row_stride + (int64_t)k * P.k_stride;
@@ -605,8 +927,11 @@ template <typename Real, int KERNEL, int MODE, bool NF>
 int launch_one(const TraceParams& P, cudaStream_t s)
 {
     const void* fn = (const void*)k_trace<Real, KERNEL, MODE, NF>;
-    const size_t smem = sizeof(double) * 3 * (size_t)P.R +
-                        ((sizeof(Real) == 4 && KERNEL == URCHIN_KERNEL_M4) ? sizeof(float2) * (kKTab + 1) : 0);
+    const size_t smem = (sizeof(Real) == 4 && MODE != MODE_COUNT)
+                            ? trace_queue_offset(P.R, KERNEL) + sizeof(PartQueue) * (256 / 32)
+                            : sizeof(double) * 3 * (size_t)P.R +
+                                  ((sizeof(Real) == 4 && KERNEL == URCHIN_KERNEL_M4) ? sizeof(float2) * (kKTab + 1) : 0);
+    if (smem > 48 * 1024) URCHIN_TRY_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int grid = 0;
     URCHIN_TRY(grid_for(fn, 256, smem, &grid));
     int64_t tasks = P.n_chunks * P.R;
@@ -736,26 +1061,30 @@ int launch_trace(const TraceJob& job, cudaStream_t s)
 
 namespace {
 
-__device__ __forceinline__ uint32_t spread10(uint32_t v)
+// Every third bit of a 64-bit word from the low 21 bits of v (the standard
+// Morton interleave).
+__device__ __forceinline__ uint64_t spread21(uint32_t v)
 {
-    v &= 0x3ffu;
-    v = (v | (v << 16)) & 0x030000ffu;
-    v = (v | (v << 8)) & 0x0300f00fu;
-    v = (v | (v << 4)) & 0x030c30c3u;
-    v = (v | (v << 2)) & 0x09249249u;
-    return v;
+    uint64_t x = v & 0x1fffffu;
+    x = (x | x << 32) & 0x001f00000000ffffull;
+    x = (x | x << 16) & 0x001f0000ff0000ffull;
+    x = (x | x << 8) & 0x100f00f00f00f00full;
+    x = (x | x << 4) & 0x10c30c30c30c30c3ull;
+    x = (x | x << 2) & 0x1249249249249249ull;
+    return x;
 }
 
-__device__ __forceinline__ uint32_t quant10(float f)
+__device__ __forceinline__ uint32_t quant21(float f)
 {
-    return (uint32_t)fminf(fmaxf(f * 1024.f, 0.f), 1023.f);
+    return (uint32_t)fminf(fmaxf(f * 2097152.f, 0.f), 2097151.f);
 }
 
-// keys of the items for one direction: Morton code of (u, v, t / E) in the
-// frame (e1, e2, d), coordinates relative to c scaled by inv into [0, 1)
+// keys of the items for one direction: the 63-bit Morton code of
+// (u, v, t / E) in the frame (e1, e2, d), coordinates relative to c scaled by
+// inv into [0, 1), as its low 32 bits (lo) and high 31 bits (hi)
 __global__ void k_ray_keys(const float4* __restrict__ xyzh, const int32_t* __restrict__ items, int64_t n_items,
-                           float3 e1, float3 e2, float3 d, float3 c, float inv, float inv_E, uint32_t* keys,
-                           int32_t* vals)
+                           float3 e1, float3 e2, float3 d, float3 c, float inv, float inv_E, uint32_t* lo,
+                           uint32_t* hi, int32_t* vals)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_items;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -764,9 +1093,19 @@ __global__ void k_ray_keys(const float4* __restrict__ xyzh, const int32_t* __res
         const float u = (rx * e1.x + ry * e1.y + rz * e1.z) * inv + 0.5f;
         const float v = (rx * e2.x + ry * e2.y + rz * e2.z) * inv + 0.5f;
         const float t = (rx * d.x + ry * d.y + rz * d.z) * inv * inv_E + 0.5f;
-        keys[i] = (spread10(quant10(u)) << 2) | (spread10(quant10(v)) << 1) | spread10(quant10(t));
+        const uint64_t key = (spread21(quant21(u)) << 2) | (spread21(quant21(v)) << 1) | spread21(quant21(t));
+        lo[i] = (uint32_t)key;
+        hi[i] = (uint32_t)(key >> 32);
         vals[i] = (int32_t)i;
     }
+}
+
+// key[p] = hi[vals[p]]: the high words in the order of the first sort
+__global__ void k_gather_hi(const uint32_t* __restrict__ hi, const int32_t* __restrict__ vals, int64_t n,
+                            uint32_t* key)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x)
+        key[p] = hi[vals[p]];
 }
 
 }  // namespace
@@ -775,20 +1114,29 @@ size_t ray_order_tmp_bytes(int64_t n_items)
 {
     Layout lay;
     lay.take(sizeof(uint32_t) * (size_t)n_items);
+    lay.take(sizeof(uint32_t) * (size_t)n_items);
     lay.take(radix_tmp_bytes(n_items));
     return lay.bytes;
 }
 
-int ray_order(const urchin_bvh* b, const int32_t* items, int64_t n_items, const double* dirs, int R,
+double ray_order_elongation(const urchin_bvh* b, double l_ray)
+{
+    const double hg = b->hgeo > 0.f ? (double)b->hgeo : 1.0;
+    return std::min(64.0, std::max(1.0, l_ray / (2.0 * hg)));
+}
+
+int ray_order(const urchin_bvh* b, const int32_t* items, int64_t n_items, const double* dirs, int R, double l_ray,
               int32_t* order, void* tmp, cudaStream_t s)
 {
     if (n_items <= 0) return URCHIN_OK;
     Layout lay;
-    const size_t o_k = lay.take(sizeof(uint32_t) * (size_t)n_items);
+    const size_t o_lo = lay.take(sizeof(uint32_t) * (size_t)n_items);
+    const size_t o_hi = lay.take(sizeof(uint32_t) * (size_t)n_items);
     const size_t o_t = lay.take(radix_tmp_bytes(n_items));
-    uint32_t* keys = reinterpret_cast<uint32_t*>(static_cast<char*>(tmp) + o_k);
+    uint32_t* lo = reinterpret_cast<uint32_t*>(static_cast<char*>(tmp) + o_lo);
+    uint32_t* hi = reinterpret_cast<uint32_t*>(static_cast<char*>(tmp) + o_hi);
     void* rt = static_cast<char*>(tmp) + o_t;
-    const double E = kRayOrderElongation;
+    const double E = ray_order_elongation(b, l_ray);
     const float3 c = make_float3(0.5f * (b->root_lo[0] + b->root_hi[0]), 0.5f * (b->root_lo[1] + b->root_hi[1]),
                                  0.5f * (b->root_lo[2] + b->root_hi[2]));
     const double ex = b->root_hi[0] - b->root_lo[0], ey = b->root_hi[1] - b->root_lo[1],
@@ -813,9 +1161,14 @@ int ray_order(const urchin_bvh* b, const int32_t* items, int64_t n_items, const 
         k_ray_keys<<<grid, 256, 0, s>>>(b->xyzh, items, n_items, make_float3((float)e1x, (float)e1y, (float)e1z),
                                         make_float3((float)e2x, (float)e2y, (float)e2z),
                                         make_float3((float)dx, (float)dy, (float)dz), c, inv, (float)(1.0 / E),
-                                        keys, vals);
+                                        lo, hi, vals);
         URCHIN_TRY(launched());
-        URCHIN_TRY(radix_sort_pairs(keys, vals, n_items, 30, rt, s));
+        // least significant word first; the radix sort is stable, so the
+        // second pass leaves equal high words in low-word order
+        URCHIN_TRY(radix_sort_pairs(lo, vals, n_items, 32, rt, s));
+        k_gather_hi<<<grid, 256, 0, s>>>(hi, vals, n_items, lo);
+        URCHIN_TRY(launched());
+        URCHIN_TRY(radix_sort_pairs(lo, vals, n_items, 31, rt, s));
     }
     return URCHIN_OK;
 }
@@ -963,7 +1316,7 @@ int trace_columns_impl(const char* fn, const urchin_bvh* bvh, const double* x, c
         job.out_row = bvh->perm;
     }
     if (n_orig >= kRayOrderMinItems) {
-        URCHIN_TRY(ray_order(bvh, job.items, n_orig, dirs, R, scr.at<int32_t>(o_ord), scr.at<void>(o_otmp), s));
+        URCHIN_TRY(ray_order(bvh, job.items, n_orig, dirs, R, l_ray, scr.at<int32_t>(o_ord), scr.at<void>(o_otmp), s));
         job.order = scr.at<int32_t>(o_ord);
     }
     job.near_far = near_out ? 1 : 0;
