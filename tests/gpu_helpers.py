@@ -43,3 +43,64 @@ def rel_err(a, b, floor=0.0):
 
 def small_halo(n=20000, seed=1405):
     return W.halo(n=n, seed=seed)
+
+
+def lnrate_sensitivity(tau, s, w):
+    """D_o = sum_k tau_ok |d ln Gamma_o / d tau_ok| of Eq. gamma_shld, in
+    log-sum-exp form (no underflow at large tau): a relative error eps in
+    every column of origin o moves ln Gamma_o by at most eps D_o."""
+    from scipy.special import logsumexp
+    tau = np.asarray(tau, dtype=np.float64)
+    s, w = np.asarray(s, dtype=np.float64), np.asarray(w, dtype=np.float64)
+    e = -tau[:, :, None] * s[None, None, :]                       # [n, R, F]
+    n = tau.shape[0]
+    with np.errstate(divide="ignore"):
+        num = logsumexp((e + np.log(w * s)[None, None, :] + np.log(tau)[:, :, None]).reshape(n, -1), axis=1)
+    den = logsumexp((e + np.log(w)[None, None, :]).reshape(n, -1), axis=1)
+    return np.exp(num - den)
+
+
+def check_sweep(w, so, x_prev, state_prev, x_next, org, nside, sweep0, tau_skip=1e-4, case_rule=2,
+                eps_col=1e-6, eps_fold=2e-6, columns=None):
+    """One FP32 sweep of the GPU against the oracle's update of the GPU's own
+    previous state, particle by particle, with a stated error model instead
+    of a quantile: the FP32 columns carry a relative error <= eps_col (the
+    column tests measure <= 3e-7) and the spectral fold <= eps_fold in ln
+    Gamma, so |ln Gamma_gpu - ln Gamma| <= dl = eps_fold + eps_col D
+    (lnrate_sensitivity) and |ln x_gpu - ln x| <= |d ln x / d ln Gamma| dl.
+    Decisions that the error can flip are checked for validity: within dl of
+    tau_eff = 1 (unlatched) either recombination case is accepted, within dl
+    of tau_skip in sweep 0 either freezing or updating.  state_prev: uint8
+    per particle (bit 0 case B latched, bit 1 frozen) or None for sweep 0.
+    Asserts, and returns the largest error / bound (<= 1) over `org`."""
+    dirs = O.healpix(nside)
+    org = np.asarray(org)
+    cols = columns if columns is not None else (lambda x, o: O.columns(w, x, dirs, origins=o))
+    tau = cols(x_prev, org)
+    G, te = O.gamma(tau, so[0], so[1])
+    dl = eps_fold + eps_col * lnrate_sensitivity(tau, so[0], so[1])
+    worst = 0.0
+    for a, i in enumerate(org):
+        xn, xp = float(x_next[i]), float(x_prev[i])
+        if not sweep0 and state_prev is not None and (state_prev[i] & 2):
+            assert xn == xp, ("frozen particle changed", i)
+            continue
+        # frozen in sweep 0 (allowed within dl of tau_skip): x stays at x_thin, which
+        # the device and the oracle compute with their own math libraries
+        if sweep0 and te[a] < tau_skip + dl[a] and abs(xn - xp) <= 1e-12 * xp:
+            continue
+        assert not sweep0 or te[a] >= tau_skip - dl[a], ("particle should be frozen", i)
+        latched = (not sweep0) and state_prev is not None and bool(state_prev[i] & 1)
+        if case_rule == 2:
+            cases = [True] if (latched or te[a] - dl[a] >= 1.0) else ([False] if te[a] + dl[a] < 1.0 else [False, True])
+        else:
+            cases = [case_rule == 1]
+        best = np.inf
+        for cb in cases:
+            e = float(O.xeq(G[a], w.nH[i], w.T[i], 0.0, cb)[0])
+            el = abs(G[a] * float(O.xeq_dgamma(G[a], w.nH[i], w.T[i], 0.0, cb)[0]) / e)
+            bound = el * dl[a] + 1e-12
+            best = min(best, abs(xn - e) / e / bound)
+        worst = max(worst, best)
+        assert best <= 1.0, ("sweep update outside the error model", int(i), best, float(te[a]), float(dl[a]))
+    return worst

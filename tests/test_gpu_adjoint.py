@@ -3,7 +3,15 @@ pinned by finite differences of the forward oracle).  Tolerances:
   columns transpose   FP64 rel 1e-10 (atomic summation order), FP32 rel 1e-5
   gamma / equilibrium transposes on identical inputs, double arithmetic: rel 1e-10
   gradient of the converged x w.r.t. the spectrum weights (FP64 columns,
-  adjoint GMRES to 1e-12): rel 1e-7 of the largest component
+  adjoint GMRES to 1e-12): rel 1e-7 per component (floor 1e-3 of the
+  largest component, where the sum over particles cancels); with FP32
+  columns (adjoint to 1e-6) rel 5e-4 per component, same floor
+Every check is per component: a transpose that sums terms of both signs is
+measured against the sum of the terms' magnitudes (the natural bound of a
+reordered sum), a product against itself.  In FP64 a grazing chord's
+closed form cancels to ~1e-16 of the kernel's central value on both sides,
+so components made of grazing chords only are held to a floor of 1e-6 of
+the largest component.
 """
 import numpy as np
 import pytest
@@ -19,9 +27,13 @@ from paper_1304_4235_gb300 import urchin as U  # noqa: E402
 from paper_1304_4235_gb300 import autograd as UA  # noqa: E402
 
 
-def _rel(a, b):
+def _rel(a, b, mag=None, floor=0.0):
+    """Largest per-component error |a - b| relative to mag (the sum of the
+    terms' magnitudes where b is a sum with cancelling terms), else to |b|,
+    never below floor * max |b|."""
     a, b = np.asarray(a, dtype=np.float64), np.asarray(b, dtype=np.float64)
-    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+    m = np.abs(b) if mag is None else np.asarray(mag, dtype=np.float64)
+    return float(np.max(np.abs(a - b) / np.maximum(m, max(floor * np.abs(b).max(), 1e-300))))
 
 
 @pytest.mark.parametrize("precision", [U.F64, U.F32])
@@ -36,9 +48,10 @@ def test_columns_vjp_matches_oracle(precision):
     dt = torch.float64 if precision == U.F64 else torch.float32
     xb = U.urchin_trace_columns_vjp(bvh, dirs, w.l_ray, torch.from_numpy(tb).to(dt).cuda(),
                                     origins=torch.from_numpy(org.astype(np.int32)).cuda(), precision=precision)
-    ref = O.columns_vjp(w, O.healpix(1), tb.astype(np.float32).astype(np.float64) if precision == U.F32 else tb,
-                        origins=org)
-    assert _rel(xb.cpu().numpy(), ref) < (1e-10 if precision == U.F64 else 1e-5)
+    tbu = tb.astype(np.float32).astype(np.float64) if precision == U.F32 else tb
+    ref = O.columns_vjp(w, O.healpix(1), tbu, origins=org)
+    mag = O.columns_vjp(w, O.healpix(1), np.abs(tbu), origins=org)
+    assert _rel(xb.cpu().numpy(), ref, mag, floor=1e-6) < (1e-10 if precision == U.F64 else 1e-5)
 
 
 def test_columns_vjp_all_origins_periodic_accumulates():
@@ -51,7 +64,8 @@ def test_columns_vjp_all_origins_periodic_accumulates():
     x0 = torch.ones(w.n, dtype=torch.float64, device="cuda")
     xb = U.urchin_trace_columns_vjp(bvh, dirs, w.l_ray, torch.from_numpy(tb).cuda(), precision=U.F64, x_bar=x0)
     ref = O.columns_vjp(w, O.healpix(1), tb) + 1.0
-    assert _rel(xb.cpu().numpy(), ref) < 1e-10
+    mag = O.columns_vjp(w, O.healpix(1), np.abs(tb)) + 1.0
+    assert _rel(xb.cpu().numpy(), ref, mag, floor=1e-6) < 1e-10
 
 
 @pytest.mark.parametrize("precision", [U.F64, U.F32])
@@ -67,7 +81,7 @@ def test_gamma_vjp_matches_oracle(precision):
     tb, wb = U.urchin_gamma_vjp(tau_t, sg[0], sg[1], torch.from_numpy(gbar).cuda())
     dG_dtau, dG_dw = O.gamma_partials(tau_used, so[0], so[1])
     assert _rel(tb.double().cpu().numpy(), gbar[:, None] * dG_dtau) < (1e-10 if precision == U.F64 else 2e-7)
-    assert _rel(wb.cpu().numpy(), gbar @ dG_dw) < 1e-10
+    assert _rel(wb.cpu().numpy(), gbar @ dG_dw, np.abs(gbar) @ dG_dw) < 1e-10
 
 
 @pytest.mark.parametrize("case_rule", [U.CASE_A, U.CASE_B, U.CASE_AUTO])
@@ -116,7 +130,7 @@ def test_solve_vjp_matches_oracle(n0, tau_skip, segments):
                                  tau_skip=tau_skip, precision=U.F64, segments=segments)
     assert vst["converged"] and vst["max_rel_dx"] <= 1e-12
     ref, mu = O.solve_vjp(w, so[0], so[1], O.healpix(1), xs, frozen, caseB, xbar)
-    assert _rel(wb.cpu().numpy(), ref) < 1e-7
+    assert _rel(wb.cpu().numpy(), ref, floor=1e-3) < 1e-7
 
 
 @pytest.mark.parametrize("segments", [U.SEG_RECOMPUTE, U.SEG_STORE])
@@ -141,7 +155,7 @@ def test_solve_vjp_f32_columns(segments):
                                  tau_skip=1e-3, precision=U.F32, segments=segments)
     assert vst["converged"]
     ref, _ = O.solve_vjp(w, so[0], so[1], O.healpix(1), xs, (stt & 2) > 0, (stt & 1) > 0, xbar)
-    assert _rel(wb.cpu().numpy(), ref) < 1e-4
+    assert _rel(wb.cpu().numpy(), ref, floor=1e-3) < 5e-4
 
 
 def test_solve_vjp_warm_start_drops_the_frozen_term():
@@ -157,7 +171,7 @@ def test_solve_vjp_warm_start_drops_the_frozen_term():
                                torch.from_numpy(xbar).cuda(), tol=1e-12, tau_skip=1e-2, precision=U.F64,
                                warm_start=True)
     ref, _ = O.solve_vjp(w, so[0], so[1], O.healpix(1), xs, (stt & 2) > 0, (stt & 1) > 0, xbar, warm_start=True)
-    assert _rel(wb.cpu().numpy(), ref) < 1e-7
+    assert _rel(wb.cpu().numpy(), ref, floor=1e-3) < 1e-7
 
 
 def test_autograd_column_misfit_gradient_matches_finite_differences():
@@ -250,4 +264,5 @@ def test_autograd_rate_gradient_in_x_matches_oracle():
     tau_o = O.columns(w, x0, O.healpix(1))
     dG_dtau, _ = O.gamma_partials(tau_o, so[0], so[1])
     ref = O.columns_vjp(w, O.healpix(1), a[:, None] * dG_dtau)
-    assert _rel(x.grad.cpu().numpy(), ref) < 1e-9
+    mag = O.columns_vjp(w, O.healpix(1), np.abs(a[:, None] * dG_dtau))
+    assert _rel(x.grad.cpu().numpy(), ref, mag, floor=1e-6) < 1e-9

@@ -11,7 +11,7 @@ import pytest
 
 import oracle as O
 import workloads as W
-from gpu_helpers import build, rel_err, spectra
+from gpu_helpers import build, check_sweep, rel_err, spectra
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -112,29 +112,32 @@ def test_solve_full_box_converges(box128):
 def test_large_box_columns_and_recomputed_sweep_sampled():
     """The large log-normal box (256^3 = 1.68e7 particles, sigma_ln 2.5,
     8 Mpc, 12 rays of 100 kpc, 400 bins): all 2.0e8 rays traced in one call
-    (FP32), 4 seeded origins compared with the oracle; then two sweeps in
-    recompute mode, the second checked at the same origins against the
-    oracle's update of the GPU's first-sweep state."""
+    (FP32), 32 seeded origins compared with the oracle's columns (its
+    uniform-grid search, itself checked equal to its brute force at two of
+    them); then sweeps 1 and 2 in recompute mode, each checked at the same
+    32 origins against the oracle's update of the GPU's previous state with
+    check_sweep's per-particle error model."""
     w = W.lognormal_box(n_side=256, box_kpc=8000.0, sigma_ln=2.5, nside=1, F=400)
     bvh, d = build(w, torch)
     dirs = U.urchin_healpix_dirs(1)
     x = _x(w.n, 7)
     tau = U.urchin_trace_columns(bvh, torch.from_numpy(x).cuda(), dirs, w.l_ray, precision=U.F32)
-    org = W.random_origins(w.n, 4, 8)
-    ref = O.columns(w, x, O.healpix(1), origins=org)
+    grid = O.Grid(w, 80.0)
+    org = W.random_origins(w.n, 32, 8)
+    ref = grid.columns(x, O.healpix(1), origins=org)
     assert rel_err(tau.double().cpu().numpy()[org], ref).max() < 1e-5
+    brute = O.columns(w, x, O.healpix(1), origins=org[:2])
+    assert rel_err(ref[:2], brute).max() < 1e-12
     del tau
     sg, so = spectra(w, torch)
-    state = torch.zeros(w.n, dtype=torch.uint8, device="cuda")
-    x1, st1 = U.urchin_solve(bvh, dirs, w.l_ray, sg[0], sg[1], d["nH"], d["T"], tol=1e-300, max_iter=1,
-                             segments=U.SEG_RECOMPUTE, precision=U.F32, raise_not_converged=False, state=state)
-    x2, st2 = U.urchin_solve(bvh, dirs, w.l_ray, sg[0], sg[1], d["nH"], d["T"], tol=1e-300, max_iter=2,
-                             segments=U.SEG_RECOMPUTE, precision=U.F32, raise_not_converged=False)
-    assert st2["segments_stored"] == 0
-    stt = state.cpu().numpy()
-    x1, x2 = x1.cpu().numpy(), x2.cpu().numpy()
-    act = np.flatnonzero((stt & 2) == 0)
-    org = np.sort(np.random.default_rng(9).choice(act, size=min(4, act.size), replace=False))
-    g1, te1 = O.gamma(O.columns(w, x1, O.healpix(1), origins=org), so[0], so[1])
-    e2 = O.xeq(g1, w.nH[org], w.T[org], 0.0, (te1 >= 1) | ((stt[org] & 1) > 0))
-    assert np.quantile(rel_err(e2, x2[org]), 0.5) < 1e-4
+    states = []
+    for k in (1, 2):
+        state = torch.zeros(w.n, dtype=torch.uint8, device="cuda")
+        xk, st = U.urchin_solve(bvh, dirs, w.l_ray, sg[0], sg[1], d["nH"], d["T"], tol=1e-300, max_iter=k,
+                                segments=U.SEG_RECOMPUTE, precision=U.F32, raise_not_converged=False, state=state)
+        assert st["segments_stored"] == 0 and st["iterations"] == k
+        states.append((xk.cpu().numpy(), state.cpu().numpy()))
+    cols = lambda xx, o: grid.columns(xx, O.healpix(1), origins=o)
+    x0 = O.xeq(so[1].sum(), w.nH, w.T, 0.0, False)
+    assert check_sweep(w, so, x0, None, states[0][0], org, 1, True, columns=cols) <= 1.0
+    assert check_sweep(w, so, states[0][0], states[0][1], states[1][0], org, 1, False, columns=cols) <= 1.0

@@ -4,7 +4,9 @@ seeded inputs.  Tolerances (stated per test):
   Gamma    FP64 rel 1e-12; FP32 rel 2e-6 on identical FP32 columns (every
            bin's exponent s_j tau formed without rounding error)
   x        equilibrium on identical FP64 inputs rel 1e-12; end to end FP64
-           rel 1e-9
+           rel 1e-9; FP32 sweeps per particle within check_sweep's error
+           model (FP32 columns to 1e-6, fold to 2e-6 in ln Gamma, propagated
+           through d ln x / d ln Gamma)
 """
 import math
 
@@ -13,7 +15,7 @@ import pytest
 
 import oracle as O
 import workloads as W
-from gpu_helpers import build, device_particles, rel_err, small_halo, spectra
+from gpu_helpers import build, check_sweep, device_particles, rel_err, small_halo, spectra
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -185,11 +187,12 @@ def test_gamma_random_columns(R, F, tau_max):
     # without rounding, so the rate is within 2e-6 (the target is 1e-5) at
     # every tau; tau_eff = -ln(Gamma / Gamma_thin) within 2e-6 absolute plus
     # the rounding of the float32 output (an ulp, 1.2e-7 tau_eff)
-    assert rel_err(g32.cpu().numpy(), g_ref).max() < 2e-6
+    # (where exp(-s tau) underflows double both rates are 0)
+    assert rel_err(g32.cpu().numpy(), g_ref, floor=1e-300).max() < 2e-6
     te32 = te32.cpu().numpy().astype(np.float64)
     assert np.all(np.abs(te32 - te_ref) <= 2e-6 + 1.2e-7 * np.abs(te_ref))
     g64, te64 = U.urchin_gamma(torch.from_numpy(tau.astype(np.float64)).cuda(), sg, wg)
-    assert rel_err(g64.cpu().numpy(), g_ref).max() < 1e-12
+    assert rel_err(g64.cpu().numpy(), g_ref, floor=1e-300).max() < 1e-12
     assert np.all(g64.cpu().numpy()[:5] == pytest.approx(wts.sum(), rel=1e-14))
 
 
@@ -256,17 +259,41 @@ def test_solve_lattice_fp64_converged(lattice):
     assert st["n_active"] == int((~fr).sum())
 
 
+def _gpu_states(w, bvh, d, sg, sweeps, **kw):
+    """x and the per-particle state (bit 0 case B latched, bit 1 frozen) after
+    1..sweeps sweeps of the GPU solve (each a fresh, deterministic solve)."""
+    out = []
+    for k in range(1, sweeps + 1):
+        state = torch.zeros(w.n, dtype=torch.uint8, device="cuda")
+        x, st = _solve_gpu(w, bvh, d, sg, U.F32, tol=1e-300, max_iter=k, state=state, **kw)
+        assert st["iterations"] == k
+        out.append((x, state.cpu().numpy()))
+    return out
+
+
+def _check_chain(w, so, states, org, nside=1, columns=None):
+    """Every sweep of the chain against the oracle's update of the GPU's
+    previous state (check_sweep's per-particle error model); sweep 0 from
+    the oracle's x_thin."""
+    x0 = O.xeq(so[1].sum(), w.nH, w.T, 0.0, False)
+    worst = check_sweep(w, so, x0, None, states[0][0], org, nside, True, columns=columns)
+    for (xp, sp), (xn, _) in zip(states[:-1], states[1:]):
+        worst = max(worst, check_sweep(w, so, xp, sp, xn, org, nside, False, columns=columns))
+    return worst
+
+
 def test_solve_halo_small_fp32_step_matched(halo_small):
+    """FP32 columns, FP64 equilibrium: sweeps 1-3, each checked at 4000
+    seeded particles against the oracle's update of the GPU's previous state
+    with the per-particle error model of check_sweep (no quantiles)."""
     w, bvh, d = halo_small
     sg, so = spectra(w, torch)
-    for sweeps in (1, 3):
-        x, st = _solve_gpu(w, bvh, d, sg, U.F32, tol=1e-300, max_iter=sweeps)
-        xr, fr, sr = O.solve(w, so[0], so[1], O.healpix(1), sweeps=sweeps)
-        err = rel_err(x, xr)
-        # x inherits the FP32 column error amplified by s tau_eff; the case
-        # switch at tau_eff = 1 may flip for particles sitting on it
-        assert np.quantile(err, 0.999) < 1e-4, sweeps
-        assert st["rays"] == sr["rays"]
+    states = _gpu_states(w, bvh, d, sg, 3)
+    worst = _check_chain(w, so, states, W.random_origins(w.n, 4000, 31))
+    assert worst <= 1.0
+    _, st = _solve_gpu(w, bvh, d, sg, U.F32, tol=1e-300, max_iter=3)
+    _, _, sr = O.solve(w, so[0], so[1], O.healpix(1), sweeps=3)
+    assert st["rays"] == sr["rays"]
 
 
 def test_solve_not_converged_and_bad_inputs(halo_small):
@@ -285,27 +312,22 @@ def test_solve_not_converged_and_bad_inputs(halo_small):
 
 @pytest.mark.parametrize("segments", [U.SEG_RECOMPUTE, U.SEG_AUTO])
 def test_solve_full_size_halo_one_sweep_sampled(segments):
-    """Benchmark-size halo: the GPU's sweep-2 x at sampled particles equals
-    the oracle's update computed from the GPU's sweep-1 state.  With stored
-    segments (the benchmark's launch configuration) sweep 2 reads its
-    columns from the padded segment lists (FP32 values, 24-bit particle
-    indices split into 16 + 8 bits, 8 segments per lane)."""
+    """Benchmark-size halo: sweeps 1-4 of the GPU at 256 seeded particles
+    against the oracle's update of the GPU's previous state, per particle
+    within check_sweep's error model.  With SEG_AUTO, sweeps 1-2 trace
+    recomputed columns (the first counting hits), sweep 3 fills the padded
+    segment lists (FP32 values, 24-bit particle indices split into 16 + 8
+    bits) and sweep 4 reads its columns from them (8 segments per lane)."""
     w = W.halo()
     bvh, d = build(w, torch)
     sg, so = spectra(w, torch)
-    x1, st1 = _solve_gpu(w, bvh, d, sg, U.F32, tol=1e-300, max_iter=1, segments=segments)
-    x2, st2 = _solve_gpu(w, bvh, d, sg, U.F32, tol=1e-300, max_iter=2, segments=segments)
-    assert bool(st2["segments_stored"]) == (segments == U.SEG_AUTO)
-    x0 = O.xeq(so[1].sum(), w.nH, w.T, 0.0, False)
-    org = W.random_origins(w.n, 200, 10)
-    # freeze decision of sweep 0 at the sample, from x0
-    g0, te0 = O.gamma(O.columns(w, x0, O.healpix(1), origins=org), so[0], so[1])
-    tau = O.columns(w, x1, O.healpix(1), origins=org)
-    g1, te1 = O.gamma(tau, so[0], so[1])
-    expect = O.xeq(g1, w.nH[org], w.T[org], 0.0, te1 >= 1)
-    expect = np.where(te0 < 1e-4, x1[org], expect)
-    err = rel_err(x2[org], expect)
-    assert np.quantile(err, 0.99) < 1e-4
+    states = _gpu_states(w, bvh, d, sg, 4, segments=segments)
+    _, st2 = _solve_gpu(w, bvh, d, sg, U.F32, tol=1e-300, max_iter=2, segments=segments)
+    _, st4 = _solve_gpu(w, bvh, d, sg, U.F32, tol=1e-300, max_iter=4, segments=segments, profile=True)
+    assert st2["segments_stored"] == 0
+    assert bool(st4["segments_stored"]) == (segments == U.SEG_AUTO)
+    assert st4["spmv_launches"] == (1 if segments == U.SEG_AUTO else 0)
+    assert _check_chain(w, so, states, W.random_origins(w.n, 256, 10)) <= 1.0
 
 
 # --------------------------------------------------------------------------
@@ -330,13 +352,15 @@ def test_stored_segments_match_recompute_fp64(lattice, sweeps):
 
 
 def test_stored_segments_match_recompute_fp32(halo_small):
+    """Four FP32 sweeps with stored segments: every sweep within
+    check_sweep's error model of the oracle's update of the GPU's previous
+    state, like the recomputed columns (test_solve_halo_small_fp32_step_matched)."""
     w, bvh, d = halo_small
     sg, so = spectra(w, torch)
-    xr, sr = _solve_gpu(w, bvh, d, sg, U.F32, tol=1e-300, max_iter=4)
-    xs, ss = _solve_gpu(w, bvh, d, sg, U.F32, tol=1e-300, max_iter=4, segments=U.SEG_AUTO)
+    states = _gpu_states(w, bvh, d, sg, 4, segments=U.SEG_AUTO)
+    _, ss = _solve_gpu(w, bvh, d, sg, U.F32, tol=1e-300, max_iter=4, segments=U.SEG_AUTO)
     assert ss["segments_stored"] == 1
-    err = rel_err(xs, xr)
-    assert np.quantile(err, 0.999) < 1e-4
+    assert _check_chain(w, so, states, W.random_origins(w.n, 2000, 32)) <= 1.0
 
 
 def test_newton_reaches_plain_fixed_point_lattice(lattice):
