@@ -1,27 +1,35 @@
 #!/usr/bin/env python
-"""Benchmark of the reverse ray tracing solve (Altay & Theuns, arXiv:1304.4235)
-on the 262144-particle self-shielding halo: n_H = 10 (r/kpc)^-2 cm^-3 over
-r = 1-100 kpc, T = 1e4 K, h from 48 neighbours, 12 HEALPix rays per particle
-of length 200 kpc, 100 frequency bins (nu^-1.5, 13.6-54.4 eV), FP32 columns
-and spectral sum, FP64 equilibrium; iterate to max |dx|/x < 1e-3.
+"""Benchmark of the reverse ray tracing hot path (Altay & Theuns,
+arXiv:1304.4235) on the large log-normal box: 2^24 SPH particles (256^3)
+sampling a log-normal density field (sigma_ln rho = 2.5, P(k) ~ k^-2.5, mean
+n_H = 1e-5 cm^-3, T = 1e4 (rho/rho_mean)^0.6 K) in a periodic 8 Mpc box, h
+from 32 neighbours, 12 HEALPix rays of 100 kpc per particle with periodic
+wrapping, 400 frequency bins (nu^-1.5, 13.6-54.4 eV), FP32 columns and
+spectral sum, FP64 equilibrium.
 
-One step = one full pass of the hot path on a fresh copy of the inputs:
-BVH build, then the solve from x_thin to convergence.  Metric: rays/s (all
-rays traced, value and tangent) and particle-updates/s, whole job.
+One step = one full solve of the hot path: BVH build, then the Sec. 4
+iteration from x_thin to the paper's stopping test (max |dx|/x < 1e-3), each
+sweep tracing every active particle's 12 rays (Eq. colden, FP32 columns),
+folding them through the spectrum (Eq. gamma_shld) and updating x in FP64
+(Eq. xroots); segment lists stored once a solve runs past two sweeps and
+they fit in HBM (the box converges in two sweeps, so its columns are
+recomputed).  Metric: rays/s and particle-updates/s, whole job.  Beside it
+(untimed by the step count, CUDA events): wall time to x within rel 1e-3 of
+a tightly converged x* for plain sweeps and for Newton-Krylov, the adjoint
+gradient with recomputed segments, the 262144-particle halo and the
+differentiation workload.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--method plain|newton]
-                  [--segments recompute|store|auto] [--impl ours|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload c5|halo] [--no-compare] [--no-cpu-baseline] [--no-e2e]
 
-Under torchrun every rank solves its own copy of the halo (replicas; the
-method needs no exchange between independent halos) and rank 0 prints one
-JSON line.
+Under torchrun every rank solves its own copy (replicas; independent boxes
+need no exchange) and rank 0 prints one JSON line.
 """
 from __future__ import annotations
 
 import argparse
 import hashlib
 import json
-import math
 import os
 import statistics
 import subprocess
@@ -35,24 +43,35 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "rays/s and particle-updates/s to converged x (rel 1e-3), Newton+adjoint vs plain"
-def workload_name(w) -> str:
-    """The halo as benchmarked: particles, HEALPix N_side, ray length, bins."""
+
+# The benchmark workloads (seeded generators of workloads/): the large
+# log-normal box (default) and the 262144-particle self-shielding halo.
+WORKLOADS = {
+    "c5": ("lognormal_box", dict(n_side=256, box_kpc=8000.0, sigma_ln=2.5, nside=1, F=400)),
+    "halo": ("halo", dict()),
+}
+
+# Grid cell (kpc) of the oracle's uniform-grid search for each workload.
+GRID_CELL = {"c5": 80.0, "halo": 4.0}
+
+
+def workload_name(key: str, w) -> str:
+    if w.name == "lognormal_box":
+        side = round(w.n ** (1 / 3))
+        sig = WORKLOADS[key][1].get("sigma_ln", 2.0)
+        return f"lognormal_{side}cube_sigma{sig:g}_L{w.box:g}kpc_nside{w.nside}_l{w.l_ray:g}kpc_F{w.F}"
     return f"halo_{w.n}_nside{w.nside}_l{w.l_ray:g}kpc_F{w.F}"
 
+
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per unit of work
-# of a kernel, from one ncu capture, keyed by the hash of the kernel's source
+# of a kernel from one ncu capture, keyed by the hash of the kernel's source
 # files at capture time; a changed kernel reports traffic null.
-#   k_spmv: bytes per stored segment read;  k_trace: bytes per ray-sphere hit
+#   k_trace: bytes per ray-sphere hit;  k_spmv: bytes per stored segment
 MEASURED_TRAFFIC = {
-    # 65536-particle halo: 2.2773e9 DRAM bytes for 3.2360e8 segments (rays padded
-    # to multiples of 8) in one launch of k_spmv8 (7 algorithmic bytes per segment);
-    # captured at 41377b11515427e3, whose sources differ from 87756054aa5bee94
-    # only in the rewrapped file comment of linalg.cu
-    "k_spmv": {"41377b11515427e3": 7.038, "87756054aa5bee94": 7.038},
     "k_trace": {},
+    "k_spmv": {},
 }
-KERNEL_SOURCES = {"k_spmv": ("linalg.cu", "linalg.cuh"),
-                  "k_trace": ("trace.cu", "common.cuh")}
+KERNEL_SOURCES = {"k_trace": ("trace.cu", "common.cuh"), "k_spmv": ("linalg.cu", "linalg.cuh")}
 
 
 def source_hash(kernel: str) -> str:
@@ -66,19 +85,23 @@ def source_hash(kernel: str) -> str:
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--method", choices=["plain", "newton"], default="plain")
-    ap.add_argument("--segments", choices=["recompute", "store", "auto"], default="auto")
-    ap.add_argument("--blocks", type=int, default=1, help="update order: 1 Jacobi, B>1 density blocks")
-    ap.add_argument("--no-compare", action="store_true", help="skip the untimed Newton / tight-tolerance runs")
-    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--workload", choices=list(WORKLOADS), default="c5")
+    ap.add_argument("--no-compare", action="store_true", help="skip the untimed convergence / adjoint runs")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--max-iter", type=int, default=1000, help="sweep / Newton-step limit of one solve")
-    ap.add_argument("--halo-n", type=int, default=262144, help="particles (profiling of smaller cases)")
+    ap.add_argument("--max-iter", type=int, default=4000, help="sweep / Newton-step limit of one solve")
+    ap.add_argument("--cache-dir", default=os.path.join(ROOT, "_cache"), help="generated inputs")
     return ap.parse_args()
+
+
+def load_workload(key: str, cache_dir: str):
+    import workloads as W
+    fn, kw = WORKLOADS[key]
+    return W.cached(getattr(W, fn), cache_dir, **kw)
 
 
 def peaks():
@@ -155,43 +178,62 @@ def combine_ranks(total_ms: float, counts, device=None):
     return float(t.item()), [float(v) for v in c.tolist()]
 
 
-def oracle_sample(w, s, wts, dirs, seconds: float):
-    """The FP64 oracle on a bounded sample of the workload: one sweep (columns
-    of every ray, Gamma and the equilibrium x) for a seeded sample of origins
-    sized to take about `seconds` of CPU time."""
-    import oracle as O
-    import workloads as W
+class OracleSample:
+    """The FP64 oracle (test infrastructure) on a bounded sample of the
+    workload: its uniform-grid search (equal to the brute-force sums of Eq.
+    colden to rounding order) built once, then one sweep -- columns of every
+    ray, Gamma and the equilibrium x -- for seeded samples of origins sized to
+    take about `seconds` of CPU time."""
 
-    x0 = O.xeq(wts.sum(), w.nH, w.T, 0.0, False)
+    def __init__(self, w, cell: float):
+        import oracle as O
 
-    def run(count, seed):
+        self.O, self.w = O, w
+        e, J = w.spectrum()
+        self.s, self.wts = O.spectrum(e, J, w.gamma_thin)
+        self.dirs = O.healpix(w.nside)
+        self.x0 = O.xeq(self.wts.sum(), w.nH, w.T, 0.0, False)
+        t0 = time.perf_counter()
+        self.grid = O.Grid(w, cell)
+        self.build_s = time.perf_counter() - t0
+        self.cell = cell
+        self.count = 64
+
+    def run(self, count: int, seed: int) -> float:
+        import workloads as W
+
+        O, w = self.O, self.w
         org = W.random_origins(w.n, count, seed)
         t0 = time.perf_counter()
-        tau = O.columns(w, x0, dirs, origins=org)
-        g, te = O.gamma(tau, s, wts)
+        tau = self.grid.columns(self.x0, self.dirs, origins=org)
+        g, te = O.gamma(tau, self.s, self.wts)
         O.xeq(g, w.nH[org], w.T[org], 0.0, te >= 1)
         return time.perf_counter() - t0
 
-    t = run(32, 1)
-    count = int(min(w.n, max(32, 32 * seconds / max(t, 1e-3))))
-    dt = run(count, 2)
-    rays = count * dirs.shape[0]
-    return {"rays": rays, "origins": count, "seconds": dt, "cores": O.num_threads()}
+    def sample(self, seconds: float, seed: int):
+        """One sample of about `seconds`; the size is calibrated on the first call."""
+        if self.count == 64:
+            t = self.run(64, seed + 1000)
+            self.count = int(min(self.w.n, max(64, 64 * seconds / max(t, 1e-3))))
+        dt = self.run(self.count, seed)
+        return {"rays": self.count * self.dirs.shape[0], "origins": self.count, "seconds": dt,
+                "cores": self.O.num_threads()}
+
+    def describe(self, r) -> str:
+        return (f"{r['origins']} seeded origins x {self.dirs.shape[0]} rays, one sweep (columns by the "
+                f"oracle's uniform-grid search, {self.cell:g} kpc cells, {self.grid.entries} entries, built once "
+                f"in {self.build_s:.1f} s and not counted; FP64 Gamma and x) per sample")
 
 
-def reference_arm(args, w):
-    import oracle as O
-
+def reference_arm(args, key, w):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    e, J = w.spectrum()
-    s, wts = O.spectrum(e, J, w.gamma_thin)
-    dirs = O.healpix(w.nside)
+    ors = OracleSample(w, GRID_CELL[key])
     per = max(2.0, args.cpu_seconds / max(1, args.steps + args.warmup))
-    for _ in range(args.warmup):
-        oracle_sample(w, s, wts, dirs, per)
-    runs = [oracle_sample(w, s, wts, dirs, per) for _ in range(args.steps)]
+    for i in range(args.warmup):
+        ors.sample(per, 1 + i)
+    runs = [ors.sample(per, 100 + i) for i in range(args.steps)]
     rays = sum(r["rays"] for r in runs)
     secs = sum(r["seconds"] for r in runs)
     value = rays / secs
@@ -199,23 +241,124 @@ def reference_arm(args, w):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": workload_name(w), "l2": "n/a (CPU)"},
+        "data": "synthetic", "config": {"workload": workload_name(key, w), "l2": "n/a (CPU)"},
         "particle_updates_per_s": sum(r["origins"] for r in runs) / secs,
-        "cpu_baseline": {"value": value, "unit": "rays/s", "cores": runs[0]["cores"], "kind": "oracle",
-                         "sample": f"{runs[0]['origins']} seeded origins x {dirs.shape[0]} rays, one sweep "
-                                   f"(brute-force columns over all {w.n} particles, Gamma, x) per step"},
+        "cpu_baseline": {"value": value, "unit": "rays/s", "cores": runs[0]["cores"], "kind": "oracle-grid",
+                         "sample": ors.describe(runs[0])},
         "e2e": {"value": value, "unit": "rays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
+class Device:
+    """The workload's inputs as pinned host tensors and on the device, the
+    spectrum and the ray set."""
+
+    def __init__(self, w, dev):
+        import torch
+        from paper_1304_4235_gb300 import urchin as U
+
+        self.w, self.dev, self.U = w, dev, U
+        pos = w.pos.astype(np.float32)
+        host = {
+            "px": np.ascontiguousarray(pos[:, 0]), "py": np.ascontiguousarray(pos[:, 1]),
+            "pz": np.ascontiguousarray(pos[:, 2]), "h": np.ascontiguousarray(w.h, dtype=np.float32),
+            "m": np.ascontiguousarray(w.mass_H), "nH": np.ascontiguousarray(w.nH),
+            "T": np.ascontiguousarray(w.T),
+        }
+        self.pinned = {k: torch.from_numpy(v).pin_memory() for k, v in host.items()}
+        self.d = {k: v.to(dev) for k, v in self.pinned.items()}
+        e, J = w.spectrum()
+        s_h, w_h = U.urchin_spectrum_weights(e, J, w.gamma_thin)
+        self.s, self.wts = torch.from_numpy(s_h).to(dev), torch.from_numpy(w_h).to(dev)
+        self.dirs = U.urchin_healpix_dirs(w.nside)
+
+    def bvh(self, d=None):
+        d = self.d if d is None else d
+        w = self.w
+        return self.U.urchin_build_bvh(d["px"], d["py"], d["pz"], d["h"], d["m"], w.periodic, w.box, w.unit_cm)
+
+    def solve(self, bvh, d=None, s=None, wts=None, **kw):
+        d = self.d if d is None else d
+        kw.setdefault("precision", self.U.F32)
+        kw.setdefault("raise_not_converged", False)
+        return self.U.urchin_solve(bvh, self.dirs, self.w.l_ray, self.s if s is None else s,
+                                   self.wts if wts is None else wts, d["nH"], d["T"], **kw)
+
+    def solve_step(self, d=None, max_iter=4000):
+        """One full solve: BVH build, then plain sweeps from x_thin to
+        max |dx|/x < 1e-3 (segments stored where a long solve pays for them)."""
+        bvh = self.bvh(d)
+        x, st = self.solve(bvh, d, tol=1e-3, max_iter=max_iter, segments=self.U.SEG_AUTO, profile=True)
+        bvh.close()
+        return x, st
+
+
+def events():
+    import torch
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def timed(stream, fn):
+    """(result, seconds) of fn() bracketed by CUDA events on `stream`."""
+    a, b = events()
+    a.record(stream)
+    r = fn()
+    b.record(stream)
+    b.synchronize()
+    return r, a.elapsed_time(b) * 1e-3
+
+
+def roofline_spmv(stats, hbm, peak_kind):
+    """k_spmv8 (stored-segment columns) against the HBM roofline: 8
+    algorithmic bytes per segment (a 4-byte particle index and a 4-byte
+    value; the kernel moves 7, the index split in 16 + 8 bits), plus each
+    ray's 4-byte column and the 4-byte x gather per particle, over the
+    launch's mean duration."""
+    launches = sum(st["spmv_launches"] for st in stats)
+    spmv_s = sum(st["spmv_s"] for st in stats)
+    moved = sum(st["spmv_bytes"] for st in stats)          # 7 per segment + columns + x
+    st0 = stats[-1]
+    extra = launches * (st0["n_active"] * 12 * 4 + st0["n_active"] * 4)
+    seg = max(moved - extra, 0) / 7.0
+    per_bytes = (seg * 8 + extra) / max(launches, 1)
+    per_s = spmv_s / max(launches, 1)
+    achieved = per_bytes / per_s / 1e9 if per_s > 0 else None
+    t = MEASURED_TRAFFIC["k_spmv"].get(source_hash("k_spmv"))
+    return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm if achieved else None, "traffic": (t * seg / max(launches, 1)) if t else None,
+            "kernel": "k_spmv8 (FP32 stored segments)", "peak_kind": peak_kind, "alg_bytes_per_launch": per_bytes,
+            "launch_ms": per_s * 1e3, "segments_per_launch": seg / max(launches, 1)}
+
+
+def roofline(stats, trace_launches_total, hbm, peak_kind):
+    """k_trace against the HBM roofline: algorithmic bytes per launch (every
+    ray-sphere hit reads a 16-byte particle record and its 4-byte weight; every
+    ray writes its 4-byte column) over the launch's mean duration."""
+    hits = sum(st["hits"] for st in stats)
+    rays = sum(st["rays"] for st in stats)
+    trace_s = sum(st["trace_s"] for st in stats)
+    n = max(trace_launches_total, 1)
+    per_bytes = (hits * 20 + rays * 4) / n
+    per_s = trace_s / n
+    achieved = per_bytes / per_s / 1e9 if per_s > 0 else None
+    t = MEASURED_TRAFFIC["k_trace"].get(source_hash("k_trace"))
+    return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm if achieved else None,
+            "traffic": (t * hits / n) if t else None,
+            "kernel": "k_trace<float,M4> (FP32 columns, recomputed)", "peak_kind": peak_kind,
+            "alg_bytes_per_launch": per_bytes, "launch_ms": per_s * 1e3,
+            "hits_per_launch": hits / n, "rays_per_launch": rays / n,
+            "sphere_tests_per_hit": sum(st["sphere_tests"] for st in stats) / max(hits, 1),
+            "node_visits_per_hit": sum(st["node_visits"] for st in stats) / max(hits, 1)}
+
+
 def main():
     args = parse()
-    import workloads as W
-
-    w = W.halo(n=args.halo_n)
+    key = args.workload
+    w = load_workload(key, args.cache_dir)
     if args.impl == "reference":
-        reference_arm(args, w)
+        reference_arm(args, key, w)
         return
 
     import torch
@@ -232,49 +375,16 @@ def main():
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     U.load()
-
-    method = U.METHOD_NEWTON if args.method == "newton" else U.METHOD_PLAIN
-    segs = {"recompute": U.SEG_RECOMPUTE, "store": U.SEG_STORE, "auto": U.SEG_AUTO}[args.segments]
-    pos = w.pos.astype(np.float32)
-    host = {
-        "px": np.ascontiguousarray(pos[:, 0]), "py": np.ascontiguousarray(pos[:, 1]),
-        "pz": np.ascontiguousarray(pos[:, 2]), "h": np.ascontiguousarray(w.h, dtype=np.float32),
-        "m": np.ascontiguousarray(w.mass_H), "nH": np.ascontiguousarray(w.nH),
-        "T": np.ascontiguousarray(w.T),
-    }
-    pinned = {k: torch.from_numpy(v).pin_memory() for k, v in host.items()}
-    d = {k: v.to(dev) for k, v in pinned.items()}
-    e, J = w.spectrum()
-    s_h, w_h = U.urchin_spectrum_weights(e, J, w.gamma_thin)
-    s_d, w_d = torch.from_numpy(s_h).to(dev), torch.from_numpy(w_h).to(dev)
-    dirs = U.urchin_healpix_dirs(w.nside)
+    D = Device(w, dev)
     stream = torch.cuda.current_stream(dev)
+    # inputs larger than L2 (129 MB) on the largest box; the halo's are
+    # smaller, so a 256 MB write flushes L2 before every timed step
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    # the timed method: plain sweeps to the paper's dx_tol = 1e-3, or
-    # Newton-Krylov to dx_tol = 1e-5 (GMRES(60) to relative residual 1e-4)
-    timed = dict(tol=1e-3) if method == U.METHOD_PLAIN else dict(tol=1e-5, gmres_m=60, newton_eta=1e-4)
-
-    def step(dd, x_out=None, meth=None, tol=None, max_iter=None, gmres_m=None, newton_eta=None):
-        tol = timed["tol"] if tol is None else tol
-        gmres_m = timed.get("gmres_m", 20) if gmres_m is None else gmres_m
-        newton_eta = timed.get("newton_eta", 0.0) if newton_eta is None else newton_eta
-        bvh = U.urchin_build_bvh(dd["px"], dd["py"], dd["pz"], dd["h"], dd["m"], w.periodic, w.box, w.unit_cm)
-        x = torch.empty(w.n, dtype=torch.float64, device=dev) if x_out is None else x_out
-        x, st = U.urchin_solve(bvh, dirs, w.l_ray, s_d, w_d, dd["nH"], dd["T"], x, tol=tol, tau_skip=1e-4,
-                               max_iter=max_iter or args.max_iter, method=method if meth is None else meth,
-                               segments=segs, precision=U.F32, case_rule=U.CASE_AUTO, profile=True,
-                               raise_not_converged=False, blocks=args.blocks, gmres_m=gmres_m,
-                               newton_eta=newton_eta)
-        bvh.close()
-        return x, st
-
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
     for _ in range(args.warmup):
-        step(d)
-
+        D.solve_step(max_iter=args.max_iter)
     clocks = Clocks(dev.index if dev.index is not None else 0)
-    stats = []
-    step_ms = []
+    stats, step_s = [], []
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize(dev)
@@ -282,51 +392,42 @@ def main():
     clocks.start()
     for _ in range(args.steps):
         flush.zero_()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        _, st = step(d)
-        b.record(stream)
-        b.synchronize()
-        step_ms.append(a.elapsed_time(b))
+        (_, st), dt = timed(stream, lambda: D.solve_step(max_iter=args.max_iter))
+        step_s.append(dt)
         stats.append(st)
     torch.cuda.synchronize(dev)
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
     launches = U.urchin_kernel_launches() - launches0
-
-    total_ms = sum(step_ms)
+    total_ms = 1e3 * sum(step_s)
     rays = sum(st["rays"] for st in stats)
     updates = sum(st["particle_updates"] for st in stats)
-    hits = sum(st["hits"] for st in stats)
-    trace_s = sum(st["trace_s"] for st in stats)
-    trace_launches = sum(st["trace_launches"] for st in stats)
     total_ms, (rays, updates) = combine_ranks(total_ms, (rays, updates), device=dev)
 
     # end to end through the public API with host buffers: pinned H2D of the
-    # inputs, build, solve, D2H of x, all inside the timed region
+    # inputs, build, sweep, D2H of x, all inside the timed region
     e2e = None
     if not args.no_e2e:
         x_host = torch.empty(w.n, dtype=torch.float64).pin_memory()
-        e2e_ms, e2e_rays = [], 0
-        h2d = sum(v.numel() * v.element_size() for v in pinned.values())
+        h2d = sum(v.numel() * v.element_size() for v in D.pinned.values())
         d2h = x_host.numel() * x_host.element_size()
+        e2e_s, e2e_rays = [], 0
+
+        def e2e_step():
+            dd = {k: v.to(dev, non_blocking=True) for k, v in D.pinned.items()}
+            x, st = D.solve_step(dd, max_iter=args.max_iter)
+            x_host.copy_(x, non_blocking=True)
+            return st
+
         for _ in range(args.steps):
             flush.zero_()
             torch.cuda.synchronize(dev)
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            dd = {k: v.to(dev, non_blocking=True) for k, v in pinned.items()}
-            x, st = step(dd)
-            x_host.copy_(x, non_blocking=True)
-            b.record(stream)
-            b.synchronize()
-            e2e_ms.append(a.elapsed_time(b))
+            st, dt = timed(stream, e2e_step)
+            e2e_s.append(dt)
             e2e_rays += st["rays"]
-        e2e = {"value": e2e_rays / (sum(e2e_ms) * 1e-3) * world, "unit": "rays/s",
-               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+        e2e = {"value": e2e_rays / sum(e2e_s) * world, "unit": "rays/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
 
     if rank != 0:
         if world > 1:
@@ -334,180 +435,175 @@ def main():
         return
 
     hbm, peak_kind = peaks()
-    # per-kernel GPU time of the timed steps (CUDA events on the solve's stream)
-    spmv_s = sum(st["spmv_s"] for st in stats)
+    trace_s = sum(st["trace_s"] for st in stats)
     sweep_s = sum(st["sweep_s"] for st in stats)
-    spmv_launches = sum(st["spmv_launches"] for st in stats)
-    spmv_bytes = sum(st["spmv_bytes"] for st in stats)
-    trace_bytes = hits * 20 + sum(st["rays"] for st in stats if st["spmv_launches"] == 0) * 4
+    trace_launches = sum(st["trace_launches"] for st in stats)
     kernels = {
-        "k_spmv": {"s": spmv_s, "launches": spmv_launches},
         "k_trace": {"s": trace_s, "launches": trace_launches},
-        "k_sweep": {"s": sweep_s, "launches": sum(st["sweep_launches"] for st in stats)},
+        "k_sweep_pp": {"s": sweep_s, "launches": sum(st["sweep_launches"] for st in stats)},
+        "k_spmv8": {"s": sum(st["spmv_s"] for st in stats), "launches": sum(st["spmv_launches"] for st in stats)},
     }
     for k in kernels.values():
         k["share_of_step"] = k["s"] / (total_ms * 1e-3 / world) if total_ms > 0 else None
-    if spmv_s >= trace_s and spmv_launches > 0:
-        per_bytes = spmv_bytes / spmv_launches
-        per_s = spmv_s / spmv_launches
-        # 4-byte value + 3-byte split particle index per FP32 segment (n <= 2^24);
-        # the per-ray output and per-particle gather bytes are ~0.1 % of a launch
-        seg_per_launch = (spmv_bytes / spmv_launches) / (7.0 if w.n <= (1 << 24) else 8.0)
-        t = MEASURED_TRAFFIC["k_spmv"].get(source_hash("k_spmv"))
-        roof = {"bound": "hbm", "achieved": per_bytes / per_s / 1e9, "peak": hbm, "unit": "GB/s",
-                "frac": per_bytes / per_s / 1e9 / hbm,
-                "traffic": (t * seg_per_launch) if t else None,
-                "kernel": "k_spmv8 (FP32 stored segments)", "peak_kind": peak_kind,
-                "alg_bytes_per_launch": per_bytes, "launch_ms": per_s * 1e3}
-    else:
-        per_bytes = trace_bytes / max(trace_launches, 1)
-        per_s = trace_s / max(trace_launches, 1)
-        t = MEASURED_TRAFFIC["k_trace"].get(source_hash("k_trace"))
-        roof = {"bound": "hbm", "achieved": per_bytes / per_s / 1e9 if per_s > 0 else None, "peak": hbm,
-                "unit": "GB/s", "frac": (per_bytes / per_s / 1e9 / hbm) if per_s > 0 else None,
-                "traffic": (t * hits / max(trace_launches, 1)) if t else None,
-                "kernel": "k_trace<float,M4>", "peak_kind": peak_kind,
-                "alg_bytes_per_launch": per_bytes, "launch_ms": per_s * 1e3}
-    roof["traversal"] = {"hits_per_launch": hits / max(trace_launches, 1), "launch_ms": 1e3 * trace_s / max(trace_launches, 1),
-                         "sphere_tests_per_hit": sum(st["sphere_tests"] for st in stats) / max(hits, 1),
-                         "node_visits_per_hit": sum(st["node_visits"] for st in stats) / max(hits, 1)}
     st0 = stats[-1]
     line = {
         "metric": METRIC, "value": rays / (total_ms * 1e-3), "unit": "rays/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": workload_name(w), "particles": w.n, "rays_per_particle": w.R, "l_ray_kpc": w.l_ray,
-                   "bins": w.F, "method": args.method, "segments": args.segments, "blocks": args.blocks,
-                   "tol": timed["tol"], "l2": "flushed before each step (256 MB write); stored segments >> L2"},
+        "config": {"workload": workload_name(key, w), "particles": w.n, "rays_per_particle": w.R,
+                   "l_ray_kpc": w.l_ray, "bins": w.F, "method": "plain", "tol": 1e-3, "segments": "auto",
+                   "step": "BVH build + plain sweeps from x_thin to max |dx|/x < 1e-3",
+                   "l2": "inputs > L2 (129 MB); a 256 MB write before each step"},
         "particle_updates_per_s": updates / (total_ms * 1e-3),
-        "iterations": st0["iterations"], "n_active": st0["n_active"], "converged": bool(st0["converged"]),
-        "segments_stored": bool(st0["segments_stored"]), "nnz": st0["nnz"],
+        "iterations": st0["iterations"], "converged": bool(st0["converged"]),
+        "segments_stored": bool(st0["segments_stored"]), "n_active": st0["n_active"], "hits_per_step": st0["hits"],
         "wall_s_to_converged": total_ms * 1e-3 / args.steps,
         "gpu_launches": int(launches),
-        "roofline": roof,
+        "roofline": (roofline_spmv(stats, hbm, peak_kind) if sum(st["spmv_s"] for st in stats) > trace_s
+                     else roofline(stats, trace_launches, hbm, peak_kind)),
         "kernels": kernels,
         "clocks": clk,
         "e2e": e2e,
     }
     if not args.no_compare and world == 1:
-        # untimed: wall time to x within rel 1e-3 of a tightly converged x*
-        # (max over particles), for plain sweeps at decreasing step
-        # tolerances and for Newton-Krylov (plain sweeps until at most 1 % of
-        # the particles move by >= 1e-5, then Newton steps with GMRES(60) to
-        # relative residual 1e-4)
-        comp = {}
-        xr, sr = step(d, meth=U.METHOD_PLAIN, tol=1e-6, max_iter=20000)
-        xr = xr.cpu().numpy()
-        runs = [("plain", U.METHOD_PLAIN, 1e-3, {}), ("plain_tol1e-4", U.METHOD_PLAIN, 1e-4, {}),
-                ("plain_tol1e-5", U.METHOD_PLAIN, 1e-5, {}),
-                ("newton", U.METHOD_NEWTON, 1e-5, dict(gmres_m=60, newton_eta=1e-4))]
-        for name, meth, tol, extra in runs:
-            torch.cuda.synchronize(dev)
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            xm, sm = step(d, meth=meth, tol=tol, max_iter=args.max_iter * 3, **extra)
-            b.record(stream)
-            b.synchronize()
-            dist = np.abs(xm.cpu().numpy() - xr) / xr
-            comp[name] = {"wall_s": a.elapsed_time(b) * 1e-3, "dx_tol": tol, "iterations": sm["iterations"],
-                          "converged": bool(sm["converged"]), "rays": sm["rays"],
-                          "newton_start": sm["newton_start"], "newton_fallbacks": sm["newton_fallbacks"],
-                          "max_rel_to_xstar": float(dist.max()), "p999_rel_to_xstar": float(np.quantile(dist, 0.999))}
-        comp["xstar"] = {"method": "plain", "dx_tol": 1e-6, "iterations": sr["iterations"],
-                         "converged": bool(sr["converged"])}
-        ok = [v["wall_s"] for k, v in comp.items() if k.startswith("plain") and v["max_rel_to_xstar"] < 1e-3]
-        comp["to_rel_1e-3_of_xstar"] = {
-            "plain_wall_s": min(ok) if ok else None,
-            "newton_wall_s": comp["newton"]["wall_s"] if comp["newton"]["max_rel_to_xstar"] < 1e-3 else None}
-        t = comp["to_rel_1e-3_of_xstar"]
-        t["newton_speedup"] = (t["plain_wall_s"] / t["newton_wall_s"]) if (t["plain_wall_s"] and t["newton_wall_s"]) else None
-        # the near/far split of the paper (a different model of the near
-        # particles, so its x is not compared with the plain scheme's x*),
-        # with the analytic (threshold) and the numerical (spectrum) slab
-        for name, slab in (("near_far_threshold", U.SLAB_THRESHOLD), ("near_far_spectrum", U.SLAB_SPECTRUM)):
-            bvh = U.urchin_build_bvh(d["px"], d["py"], d["pz"], d["h"], d["m"], w.periodic, w.box, w.unit_cm)
-            torch.cuda.synchronize(dev)
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            xnf, snf = U.urchin_solve(bvh, dirs, w.l_ray, s_d, w_d, d["nH"], d["T"], tol=1e-3, tau_skip=1e-4,
-                                      max_iter=args.max_iter, segments=segs, precision=U.F32, near_far=slab,
-                                      raise_not_converged=False, profile=True)
-            b.record(stream)
-            b.synchronize()
-            bvh.close()
-            xnf = xnf.cpu().numpy()
-            comp[name] = {"wall_s": a.elapsed_time(b) * 1e-3, "dx_tol": 1e-3, "iterations": snf["iterations"],
-                          "converged": bool(snf["converged"]), "rays": snf["rays"],
-                          "trace_s": snf["trace_s"], "spmv_s": snf["spmv_s"], "sweep_s": snf["sweep_s"],
-                          "median_x_over_plain_xstar": float(np.median(xnf / xr))}
-        # reverse mode at the converged state: gradient of L = sum_i ln x*_i
-        # with respect to the spectrum weights (adjoint GMRES, one transposed
-        # column pass per product)
-        bvh = U.urchin_build_bvh(d["px"], d["py"], d["pz"], d["h"], d["m"], w.periodic, w.box, w.unit_cm)
-        state = torch.empty(w.n, dtype=torch.uint8, device=dev)
-        xs, ss = U.urchin_solve(bvh, dirs, w.l_ray, s_d, w_d, d["nH"], d["T"], tol=1e-3, tau_skip=1e-4,
-                                max_iter=args.max_iter, segments=segs, precision=U.F32, state=state,
-                                raise_not_converged=False)
-        torch.cuda.synchronize(dev)
-        # the first call after the forward solve, then the same call again
-        for name in ("adjoint", "adjoint_repeat"):
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            wb, vs = U.urchin_solve_vjp(bvh, dirs, w.l_ray, s_d, w_d, d["nH"], d["T"], xs, state, 1.0 / xs,
-                                        tol=1e-6, max_iter=600, gmres_m=30, segments=segs, precision=U.F32,
-                                        raise_not_converged=False, profile=True)
-            b.record(stream)
-            b.synchronize()
-            comp[name] = {"loss": "sum ln x*", "wall_s": a.elapsed_time(b) * 1e-3, "products": vs["iterations"],
-                          "rel_residual": vs["max_rel_dx"], "converged": bool(vs["converged"]),
-                          "rays": vs["rays"], "grad_norm": float(wb.norm()), "trace_s": vs["trace_s"],
-                          "spmv_s": vs["spmv_s"]}
-        # the differentiation workload on the same halo: 200 bins, loss = sum over
-        # all rays of (log10 N_HI - log10 N_target)^2, the target from seeded
-        # +-20 % bin weights; x* by Newton-Krylov, gradient by autograd (adjoint
-        # solve + column transpose)
-        from paper_1304_4235_gb300 import autograd as UA
-        e2, J2 = W.powerlaw_spectrum(200, w.e_lo, w.e_hi)
-        s2h, w2h = U.urchin_spectrum_weights(e2, J2, w.gamma_thin)
-        s2, w2 = torch.from_numpy(s2h).to(dev), torch.from_numpy(w2h).to(dev)
-        kw = dict(tol=1e-5, tau_skip=1e-4, max_iter=args.max_iter, method=U.METHOD_NEWTON, gmres_m=60,
-                  newton_eta=1e-4, segments=segs, precision=U.F32, raise_not_converged=False)
-        w2t = w2 * torch.from_numpy(np.random.default_rng(1308).uniform(0.8, 1.2, 200)).to(dev)
-        xt, _ = U.urchin_solve(bvh, dirs, w.l_ray, s2, w2t, d["nH"], d["T"], **kw)
-        target = torch.log10(U.urchin_trace_columns(bvh, xt, dirs, w.l_ray).double())
-        wv = w2.clone().requires_grad_(True)
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-        ev[0].record(stream)
-        xg = UA.converged_x(wv, bvh, dirs, w.l_ray, s2, d["nH"], d["T"], solve_kw=kw,
-                            vjp_kw=dict(tol=1e-6, max_iter=600, gmres_m=30, raise_not_converged=False))
-        L = ((torch.log10(UA.columns(xg, bvh, dirs, w.l_ray).double()) - target) ** 2).sum()
-        ev[1].record(stream)
-        L.backward()
-        ev[2].record(stream)
-        ev[2].synchronize()
-        comp["gradient_column_misfit_200_bins"] = {
-            "loss": float(L.detach()), "forward_s": ev[0].elapsed_time(ev[1]) * 1e-3,
-            "backward_s": ev[1].elapsed_time(ev[2]) * 1e-3, "grad_norm": float(wv.grad.norm()),
-            "forward": "Newton-Krylov to dx_tol 1e-5 + columns of x*",
-            "backward": "adjoint GMRES(30) to 1e-6 + column transpose"}
-        bvh.close()
-        line["compare"] = comp
+        line["compare"] = compare(args, key, w, D, stream)
     if world == 1 and not args.no_cpu_baseline:
-        import oracle as O
-        e_, J_ = w.spectrum()
-        so, wo = O.spectrum(e_, J_, w.gamma_thin)
-        r = oracle_sample(w, so, wo, O.healpix(w.nside), args.cpu_seconds)
-        line["cpu_baseline"] = {
-            "value": r["rays"] / r["seconds"], "unit": "rays/s", "cores": r["cores"], "kind": "oracle",
-            "sample": f"{r['origins']} seeded origins x {w.R} rays, one sweep (brute-force columns over all "
-                      f"{w.n} particles, Gamma, x), {r['seconds']:.1f} s"}
+        ors = OracleSample(w, GRID_CELL[key])
+        r = ors.sample(args.cpu_seconds, 7)
+        line["cpu_baseline"] = {"value": r["rays"] / r["seconds"], "unit": "rays/s", "cores": r["cores"],
+                                "kind": "oracle-grid", "sample": ors.describe(r) + f", {r['seconds']:.1f} s"}
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def convergence(D, stream, max_iter: int):
+    """Wall time to x within rel 1e-3 of a tightly converged x* (plain sweeps
+    to dx_tol 1e-6), for plain sweeps at decreasing dx_tol and for
+    Newton-Krylov (plain sweeps until at most 1 % of the particles move by
+    >= 1e-5, then GMRES(60) to relative residual 1e-4); stored segments where
+    they fit (SEG_AUTO).  Each run: BVH build + solve, CUDA events."""
+    U = D.U
+    out = {}
+
+    def run(**kw):
+        def go():
+            bvh = D.bvh()
+            x, st = D.solve(bvh, segments=U.SEG_AUTO, profile=True, **kw)
+            bvh.close()
+            return x, st
+        (x, st), dt = timed(stream, go)
+        return x.cpu().numpy(), st, dt
+
+    xr, sr, dtr = run(tol=1e-6, max_iter=max_iter * 5)
+    out["xstar"] = {"method": "plain", "dx_tol": 1e-6, "iterations": sr["iterations"],
+                    "converged": bool(sr["converged"]), "wall_s": dtr}
+    runs = [("plain", U.METHOD_PLAIN, 1e-3, {}), ("plain_tol1e-4", U.METHOD_PLAIN, 1e-4, {}),
+            ("plain_tol1e-5", U.METHOD_PLAIN, 1e-5, {}),
+            ("newton", U.METHOD_NEWTON, 1e-5, dict(gmres_m=60, newton_eta=1e-4))]
+    for name, meth, tol, extra in runs:
+        xm, sm, dt = run(method=meth, tol=tol, max_iter=max_iter, **extra)
+        dist = np.abs(xm - xr) / xr
+        out[name] = {"wall_s": dt, "dx_tol": tol, "iterations": sm["iterations"], "converged": bool(sm["converged"]),
+                     "rays": sm["rays"], "rays_per_s": sm["rays"] / dt,
+                     "particle_updates_per_s": sm["particle_updates"] / dt,
+                     "segments_stored": bool(sm["segments_stored"]), "nnz": sm["nnz"],
+                     "trace_s": sm["trace_s"], "spmv_s": sm["spmv_s"], "sweep_s": sm["sweep_s"],
+                     "newton_start": sm["newton_start"], "newton_fallbacks": sm["newton_fallbacks"],
+                     "max_rel_to_xstar": float(dist.max()), "p999_rel_to_xstar": float(np.quantile(dist, 0.999))}
+    ok = [v["wall_s"] for k, v in out.items() if k.startswith("plain") and v["max_rel_to_xstar"] < 1e-3]
+    t = {"plain_wall_s": min(ok) if ok else None,
+         "newton_wall_s": out["newton"]["wall_s"] if out["newton"]["max_rel_to_xstar"] < 1e-3 else None}
+    t["newton_speedup"] = (t["plain_wall_s"] / t["newton_wall_s"]) if (t["plain_wall_s"] and t["newton_wall_s"]) else None
+    out["to_rel_1e-3_of_xstar"] = t
+    return out
+
+
+def adjoint(D, stream, max_iter: int, segments):
+    """Reverse mode at the converged state (plain sweeps to dx_tol 1e-3):
+    gradient of L = sum_i ln x*_i with respect to the spectrum weights
+    (adjoint GMRES(30) to 1e-6, one transposed column pass per product)."""
+    import torch
+    U = D.U
+    bvh = D.bvh()
+    state = torch.empty(D.w.n, dtype=torch.uint8, device=D.dev)
+    xs, ss = D.solve(bvh, tol=1e-3, max_iter=max_iter, segments=U.SEG_AUTO, state=state)
+    torch.cuda.synchronize(D.dev)
+
+    def go():
+        return U.urchin_solve_vjp(bvh, D.dirs, D.w.l_ray, D.s, D.wts, D.d["nH"], D.d["T"], xs, state, 1.0 / xs,
+                                  tol=1e-6, max_iter=600, gmres_m=30, segments=segments, precision=U.F32,
+                                  raise_not_converged=False, profile=True)
+    (wb, vs), dt = timed(stream, go)
+    bvh.close()
+    return {"loss": "sum ln x*", "segments": "recompute" if segments == U.SEG_RECOMPUTE else "auto",
+            "wall_s": dt, "products": vs["iterations"], "rel_residual": vs["max_rel_dx"],
+            "converged": bool(vs["converged"]), "rays": vs["rays"], "grad_norm": float(wb.norm()),
+            "trace_s": vs["trace_s"], "spmv_s": vs["spmv_s"]}
+
+
+def gradient_workload(D, stream, max_iter: int):
+    """The differentiation workload on the halo: 200 bins, loss = sum over all
+    rays of (log10 N_HI - log10 N_target)^2, the target from seeded +-20 %
+    bin weights; x* by Newton-Krylov, gradient by autograd (adjoint solve +
+    column transpose).  Reports the solves' segment mode, sweeps and Newton
+    fallbacks beside the times."""
+    import torch
+    import workloads as W
+    from paper_1304_4235_gb300 import autograd as UA
+    U, w, dev = D.U, D.w, D.dev
+    e2, J2 = W.powerlaw_spectrum(200, w.e_lo, w.e_hi)
+    s2h, w2h = U.urchin_spectrum_weights(e2, J2, w.gamma_thin)
+    s2, w2 = torch.from_numpy(s2h).to(dev), torch.from_numpy(w2h).to(dev)
+    kw = dict(tol=1e-5, tau_skip=1e-4, max_iter=max_iter, method=U.METHOD_NEWTON, gmres_m=60, newton_eta=1e-4,
+              segments=U.SEG_AUTO, precision=U.F32, raise_not_converged=False)
+    bvh = D.bvh()
+    w2t = w2 * torch.from_numpy(np.random.default_rng(1308).uniform(0.8, 1.2, 200)).to(dev)
+    xt, stt = U.urchin_solve(bvh, D.dirs, w.l_ray, s2, w2t, D.d["nH"], D.d["T"], **kw)
+    target = torch.log10(U.urchin_trace_columns(bvh, xt, D.dirs, w.l_ray).double())
+    wv = w2.clone().requires_grad_(True)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    torch.cuda.synchronize(dev)
+    ev[0].record(stream)
+    info = {}
+    xg = UA.converged_x(wv, bvh, D.dirs, w.l_ray, s2, D.d["nH"], D.d["T"], solve_kw=kw,
+                        vjp_kw=dict(tol=1e-6, max_iter=600, gmres_m=30, raise_not_converged=False), info=info)
+    L = ((torch.log10(UA.columns(xg, bvh, D.dirs, w.l_ray).double()) - target) ** 2).sum()
+    ev[1].record(stream)
+    L.backward()
+    ev[2].record(stream)
+    ev[2].synchronize()
+    bvh.close()
+    fs = info.get("forward_stats", {})
+    bs = info.get("vjp_stats", {})
+    return {"loss": float(L.detach()), "forward_s": ev[0].elapsed_time(ev[1]) * 1e-3,
+            "backward_s": ev[1].elapsed_time(ev[2]) * 1e-3, "grad_norm": float(wv.grad.norm()),
+            "forward": "Newton-Krylov to dx_tol 1e-5 + columns of x*",
+            "backward": "adjoint GMRES(30) to 1e-6 + column transpose",
+            "forward_iterations": fs.get("iterations"), "forward_segments_stored": fs.get("segments_stored"),
+            "forward_newton_start": fs.get("newton_start"), "forward_newton_fallbacks": fs.get("newton_fallbacks"),
+            "backward_products": bs.get("iterations"), "target_solve_iterations": stt["iterations"]}
+
+
+def compare(args, key, w, D, stream):
+    import torch
+    comp = {"workload": workload_name(key, w)}
+    comp.update(convergence(D, stream, args.max_iter))
+    comp["adjoint_recompute"] = adjoint(D, stream, args.max_iter, D.U.SEG_RECOMPUTE)
+    if key == "c5":
+        # the 262144-particle halo (the round's earlier headline) beside it
+        wh = load_workload("halo", args.cache_dir)
+        Dh = Device(wh, D.dev)
+        comp["halo"] = {"workload": workload_name("halo", wh)}
+        comp["halo"].update(convergence(Dh, stream, args.max_iter))
+        comp["halo"]["adjoint"] = adjoint(Dh, stream, args.max_iter, D.U.SEG_AUTO)
+        comp["gradient_column_misfit_200_bins"] = gradient_workload(Dh, stream, args.max_iter)
+        del Dh
+        torch.cuda.empty_cache()
+    else:
+        comp["gradient_column_misfit_200_bins"] = gradient_workload(D, stream, args.max_iter)
+    return comp
 
 
 if __name__ == "__main__":

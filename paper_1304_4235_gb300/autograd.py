@@ -72,24 +72,27 @@ class _Equilibrium(torch.autograd.Function):
 
 class _ConvergedX(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, w, bvh, dirs, l_ray, s, nH, T, solve_kw, vjp_kw):
+    def forward(ctx, w, bvh, dirs, l_ray, s, nH, T, solve_kw, vjp_kw, info):
         state = torch.empty(bvh.n, dtype=torch.uint8, device=w.device)
         x, st = U.urchin_solve(bvh, dirs, l_ray, s, w.detach().contiguous(), nH, T, state=state, **solve_kw)
         ctx.save_for_backward(w, s, nH, T, x, state)
-        ctx.args = (bvh, dirs, l_ray, solve_kw, vjp_kw)
-        ctx.stats = st
+        ctx.args = (bvh, dirs, l_ray, solve_kw, vjp_kw, info)
+        if info is not None:
+            info["forward_stats"] = st
         return x
 
     @staticmethod
     def backward(ctx, x_bar):
         w, s, nH, T, x, state = ctx.saved_tensors
-        bvh, dirs, l_ray, solve_kw, vjp_kw = ctx.args
+        bvh, dirs, l_ray, solve_kw, vjp_kw, info = ctx.args
         keep = {k: solve_kw[k] for k in ("y", "tau_skip", "segments", "kernel", "precision", "case_rule",
                                          "warm_start") if k in solve_kw}
         keep.update(vjp_kw)
         wb, st = U.urchin_solve_vjp(bvh, dirs, l_ray, s, w.detach().contiguous(), nH, T, x, state,
                                     x_bar.to(torch.float64).contiguous(), **keep)
-        return wb, None, None, None, None, None, None, None, None
+        if info is not None:
+            info["vjp_stats"] = st
+        return wb, None, None, None, None, None, None, None, None, None
 
 
 def columns(x, bvh, dirs, l_ray, origins=None, kernel=U.KERNEL_M4, precision=U.F32):
@@ -108,9 +111,11 @@ def equilibrium(gamma, tau_eff, nH, T, case_rule=U.CASE_AUTO, y=0.0):
     return _Equilibrium.apply(gamma, tau_eff, nH, T, case_rule, y)
 
 
-def converged_x(w, bvh, dirs, l_ray, s, nH, T, solve_kw=None, vjp_kw=None):
+def converged_x(w, bvh, dirs, l_ray, s, nH, T, solve_kw=None, vjp_kw=None, info=None):
     """x* of urchin_solve for spectrum weights w, differentiable in w by the
     implicit function theorem (urchin_solve_vjp).  solve_kw go to
     urchin_solve (tol should be tight: the gradient is that of the exact
-    fixed point), vjp_kw (tol, max_iter, gmres_m) to urchin_solve_vjp."""
-    return _ConvergedX.apply(w, bvh, dirs, l_ray, s, nH, T, dict(solve_kw or {}), dict(vjp_kw or {}))
+    fixed point), vjp_kw (tol, max_iter, gmres_m) to urchin_solve_vjp.  A
+    dict `info` receives the forward solve's statistics ("forward_stats")
+    and, after backward, the adjoint's ("vjp_stats")."""
+    return _ConvergedX.apply(w, bvh, dirs, l_ray, s, nH, T, dict(solve_kw or {}), dict(vjp_kw or {}), info)

@@ -221,6 +221,34 @@ def random_origins(n: int, count: int, seed: int) -> np.ndarray:
     return np.sort(rng.choice(n, size=count, replace=False)).astype(np.int32)
 
 
+def cached(fn, cache_dir: str, **kw) -> Workload:
+    """fn(**kw), stored under cache_dir as .npy arrays plus the scalar fields
+    and reloaded on later calls with the same name and arguments (the
+    generation of the largest boxes takes tens of seconds; the arrays are
+    the same seeded values either way)."""
+    import json
+    import os
+    key = fn.__name__ + "".join(f"_{k}{kw[k]}" for k in sorted(kw))
+    d = os.path.join(cache_dir, key)
+    arrays = ("pos", "h", "mass_H", "nH", "T")
+    meta_path = os.path.join(d, "meta.json")
+    if os.path.exists(meta_path):
+        meta = json.load(open(meta_path))
+        return Workload(**meta, **{a: np.load(os.path.join(d, a + ".npy")) for a in arrays})
+    w = fn(**kw)
+    tmp = d + f".tmp{os.getpid()}"
+    os.makedirs(tmp, exist_ok=True)
+    for a in arrays:
+        np.save(os.path.join(tmp, a + ".npy"), getattr(w, a))
+    meta = {f.name: getattr(w, f.name) for f in dataclasses.fields(w) if f.name not in arrays}
+    json.dump(meta, open(os.path.join(tmp, "meta.json"), "w"))
+    try:
+        os.replace(tmp, d)
+    except OSError:           # another process stored it first
+        pass
+    return w
+
+
 CONFIGS = {
     "lattice_box": lattice_box,
     "halo": halo,
