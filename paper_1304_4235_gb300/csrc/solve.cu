@@ -205,14 +205,22 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs A)
     Real* wn = e2 + A.F;
     Real* sj = wn + A.F;
     Real* e2t = kF32 ? sj + A.F : nullptr;
-    Real* sh1 = sj + (kF32 ? 2 : 1) * A.F;      // helium cross sections (kHe)
-    Real* sh2 = sh1 + A.F;
+    Real* sh1 = sj + (kF32 ? 2 : 1) * A.F;      // helium cross sections (kHe) and, in FP32,
+    Real* sh2 = sh1 + A.F;                      // the float tails of all three (fold_ray_he)
+    Real* sjt = sh2 + A.F;
+    Real* sh1t = sjt + A.F;
+    Real* sh2t = sh1t + A.F;
     __shared__ double sh[2];
     fold_prepare<Real>(A.s, A.w, A.F, e2, e2t, wn, (A.want_tangent || kHe) ? sj : nullptr, sh);
     if (kHe) {
         for (int j = threadIdx.x; j < A.F; j += blockDim.x) {
             sh1[j] = (Real)A.s_he1[j];
             sh2[j] = (Real)A.s_he2[j];
+            if (kF32) {
+                sjt[j] = (Real)(A.s[j] - (double)(Real)A.s[j]);
+                sh1t[j] = (Real)(A.s_he1[j] - (double)(Real)A.s_he1[j]);
+                sh2t[j] = (Real)(A.s_he2[j] - (double)(Real)A.s_he2[j]);
+            }
         }
         __syncthreads();
     }
@@ -238,7 +246,14 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(SweepArgs A)
             }
             // ln(Gamma_k / Gamma_thin) = -s_min tau_k + ln S_k
             double lkv = fold ? ray_lnrate(smin, tau, S) : 0.0;
-            if (kHe) {
+            if (kHe && kF32) {
+                // H I, He I and He II columns: E_j = s_j tau + s1_j tau1 + s2_j tau2 (fold_ray_he)
+                const int32_t ir = A.items ? A.items[row] : (int32_t)row;
+                const float t1 = static_cast<const float*>(A.tau_he1)[ir + (int64_t)k * A.near_k_stride];
+                const float t2 = static_cast<const float*>(A.tau_he2)[ir + (int64_t)k * A.near_k_stride];
+                lkv = fold_ray_he((float)tau, t1, t2, (const float*)sj, (const float*)sjt, (const float*)sh1,
+                                  (const float*)sh1t, (const float*)sh2, (const float*)sh2t, (const float*)wn, A.F);
+            } else if (kHe) {
                 // H I, He I and He II columns: E_j = s_j tau + s1_j tau1 + s2_j tau2, the
                 // smallest E_j factored out of the sum
                 const int32_t ir = A.items ? A.items[row] : (int32_t)row;
@@ -525,7 +540,8 @@ __global__ void k_adj_frozen(const uint8_t* __restrict__ active, const int32_t* 
 //   w_bar_b += sum_a phi_a (1/R) sum_k exp(-s_b tau_ak) / Gamma_a,
 //   phi_a = nu_a (E_a / x_a) elas_a,  elas_a = Gamma_a (dE_a/dGamma_a) / E_a,
 // as lc = ln|phi_a / (R Gamma_thin)| - ln(Gamma_a / Gamma_thin), sg = sign
-// (Gamma_a recomputed in double from tau with the factored log-sum-exp).
+// (Gamma_a recomputed from tau with the sweep's fold: fold_ray, the
+// per-ray log rates and their log-sum-exp in double).
 template <typename Real>
 __global__ void k_adj_wcoef(const int32_t* __restrict__ items, int64_t na, int R, const Real* __restrict__ tau,
                             const double* __restrict__ sv, const double* __restrict__ wv, int F,
@@ -534,42 +550,23 @@ __global__ void k_adj_wcoef(const int32_t* __restrict__ items, int64_t na, int R
                             const double* __restrict__ aB, const double* __restrict__ gc,
                             const uint8_t* __restrict__ latch, int case_rule, double y, double* lc, double* sg)
 {
-    extern __shared__ double sm[];
-    double* ss = sm;
-    double* ws = sm + F;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr bool kF32 = sizeof(Real) == 4;
+    Real* e2 = reinterpret_cast<Real*>(smem_raw);
+    Real* wn = e2 + F;
+    Real* e2t = kF32 ? wn + F : nullptr;
     __shared__ double sh[2];
-    if (threadIdx.x == 0) {
-        double g = 0.0, m = sv[0];
-        for (int b = 0; b < F; ++b) {
-            g += wv[b];
-            m = fmin(m, sv[b]);
-        }
-        sh[0] = g;
-        sh[1] = m;
-    }
-    __syncthreads();
+    fold_prepare<Real>(sv, wv, F, e2, e2t, wn, nullptr, sh);
     const double gthin = sh[0], smin = sh[1];
-    for (int b = threadIdx.x; b < F; b += blockDim.x) {
-        ss[b] = sv[b] - smin;
-        ws[b] = wv[b] / gthin;
-    }
-    __syncthreads();
     for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < na; a += (int64_t)gridDim.x * blockDim.x) {
-        double m = -INFINITY, acc = 0.0;
-        for (int k = 0; k < R; ++k) {            // streaming log-sum-exp over rays
-            const double t = (double)tau[a + (int64_t)k * na];
-            double S = 0.0;
-            for (int b = 0; b < F; ++b) S += ws[b] * exp(-ss[b] * t);
-            const double l = -smin * t + log(S);
-            if (!(l > -INFINITY)) continue;      // a ray with no transmitted flux adds nothing
-            if (l > m) {
-                acc = acc * exp(m - l) + 1.0;
-                m = l;
-            } else {
-                acc += exp(l - m);
-            }
+        RayMean<Real> lse;
+        for (int k = 0; k < R; ++k) {
+            const Real t = tau[a + (int64_t)k * na];
+            Real S, S2;
+            fold_ray<false>(t, e2, e2t, wn, nullptr, F, S, S2);
+            lse.add(ray_lnrate(smin, t, S));
         }
-        const double lnr = m + log(acc / (double)R);      // ln(Gamma_a / Gamma_thin)
+        const double lnr = lse.mean(R);                    // ln(Gamma_a / Gamma_thin)
         const int32_t i = items[a];
         const double G = gthin * exp(lnr);
         const bool caseB = case_rule == URCHIN_CASE_B || (case_rule == URCHIN_CASE_AUTO && latch[i]);
@@ -608,8 +605,10 @@ int launch_sweep(const SweepArgs& A, cudaStream_t s)
         return launched();
     }
     const bool f64 = A.precision == URCHIN_F64;
-    // two per-ray log-rate arrays in double, then e2, wn, s, (FP32) e2t and (helium) s1, s2
-    const size_t smem = 2 * sizeof(double) * kSweepThreads + ((f64 ? 3 : 4) + (A.he ? 2 : 0)) * (size_t)A.F * rsz;
+    // two per-ray log-rate arrays in double, then e2, wn, s, (FP32) e2t, (helium) s1, s2 and
+    // their three FP32 tails
+    const size_t smem =
+        2 * sizeof(double) * kSweepThreads + ((f64 ? 3 : 4) + (A.he ? (f64 ? 2 : 5) : 0)) * (size_t)A.F * rsz;
     const int var = A.he ? kSweepHelium : (A.near_far ? kSweepNearFar : kSweepPlain);
     const void* fns[2][3] = {
         {(const void*)k_sweep<float, kSweepPlain>, (const void*)k_sweep<float, kSweepNearFar>,
@@ -1586,7 +1585,8 @@ int Solver::adjoint(const uint8_t* state_orig, const double* xbar_orig, int cold
         stats.max_rel_dx = gres.rel_residual;
         stats.converged = gres.rel_residual <= P.tol ? 1 : 0;
         // active particles: w_bar_b += sum_a phi_a rho_ab
-        const size_t smem = sizeof(double) * 2 * (size_t)P.spectrum.F;
+        // e2, wn and (FP32) the tail e2t of fold_prepare
+        const size_t smem = (f64 ? 2 * sizeof(double) : 3 * sizeof(float)) * (size_t)P.spectrum.F;
         const void* fw = f64 ? (const void*)k_adj_wcoef<double> : (const void*)k_adj_wcoef<float>;
         if (smem > 48 * 1024)
             URCHIN_TRY_CUDA(cudaFuncSetAttribute(fw, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

@@ -170,6 +170,85 @@ __global__ void k_wbar_tiles(const Real* __restrict__ tau, int64_t n_rays, const
     for (int b = threadIdx.x; b < F; b += blockDim.x) partial[(int64_t)blockIdx.x * F + b] = acc[b];
 }
 
+// The FP32 form of k_wbar_tiles: with l_r = lc_r - s_min tau_r and m the
+// largest l_r of the tile, every term is sg_r exp(l_r - m) (a float in
+// [-1, 1], from one double exp per ray) times exp(-(s_b - s_min) tau_r)
+// (the fold's float exponent with its rounding error carried, see
+// fold_ray), summed over the tile in float with compensation and added to
+// the bin's double sum times exp(m): one double operation per tile and bin
+// instead of a double exp per ray and bin.
+__global__ void k_wbar_tiles_f32(const float* __restrict__ tau, int64_t n_rays, const double* __restrict__ lc_in,
+                                 const double* __restrict__ sg_in, const double* __restrict__ sv, int F,
+                                 double* partial)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double* acc = reinterpret_cast<double*>(smem_raw);           // [F]
+    double* ld = acc + F;                                         // [kWTile]
+    float* e2 = reinterpret_cast<float*>(ld + kWTile);            // [F]
+    float* e2t = e2 + F;                                          // [F]
+    float* tt = e2t + F;                                          // [kWTile]
+    float* fr = tt + kWTile;                                      // [kWTile]
+    __shared__ double sh_smin, sh_m;
+    if (threadIdx.x == 0) {
+        double m = sv[0];
+        for (int b = 1; b < F; ++b) m = fmin(m, sv[b]);
+        sh_smin = m;
+    }
+    __syncthreads();
+    const double smin = sh_smin;
+    for (int b = threadIdx.x; b < F; b += blockDim.x) {
+        const double c = (sv[b] - smin) * 1.4426950408889634;
+        e2[b] = (float)c;
+        e2t[b] = (float)(c - (double)(float)c);
+        acc[b] = 0.0;
+    }
+    const int64_t tiles = (n_rays + kWTile - 1) / kWTile;
+    for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < kWTile; i += blockDim.x) {
+            const int64_t r = tile * kWTile + i;
+            const bool in = r < n_rays;
+            const float t = in ? tau[r] : 0.f;
+            tt[i] = t < 1e30f ? t : (t == t ? 1e30f : t);
+            ld[i] = in ? fma(-smin, (double)t, lc_in[r]) : -INFINITY;
+        }
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            double m = -INFINITY;
+            for (int i = threadIdx.x; i < kWTile; i += 32) m = fmax(m, ld[i]);
+            for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+            if (threadIdx.x == 0) sh_m = m;
+        }
+        __syncthreads();
+        const double m = sh_m;
+        if (!(m > -INFINITY)) continue;                            // no coefficient in this tile
+        for (int i = threadIdx.x; i < kWTile; i += blockDim.x) {
+            const int64_t r = tile * kWTile + i;
+            fr[i] = (r < n_rays && ld[i] > -INFINITY) ? (float)(sg_in[r] * exp(ld[i] - m)) : 0.f;
+        }
+        __syncthreads();
+        const double em = exp(m);
+        for (int b = threadIdx.x; b < F; b += blockDim.x) {
+            const float eb = e2[b], ebt = e2t[b];
+            float S = 0.f, c = 0.f;
+            for (int i = 0; i < kWTile; ++i) {
+                const float t = tt[i];
+                const float p = eb * t;
+                const float err = fmaf(ebt, t, fmaf(eb, t, -p));
+                const float v0 = fr[i] * exp2f(-p);
+                const float v = fmaf(-v0, err * 0.6931471805599453f, v0);
+                const float yy = v - c;
+                const float u = S + yy;
+                c = (u - S) - yy;
+                S = u;
+            }
+            acc[b] = fma((double)S, em, acc[b]);
+        }
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < F; b += blockDim.x) partial[(int64_t)blockIdx.x * F + b] = acc[b];
+}
+
 // per-ray coefficient of Eq. gamma_shld's reverse mode: c_r = gamma_bar_o / R
 __global__ void k_gamma_coef(int64_t n_rays, int R, const double* __restrict__ gbar, double* lc, double* sg)
 {
@@ -406,8 +485,10 @@ int launch_wbar(const void* tau, int precision, int64_t n_rays, const double* lc
                 int F, double* w_bar, cudaStream_t s)
 {
     if (n_rays <= 0) return URCHIN_OK;
-    const size_t smem = sizeof(double) * (2 * (size_t)F + 3 * kWTile);
-    const void* fn = precision == URCHIN_F64 ? (const void*)k_wbar_tiles<double> : (const void*)k_wbar_tiles<float>;
+    const bool f64 = precision == URCHIN_F64;
+    const size_t smem = f64 ? sizeof(double) * (2 * (size_t)F + 3 * kWTile)
+                            : sizeof(double) * ((size_t)F + kWTile) + sizeof(float) * (2 * (size_t)F + 2 * kWTile);
+    const void* fn = f64 ? (const void*)k_wbar_tiles<double> : (const void*)k_wbar_tiles_f32;
     if (smem > 48 * 1024)
         URCHIN_TRY_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int64_t tiles = (n_rays + kWTile - 1) / kWTile;
@@ -418,8 +499,8 @@ int launch_wbar(const void* tau, int precision, int64_t n_rays, const double* lc
         k_wbar_tiles<double><<<nb, 256, smem, s>>>(static_cast<const double*>(tau), n_rays, lc, sg, sv, F,
                                                    part.at<double>(0));
     else
-        k_wbar_tiles<float><<<nb, 256, smem, s>>>(static_cast<const float*>(tau), n_rays, lc, sg, sv, F,
-                                                  part.at<double>(0));
+        k_wbar_tiles_f32<<<nb, 256, smem, s>>>(static_cast<const float*>(tau), n_rays, lc, sg, sv, F,
+                                               part.at<double>(0));
     URCHIN_TRY(launched());
     k_sum_partials<<<(F + 255) / 256, 256, 0, s>>>(part.at<double>(0), nb, F, w_bar);
     URCHIN_TRY(launched());
