@@ -60,8 +60,28 @@ def lnrate_sensitivity(tau, s, w):
     return np.exp(num - den)
 
 
+def helium_rate(w, so, he, columns, eps_col):
+    """A rate for check_sweep with fixed helium columns: he = dict(t1, t2
+    [n, R] (the oracle's He I / He II columns of every particle), s1, s2).
+    The GPU traces the helium columns in FP32 too, so the sensitivity is that
+    of ln Gamma to all three columns at once, by central differences of the
+    oracle's rate under a common relative change (every partial derivative
+    has the same sign, so this is the sum of their magnitudes)."""
+    def rate(x_prev, org):
+        tau = columns(x_prev, org)
+        t1, t2 = he["t1"][org], he["t2"][org]
+        G, te = O.gamma_he(tau, t1, t2, so[0], he["s1"], he["s2"], so[1])
+        d = 1e-4
+        gp, _ = O.gamma_he(tau * (1 + d), t1 * (1 + d), t2 * (1 + d), so[0], he["s1"], he["s2"], so[1])
+        gm, _ = O.gamma_he(tau * (1 - d), t1 * (1 - d), t2 * (1 - d), so[0], he["s1"], he["s2"], so[1])
+        with np.errstate(divide="ignore", invalid="ignore"):
+            D = np.nan_to_num(np.abs(np.log(gm) - np.log(gp)) / (2 * d), nan=0.0)
+        return G, te, D
+    return rate
+
+
 def check_sweep(w, so, x_prev, state_prev, x_next, org, nside, sweep0, tau_skip=1e-4, case_rule=2,
-                eps_col=1e-6, eps_fold=2e-6, columns=None):
+                eps_col=1e-6, eps_fold=2e-6, columns=None, rate=None):
     """One FP32 sweep of the GPU against the oracle's update of the GPU's own
     previous state, particle by particle, with a stated error model instead
     of a quantile: the FP32 columns carry a relative error <= eps_col (the
@@ -72,13 +92,19 @@ def check_sweep(w, so, x_prev, state_prev, x_next, org, nside, sweep0, tau_skip=
     tau_eff = 1 (unlatched) either recombination case is accepted, within dl
     of tau_skip in sweep 0 either freezing or updating.  state_prev: uint8
     per particle (bit 0 case B latched, bit 1 frozen) or None for sweep 0.
-    Asserts, and returns the largest error / bound (<= 1) over `org`."""
+    rate (optional) replaces the hydrogen-only fold: rate(x_prev, org) ->
+    (Gamma, tau_eff, D) (helium_rate).  Asserts, and returns the largest
+    error / bound (<= 1) over `org`."""
     dirs = O.healpix(nside)
     org = np.asarray(org)
     cols = columns if columns is not None else (lambda x, o: O.columns(w, x, dirs, origins=o))
-    tau = cols(x_prev, org)
-    G, te = O.gamma(tau, so[0], so[1])
-    dl = eps_fold + eps_col * lnrate_sensitivity(tau, so[0], so[1])
+    if rate is None:
+        tau = cols(x_prev, org)
+        G, te = O.gamma(tau, so[0], so[1])
+        D = lnrate_sensitivity(tau, so[0], so[1])
+    else:
+        G, te, D = rate(x_prev, org)
+    dl = eps_fold + eps_col * D
     worst = 0.0
     for a, i in enumerate(org):
         xn, xp = float(x_next[i]), float(x_prev[i])

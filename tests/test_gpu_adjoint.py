@@ -81,7 +81,9 @@ def test_gamma_vjp_matches_oracle(precision):
     tb, wb = U.urchin_gamma_vjp(tau_t, sg[0], sg[1], torch.from_numpy(gbar).cuda())
     dG_dtau, dG_dw = O.gamma_partials(tau_used, so[0], so[1])
     assert _rel(tb.double().cpu().numpy(), gbar[:, None] * dG_dtau) < (1e-10 if precision == U.F64 else 2e-7)
-    assert _rel(wb.cpu().numpy(), gbar @ dG_dw, np.abs(gbar) @ dG_dw) < 1e-10
+    # w_bar: double sums in FP64; in FP32 the per-bin sum runs in float over
+    # tiles of 128 rays (k_wbar_tiles_f32), within 2e-6 of the magnitude sum
+    assert _rel(wb.cpu().numpy(), gbar @ dG_dw, np.abs(gbar) @ dG_dw) < (1e-10 if precision == U.F64 else 2e-6)
 
 
 @pytest.mark.parametrize("case_rule", [U.CASE_A, U.CASE_B, U.CASE_AUTO])

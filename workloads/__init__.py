@@ -214,6 +214,26 @@ def subset(w: Workload, idx: np.ndarray, name: str | None = None) -> Workload:
         T=w.T[idx].copy())
 
 
+def helium_fractions(w: Workload, seed: int):
+    """Fixed He I and He II abundances per H atom for every particle (the
+    paper iterates hydrogen only): n_He/n_H = 0.079 (X = 0.76) times seeded
+    ion fractions, He I in [0, 0.3) and He II in [0, 0.5) of the rest."""
+    rng = np.random.default_rng(seed)
+    y = 0.079
+    f1 = rng.uniform(0.0, 0.3, w.n)
+    f2 = rng.uniform(0.0, 0.5, w.n) * (1 - f1)
+    return y * f1, y * f2
+
+
+def hei_cross_section_standin(edges: np.ndarray) -> np.ndarray:
+    """A He I cross-section shape in units of sigma_th at the geometric bin
+    centres, zero below the 24.59 eV edge and 1.2 (24.59 eV / E)^2 above it.
+    The paper gives no He I fit; this stand-in only has to be the same input
+    on every side that uses it."""
+    centres = np.sqrt(edges[:-1] * edges[1:])
+    return np.where(centres >= 24.59, 1.2 * (24.59 / centres) ** 2, 0.0)
+
+
 def random_origins(n: int, count: int, seed: int) -> np.ndarray:
     """A seeded sample of ``count`` distinct particle indices (sorted)."""
     rng = np.random.default_rng(seed)
