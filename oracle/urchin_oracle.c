@@ -919,6 +919,12 @@ void oracle_gamma_nearfar(const double* tau_far, const double* tau_near, int64_t
             }
             if (lk[k] > m) m = lk[k];
         }
+        if (m == -INFINITY) {
+            /* no ray's radiation reaches the origin: the rate is the empty sum */
+            lnratio_out[o] = -INFINITY;
+            gamma_out[o] = 0.0;
+            continue;
+        }
         double acc = 0.0;
         for (int k = 0; k < R; ++k) acc += exp(lk[k] - m);
         double lr = m + log(acc);

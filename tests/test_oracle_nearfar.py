@@ -97,6 +97,30 @@ def test_gamma_nearfar_without_near_column_is_the_plain_rate():
     np.testing.assert_allclose(-lr, te0, rtol=1e-11, atol=1e-14)
 
 
+def test_gamma_nearfar_fully_shielded_is_zero():
+    """Eq. gammashld: when the far column of every ray is so thick that no
+    radiation reaches the slab (every bin's attenuation underflows), the
+    particle's rate is the empty sum: Gamma = 0, and the equilibrium is the
+    collisional x = alpha / (alpha + gamma_c).  The analytic slab, lit by the
+    far-attenuated rate, reports ln(Gamma / Gamma_thin) = -inf; the
+    polychromatic slab carries the attenuation in log form and reports its
+    finite logarithm (far below the smallest double).  A ray that still lets
+    radiation through keeps the rate finite."""
+    w = W.halo(n=10, seed=1)
+    e, J = w.spectrum()
+    s, wts = O.spectrum(e, J, w.gamma_thin)
+    tf = np.full((2, 12), 1e6)
+    tf[1, 3] = 2.0
+    tn = np.full((2, 12), 5.0)
+    for poly in (False, True):
+        lr, g = O.gamma_nearfar(tf, tn, s, wts, np.array([1.0, 1.0]), np.array([1e4, 1e4]),
+                                np.array([True, True]), poly=poly)
+        assert g[0] == 0.0 and (lr[0] < -745.0 if poly else lr[0] == -np.inf), (poly, lr[0])
+        assert np.isfinite(lr[1]) and g[1] > 0.0, poly
+        aA, aB, gc = O.rates(1e4)
+        assert abs(O.xeq(g[0], 1.0, 1e4, 0.0, True)[0] - aB / (aB + gc)) <= 1e-15
+
+
 def test_near_far_iteration_converges_faster_than_the_plain_scheme():
     """Sec. 3.3.3: with the near particles modelled as a slab, Gamma of a
     particle no longer depends on its own and its neighbours' x, which
