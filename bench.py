@@ -20,7 +20,7 @@ gradient with recomputed segments, the 262144-particle halo and the
 differentiation workload.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload c5|halo] [--no-compare] [--no-cpu-baseline] [--no-e2e]
+                  [--workload c5|halo|c5_eighth] [--no-compare] [--no-cpu-baseline] [--no-e2e]
 
 Under torchrun every rank solves its own copy (replicas; independent boxes
 need no exchange) and rank 0 prints one JSON line.
@@ -49,10 +49,12 @@ METRIC = "rays/s and particle-updates/s to converged x (rel 1e-3), Newton+adjoin
 WORKLOADS = {
     "c5": ("lognormal_box", dict(n_side=256, box_kpc=8000.0, sigma_ln=2.5, nside=1, F=400)),
     "halo": ("halo", dict()),
+    # the same density field at 1/8 of the particles (profiling captures)
+    "c5_eighth": ("lognormal_box", dict(n_side=128, box_kpc=4000.0, sigma_ln=2.5, nside=1, F=400)),
 }
 
 # Grid cell (kpc) of the oracle's uniform-grid search for each workload.
-GRID_CELL = {"c5": 80.0, "halo": 4.0}
+GRID_CELL = {"c5": 80.0, "halo": 4.0, "c5_eighth": 80.0}
 
 
 def workload_name(key: str, w) -> str:
@@ -68,7 +70,9 @@ def workload_name(key: str, w) -> str:
 # files at capture time; a changed kernel reports traffic null.
 #   k_trace: bytes per ray-sphere hit;  k_spmv: bytes per stored segment
 MEASURED_TRAFFIC = {
-    "k_trace": {},
+    # the 256^3 box's own sweep-0 launch (one-pass capture): 7.34e9 + 3.16e9
+    # DRAM bytes for 1.762e10 hits
+    "k_trace": {"7e6723a718a4b0cf": 0.595},
     "k_spmv": {},
 }
 KERNEL_SOURCES = {"k_trace": ("trace.cu", "common.cuh"), "k_spmv": ("linalg.cu", "linalg.cuh")}
@@ -622,8 +626,8 @@ def compare(args, key, w, D, stream):
     comp = {"workload": workload_name(key, w)}
     comp.update(convergence(D, stream, args.max_iter))
     comp["adjoint_recompute"] = adjoint(D, stream, args.max_iter, D.U.SEG_RECOMPUTE)
-    if key == "c5":
-        # the 262144-particle halo (the round's earlier headline) beside it
+    if key.startswith("c5"):
+        # the 262144-particle halo beside it
         wh = load_workload("halo", args.cache_dir)
         Dh = Device(wh, D.dev)
         comp["halo"] = {"workload": workload_name("halo", wh)}

@@ -149,7 +149,7 @@ constexpr unsigned kStWarm = 16u;       // warm-start x outside (0, 1]
 constexpr unsigned kStVisit = 32u;      // traversal visit limit (malformed tree)
 constexpr unsigned kStSegment = 64u;    // stored-segment fill disagrees with its count
 
-constexpr int kLeafMax = 16;      // subtrees with <= kLeafMax particles become leaves
+constexpr int kLeafMax = 32;      // subtrees with <= kLeafMax particles become leaves
 constexpr int kSegPad = 8;        // stored rays are padded to a multiple of kSegPad segments (zero
                                   // values, particle 0) so the SpMV reads 8 segments per lane
 constexpr int kKTab = 2048;       // intervals of the full-chord M4 table in t = b^2/h^2

@@ -120,21 +120,42 @@ def test_near_far_periodic_lattice_sweeps():
 def test_near_far_full_halo_converges_in_few_sweeps(slab):
     """Benchmark halo, FP32 columns, stored (far) segments: the near/far
     iteration converges at dx_tol 1e-3 in a few sweeps (the plain scheme
-    needs 292), and at seeded non-frozen particles the oracle's near/far
-    update of the converged state reproduces it."""
+    needs 292).  Its last sweep is then checked particle by particle at 64
+    seeded active particles against the oracle's near/far update of the
+    GPU's state one sweep earlier, within an envelope instead of a quantile:
+    the FP32 far and near columns carry a relative error <= eps_col = 1e-6
+    (the column tests measure <= 3e-7), and the update x is increasing in
+    every column (more column, less rate, more neutral gas), so the exact
+    update at the GPU's columns lies between the oracle's updates at all
+    columns scaled by 1 - eps_col and 1 + eps_col.  The GPU's rate itself
+    may differ by eps_rate (the far fold 2e-6; the FP32 numerical slab
+    2e-5 more), and within that envelope either recombination case is
+    accepted where tau_eff straddles 1."""
     w = W.halo()
     bvh, d = build(w, torch)
     sg, so = spectra(w, torch)
-    state = torch.zeros(w.n, dtype=torch.uint8, device="cuda")
-    x, st = U.urchin_solve(bvh, U.urchin_healpix_dirs(1), w.l_ray, sg[0], sg[1], d["nH"], d["T"], tol=1e-3,
-                           max_iter=300, precision=U.F32, segments=U.SEG_STORE, near_far=slab, state=state)
+    dirs = U.urchin_healpix_dirs(1)
+    kw = dict(precision=U.F32, segments=U.SEG_STORE, near_far=slab)
+    x, st = U.urchin_solve(bvh, dirs, w.l_ray, sg[0], sg[1], d["nH"], d["T"], tol=1e-3, max_iter=300, **kw)
     assert st["converged"] and st["iterations"] < 60
-    xa = x.cpu().numpy()
-    stt = state.cpu().numpy()
-    act = np.flatnonzero((stt & 2) == 0)
-    org = np.sort(np.random.default_rng(6).choice(act, size=min(24, act.size), replace=False))
-    tf, tn = O.columns_nearfar(w, xa, O.healpix(1), origins=org)
-    caseB = (stt[org] & 1) > 0
-    lr, g = O.gamma_nearfar(tf, tn, so[0], so[1], w.nH[org], w.T[org], caseB, poly=(slab == U.SLAB_SPECTRUM))
-    e = O.xeq(g, w.nH[org], w.T[org], 0.0, caseB | (-lr >= 1))
-    assert np.quantile(rel_err(e, xa[org]), 0.9) < 3e-3
+    n = st["iterations"]
+    state = torch.zeros(w.n, dtype=torch.uint8, device="cuda")
+    xp, _ = U.urchin_solve(bvh, dirs, w.l_ray, sg[0], sg[1], d["nH"], d["T"], tol=1e-300, max_iter=n - 1,
+                           state=state, raise_not_converged=False, **kw)
+    xa, xpa, stp = x.cpu().numpy(), xp.cpu().numpy(), state.cpu().numpy()
+    act = np.flatnonzero((stp & 2) == 0)
+    org = np.sort(np.random.default_rng(6).choice(act, size=min(64, act.size), replace=False))
+    tf, tn = O.columns_nearfar(w, xpa, O.healpix(1), origins=org)
+    latched = (stp[org] & 1) > 0
+    poly = slab == U.SLAB_SPECTRUM
+    eps_col, eps_rate = 1e-6, (2e-6 + 2e-5 if poly else 2e-6)
+    nH, T = w.nH[org], w.T[org]
+    lr_lo, g_lo = O.gamma_nearfar(tf * (1 - eps_col), tn * (1 - eps_col), so[0], so[1], nH, T, latched, poly=poly)
+    lr_hi, g_hi = O.gamma_nearfar(tf * (1 + eps_col), tn * (1 + eps_col), so[0], so[1], nH, T, latched, poly=poly)
+    g_lo, g_hi = g_lo * (1 + eps_rate), g_hi * (1 - eps_rate)         # most and least rate
+    te_lo, te_hi = -lr_lo - eps_rate, -lr_hi + eps_rate
+    for a, i in enumerate(org):
+        cases = [True] if (latched[a] or te_lo[a] >= 1.0) else ([False] if te_hi[a] < 1.0 else [False, True])
+        lo = min(float(O.xeq(g_lo[a], nH[a], T[a], 0.0, c)[0]) for c in cases)
+        hi = max(float(O.xeq(g_hi[a], nH[a], T[a], 0.0, c)[0]) for c in cases)
+        assert lo * (1 - 1e-12) <= xa[i] <= hi * (1 + 1e-12), (int(i), xa[i], lo, hi)
