@@ -215,10 +215,12 @@ class OracleSample:
         return time.perf_counter() - t0
 
     def sample(self, seconds: float, seed: int):
-        """One sample of about `seconds`; the size is calibrated on the first call."""
+        """One sample of about `seconds`; the size is calibrated on the first
+        call (twice: the first small run also pays the threads' start-up)."""
         if self.count == 64:
-            t = self.run(64, seed + 1000)
-            self.count = int(min(self.w.n, max(64, 64 * seconds / max(t, 1e-3))))
+            for c in (64, 1024):
+                t = self.run(c, seed + 1000 + c)
+                self.count = int(min(self.w.n, max(64, c * seconds / max(t, 1e-3))))
         dt = self.run(self.count, seed)
         return {"rays": self.count * self.dirs.shape[0], "origins": self.count, "seconds": dt,
                 "cores": self.O.num_threads()}
@@ -561,33 +563,54 @@ def gradient_workload(D, stream, max_iter: int):
     s2h, w2h = U.urchin_spectrum_weights(e2, J2, w.gamma_thin)
     s2, w2 = torch.from_numpy(s2h).to(dev), torch.from_numpy(w2h).to(dev)
     kw = dict(tol=1e-5, tau_skip=1e-4, max_iter=max_iter, method=U.METHOD_NEWTON, gmres_m=60, newton_eta=1e-4,
-              segments=U.SEG_AUTO, precision=U.F32, raise_not_converged=False)
+              segments=U.SEG_AUTO, precision=U.F32, raise_not_converged=False, profile=True)
+    clocks = Clocks(dev.index if dev.index is not None else 0)
+    clocks.start()
     bvh = D.bvh()
     w2t = w2 * torch.from_numpy(np.random.default_rng(1308).uniform(0.8, 1.2, 200)).to(dev)
     xt, stt = U.urchin_solve(bvh, D.dirs, w.l_ray, s2, w2t, D.d["nH"], D.d["T"], **kw)
     target = torch.log10(U.urchin_trace_columns(bvh, xt, D.dirs, w.l_ray).double())
     wv = w2.clone().requires_grad_(True)
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    free0 = torch.cuda.mem_get_info(dev)[0]
     torch.cuda.synchronize(dev)
+    host = [time.perf_counter()]
     ev[0].record(stream)
     info = {}
     xg = UA.converged_x(wv, bvh, D.dirs, w.l_ray, s2, D.d["nH"], D.d["T"], solve_kw=kw,
-                        vjp_kw=dict(tol=1e-6, max_iter=600, gmres_m=30, raise_not_converged=False), info=info)
-    L = ((torch.log10(UA.columns(xg, bvh, D.dirs, w.l_ray).double()) - target) ** 2).sum()
+                        vjp_kw=dict(tol=1e-6, max_iter=600, gmres_m=30, raise_not_converged=False, profile=True),
+                        info=info)
+    ev[3].record(stream)
+    host.append(time.perf_counter())
+    cols = UA.columns(xg, bvh, D.dirs, w.l_ray)
+    ev[4].record(stream)
+    host.append(time.perf_counter())
+    L = ((torch.log10(cols.double()) - target) ** 2).sum()
     ev[1].record(stream)
+    host.append(time.perf_counter())
     L.backward()
     ev[2].record(stream)
     ev[2].synchronize()
+    host.append(time.perf_counter())
     bvh.close()
+    clk = clocks.stop()
     fs = info.get("forward_stats", {})
     bs = info.get("vjp_stats", {})
+    # where the time goes, to tell a slow GPU from host-side waits
+    phases = {f"{tag}_{k}": st.get(k) for tag, st in (("forward", fs), ("backward", bs), ("target", stt))
+              for k in ("wall_s", "trace_s", "spmv_s", "sweep_s", "spmv_launches", "trace_launches")}
+    phases.update({"gpu_solve_s": ev[0].elapsed_time(ev[3]) * 1e-3, "gpu_columns_s": ev[3].elapsed_time(ev[4]) * 1e-3,
+                   "gpu_loss_s": ev[4].elapsed_time(ev[1]) * 1e-3, "host_solve_s": host[1] - host[0],
+                   "host_columns_s": host[2] - host[1], "host_loss_s": host[3] - host[2],
+                   "host_backward_s": host[4] - host[3], "free_bytes_at_start": free0})
     return {"loss": float(L.detach()), "forward_s": ev[0].elapsed_time(ev[1]) * 1e-3,
             "backward_s": ev[1].elapsed_time(ev[2]) * 1e-3, "grad_norm": float(wv.grad.norm()),
             "forward": "Newton-Krylov to dx_tol 1e-5 + columns of x*",
             "backward": "adjoint GMRES(30) to 1e-6 + column transpose",
             "forward_iterations": fs.get("iterations"), "forward_segments_stored": fs.get("segments_stored"),
             "forward_newton_start": fs.get("newton_start"), "forward_newton_fallbacks": fs.get("newton_fallbacks"),
-            "backward_products": bs.get("iterations"), "target_solve_iterations": stt["iterations"]}
+            "backward_products": bs.get("iterations"), "target_solve_iterations": stt["iterations"],
+            "phases": phases, "clocks": clk}
 
 
 def cosmological_box(args, dev, stream):

@@ -55,6 +55,34 @@ __global__ void k_setup(const urchin_bvh b, const double* __restrict__ nH, const
     }
 }
 
+// The active list's ray order from the order of all particles (Solver::
+// derive_list_order): list positions of the particles, each direction's
+// full order flagged where its particle is active, and the compacted slots
+// mapped to list positions.
+__global__ void k_list_pos(const int32_t* __restrict__ list, int64_t na, int64_t n, int32_t* __restrict__ pos)
+{
+    for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < na; a += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t i = list[a];
+        if ((uint64_t)i < (uint64_t)n) pos[i] = (int32_t)a;
+    }
+}
+
+__global__ void k_order_flags(const int32_t* __restrict__ order, const uint8_t* __restrict__ active, int64_t n,
+                              uint8_t* __restrict__ flags)
+{
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t i = order[t];
+        flags[t] = (uint64_t)i < (uint64_t)n && active[i] ? 1 : 0;
+    }
+}
+
+__global__ void k_order_map(const int32_t* __restrict__ order, const int32_t* __restrict__ pos, int64_t na,
+                            int32_t* __restrict__ out)
+{
+    for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < na; m += (int64_t)gridDim.x * blockDim.x)
+        out[m] = pos[order[out[m]]];
+}
+
 __global__ void k_finish(const int32_t* __restrict__ perm, const double* __restrict__ x, int64_t n, double* x_out)
 {
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n;
@@ -815,6 +843,37 @@ int Solver::order_for(const int32_t* items, int64_t n_items, const int32_t** out
     return URCHIN_OK;
 }
 
+// The ray order of the active list, derived from sweep 0's order of all
+// particles instead of sorted afresh: ray_order sorts stably by a key of the
+// origin alone, and the list holds the active particles in ascending Morton
+// slot, so the full order restricted to the list is exactly the order a sort
+// of the list would give (2 R radix passes over the list saved per solve).
+int Solver::derive_list_order(const int32_t* full)
+{
+    const int64_t na = n_act;
+    const int64_t rn = (int64_t)P.R * n;
+    if (full != ord_base || na < kRayOrderMinItems || na > n || rn + (int64_t)P.R * na > ord_cap) return URCHIN_OK;
+    int32_t* pos = static_cast<int32_t*>(ord_tmp);
+    uint8_t* flags = reinterpret_cast<uint8_t*>(static_cast<char*>(ord_tmp) + (((size_t)n * 4 + 255) & ~size_t(255)));
+    int32_t* out = ord_base + rn;
+    uint32_t* cnt = reinterpret_cast<uint32_t*>(misc + 2);
+    const unsigned ga = (unsigned)std::max<int64_t>(1, std::min<int64_t>((na + 255) / 256, 4096));
+    const unsigned gn = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 4096));
+    k_list_pos<<<ga, 256, 0, s>>>(list, na, n, pos);
+    URCHIN_TRY(launched());
+    for (int k = 0; k < P.R; ++k) {
+        k_order_flags<<<gn, 256, 0, s>>>(full + (int64_t)k * n, active, n, flags);
+        URCHIN_TRY(launched());
+        URCHIN_TRY(compact_indices(flags, n, out + (int64_t)k * na, cnt, comp_tmp, s));
+        k_order_map<<<ga, 256, 0, s>>>(full + (int64_t)k * n, pos, na, out + (int64_t)k * na);
+        URCHIN_TRY(launched());
+    }
+    orders.push_back(OrderEntry{nullptr, n, ord_base});
+    orders.push_back(OrderEntry{list, na, out});
+    ord_used = rn + (int64_t)P.R * na;
+    return URCHIN_OK;
+}
+
 int Solver::trace(const int32_t* items, int64_t n_items, const float* tw32, const double* tw64)
 {
     TraceJob job{};
@@ -1116,6 +1175,9 @@ int Solver::first_sweep()
     URCHIN_TRY(timed_sweep(sweep_args(nullptr, n, 1), s));
     uint32_t* cnt = reinterpret_cast<uint32_t*>(misc + 2);
     URCHIN_TRY(compact_indices(active, n, list, cnt, comp_tmp, s));
+    const int32_t* full = nullptr;                // sweep 0's ray order of all particles
+    for (const OrderEntry& e : orders)
+        if (e.items == nullptr && e.n == n) full = e.order;
     items_changed();
     uint32_t hc = 0;
     URCHIN_TRY_CUDA(cudaMemcpyAsync(&hc, cnt, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
@@ -1123,6 +1185,7 @@ int Solver::first_sweep()
     unsigned st;
     URCHIN_TRY(read_scalars(&m, &st));
     n_act = hc;
+    if (full) URCHIN_TRY(derive_list_order(full));
     stats.n_active = n_act;
     stats.particle_updates += n_act;
     stats.iterations = 1;

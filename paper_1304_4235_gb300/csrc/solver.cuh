@@ -122,6 +122,7 @@ struct Solver {
     };
     std::vector<OrderEntry> orders;
     int order_for(const int32_t* items, int64_t n_items, const int32_t** out);
+    int derive_list_order(const int32_t* full);
     void items_changed()
     {
         orders.clear();
