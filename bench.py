@@ -544,6 +544,7 @@ def adjoint(D, stream, max_iter: int, segments):
     (wb, vs), dt = timed(stream, go)
     bvh.close()
     return {"loss": "sum ln x*", "segments": "recompute" if segments == U.SEG_RECOMPUTE else "auto",
+            "segments_stored": bool(vs["segments_stored"]),
             "wall_s": dt, "products": vs["iterations"], "rel_residual": vs["max_rel_dx"],
             "converged": bool(vs["converged"]), "rays": vs["rays"], "grad_norm": float(wb.norm()),
             "trace_s": vs["trace_s"], "spmv_s": vs["spmv_s"]}
@@ -656,6 +657,9 @@ def compare(args, key, w, D, stream):
     comp = {"workload": workload_name(key, w)}
     comp.update(convergence(D, stream, args.max_iter))
     comp["adjoint_recompute"] = adjoint(D, stream, args.max_iter, D.U.SEG_RECOMPUTE)
+    # the same gradient with the segment lists stored once (count + fill)
+    # and every transposed product read from them
+    comp["adjoint_stored"] = adjoint(D, stream, args.max_iter, D.U.SEG_AUTO)
     if key.startswith("c5"):
         # the 262144-particle halo beside it
         wh = load_workload("halo", args.cache_dir)
