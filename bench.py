@@ -20,7 +20,7 @@ gradient with recomputed segments, the 262144-particle halo and the
 differentiation workload.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload c5|halo|c5_eighth] [--no-compare] [--no-cpu-baseline] [--no-e2e]
+                  [--workload c5|halo|c5_eighth|halo_65536] [--no-compare] [--no-cpu-baseline] [--no-e2e]
 
 Under torchrun every rank solves its own copy (replicas; independent boxes
 need no exchange) and rank 0 prints one JSON line.
@@ -51,10 +51,12 @@ WORKLOADS = {
     "halo": ("halo", dict()),
     # the same density field at 1/8 of the particles (profiling captures)
     "c5_eighth": ("lognormal_box", dict(n_side=128, box_kpc=4000.0, sigma_ln=2.5, nside=1, F=400)),
+    # the halo at 1/4 of the particles (profiling captures of the stored-segment path)
+    "halo_65536": ("halo", dict(n=65536)),
 }
 
 # Grid cell (kpc) of the oracle's uniform-grid search for each workload.
-GRID_CELL = {"c5": 80.0, "halo": 4.0, "c5_eighth": 80.0}
+GRID_CELL = {"c5": 80.0, "halo": 4.0, "c5_eighth": 80.0, "halo_65536": 4.0}
 
 
 def workload_name(key: str, w) -> str:
