@@ -157,6 +157,7 @@ constexpr int kKTab = 2048;       // intervals of the full-chord M4 table in t =
 // Full-chord M4 integral K(t) = int_{-c}^{c} shape(sqrt(t + u^2)) du, c = sqrt(1-t),
 // tabulated at t_i = i / kKTab as (K(t_i), dK/dt(t_i) / kKTab), host side.
 void m4_full_table(float2* out /* [kKTab + 1] */);
+constexpr int kChunkEntries = 32;   // MODE_CHUNK: segment entries per chunk
 constexpr int kStackMax = 64;     // traversal stack (tree depth <= 62 for 30-bit codes)
 
 // Column tracing shared by urchin_trace_columns and urchin_solve.
@@ -179,7 +180,8 @@ struct TraceJob {
     unsigned int* status;         // one device uint: error flags (may be NULL)
     unsigned long long* hits;     // chord evaluations (may be NULL)
     int mode;                     // 0: columns, 1: count hits per ray, 2: fill segments (+ columns),
-                                  // 3: transpose (scatter coef * A_j * chord into xbar)
+                                  // 3: transpose (scatter coef * A_j * chord into xbar),
+                                  // 4: columns + counts + segments in linked chunks (FP32, no near/far)
     uint32_t* counts;             // mode 1 (and mode 0 when not NULL): [R * n], index k * n + the origin's
                                   //    Morton slot: hits rounded up to a multiple of kSegPad
     const uint64_t* row_ptr;      // mode 2: [R * n + 1] offsets of each ray's segments (same index)
@@ -196,6 +198,13 @@ struct TraceJob {
     void* out_near;               // near_far: hydrogen column (x = 1) of the near particles, in tau units,
                                   //    at [origin's Morton slot + k * near_k_stride] (modes 0 and 2)
     int64_t near_k_stride;
+    uint32_t* chunk_head;         // mode 4: [R * n] first chunk of each ray (index k * n + slot)
+    uint32_t* chunk_next;         // mode 4: [chunk_cap] next chunk of the same ray
+    unsigned long long* chunk_counter;   // mode 4: chunks handed out, zeroed by the caller; above
+                                  //    chunk_cap some rays' lists are incomplete
+    unsigned long long chunk_cap; // mode 4: chunks that chunk_seg holds (32 entries each)
+    int2* chunk_seg;              // mode 4: [chunk_cap * 32] entries (particle index, value bits), a
+                                  //    ray's entries padded with (0, 0) to a multiple of kSegPad
 };
 int launch_trace(const TraceJob& job, cudaStream_t s);
 

@@ -112,6 +112,71 @@ __global__ void __launch_bounds__(kSpmvThreads) k_spmv8(SpmvArgs A)
     }
 }
 
+// FP32 columns from chunked lists: one warp per ray, one entry per lane in
+// each chunk of kChunkEntries (32), following the row's links; the next link
+// is read before the chunk's entries so that its latency overlaps them.
+__global__ void __launch_bounds__(kSpmvThreads) k_spmv_chunk(SpmvArgs A)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (kSpmvThreads / 32);
+    const int64_t total = (int64_t)A.R * A.n_items;
+    const float* xv = static_cast<const float*>(A.xvec);
+    float* out = static_cast<float*>(A.out);
+    for (int64_t w = (int64_t)blockIdx.x * (kSpmvThreads / 32) + (threadIdx.x >> 5); w < total; w += warps) {
+        const int64_t k = w / A.n_items;
+        const int64_t a = w - k * A.n_items;
+        const int64_t i = A.items ? (int64_t)A.items[a] : a;
+        const int64_t row = k * A.n_rows_per_k + i;
+        const uint32_t cnt = A.row_cnt[row];
+        float s = 0.f, c = 0.f;
+        uint32_t ch = cnt ? A.chunk_head[row] : 0u;
+        for (uint32_t done = 0; done < cnt; done += kChunkEntries) {
+            const uint32_t nxt = done + kChunkEntries < cnt ? __ldg(A.chunk_next + ch) : 0u;
+            if (done + (uint32_t)lane < cnt) {
+                const int2 q = __ldcs(A.chunk_seg + (int64_t)ch * kChunkEntries + lane);
+                const float t = __int_as_float(q.y) * __ldg(xv + q.x);
+                const float y = t - c;
+                const float u = s + y;
+                c = (u - s) - y;
+                s = u;
+            }
+            ch = nxt;
+        }
+        s -= c;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) out[a + k * A.n_items] = s;
+    }
+}
+
+// One warp per row: the row's chunks in order, one entry per lane.
+__global__ void __launch_bounds__(kSpmvThreads) k_chunk_compact(ChunkCompactArgs A)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (kSpmvThreads / 32);
+    for (int64_t r = (int64_t)blockIdx.x * (kSpmvThreads / 32) + (threadIdx.x >> 5); r < A.rows; r += warps) {
+        const uint32_t cnt = A.cnt[r];
+        if (cnt == 0) continue;
+        const uint64_t base = A.row_ptr[r];
+        uint32_t ch = A.head[r];
+        for (uint32_t done = 0; done < cnt; done += kChunkEntries) {
+            const uint32_t nxt = done + kChunkEntries < cnt ? __ldg(A.next + ch) : 0u;
+            if (done + (uint32_t)lane < cnt) {
+                const int2 q = __ldcs(A.seg + (int64_t)ch * kChunkEntries + lane);
+                const uint64_t pos = base + done + (uint32_t)lane;
+                if (A.col) {
+                    A.col[pos] = q.x;
+                } else {
+                    A.lo[pos] = (uint16_t)((unsigned)q.x & 0xffffu);
+                    A.hi[pos] = (uint8_t)(((unsigned)q.x >> 16) & 0xffu);
+                }
+                A.val[pos] = __int_as_float(q.y);
+            }
+            ch = nxt;
+        }
+    }
+}
+
 // One warp per ray: the ray's coefficient times each stored segment value is
 // added to z at the segment's particle.
 template <typename Real>
@@ -206,6 +271,15 @@ unsigned grid1(int64_t n) { return (unsigned)std::max<int64_t>(1, std::min<int64
 
 }  // namespace
 
+int launch_chunk_compact(const ChunkCompactArgs& A, cudaStream_t s)
+{
+    if (A.rows <= 0) return URCHIN_OK;
+    int grid = 0;
+    URCHIN_TRY(grid_for((const void*)k_chunk_compact, kSpmvThreads, 0, &grid));
+    k_chunk_compact<<<grid, kSpmvThreads, 0, s>>>(A);
+    return launched();
+}
+
 int launch_spmv(const SpmvArgs& A, cudaStream_t s)
 {
     if (A.n_items <= 0) return URCHIN_OK;
@@ -216,6 +290,11 @@ int launch_spmv(const SpmvArgs& A, cudaStream_t s)
     const void* fn = A.precision == URCHIN_F64 ? (const void*)k_spmv<double>
                                                : (A.col ? (const void*)k_spmv<float> : (const void*)k_spmv8);
     if (A.precision == URCHIN_F64 && !A.col) return set_error(URCHIN_ERR_ARG, "spmv: FP64 segments need int32 indices");
+    if (A.chunk_head) {
+        if (A.precision == URCHIN_F64 || !A.chunk_next || !A.row_cnt || !A.chunk_seg)
+            return set_error(URCHIN_ERR_ARG, "spmv: chunked lists are FP32, with links and row counts");
+        fn = (const void*)k_spmv_chunk;
+    }
     URCHIN_TRY(grid_for(fn, kSpmvThreads, 0, &grid));
     int64_t need = (warps + 7) / 8;
     if (need < grid) grid = (int)std::max<int64_t>(need, 1);

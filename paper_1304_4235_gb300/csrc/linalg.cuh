@@ -21,8 +21,31 @@ struct SpmvArgs {
     int R;
     int precision;
     void* out;                   // [R * n_items], index k * n_items + item
+    // FP32 lists in linked chunks of kChunkEntries (the traversal's MODE_CHUNK)
+    // instead of rows: row_ptr, col, lo, hi and val are then unused
+    const uint32_t* chunk_head;  // [R * n_rows_per_k] first chunk of each row, or NULL: row-major lists
+    const uint32_t* chunk_next;  // the next chunk of the same row
+    const uint32_t* row_cnt;     // [R * n_rows_per_k] entries of each row (padded with zero values)
+    const int2* chunk_seg;       // [chunks * kChunkEntries] entries (particle index, value bits)
 };
 int launch_spmv(const SpmvArgs& A, cudaStream_t s);
+
+// Chunked lists (MODE_CHUNK) copied into rows: row r's entries to
+// [row_ptr[r], row_ptr[r] + cnt[r]) as a particle index (int32 col, or 16 + 8
+// bits in lo / hi) and a value.  Rows with cnt 0 are skipped.
+struct ChunkCompactArgs {
+    const uint32_t* head;
+    const uint32_t* next;
+    const int2* seg;
+    const uint32_t* cnt;         // [rows]
+    const uint64_t* row_ptr;     // [rows + 1]
+    int64_t rows;
+    int32_t* col;                // or NULL:
+    uint16_t* lo;
+    uint8_t* hi;
+    float* val;
+};
+int launch_chunk_compact(const ChunkCompactArgs& A, cudaStream_t s);
 
 // Transpose of the stored columns: z[col_e] += coef[k * n_items + a] * val_e
 // over the segments of every ray (k, items[a]); z is double [n] (Morton),

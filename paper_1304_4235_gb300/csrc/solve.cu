@@ -796,7 +796,7 @@ int Solver::count_spmv(const int32_t* items, int64_t n_items)
         seg = (int64_t)h;
         if (items == list && n_items == n_act) active_nnz = seg;
     }
-    const int64_t isz = seg_col ? (int64_t)sizeof(int32_t) : (int64_t)(sizeof(uint16_t) + sizeof(uint8_t));
+    const int64_t isz = (seg_col || chunked) ? (int64_t)sizeof(int32_t) : (int64_t)(sizeof(uint16_t) + sizeof(uint8_t));
     stats.spmv_bytes += seg * (isz + (int64_t)vsz) + n_items * P.R * (int64_t)vsz + n * (int64_t)vsz;
     return URCHIN_OK;
 }
@@ -924,15 +924,191 @@ __global__ void k_clear_inactive_rows(const uint8_t* __restrict__ active, int64_
 //     292 sweeps, 0.86 s; one traversal 0.04 s).
 constexpr int kAutoStoreSweep = 2;
 
+// The stored lists for a product: rows (row_ptr) or linked chunks.
+void Solver::spmv_lists(SpmvArgs& A) const
+{
+    A.row_ptr = row_ptr;
+    A.col = seg_col;
+    A.lo = seg_lo;
+    A.hi = seg_hi;
+    A.val = seg_val;
+    if (chunked) {
+        A.chunk_head = chunk_head;
+        A.chunk_next = chunk_next;
+        A.row_cnt = counts;
+        A.chunk_seg = chunk_seg;
+    }
+}
+
+// Origins i * stride for the hit-count sample of trace_chunked.
+__global__ void k_strided(int32_t* out, int64_t m, int64_t stride)
+{
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < m; t += (int64_t)gridDim.x * blockDim.x)
+        out[t] = (int32_t)(t * stride);
+}
+
+// The first sweep's traversal of every particle, storing each ray's segments
+// in chunks as it goes (MODE_CHUNK).  The number of segments is not known in
+// advance: it is estimated from the hit counts of a sample of every 64th
+// origin, with room for 15 % more, for half a chunk per ray and for the
+// warps' unused blocks.  When the lists do not fit, or the estimate proves
+// short (some rays' lists are then incomplete), the lists are dropped and the
+// solve goes on as without them: the columns and counts of this traversal are
+// complete either way.
+int Solver::trace_chunked(TraceJob& job)
+{
+    const int64_t rays = (int64_t)P.R * n;
+    const int64_t stride = 64, m = (n + stride - 1) / stride;
+    const double entry_bytes = 8.0;               // particle index + value
+    uint64_t* total = reinterpret_cast<uint64_t*>(misc + 6);
+    unsigned long long cap = 0;
+    {
+        Scratch smp;
+        URCHIN_TRY(smp.alloc(sizeof(int32_t) * (size_t)m, s));
+        int32_t* org = smp.at<int32_t>(0);
+        const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>((m + 255) / 256, 4096));
+        k_strided<<<g, 256, 0, s>>>(org, m, stride);
+        URCHIN_TRY(launched());
+        TraceJob cj = job;
+        cj.items = org;
+        cj.n_items = m;
+        cj.k_stride = m;
+        cj.mode = 1;
+        cj.order = nullptr;
+        cj.counter = counter;
+        cj.status = status;
+        cj.hits = nullptr;
+        URCHIN_TRY(launch_trace(cj, s));
+        URCHIN_TRY(scan_counts_u64(counts, row_ptr, rays, scan_tmp, total, s));
+        uint64_t sample = 0;
+        URCHIN_TRY_CUDA(cudaMemcpyAsync(&sample, total, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+        URCHIN_TRY_CUDA(cudaStreamSynchronize(s));
+        URCHIN_TRY_CUDA(cudaMemsetAsync(counts, 0, sizeof(uint32_t) * (size_t)rays, s));
+        const double est = (double)sample * (double)n / (double)m;
+        int dev = 0, sms = 0;
+        URCHIN_TRY_CUDA(cudaGetDevice(&dev));
+        URCHIN_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        const double chunks = (1.15 * est + 0.5 * kChunkEntries * (double)rays) / kChunkEntries +
+                              (double)sms * 64.0 * 64.0 + 4096.0;
+        size_t free_b = 0, total_b = 0;
+        URCHIN_TRY_CUDA(cudaMemGetInfo(&free_b, &total_b));
+        const double per_chunk = entry_bytes * kChunkEntries + 4.0;
+        const double avail = 0.85 * (double)(free_b + pool_idle_bytes()) - 4.0 * (double)rays;
+        if (chunks * per_chunk <= avail && chunks < 4.0e9) cap = (unsigned long long)chunks;
+    }
+    if (cap > 0) {
+        const size_t entries = (size_t)cap * kChunkEntries;
+        Layout lay;
+        const size_t o_ctr = lay.take(sizeof(unsigned long long));
+        const size_t o_head = lay.take(sizeof(uint32_t) * (size_t)rays);
+        const size_t o_next = lay.take(sizeof(uint32_t) * (size_t)cap);
+        const size_t o_seg = lay.take(sizeof(int2) * entries);
+        if (chunk_mem.alloc(lay.bytes, s) != URCHIN_OK) {
+            clear_error();
+            cap = 0;
+        } else {
+            unsigned long long* ctr = chunk_mem.at<unsigned long long>(o_ctr);
+            URCHIN_TRY_CUDA(cudaMemsetAsync(ctr, 0, sizeof(unsigned long long), s));
+            chunk_head = chunk_mem.at<uint32_t>(o_head);
+            chunk_next = chunk_mem.at<uint32_t>(o_next);
+            job.mode = 4;
+            job.chunk_head = chunk_head;
+            job.chunk_next = chunk_next;
+            job.chunk_counter = ctr;
+            job.chunk_cap = cap;
+            job.chunk_seg = chunk_mem.at<int2>(o_seg);
+            URCHIN_TRY(timed_trace(job));
+            unsigned long long used = 0;
+            URCHIN_TRY_CUDA(cudaMemcpyAsync(&used, ctr, sizeof(used), cudaMemcpyDeviceToHost, s));
+            URCHIN_TRY_CUDA(cudaStreamSynchronize(s));
+            if (used <= cap) {
+                chunk_seg = job.chunk_seg;
+                chunked = true;
+                stored = true;
+                stats.segments_stored = 1;
+                URCHIN_TRY(scan_counts_u64(counts, row_ptr, rays, scan_tmp, total, s));
+                URCHIN_TRY_CUDA(cudaMemcpyAsync(row_ptr + rays, total, sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+                uint64_t nnz = 0;
+                URCHIN_TRY_CUDA(cudaMemcpyAsync(&nnz, total, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+                URCHIN_TRY_CUDA(cudaStreamSynchronize(s));
+                stats.nnz = (int64_t)nnz;
+                return URCHIN_OK;
+            }
+            // the estimate was short: the lists are incomplete, the columns are not
+            chunk_mem.release();
+            chunk_head = chunk_next = nullptr;
+            return URCHIN_OK;
+        }
+    }
+    job.mode = 0;
+    return timed_trace(job);
+}
+
+// From the fourth sweep on, the chunked lists of the active rows are copied
+// into rows (the 7-byte layout of the row product, which streams at the
+// bandwidth bound where following chunk links does not) when both fit at
+// once; the chunks are then released.  A solve of two or three sweeps keeps
+// the chunks.
+constexpr int kCompactSweep = 3;
+
+int Solver::compact_chunks()
+{
+    const int64_t rays = (int64_t)P.R * n;
+    const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>((rays + 255) / 256, 4096));
+    k_clear_inactive_rows<<<g, 256, 0, s>>>(active, n, P.R, counts);
+    URCHIN_TRY(launched());
+    uint64_t* total = reinterpret_cast<uint64_t*>(misc + 6);
+    URCHIN_TRY(scan_counts_u64(counts, row_ptr, rays, scan_tmp, total, s));
+    URCHIN_TRY_CUDA(cudaMemcpyAsync(row_ptr + rays, total, sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+    uint64_t nnz = 0;
+    URCHIN_TRY_CUDA(cudaMemcpyAsync(&nnz, total, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+    URCHIN_TRY_CUDA(cudaStreamSynchronize(s));
+    const bool split = n <= (int64_t(1) << 24);
+    Layout lay;
+    const size_t o_col = split ? 0 : lay.take(sizeof(int32_t) * (size_t)nnz);
+    const size_t o_lo = split ? lay.take(sizeof(uint16_t) * (size_t)nnz) : 0;
+    const size_t o_hi = split ? lay.take(sizeof(uint8_t) * (size_t)nnz) : 0;
+    const size_t o_val = lay.take(sizeof(float) * (size_t)nnz);
+    size_t free_b = 0, total_b = 0;
+    URCHIN_TRY_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    if ((double)lay.bytes > 0.85 * (double)(free_b + pool_idle_bytes()) || seg.alloc(lay.bytes, s) != URCHIN_OK) {
+        clear_error();
+        return URCHIN_OK;                          // keep the chunks
+    }
+    ChunkCompactArgs C{};
+    C.head = chunk_head;
+    C.next = chunk_next;
+    C.seg = chunk_seg;
+    C.cnt = counts;
+    C.row_ptr = row_ptr;
+    C.rows = rays;
+    C.col = split ? nullptr : seg.at<int32_t>(o_col);
+    C.lo = split ? seg.at<uint16_t>(o_lo) : nullptr;
+    C.hi = split ? seg.at<uint8_t>(o_hi) : nullptr;
+    C.val = seg.at<float>(o_val);
+    URCHIN_TRY(launch_chunk_compact(C, s));
+    seg_col = C.col;
+    seg_lo = C.lo;
+    seg_hi = C.hi;
+    seg_val = C.val;
+    chunked = false;
+    chunk_mem.release();
+    chunk_head = chunk_next = nullptr;
+    chunk_seg = nullptr;
+    stats.nnz = (int64_t)nnz;
+    active_nnz = -1;
+    return URCHIN_OK;
+}
+
 int Solver::columns(const int32_t* items, int64_t n_items, int sweep0, bool build)
 {
+    if (!sweep0 && chunked && !compact_tried && stats.iterations >= kCompactSweep) {
+        compact_tried = true;
+        URCHIN_TRY(compact_chunks());
+    }
     if (!sweep0 && stored) {
         SpmvArgs A{};
-        A.row_ptr = row_ptr;
-        A.col = seg_col;
-        A.lo = seg_lo;
-        A.hi = seg_hi;
-        A.val = seg_val;
+        spmv_lists(A);
         A.xvec = f64 ? (const void*)xs64 : (const void*)xs32;
         A.items = items;
         A.n_items = n_items;
@@ -973,10 +1149,16 @@ int Solver::columns(const int32_t* items, int64_t n_items, int sweep0, bool buil
     const int64_t rays = (int64_t)P.R * n;
     const bool deferred = P.segments == URCHIN_SEG_AUTO && !build && P.blocks <= 1;
     if (deferred && !counts_ready) {
-        // recomputed columns, every ray's hits counted on the way
+        // recomputed columns, every ray's hits counted on the way; for a
+        // first sweep over every particle the segment lists are kept too
+        // (in chunks) where they fit, so that the next sweeps need no traversal
         URCHIN_TRY_CUDA(cudaMemsetAsync(counts, 0, sizeof(uint32_t) * (size_t)rays, s));
-        job.mode = 0;
-        URCHIN_TRY(timed_trace(job));
+        if (!f64 && !P.near_far && items == nullptr && n_items == n) {
+            URCHIN_TRY(trace_chunked(job));
+        } else {
+            job.mode = 0;
+            URCHIN_TRY(timed_trace(job));
+        }
         counts_ready = true;
         counted_all = items == nullptr && n_items == n;
         stats.traversals += 1;
@@ -1060,11 +1242,7 @@ int Solver::linear_columns(const int32_t* items, int64_t n_items, const float* z
     stats.traversals += 1;
     if (stored) {
         SpmvArgs A{};
-        A.row_ptr = row_ptr;
-        A.col = seg_col;
-        A.lo = seg_lo;
-        A.hi = seg_hi;
-        A.val = seg_val;
+        spmv_lists(A);
         A.xvec = f64 ? (const void*)z64 : (const void*)z32;
         A.items = items;
         A.n_items = n_items;
@@ -1763,6 +1941,7 @@ int Solver::finish(double* x_inout)
     }
     nk.release();
     seg.release();
+    chunk_mem.release();
     ord.release();
     scr.release();
     URCHIN_TRY_CUDA(cudaStreamSynchronize(s));

@@ -5,6 +5,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "linalg.cuh"
 #include "spectral_device.cuh"
 
 namespace urchin {
@@ -109,6 +110,17 @@ struct Solver {
     uint8_t* seg_hi = nullptr;                   // n <= 2^24: 7 bytes per segment instead of 8)
     void* seg_val = nullptr;
     Scratch seg;
+    // segment lists stored by the first sweep's traversal in linked chunks
+    // (SEG_AUTO, FP32): later sweeps read them instead of tracing again
+    bool chunked = false;
+    bool compact_tried = false;
+    Scratch chunk_mem;
+    uint32_t* chunk_head = nullptr;
+    uint32_t* chunk_next = nullptr;
+    int2* chunk_seg = nullptr;
+    int trace_chunked(TraceJob& job);
+    int compact_chunks();
+    void spmv_lists(SpmvArgs& A) const;
     // per-direction traversal orders, cached per item list (any permutation
     // is correct; a stale one only costs coherence)
     Scratch ord;

@@ -65,9 +65,23 @@ struct TraceParams {
     // near/far split
     void* out_near;               // [slot + k * near_k_stride] near column (x = 1)
     int64_t near_k_stride;
+    // MODE_CHUNK: segment lists in chunks of kChunk entries taken while tracing
+    uint32_t* chunk_head;         // [R * n] first chunk of each ray (rays with hits)
+    uint32_t* chunk_next;         // [cap] the chunk after each chunk of a ray
+    unsigned long long* chunk_counter;   // chunks handed out (may exceed cap: then the lists are incomplete)
+    unsigned long long chunk_cap;
+    int2* chunk_seg;              // [cap * kChunk] (particle, value bits): one 8-byte store per full chord
 };
 
-constexpr int MODE_TAU = 0, MODE_COUNT = 1, MODE_FILL = 2, MODE_SCATTER = 3;
+constexpr int MODE_TAU = 0, MODE_COUNT = 1, MODE_FILL = 2, MODE_SCATTER = 3, MODE_CHUNK = 4;
+// MODE_CHUNK: the columns as in MODE_TAU, the hit counts as in MODE_COUNT, and
+// every ray's segments stored while tracing, in chunks of kChunk entries that
+// the warp takes from a global counter kStash at a time (the counts are not
+// known before the traversal); the chunks of a ray are linked through
+// chunk_next.  Used by the solver's first sweep, so that a solve of two sweeps
+// traces once.
+constexpr int kChunk = kChunkEntries;   // entries per chunk (a multiple of kSegPad)
+constexpr int kStash = 64;        // chunks a warp takes from the counter at a time
 
 // Where a ray's hits go: the running column sum, and in MODE_FILL the
 // cursor into the ray's stored segment list.
@@ -81,6 +95,7 @@ struct Sink {
     Real near, near_c;            // near/far: near column and its compensation
     double ox, oy, oz;            // near/far: shifted origin in double (the near test)
     uint32_t lo_pend, hi_pend;    // MODE_FILL, split indices: halves / bytes of the current word
+    int64_t ray;                  // MODE_CHUNK: row k n + origin slot
 };
 
 // Near/far split (Sec. 3.3.3): particle j is near the ray's origin when the
@@ -551,6 +566,7 @@ __device__ __noinline__ void flush_partials(const TraceParams& P, const float2* 
             const bool near = NF && (it.owner & kPQNear);
             v = near ? A * F : __ldg(P.w32 + it.j) * F;
             if (MODE == MODE_FILL && !near) static_cast<float*>(P.seg_val)[it.pos] = A * F;
+            if (MODE == MODE_CHUNK && it.pos >= 0) P.chunk_seg[it.pos].y = __float_as_int(A * F);
             owner = it.owner & (31 | kPQNear);
         }
     }
@@ -576,6 +592,21 @@ __device__ __noinline__ void flush_partials(const TraceParams& P, const float2* 
     count = rest;
 }
 
+// MODE_CHUNK: `want` consecutive chunks from the warp's block of chunks in
+// shared memory, a new block of kStash (or more) from the global counter when
+// it runs out.  Called by lane 0 with the warp converged.
+__device__ __forceinline__ unsigned long long chunk_block(const TraceParams& P, unsigned long long* stash, int want)
+{
+    unsigned long long b = stash[0];
+    if (b + (unsigned long long)want > stash[1]) {
+        const unsigned long long take = want > kStash ? (unsigned long long)want : (unsigned long long)kStash;
+        b = atomicAdd(P.chunk_counter, take);
+        stash[1] = b + take;
+    }
+    stash[0] = b + (unsigned long long)want;
+    return b;
+}
+
 // FP32 hit evaluation: cheap rejection, then the impact parameter from an
 // error-free cross product, then the tabulated / piecewise chord integral.
 // FP32 hit evaluation: cheap rejection, then the impact parameter from an
@@ -584,18 +615,18 @@ __device__ __noinline__ void flush_partials(const TraceParams& P, const float2* 
 // queue is shared); lanes that are not live only take part in the queue.
 template <int KERNEL, int MODE, bool NF>
 __device__ __forceinline__ void leaf_hits_f32(const TraceParams& P, const float2* tab, PartQueue* pq, int& pq_count,
-                                              int ref, int cnt, unsigned mask, bool live, float sx, float sy,
-                                              float sz, float dx, float dy, float dz, float L, Sink<float>& k,
-                                              unsigned& err)
+                                              unsigned long long* stash, int ref, int cnt, unsigned mask, bool live,
+                                              float sx, float sy, float sz, float dx, float dy, float dz, float L,
+                                              Sink<float>& k, unsigned& err)
 {
     if (ref < 0 || cnt > kLeafMax || ref + cnt > P.n) return;   // never true for a well-formed tree
     if (live) k.ntest += (unsigned)__popc(mask);
     const int lane = threadIdx.x & 31;
     for (unsigned m = mask; m; m &= m - 1) {
         const int j = ref + __ffs(m) - 1;
-        bool part = false, near = false;
+        bool part = false, near = false, store = false;
         int clip = 0;
-        float beta2 = 0.f, u1 = 0.f, u2 = 0.f;
+        float beta2 = 0.f, u1 = 0.f, u2 = 0.f, segv = 0.f;
         int64_t spos = 0;
         if (live) {
             // The hit decision is written with explicit roundings (no
@@ -625,6 +656,7 @@ __device__ __forceinline__ void leaf_hits_f32(const TraceParams& P, const float2
             if (hit) {
                 near = NF && is_near(k, q, tc, ch);
                 if (!near) ++k.nhit;
+                if (MODE == MODE_CHUNK && !near) store = true;
                 if (MODE != MODE_COUNT) {
                     const float ih = 1.f / q.w;
                     beta2 = b2 * ih * ih;
@@ -649,6 +681,7 @@ __device__ __forceinline__ void leaf_hits_f32(const TraceParams& P, const float2
                         } else {
                             Kahan::add(k.sum, k.comp, __ldg(P.w32 + j) * F);
                             if (MODE == MODE_FILL) static_cast<float*>(P.seg_val)[spos] = A * F;
+                            if (MODE == MODE_CHUNK) segv = A * F;
                         }
                     } else if (hit) {
                         part = true;
@@ -660,6 +693,36 @@ __device__ __forceinline__ void leaf_hits_f32(const TraceParams& P, const float2
             }
         }
         if (MODE == MODE_COUNT) continue;
+        if constexpr (MODE == MODE_CHUNK) {
+            // with the warp converged: a new chunk for every ray whose chunk
+            // is full (or that has none yet), then the segment's index (and a
+            // full chord's value; a partial chord's at the flush)
+            const bool need = store && k.pos >= 0 && k.pos == k.end;
+            const unsigned nm = __ballot_sync(0xffffffffu, need);
+            if (nm) {
+                unsigned long long base = 0;
+                if (lane == 0) base = chunk_block(P, stash, __popc(nm));
+                base = __shfl_sync(0xffffffffu, base, 0);
+                if (need) {
+                    const unsigned long long c = base + (unsigned long long)__popc(nm & ((1u << lane) - 1u));
+                    if (c < P.chunk_cap) {
+                        if (k.end == 0) P.chunk_head[k.ray] = (uint32_t)c;
+                        else P.chunk_next[(k.end - 1) / kChunk] = (uint32_t)c;
+                        k.pos = (int64_t)c * kChunk;
+                        k.end = k.pos + kChunk;
+                    } else {
+                        k.pos = k.end = -1;         // the pool is exhausted: this ray stores no more
+                    }
+                }
+            }
+            spos = -1;
+            if (store && k.pos >= 0) {
+                // a partial chord's value follows at the flush
+                if (!part) P.chunk_seg[k.pos] = make_int2(j, __float_as_int(segv));
+                else P.chunk_seg[k.pos].x = j;
+                spos = k.pos++;
+            }
+        }
         const unsigned pb = __ballot_sync(0xffffffffu, part);
         if (!pb) continue;
         if (part) {
@@ -742,8 +805,8 @@ __device__ __forceinline__ void leaf_hits(const TraceParams& P, int ref, int cnt
 
 template <typename Real, int KERNEL, int MODE, bool NF>
 __device__ void ray_column(const TraceParams& P, const float2* tab, Beam* beam, PartQueue* pq, int& pq_count,
-                           float4 o, Real dx, Real dy, Real dz, bool live, Sink<Real>& sk, unsigned& err,
-                           unsigned& nvisit)
+                           unsigned long long* stash, float4 o, Real dx, Real dy, Real dz, bool live, Sink<Real>& sk,
+                           unsigned& err, unsigned& nvisit)
 {
     const Real L = Real(P.l_ray);
     const float Lf = (float)P.l_ray * 1.000001f + 1e-30f;
@@ -797,8 +860,8 @@ __device__ void ray_column(const TraceParams& P, const float2* tab, Beam* beam, 
                 const unsigned mask = beam_mask(P, *beam, ref, cnt);
                 if (mask) {
                     if constexpr (sizeof(Real) == 4)
-                        leaf_hits_f32<KERNEL, MODE, NF>(P, tab, pq, pq_count, ref, cnt, mask, live, sx, sy, sz, dx,
-                                                        dy, dz, L, sk, err);
+                        leaf_hits_f32<KERNEL, MODE, NF>(P, tab, pq, pq_count, stash, ref, cnt, mask, live, sx, sy,
+                                                        sz, dx, dy, dz, L, sk, err);
                     else if (live)
                         leaf_hits<Real, KERNEL, MODE, NF>(P, ref, cnt, mask, sx, sy, sz, dx, dy, dz, L, sk, err);
                 }
@@ -827,6 +890,7 @@ __global__ void __launch_bounds__(256, 4) k_trace(TraceParams P)
     extern __shared__ double s_dirs[];
     float2* s_tab = reinterpret_cast<float2*>(s_dirs + 3 * P.R);
     __shared__ Beam s_beam[256 / 32];
+    __shared__ unsigned long long s_stash[256 / 32][2];   // MODE_CHUNK: the warp's block of chunks
     // the warps' partial-chord queues (FP32 modes that evaluate chords), after the table
     constexpr bool kQueue = sizeof(Real) == 4 && MODE != MODE_COUNT;
     PartQueue* pq = nullptr;
@@ -837,6 +901,10 @@ __global__ void __launch_bounds__(256, 4) k_trace(TraceParams P)
         pq->own[(threadIdx.x & 31) + kPQNear] = 0u;
     }
     int pq_count = 0;
+    if ((threadIdx.x & 31) == 0) {
+        s_stash[threadIdx.x >> 5][0] = 0ull;
+        s_stash[threadIdx.x >> 5][1] = 0ull;
+    }
     for (int t = threadIdx.x; t < 3 * P.R; t += blockDim.x) s_dirs[t] = P.dirs[t];
     if (sizeof(Real) == 4 && KERNEL == URCHIN_KERNEL_M4)
         for (int t = threadIdx.x; t <= kKTab; t += blockDim.x) s_tab[t] = P.ktab[t];
@@ -866,6 +934,7 @@ __global__ void __launch_bounds__(256, 4) k_trace(TraceParams P)
         // stored-segment rows are indexed by direction and Morton slot (rows
         // of particles not in the item list stay empty)
         const int64_t ray = (int64_t)k * P.n + org;
+        sk.ray = ray;
         const int64_t orow = live ? (P.out_row ? (int64_t)P.out_row[item] : item) : 0;
         if (live && MODE == MODE_FILL) {
             sk.pos = (int64_t)P.row_ptr[ray];
@@ -875,8 +944,8 @@ __global__ void __launch_bounds__(256, 4) k_trace(TraceParams P)
             sk.coef = static_cast<const Real*>(P.coef)[orow * P.row_stride + (int64_t)k * P.k_stride];
             live = sk.coef != Real(0);
         }
-        ray_column<Real, KERNEL, MODE, NF>(P, s_tab, s_beam + (threadIdx.x >> 5), pq, pq_count, o, dx, dy, dz, live,
-                                           sk, err, nvisit);
+        ray_column<Real, KERNEL, MODE, NF>(P, s_tab, s_beam + (threadIdx.x >> 5), pq, pq_count,
+                                           s_stash[threadIdx.x >> 5], o, dx, dy, dz, live, sk, err, nvisit);
         if constexpr (kQueue) {
             if (pq_count > 0) flush_partials<KERNEL, MODE, NF>(P, s_tab, pq, pq_count, pq_count, sk);
         }
@@ -884,9 +953,13 @@ __global__ void __launch_bounds__(256, 4) k_trace(TraceParams P)
             hits += sk.nhit;
             tests += sk.ntest;
             visits += nvisit;
-            if (MODE == MODE_COUNT || (MODE == MODE_TAU && P.counts))
+            if (MODE == MODE_COUNT || MODE == MODE_CHUNK || (MODE == MODE_TAU && P.counts))
                 P.counts[ray] = (sk.nhit + (unsigned)kSegPad - 1u) / (unsigned)kSegPad * (unsigned)kSegPad;
             if (MODE != MODE_COUNT && MODE != MODE_SCATTER) {
+                if (MODE == MODE_CHUNK && sk.pos >= 0) {
+                    // zero entries up to a multiple of kSegPad (inside the chunk)
+                    for (; (sk.pos & (int64_t)(kSegPad - 1)) != 0; ++sk.pos) P.chunk_seg[sk.pos] = make_int2(0, 0);
+                }
                 if (MODE == MODE_FILL) {
                     // the padding (fewer than kSegPad entries) holds zero values
                     if (sk.end - sk.pos >= kSegPad || sk.pos > sk.end) err |= kStSegment;
@@ -949,11 +1022,16 @@ int dispatch_k(const TraceParams& P, int mode, bool nf, cudaStream_t s)
         if (mode == MODE_COUNT) return launch_one<Real, KERNEL, MODE_COUNT, true>(P, s);
         if (mode == MODE_FILL) return launch_one<Real, KERNEL, MODE_FILL, true>(P, s);
         if (mode == MODE_SCATTER) return set_error(URCHIN_ERR_ARG, "trace: no transpose with the near/far split");
+        if (mode == MODE_CHUNK) return set_error(URCHIN_ERR_ARG, "trace: no chunked segment lists with the near/far split");
         return launch_one<Real, KERNEL, MODE_TAU, true>(P, s);
     }
     if (mode == MODE_COUNT) return launch_one<Real, KERNEL, MODE_COUNT, false>(P, s);
     if (mode == MODE_FILL) return launch_one<Real, KERNEL, MODE_FILL, false>(P, s);
     if (mode == MODE_SCATTER) return launch_one<Real, KERNEL, MODE_SCATTER, false>(P, s);
+    if (mode == MODE_CHUNK) {
+        if constexpr (sizeof(Real) == 4) return launch_one<Real, KERNEL, MODE_CHUNK, false>(P, s);
+        return set_error(URCHIN_ERR_ARG, "trace: chunked segment lists are FP32 only");
+    }
     return launch_one<Real, KERNEL, MODE_TAU, false>(P, s);
 }
 
@@ -1052,10 +1130,18 @@ int launch_trace(const TraceJob& job, cudaStream_t s)
     P.order = job.order;
     P.out_near = job.out_near;
     P.near_k_stride = job.near_k_stride;
+    P.chunk_head = job.chunk_head;
+    P.chunk_next = job.chunk_next;
+    P.chunk_counter = job.chunk_counter;
+    P.chunk_cap = job.chunk_cap;
+    P.chunk_seg = job.chunk_seg;
     if (job.near_far && !job.out_near && job.mode != MODE_COUNT)
         return set_error(URCHIN_ERR_ARG, "trace: near/far split without a near-column output");
     if (job.mode == MODE_FILL && !job.seg_col && !(job.seg_lo && job.seg_hi && b->n <= (int64_t(1) << 24)))
         return set_error(URCHIN_ERR_ARG, "trace: segment fill without a particle-index array");
+    if (job.mode == MODE_CHUNK && (!job.chunk_head || !job.chunk_next || !job.chunk_counter || !job.counts ||
+                                   !job.chunk_seg || job.chunk_cap == 0 || job.chunk_cap > 0xffffffffull))
+        return set_error(URCHIN_ERR_ARG, "trace: chunked segment lists need heads, links, a counter and counts");
     return dispatch_mode(P, job.precision, job.kernel, job.mode, job.near_far != 0, s);
 }
 

@@ -41,6 +41,17 @@ def test_only_abi_symbols_exported():
     assert exported == set(declared_symbols())
 
 
+def test_library_resolves_every_symbol_at_load():
+    """Loaded with immediate binding, so that a function the library calls
+    but does not define (one left with internal linkage in another
+    translation unit, say) fails here rather than at its first call."""
+    C.CDLL(U.library_path(), mode=os.RTLD_NOW | os.RTLD_LOCAL)
+    import subprocess
+    out = subprocess.run(["nm", "-D", "--undefined-only", U.library_path()], capture_output=True,
+                         text=True).stdout
+    assert not [l for l in out.splitlines() if "urchin" in l], out
+
+
 def test_version():
     assert "sm_103a" in U.urchin_version()
 

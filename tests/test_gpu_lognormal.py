@@ -114,9 +114,10 @@ def test_large_box_columns_and_recomputed_sweep_sampled():
     8 Mpc, 12 rays of 100 kpc, 400 bins): all 2.0e8 rays traced in one call
     (FP32), 32 seeded origins compared with the oracle's columns (its
     uniform-grid search, itself checked equal to its brute force at two of
-    them); then sweeps 1 and 2 in recompute mode, each checked at the same
-    32 origins against the oracle's update of the GPU's previous state with
-    check_sweep's per-particle error model."""
+    them); then sweeps 1 and 2 as the benchmark runs them (SEG_AUTO: sweep
+    0 keeps the segment lists in chunks while tracing, sweep 1 reads them),
+    each checked at the same 32 origins against the oracle's update of the
+    GPU's previous state with check_sweep's per-particle error model."""
     w = W.lognormal_box(n_side=256, box_kpc=8000.0, sigma_ln=2.5, nside=1, F=400)
     bvh, d = build(w, torch)
     dirs = U.urchin_healpix_dirs(1)
@@ -134,8 +135,9 @@ def test_large_box_columns_and_recomputed_sweep_sampled():
     for k in (1, 2):
         state = torch.zeros(w.n, dtype=torch.uint8, device="cuda")
         xk, st = U.urchin_solve(bvh, dirs, w.l_ray, sg[0], sg[1], d["nH"], d["T"], tol=1e-300, max_iter=k,
-                                segments=U.SEG_RECOMPUTE, precision=U.F32, raise_not_converged=False, state=state)
-        assert st["segments_stored"] == 0 and st["iterations"] == k
+                                segments=U.SEG_AUTO, precision=U.F32, raise_not_converged=False, state=state,
+                                profile=True)
+        assert st["segments_stored"] == 1 and st["iterations"] == k and st["trace_launches"] == 1
         states.append((xk.cpu().numpy(), state.cpu().numpy()))
     cols = lambda xx, o: grid.columns(xx, O.healpix(1), origins=o)
     x0 = O.xeq(so[1].sum(), w.nH, w.T, 0.0, False)

@@ -314,19 +314,19 @@ def test_solve_not_converged_and_bad_inputs(halo_small):
 def test_solve_full_size_halo_one_sweep_sampled(segments):
     """Benchmark-size halo: sweeps 1-4 of the GPU at 256 seeded particles
     against the oracle's update of the GPU's previous state, per particle
-    within check_sweep's error model.  With SEG_AUTO, sweeps 1-2 trace
-    recomputed columns (the first counting hits), sweep 3 fills the padded
-    segment lists (FP32 values, 24-bit particle indices split into 16 + 8
-    bits) and sweep 4 reads its columns from them (8 segments per lane)."""
+    within check_sweep's error model.  With SEG_AUTO, sweep 0 traces every
+    particle and keeps each ray's segment list in linked chunks of 32
+    (FP32 values, 24-bit particle indices split into 16 + 8 bits), taken
+    while tracing; sweeps 1-3 read their columns from those lists."""
     w = W.halo()
     bvh, d = build(w, torch)
     sg, so = spectra(w, torch)
     states = _gpu_states(w, bvh, d, sg, 4, segments=segments)
     _, st2 = _solve_gpu(w, bvh, d, sg, U.F32, tol=1e-300, max_iter=2, segments=segments)
     _, st4 = _solve_gpu(w, bvh, d, sg, U.F32, tol=1e-300, max_iter=4, segments=segments, profile=True)
-    assert st2["segments_stored"] == 0
-    assert bool(st4["segments_stored"]) == (segments == U.SEG_AUTO)
-    assert st4["spmv_launches"] == (1 if segments == U.SEG_AUTO else 0)
+    assert bool(st2["segments_stored"]) == bool(st4["segments_stored"]) == (segments == U.SEG_AUTO)
+    assert st4["spmv_launches"] == (3 if segments == U.SEG_AUTO else 0)
+    assert st4["trace_launches"] == (1 if segments == U.SEG_AUTO else 4)
     assert _check_chain(w, so, states, W.random_origins(w.n, 256, 10)) <= 1.0
 
 
