@@ -339,22 +339,31 @@ def roofline_spmv(stats, hbm, peak_kind):
             "launch_ms": per_s * 1e3, "segments_per_launch": seg / max(launches, 1)}
 
 
-def roofline(stats, trace_launches_total, hbm, peak_kind):
+def roofline(stats, trace_launches_total, hbm, peak_kind, rays_per_sweep):
     """k_trace against the HBM roofline: algorithmic bytes per launch (every
     ray-sphere hit reads a 16-byte particle record and its 4-byte weight; every
-    ray writes its 4-byte column) over the launch's mean duration."""
+    ray writes its 4-byte column) over the launch's mean duration.  When the
+    solve's one traversal also stored the segment lists (one per step, over
+    every particle's rays), it writes each ray's 4-byte hit count and every
+    stored entry (8 bytes: particle index and value, the padding included)."""
     hits = sum(st["hits"] for st in stats)
-    rays = sum(st["rays"] for st in stats)
     trace_s = sum(st["trace_s"] for st in stats)
     n = max(trace_launches_total, 1)
-    per_bytes = (hits * 20 + rays * 4) / n
+    if all(st["trace_launches"] == 1 and st["segments_stored"] for st in stats):
+        rays = rays_per_sweep * len(stats)
+        stored = sum(st["nnz"] for st in stats)
+        per_bytes = (hits * 20 + rays * 8 + stored * 8) / n
+    else:
+        rays = sum(st["rays"] for st in stats)
+        per_bytes = (hits * 20 + rays * 4) / n
     per_s = trace_s / n
     achieved = per_bytes / per_s / 1e9 if per_s > 0 else None
     t = MEASURED_TRAFFIC["k_trace"].get(source_hash("k_trace"))
     return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": achieved / hbm if achieved else None,
             "traffic": (t * hits / n) if t else None,
-            "kernel": "k_trace<float,M4> (FP32 columns, recomputed)", "peak_kind": peak_kind,
+            "kernel": "k_trace<float,M4> (FP32 columns; segment lists stored while tracing where the solve "
+                      "keeps them)", "peak_kind": peak_kind,
             "alg_bytes_per_launch": per_bytes, "launch_ms": per_s * 1e3,
             "hits_per_launch": hits / n, "rays_per_launch": rays / n,
             "sphere_tests_per_hit": sum(st["sphere_tests"] for st in stats) / max(hits, 1),
@@ -449,7 +458,8 @@ def main():
     kernels = {
         "k_trace": {"s": trace_s, "launches": trace_launches},
         "k_sweep_pp": {"s": sweep_s, "launches": sum(st["sweep_launches"] for st in stats)},
-        "k_spmv8": {"s": sum(st["spmv_s"] for st in stats), "launches": sum(st["spmv_launches"] for st in stats)},
+        "stored_columns": {"s": sum(st["spmv_s"] for st in stats),
+                           "launches": sum(st["spmv_launches"] for st in stats)},
     }
     for k in kernels.values():
         k["share_of_step"] = k["s"] / (total_ms * 1e-3 / world) if total_ms > 0 else None
@@ -469,7 +479,7 @@ def main():
         "wall_s_to_converged": total_ms * 1e-3 / args.steps,
         "gpu_launches": int(launches),
         "roofline": (roofline_spmv(stats, hbm, peak_kind) if sum(st["spmv_s"] for st in stats) > trace_s
-                     else roofline(stats, trace_launches, hbm, peak_kind)),
+                     else roofline(stats, trace_launches, hbm, peak_kind, w.n * len(D.dirs))),
         "kernels": kernels,
         "clocks": clk,
         "e2e": e2e,

@@ -112,29 +112,42 @@ __global__ void __launch_bounds__(kSpmvThreads) k_spmv8(SpmvArgs A)
     }
 }
 
-// FP32 columns from chunked lists: one warp per ray, one entry per lane in
-// each chunk of kChunkEntries (32), following the row's links; the next link
-// is read before the chunk's entries so that its latency overlaps them.
+// FP32 columns from chunked lists: four rays per warp, eight lanes per ray
+// and four entries per lane in each chunk of kChunkEntries (32), each group
+// following its own row's links, so that a warp keeps four chains of
+// dependent loads in flight; the next link is read before the chunk's entries.
+constexpr int kChunkLanes = 8;
 __global__ void __launch_bounds__(kSpmvThreads) k_spmv_chunk(SpmvArgs A)
 {
     const int lane = threadIdx.x & 31;
-    const int64_t warps = (int64_t)gridDim.x * (kSpmvThreads / 32);
+    const int sub = lane & (kChunkLanes - 1);
+    const int64_t groups = (int64_t)gridDim.x * (kSpmvThreads / kChunkLanes);
     const int64_t total = (int64_t)A.R * A.n_items;
     const float* xv = static_cast<const float*>(A.xvec);
     float* out = static_cast<float*>(A.out);
-    for (int64_t w = (int64_t)blockIdx.x * (kSpmvThreads / 32) + (threadIdx.x >> 5); w < total; w += warps) {
-        const int64_t k = w / A.n_items;
-        const int64_t a = w - k * A.n_items;
-        const int64_t i = A.items ? (int64_t)A.items[a] : a;
-        const int64_t row = k * A.n_rows_per_k + i;
-        const uint32_t cnt = A.row_cnt[row];
+    // every lane of the warp loops alike (the group count per warp is fixed)
+    const int64_t first = ((int64_t)blockIdx.x * kSpmvThreads + threadIdx.x) / kChunkLanes;
+    for (int64_t w0 = first - (lane / kChunkLanes); w0 < total; w0 += groups) {
+        const int64_t w = w0 + lane / kChunkLanes;
+        uint32_t cnt = 0, ch = 0;
+        int64_t a = 0, k = 0;
+        if (w < total) {
+            k = w / A.n_items;
+            a = w - k * A.n_items;
+            const int64_t i = A.items ? (int64_t)A.items[a] : a;
+            const int64_t row = k * A.n_rows_per_k + i;
+            cnt = A.row_cnt[row];
+            ch = cnt ? A.chunk_head[row] : 0u;
+        }
         float s = 0.f, c = 0.f;
-        uint32_t ch = cnt ? A.chunk_head[row] : 0u;
         for (uint32_t done = 0; done < cnt; done += kChunkEntries) {
             const uint32_t nxt = done + kChunkEntries < cnt ? __ldg(A.chunk_next + ch) : 0u;
-            if (done + (uint32_t)lane < cnt) {
-                const int2 q = __ldcs(A.chunk_seg + (int64_t)ch * kChunkEntries + lane);
-                const float t = __int_as_float(q.y) * __ldg(xv + q.x);
+            const int4* q4 = reinterpret_cast<const int4*>(A.chunk_seg + (int64_t)ch * kChunkEntries + 4 * sub);
+            const uint32_t at = done + 4u * (uint32_t)sub;
+            if (at < cnt) {            // rows hold whole multiples of kSegPad (8) entries
+                const int4 p = __ldcs(q4), r = __ldcs(q4 + 1);
+                const float t = (__int_as_float(p.y) * __ldg(xv + p.x) + __int_as_float(p.w) * __ldg(xv + p.z)) +
+                                (__int_as_float(r.y) * __ldg(xv + r.x) + __int_as_float(r.w) * __ldg(xv + r.z));
                 const float y = t - c;
                 const float u = s + y;
                 c = (u - s) - y;
@@ -144,8 +157,8 @@ __global__ void __launch_bounds__(kSpmvThreads) k_spmv_chunk(SpmvArgs A)
         }
         s -= c;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) out[a + k * A.n_items] = s;
+        for (int o = kChunkLanes / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (sub == 0 && w < total) out[a + k * A.n_items] = s;
     }
 }
 

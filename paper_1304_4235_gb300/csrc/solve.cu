@@ -940,17 +940,19 @@ void Solver::spmv_lists(SpmvArgs& A) const
     }
 }
 
-// Origins i * stride for the hit-count sample of trace_chunked.
-__global__ void k_strided(int32_t* out, int64_t m, int64_t stride)
+// The hit-count sample of trace_chunked: the first 32 Morton slots of every
+// block of 32 * stride (a packet of neighbouring origins, traced as coherently
+// as in the full traversal), up to n.
+__global__ void k_sample_origins(int32_t* out, int64_t m, int64_t stride)
 {
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < m; t += (int64_t)gridDim.x * blockDim.x)
-        out[t] = (int32_t)(t * stride);
+        out[t] = (int32_t)((t / 32) * 32 * stride + (t % 32));
 }
 
 // The first sweep's traversal of every particle, storing each ray's segments
 // in chunks as it goes (MODE_CHUNK).  The number of segments is not known in
-// advance: it is estimated from the hit counts of a sample of every 64th
-// origin, with room for 15 % more, for half a chunk per ray and for the
+// advance: it is estimated from the hit counts of a sample of 1/64 of the
+// origins (32 neighbouring slots in every 2048), with room for 15 % more, for half a chunk per ray and for the
 // warps' unused blocks.  When the lists do not fit, or the estimate proves
 // short (some rays' lists are then incomplete), the lists are dropped and the
 // solve goes on as without them: the columns and counts of this traversal are
@@ -958,7 +960,8 @@ __global__ void k_strided(int32_t* out, int64_t m, int64_t stride)
 int Solver::trace_chunked(TraceJob& job)
 {
     const int64_t rays = (int64_t)P.R * n;
-    const int64_t stride = 64, m = (n + stride - 1) / stride;
+    const int64_t stride = 64, block = 32 * stride, nb = (n + block - 1) / block;
+    const int64_t m = (nb - 1) * 32 + std::min<int64_t>(32, n - (nb - 1) * block);
     const double entry_bytes = 8.0;               // particle index + value
     uint64_t* total = reinterpret_cast<uint64_t*>(misc + 6);
     unsigned long long cap = 0;
@@ -967,7 +970,7 @@ int Solver::trace_chunked(TraceJob& job)
         URCHIN_TRY(smp.alloc(sizeof(int32_t) * (size_t)m, s));
         int32_t* org = smp.at<int32_t>(0);
         const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>((m + 255) / 256, 4096));
-        k_strided<<<g, 256, 0, s>>>(org, m, stride);
+        k_sample_origins<<<g, 256, 0, s>>>(org, m, stride);
         URCHIN_TRY(launched());
         TraceJob cj = job;
         cj.items = org;

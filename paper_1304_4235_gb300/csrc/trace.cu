@@ -566,7 +566,7 @@ __device__ __noinline__ void flush_partials(const TraceParams& P, const float2* 
             const bool near = NF && (it.owner & kPQNear);
             v = near ? A * F : __ldg(P.w32 + it.j) * F;
             if (MODE == MODE_FILL && !near) static_cast<float*>(P.seg_val)[it.pos] = A * F;
-            if (MODE == MODE_CHUNK && it.pos >= 0) P.chunk_seg[it.pos].y = __float_as_int(A * F);
+            if (MODE == MODE_CHUNK && it.pos >= 0) P.chunk_seg[it.pos] = make_int2(it.j, __float_as_int(A * F));
             owner = it.owner & (31 | kPQNear);
         }
     }
@@ -717,9 +717,8 @@ __device__ __forceinline__ void leaf_hits_f32(const TraceParams& P, const float2
             }
             spos = -1;
             if (store && k.pos >= 0) {
-                // a partial chord's value follows at the flush
+                // a partial chord's entry is written whole at the flush
                 if (!part) P.chunk_seg[k.pos] = make_int2(j, __float_as_int(segv));
-                else P.chunk_seg[k.pos].x = j;
                 spos = k.pos++;
             }
         }
