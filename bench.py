@@ -72,9 +72,9 @@ def workload_name(key: str, w) -> str:
 # files at capture time; a changed kernel reports traffic null.
 #   k_trace: bytes per ray-sphere hit;  k_spmv: bytes per stored segment
 MEASURED_TRAFFIC = {
-    # the 256^3 box's own sweep-0 launch (one-pass capture): 7.34e9 + 3.16e9
-    # DRAM bytes for 1.762e10 hits
-    "k_trace": {"7e6723a718a4b0cf": 0.595},
+    # the 256^3 box's own traversal (one-pass capture), which also stores the
+    # segment lists: 53.7e9 + 211.2e9 DRAM bytes for 1.762e10 hits
+    "k_trace": {"b0244c427093223b": 15.04},
     "k_spmv": {},
 }
 KERNEL_SOURCES = {"k_trace": ("trace.cu", "common.cuh"), "k_spmv": ("linalg.cu", "linalg.cuh")}

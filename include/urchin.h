@@ -81,7 +81,14 @@ typedef struct CUstream_st* urchin_stream_t;
 #define URCHIN_SEG_AUTO         2     /* store when the lists fit in memory     */
 /* A stored segment is the FP32 value and the particle's Morton index split
  * into 16 + 8 bits (7 bytes; n <= 2^24), or FP64 value and int32 index (12
- * bytes); each ray's list is padded with zero entries to a multiple of 8. */
+ * bytes); each ray's list is padded with zero entries to a multiple of 8.
+ * URCHIN_SEG_AUTO in FP32 (no near/far split, blocks <= 1) keeps the lists
+ * of the first sweep's traversal itself, in linked chunks of 32 (index,
+ * value) pairs of 8 bytes sized from a sampled estimate, so that a solve of
+ * two sweeps traces once; from the fourth sweep the active rows are copied
+ * into the 7-byte row layout when both fit.  When the chunks do not fit or
+ * the estimate proves short, the lists are stored from the third sweep (a
+ * counting and a filling traversal) where they fit, else every sweep traces. */
 
 #define URCHIN_MAX_RAYS       192     /* HEALPix N_side <= 4                    */
 #define URCHIN_MAX_BINS      4096     /* frequency bins                         */
