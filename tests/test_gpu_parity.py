@@ -315,9 +315,10 @@ def test_solve_full_size_halo_one_sweep_sampled(segments):
     """Benchmark-size halo: sweeps 1-4 of the GPU at 256 seeded particles
     against the oracle's update of the GPU's previous state, per particle
     within check_sweep's error model.  With SEG_AUTO, sweep 0 traces every
-    particle and keeps each ray's segment list in linked chunks of 32
-    (FP32 values, 24-bit particle indices split into 16 + 8 bits), taken
-    while tracing; sweeps 1-3 read their columns from those lists."""
+    particle and keeps each ray's segment list (particle index, FP32 value)
+    in linked chunks of 32 taken while tracing; sweeps 1-2 read their
+    columns from the chunks and sweep 3 from the 7-byte rows (24-bit
+    particle indices split into 16 + 8 bits) the chunks are copied into."""
     w = W.halo()
     bvh, d = build(w, torch)
     sg, so = spectra(w, torch)
