@@ -73,8 +73,8 @@ def workload_name(key: str, w) -> str:
 #   k_trace: bytes per ray-sphere hit;  k_spmv: bytes per stored segment
 MEASURED_TRAFFIC = {
     # the 256^3 box's own traversal (one-pass capture), which also stores the
-    # segment lists: 53.7e9 + 211.2e9 DRAM bytes for 1.762e10 hits
-    "k_trace": {"b0244c427093223b": 15.04},
+    # segment lists: 34.2e9 + 180.7e9 DRAM bytes for 1.762e10 hits
+    "k_trace": {"22dc0f23cad58a84": 12.20},
     "k_spmv": {},
 }
 KERNEL_SOURCES = {"k_trace": ("trace.cu", "common.cuh"), "k_spmv": ("linalg.cu", "linalg.cuh")}

@@ -96,7 +96,11 @@ struct Sink {
     double ox, oy, oz;            // near/far: shifted origin in double (the near test)
     uint32_t lo_pend, hi_pend;    // MODE_FILL, split indices: halves / bytes of the current word
     int64_t ray;                  // MODE_CHUNK: row k n + origin slot
+    int2* cw;                     // MODE_CHUNK: the ray's current chunk
+    int coff;                     // MODE_CHUNK: entries used in it (kChunk: none or full; kChunk + 1: pool exhausted)
+    uint32_t cur;                 // MODE_CHUNK: its index (kNoChunk before the first)
 };
+constexpr uint32_t kNoChunk = 0xffffffffu;
 
 // Near/far split (Sec. 3.3.3): particle j is near the ray's origin when the
 // origin lies inside j's smoothing sphere.  For a crossed sphere that is the
@@ -545,10 +549,13 @@ __host__ __device__ __forceinline__ size_t trace_queue_offset(int R, int kernel)
 }
 
 // Evaluate the first n (<= 32) queued chords, one per lane, and move the
-// rest to the front.  Every lane of the warp calls it.
+// rest to the front.  Every lane of the warp calls it.  Inlined: as a called
+// function its reference arguments kept the ray's running state (sums,
+// cursor, queue length) in local memory for the whole traversal, which cost
+// 7 % of the traversal's time.
 template <int KERNEL, int MODE, bool NF>
-__device__ __noinline__ void flush_partials(const TraceParams& P, const float2* tab, PartQueue* pq, int& count, int n,
-                                            Sink<float>& k)
+__device__ __forceinline__ void flush_partials(const TraceParams& P, const float2* tab, PartQueue* pq, int& count,
+                                               int n, Sink<float>& k)
 {
     const int lane = threadIdx.x & 31;
     int owner = -1;
@@ -697,7 +704,7 @@ __device__ __forceinline__ void leaf_hits_f32(const TraceParams& P, const float2
             // with the warp converged: a new chunk for every ray whose chunk
             // is full (or that has none yet), then the segment's index (and a
             // full chord's value; a partial chord's at the flush)
-            const bool need = store && k.pos >= 0 && k.pos == k.end;
+            const bool need = store && k.coff == kChunk;
             const unsigned nm = __ballot_sync(0xffffffffu, need);
             if (nm) {
                 unsigned long long base = 0;
@@ -706,20 +713,22 @@ __device__ __forceinline__ void leaf_hits_f32(const TraceParams& P, const float2
                 if (need) {
                     const unsigned long long c = base + (unsigned long long)__popc(nm & ((1u << lane) - 1u));
                     if (c < P.chunk_cap) {
-                        if (k.end == 0) P.chunk_head[k.ray] = (uint32_t)c;
-                        else P.chunk_next[(k.end - 1) / kChunk] = (uint32_t)c;
-                        k.pos = (int64_t)c * kChunk;
-                        k.end = k.pos + kChunk;
+                        if (k.cur == kNoChunk) P.chunk_head[k.ray] = (uint32_t)c;
+                        else P.chunk_next[k.cur] = (uint32_t)c;
+                        k.cur = (uint32_t)c;
+                        k.cw = P.chunk_seg + c * (unsigned long long)kChunk;
+                        k.coff = 0;
                     } else {
-                        k.pos = k.end = -1;         // the pool is exhausted: this ray stores no more
+                        k.coff = kChunk + 1;        // the pool is exhausted: this ray stores no more
                     }
                 }
             }
             spos = -1;
-            if (store && k.pos >= 0) {
+            if (store && k.coff < kChunk) {
                 // a partial chord's entry is written whole at the flush
-                if (!part) P.chunk_seg[k.pos] = make_int2(j, __float_as_int(segv));
-                spos = k.pos++;
+                if (!part) k.cw[k.coff] = make_int2(j, __float_as_int(segv));
+                else spos = (int64_t)k.cur * kChunk + k.coff;
+                ++k.coff;
             }
         }
         const unsigned pb = __ballot_sync(0xffffffffu, part);
@@ -883,8 +892,11 @@ __device__ void ray_column(const TraceParams& P, const float2* tab, Beam* beam, 
     }
 }
 
+// Three blocks of 256 per SM (80 registers a thread): with four (64
+// registers) the spills cost more than the fourth block's warps hide; with
+// two (no spills) too few warps are left to hide the loads.
 template <typename Real, int KERNEL, int MODE, bool NF>
-__global__ void __launch_bounds__(256, 4) k_trace(TraceParams P)
+__global__ void __launch_bounds__(256, 3) k_trace(TraceParams P)
 {
     extern __shared__ double s_dirs[];
     float2* s_tab = reinterpret_cast<float2*>(s_dirs + 3 * P.R);
@@ -934,6 +946,9 @@ __global__ void __launch_bounds__(256, 4) k_trace(TraceParams P)
         // of particles not in the item list stay empty)
         const int64_t ray = (int64_t)k * P.n + org;
         sk.ray = ray;
+        sk.cw = nullptr;
+        sk.coff = kChunk;
+        sk.cur = kNoChunk;
         const int64_t orow = live ? (P.out_row ? (int64_t)P.out_row[item] : item) : 0;
         if (live && MODE == MODE_FILL) {
             sk.pos = (int64_t)P.row_ptr[ray];
@@ -955,9 +970,9 @@ __global__ void __launch_bounds__(256, 4) k_trace(TraceParams P)
             if (MODE == MODE_COUNT || MODE == MODE_CHUNK || (MODE == MODE_TAU && P.counts))
                 P.counts[ray] = (sk.nhit + (unsigned)kSegPad - 1u) / (unsigned)kSegPad * (unsigned)kSegPad;
             if (MODE != MODE_COUNT && MODE != MODE_SCATTER) {
-                if (MODE == MODE_CHUNK && sk.pos >= 0) {
+                if (MODE == MODE_CHUNK && sk.coff < kChunk) {
                     // zero entries up to a multiple of kSegPad (inside the chunk)
-                    for (; (sk.pos & (int64_t)(kSegPad - 1)) != 0; ++sk.pos) P.chunk_seg[sk.pos] = make_int2(0, 0);
+                    for (; (sk.coff & (kSegPad - 1)) != 0; ++sk.coff) sk.cw[sk.coff] = make_int2(0, 0);
                 }
                 if (MODE == MODE_FILL) {
                     // the padding (fewer than kSegPad entries) holds zero values
