@@ -894,9 +894,10 @@ __device__ void ray_column(const TraceParams& P, const float2* tab, Beam* beam, 
 
 // Three blocks of 256 per SM (80 registers a thread): with four (64
 // registers) the spills cost more than the fourth block's warps hide; with
-// two (no spills) too few warps are left to hide the loads.
+// two (no spills) too few warps are left to hide the loads.  The transpose
+// keeps four: its FP64 atomic adds want the warps more than the registers.
 template <typename Real, int KERNEL, int MODE, bool NF>
-__global__ void __launch_bounds__(256, 3) k_trace(TraceParams P)
+__global__ void __launch_bounds__(256, MODE == MODE_SCATTER ? 4 : 3) k_trace(TraceParams P)
 {
     extern __shared__ double s_dirs[];
     float2* s_tab = reinterpret_cast<float2*>(s_dirs + 3 * P.R);
