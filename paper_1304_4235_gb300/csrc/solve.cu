@@ -180,11 +180,13 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep_pp(SweepArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr bool kF32 = sizeof(Real) == 4;
-    Real* e2 = reinterpret_cast<Real*>(smem_raw);
-    Real* wn = e2 + A.F;
-    Real* e2t = kF32 ? wn + A.F : nullptr;
+    // FP32: the packed coefficients {e2, e2t, wn, 0} of fold_ray_q4; FP64:
+    // e2 and wn
+    float4* q4 = kF32 ? reinterpret_cast<float4*>(smem_raw) : nullptr;
+    Real* e2 = kF32 ? nullptr : reinterpret_cast<Real*>(smem_raw);
+    Real* wn = kF32 ? nullptr : e2 + A.F;
     __shared__ double sh[2];
-    fold_prepare<Real>(A.s, A.w, A.F, e2, e2t, wn, nullptr, sh);
+    fold_prepare<Real>(A.s, A.w, A.F, e2, nullptr, wn, nullptr, sh, q4);
     const double gthin = sh[0];
     const double smin = sh[1];
     const Real* tau = static_cast<const Real*>(A.tau);
@@ -197,7 +199,8 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep_pp(SweepArgs A)
         for (int k = 0; k < A.R; ++k) {
             const Real t = tau[row + (int64_t)k * A.k_stride];
             Real S, S2;
-            fold_ray<false>(t, e2, e2t, wn, nullptr, A.F, S, S2);
+            if constexpr (kF32) S = fold_ray_q4(t, q4, A.F);
+            else fold_ray<false>(t, e2, nullptr, wn, nullptr, A.F, S, S2);
             lse.add(ray_lnrate(smin, t, S));
         }
         double xn, G, alpha;
@@ -619,8 +622,8 @@ int launch_sweep(const SweepArgs& A, cudaStream_t s)
     // plain sweeps without tangent: one thread per particle (0.152 ms against
     // 0.184 ms per sweep of the 262144-particle halo for the ray-parallel layout)
     if (!A.he && !A.near_far && !A.want_tangent) {
-        // e2, wn and (FP32) the tail e2t
-        const size_t sm = (A.precision == URCHIN_F64 ? 2 : 3) * (size_t)A.F * rsz;
+        // e2 and wn (FP64), or the packed {e2, e2t, wn, 0} (FP32)
+        const size_t sm = (A.precision == URCHIN_F64 ? 2 : 4) * (size_t)A.F * rsz;
         const void* fp = A.precision == URCHIN_F64 ? (const void*)k_sweep_pp<double> : (const void*)k_sweep_pp<float>;
         if (sm > 48 * 1024)
             URCHIN_TRY_CUDA(cudaFuncSetAttribute(fp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));

@@ -31,9 +31,11 @@ __device__ __forceinline__ double log_p(double x) { return log(x); }
 // Block-wide preparation in shared memory (every thread of the block calls
 // it; at most 1024 threads): sh[0] = Gamma_thin = sum_j w_j, sh[1] = s_min,
 // e2 and wn as above, e2t the FP32 tail (NULL in FP64), sj = s_j (or NULL).
+// With q4 (FP32), the same e2, e2t and wn are written packed, q4[j] =
+// {e2, e2t, wn, 0}, for fold_ray_q4, and e2, e2t and wn are not written.
 template <typename Real>
 __device__ void fold_prepare(const double* s, const double* w, int F, Real* e2, Real* e2t, Real* wn, Real* sj,
-                             double* sh)
+                             double* sh, float4* q4 = nullptr)
 {
     __shared__ double red[32][2];
     double tot = 0.0, smin = 1e300;
@@ -63,9 +65,14 @@ __device__ void fold_prepare(const double* s, const double* w, int F, Real* e2, 
     const double g = sh[0], m = sh[1];
     for (int j = threadIdx.x; j < F; j += blockDim.x) {
         const double c = (s[j] - m) * 1.4426950408889634;
-        e2[j] = (Real)c;
-        if (e2t) e2t[j] = (Real)(c - (double)(Real)c);
-        wn[j] = (Real)(w[j] / g);
+        if (q4) {
+            const float h = (float)c;
+            q4[j] = make_float4(h, (float)(c - (double)h), (float)(w[j] / g), 0.f);
+        } else {
+            e2[j] = (Real)c;
+            if (e2t) e2t[j] = (Real)(c - (double)(Real)c);
+            wn[j] = (Real)(w[j] / g);
+        }
         if (sj) sj[j] = (Real)s[j];
     }
     __syncthreads();
@@ -100,6 +107,27 @@ __device__ __forceinline__ void fold_ray(float tau, const float* e2, const float
     }
     S_out = S;
     S2_out = S2;
+}
+
+// fold_ray<false> in FP32 with each bin's three coefficients read as one
+// 16-byte word, q = {e2, e2t, wn, 0} (the same arithmetic in the same order,
+// so the same S bit for bit; one shared-memory load per bin instead of three).
+__device__ __forceinline__ float fold_ray_q4(float tau, const float4* q4, int F)
+{
+    tau = tau < 1e30f ? tau : (tau == tau ? 1e30f : tau);
+    float S = 0.f, c = 0.f;
+    for (int j = 0; j < F; ++j) {
+        const float4 q = q4[j];
+        const float p = q.x * tau;
+        const float err = fmaf(q.y, tau, fmaf(q.x, tau, -p));
+        const float v0 = q.z * exp2f(-p);
+        const float v = fmaf(-v0, err * 0.6931471805599453f, v0);
+        const float yy = v - c;
+        const float t = S + yy;
+        c = (t - S) - yy;
+        S = t;
+    }
+    return S;
 }
 
 template <bool kTan>
@@ -221,15 +249,26 @@ struct Rates {
 //   alpha_B = 2.753e-14 lambda^1.500 / [1 + (lambda/2.740)^0.407]^2.242
 //   gamma   = 21.11 T^-3/2 e^(-lambda/2) lambda^-1.089 / [1 + (lambda/0.354)^0.874]^1.101
 // (App. C3 names fits of this kind for the temperature dependence.)
+// Evaluated with one logarithm, six exponentials and three log1p (FP64 is the
+// slow path of this GPU; no pow, no logarithm of a constant): each bracket as
+// exp(-p log1p((lambda/c)^q)), the powers of lambda from ll = ln lambda, and
+// ln T = ln 315614 - ll.
 __device__ __forceinline__ Rates hg97_rates(double T)
 {
+    constexpr double kLn0522 = -0.6500876910994983;     // ln 0.522
+    constexpr double kLn2740 = 1.007957920399979;       // ln 2.740
+    constexpr double kLn0354 = -1.0384583658483626;     // ln 0.354
+    constexpr double kLn2THI = 12.662275226919286;      // ln 315614
     const double lam = 315614.0 / T;
     const double ll = log(lam);
+    const double uA = exp(0.470 * (ll - kLn0522));
+    const double uB = exp(0.407 * (ll - kLn2740));
+    const double uC = exp(0.874 * (ll - kLn0354));
     Rates r;
-    r.alphaA = 1.269e-13 * exp(1.503 * ll) / pow(1.0 + exp(0.470 * (ll - log(0.522))), 1.923);
-    r.alphaB = 2.753e-14 * exp(1.500 * ll) / pow(1.0 + exp(0.407 * (ll - log(2.740))), 2.242);
-    r.gamma_c = 21.11 * pow(T, -1.5) * exp(-0.5 * lam - 1.089 * ll) /
-                pow(1.0 + exp(0.874 * (ll - log(0.354))), 1.101);
+    r.alphaA = 1.269e-13 * exp(1.503 * ll - 1.923 * log1p(uA));
+    r.alphaB = 2.753e-14 * exp(1.500 * ll - 2.242 * log1p(uB));
+    // T^-3/2 lambda^-1.089 = exp(-1.5 (ln 315614 - ll) - 1.089 ll)
+    r.gamma_c = 21.11 * exp(-1.5 * kLn2THI + 0.411 * ll - 0.5 * lam - 1.101 * log1p(uC));
     return r;
 }
 
