@@ -615,8 +615,6 @@ __device__ __forceinline__ unsigned long long chunk_block(const TraceParams& P, 
 }
 
 // FP32 hit evaluation: cheap rejection, then the impact parameter from an
-// error-free cross product, then the tabulated / piecewise chord integral.
-// FP32 hit evaluation: cheap rejection, then the impact parameter from an
 // error-free cross product; full chords from the table at once, partial
 // chords queued for flush_partials.  Every lane of the warp calls it (the
 // queue is shared); lanes that are not live only take part in the queue.
