@@ -11,13 +11,15 @@ One step = one full solve of the hot path: BVH build, then the Sec. 4
 iteration from x_thin to the paper's stopping test (max |dx|/x < 1e-3), each
 sweep tracing every active particle's 12 rays (Eq. colden, FP32 columns),
 folding them through the spectrum (Eq. gamma_shld) and updating x in FP64
-(Eq. xroots); segment lists stored once a solve runs past two sweeps and
-they fit in HBM (the box converges in two sweeps, so its columns are
-recomputed).  Metric: rays/s and particle-updates/s, whole job.  Beside it
-(untimed by the step count, CUDA events): wall time to x within rel 1e-3 of
-a tightly converged x* for plain sweeps and for Newton-Krylov, the adjoint
-gradient with recomputed segments, the 262144-particle halo and the
-differentiation workload.
+(Eq. xroots).  Sweep 0's traversal also keeps every ray's segment list
+where it fits in HBM, and later sweeps read their columns from the lists
+(the box converges in two sweeps: one traversal and one product).  Metric:
+rays/s and particle-updates/s, whole job.  Beside it (untimed by the step
+count, CUDA events): wall time to x within rel 1e-3 of a tightly converged
+x* for plain sweeps and for Newton-Krylov, the adjoint gradient with
+recomputed and with stored segments, the 262144-particle halo, the
+differentiation workload, the 128^3 box with helium, and the plain FP64
+method on the 4096-particle lattice beside the oracle solving it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload c5|halo|c5_eighth|halo_65536] [--no-compare] [--no-cpu-baseline] [--no-e2e]
@@ -493,6 +495,8 @@ def main():
         r = ors.sample(args.cpu_seconds, 7)
         line["cpu_baseline"] = {"value": r["rays"] / r["seconds"], "unit": "rays/s", "cores": r["cores"],
                                 "kind": "oracle-grid", "sample": ors.describe(r) + f", {r['seconds']:.1f} s"}
+        if "compare" in line:
+            line["compare"]["lattice_fp64"] = lattice_fp64(args, dev, stream)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -664,6 +668,50 @@ def cosmological_box(args, dev, stream):
             "rays": st["rays"], "rays_per_s": st["rays"] / dt, "particle_updates_per_s": st["particle_updates"] / dt,
             "segments_stored": bool(st["segments_stored"]), "trace_s": st["trace_s"], "spmv_s": st["spmv_s"],
             "sweep_s": st["sweep_s"], "hits": st["hits"]}
+
+
+def lattice_fp64(args, dev, stream):
+    """The plain FP64 method on the 4096-particle jittered lattice (16^3 in a
+    periodic 1 Mpc box, n_H 1.5e-3 cm^-3, 12 rays of 500 kpc, 50 bins): BVH
+    build + FP64 plain sweeps from x_thin to max |dx|/x < 1e-3 on the GPU
+    (CUDA events), and beside it, as this workload's CPU baseline, the FP64
+    oracle solving the same problem to the same tolerance by brute force on
+    all host cores, with the largest relative difference of the two x."""
+    import traceback
+
+    import oracle as O
+    import workloads as W
+    out = {"workload": "lattice_16cube_L1000kpc_nside1_l500kpc_F50", "precision": "f64", "method": "plain",
+           "tol": 1e-3}
+    try:
+        w = W.lattice_box()
+        D = Device(w, dev)
+        U = D.U
+
+        def go():
+            bvh = D.bvh()
+            x, st = D.solve(bvh, tol=1e-3, max_iter=args.max_iter, precision=U.F64, profile=True)
+            bvh.close()
+            return x, st
+        go()
+        (x, st), dt = timed(stream, go)
+        xg = x.cpu().numpy()
+        out.update({"wall_s": dt, "iterations": st["iterations"], "converged": bool(st["converged"]),
+                    "rays": st["rays"], "rays_per_s": st["rays"] / dt,
+                    "particle_updates_per_s": st["particle_updates"] / dt})
+        e, J = w.spectrum()
+        s, wts = O.spectrum(e, J, w.gamma_thin)
+        t0 = time.perf_counter()
+        xo, _, info = O.solve(w, s, wts, O.healpix(w.nside), tol=1e-3)
+        to = time.perf_counter() - t0
+        out["oracle"] = {"kind": "oracle", "search": "brute force", "cores": O.num_threads(), "wall_s": to,
+                         "iterations": int(info["sweeps"]), "converged": bool(info["converged"]),
+                         "rays": float(info["rays"]), "rays_per_s": float(info["rays"]) / to}
+        out["max_rel_gpu_vs_oracle"] = float(np.max(np.abs(xg - xo) / xo))
+    except Exception as exc:       # a failed side comparison must not cost the benchmark line
+        traceback.print_exc()
+        out["error"] = f"{type(exc).__name__}: {exc}"
+    return out
 
 
 def compare(args, key, w, D, stream):
